@@ -1,0 +1,25 @@
+"""FP64 CPU oracle of the augmented-Lagrangian (ADMM) dynamic-SENSE method.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The CUDA library
+never calls it, and it shares no code with the CUDA path.
+
+Plain NumPy complex128 restatement of Bilen, Wang & Selesnick, "High Speed
+Compressed Sensing Reconstruction in Dynamic Parallel MRI Using Augmented
+Lagrangian and Parallel Processing":
+
+* operators H, H' of the Cartesian multi-coil model (Section II-A, Eqs.
+  mri_csmcoill, H_1, S, F)
+* complex soft threshold (Section III, definition of S(a, tau))
+* per-column Gram blocks and the exact inverse (mu I + H'H)^{-1}
+  (Section IV-C, Eqs. HconjH, separate_x, eigen_mu)
+* Algorithm 1 (synthesis prior, temporal DFT) and Algorithm 2 (analysis prior,
+  temporal TV), step by step in the paper's order
+* objective J and the convergence ratio Delta(k) (Section V, Eq. r_ratio)
+
+Every function here is pinned by a ``-m "not gpu"`` test in
+``tests/test_oracle_pins.py`` against closed forms, brute force or invariants.
+"""
+
+from .admm import *  # noqa: F401,F403
+from .admm import __all__  # noqa: F401
