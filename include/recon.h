@@ -1,0 +1,183 @@
+/*
+ * recon.h - C ABI of the GB300 dynamic-SENSE ADMM reconstruction library.
+ *
+ * Method: Bilen, Wang & Selesnick, "High Speed Compressed Sensing
+ * Reconstruction in Dynamic Parallel MRI Using Augmented Lagrangian and
+ * Parallel Processing".  The library solves
+ *
+ *   analysis prior   (Eq. L1an_pri, R = temporal TV, Algorithm 2)
+ *       min_x  lambda ||D_t x||_1 + ||y - H x||^2
+ *   synthesis prior  (Eq. L1unconst, Psi = unitary temporal DFT, Algorithm 1)
+ *       min_w  lambda ||w||_1 + ||y - H Psi' w||^2,   x = Psi' w
+ *
+ * for Cartesian ky-t undersampled multi-coil data, y_{t,c} = M_{v,t} F_h F_v
+ * (s_c . x_t) + n (Eqs. mri_csmcoill, H_1, S, F).  The data-consistency
+ * inverse (mu I + H'H)^{-1} is applied exactly, one dense Hermitian
+ * Ny x Ny block per image column and frame (Section IV-C, Eqs. HconjH,
+ * eigen_mu).
+ *
+ * Conventions shared by every entry point
+ *   - Complex arrays are interleaved complex64: element k is (re, im) at
+ *     float offsets 2k, 2k+1.  Row-major, last index fastest:
+ *       mask    uint8  [Nt][Ny]          (or [Nt][Ny][Nx], see opts.mask_full)
+ *       sens    c64    [Nc][Ny][Nx]
+ *       kspace  c64    [Nt][Nc][Ny][Nx]  (ky rows; unsampled rows are ignored)
+ *       image   c64    [Nt][Ny][Nx]
+ *     Index j (0..Ny-1) is the vertical / ky axis, i (0..Nx-1) the horizontal
+ *     / kx axis.  ky indices are in FFT order (row 0 is ky = 0).
+ *   - All Fourier transforms are unitary: forward exp(-2 pi i k n / N) / sqrt(N).
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Calls are stream-ordered; unless stated otherwise they return
+ *     after enqueueing the work.
+ *   - Pointers marked "device" must be device (or managed) memory of the
+ *     current device.  The caller owns every buffer it passes; the library
+ *     only reads inputs during the call and keeps no reference to them.
+ *   - Every function returns a recon_status; no function throws or aborts.
+ *     recon_last_error() gives a human-readable reason for the last failure
+ *     of the calling thread.
+ */
+#ifndef RECON_H
+#define RECON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct recon_plan recon_plan; /* opaque, owned by the library */
+
+typedef enum {
+  RECON_PRIOR_TV = 0,  /* Algorithm 2: analysis prior, R = D_t (non-circular temporal differences) */
+  RECON_PRIOR_DFT = 1  /* Algorithm 1: synthesis prior, Psi = unitary temporal DFT */
+} recon_prior;
+
+typedef enum {
+  RECON_OK = 0,
+  RECON_ERR_INVALID_ARG = 1,        /* bad size, pointer or parameter */
+  RECON_ERR_MASK_NOT_CARTESIAN = 2, /* a full [Nt][Ny][Nx] mask that differs along kx */
+  RECON_ERR_OOM = 3,                /* device allocation failed */
+  RECON_ERR_CUDA = 4,               /* a CUDA call failed (see recon_last_error) */
+  RECON_ERR_TIMEOUT = 5,            /* a bounded device-side wait gave up */
+  RECON_ERR_NONFINITE = 6,          /* a non-finite objective or a non-positive-definite block */
+  RECON_ERR_UNSUPPORTED = 7         /* valid request this build does not support */
+} recon_status;
+
+typedef enum {
+  RECON_STORAGE_FP32 = 0, /* inverses stored as complex64 */
+  RECON_STORAGE_FP16 = 1, /* inverses stored as 2 x fp16, arithmetic in FP32 */
+  RECON_STORAGE_BF16 = 2  /* inverses stored as 2 x bf16, arithmetic in FP32 */
+} recon_storage;
+
+typedef struct {
+  float rho;        /* mu2 / mu1 for Algorithm 2 (default 0.5, Section V); ignored for DFT */
+  int max_iters;    /* iterations K (default 50); 0 returns H'y */
+  double tol;       /* stop when 0 <= Delta(k) < tol (Eq. r_ratio); 0 = run K iterations */
+  int storage;      /* recon_storage of the packed inverses (default FP32) */
+  int objective;    /* 1 = evaluate J(k) every iteration (default 1; forced on when tol > 0) */
+  int mask_full;    /* 1 = mask is [Nt][Ny][Nx] and must be constant along kx (default 0) */
+  int col_stages;   /* ring depth of the inverse kernel; 0 = autotuned (default 0) */
+  int profile;      /* 1 = time every kernel of a solve with CUDA events (default 0) */
+} recon_opts;
+
+typedef struct {
+  int iters;        /* iterations performed */
+  double J;         /* J(iters), NaN when the objective was off */
+  double J0;        /* J(0) at the initial point x = H'y */
+  double delta;     /* Delta(iters) = (J(iters-1) - J(iters)) / J(iters), NaN if undefined */
+  int stopped;      /* 1 when the tolerance test ended the run */
+} recon_info;
+
+/* Fills `opts` with the defaults listed above.  NULL-safe. */
+void recon_default_opts(recon_opts* opts);
+
+/* Builds a plan: validates the mask, copies sensitivities and the sampled row
+ * lists into plan-owned device memory and computes every packed inverse
+ * A_{i,t} = (mu2 I + G_{i,t})^{-1}, G_{i,t} = C_t (.) sum_c conj(s_{.,i,c}) s_{.,i,c}^T
+ * (Section IV-C; C_t = F_v' P_t F_v is circulant).  The factorisation runs in
+ * FP64 on the GPU and is rounded once to the storage type.
+ *   out     receives the plan (set to NULL on failure)
+ *   Nx, Ny, Nt, Nc >= 1
+ *   mask    host or device uint8, nonzero = sampled row (see opts.mask_full)
+ *   sens    host or device complex64 [Nc][Ny][Nx]
+ *   lambda  >= 0;  mu > 0: mu of Algorithm 1, mu2 of Algorithm 2 (mu1 = mu / rho)
+ *   opts    NULL for defaults
+ * Blocks until the plan is built (the factorisation is done once, outside
+ * the timed iterations, as in Section V).  Errors: INVALID_ARG,
+ * MASK_NOT_CARTESIAN, OOM, CUDA, NONFINITE (a block not positive definite). */
+recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc, const uint8_t* mask,
+                               const float* sens, float lambda, float mu, recon_prior prior,
+                               const recon_opts* opts, void* stream);
+
+/* Runs the reconstruction: H'y prologue (batched row/column IFFTs and coil
+ * combine), K ADMM iterations, and writes the image.
+ *   kspace  device complex64 [Nt][Nc][Ny][Nx]; entries on unsampled rows are ignored
+ *   image   device complex64 [Nt][Ny][Nx], written (x of Algorithm 2, Psi'w of Algorithm 1)
+ *   info    host, may be NULL.  When non-NULL the call synchronises `stream`
+ *           and fills it; otherwise it returns after enqueueing.
+ * Errors: INVALID_ARG, CUDA, TIMEOUT, NONFINITE (only reported when info != NULL). */
+recon_status recon_solve(recon_plan* plan, const float* kspace, float* image, recon_info* info, void* stream);
+
+/* Same as recon_solve with HOST buffers: copies kspace host->device, solves,
+ * copies the image device->host and synchronises `stream`.  Pinned host memory
+ * gives asynchronous, full-bandwidth copies; pageable memory works too.
+ *   kspace_host  complex64 [Nt][Nc][Ny][Nx];  image_host complex64 [Nt][Ny][Nx] */
+recon_status recon_solve_host(recon_plan* plan, const float* kspace_host, float* image_host, recon_info* info,
+                              void* stream);
+
+/* Copies J(0..n-1) of the last solve to `J_host` (synchronises the plan's
+ * last stream).  Entries past the last iteration are NaN. */
+recon_status recon_get_trace(recon_plan* plan, double* J_host, int n);
+
+/* Device time of the kernels of the last solve, from CUDA events recorded on
+ * the solve's stream when opts.profile == 1 (synchronises that stream).
+ * Fields are zero when profiling was off. */
+typedef struct {
+  double inverse_ms;      /* column-inverse kernel (x = A r + data-term epilogue), summed */
+  int inverse_launches;
+  double temporal_ms;     /* temporal kernel (prior step along t), summed */
+  int temporal_launches;
+  double solve_ms;        /* whole solve: prologue, iterations, output */
+} recon_profile;
+recon_status recon_get_profile(recon_plan* plan, recon_profile* out);
+
+/* Number of CUDA kernels this library has launched in this process. */
+unsigned long long recon_kernel_launches(void);
+
+/* Frees the plan and all its device memory.  NULL-safe. */
+recon_status recon_destroy(recon_plan* plan);
+
+/* ---- operators of the forward model (used by solves, exposed for tests and
+ *      for callers that compose their own iterations) ---------------------- */
+
+/* image = H' kspace = sum_c conj(s_c) . F_v' M_t' F_h' y_{t,c}  (adjoint of Eq. mri_csmcoill).
+ *   kspace device complex64 [Nt][Nc][Ny][Nx];  image device complex64 [Nt][Ny][Nx] */
+recon_status recon_apply_adjoint(recon_plan* plan, const float* kspace, float* image, void* stream);
+
+/* kspace = H image = M_t F_h F_v (s_c . x_t); unsampled rows are written as 0.
+ *   image device complex64 [Nt][Ny][Nx];  kspace device complex64 [Nt][Nc][Ny][Nx] */
+recon_status recon_apply_forward(recon_plan* plan, const float* image, float* kspace, void* stream);
+
+/* out = (mu I + H'H)^{-1} in, column by column with the packed inverses
+ * (Eq. eigen_mu).  in, out device complex64 [Nt][Ny][Nx]; may not alias. */
+recon_status recon_apply_inverse(recon_plan* plan, const float* in, float* out, void* stream);
+
+/* Unpacks A_{i,t} into a dense row-major Ny x Ny complex64 matrix (device
+ * `dense`), for inspection and tests.  0 <= i < Nx, 0 <= t < Nt. */
+recon_status recon_export_inverse(recon_plan* plan, int i, int t, float* dense, void* stream);
+
+/* Bytes of the packed inverses streamed per ADMM iteration. */
+size_t recon_inverse_bytes(const recon_plan* plan);
+
+/* Human-readable status name; never NULL. */
+const char* recon_status_string(recon_status s);
+
+/* Reason for the last failure on the calling thread ("" if none); never NULL. */
+const char* recon_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RECON_H */

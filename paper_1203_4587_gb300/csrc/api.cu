@@ -1,0 +1,725 @@
+// C ABI of the reconstruction library (include/recon.h).
+//
+// A plan owns every device buffer a solve needs, so recon_solve allocates
+// nothing.  One ADMM iteration enqueues: the temporal kernel (Algorithm 2's
+// v, m, d1 updates, or Algorithm 1's v, d and Psi/Psi' steps), the J(k-1)
+// finalize kernel (when the objective is on) and the column-inverse kernel
+// (x = (mu I + H'H)^{-1} r with the ||y - Hx||^2 epilogue).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/recon.h"
+#include "kernels.h"
+
+using namespace recon;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+recon_status fail(recon_status st, const std::string& why) {
+  g_last_error = why;
+  return st;
+}
+
+recon_status cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? RECON_ERR_OOM : RECON_ERR_CUDA;
+}
+
+#define RC(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+}  // namespace
+
+namespace recon {
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void fill_twiddles_host(int n, float2* tw) {
+  for (int k = 0; k < n; ++k) {
+    const double a = -2.0 * M_PI * (double)k / (double)n;
+    tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+}
+
+void fill_twiddles_host64(int n, double2* tw) {
+  for (int k = 0; k < n; ++k) {
+    const double a = -2.0 * M_PI * (double)k / (double)n;
+    tw[k] = make_double2(std::cos(a), std::sin(a));
+  }
+}
+
+template <typename T>
+static FftPlanT<T> fft_plan_t(int n, const T* d_tw) {
+  FftPlanT<T> P{};
+  P.n = n;
+  P.tw = d_tw;
+  int m = n, ns = 0;
+  const int pref[] = {4, 2, 3, 5, 7};
+  for (int r : pref) {
+    while (m % r == 0 && ns < kFftMaxStages) { P.radix[ns++] = r; m /= r; }
+  }
+  for (int r = 11; m > 1 && ns < kFftMaxStages; r += 2) {
+    while (m % r == 0) { P.radix[ns++] = r; m /= r; }
+  }
+  P.ns = ns;
+  return P;
+}
+
+FftPlanDev make_fft_plan_host(int n, const float2* d_tw) { return fft_plan_t<float2>(n, d_tw); }
+FftPlanDev64 make_fft_plan_host64(int n, const double2* d_tw) { return fft_plan_t<double2>(n, d_tw); }
+
+}  // namespace recon
+
+struct recon_plan {
+  int Nx = 0, Ny = 0, Nt = 0, Nc = 0;
+  recon_prior prior = RECON_PRIOR_TV;
+  float lam = 0.f, mu = 0.f;
+  recon_opts opts{};
+  int device = 0, num_sms = 0;
+  cudaStream_t last_stream = nullptr;
+  PackInfo pk{};
+  int storage = 0;
+  size_t esize = 8;
+  std::vector<int> h_rows, h_rowoff;
+  int maxm = 0, total_rows = 0;
+  // device memory
+  std::vector<void*> allocs;
+  void* A = nullptr;
+  int4* units = nullptr;
+  float2* sens = nullptr;
+  int* rows = nullptr;
+  int* rowoff = nullptr;
+  float2 *tw_x = nullptr, *tw_y = nullptr, *tw_t = nullptr;
+  double2 *tw64_x = nullptr, *tw64_y = nullptr;
+  double2* yhat64 = nullptr;           // FP64 hybrid data of the prologue
+  float* thomas = nullptr;
+  float2* yhat = nullptr;
+  float2* b = nullptr;
+  float2* s0[2] = {nullptr, nullptr};  // TV: m;  DFT: u
+  float2* s1[2] = {nullptr, nullptr};  // TV: d1
+  float2* s2[2] = {nullptr, nullptr};  // TV: p
+  float2* x = nullptr;                 // TV: x; DFT: xhat
+  float2* r = nullptr;                 // DFT: r
+  float2* tmp_a = nullptr;             // operator entry points
+  float2* tmp_b = nullptr;
+  float2* kstage = nullptr;            // host-solve staging
+  float2* istage = nullptr;
+  double* trace_fid = nullptr;
+  double* trace_prior = nullptr;
+  double* trace_J = nullptr;
+  int* flags = nullptr;
+  FftPlanDev fx{}, fy{}, ft{};
+  FftPlanDev64 fx64{}, fy64{};
+  int col_stages = 0, col_grid = 0;
+  size_t col_smem = 0;
+  int last_iters = 0;
+  // opts.profile: event pairs around every inverse / temporal launch of a solve
+  std::vector<cudaEvent_t> ev_col, ev_tmp;
+  cudaEvent_t ev_solve[2] = {nullptr, nullptr};
+  int n_col = 0, n_tmp = 0;
+  bool prof_valid = false;
+
+  cudaError_t alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) allocs.push_back(*p);
+    return e;
+  }
+  ~recon_plan() {
+    for (cudaEvent_t e : ev_col) cudaEventDestroy(e);
+    for (cudaEvent_t e : ev_tmp) cudaEventDestroy(e);
+    for (cudaEvent_t e : ev_solve) if (e) cudaEventDestroy(e);
+    for (void* p : allocs) cudaFree(p);
+  }
+  void mark(std::vector<cudaEvent_t>& v, int& n, bool begin, cudaStream_t s) {
+    if (!opts.profile) return;
+    const size_t idx = 2 * (size_t)n + (begin ? 0 : 1);
+    if (idx < v.size()) cudaEventRecord(v[idx], s);
+    if (!begin) ++n;
+  }
+  size_t npix() const { return (size_t)Nx * Ny; }
+  size_t nimg() const { return (size_t)Nx * Ny * Nt; }
+};
+
+extern "C" {
+
+void recon_default_opts(recon_opts* o) {
+  if (!o) return;
+  o->rho = 0.5f;
+  o->max_iters = 50;
+  o->tol = 0.0;
+  o->storage = RECON_STORAGE_FP32;
+  o->objective = 1;
+  o->mask_full = 0;
+  o->col_stages = 0;
+  o->profile = 0;
+}
+
+const char* recon_status_string(recon_status s) {
+  switch (s) {
+    case RECON_OK: return "RECON_OK";
+    case RECON_ERR_INVALID_ARG: return "RECON_ERR_INVALID_ARG";
+    case RECON_ERR_MASK_NOT_CARTESIAN: return "RECON_ERR_MASK_NOT_CARTESIAN";
+    case RECON_ERR_OOM: return "RECON_ERR_OOM";
+    case RECON_ERR_CUDA: return "RECON_ERR_CUDA";
+    case RECON_ERR_TIMEOUT: return "RECON_ERR_TIMEOUT";
+    case RECON_ERR_NONFINITE: return "RECON_ERR_NONFINITE";
+    case RECON_ERR_UNSUPPORTED: return "RECON_ERR_UNSUPPORTED";
+  }
+  return "RECON_ERR_UNKNOWN";
+}
+
+const char* recon_last_error(void) { return g_last_error.c_str(); }
+
+size_t recon_inverse_bytes(const recon_plan* p) {
+  if (!p) return 0;
+  return (size_t)p->pk.col_elems * p->esize * (size_t)p->Nx * p->Nt;
+}
+
+recon_status recon_destroy(recon_plan* p) {
+  if (!p) return RECON_OK;
+  cudaSetDevice(p->device);
+  if (p->last_stream) cudaStreamSynchronize(p->last_stream);
+  delete p;
+  return RECON_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+PackInfo make_pack(int Ny) {
+  PackInfo pk{};
+  pk.nb = (Ny + 31) / 32;
+  pk.ntiles = pk.nb * (pk.nb - 1) / 2;
+  const int nrect = (pk.nb + 1) / 2;
+  pk.nunits = pk.ntiles + nrect;
+  pk.col_elems = (long long)pk.ntiles * kTileElems + (long long)nrect * kRectElems;
+  return pk;
+}
+
+std::vector<int4> make_units(const PackInfo& pk) {
+  std::vector<int4> u;
+  long long off = 0;
+  for (int bk = 0; bk < pk.nb; ++bk)
+    for (int bj = 0; bj < bk; ++bj) { u.push_back(make_int4(UNIT_TILE, bj, bk, (int)off)); off += kTileElems; }
+  for (int q = 0; q < (pk.nb + 1) / 2; ++q) {
+    u.push_back(make_int4(UNIT_RECT, 2 * q, 2 * q + 1, (int)off));
+    off += kRectElems;
+  }
+  return u;
+}
+
+// Pivots of the tridiagonal (rho I + D_t'D_t) for the Thomas sweep: with
+// sub/super-diagonal -1, inv_t = 1 / (b_t - inv_{t-1}), b_t = rho + deg_t.
+std::vector<float> thomas_pivots(int Nt, double rho) {
+  std::vector<float> out(Nt);
+  double prev = 0.0;
+  for (int t = 0; t < Nt; ++t) {
+    const double deg = (Nt == 1) ? 0.0 : ((t == 0 || t == Nt - 1) ? 1.0 : 2.0);
+    const double den = rho + deg - (t > 0 ? prev : 0.0);
+    prev = 1.0 / den;
+    out[t] = (float)prev;
+  }
+  return out;
+}
+
+int coil_group_for(int Nc, int Ny) {
+  int g = 8;
+  while (g > 1 && 2 * (size_t)g * Ny * 8 > 48 * 1024) --g;
+  return std::min(g, Nc);
+}
+
+ColParams base_col_params(const recon_plan* p) {
+  ColParams c{};
+  c.A = p->A;
+  c.col_elems = p->pk.col_elems;
+  c.nunits = p->pk.nunits;
+  c.units = p->units;
+  c.Nx = p->Nx; c.Ny = p->Ny; c.Nt = p->Nt; c.Nc = p->Nc; c.nb = p->pk.nb;
+  c.ncols = p->Nx * p->Nt;
+  c.stages = p->col_stages;
+  c.ncg = coil_group_for(p->Nc, p->Ny);
+  c.sens = p->sens;
+  c.yhat = p->yhat;
+  c.rows = p->rows;
+  c.rowoff = p->rowoff;
+  c.fy = p->fy;
+  c.flags = p->flags;
+  return c;
+}
+
+recon_status run_col(recon_plan* p, ColParams c, cudaStream_t s) {
+  c.stages = p->col_stages;
+  const size_t smem = col_inverse_smem(c, p->storage);
+  RC(launch_col_inverse(c, p->storage, p->col_grid, smem, s));
+  return RECON_OK;
+}
+
+// user layout [Nt][Ny][Nx] -> internal [Nt][Nx][Ny]
+recon_status to_internal(recon_plan* p, const float2* in, float2* out, cudaStream_t s) {
+  RC(launch_transpose(in, out, p->Nt, p->Ny, p->Nx, (long long)p->npix(), (long long)p->npix(), p->Ny, s));
+  return RECON_OK;
+}
+recon_status to_user(recon_plan* p, const float2* in, float2* out, cudaStream_t s) {
+  RC(launch_transpose(in, out, p->Nt, p->Nx, p->Ny, (long long)p->npix(), (long long)p->npix(), p->Nx, s));
+  return RECON_OK;
+}
+
+// H'y in FP64 (rounded once to FP32) and the FP32 hybrid data for J(k).
+recon_status adjoint64(recon_plan* p, const float* kspace, float2* yhat32, float2* b, cudaStream_t s) {
+  RC(launch_hybrid_rows64(reinterpret_cast<const float2*>(kspace), p->yhat64, yhat32, p->rows, p->rowoff, p->maxm,
+                          p->Nx, p->Ny, p->Nt, p->Nc, p->fx64, s));
+  RC(launch_adjoint_combine64(p->yhat64, p->sens, b, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fy64, s));
+  return RECON_OK;
+}
+
+recon_status prologue(recon_plan* p, const float* kspace, cudaStream_t s) {
+  return adjoint64(p, kspace, p->yhat, p->b, s);
+}
+
+// K iterations from the initial point (x = H'y).  Leaves the image (internal
+// layout) in *result.
+recon_status iterate(recon_plan* p, cudaStream_t s, const float2** result) {
+  const int K = p->opts.max_iters;
+  const bool obj = p->opts.objective || p->opts.tol > 0.0;
+  const size_t nt = (size_t)K + 2;
+  RC(cudaMemsetAsync(p->flags, 0, FLAG_COUNT * sizeof(int), s));
+  RC(cudaMemsetAsync(p->trace_fid, 0, nt * sizeof(double), s));
+  RC(cudaMemsetAsync(p->trace_prior, 0, nt * sizeof(double), s));
+  RC(cudaMemsetAsync(p->trace_J, 0xff, nt * sizeof(double), s));  // NaN
+  if (obj) {
+    ObjParams o{};
+    o.Nx = p->Nx; o.Ny = p->Ny; o.Nt = p->Nt; o.Nc = p->Nc; o.ncg = coil_group_for(p->Nc, p->Ny);
+    o.x = p->b; o.sens = p->sens; o.yhat = p->yhat; o.rows = p->rows; o.rowoff = p->rowoff; o.fy = p->fy;
+    o.fid_acc = p->trace_fid; o.flags = p->flags;
+    RC(launch_objective(o, s));
+  }
+  const double mu2 = p->mu;
+  const double rho = p->opts.rho;
+  const long long npix = (long long)p->npix();
+  ColParams c = base_col_params(p);
+  c.do_obj = obj ? 1 : 0;
+  if (p->prior == RECON_PRIOR_TV) {
+    const double mu1 = mu2 / rho;
+    TvParams tp{};
+    tp.Nt = p->Nt; tp.npix = npix;
+    tp.tau1 = (float)(p->lam / (2.0 * mu1));
+    tp.rho = (float)rho;
+    tp.thomas = p->thomas;
+    tp.flags = p->flags;
+    const float2 *m_in = p->b, *d1_in = nullptr, *x_in = p->b, *p_in = p->b;
+    for (int k = 1; k <= K; ++k) {
+      const int par = k & 1;
+      tp.m = m_in; tp.d1 = d1_in; tp.x = x_in; tp.p = p_in;
+      tp.m_out = p->s0[par]; tp.d1_out = p->s1[par]; tp.p_out = p->s2[par];
+      tp.write_state = 1;
+      tp.prior_acc = p->trace_prior + (k - 1);
+      p->mark(p->ev_tmp, p->n_tmp, true, s);
+      RC(launch_tv_temporal(tp, s));
+      p->mark(p->ev_tmp, p->n_tmp, false, s);
+      if (obj) RC(launch_finalize(p->trace_fid, p->trace_prior, p->trace_J, k - 1, p->lam, p->opts.tol, p->flags, s));
+      c.base = p->b; c.add = p->s2[par]; c.coef = (float)mu2; c.xout = p->x;
+      c.fid_acc = p->trace_fid + k;
+      p->mark(p->ev_col, p->n_col, true, s);
+      recon_status st = run_col(p, c, s);
+      if (st != RECON_OK) return st;
+      p->mark(p->ev_col, p->n_col, false, s);
+      m_in = p->s0[par]; d1_in = p->s1[par]; p_in = p->s2[par]; x_in = p->x;
+    }
+    if (obj) {
+      tp.x = x_in; tp.write_state = 0; tp.prior_acc = p->trace_prior + K;
+      RC(launch_tv_temporal(tp, s));
+      RC(launch_finalize(p->trace_fid, p->trace_prior, p->trace_J, K, p->lam, p->opts.tol, p->flags, s));
+    }
+    *result = (K == 0) ? p->b : p->x;
+  } else {
+    DftParams dp{};
+    dp.Nt = p->Nt; dp.npix = npix;
+    dp.b = p->b;
+    dp.tau = (float)(p->lam / (2.0 * mu2));
+    dp.mu = (float)mu2;
+    dp.ft = p->ft;
+    dp.flags = p->flags;
+    const float2 *xh_in = p->b, *u_in = nullptr;
+    for (int k = 1; k <= K; ++k) {
+      const int par = k & 1;
+      dp.xh = xh_in; dp.u = u_in; dp.first = (k == 1);
+      dp.u_out = p->s0[par]; dp.r_out = p->r;
+      dp.write_state = 1;
+      dp.prior_acc = p->trace_prior + (k - 1);
+      p->mark(p->ev_tmp, p->n_tmp, true, s);
+      RC(launch_dft_temporal(dp, s));
+      p->mark(p->ev_tmp, p->n_tmp, false, s);
+      if (obj) RC(launch_finalize(p->trace_fid, p->trace_prior, p->trace_J, k - 1, p->lam, p->opts.tol, p->flags, s));
+      c.base = p->r; c.add = nullptr; c.coef = 0.f; c.xout = p->x;
+      c.fid_acc = p->trace_fid + k;
+      p->mark(p->ev_col, p->n_col, true, s);
+      recon_status st = run_col(p, c, s);
+      if (st != RECON_OK) return st;
+      p->mark(p->ev_col, p->n_col, false, s);
+      xh_in = p->x; u_in = p->s0[par];
+    }
+    if (obj) {
+      dp.xh = xh_in; dp.write_state = 0; dp.first = 1; dp.prior_acc = p->trace_prior + K;
+      RC(launch_dft_temporal(dp, s));
+      RC(launch_finalize(p->trace_fid, p->trace_prior, p->trace_J, K, p->lam, p->opts.tol, p->flags, s));
+    }
+    *result = (K == 0) ? p->b : p->x;
+  }
+  return RECON_OK;
+}
+
+recon_status fill_info(recon_plan* p, recon_info* info, cudaStream_t s) {
+  RC(cudaStreamSynchronize(s));
+  int fl[FLAG_COUNT];
+  RC(cudaMemcpy(fl, p->flags, sizeof(fl), cudaMemcpyDeviceToHost));
+  const int K = p->opts.max_iters;
+  const int iters = fl[FLAG_STOP] ? fl[FLAG_ITERS] : K;
+  p->last_iters = iters;
+  std::vector<double> J((size_t)K + 2);
+  RC(cudaMemcpy(J.data(), p->trace_J, J.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  if (info) {
+    info->iters = iters;
+    info->stopped = fl[FLAG_STOP] ? 1 : 0;
+    info->J = J[iters];
+    info->J0 = J[0];
+    info->delta = (iters >= 1) ? (J[iters - 1] - J[iters]) / J[iters] : NAN;
+  }
+  if (fl[FLAG_ERR] & DEV_ERR_TIMEOUT) return fail(RECON_ERR_TIMEOUT, "a bounded device-side wait timed out");
+  if (fl[FLAG_ERR] & DEV_ERR_NONFINITE) return fail(RECON_ERR_NONFINITE, "non-finite objective value");
+  return RECON_OK;
+}
+
+bool valid_ptr(const void* p) { return p != nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc, const uint8_t* mask,
+                               const float* sens, float lambda, float mu, recon_prior prior, const recon_opts* opts,
+                               void* stream) {
+  g_last_error.clear();
+  if (!out) return fail(RECON_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (Nx < 1 || Ny < 1 || Nt < 1 || Nc < 1) return fail(RECON_ERR_INVALID_ARG, "dimensions must be >= 1");
+  if (Ny > 1024 || Nx > 1024 || Nt > 128 || Nc > 64 || (size_t)(Nc + 1) * Ny * 16 > 200 * 1024)
+    return fail(RECON_ERR_UNSUPPORTED,
+                "size beyond supported limits (Nx, Ny <= 1024, Nt <= 128, Nc <= 64, (Nc+1)*Ny <= 12800)");
+  if (!valid_ptr(mask) || !valid_ptr(sens)) return fail(RECON_ERR_INVALID_ARG, "mask or sens is NULL");
+  if (!(mu > 0.f) || !std::isfinite(mu)) return fail(RECON_ERR_INVALID_ARG, "mu must be > 0");
+  if (!(lambda >= 0.f) || !std::isfinite(lambda)) return fail(RECON_ERR_INVALID_ARG, "lambda must be >= 0");
+  if (prior != RECON_PRIOR_TV && prior != RECON_PRIOR_DFT) return fail(RECON_ERR_INVALID_ARG, "unknown prior");
+  recon_opts o;
+  recon_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.rho > 0.f) || o.max_iters < 0 || !(o.tol >= 0.0) || o.storage < 0 || o.storage > 2 || o.col_stages < 0)
+    return fail(RECON_ERR_INVALID_ARG, "invalid options");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  // mask -> sampled row lists (host)
+  const size_t mcount = o.mask_full ? (size_t)Nt * Ny * Nx : (size_t)Nt * Ny;
+  std::vector<uint8_t> hm(mcount);
+  {
+    cudaError_t e = cudaMemcpy(hm.data(), mask, mcount, cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(e, "copy mask");
+  }
+  auto* p = new recon_plan();
+  p->Nx = Nx; p->Ny = Ny; p->Nt = Nt; p->Nc = Nc;
+  p->prior = prior; p->lam = lambda; p->mu = mu; p->opts = o;
+  p->storage = o.storage;
+  p->esize = (o.storage == 0) ? 8 : 4;
+  cudaGetDevice(&p->device);
+  cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+  p->h_rowoff.assign(Nt + 1, 0);
+  for (int t = 0; t < Nt; ++t) {
+    for (int j = 0; j < Ny; ++j) {
+      bool on;
+      if (o.mask_full) {
+        const uint8_t* rowp = &hm[((size_t)t * Ny + j) * Nx];
+        on = rowp[0] != 0;
+        for (int i = 1; i < Nx; ++i) {
+          if ((rowp[i] != 0) != on) {
+            delete p;
+            return fail(RECON_ERR_MASK_NOT_CARTESIAN, "mask differs along kx (row " + std::to_string(j) +
+                                                          ", frame " + std::to_string(t) + ")");
+          }
+        }
+      } else {
+        on = hm[(size_t)t * Ny + j] != 0;
+      }
+      if (on) p->h_rows.push_back(j);
+    }
+    p->h_rowoff[t + 1] = (int)p->h_rows.size();
+    p->maxm = std::max(p->maxm, p->h_rowoff[t + 1] - p->h_rowoff[t]);
+  }
+  p->total_rows = (int)p->h_rows.size();
+  p->pk = make_pack(Ny);
+
+  auto cleanup = [&](recon_status st) { delete p; return st; };
+#define PC(call)                                                      \
+  do {                                                                \
+    cudaError_t e_ = (call);                                          \
+    if (e_ != cudaSuccess) return cleanup(cuda_fail(e_, #call));      \
+  } while (0)
+
+  const size_t nimg = p->nimg();
+  const size_t ncols = (size_t)Nx * Nt;
+  PC(p->alloc(&p->A, (size_t)p->pk.col_elems * p->esize * ncols));
+  std::vector<int4> hu = make_units(p->pk);
+  PC(p->alloc((void**)&p->units, hu.size() * sizeof(int4)));
+  PC(p->alloc((void**)&p->sens, (size_t)Nx * Nc * Ny * sizeof(float2)));
+  PC(p->alloc((void**)&p->rows, std::max<size_t>(1, p->h_rows.size()) * sizeof(int)));
+  PC(p->alloc((void**)&p->rowoff, (Nt + 1) * sizeof(int)));
+  PC(p->alloc((void**)&p->tw_x, Nx * sizeof(float2)));
+  PC(p->alloc((void**)&p->tw_y, Ny * sizeof(float2)));
+  PC(p->alloc((void**)&p->tw_t, Nt * sizeof(float2)));
+  PC(p->alloc((void**)&p->tw64_x, Nx * sizeof(double2)));
+  PC(p->alloc((void**)&p->tw64_y, Ny * sizeof(double2)));
+  PC(p->alloc((void**)&p->yhat64, std::max<size_t>(1, (size_t)p->total_rows * Nx * Nc) * sizeof(double2)));
+  PC(p->alloc((void**)&p->thomas, Nt * sizeof(float)));
+  PC(p->alloc((void**)&p->yhat, std::max<size_t>(1, (size_t)p->total_rows * Nx * Nc) * sizeof(float2)));
+  PC(p->alloc((void**)&p->b, nimg * sizeof(float2)));
+  for (int k = 0; k < 2; ++k) {
+    PC(p->alloc((void**)&p->s0[k], nimg * sizeof(float2)));
+    if (prior == RECON_PRIOR_TV) {
+      PC(p->alloc((void**)&p->s1[k], nimg * sizeof(float2)));
+      PC(p->alloc((void**)&p->s2[k], nimg * sizeof(float2)));
+    }
+  }
+  PC(p->alloc((void**)&p->x, nimg * sizeof(float2)));
+  if (prior == RECON_PRIOR_DFT) PC(p->alloc((void**)&p->r, nimg * sizeof(float2)));
+  PC(p->alloc((void**)&p->tmp_a, nimg * sizeof(float2)));
+  PC(p->alloc((void**)&p->tmp_b, std::max<size_t>(nimg, (size_t)p->total_rows * Nx * Nc) * sizeof(float2)));
+  const size_t nt = (size_t)o.max_iters + 2;
+  PC(p->alloc((void**)&p->trace_fid, nt * sizeof(double)));
+  PC(p->alloc((void**)&p->trace_prior, nt * sizeof(double)));
+  PC(p->alloc((void**)&p->trace_J, nt * sizeof(double)));
+  PC(p->alloc((void**)&p->flags, FLAG_COUNT * sizeof(int)));
+
+  // tables
+  std::vector<float2> tw(std::max(std::max(Nx, Ny), Nt));
+  fill_twiddles_host(Nx, tw.data());
+  PC(cudaMemcpy(p->tw_x, tw.data(), Nx * sizeof(float2), cudaMemcpyHostToDevice));
+  fill_twiddles_host(Ny, tw.data());
+  PC(cudaMemcpy(p->tw_y, tw.data(), Ny * sizeof(float2), cudaMemcpyHostToDevice));
+  fill_twiddles_host(Nt, tw.data());
+  PC(cudaMemcpy(p->tw_t, tw.data(), Nt * sizeof(float2), cudaMemcpyHostToDevice));
+  {
+    std::vector<double2> tw64(std::max(Nx, Ny));
+    fill_twiddles_host64(Nx, tw64.data());
+    PC(cudaMemcpy(p->tw64_x, tw64.data(), Nx * sizeof(double2), cudaMemcpyHostToDevice));
+    fill_twiddles_host64(Ny, tw64.data());
+    PC(cudaMemcpy(p->tw64_y, tw64.data(), Ny * sizeof(double2), cudaMemcpyHostToDevice));
+    p->fx64 = make_fft_plan_host64(Nx, p->tw64_x);
+    p->fy64 = make_fft_plan_host64(Ny, p->tw64_y);
+  }
+  p->fx = make_fft_plan_host(Nx, p->tw_x);
+  p->fy = make_fft_plan_host(Ny, p->tw_y);
+  p->ft = make_fft_plan_host(Nt, p->tw_t);
+  std::vector<float> th = thomas_pivots(Nt, o.rho);
+  PC(cudaMemcpy(p->thomas, th.data(), Nt * sizeof(float), cudaMemcpyHostToDevice));
+  PC(cudaMemcpy(p->units, hu.data(), hu.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  if (!p->h_rows.empty())
+    PC(cudaMemcpy(p->rows, p->h_rows.data(), p->h_rows.size() * sizeof(int), cudaMemcpyHostToDevice));
+  PC(cudaMemcpy(p->rowoff, p->h_rowoff.data(), (Nt + 1) * sizeof(int), cudaMemcpyHostToDevice));
+
+  // sensitivities -> [Nx][Nc][Ny]
+  {
+    float2* stage = p->tmp_a;  // Nc*Ny*Nx <= nimg is not guaranteed; use a temporary
+    void* tmp = nullptr;
+    const size_t sbytes = (size_t)Nc * Ny * Nx * sizeof(float2);
+    PC(cudaMalloc(&tmp, sbytes));
+    stage = static_cast<float2*>(tmp);
+    cudaError_t e = cudaMemcpyAsync(stage, sens, sbytes, cudaMemcpyDefault, s);
+    if (e == cudaSuccess)
+      e = launch_transpose(stage, p->sens, Nc, Ny, Nx, (long long)Ny * Nx, (long long)Ny, (long long)Nc * Ny, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "sensitivity upload"));
+  }
+
+  // packed inverses (FP64 factorisation, rounded once)
+  {
+    std::vector<double2> w64(Ny);
+    for (int k = 0; k < Ny; ++k) {
+      const double a = 2.0 * M_PI * (double)k / (double)Ny;
+      w64[k] = make_double2(std::cos(a), std::sin(a));
+    }
+    void *d_w64 = nullptr, *d_circ = nullptr, *d_scr = nullptr;
+    int grid = std::max(1, std::min<int>((int)ncols, 2 * p->num_sms));
+    cudaError_t e = cudaMalloc(&d_w64, Ny * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&d_circ, (size_t)Nt * Ny * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&d_scr, (size_t)grid * Ny * Ny * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMemcpy(d_w64, w64.data(), Ny * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->flags, 0, FLAG_COUNT * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->A, 0, (size_t)p->pk.col_elems * p->esize * ncols, s);
+    if (e == cudaSuccess)
+      e = launch_circulant(p->rows, p->rowoff, static_cast<double2*>(d_w64), static_cast<double2*>(d_circ), Ny, Nt,
+                           s);
+    if (e == cudaSuccess)
+      e = launch_plan_inverse(p->sens, static_cast<double2*>(d_circ), (double)mu, Nx, Ny, Nt, Nc, p->A, p->storage,
+                              p->pk, static_cast<double2*>(d_scr), grid, p->flags, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_w64); cudaFree(d_circ); cudaFree(d_scr);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "plan inverse"));
+    int fl[FLAG_COUNT];
+    PC(cudaMemcpy(fl, p->flags, sizeof(fl), cudaMemcpyDeviceToHost));
+    if (fl[FLAG_ERR] & DEV_ERR_NOT_PD) return cleanup(fail(RECON_ERR_NONFINITE, "a Gram block is not positive definite"));
+  }
+
+  // column-inverse launch shape: one persistent CTA per SM, ring as deep as fits
+  {
+    ColParams c = base_col_params(p);
+    c.do_obj = 1;
+    const int maxst = col_inverse_max_stages(c, p->storage);
+    p->col_stages = o.col_stages > 0 ? std::min(o.col_stages, maxst) : std::min(16, maxst);
+    p->col_grid = std::max(1, std::min<int>((int)ncols, p->num_sms));
+  }
+  if (o.profile) {
+    const size_t ne = 2 * ((size_t)o.max_iters + 2);
+    p->ev_col.resize(ne);
+    p->ev_tmp.resize(ne);
+    for (auto& e : p->ev_col) PC(cudaEventCreate(&e));
+    for (auto& e : p->ev_tmp) PC(cudaEventCreate(&e));
+    PC(cudaEventCreate(&p->ev_solve[0]));
+    PC(cudaEventCreate(&p->ev_solve[1]));
+  }
+  p->last_stream = s;
+  *out = p;
+  return RECON_OK;
+#undef PC
+}
+
+recon_status recon_solve(recon_plan* p, const float* kspace, float* image, recon_info* info, void* stream) {
+  g_last_error.clear();
+  if (!p || !kspace || !image) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->last_stream = s;
+  p->n_col = p->n_tmp = 0;
+  p->prof_valid = p->opts.profile != 0;
+  if (p->opts.profile) cudaEventRecord(p->ev_solve[0], s);
+  recon_status st = prologue(p, kspace, s);
+  if (st != RECON_OK) return st;
+  const float2* res = nullptr;
+  st = iterate(p, s, &res);
+  if (st != RECON_OK) return st;
+  st = to_user(p, res, reinterpret_cast<float2*>(image), s);
+  if (st != RECON_OK) return st;
+  if (p->opts.profile) cudaEventRecord(p->ev_solve[1], s);
+  if (info) return fill_info(p, info, s);
+  return RECON_OK;
+}
+
+recon_status recon_get_profile(recon_plan* p, recon_profile* out) {
+  if (!p || !out) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  if (!p->prof_valid) return RECON_OK;
+  if (p->last_stream) RC(cudaStreamSynchronize(p->last_stream));
+  else RC(cudaDeviceSynchronize());
+  auto sum = [&](std::vector<cudaEvent_t>& v, int n, double* ms) -> cudaError_t {
+    double acc = 0.0;
+    for (int k = 0; k < n && 2 * (size_t)k + 1 < v.size(); ++k) {
+      float m = 0.f;
+      cudaError_t e = cudaEventElapsedTime(&m, v[2 * k], v[2 * k + 1]);
+      if (e != cudaSuccess) return e;
+      acc += m;
+    }
+    *ms = acc;
+    return cudaSuccess;
+  };
+  RC(sum(p->ev_col, p->n_col, &out->inverse_ms));
+  out->inverse_launches = p->n_col;
+  RC(sum(p->ev_tmp, p->n_tmp, &out->temporal_ms));
+  out->temporal_launches = p->n_tmp;
+  float m = 0.f;
+  RC(cudaEventElapsedTime(&m, p->ev_solve[0], p->ev_solve[1]));
+  out->solve_ms = m;
+  return RECON_OK;
+}
+
+unsigned long long recon_kernel_launches(void) { return g_launches.load(); }
+
+recon_status recon_solve_host(recon_plan* p, const float* kspace_host, float* image_host, recon_info* info,
+                              void* stream) {
+  g_last_error.clear();
+  if (!p || !kspace_host || !image_host) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t kbytes = (size_t)p->Nt * p->Nc * p->Ny * p->Nx * sizeof(float2);
+  const size_t ibytes = p->nimg() * sizeof(float2);
+  if (!p->kstage) RC(p->alloc((void**)&p->kstage, kbytes));
+  if (!p->istage) RC(p->alloc((void**)&p->istage, ibytes));
+  RC(cudaMemcpyAsync(p->kstage, kspace_host, kbytes, cudaMemcpyHostToDevice, s));
+  recon_status st = recon_solve(p, reinterpret_cast<const float*>(p->kstage), reinterpret_cast<float*>(p->istage),
+                                nullptr, stream);
+  if (st != RECON_OK) return st;
+  RC(cudaMemcpyAsync(image_host, p->istage, ibytes, cudaMemcpyDeviceToHost, s));
+  return fill_info(p, info, s);
+}
+
+recon_status recon_get_trace(recon_plan* p, double* J_host, int n) {
+  if (!p || !J_host || n < 0) return fail(RECON_ERR_INVALID_ARG, "bad argument");
+  if (p->last_stream) RC(cudaStreamSynchronize(p->last_stream));
+  const int avail = p->opts.max_iters + 2;
+  std::vector<double> J(avail);
+  RC(cudaMemcpy(J.data(), p->trace_J, avail * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < n; ++k) J_host[k] = (k < avail) ? J[k] : NAN;
+  return RECON_OK;
+}
+
+recon_status recon_apply_adjoint(recon_plan* p, const float* kspace, float* image, void* stream) {
+  if (!p || !kspace || !image) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  recon_status st = adjoint64(p, kspace, p->tmp_b, p->tmp_a, s);
+  if (st != RECON_OK) return st;
+  return to_user(p, p->tmp_a, reinterpret_cast<float2*>(image), s);
+}
+
+recon_status recon_apply_forward(recon_plan* p, const float* image, float* kspace, void* stream) {
+  if (!p || !image || !kspace) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  recon_status st = to_internal(p, reinterpret_cast<const float2*>(image), p->tmp_a, s);
+  if (st != RECON_OK) return st;
+  RC(launch_forward_cols(p->tmp_a, p->sens, p->tmp_b, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fy, s));
+  RC(cudaMemsetAsync(kspace, 0, (size_t)p->Nt * p->Nc * p->Ny * p->Nx * sizeof(float2), s));
+  RC(launch_forward_rows(p->tmp_b, reinterpret_cast<float2*>(kspace), p->rows, p->rowoff, p->maxm, p->Nx, p->Ny,
+                         p->Nt, p->Nc, p->fx, s));
+  return RECON_OK;
+}
+
+recon_status recon_apply_inverse(recon_plan* p, const float* in, float* out, void* stream) {
+  if (!p || !in || !out || in == out) return fail(RECON_ERR_INVALID_ARG, "NULL or aliased argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  recon_status st = to_internal(p, reinterpret_cast<const float2*>(in), p->tmp_a, s);
+  if (st != RECON_OK) return st;
+  RC(cudaMemsetAsync(p->flags, 0, FLAG_COUNT * sizeof(int), s));
+  ColParams c = base_col_params(p);
+  c.do_obj = 0;
+  c.base = p->tmp_a; c.add = nullptr; c.coef = 0.f; c.xout = p->tmp_b;
+  c.fid_acc = nullptr;
+  st = run_col(p, c, s);
+  if (st != RECON_OK) return st;
+  return to_user(p, p->tmp_b, reinterpret_cast<float2*>(out), s);
+}
+
+recon_status recon_export_inverse(recon_plan* p, int i, int t, float* dense, void* stream) {
+  if (!p || !dense || i < 0 || i >= p->Nx || t < 0 || t >= p->Nt) return fail(RECON_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  RC(launch_unpack(p->A, p->storage, p->pk, (long long)t * p->Nx + i, p->Ny, reinterpret_cast<float2*>(dense), s));
+  return RECON_OK;
+}
+
+}  // extern "C"

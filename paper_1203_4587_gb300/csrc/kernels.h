@@ -1,0 +1,167 @@
+// Internal launch interfaces between the C-ABI layer (api.cu) and the kernels.
+//
+// Internal layouts (device):
+//   image fields   [Nt][Nx][Ny]  column-stacked per frame (Eq. x_def: the
+//                  vertical index j is fastest, so column x_{v,i,t} is
+//                  contiguous)
+//   sensitivities  [Nx][Nc][Ny]
+//   hybrid data    yhat = F_h' y on sampled rows: frame t starts at
+//                  rowoff[t]*Nx*Nc, then [Nx][Nc][m_t]
+//   inverses       one packed stream of `col_elems` elements per column
+//                  (i,t), column index col = t*Nx + i (see packing below)
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+
+namespace recon {
+
+// ---- packed Hermitian storage of A_{i,t} = (mu I + G_{i,t})^{-1} -------------
+// Ny is padded to Nyp = 32*nb.  The upper triangle is cut into 32x32 blocks.
+// Units, in stream order:
+//   * every off-diagonal block (bj < bk), bk-major: 1024 elements in the
+//     order the matvec lanes read them: element (R, C) of the block sits at
+//     ((R%4)*4 + (C%8)/2)*64 + ((R/4)*4 + C/8)*2 + C%2.
+//   * diagonal blocks in pairs (2q, 2q+1): 32 x 33 = 1056 elements.  Cell
+//     (a, b) holds P[a][b-1] for b > a (upper triangle of block 2q, row a)
+//     and Q[b][a] for b <= a (upper triangle of block 2q+1, column a); it is
+//     stored at b*32 + ((a+b) & 31).  With nb odd the last pair has no Q
+//     block (zeros).
+// This is exactly Ny(Ny+1)/2 elements when Ny is a multiple of 64.
+enum UnitKind : int { UNIT_TILE = 0, UNIT_RECT = 1 };
+constexpr int kTileElems = 1024;
+constexpr int kRectElems = 1056;
+
+struct PackInfo {
+  int nb;          // 32-blocks per column
+  int nunits;
+  int ntiles;      // off-diagonal blocks
+  long long col_elems;
+};
+
+// ---- FFT plan (host side holds the device twiddle table) -------------------
+FftPlanDev make_fft_plan_host(int n, const float2* d_tw);  // factorisation only
+FftPlanDev64 make_fft_plan_host64(int n, const double2* d_tw);
+void fill_twiddles_host(int n, float2* host_tw);           // exp(-2 pi i k/n)
+void fill_twiddles_host64(int n, double2* host_tw);
+
+// ---- kernel parameter blocks ----------------------------------------------
+struct ColParams {           // data-consistency inverse x = A r, per column
+  const void* A;             // packed stream base
+  long long col_elems;
+  int nunits;
+  const int4* units;         // {kind, p, q, elem offset}
+  int Nx, Ny, Nt, Nc, nb;
+  int ncols;
+  int stages;                // ring depth
+  const float2* base;        // r = base + coef * add   ([Nt][Nx][Ny])
+  const float2* add;         // may be null
+  float coef;
+  float2* xout;
+  // objective epilogue: ||y - H x||^2 of this column
+  int do_obj;
+  int ncg;                   // coils per FFT group
+  const float2* sens;        // [Nx][Nc][Ny]
+  const float2* yhat;
+  const int* rows;
+  const int* rowoff;
+  FftPlanDev fy;
+  double* fid_acc;
+  int* flags;
+};
+
+struct TvParams {            // temporal step of Algorithm 2 (R = D_t)
+  int Nt;
+  long long npix;            // Nx*Ny
+  const float2* m;           // [Nt][npix]
+  const float2* d1;          // [Nt-1][npix] or null (zeros)
+  const float2* x;
+  const float2* p;           // p = m_prev - d2_prev, so d2 = x - p
+  float2* m_out;
+  float2* d1_out;
+  float2* p_out;
+  float tau1;                // lambda / (2 mu1)
+  float rho;                 // mu2 / mu1
+  const float* thomas;       // [Nt] pivots of (rho I + D'D)
+  int write_state;           // 0: only the prior term
+  double* prior_acc;         // += ||D_t x||_1
+  const int* flags;
+};
+
+struct DftParams {           // temporal step of Algorithm 1 (Psi = temporal DFT)
+  int Nt;
+  long long npix;
+  const float2* xh;          // xhat = A r of the previous iteration (b at k=1)
+  const float2* u;           // u = v + d of the previous iteration
+  const float2* b;
+  float2* u_out;
+  float2* r_out;             // r = b + mu Psi'(v + d)
+  float tau;                 // lambda / (2 mu)
+  float mu;
+  int first;                 // k == 1: d = 0
+  int write_state;
+  FftPlanDev ft;
+  double* prior_acc;         // += ||w||_1
+  const int* flags;
+};
+
+struct ObjParams {           // ||y - H x||^2 of a given field (no inverse)
+  int Nx, Ny, Nt, Nc, ncg;
+  const float2* x;           // [Nt][Nx][Ny]
+  const float2* sens;
+  const float2* yhat;
+  const int* rows;
+  const int* rowoff;
+  FftPlanDev fy;
+  double* fid_acc;
+  const int* flags;
+};
+
+// Counts kernel launches of this library (process-wide); every launcher calls it.
+void note_launch();
+
+// ---- launchers (return cudaGetLastError()) ---------------------------------
+cudaError_t launch_col_inverse(const ColParams& p, int storage, int grid, size_t smem, cudaStream_t s);
+size_t col_inverse_smem(const ColParams& p, int storage);
+int col_inverse_max_stages(const ColParams& p, int storage);
+cudaError_t launch_tv_temporal(const TvParams& p, cudaStream_t s);
+cudaError_t launch_dft_temporal(const DftParams& p, cudaStream_t s);
+cudaError_t launch_objective(const ObjParams& p, cudaStream_t s);
+cudaError_t launch_finalize(const double* fid, const double* prior, double* J, int k, float lam, double tol,
+                            int* flags, cudaStream_t s);
+
+// prologue / operators
+cudaError_t launch_hybrid_rows(const void* kspace, int kdtype, const float* kscale, float2* yhat, const int* rows,
+                               const int* rowoff, int maxm, int Nx, int Ny, int Nt, int Nc, FftPlanDev fx,
+                               cudaStream_t s);
+cudaError_t launch_adjoint_combine(const float2* yhat, const float2* sens, float2* b, const int* rows,
+                                   const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, cudaStream_t s);
+// FP64 H'y prologue: the solution of the iterations is ~100x more sensitive to
+// errors in H'y than to rounding elsewhere, so H'y is formed in FP64 and
+// rounded once.  yhat32 receives the FP32 rounding of the hybrid data.
+cudaError_t launch_hybrid_rows64(const float2* kspace, double2* yhat64, float2* yhat32, const int* rows,
+                                 const int* rowoff, int maxm, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fx,
+                                 cudaStream_t s);
+cudaError_t launch_adjoint_combine64(const double2* yhat64, const float2* sens, float2* b, const int* rows,
+                                     const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fy,
+                                     cudaStream_t s);
+cudaError_t launch_forward_cols(const float2* x, const float2* sens, float2* zhat, const int* rows,
+                                const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, cudaStream_t s);
+cudaError_t launch_forward_rows(const float2* zhat, float2* kspace, const int* rows, const int* rowoff, int maxm,
+                                int Nx, int Ny, int Nt, int Nc, FftPlanDev fx, cudaStream_t s);
+// out[b*obs + c*ors + r] = in[b*ibs + r*C + c], for r < R, c < C, b < B
+cudaError_t launch_transpose(const float2* in, float2* out, int B, int R, int C, long long ibs, long long obs,
+                             long long ors, cudaStream_t s);
+
+// plan
+cudaError_t launch_circulant(const int* rows, const int* rowoff, const double2* w64, double2* circ, int Ny, int Nt,
+                             cudaStream_t s);
+cudaError_t launch_plan_inverse(const float2* sens, const double2* circ, double mu, int Nx, int Ny, int Nt, int Nc,
+                                void* A, int storage, const PackInfo& pk, double2* scratch, int grid,
+                                int* flags, cudaStream_t s);
+cudaError_t launch_unpack(const void* A, int storage, const PackInfo& pk, long long col, int Ny, float2* dense,
+                          cudaStream_t s);
+
+}  // namespace recon

@@ -1,0 +1,295 @@
+// Forward model operators (Section II-A, Eqs. mri_csmcoill, H_1, S, F).
+//
+//   H x  = M_{v,t} F_h F_v (s_c . x_t)
+//   H' y = sum_c conj(s_c) . F_v' M' F_h' y_{t,c}
+//
+// F_h acts along k-space rows and F_v along image columns, so each is a batch
+// of independent 1D unitary FFTs (shared-memory Stockham, fft.cuh):
+//   k_hybrid_rows     yhat = F_h' y on the sampled rows only (rows [t][c][ky][:])
+//   k_adjoint_combine b = sum_c conj(s_c) . F_v'(zero-filled yhat_c), per column
+//   k_forward_cols    zhat = M F_v (s_c . x), per column (sampled rows only)
+//   k_forward_rows    y = F_h zhat on the sampled rows
+//   k_transpose       layout changes between [..][Ny][Nx] and [..][Nx][Ny]
+#include "kernels.h"
+
+namespace recon {
+
+constexpr int kRowGroup = 8;  // k-space rows per block in the row kernels (at most)
+
+// Rows per block so that two [g][Nx+1] buffers of T fit in 96 KB.
+template <typename T>
+static int row_group(int Nx) {
+  int g = kRowGroup;
+  while (g > 1 && 2 * (size_t)g * (Nx + 1) * sizeof(T) > 96 * 1024) --g;
+  return g;
+}
+
+// yhat = F_h' y on the sampled rows.  T = double2 computes in FP64 and also
+// writes the FP32 rounding (yhat32) used by the objective.
+template <typename T>
+__global__ void __launch_bounds__(256) k_hybrid_rows(const float2* __restrict__ ksp, T* __restrict__ yhat,
+                                                     float2* __restrict__ yhat32, const int* __restrict__ rows,
+                                                     const int* __restrict__ rowoff, int Nx, int Ny, int Nt, int Nc,
+                                                     int G, FftPlanT<T> fx, double scl) {
+  extern __shared__ __align__(16) unsigned char sm_rows_raw[];
+  T* sm_rows = reinterpret_cast<T*>(sm_rows_raw);
+  const int t = blockIdx.z, c = blockIdx.y, m0 = blockIdx.x * G;
+  const int r0 = rowoff[t], mt = rowoff[t + 1] - r0;
+  if (m0 >= mt) return;
+  const int g = min(G, mt - m0);
+  const int ss = Nx + 1;  // padded sequence stride: conflict-free transposed reads
+  T* A = sm_rows;
+  T* B = sm_rows + (size_t)G * ss;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int idx = tid; idx < g * Nx; idx += nth) {
+    const int gg = idx / Nx, kx = idx - gg * Nx;
+    const int row = rows[r0 + m0 + gg];
+    A[gg * ss + kx] = from_f2<T>(ksp[(((size_t)t * Nc + c) * Ny + row) * Nx + kx]);
+  }
+  __syncthreads();
+  const BlockBar bar;
+  T* R = fft_run(A, B, g, ss, 1, fx, true, tid, nth, bar);
+  const size_t base = (size_t)r0 * Nx * Nc;
+  for (int idx = tid; idx < g * Nx; idx += nth) {
+    const int i = idx / g, gg = idx - i * g;
+    const size_t o = base + ((size_t)i * Nc + c) * mt + m0 + gg;
+    const T v = c_scale(R[gg * ss + i], scl);
+    yhat[o] = v;
+    if (yhat32) yhat32[o] = to_f2(v);
+  }
+}
+
+template <typename T>
+static cudaError_t launch_rows_t(const float2* ksp, T* yhat, float2* yhat32, const int* rows, const int* rowoff,
+                                 int maxm, int Nx, int Ny, int Nt, int Nc, const FftPlanT<T>& fx, cudaStream_t s) {
+  if (maxm <= 0) return cudaSuccess;
+  const int G = row_group<T>(Nx);
+  const size_t smem = 2 * (size_t)G * (Nx + 1) * sizeof(T);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_hybrid_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  dim3 grid((maxm + G - 1) / G, Nc, Nt);
+  k_hybrid_rows<T><<<grid, 256, smem, s>>>(ksp, yhat, yhat32, rows, rowoff, Nx, Ny, Nt, Nc, G, fx,
+                                           1.0 / sqrt((double)Nx)); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hybrid_rows(const void* kspace, int kdtype, const float* kscale, float2* yhat, const int* rows,
+                               const int* rowoff, int maxm, int Nx, int Ny, int Nt, int Nc, FftPlanDev fx,
+                               cudaStream_t s) {
+  (void)kscale;
+  if (kdtype != 0) return cudaErrorInvalidValue;
+  return launch_rows_t<float2>(static_cast<const float2*>(kspace), yhat, nullptr, rows, rowoff, maxm, Nx, Ny, Nt,
+                               Nc, fx, s);
+}
+
+cudaError_t launch_hybrid_rows64(const float2* kspace, double2* yhat64, float2* yhat32, const int* rows,
+                                 const int* rowoff, int maxm, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fx,
+                                 cudaStream_t s) {
+  return launch_rows_t<double2>(kspace, yhat64, yhat32, rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, s);
+}
+
+constexpr int kCoilGroupMax = 8;
+
+// b = sum_c conj(s_c) . F_v'(zero-filled yhat_c), accumulated in T and rounded
+// once to FP32.
+template <typename T>
+__global__ void __launch_bounds__(256) k_adjoint_combine(const T* __restrict__ yhat,
+                                                         const float2* __restrict__ sens, float2* __restrict__ b,
+                                                         const int* __restrict__ rows,
+                                                         const int* __restrict__ rowoff, int Nx, int Ny, int Nt,
+                                                         int Nc, int ncg, FftPlanT<T> fy, double scl) {
+  extern __shared__ __align__(16) unsigned char sm_adj_raw[];
+  T* sm_adj = reinterpret_cast<T*>(sm_adj_raw);
+  const int i = blockIdx.x, t = blockIdx.y;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int r0 = rowoff[t], mt = rowoff[t + 1] - r0;
+  const T* yh = yhat + (size_t)r0 * Nx * Nc + (size_t)i * Nc * mt;
+  const float2* sc = sens + (size_t)i * Nc * Ny;
+  T* A = sm_adj;
+  T* B = sm_adj + (size_t)ncg * Ny;
+  T acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] = c_zero<T>();
+  const BlockBar bar;
+  for (int c0 = 0; c0 < Nc; c0 += ncg) {
+    const int cg = min(ncg, Nc - c0);
+    for (int idx = tid; idx < cg * Ny; idx += nth) A[idx] = c_zero<T>();
+    __syncthreads();
+    for (int idx = tid; idx < cg * mt; idx += nth) {
+      const int c = idx / mt, m = idx - c * mt;
+      A[c * Ny + rows[r0 + m]] = yh[(size_t)(c0 + c) * mt + m];
+    }
+    __syncthreads();
+    T* R = fft_run(A, B, cg, Ny, 1, fy, true, tid, nth, bar);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = tid + q * nth;
+      if (j < Ny) {
+        for (int c = 0; c < cg; ++c) c_fmac(acc[q], from_f2<T>(__ldg(sc + (size_t)(c0 + c) * Ny + j)), R[c * Ny + j]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = tid + q * nth;
+    if (j < Ny) b[((size_t)t * Nx + i) * Ny + j] = to_f2(c_scale(acc[q], scl));
+  }
+}
+
+template <typename T>
+static int coil_group(int Nc, int Ny) {
+  int g = kCoilGroupMax;
+  while (g > 1 && 2 * (size_t)g * Ny * sizeof(T) > 96 * 1024) --g;
+  return g < Nc ? g : Nc;
+}
+
+template <typename T>
+static cudaError_t launch_combine_t(const T* yhat, const float2* sens, float2* b, const int* rows, const int* rowoff,
+                                    int Nx, int Ny, int Nt, int Nc, const FftPlanT<T>& fy, cudaStream_t s) {
+  if (Ny > 1024) return cudaErrorInvalidValue;
+  const int ncg = coil_group<T>(Nc, Ny);
+  const size_t smem = 2 * (size_t)ncg * Ny * sizeof(T);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_adjoint_combine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  k_adjoint_combine<T><<<dim3(Nx, Nt), 256, smem, s>>>(yhat, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, ncg, fy,
+                                                       1.0 / sqrt((double)Ny)); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_combine(const float2* yhat, const float2* sens, float2* b, const int* rows,
+                                   const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, cudaStream_t s) {
+  return launch_combine_t<float2>(yhat, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, fy, s);
+}
+
+cudaError_t launch_adjoint_combine64(const double2* yhat64, const float2* sens, float2* b, const int* rows,
+                                     const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fy,
+                                     cudaStream_t s) {
+  return launch_combine_t<double2>(yhat64, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, fy, s);
+}
+
+__global__ void __launch_bounds__(256) k_forward_cols(const float2* __restrict__ x, const float2* __restrict__ sens,
+                                                      float2* __restrict__ zhat, const int* __restrict__ rows,
+                                                      const int* __restrict__ rowoff, int Nx, int Ny, int Nt, int Nc,
+                                                      int ncg, FftPlanDev fy, float scl) {
+  extern __shared__ float2 sm_fwd[];
+  const int i = blockIdx.x, t = blockIdx.y;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int r0 = rowoff[t], mt = rowoff[t + 1] - r0;
+  float2* xc = sm_fwd;
+  float2* A = xc + Ny;
+  float2* B = A + (size_t)ncg * Ny;
+  const float2* sc = sens + (size_t)i * Nc * Ny;
+  float2* zh = zhat + (size_t)r0 * Nx * Nc + (size_t)i * Nc * mt;
+  for (int j = tid; j < Ny; j += nth) xc[j] = x[((size_t)t * Nx + i) * Ny + j];
+  __syncthreads();
+  const BlockBar bar;
+  for (int c0 = 0; c0 < Nc; c0 += ncg) {
+    const int cg = min(ncg, Nc - c0);
+    for (int idx = tid; idx < cg * Ny; idx += nth) {
+      const int c = idx / Ny, j = idx - c * Ny;
+      A[idx] = c_mul(__ldg(sc + (size_t)(c0 + c) * Ny + j), xc[j]);
+    }
+    __syncthreads();
+    float2* R = fft_run(A, B, cg, Ny, 1, fy, false, tid, nth, bar);
+    for (int idx = tid; idx < cg * mt; idx += nth) {
+      const int c = idx / mt, m = idx - c * mt;
+      zh[(size_t)(c0 + c) * mt + m] = c_scale(R[c * Ny + rows[r0 + m]], scl);
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_forward_cols(const float2* x, const float2* sens, float2* zhat, const int* rows,
+                                const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, cudaStream_t s) {
+  const int ncg = coil_group<float2>(Nc, Ny);
+  const size_t smem = ((size_t)Ny + 2 * (size_t)ncg * Ny) * sizeof(float2);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_forward_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  k_forward_cols<<<dim3(Nx, Nt), 256, smem, s>>>(x, sens, zhat, rows, rowoff, Nx, Ny, Nt, Nc, ncg, fy,
+                                                 (float)(1.0 / sqrt((double)Ny))); note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_forward_rows(const float2* __restrict__ zhat, float2* __restrict__ ksp,
+                                                      const int* __restrict__ rows, const int* __restrict__ rowoff,
+                                                      int Nx, int Ny, int Nt, int Nc, FftPlanDev fx, float scl) {
+  extern __shared__ float2 sm_frow[];
+  const int t = blockIdx.z, c = blockIdx.y, m0 = blockIdx.x * kRowGroup;
+  const int r0 = rowoff[t], mt = rowoff[t + 1] - r0;
+  if (m0 >= mt) return;
+  const int g = min(kRowGroup, mt - m0);
+  const int ss = Nx + 1;
+  float2* A = sm_frow;
+  float2* B = sm_frow + (size_t)kRowGroup * ss;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const size_t base = (size_t)r0 * Nx * Nc;
+  for (int idx = tid; idx < g * Nx; idx += nth) {
+    const int i = idx / g, gg = idx - i * g;
+    A[gg * ss + i] = zhat[base + ((size_t)i * Nc + c) * mt + m0 + gg];
+  }
+  __syncthreads();
+  const BlockBar bar;
+  float2* R = fft_run(A, B, g, ss, 1, fx, false, tid, nth, bar);
+  for (int idx = tid; idx < g * Nx; idx += nth) {
+    const int gg = idx / Nx, kx = idx - gg * Nx;
+    const int row = rows[r0 + m0 + gg];
+    ksp[(((size_t)t * Nc + c) * Ny + row) * Nx + kx] = c_scale(R[gg * ss + kx], scl);
+  }
+}
+
+cudaError_t launch_forward_rows(const float2* zhat, float2* kspace, const int* rows, const int* rowoff, int maxm,
+                                int Nx, int Ny, int Nt, int Nc, FftPlanDev fx, cudaStream_t s) {
+  if (maxm <= 0) return cudaSuccess;
+  const size_t smem = 2 * (size_t)kRowGroup * (Nx + 1) * sizeof(float2);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_forward_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  dim3 grid((maxm + kRowGroup - 1) / kRowGroup, Nc, Nt);
+  k_forward_rows<<<grid, 256, smem, s>>>(zhat, kspace, rows, rowoff, Nx, Ny, Nt, Nc, fx,
+                                         (float)(1.0 / sqrt((double)Nx))); note_launch();
+  return cudaGetLastError();
+}
+
+// out[b*obs + c*ors + r] = in[b*ibs + r*C + c]
+__global__ void k_transpose(const float2* __restrict__ in, float2* __restrict__ out, int R, int C, long long ibs,
+                            long long obs, long long ors) {
+  __shared__ float2 tile[32][33];
+  const int b = blockIdx.z;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int k = ty; k < 32; k += 8) {
+    const int r = r0 + k, c = c0 + tx;
+    if (r < R && c < C) tile[k][tx] = in[b * ibs + (long long)r * C + c];
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int c = c0 + k, r = r0 + tx;
+    if (r < R && c < C) out[b * obs + (long long)c * ors + r] = tile[tx][k];
+  }
+}
+
+cudaError_t launch_transpose(const float2* in, float2* out, int B, int R, int C, long long ibs, long long obs,
+                             long long ors, cudaStream_t s) {
+  dim3 grid((C + 31) / 32, (R + 31) / 32, B);
+  k_transpose<<<grid, dim3(32, 8), 0, s>>>(in, out, R, C, ibs, obs, ors); note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace recon

@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads and exports every entry point of include/recon.h.
+
+These run without a GPU: only argument checks that return before any CUDA
+call are exercised here; everything that computes is in the `gpu` tests.
+"""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1203_4587_gb300 import build
+    return build.build()
+
+
+def _declared():
+    hdr = open(os.path.join(ROOT, "include", "recon.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(recon_[a-z_]+)\s*\(", hdr)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("recon_plan_create", "recon_solve", "recon_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = C.CDLL(libpath)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_lists_every_export():
+    from paper_1203_4587_gb300 import binding
+    assert sorted(binding.EXPORTS) == _declared()
+
+
+def test_invalid_arguments_rejected_before_any_cuda_call(libpath):
+    from paper_1203_4587_gb300 import binding
+    lib = binding.load(libpath)
+    h = C.c_void_p()
+    mask = (C.c_uint8 * 8)()
+    sens = (C.c_float * 16)()
+    o = binding.Opts()
+    lib.recon_default_opts(C.byref(o))
+    assert o.rho == pytest.approx(0.5) and o.max_iters == 50 and o.storage == 0 and o.objective == 1
+    cases = [
+        (0, 4, 2, 1, 0.01, 0.1, 0),       # Nx = 0
+        (4, 4, 2, 1, 0.01, 0.0, 0),       # mu = 0
+        (4, 4, 2, 1, -1.0, 0.1, 0),       # lambda < 0
+        (4, 4, 2, 1, 0.01, 0.1, 7),       # unknown prior
+    ]
+    for Nx, Ny, Nt, Nc, lam, mu, prior in cases:
+        st = lib.recon_plan_create(C.byref(h), Nx, Ny, Nt, Nc, C.cast(mask, C.c_void_p), C.cast(sens, C.c_void_p),
+                                   lam, mu, prior, None, None)
+        assert st == 1, (Nx, mu, lam, prior)
+        assert not h.value
+        assert lib.recon_last_error()
+    bad = binding.Opts()
+    lib.recon_default_opts(C.byref(bad))
+    bad.rho = -1.0
+    st = lib.recon_plan_create(C.byref(h), 4, 4, 2, 1, C.cast(mask, C.c_void_p), C.cast(sens, C.c_void_p),
+                               0.01, 0.1, 0, C.byref(bad), None)
+    assert st == 1
+    st = lib.recon_plan_create(C.byref(h), 4, 4096, 2, 1, C.cast(mask, C.c_void_p), C.cast(sens, C.c_void_p),
+                               0.01, 0.1, 0, None, None)
+    assert st == 7  # unsupported size
+    assert lib.recon_destroy(None) == 0
+    assert lib.recon_solve(None, None, None, None, None) == 1
+    assert lib.recon_status_string(2) == b"RECON_ERR_MASK_NOT_CARTESIAN"

@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP32 results must be within relative L2 1e-5 of the oracle (image
+after K iterations, and every J(k)); single operator applications (H, H',
+the packed inverses) within 1e-5 as well.  Inputs are the seeded synthetic
+workloads of ``synthdata``; the oracle sees the same complex64-rounded data.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synthdata
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def c64(x):
+    return np.asarray(x, dtype=np.complex64)
+
+
+def as64(x):
+    return np.asarray(x, dtype=np.complex64).astype(np.complex128)
+
+
+def gpu(x):
+    return torch.from_numpy(c64(x)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+def make(name="tiny", **over):
+    case = synthdata.make_case(name, **over)
+    # both sides see the complex64-rounded inputs
+    case.kspace = as64(case.kspace)
+    case.sens = as64(case.sens)
+    return case
+
+
+def plan_for(case, prior="tv", **opts):
+    from paper_1203_4587_gb300 import Plan
+    opts.setdefault("max_iters", case.iters)
+    return Plan(case.mask.astype(np.uint8), gpu(case.sens), case.lam, case.mu, prior=prior, rho=case.rho, **opts)
+
+
+SHAPES = [
+    dict(Nx=64, Ny=64, Nt=8, Nc=4, R=4),      # tiny workload
+    dict(Nx=45, Ny=40, Nt=3, Nc=3, R=3),      # radix 3/5, Ny not a multiple of 32
+    dict(Nx=20, Ny=97, Nt=2, Nc=2, R=4),      # prime length: direct DFT stage; odd block count
+    dict(Nx=33, Ny=96, Nt=5, Nc=1, R=2),      # single coil, 3 blocks (odd), radix 3 in Ny
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(str(s[k]) for k in ("Nx", "Ny", "Nt", "Nc")))
+def test_adjoint_and_forward_operators(shape):
+    case = make("tiny", **shape)
+    P = plan_for(case, max_iters=1)
+    b = host(P.adjoint(gpu(case.kspace)))
+    ref = oracle.adjoint_op(case.kspace, case.sens, case.mask)
+    assert rel(b, ref) < TOL
+    rng = np.random.default_rng(0)
+    x = as64(rng.standard_normal(case.x_true.shape) + 1j * rng.standard_normal(case.x_true.shape))
+    y = host(P.forward(gpu(x)))
+    yref = oracle.forward_op(x, case.sens, case.mask)
+    assert rel(y, yref) < TOL
+    # unsampled rows are exactly zero
+    assert np.all(y[~np.broadcast_to(case.mask[:, None, :, None], y.shape)] == 0)
+
+
+def test_frame_without_samples_and_full_frame():
+    case = make("tiny", Nx=16, Ny=32, Nt=3, Nc=2)
+    mask = case.mask.copy()
+    mask[1] = False
+    mask[2] = True
+    case.mask = mask
+    case.kspace = case.kspace * mask[:, None, :, None]
+    P = plan_for(case, max_iters=1)
+    assert rel(host(P.adjoint(gpu(case.kspace))), oracle.adjoint_op(case.kspace, case.sens, mask)) < TOL
+    A1 = host(P.export_inverse(3, 1))
+    np.testing.assert_allclose(A1, np.eye(32) / case.mu, atol=1e-6 / case.mu)
+
+
+@pytest.mark.parametrize("shape", SHAPES[:3], ids=["tiny", "45x40", "20x97"])
+def test_packed_inverse_blocks(shape):
+    case = make("tiny", **shape)
+    P = plan_for(case, max_iters=1)
+    Nt, Ny, Nx = case.x_true.shape
+    rng = np.random.default_rng(1)
+    for _ in range(4):
+        i, t = int(rng.integers(Nx)), int(rng.integers(Nt))
+        G = oracle.gram_blocks(case.sens, case.mask, [i])[t, 0]
+        Aref = oracle.inverse_blocks(G, case.mu)
+        A = host(P.export_inverse(i, t))
+        assert rel(A, Aref) < 2e-7          # FP64 factorisation, one FP32 rounding
+        res = A @ (case.mu * np.eye(Ny) + G) - np.eye(Ny)
+        assert np.abs(res).max() < 1e-5
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(str(s[k]) for k in ("Nx", "Ny", "Nt", "Nc")))
+def test_apply_inverse(shape):
+    case = make("tiny", **shape)
+    P = plan_for(case, max_iters=1)
+    rng = np.random.default_rng(2)
+    r = as64(rng.standard_normal(case.x_true.shape) + 1j * rng.standard_normal(case.x_true.shape))
+    x = host(P.inverse(gpu(r)))
+    inv = oracle.ColumnInverse(case.sens, case.mask, case.mu)
+    assert rel(x, inv.apply(r)) < TOL
+
+
+def _oracle_solve(case, prior, iters=None, cols=None, tol=0.0):
+    prob = oracle.Problem(case.kspace, case.sens, case.mask, case.mu, cols)
+    return prob.solve(prior, case.lam, case.mu, case.rho, case.iters if iters is None else iters, tol=tol)
+
+
+@pytest.mark.parametrize("prior", ["tv", "dft"])
+def test_tiny_workload_parity(prior):
+    """64x64, 8 frames, 4 coils, R=4, lambda=0.01, mu=0.1, 50 iterations."""
+    case = make("tiny")
+    P = plan_for(case, prior=prior)
+    x, info = P.solve(gpu(case.kspace))
+    xr, oinfo = _oracle_solve(case, prior)
+    assert info.iters == case.iters
+    assert rel(host(x), xr) < TOL
+    J = np.array(P.trace(case.iters + 1))
+    Jr = np.array(oinfo["J"])
+    assert np.max(np.abs(J - Jr) / Jr) < TOL
+    assert abs(info.J - Jr[-1]) / Jr[-1] < TOL and abs(info.J0 - Jr[0]) / Jr[0] < TOL
+
+
+EDGE = [
+    dict(Nx=12, Ny=16, Nt=1, Nc=2, R=2),      # one frame: no temporal differences
+    dict(Nx=10, Ny=32, Nt=2, Nc=3, R=2),      # two frames
+    dict(Nx=45, Ny=40, Nt=6, Nc=3, R=3),      # ragged Ny (padded block), radix 3/5
+    dict(Nx=18, Ny=96, Nt=7, Nc=2, R=4),      # odd block count, odd Nt (radix 7)
+    dict(Nx=8, Ny=64, Nt=22, Nc=2, R=8),      # Nt = 22 = 2*11 (generic radix stage)
+]
+
+
+@pytest.mark.parametrize("prior", ["tv", "dft"])
+@pytest.mark.parametrize("shape", EDGE, ids=lambda s: "x".join(str(s[k]) for k in ("Nx", "Ny", "Nt", "Nc")))
+def test_edge_shapes(shape, prior):
+    case = make("tiny", **shape)
+    iters = 12
+    P = plan_for(case, prior=prior, max_iters=iters)
+    x, info = P.solve(gpu(case.kspace))
+    xr, oinfo = _oracle_solve(case, prior, iters)
+    assert rel(host(x), xr) < TOL
+    J = np.array(P.trace(iters + 1))
+    assert np.max(np.abs(J - oinfo["J"]) / np.array(oinfo["J"])) < TOL
+
+
+def test_zero_iterations_returns_adjoint():
+    case = make("tiny", Nx=16, Ny=32, Nt=3, Nc=2)
+    P = plan_for(case, max_iters=0)
+    x, info = P.solve(gpu(case.kspace))
+    assert info.iters == 0
+    assert rel(host(x), oracle.adjoint_op(case.kspace, case.sens, case.mask)) < TOL
+
+
+def test_full_sampling_alg1_reaches_closed_form():
+    case = make("tiny", Nx=16, Ny=32, Nt=8, Nc=3, mask=np.ones((8, 32), bool), lam=0.05, mu=0.2)
+    P = plan_for(case, prior="dft", max_iters=60)
+    x, _ = P.solve(gpu(case.kspace))
+    b = oracle.adjoint_op(case.kspace, case.sens, case.mask)
+    w_star = oracle.soft(oracle.psi_dft(b), case.lam / 2)
+    assert rel(oracle.psi_dft(host(x)), w_star) < 1e-5
+
+
+def test_lambda_zero_full_sampling_is_sense():
+    case = make("tiny", Nx=16, Ny=32, Nt=4, Nc=3, mask=np.ones((4, 32), bool), lam=0.0, noise=0.0)
+    P = plan_for(case, prior="tv", max_iters=40)
+    x, _ = P.solve(gpu(case.kspace))
+    assert rel(host(x), case.x_true) < 1e-5
+
+
+def test_tolerance_stop_matches_oracle():
+    case = make("tiny")
+    _, full = _oracle_solve(case, "tv", 40)
+    J = np.array(full["J"])
+    d = (J[:-1] - J[1:]) / J[1:]
+    # the first k with 0 <= Delta(k) < tol, with tol chosen well inside a gap
+    tol = float(np.sqrt(d[9] * d[10])) if d[10] < d[9] else float(d[9] * 1.001)
+    _, ostop = _oracle_solve(case, "tv", 40, tol=tol)
+    P = plan_for(case, prior="tv", max_iters=40, tol=tol)
+    x, info = P.solve(gpu(case.kspace))
+    assert info.stopped == 1 and info.iters == ostop["iters"]
+    xr, _ = _oracle_solve(case, "tv", ostop["iters"])
+    assert rel(host(x), xr) < TOL
+
+
+def test_mask_not_cartesian_is_rejected():
+    from paper_1203_4587_gb300 import Plan, ReconError
+    case = make("tiny", Nx=16, Ny=32, Nt=2, Nc=2)
+    full = np.repeat(case.mask[:, :, None], 16, axis=2).astype(np.uint8)
+    Plan(full, gpu(case.sens), 0.01, 0.1).close()           # constant along kx: accepted
+    full[1, 3, 5] ^= 1
+    with pytest.raises(ReconError) as e:
+        Plan(full, gpu(case.sens), 0.01, 0.1)
+    assert e.value.status == 2
+
+
+@pytest.mark.parametrize("prior", ["tv", "dft"])
+def test_cardiac_workload_column_subset(prior):
+    """256x256, 32 frames, 12 coils, R=8, 100 iterations: sampled columns vs the oracle.
+
+    Columns are independent (Section IV-C), so the oracle restricted to a
+    seeded subset of columns computes those columns exactly.
+    """
+    case = make("cardiac")
+    P = plan_for(case, prior=prior)
+    x, info = P.solve(gpu(case.kspace))
+    assert info.iters == case.iters and np.isfinite(info.J)
+    cols = np.sort(np.random.default_rng(7).choice(256, size=4, replace=False))
+    xr, _ = _oracle_solve(case, prior, cols=cols)
+    xg = host(x)[:, :, cols]
+    assert rel(xg, xr) < TOL
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 5e-3), ("bf16", 3e-2)])
+def test_reduced_precision_storage_error_is_reported(storage, tol):
+    """16-bit packed inverses, FP32 arithmetic: error against FP64 stated, not bit-level."""
+    case = make("tiny")
+    P = plan_for(case, prior="tv", storage=storage)
+    x, info = P.solve(gpu(case.kspace))
+    xr, _ = _oracle_solve(case, "tv")
+    e = rel(host(x), xr)
+    assert e < tol, e
