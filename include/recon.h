@@ -75,9 +75,15 @@ typedef struct {
   int max_iters;    /* iterations K (default 50); 0 returns H'y */
   double tol;       /* stop when 0 <= Delta(k) < tol (Eq. r_ratio); 0 = run K iterations */
   int storage;      /* recon_storage of the packed inverses (default FP32) */
-  int objective;    /* 1 = evaluate J(k) every iteration (default 1; forced on when tol > 0) */
+  int objective;    /* J(k) every iteration: 0 = off (tol must be 0), 1 = fused (default), 2 = exact.
+                       Fused: the data term ||y - Hx||^2 = ||y||^2 - 2Re<H'y,x> + Re<x,r> - mu||x||^2
+                       uses (mu I + H'H) x = r of the inverse step, in the inverse kernel; its absolute
+                       error is about 2 eps ||x||^2 (eps = 2^-24), adequate for Delta(k) (Eq. r_ratio).
+                       Exact: ||y - Hx||^2 by explicit FFTs after each inverse step.  16-bit storage
+                       always uses the exact form. */
   int mask_full;    /* 1 = mask is [Nt][Ny][Nx] and must be constant along kx (default 0) */
-  int col_stages;   /* ring depth of the inverse kernel; 0 = autotuned (default 0) */
+  int col_stages;   /* ring depth of the inverse kernel, rounded down to a multiple of 8
+                       (min 8) and capped by shared memory; 0 = deepest that fits (default) */
   int profile;      /* 1 = time every kernel of a solve with CUDA events (default 0) */
 } recon_opts;
 

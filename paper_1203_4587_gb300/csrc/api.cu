@@ -118,6 +118,7 @@ struct recon_plan {
   double* trace_fid = nullptr;
   double* trace_prior = nullptr;
   double* trace_J = nullptr;
+  double* yy = nullptr;                // ||y||^2 over the sampled entries (FP64)
   int* flags = nullptr;
   FftPlanDev fx{}, fy{}, ft{};
   FftPlanDev64 fx64{}, fy64{};
@@ -248,15 +249,11 @@ ColParams base_col_params(const recon_plan* p) {
   c.col_elems = p->pk.col_elems;
   c.nunits = p->pk.nunits;
   c.units = p->units;
-  c.Nx = p->Nx; c.Ny = p->Ny; c.Nt = p->Nt; c.Nc = p->Nc; c.nb = p->pk.nb;
+  c.Nx = p->Nx; c.Ny = p->Ny; c.Nt = p->Nt; c.nb = p->pk.nb;
   c.ncols = p->Nx * p->Nt;
   c.stages = p->col_stages;
-  c.ncg = coil_group_for(p->Nc, p->Ny);
-  c.sens = p->sens;
-  c.yhat = p->yhat;
-  c.rows = p->rows;
-  c.rowoff = p->rowoff;
-  c.fy = p->fy;
+  c.mu = p->mu;
+  c.r_tma = ((size_t)p->Ny * sizeof(float2)) % 16 == 0 ? 1 : 0;
   c.flags = p->flags;
   return c;
 }
@@ -265,6 +262,18 @@ recon_status run_col(recon_plan* p, ColParams c, cudaStream_t s) {
   c.stages = p->col_stages;
   const size_t smem = col_inverse_smem(c, p->storage);
   RC(launch_col_inverse(c, p->storage, p->col_grid, smem, s));
+  return RECON_OK;
+}
+
+// ||y - H x||^2 of a field by explicit FFTs (J(0), and every J(k) when the
+// inverses are stored in 16 bit, where (mu I + H'H) x = r holds only to the
+// storage precision).
+recon_status run_objective(recon_plan* p, const float2* x, double* acc, cudaStream_t s) {
+  ObjParams o{};
+  o.Nx = p->Nx; o.Ny = p->Ny; o.Nt = p->Nt; o.Nc = p->Nc; o.ncg = coil_group_for(p->Nc, p->Ny);
+  o.x = x; o.sens = p->sens; o.yhat = p->yhat; o.rows = p->rows; o.rowoff = p->rowoff; o.fy = p->fy;
+  o.fid_acc = acc; o.flags = p->flags;
+  RC(launch_objective(o, s));
   return RECON_OK;
 }
 
@@ -278,40 +287,50 @@ recon_status to_user(recon_plan* p, const float2* in, float2* out, cudaStream_t 
   return RECON_OK;
 }
 
-// H'y in FP64 (rounded once to FP32) and the FP32 hybrid data for J(k).
-recon_status adjoint64(recon_plan* p, const float* kspace, float2* yhat32, float2* b, cudaStream_t s) {
-  RC(launch_hybrid_rows64(reinterpret_cast<const float2*>(kspace), p->yhat64, yhat32, p->rows, p->rowoff, p->maxm,
-                          p->Nx, p->Ny, p->Nt, p->Nc, p->fx64, s));
+// H'y in FP64 (rounded once to FP32), the FP32 hybrid data for J(k) and
+// ||y||^2 (into *yy, which must be zeroed first).
+recon_status adjoint64(recon_plan* p, const float* kspace, float2* yhat32, float2* b, double* yy, cudaStream_t s) {
+  RC(launch_hybrid_rows64(reinterpret_cast<const float2*>(kspace), p->yhat64, yhat32, yy, p->rows, p->rowoff,
+                          p->maxm, p->Nx, p->Ny, p->Nt, p->Nc, p->fx64, s));
   RC(launch_adjoint_combine64(p->yhat64, p->sens, b, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fy64, s));
   return RECON_OK;
 }
 
 recon_status prologue(recon_plan* p, const float* kspace, cudaStream_t s) {
-  return adjoint64(p, kspace, p->yhat, p->b, s);
+  RC(cudaMemsetAsync(p->yy, 0, sizeof(double), s));
+  return adjoint64(p, kspace, p->yhat, p->b, p->yy, s);
 }
 
 // K iterations from the initial point (x = H'y).  Leaves the image (internal
 // layout) in *result.
 recon_status iterate(recon_plan* p, cudaStream_t s, const float2** result) {
   const int K = p->opts.max_iters;
-  const bool obj = p->opts.objective || p->opts.tol > 0.0;
+  const bool obj = p->opts.objective != 0 || p->opts.tol > 0.0;
+  // mode 1 with FP32 inverses: data term from (mu I + H'H) x = r inside the
+  // inverse kernel; mode 2 or 16-bit inverses: explicit FFT objective.
+  const bool fused_obj = obj && p->opts.objective != 2 && p->storage == 0;
+  const double* yy = fused_obj ? p->yy : nullptr;
   const size_t nt = (size_t)K + 2;
   RC(cudaMemsetAsync(p->flags, 0, FLAG_COUNT * sizeof(int), s));
   RC(cudaMemsetAsync(p->trace_fid, 0, nt * sizeof(double), s));
   RC(cudaMemsetAsync(p->trace_prior, 0, nt * sizeof(double), s));
   RC(cudaMemsetAsync(p->trace_J, 0xff, nt * sizeof(double), s));  // NaN
   if (obj) {
-    ObjParams o{};
-    o.Nx = p->Nx; o.Ny = p->Ny; o.Nt = p->Nt; o.Nc = p->Nc; o.ncg = coil_group_for(p->Nc, p->Ny);
-    o.x = p->b; o.sens = p->sens; o.yhat = p->yhat; o.rows = p->rows; o.rowoff = p->rowoff; o.fy = p->fy;
-    o.fid_acc = p->trace_fid; o.flags = p->flags;
-    RC(launch_objective(o, s));
+    recon_status st = run_objective(p, p->b, p->trace_fid, s);
+    if (st != RECON_OK) return st;
   }
+  auto finalize = [&](int k) -> recon_status {
+    // J(0) is always the explicit objective (no yy term)
+    RC(launch_finalize(p->trace_fid, p->trace_prior, k == 0 ? nullptr : yy, p->trace_J, k, p->lam, p->opts.tol,
+                       p->flags, s));
+    return RECON_OK;
+  };
   const double mu2 = p->mu;
   const double rho = p->opts.rho;
   const long long npix = (long long)p->npix();
   ColParams c = base_col_params(p);
-  c.do_obj = obj ? 1 : 0;
+  c.do_obj = fused_obj ? 1 : 0;
+  recon_status st = RECON_OK;
   if (p->prior == RECON_PRIOR_TV) {
     const double mu1 = mu2 / rho;
     TvParams tp{};
@@ -330,19 +349,19 @@ recon_status iterate(recon_plan* p, cudaStream_t s, const float2** result) {
       p->mark(p->ev_tmp, p->n_tmp, true, s);
       RC(launch_tv_temporal(tp, s));
       p->mark(p->ev_tmp, p->n_tmp, false, s);
-      if (obj) RC(launch_finalize(p->trace_fid, p->trace_prior, p->trace_J, k - 1, p->lam, p->opts.tol, p->flags, s));
-      c.base = p->b; c.add = p->s2[par]; c.coef = (float)mu2; c.xout = p->x;
+      if (obj && (st = finalize(k - 1)) != RECON_OK) return st;
+      c.base = p->b; c.add = p->s2[par]; c.coef = (float)mu2; c.bsrc = p->b; c.xout = p->x;
       c.fid_acc = p->trace_fid + k;
       p->mark(p->ev_col, p->n_col, true, s);
-      recon_status st = run_col(p, c, s);
-      if (st != RECON_OK) return st;
+      if ((st = run_col(p, c, s)) != RECON_OK) return st;
       p->mark(p->ev_col, p->n_col, false, s);
+      if (obj && !fused_obj && (st = run_objective(p, p->x, p->trace_fid + k, s)) != RECON_OK) return st;
       m_in = p->s0[par]; d1_in = p->s1[par]; p_in = p->s2[par]; x_in = p->x;
     }
     if (obj) {
       tp.x = x_in; tp.write_state = 0; tp.prior_acc = p->trace_prior + K;
       RC(launch_tv_temporal(tp, s));
-      RC(launch_finalize(p->trace_fid, p->trace_prior, p->trace_J, K, p->lam, p->opts.tol, p->flags, s));
+      if ((st = finalize(K)) != RECON_OK) return st;
     }
     *result = (K == 0) ? p->b : p->x;
   } else {
@@ -363,19 +382,19 @@ recon_status iterate(recon_plan* p, cudaStream_t s, const float2** result) {
       p->mark(p->ev_tmp, p->n_tmp, true, s);
       RC(launch_dft_temporal(dp, s));
       p->mark(p->ev_tmp, p->n_tmp, false, s);
-      if (obj) RC(launch_finalize(p->trace_fid, p->trace_prior, p->trace_J, k - 1, p->lam, p->opts.tol, p->flags, s));
-      c.base = p->r; c.add = nullptr; c.coef = 0.f; c.xout = p->x;
+      if (obj && (st = finalize(k - 1)) != RECON_OK) return st;
+      c.base = p->r; c.add = nullptr; c.coef = 0.f; c.bsrc = p->b; c.xout = p->x;
       c.fid_acc = p->trace_fid + k;
       p->mark(p->ev_col, p->n_col, true, s);
-      recon_status st = run_col(p, c, s);
-      if (st != RECON_OK) return st;
+      if ((st = run_col(p, c, s)) != RECON_OK) return st;
       p->mark(p->ev_col, p->n_col, false, s);
+      if (obj && !fused_obj && (st = run_objective(p, p->x, p->trace_fid + k, s)) != RECON_OK) return st;
       xh_in = p->x; u_in = p->s0[par];
     }
     if (obj) {
       dp.xh = xh_in; dp.write_state = 0; dp.first = 1; dp.prior_acc = p->trace_prior + K;
       RC(launch_dft_temporal(dp, s));
-      RC(launch_finalize(p->trace_fid, p->trace_prior, p->trace_J, K, p->lam, p->opts.tol, p->flags, s));
+      if ((st = finalize(K)) != RECON_OK) return st;
     }
     *result = (K == 0) ? p->b : p->x;
   }
@@ -426,7 +445,8 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
   recon_opts o;
   recon_default_opts(&o);
   if (opts) o = *opts;
-  if (!(o.rho > 0.f) || o.max_iters < 0 || !(o.tol >= 0.0) || o.storage < 0 || o.storage > 2 || o.col_stages < 0)
+  if (!(o.rho > 0.f) || o.max_iters < 0 || !(o.tol >= 0.0) || o.storage < 0 || o.storage > 2 || o.col_stages < 0 ||
+      o.objective < 0 || o.objective > 2)
     return fail(RECON_ERR_INVALID_ARG, "invalid options");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
@@ -509,6 +529,7 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
   PC(p->alloc((void**)&p->trace_prior, nt * sizeof(double)));
   PC(p->alloc((void**)&p->trace_J, nt * sizeof(double)));
   PC(p->alloc((void**)&p->flags, FLAG_COUNT * sizeof(int)));
+  PC(p->alloc((void**)&p->yy, sizeof(double)));
 
   // tables
   std::vector<float2> tw(std::max(std::max(Nx, Ny), Nt));
@@ -584,9 +605,11 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
   // column-inverse launch shape: one persistent CTA per SM, ring as deep as fits
   {
     ColParams c = base_col_params(p);
-    c.do_obj = 1;
     const int maxst = col_inverse_max_stages(c, p->storage);
-    p->col_stages = o.col_stages > 0 ? std::min(o.col_stages, maxst) : std::min(16, maxst);
+    const int q = col_inverse_stage_quantum();
+    int st = o.col_stages > 0 ? std::min(o.col_stages, maxst) : maxst;
+    st = std::max(q, st / q * q);  // a positive multiple of the consumer warp count
+    p->col_stages = st;
     p->col_grid = std::max(1, std::min<int>((int)ncols, p->num_sms));
   }
   if (o.profile) {
@@ -683,7 +706,7 @@ recon_status recon_get_trace(recon_plan* p, double* J_host, int n) {
 recon_status recon_apply_adjoint(recon_plan* p, const float* kspace, float* image, void* stream) {
   if (!p || !kspace || !image) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  recon_status st = adjoint64(p, kspace, p->tmp_b, p->tmp_a, s);
+  recon_status st = adjoint64(p, kspace, p->tmp_b, p->tmp_a, nullptr, s);
   if (st != RECON_OK) return st;
   return to_user(p, p->tmp_a, reinterpret_cast<float2*>(image), s);
 }
@@ -708,7 +731,7 @@ recon_status recon_apply_inverse(recon_plan* p, const float* in, float* out, voi
   RC(cudaMemsetAsync(p->flags, 0, FLAG_COUNT * sizeof(int), s));
   ColParams c = base_col_params(p);
   c.do_obj = 0;
-  c.base = p->tmp_a; c.add = nullptr; c.coef = 0.f; c.xout = p->tmp_b;
+  c.base = p->tmp_a; c.add = nullptr; c.coef = 0.f; c.bsrc = p->tmp_a; c.xout = p->tmp_b;
   c.fid_acc = nullptr;
   st = run_col(p, c, s);
   if (st != RECON_OK) return st;

@@ -2,8 +2,8 @@
 //
 // k_col_inverse  x_{i,t} = A_{i,t} r_{i,t} for every column (Section IV-C,
 //                Eq. eigen_mu; Algorithm 2 x-update, Algorithm 1 w-update),
-//                with the objective's data term ||y - Hx||^2 of the new x
-//                fused into the epilogue (Eq. r_ratio needs J(k)).
+//                with the data term of J(k) for the new x fused into the
+//                epilogue (Eq. r_ratio needs J(k)).
 // k_tv_temporal  v, m and d1 updates of Algorithm 2 along t for every pixel.
 // k_dft_temporal v-update, dual and Psi / Psi' of Algorithm 1 along t.
 // k_objective    ||y - Hx||^2 of a given field (J(0)).
@@ -14,7 +14,7 @@ namespace recon {
 
 constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;
-constexpr int kColThreads = kConsumers + 32;  // + one producer warp
+constexpr int kColThreads = kConsumers + 96;  // + producer, r loader, column manager
 constexpr int kStageBytes = kRectElems * 8;   // largest unit (FP32 rect)
 
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
@@ -172,164 +172,286 @@ struct ConsumerBar {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+constexpr int kRSlots = 2;  // double-buffered r inputs / partial sums
+
 struct ColLayout {
-  size_t bars, ring, ycopy, rvec, xcol, units, red, fa, fb, total;
+  size_t bars, ring, ycopy, rvec, bvec, rslot, units, total;
 };
-__host__ __device__ inline ColLayout col_layout(int stages, int nb, int nunits, int ncg, int Ny, int do_obj) {
+__host__ __device__ inline ColLayout col_layout(int stages, int nb, int nunits) {
   ColLayout L;
   const size_t ny32 = (size_t)(nb + 1) * 32;
   size_t o = 0;
-  L.bars = o; o += 2 * (size_t)stages * 8;
+  // full[S], empty[S], rfull[2], rempty[2], rv_full[2], yc_empty[2], col_done[2]
+  L.bars = o; o += (2 * (size_t)stages + 5 * kRSlots) * 8;
   o = align_up(o, 128);
   L.ring = o; o += (size_t)stages * kStageBytes;
   o = align_up(o, 16);
-  L.ycopy = o; o += (size_t)kConsumerWarps * ny32 * 8;
-  L.rvec = o; o += ny32 * 8;
-  L.xcol = o; o += ny32 * 8;
+  L.ycopy = o; o += (size_t)kRSlots * kConsumerWarps * ny32 * 8;   // [buf][warp][ny32]
+  L.rvec = o; o += (size_t)kRSlots * ny32 * 8;
+  L.bvec = o; o += (size_t)kRSlots * ny32 * 8;
+  L.rslot = o; o += (size_t)kRSlots * 3 * ny32 * 8;   // [slot][base, add, b][ny32]
   L.units = o; o += (size_t)nunits * 16;
-  L.red = o; o += 32 * 8;
-  L.fa = o; o += do_obj ? (size_t)ncg * Ny * 8 : 0;
-  L.fb = o; o += do_obj ? (size_t)ncg * Ny * 8 : 0;
   L.total = align_up(o, 128);
   return L;
 }
 
+// Persistent column-inverse kernel, warp-specialised and free of block-wide
+// barriers in the main loop (all hand-offs are bounded mbarrier waits):
+//   warp 8   producer: streams the packed inverses with the TMA engine
+//            (cp.async.bulk, L2 evict_first) into a ring of S stages
+//   warp 9   r loader: bulk-copies each column's right-hand-side inputs
+//   warp 10  column manager: r = base + coef*add into rvec[n&1]; after the
+//            consumers are done, x = sum of the 8 partial y vectors, store,
+//            objective dot products, clear the partials
+//   warps 0-7 consumers: Hermitian matvec of each unit into their own
+//            partial y vector of buffer n&1, column after column
 template <typename E>
 __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   if (P.flags[FLAG_STOP]) return;
-  const ColLayout L = col_layout(P.stages, P.nb, P.nunits, P.ncg, P.Ny, P.do_obj);
+  const ColLayout L = col_layout(P.stages, P.nb, P.nunits);
   const int S = P.stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
   uint64_t* empty = full + S;
+  uint64_t* rfull = empty + S;
+  uint64_t* rempty = rfull + kRSlots;
+  uint64_t* rv_full = rempty + kRSlots;
+  uint64_t* yc_empty = rv_full + kRSlots;
+  uint64_t* col_done = yc_empty + kRSlots;
   unsigned char* ring = smem + L.ring;
   const int ny32 = (P.nb + 1) * 32;
   float2* ycopy = reinterpret_cast<float2*>(smem + L.ycopy);
   float2* rvec = reinterpret_cast<float2*>(smem + L.rvec);
-  float2* xcol = reinterpret_cast<float2*>(smem + L.xcol);
+  float2* bvec = reinterpret_cast<float2*>(smem + L.bvec);
+  float2* rslot = reinterpret_cast<float2*>(smem + L.rslot);
   int4* units = reinterpret_cast<int4*>(smem + L.units);
-  double* red = reinterpret_cast<double*>(smem + L.red);
-  float2* fa = reinterpret_cast<float2*>(smem + L.fa);
-  float2* fb = reinterpret_cast<float2*>(smem + L.fb);
-  __shared__ int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int u = tid; u < P.nunits; u += blockDim.x) units[u] = P.units[u];
+  for (int j = tid; j < kRSlots * kConsumerWarps * ny32; j += blockDim.x) ycopy[j] = make_float2(0.f, 0.f);
   if (tid == 0) {
     for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int s = 0; s < kRSlots; ++s) {
+      mbar_init(&rfull[s], P.r_tma ? 1 : 32);
+      mbar_init(&rempty[s], 1);
+      mbar_init(&rv_full[s], 1);
+      mbar_init(&yc_empty[s], 1);
+      mbar_init(&col_done[s], kConsumerWarps);
+    }
     fence_mbar_init();
-    s_abort = 0;
   }
   __syncthreads();
   constexpr int ES = Elem<E>::bytes;
+  const bool sep_b = P.do_obj && P.bsrc != P.base;
 
   if (warp == kConsumerWarps) {
     // ---------------- producer: stream packed inverses into the ring --------
     if (lane == 0) {
       const uint64_t pol = policy_evict_first();
       const unsigned char* Ab = reinterpret_cast<const unsigned char*>(P.A);
-      long long g = 0;
+      // stage st of the ring, wraps = completed passes over the ring (no
+      // divisions on the issue path)
+      int st = 0, wraps = 0;
       bool ok = true;
       for (int col = blockIdx.x; col < P.ncols && ok; col += gridDim.x) {
         const unsigned char* cb = Ab + (size_t)col * (size_t)P.col_elems * ES;
         for (int u = 0; u < P.nunits; ++u) {
-          const int st = (int)(g % S);
-          if (g >= S && !mbar_wait(&empty[st], (uint32_t)(((g / S) - 1) & 1), P.flags)) { ok = false; break; }
+          if (wraps > 0 && !mbar_wait(&empty[st], (uint32_t)((wraps - 1) & 1), P.flags)) { ok = false; break; }
           const int4 un = units[u];
           const uint32_t bytes = (uint32_t)((un.x == UNIT_TILE ? kTileElems : kRectElems) * ES);
           mbar_arrive_expect_tx(&full[st], bytes);
           bulk_g2s(ring + (size_t)st * kStageBytes, cb + (size_t)un.w * ES, bytes, &full[st], pol);
-          ++g;
+          if (++st == S) { st = 0; ++wraps; }
         }
       }
       if (!ok) {
         // error path: let every copy still in flight land before the CTA exits
+        const long long g = (long long)wraps * S + st;
         for (long long h = (g > S ? g - S : 0); h < g; ++h) {
-          uint64_t* b = &full[h % S];
+          uint64_t* bb = &full[h % S];
           const uint32_t par = (uint32_t)((h / S) & 1);
           unsigned long long t0 = global_ns();
-          while (!mbar_try_wait(b, par) && global_ns() - t0 < kWaitLimitNs) {}
+          while (!mbar_try_wait(bb, par) && global_ns() - t0 < kWaitLimitNs) {}
         }
       }
     }
     return;
   }
-
-  // ---------------- consumers (8 warps) --------------------------------------
-  const ConsumerBar cbar;
-  const float scl = rsqrtf((float)P.Ny);
-  float2* yw = ycopy + (size_t)warp * ny32;
-  double fid = 0.0;
-  long long gbase = 0;
-  bool failed = false;
-  for (int col = blockIdx.x; col < P.ncols; col += gridDim.x, gbase += P.nunits) {
-    const size_t cofs = (size_t)col * P.Ny;
-    for (int j = tid; j < ny32; j += kConsumers) {
-      float2 v = make_float2(0.f, 0.f);
-      if (j < P.Ny) {
-        v = P.base[cofs + j];
-        if (P.add) {
-          float2 a = P.add[cofs + j];
-          v.x = fmaf(P.coef, a.x, v.x); v.y = fmaf(P.coef, a.y, v.y);
+  if (warp == kConsumerWarps + 1) {
+    // ---------------- r loader: each column's inputs into a slot -------------
+    // With 16-byte aligned columns (Ny even) one lane moves them with the TMA
+    // engine; otherwise all lanes load them (unrolled) and arrive.
+    int n = 0;
+    for (int col = blockIdx.x; col < P.ncols; col += gridDim.x, ++n) {
+      const int sl = n % kRSlots;
+      if (n >= kRSlots && !mbar_wait(&rempty[sl], (uint32_t)(((n / kRSlots) - 1) & 1), P.flags)) break;
+      float2* d = rslot + (size_t)sl * 3 * ny32;
+      const size_t cofs = (size_t)col * P.Ny;
+      if (P.r_tma) {
+        if (lane == 0) {
+          const uint32_t bytes = (uint32_t)P.Ny * 8u;
+          const uint32_t total = bytes * (1u + (P.add ? 1u : 0u) + (sep_b ? 1u : 0u));
+          const uint64_t pol = policy_evict_first();
+          mbar_arrive_expect_tx(&rfull[sl], total);
+          bulk_g2s(d, P.base + cofs, bytes, &rfull[sl], pol);
+          if (P.add) bulk_g2s(d + ny32, P.add + cofs, bytes, &rfull[sl], pol);
+          if (sep_b) bulk_g2s(d + 2 * ny32, P.bsrc + cofs, bytes, &rfull[sl], pol);
+        }
+      } else {
+        for (int j0 = 0; j0 < P.Ny; j0 += 32 * 8) {
+          float2 va[8], vb[8], vc[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int j = j0 + q * 32 + lane;
+            if (j < P.Ny) {
+              va[q] = P.base[cofs + j];
+              if (P.add) vb[q] = P.add[cofs + j];
+              if (sep_b) vc[q] = P.bsrc[cofs + j];
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int j = j0 + q * 32 + lane;
+            if (j < P.Ny) {
+              d[j] = va[q];
+              if (P.add) d[ny32 + j] = vb[q];
+              if (sep_b) d[2 * ny32 + j] = vc[q];
+            }
+          }
+        }
+        mbar_arrive(&rfull[sl]);
+      }
+    }
+    if (P.r_tma && lane == 0) {
+      // copies of the last slots may still be in flight if the kernel quits early
+      for (int h = (n > kRSlots ? n - kRSlots : 0); h < n; ++h) {
+        unsigned long long t0 = global_ns();
+        while (!mbar_try_wait(&rfull[h % kRSlots], (uint32_t)((h / kRSlots) & 1)) && global_ns() - t0 < kWaitLimitNs) {}
+      }
+    }
+    return;
+  }
+  if (warp == kConsumerWarps + 2) {
+    // ---------------- column manager -----------------------------------------
+    // prepare(n): rvec[n&1] = base + coef*add (zero padded), bvec[n&1] = b
+    auto prepare = [&](int n) -> bool {
+      const int sl = n % kRSlots;
+      if (!mbar_wait(&rfull[sl], (uint32_t)((n / kRSlots) & 1), P.flags)) return false;
+      const float2* d = rslot + (size_t)sl * 3 * ny32;
+      float2* rv = rvec + (size_t)(n & 1) * ny32;
+      float2* bv = bvec + (size_t)(n & 1) * ny32;
+      for (int j = lane; j < ny32; j += 32) {
+        float2 v = make_float2(0.f, 0.f), bb = make_float2(0.f, 0.f);
+        if (j < P.Ny) {
+          v = d[j];
+          bb = sep_b ? d[2 * ny32 + j] : v;
+          if (P.add) {
+            const float2 a = d[ny32 + j];
+            v.x = fmaf(P.coef, a.x, v.x); v.y = fmaf(P.coef, a.y, v.y);
+          }
+        }
+        rv[j] = v;
+        bv[j] = bb;
+      }
+      __syncwarp();
+      if (lane == 0) { mbar_arrive(&rempty[sl]); mbar_arrive(&rv_full[n & 1]); }
+      return true;
+    };
+    int ncol = 0;
+    for (int col = blockIdx.x; col < P.ncols; col += gridDim.x) ++ncol;
+    double fid = 0.0;
+    bool ok = true;
+    for (int n = 0; n < ncol && n < kRSlots && ok; ++n) ok = prepare(n);
+    for (int n = 0; n < ncol && ok; ++n) {
+      const int bb = n & 1;
+      if (!mbar_wait(&col_done[bb], (uint32_t)((n >> 1) & 1), P.flags)) break;
+      const size_t cofs = (size_t)(blockIdx.x + (size_t)n * gridDim.x) * P.Ny;
+      float2* yc = ycopy + (size_t)bb * kConsumerWarps * ny32;
+      const float2* rv = rvec + (size_t)bb * ny32;
+      const float2* bv = bvec + (size_t)bb * ny32;
+      for (int j = lane; j < ny32; j += 32) {
+        float2 x = yc[j];
+        yc[j] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 1; w < kConsumerWarps; ++w) {
+          x = c_add(x, yc[(size_t)w * ny32 + j]);
+          yc[(size_t)w * ny32 + j] = make_float2(0.f, 0.f);
+        }
+        if (j < P.Ny) {
+          P.xout[cofs + j] = x;
+          if (P.do_obj) {
+            const float2 r = rv[j], b = bv[j];
+            // -2 Re<b, x> + Re<x, r> - mu |x|^2
+            fid += -2.0 * ((double)b.x * x.x + (double)b.y * x.y) + ((double)x.x * r.x + (double)x.y * r.y) -
+                   (double)P.mu * ((double)x.x * x.x + (double)x.y * x.y);
+          }
         }
       }
-      rvec[j] = v;
-    }
-    for (int j = tid; j < kConsumerWarps * ny32; j += kConsumers) ycopy[j] = make_float2(0.f, 0.f);
-    cbar();
-    for (int u = warp; u < P.nunits; u += kConsumerWarps) {
-      const long long g = gbase + u;
-      const int st = (int)(g % S);
-      if (failed) continue;
-      if (!mbar_wait(&full[st], (uint32_t)((g / S) & 1), P.flags)) { failed = true; continue; }
-      const int4 un = units[u];
-      const E* tl = reinterpret_cast<const E*>(ring + (size_t)st * kStageBytes);
-      if (un.x == UNIT_TILE) proc_tile<E>(tl, rvec, yw, un.y, un.z, lane);
-      else proc_rect<E>(tl, rvec, yw, un.y, un.z, lane);
-      if (lane == 0) mbar_arrive(&empty[st]);
-    }
-    cbar();
-    for (int j = tid; j < P.Ny; j += kConsumers) {
-      float2 s = ycopy[j];
-#pragma unroll
-      for (int w = 1; w < kConsumerWarps; ++w) s = c_add(s, ycopy[(size_t)w * ny32 + j]);
-      xcol[j] = s;
-      P.xout[cofs + j] = s;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&yc_empty[bb]);
+      if (n + kRSlots < ncol) ok = prepare(n + kRSlots);
     }
     if (P.do_obj) {
-      cbar();
-      const int t = col / P.Nx, i = col - t * P.Nx;
-      fid += column_fid(xcol, i, t, P.Nx, P.Ny, P.Nc, P.ncg, P.sens, P.yhat, P.rows, P.rowoff, P.fy, scl, fa, fb,
-                        tid, kConsumers, cbar);
+      fid = warp_sum(fid);
+      if (lane == 0) atomicAdd(P.fid_acc, fid);
     }
-    cbar();
-    if (tid == 0) s_abort = (*((volatile int*)&P.flags[FLAG_ERR]) != 0) || failed;
-    cbar();
-    if (s_abort || failed) break;
+    return;
   }
-  if (P.do_obj) {
-    double s = group_sum(fid, red, tid, kConsumers, cbar);
-    if (tid == 0) atomicAdd(P.fid_acc, s);
+
+  // ---------------- consumers (8 warps) --------------------------------------
+  // Unit g (counted across this CTA's columns) belongs to warp g mod 8, so a
+  // warp walks g = warp, warp+8, ...: within column n that is unit index u,
+  // and its ring stage advances by 8 per unit.  With S a multiple of 8 the
+  // previous fill of a stage was consumed by this same warp, so every parity
+  // wait is at most one phase ahead of its barrier.  Every column's rv/yc
+  // barriers are waited on (and col_done arrived at) even when the warp has
+  // no unit in that column, for the same reason.
+  int ncol = 0;
+  for (int col = blockIdx.x; col < P.ncols; col += gridDim.x) ++ncol;
+  int u = warp, st = warp;
+  uint32_t ph = 0;
+  for (int n = 0; n < ncol; ++n) {
+    const int bb = n & 1;
+    if (!mbar_wait(&rv_full[bb], (uint32_t)((n >> 1) & 1), P.flags)) break;
+    if (n >= 2 && !mbar_wait(&yc_empty[bb], (uint32_t)(((n >> 1) - 1) & 1), P.flags)) break;
+    const float2* rv = rvec + (size_t)bb * ny32;
+    float2* yw = ycopy + ((size_t)bb * kConsumerWarps + warp) * ny32;
+    bool failed = false;
+    for (; u < P.nunits; u += kConsumerWarps) {
+      if (!mbar_wait(&full[st], ph, P.flags)) { failed = true; break; }
+      const int4 un = units[u];
+      const E* tl = reinterpret_cast<const E*>(ring + (size_t)st * kStageBytes);
+      if (un.x == UNIT_TILE) proc_tile<E>(tl, rv, yw, un.y, un.z, lane);
+      else proc_rect<E>(tl, rv, yw, un.y, un.z, lane);
+      if (lane == 0) mbar_arrive(&empty[st]);
+      st += kConsumerWarps;
+      if (st >= S) { st -= S; ph ^= 1u; }
+    }
+    if (failed) break;
+    u -= P.nunits;
+    if (lane == 0) mbar_arrive(&col_done[bb]);
   }
 }
 
-size_t col_inverse_smem(const ColParams& p, int) {
-  return col_layout(p.stages, p.nb, p.nunits, p.ncg, p.Ny, p.do_obj).total;
-}
+size_t col_inverse_smem(const ColParams& p, int) { return col_layout(p.stages, p.nb, p.nunits).total; }
 
+// Largest ring depth that fits, a multiple of the consumer warp count (the
+// parity waits rely on it; see the consumer loop).
 int col_inverse_max_stages(const ColParams& p, int storage) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  int s = 32;
-  while (s > 2) {
+  int s = 4 * kConsumerWarps;
+  while (s > kConsumerWarps) {
     ColParams q = p;
     q.stages = s;
     if (col_inverse_smem(q, storage) + 1024 <= (size_t)optin) break;
-    --s;
+    s -= kConsumerWarps;
   }
   return s;
 }
+
+int col_inverse_stage_quantum() { return kConsumerWarps; }
 
 template <typename E>
 static cudaError_t launch_col_t(const ColParams& p, int grid, size_t smem, cudaStream_t s) {
@@ -353,83 +475,104 @@ cudaError_t launch_col_inverse(const ColParams& p, int storage, int grid, size_t
 }
 
 // ---------------------------------------------------------------------------
-// Algorithm 2 temporal step, one thread per pixel (column layout keeps the
-// threads of a warp on consecutive j, so every access is coalesced):
+// Algorithm 2 temporal step, one thread per pixel over a tile of kTvPix
+// pixels (column layout keeps a tile's pixels contiguous for every t):
 //   v  = S(D_t m + d1, lambda/(2 mu1))
 //   m' = (rho I + D_t'D_t)^{-1} [D_t'(v - d1) + rho (x + d2)]    (Thomas)
 //   d1' = d1 - (v - D_t m')
 // with d2 = x - p, and p' = m' - d2 handed to the inverse step, which forms
 // r = H'y + mu2 (m' - d2) = b + mu2 p'.  The next d2 is then x' - p'.
-// Also accumulates ||D_t x||_1 of the incoming x (the prior term of J).
+// The tile's inputs are staged in shared memory with asynchronous copies
+// (all in flight at once), then both sweeps run from shared memory.  Also
+// accumulates ||D_t x||_1 of the incoming x (the prior term of J).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_tv_temporal(TvParams P) {
-  extern __shared__ float2 sm_tv[];
+__global__ void __launch_bounds__(64) k_tv_temporal(TvParams P) {
+  extern __shared__ __align__(16) float2 sm_tv[];
   __shared__ double red[32];
   if (P.flags[FLAG_STOP]) return;
-  const int nth = blockDim.x, tid = threadIdx.x;
-  float2* sd = sm_tv;                  // forward-sweep values d'_t
-  float2* se = sm_tv + P.Nt * nth;     // e_t = d1_t - v_t
+  const int tid = threadIdx.x, PX = blockDim.x, Nt = P.Nt;
   const long long N = P.npix;
-  const long long pix = (long long)blockIdx.x * nth + tid;
-  double tv = 0.0;
-  if (pix < N) {
-    float2 x_prev = make_float2(0.f, 0.f);
-    float2 m_t = P.write_state ? P.m[pix] : make_float2(0.f, 0.f);
-    float2 e_prev = make_float2(0.f, 0.f), d_prev = make_float2(0.f, 0.f);
-    for (int t = 0; t < P.Nt; ++t) {
-      const float2 x_t = P.x[t * N + pix];
-      if (t > 0) tv += (double)c_abs(c_sub(x_t, x_prev));
-      x_prev = x_t;
-      if (!P.write_state) continue;
-      const float2 p_t = P.p[t * N + pix];
-      float2 e_t = make_float2(0.f, 0.f), m_n = make_float2(0.f, 0.f);
-      if (t + 1 < P.Nt) {
-        m_n = P.m[(t + 1) * N + pix];
-        const float2 d1_t = P.d1 ? P.d1[t * N + pix] : make_float2(0.f, 0.f);
-        const float2 v = c_soft(c_add(c_sub(m_n, m_t), d1_t), P.tau1);
-        e_t = c_sub(d1_t, v);
+  const long long pix0 = (long long)blockIdx.x * PX;
+  const int npx = (int)min((long long)PX, N - pix0);
+  // [Nt][PX] tiles: m, d1, x (later e = d1 - v), p (later f = p - x), d'
+  float2* sm_m = sm_tv;
+  float2* sm_d1 = sm_m + (size_t)Nt * PX;
+  float2* sm_x = sm_d1 + (size_t)Nt * PX;
+  float2* sm_p = sm_x + (size_t)Nt * PX;
+  float2* sm_dp = sm_p + (size_t)Nt * PX;
+  if (tid < npx) {
+    for (int t = 0; t < Nt; ++t) {
+      const long long g = t * N + pix0 + tid;
+      cp_async8(&sm_x[t * PX + tid], P.x + g);
+      if (P.write_state) {
+        cp_async8(&sm_m[t * PX + tid], P.m + g);
+        cp_async8(&sm_p[t * PX + tid], P.p + g);
+        if (P.d1 && t + 1 < Nt) cp_async8(&sm_d1[t * PX + tid], P.d1 + g);
       }
-      // rhs = D'(v - d1) + rho (x + d2),  (D'u)_t = u_{t-1} - u_t,  u = -e
-      float2 rhs = c_sub(e_t, e_prev);
-      rhs.x = fmaf(P.rho, 2.f * x_t.x - p_t.x, rhs.x);
-      rhs.y = fmaf(P.rho, 2.f * x_t.y - p_t.y, rhs.y);
-      const float inv = __ldg(P.thomas + t);
-      const float2 dp = c_scale(c_add(rhs, d_prev), inv);
-      sd[t * nth + tid] = dp;
-      se[t * nth + tid] = e_t;
-      d_prev = dp; e_prev = e_t; m_t = m_n;
+    }
+  }
+  cp_async_wait_all();
+  double tv = 0.0;
+  if (tid < npx) {
+    float2 x_prev = sm_x[tid];
+    for (int t = 1; t < Nt; ++t) {
+      const float2 x_t = sm_x[t * PX + tid];
+      tv += (double)c_abs(c_sub(x_t, x_prev));
+      x_prev = x_t;
     }
     if (P.write_state) {
-      float2 mnext = make_float2(0.f, 0.f);
-      for (int t = P.Nt - 1; t >= 0; --t) {
+      float2 m_t = sm_m[tid];
+      float2 e_prev = make_float2(0.f, 0.f), d_prev = make_float2(0.f, 0.f);
+      for (int t = 0; t < Nt; ++t) {
+        const float2 x_t = sm_x[t * PX + tid], p_t = sm_p[t * PX + tid];
+        float2 e_t = make_float2(0.f, 0.f), m_n = make_float2(0.f, 0.f);
+        if (t + 1 < Nt) {
+          m_n = sm_m[(t + 1) * PX + tid];
+          const float2 d1_t = P.d1 ? sm_d1[t * PX + tid] : make_float2(0.f, 0.f);
+          const float2 v = c_soft(c_add(c_sub(m_n, m_t), d1_t), P.tau1);
+          e_t = c_sub(d1_t, v);
+        }
+        // rhs = D'(v - d1) + rho (x + d2),  (D'u)_t = u_{t-1} - u_t,  u = -e
+        float2 rhs = c_sub(e_t, e_prev);
+        rhs.x = fmaf(P.rho, 2.f * x_t.x - p_t.x, rhs.x);
+        rhs.y = fmaf(P.rho, 2.f * x_t.y - p_t.y, rhs.y);
         const float inv = __ldg(P.thomas + t);
-        const float2 dp = sd[t * nth + tid];
+        const float2 dp = c_scale(c_add(rhs, d_prev), inv);
+        sm_dp[t * PX + tid] = dp;
+        sm_x[t * PX + tid] = e_t;               // x no longer needed: keep e
+        sm_p[t * PX + tid] = c_sub(p_t, x_t);   // keep f = p - x
+        d_prev = dp; e_prev = e_t; m_t = m_n;
+      }
+      float2 mnext = make_float2(0.f, 0.f);
+      for (int t = Nt - 1; t >= 0; --t) {
+        const float inv = __ldg(P.thomas + t);
+        const float2 dp = sm_dp[t * PX + tid];
         const float2 mt = make_float2(fmaf(inv, mnext.x, dp.x), fmaf(inv, mnext.y, dp.y));
-        if (t + 1 < P.Nt) P.d1_out[t * N + pix] = c_add(se[t * nth + tid], c_sub(mnext, mt));
-        const float2 x_t = P.x[t * N + pix], p_t = P.p[t * N + pix];
-        P.p_out[t * N + pix] = c_add(mt, c_sub(p_t, x_t));
-        P.m_out[t * N + pix] = mt;
+        const long long g = t * N + pix0 + tid;
+        if (t + 1 < Nt) P.d1_out[g] = c_add(sm_x[t * PX + tid], c_sub(mnext, mt));
+        P.p_out[g] = c_add(mt, sm_p[t * PX + tid]);
+        P.m_out[g] = mt;
         mnext = mt;
       }
     }
   }
-  const double s = group_sum(tv, red, tid, nth, BlockBar());
+  const double s = group_sum(tv, red, tid, PX, BlockBar());
   if (tid == 0) atomicAdd(P.prior_acc, s);
 }
 
 cudaError_t launch_tv_temporal(const TvParams& p, cudaStream_t s) {
-  // 2 x Nt x nth complex values of per-thread sweep storage must fit (Nt <= 128)
-  int nth = 128;
-  while (nth > 32 && 2 * (size_t)p.Nt * nth * sizeof(float2) > 160 * 1024) nth >>= 1;
-  const size_t smem = p.write_state ? 2 * (size_t)p.Nt * nth * sizeof(float2) : 0;
+  // five [Nt][PX] complex tiles must fit (Nt <= 128)
+  int px = 64;
+  while (px > 32 && 5 * (size_t)p.Nt * px * sizeof(float2) > 200 * 1024) px >>= 1;
+  const size_t smem = 5 * (size_t)p.Nt * px * sizeof(float2);
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(k_tv_temporal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  const long long grid = (p.npix + nth - 1) / nth;
-  k_tv_temporal<<<(unsigned)grid, nth, smem, s>>>(p); note_launch();
+  const long long grid = (p.npix + px - 1) / px;
+  k_tv_temporal<<<(unsigned)grid, px, smem, s>>>(p); note_launch();
   return cudaGetLastError();
 }
 
@@ -456,8 +599,10 @@ __global__ void __launch_bounds__(256) k_dft_temporal(DftParams P) {
   const int npx = (int)min((long long)kDftPix, N - pix0);
   for (int idx = tid; idx < Nt * kDftPix; idx += nth) {
     const int t = idx / kDftPix, pp = idx - t * kDftPix;
-    A[idx] = (pp < npx) ? P.xh[t * N + pix0 + pp] : make_float2(0.f, 0.f);
+    if (pp < npx) cp_async8(&A[idx], P.xh + t * N + pix0 + pp);
+    else A[idx] = make_float2(0.f, 0.f);
   }
+  cp_async_wait_all();
   __syncthreads();
   const BlockBar bar;
   float2* W = fft_run(A, B, kDftPix, 1, kDftPix, P.ft, false, tid, nth, bar);
@@ -545,11 +690,11 @@ cudaError_t launch_objective(const ObjParams& p, cudaStream_t s) {
 // J(k) = ||y - Hx||^2 + lambda * prior, Delta(k) (Eq. r_ratio) and the stop
 // flag: later launches see flags[FLAG_STOP] and return at once.
 // ---------------------------------------------------------------------------
-__global__ void k_finalize(const double* fid, const double* prior, double* J, int k, float lam, double tol,
-                           int* flags) {
+__global__ void k_finalize(const double* fid, const double* prior, const double* yy, double* J, int k, float lam,
+                           double tol, int* flags) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (flags[FLAG_STOP]) return;
-  const double Jk = fid[k] + (double)lam * prior[k];
+  const double Jk = fid[k] + (yy ? *yy : 0.0) + (double)lam * prior[k];
   J[k] = Jk;
   if (!isfinite(Jk)) atomicOr(&flags[FLAG_ERR], DEV_ERR_NONFINITE);
   if (tol > 0.0 && k >= 1) {
@@ -561,9 +706,9 @@ __global__ void k_finalize(const double* fid, const double* prior, double* J, in
   }
 }
 
-cudaError_t launch_finalize(const double* fid, const double* prior, double* J, int k, float lam, double tol,
-                            int* flags, cudaStream_t s) {
-  k_finalize<<<1, 32, 0, s>>>(fid, prior, J, k, lam, tol, flags); note_launch();
+cudaError_t launch_finalize(const double* fid, const double* prior, const double* yy, double* J, int k, float lam,
+                            double tol, int* flags, cudaStream_t s) {
+  k_finalize<<<1, 32, 0, s>>>(fid, prior, yy, J, k, lam, tol, flags); note_launch();
   return cudaGetLastError();
 }
 

@@ -53,21 +53,21 @@ struct ColParams {           // data-consistency inverse x = A r, per column
   long long col_elems;
   int nunits;
   const int4* units;         // {kind, p, q, elem offset}
-  int Nx, Ny, Nt, Nc, nb;
+  int Nx, Ny, Nt, nb;
   int ncols;
   int stages;                // ring depth
   const float2* base;        // r = base + coef * add   ([Nt][Nx][Ny])
   const float2* add;         // may be null
   float coef;
+  const float2* bsrc;        // H'y for the objective term (may equal base)
+  int r_tma;                 // 1: r inputs move by bulk copy (Ny*8 a multiple of 16)
   float2* xout;
-  // objective epilogue: ||y - H x||^2 of this column
+  // data term of J for the new x, with (mu I + H'H) x = r:
+  //   ||y - Hx||^2 = ||y||^2 - 2 Re<H'y, x> + Re<x, r> - mu ||x||^2
+  // the kernel adds the last three terms to *fid_acc (||y||^2 comes from the
+  // prologue).
   int do_obj;
-  int ncg;                   // coils per FFT group
-  const float2* sens;        // [Nx][Nc][Ny]
-  const float2* yhat;
-  const int* rows;
-  const int* rowoff;
-  FftPlanDev fy;
+  float mu;
   double* fid_acc;
   int* flags;
 };
@@ -126,11 +126,13 @@ void note_launch();
 cudaError_t launch_col_inverse(const ColParams& p, int storage, int grid, size_t smem, cudaStream_t s);
 size_t col_inverse_smem(const ColParams& p, int storage);
 int col_inverse_max_stages(const ColParams& p, int storage);
+int col_inverse_stage_quantum();  // ring depth must be a positive multiple of this
 cudaError_t launch_tv_temporal(const TvParams& p, cudaStream_t s);
 cudaError_t launch_dft_temporal(const DftParams& p, cudaStream_t s);
 cudaError_t launch_objective(const ObjParams& p, cudaStream_t s);
-cudaError_t launch_finalize(const double* fid, const double* prior, double* J, int k, float lam, double tol,
-                            int* flags, cudaStream_t s);
+// J(k) = fid[k] + (yy ? *yy : 0) + lambda prior[k]; Delta(k); stop flag.
+cudaError_t launch_finalize(const double* fid, const double* prior, const double* yy, double* J, int k, float lam,
+                            double tol, int* flags, cudaStream_t s);
 
 // prologue / operators
 cudaError_t launch_hybrid_rows(const void* kspace, int kdtype, const float* kscale, float2* yhat, const int* rows,
@@ -140,8 +142,9 @@ cudaError_t launch_adjoint_combine(const float2* yhat, const float2* sens, float
                                    const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, cudaStream_t s);
 // FP64 H'y prologue: the solution of the iterations is ~100x more sensitive to
 // errors in H'y than to rounding elsewhere, so H'y is formed in FP64 and
-// rounded once.  yhat32 receives the FP32 rounding of the hybrid data.
-cudaError_t launch_hybrid_rows64(const float2* kspace, double2* yhat64, float2* yhat32, const int* rows,
+// rounded once.  yhat32 receives the FP32 rounding of the hybrid data; *yy
+// accumulates ||y||^2 over the sampled entries (may be null).
+cudaError_t launch_hybrid_rows64(const float2* kspace, double2* yhat64, float2* yhat32, double* yy, const int* rows,
                                  const int* rowoff, int maxm, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fx,
                                  cudaStream_t s);
 cudaError_t launch_adjoint_combine64(const double2* yhat64, const float2* sens, float2* b, const int* rows,

@@ -28,9 +28,11 @@ static int row_group(int Nx) {
 // writes the FP32 rounding (yhat32) used by the objective.
 template <typename T>
 __global__ void __launch_bounds__(256) k_hybrid_rows(const float2* __restrict__ ksp, T* __restrict__ yhat,
-                                                     float2* __restrict__ yhat32, const int* __restrict__ rows,
+                                                     float2* __restrict__ yhat32, double* __restrict__ yy,
+                                                     const int* __restrict__ rows,
                                                      const int* __restrict__ rowoff, int Nx, int Ny, int Nt, int Nc,
                                                      int G, FftPlanT<T> fx, double scl) {
+  __shared__ double red[32];
   extern __shared__ __align__(16) unsigned char sm_rows_raw[];
   T* sm_rows = reinterpret_cast<T*>(sm_rows_raw);
   const int t = blockIdx.z, c = blockIdx.y, m0 = blockIdx.x * G;
@@ -41,12 +43,19 @@ __global__ void __launch_bounds__(256) k_hybrid_rows(const float2* __restrict__ 
   T* A = sm_rows;
   T* B = sm_rows + (size_t)G * ss;
   const int tid = threadIdx.x, nth = blockDim.x;
+  double e2 = 0.0;  // ||y||^2 over these sampled rows
   for (int idx = tid; idx < g * Nx; idx += nth) {
     const int gg = idx / Nx, kx = idx - gg * Nx;
     const int row = rows[r0 + m0 + gg];
-    A[gg * ss + kx] = from_f2<T>(ksp[(((size_t)t * Nc + c) * Ny + row) * Nx + kx]);
+    const float2 v = ksp[(((size_t)t * Nc + c) * Ny + row) * Nx + kx];
+    e2 += c_abs2d(v);
+    A[gg * ss + kx] = from_f2<T>(v);
   }
   __syncthreads();
+  if (yy) {
+    const double s2 = group_sum(e2, red, tid, nth, BlockBar());
+    if (tid == 0) atomicAdd(yy, s2);
+  }
   const BlockBar bar;
   T* R = fft_run(A, B, g, ss, 1, fx, true, tid, nth, bar);
   const size_t base = (size_t)r0 * Nx * Nc;
@@ -60,8 +69,9 @@ __global__ void __launch_bounds__(256) k_hybrid_rows(const float2* __restrict__ 
 }
 
 template <typename T>
-static cudaError_t launch_rows_t(const float2* ksp, T* yhat, float2* yhat32, const int* rows, const int* rowoff,
-                                 int maxm, int Nx, int Ny, int Nt, int Nc, const FftPlanT<T>& fx, cudaStream_t s) {
+static cudaError_t launch_rows_t(const float2* ksp, T* yhat, float2* yhat32, double* yy, const int* rows,
+                                 const int* rowoff, int maxm, int Nx, int Ny, int Nt, int Nc, const FftPlanT<T>& fx,
+                                 cudaStream_t s) {
   if (maxm <= 0) return cudaSuccess;
   const int G = row_group<T>(Nx);
   const size_t smem = 2 * (size_t)G * (Nx + 1) * sizeof(T);
@@ -72,7 +82,7 @@ static cudaError_t launch_rows_t(const float2* ksp, T* yhat, float2* yhat32, con
     configured = smem;
   }
   dim3 grid((maxm + G - 1) / G, Nc, Nt);
-  k_hybrid_rows<T><<<grid, 256, smem, s>>>(ksp, yhat, yhat32, rows, rowoff, Nx, Ny, Nt, Nc, G, fx,
+  k_hybrid_rows<T><<<grid, 256, smem, s>>>(ksp, yhat, yhat32, yy, rows, rowoff, Nx, Ny, Nt, Nc, G, fx,
                                            1.0 / sqrt((double)Nx)); note_launch();
   return cudaGetLastError();
 }
@@ -82,14 +92,14 @@ cudaError_t launch_hybrid_rows(const void* kspace, int kdtype, const float* ksca
                                cudaStream_t s) {
   (void)kscale;
   if (kdtype != 0) return cudaErrorInvalidValue;
-  return launch_rows_t<float2>(static_cast<const float2*>(kspace), yhat, nullptr, rows, rowoff, maxm, Nx, Ny, Nt,
-                               Nc, fx, s);
+  return launch_rows_t<float2>(static_cast<const float2*>(kspace), yhat, nullptr, nullptr, rows, rowoff, maxm, Nx,
+                               Ny, Nt, Nc, fx, s);
 }
 
-cudaError_t launch_hybrid_rows64(const float2* kspace, double2* yhat64, float2* yhat32, const int* rows,
+cudaError_t launch_hybrid_rows64(const float2* kspace, double2* yhat64, float2* yhat32, double* yy, const int* rows,
                                  const int* rowoff, int maxm, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fx,
                                  cudaStream_t s) {
-  return launch_rows_t<double2>(kspace, yhat64, yhat32, rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, s);
+  return launch_rows_t<double2>(kspace, yhat64, yhat32, yy, rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, s);
 }
 
 constexpr int kCoilGroupMax = 8;
