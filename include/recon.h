@@ -173,6 +173,32 @@ recon_status recon_apply_inverse(recon_plan* plan, const float* in, float* out, 
  * `dense`), for inspection and tests.  0 <= i < Nx, 0 <= t < Nt. */
 recon_status recon_export_inverse(recon_plan* plan, int i, int t, float* dense, void* stream);
 
+/* Allocation-free computation of per-column inverses, for callers that
+ * cannot call cudaMalloc: for example a real-time scanner pipeline that
+ * reserves all of its device memory at start-up and must not allocate while
+ * acquiring (an allocation can block and fragment the heap), or code embedded
+ * in a host framework whose own allocator owns the device.  The paper has no
+ * counterpart; it is the plan's factorisation offered without a plan.
+ *
+ * For each of `nblk` blocks b it writes A_b = (mu I + C_b (.) K_b)^{-1}, with
+ * C_b = F_v' P_b F_v from the row mask of the block and
+ * K_b[j][k] = sum_c conj(s_{b,c,j}) s_{b,c,k}, computed in FP64 and rounded
+ * once to FP32.
+ *   mask  device uint8 [nblk][Ny] (nonzero = sampled row)
+ *   sens  device complex64 [nblk][Nc][Ny] (the coil profiles of the block's column)
+ *   out   device complex64 [nblk][Ny][Ny], dense Hermitian, written
+ * Allocates nothing: the FP64 workspace is a fixed 16 MiB static device array
+ * that every GPU loading this library holds until exit.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls
+ * share the array, so calls that overlap on the GPU race; the call
+ * synchronises `stream` before returning.
+ * Errors: INVALID_ARG; UNSUPPORTED when Ny > 1023 (one Ny x Ny FP64 workspace
+ * must fit in the array) or (Nc + 2) * Ny > 12800; NONFINITE for a block that
+ * is not positive definite; CUDA. */
+recon_status recon_gram_inverse_noalloc(int Ny, int Nc, int nblk, const uint8_t* mask, const float* sens, float mu,
+                                        float* out, void* stream);
+
 /* Bytes of the packed inverses streamed per ADMM iteration. */
 size_t recon_inverse_bytes(const recon_plan* plan);
 

@@ -30,7 +30,7 @@ STATUS = {0: "RECON_OK", 1: "RECON_ERR_INVALID_ARG", 2: "RECON_ERR_MASK_NOT_CART
 EXPORTS = ["recon_default_opts", "recon_plan_create", "recon_solve", "recon_solve_host", "recon_get_trace",
            "recon_destroy", "recon_apply_adjoint", "recon_apply_forward", "recon_apply_inverse",
            "recon_export_inverse", "recon_inverse_bytes", "recon_status_string", "recon_last_error",
-           "recon_get_profile", "recon_kernel_launches"]
+           "recon_get_profile", "recon_kernel_launches", "recon_gram_inverse_noalloc"]
 
 
 class Opts(C.Structure):
@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
     lib.recon_get_profile.restype = i
     lib.recon_kernel_launches.argtypes = []
     lib.recon_kernel_launches.restype = C.c_ulonglong
+    lib.recon_gram_inverse_noalloc.argtypes = [i, i, i, vp, fp, f, fp, vp]
+    lib.recon_gram_inverse_noalloc.restype = i
     _lib = lib
     return lib
 
@@ -225,6 +227,22 @@ class Plan:
     @property
     def inverse_bytes(self) -> int:
         return int(load().recon_inverse_bytes(self._h))
+
+
+def gram_inverse_noalloc(mask_rows, sens_cols, mu, out=None, stream=None):
+    """Allocation-free per-column inverses (recon_gram_inverse_noalloc).
+
+    mask_rows uint8 [nblk, Ny] and sens_cols complex64 [nblk, Nc, Ny] on the
+    GPU; returns complex64 [nblk, Ny, Ny] (``out`` if given).
+    """
+    m = torch.as_tensor(mask_rows).to(torch.uint8).contiguous()
+    s = _c64(sens_cols, "cuda")
+    nblk, Nc, Ny = s.shape
+    if out is None:
+        out = torch.empty((nblk, Ny, Ny), dtype=torch.complex64, device="cuda")
+    _check(load().recon_gram_inverse_noalloc(int(Ny), int(Nc), int(nblk), _ptr(m), _ptr(s), float(mu), _ptr(out),
+                                             _stream(stream)))
+    return out
 
 
 def kernel_launches() -> int:

@@ -44,6 +44,7 @@ namespace recon {
 
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void set_last_error(const std::string& why) { g_last_error = why; }
 
 void fill_twiddles_host(int n, float2* tw) {
   for (int k = 0; k < n; ++k) {

@@ -12,6 +12,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
@@ -121,6 +122,8 @@ struct ObjParams {           // ||y - H x||^2 of a given field (no inverse)
 
 // Counts kernel launches of this library (process-wide); every launcher calls it.
 void note_launch();
+// Sets the message recon_last_error() returns on the calling thread.
+void set_last_error(const std::string& why);
 
 // ---- launchers (return cudaGetLastError()) ---------------------------------
 cudaError_t launch_col_inverse(const ColParams& p, int storage, int grid, size_t smem, cudaStream_t s);
