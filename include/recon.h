@@ -151,6 +151,33 @@ recon_status recon_get_profile(recon_plan* plan, recon_profile* out);
 /* Number of CUDA kernels this library has launched in this process. */
 unsigned long long recon_kernel_launches(void);
 
+/* ---- batched solves --------------------------------------------------------
+ * Many independent slices (plans of uneven Nx, Ny, Nt, Nc) solved together:
+ * every ADMM step is one launch over all slices (the column-inverse kernel
+ * takes a work list of (slice, column) pairs balanced by bytes across the
+ * SMs; the temporal kernel covers every slice's pixel tiles), and the whole
+ * batched solve is captured once as a CUDA graph and replayed.  Columns and
+ * slices are independent (Section IV-C), so each slice's result equals its
+ * own recon_solve. */
+typedef struct recon_batch recon_batch; /* opaque, owned by the library */
+
+/* Prepares a batch over `n` plans (borrowed: they must outlive the batch).
+ * The plans must share prior, max_iters, storage and objective mode and live
+ * on one device.  Errors: INVALID_ARG, OOM, CUDA. */
+recon_status recon_batch_create(recon_batch** out, recon_plan* const* plans, int n);
+
+/* Solves every slice: kspace[q] and image[q] are device buffers laid out as
+ * for recon_solve.  The first call with a given set of buffers runs the
+ * launches directly and captures them into a graph; later calls with the same
+ * buffers replay that graph.  Returns after enqueueing on `stream`. */
+recon_status recon_batch_solve(recon_batch* b, const float* const* kspace, float* const* image, void* stream);
+
+/* Synchronises `stream` and fills info[q] for every slice (n entries). */
+recon_status recon_batch_info(recon_batch* b, recon_info* info, void* stream);
+
+/* Frees the batch (not its plans).  NULL-safe. */
+recon_status recon_batch_destroy(recon_batch* b);
+
 /* Frees the plan and all its device memory.  NULL-safe. */
 recon_status recon_destroy(recon_plan* plan);
 

@@ -7,6 +7,6 @@ data-consistency inverse of Section IV-C.  The C ABI is in
 ``include/recon.h``; ``binding`` is its ctypes wrapper.
 """
 
-from .binding import Plan, ReconError, load, default_opts  # noqa: F401
+from .binding import Batch, Plan, ReconError, load, default_opts  # noqa: F401
 
-__all__ = ["Plan", "ReconError", "load", "default_opts"]
+__all__ = ["Batch", "Plan", "ReconError", "load", "default_opts"]

@@ -30,7 +30,8 @@ STATUS = {0: "RECON_OK", 1: "RECON_ERR_INVALID_ARG", 2: "RECON_ERR_MASK_NOT_CART
 EXPORTS = ["recon_default_opts", "recon_plan_create", "recon_solve", "recon_solve_host", "recon_get_trace",
            "recon_destroy", "recon_apply_adjoint", "recon_apply_forward", "recon_apply_inverse",
            "recon_export_inverse", "recon_inverse_bytes", "recon_status_string", "recon_last_error",
-           "recon_get_profile", "recon_kernel_launches", "recon_gram_inverse_noalloc"]
+           "recon_get_profile", "recon_kernel_launches", "recon_gram_inverse_noalloc",
+           "recon_batch_create", "recon_batch_solve", "recon_batch_info", "recon_batch_destroy"]
 
 
 class Opts(C.Structure):
@@ -95,6 +96,14 @@ def load(path: str = LIB_PATH):
     lib.recon_kernel_launches.restype = C.c_ulonglong
     lib.recon_gram_inverse_noalloc.argtypes = [i, i, i, vp, fp, f, fp, vp]
     lib.recon_gram_inverse_noalloc.restype = i
+    lib.recon_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), i]
+    lib.recon_batch_create.restype = i
+    lib.recon_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), vp]
+    lib.recon_batch_solve.restype = i
+    lib.recon_batch_info.argtypes = [vp, C.POINTER(Info), vp]
+    lib.recon_batch_info.restype = i
+    lib.recon_batch_destroy.argtypes = [vp]
+    lib.recon_batch_destroy.restype = i
     _lib = lib
     return lib
 
@@ -227,6 +236,42 @@ class Plan:
     @property
     def inverse_bytes(self) -> int:
         return int(load().recon_inverse_bytes(self._h))
+
+
+class Batch:
+    """Several plans solved together (recon_batch_*): one launch per step, graph replay."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        self._h = C.c_void_p()
+        _check(load().recon_batch_create(C.byref(self._h), arr, len(self.plans)))
+
+    def solve(self, kspaces, outs=None, stream=None):
+        """kspaces: list of device complex64 tensors; returns the list of images."""
+        ks = [_c64(k, "cuda") for k in kspaces]
+        outs = [p._img() for p in self.plans] if outs is None else outs
+        self._keep = (ks, outs)
+        ka = (C.c_void_p * len(ks))(*[k.data_ptr() for k in ks])
+        oa = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+        _check(load().recon_batch_solve(self._h, ka, oa, _stream(stream)))
+        return outs
+
+    def info(self, stream=None):
+        arr = (Info * len(self.plans))()
+        _check(load().recon_batch_info(self._h, arr, _stream(stream)))
+        return list(arr)
+
+    def close(self):
+        if self._h:
+            load().recon_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gram_inverse_noalloc(mask_rows, sens_cols, mu, out=None, stream=None):

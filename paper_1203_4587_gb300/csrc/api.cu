@@ -13,14 +13,15 @@
 #include <string>
 #include <vector>
 
-#include "../../include/recon.h"
-#include "kernels.h"
+#include "plan.h"
 
 using namespace recon;
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
+
+namespace recon {
 
 recon_status fail(recon_status st, const std::string& why) {
   g_last_error = why;
@@ -32,13 +33,7 @@ recon_status cuda_fail(cudaError_t e, const char* where) {
   return e == cudaErrorMemoryAllocation ? RECON_ERR_OOM : RECON_ERR_CUDA;
 }
 
-#define RC(call)                                         \
-  do {                                                   \
-    cudaError_t e_ = (call);                             \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
-  } while (0)
-
-}  // namespace
+}  // namespace recon
 
 namespace recon {
 
@@ -82,78 +77,15 @@ FftPlanDev64 make_fft_plan_host64(int n, const double2* d_tw) { return fft_plan_
 
 }  // namespace recon
 
-struct recon_plan {
-  int Nx = 0, Ny = 0, Nt = 0, Nc = 0;
-  recon_prior prior = RECON_PRIOR_TV;
-  float lam = 0.f, mu = 0.f;
-  recon_opts opts{};
-  int device = 0, num_sms = 0;
-  cudaStream_t last_stream = nullptr;
-  PackInfo pk{};
-  int storage = 0;
-  size_t esize = 8;
-  std::vector<int> h_rows, h_rowoff;
-  int maxm = 0, total_rows = 0;
-  // device memory
-  std::vector<void*> allocs;
-  void* A = nullptr;
-  int4* units = nullptr;
-  float2* sens = nullptr;
-  int* rows = nullptr;
-  int* rowoff = nullptr;
-  float2 *tw_x = nullptr, *tw_y = nullptr, *tw_t = nullptr;
-  double2 *tw64_x = nullptr, *tw64_y = nullptr;
-  double2* yhat64 = nullptr;           // FP64 hybrid data of the prologue
-  float* thomas = nullptr;
-  float2* yhat = nullptr;
-  float2* b = nullptr;
-  float2* s0[2] = {nullptr, nullptr};  // TV: m;  DFT: u
-  float2* s1[2] = {nullptr, nullptr};  // TV: d1
-  float2* s2[2] = {nullptr, nullptr};  // TV: p
-  float2* x = nullptr;                 // TV: x; DFT: xhat
-  float2* r = nullptr;                 // DFT: r
-  float2* tmp_a = nullptr;             // operator entry points
-  float2* tmp_b = nullptr;
-  float2* kstage = nullptr;            // host-solve staging
-  float2* istage = nullptr;
-  double* trace_fid = nullptr;
-  double* trace_prior = nullptr;
-  double* trace_J = nullptr;
-  double* yy = nullptr;                // ||y||^2 over the sampled entries (FP64)
-  int* flags = nullptr;
-  FftPlanDev fx{}, fy{}, ft{};
-  FftPlanDev64 fx64{}, fy64{};
-  int col_stages = 0, col_grid = 0;
-  size_t col_smem = 0;
-  int last_iters = 0;
-  // opts.profile: event pairs around every inverse / temporal launch of a solve
-  std::vector<cudaEvent_t> ev_col, ev_tmp;
-  cudaEvent_t ev_solve[2] = {nullptr, nullptr};
-  int n_col = 0, n_tmp = 0;
-  bool prof_valid = false;
-
-  cudaError_t alloc(void** p, size_t bytes) {
-    *p = nullptr;
-    if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e == cudaSuccess) allocs.push_back(*p);
-    return e;
-  }
-  ~recon_plan() {
-    for (cudaEvent_t e : ev_col) cudaEventDestroy(e);
-    for (cudaEvent_t e : ev_tmp) cudaEventDestroy(e);
-    for (cudaEvent_t e : ev_solve) if (e) cudaEventDestroy(e);
-    for (void* p : allocs) cudaFree(p);
-  }
-  void mark(std::vector<cudaEvent_t>& v, int& n, bool begin, cudaStream_t s) {
-    if (!opts.profile) return;
-    const size_t idx = 2 * (size_t)n + (begin ? 0 : 1);
-    if (idx < v.size()) cudaEventRecord(v[idx], s);
-    if (!begin) ++n;
-  }
-  size_t npix() const { return (size_t)Nx * Ny; }
-  size_t nimg() const { return (size_t)Nx * Ny * Nt; }
-};
+recon_plan::~recon_plan() {
+  delete eng;
+  delete eng_inv;
+  for (cudaEvent_t e : ev_col) cudaEventDestroy(e);
+  for (cudaEvent_t e : ev_tmp) cudaEventDestroy(e);
+  for (cudaEvent_t e : ev_solve)
+    if (e) cudaEventDestroy(e);
+  for (void* q : allocs) cudaFree(q);
+}
 
 extern "C" {
 
@@ -244,32 +176,14 @@ int coil_group_for(int Nc, int Ny) {
   return std::min(g, Nc);
 }
 
-ColParams base_col_params(const recon_plan* p) {
-  ColParams c{};
-  c.A = p->A;
-  c.col_elems = p->pk.col_elems;
-  c.nunits = p->pk.nunits;
-  c.units = p->units;
-  c.Nx = p->Nx; c.Ny = p->Ny; c.Nt = p->Nt; c.nb = p->pk.nb;
-  c.ncols = p->Nx * p->Nt;
-  c.stages = p->col_stages;
-  c.mu = p->mu;
-  c.r_tma = ((size_t)p->Ny * sizeof(float2)) % 16 == 0 ? 1 : 0;
-  c.flags = p->flags;
-  return c;
-}
+}  // namespace
 
-recon_status run_col(recon_plan* p, ColParams c, cudaStream_t s) {
-  c.stages = p->col_stages;
-  const size_t smem = col_inverse_smem(c, p->storage);
-  RC(launch_col_inverse(c, p->storage, p->col_grid, smem, s));
-  return RECON_OK;
-}
+namespace recon {
 
-// ||y - H x||^2 of a field by explicit FFTs (J(0), and every J(k) when the
-// inverses are stored in 16 bit, where (mu I + H'H) x = r holds only to the
-// storage precision).
-recon_status run_objective(recon_plan* p, const float2* x, double* acc, cudaStream_t s) {
+// ||y - H x||^2 of a field by explicit FFTs (J(0), and every J(k) in the
+// exact objective mode or with 16-bit inverses, where (mu I + H'H) x = r
+// holds only to the storage precision).
+recon_status plan_objective(recon_plan* p, const float2* x, double* acc, cudaStream_t s) {
   ObjParams o{};
   o.Nx = p->Nx; o.Ny = p->Ny; o.Nt = p->Nt; o.Nc = p->Nc; o.ncg = coil_group_for(p->Nc, p->Ny);
   o.x = x; o.sens = p->sens; o.yhat = p->yhat; o.rows = p->rows; o.rowoff = p->rowoff; o.fy = p->fy;
@@ -279,130 +193,31 @@ recon_status run_objective(recon_plan* p, const float2* x, double* acc, cudaStre
 }
 
 // user layout [Nt][Ny][Nx] -> internal [Nt][Nx][Ny]
-recon_status to_internal(recon_plan* p, const float2* in, float2* out, cudaStream_t s) {
+recon_status plan_to_internal(recon_plan* p, const float2* in, float2* out, cudaStream_t s) {
   RC(launch_transpose(in, out, p->Nt, p->Ny, p->Nx, (long long)p->npix(), (long long)p->npix(), p->Ny, s));
   return RECON_OK;
 }
-recon_status to_user(recon_plan* p, const float2* in, float2* out, cudaStream_t s) {
+recon_status plan_to_user(recon_plan* p, const float2* in, float2* out, cudaStream_t s) {
   RC(launch_transpose(in, out, p->Nt, p->Nx, p->Ny, (long long)p->npix(), (long long)p->npix(), p->Nx, s));
   return RECON_OK;
 }
 
 // H'y in FP64 (rounded once to FP32), the FP32 hybrid data for J(k) and
 // ||y||^2 (into *yy, which must be zeroed first).
-recon_status adjoint64(recon_plan* p, const float* kspace, float2* yhat32, float2* b, double* yy, cudaStream_t s) {
+recon_status plan_adjoint64(recon_plan* p, const float* kspace, float2* yhat32, float2* b, double* yy,
+                            cudaStream_t s) {
   RC(launch_hybrid_rows64(reinterpret_cast<const float2*>(kspace), p->yhat64, yhat32, yy, p->rows, p->rowoff,
                           p->maxm, p->Nx, p->Ny, p->Nt, p->Nc, p->fx64, s));
   RC(launch_adjoint_combine64(p->yhat64, p->sens, b, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fy64, s));
   return RECON_OK;
 }
 
-recon_status prologue(recon_plan* p, const float* kspace, cudaStream_t s) {
+recon_status plan_prologue(recon_plan* p, const float* kspace, cudaStream_t s) {
   RC(cudaMemsetAsync(p->yy, 0, sizeof(double), s));
-  return adjoint64(p, kspace, p->yhat, p->b, p->yy, s);
+  return plan_adjoint64(p, kspace, p->yhat, p->b, p->yy, s);
 }
 
-// K iterations from the initial point (x = H'y).  Leaves the image (internal
-// layout) in *result.
-recon_status iterate(recon_plan* p, cudaStream_t s, const float2** result) {
-  const int K = p->opts.max_iters;
-  const bool obj = p->opts.objective != 0 || p->opts.tol > 0.0;
-  // mode 1 with FP32 inverses: data term from (mu I + H'H) x = r inside the
-  // inverse kernel; mode 2 or 16-bit inverses: explicit FFT objective.
-  const bool fused_obj = obj && p->opts.objective != 2 && p->storage == 0;
-  const double* yy = fused_obj ? p->yy : nullptr;
-  const size_t nt = (size_t)K + 2;
-  RC(cudaMemsetAsync(p->flags, 0, FLAG_COUNT * sizeof(int), s));
-  RC(cudaMemsetAsync(p->trace_fid, 0, nt * sizeof(double), s));
-  RC(cudaMemsetAsync(p->trace_prior, 0, nt * sizeof(double), s));
-  RC(cudaMemsetAsync(p->trace_J, 0xff, nt * sizeof(double), s));  // NaN
-  if (obj) {
-    recon_status st = run_objective(p, p->b, p->trace_fid, s);
-    if (st != RECON_OK) return st;
-  }
-  auto finalize = [&](int k) -> recon_status {
-    // J(0) is always the explicit objective (no yy term)
-    RC(launch_finalize(p->trace_fid, p->trace_prior, k == 0 ? nullptr : yy, p->trace_J, k, p->lam, p->opts.tol,
-                       p->flags, s));
-    return RECON_OK;
-  };
-  const double mu2 = p->mu;
-  const double rho = p->opts.rho;
-  const long long npix = (long long)p->npix();
-  ColParams c = base_col_params(p);
-  c.do_obj = fused_obj ? 1 : 0;
-  recon_status st = RECON_OK;
-  if (p->prior == RECON_PRIOR_TV) {
-    const double mu1 = mu2 / rho;
-    TvParams tp{};
-    tp.Nt = p->Nt; tp.npix = npix;
-    tp.tau1 = (float)(p->lam / (2.0 * mu1));
-    tp.rho = (float)rho;
-    tp.thomas = p->thomas;
-    tp.flags = p->flags;
-    const float2 *m_in = p->b, *d1_in = nullptr, *x_in = p->b, *p_in = p->b;
-    for (int k = 1; k <= K; ++k) {
-      const int par = k & 1;
-      tp.m = m_in; tp.d1 = d1_in; tp.x = x_in; tp.p = p_in;
-      tp.m_out = p->s0[par]; tp.d1_out = p->s1[par]; tp.p_out = p->s2[par];
-      tp.write_state = 1;
-      tp.prior_acc = p->trace_prior + (k - 1);
-      p->mark(p->ev_tmp, p->n_tmp, true, s);
-      RC(launch_tv_temporal(tp, s));
-      p->mark(p->ev_tmp, p->n_tmp, false, s);
-      if (obj && (st = finalize(k - 1)) != RECON_OK) return st;
-      c.base = p->b; c.add = p->s2[par]; c.coef = (float)mu2; c.bsrc = p->b; c.xout = p->x;
-      c.fid_acc = p->trace_fid + k;
-      p->mark(p->ev_col, p->n_col, true, s);
-      if ((st = run_col(p, c, s)) != RECON_OK) return st;
-      p->mark(p->ev_col, p->n_col, false, s);
-      if (obj && !fused_obj && (st = run_objective(p, p->x, p->trace_fid + k, s)) != RECON_OK) return st;
-      m_in = p->s0[par]; d1_in = p->s1[par]; p_in = p->s2[par]; x_in = p->x;
-    }
-    if (obj) {
-      tp.x = x_in; tp.write_state = 0; tp.prior_acc = p->trace_prior + K;
-      RC(launch_tv_temporal(tp, s));
-      if ((st = finalize(K)) != RECON_OK) return st;
-    }
-    *result = (K == 0) ? p->b : p->x;
-  } else {
-    DftParams dp{};
-    dp.Nt = p->Nt; dp.npix = npix;
-    dp.b = p->b;
-    dp.tau = (float)(p->lam / (2.0 * mu2));
-    dp.mu = (float)mu2;
-    dp.ft = p->ft;
-    dp.flags = p->flags;
-    const float2 *xh_in = p->b, *u_in = nullptr;
-    for (int k = 1; k <= K; ++k) {
-      const int par = k & 1;
-      dp.xh = xh_in; dp.u = u_in; dp.first = (k == 1);
-      dp.u_out = p->s0[par]; dp.r_out = p->r;
-      dp.write_state = 1;
-      dp.prior_acc = p->trace_prior + (k - 1);
-      p->mark(p->ev_tmp, p->n_tmp, true, s);
-      RC(launch_dft_temporal(dp, s));
-      p->mark(p->ev_tmp, p->n_tmp, false, s);
-      if (obj && (st = finalize(k - 1)) != RECON_OK) return st;
-      c.base = p->r; c.add = nullptr; c.coef = 0.f; c.bsrc = p->b; c.xout = p->x;
-      c.fid_acc = p->trace_fid + k;
-      p->mark(p->ev_col, p->n_col, true, s);
-      if ((st = run_col(p, c, s)) != RECON_OK) return st;
-      p->mark(p->ev_col, p->n_col, false, s);
-      if (obj && !fused_obj && (st = run_objective(p, p->x, p->trace_fid + k, s)) != RECON_OK) return st;
-      xh_in = p->x; u_in = p->s0[par];
-    }
-    if (obj) {
-      dp.xh = xh_in; dp.write_state = 0; dp.first = 1; dp.prior_acc = p->trace_prior + K;
-      RC(launch_dft_temporal(dp, s));
-      if ((st = finalize(K)) != RECON_OK) return st;
-    }
-    *result = (K == 0) ? p->b : p->x;
-  }
-  return RECON_OK;
-}
-
-recon_status fill_info(recon_plan* p, recon_info* info, cudaStream_t s) {
+recon_status plan_fill_info(recon_plan* p, recon_info* info, cudaStream_t s) {
   RC(cudaStreamSynchronize(s));
   int fl[FLAG_COUNT];
   RC(cudaMemcpy(fl, p->flags, sizeof(fl), cudaMemcpyDeviceToHost));
@@ -422,6 +237,10 @@ recon_status fill_info(recon_plan* p, recon_info* info, cudaStream_t s) {
   if (fl[FLAG_ERR] & DEV_ERR_NONFINITE) return fail(RECON_ERR_NONFINITE, "non-finite objective value");
   return RECON_OK;
 }
+
+}  // namespace recon
+
+namespace {
 
 bool valid_ptr(const void* p) { return p != nullptr; }
 
@@ -490,7 +309,10 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
   p->total_rows = (int)p->h_rows.size();
   p->pk = make_pack(Ny);
 
-  auto cleanup = [&](recon_status st) { delete p; return st; };
+  auto cleanup = [&](recon_status st) {
+    delete p;
+    return st;
+  };
 #define PC(call)                                                      \
   do {                                                                \
     cudaError_t e_ = (call);                                          \
@@ -500,8 +322,7 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
   const size_t nimg = p->nimg();
   const size_t ncols = (size_t)Nx * Nt;
   PC(p->alloc(&p->A, (size_t)p->pk.col_elems * p->esize * ncols));
-  std::vector<int4> hu = make_units(p->pk);
-  PC(p->alloc((void**)&p->units, hu.size() * sizeof(int4)));
+  p->h_units = make_units(p->pk);
   PC(p->alloc((void**)&p->sens, (size_t)Nx * Nc * Ny * sizeof(float2)));
   PC(p->alloc((void**)&p->rows, std::max<size_t>(1, p->h_rows.size()) * sizeof(int)));
   PC(p->alloc((void**)&p->rowoff, (Nt + 1) * sizeof(int)));
@@ -554,7 +375,6 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
   p->ft = make_fft_plan_host(Nt, p->tw_t);
   std::vector<float> th = thomas_pivots(Nt, o.rho);
   PC(cudaMemcpy(p->thomas, th.data(), Nt * sizeof(float), cudaMemcpyHostToDevice));
-  PC(cudaMemcpy(p->units, hu.data(), hu.size() * sizeof(int4), cudaMemcpyHostToDevice));
   if (!p->h_rows.empty())
     PC(cudaMemcpy(p->rows, p->h_rows.data(), p->h_rows.size() * sizeof(int), cudaMemcpyHostToDevice));
   PC(cudaMemcpy(p->rowoff, p->h_rowoff.data(), (Nt + 1) * sizeof(int), cudaMemcpyHostToDevice));
@@ -603,15 +423,15 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
     if (fl[FLAG_ERR] & DEV_ERR_NOT_PD) return cleanup(fail(RECON_ERR_NONFINITE, "a Gram block is not positive definite"));
   }
 
-  // column-inverse launch shape: one persistent CTA per SM, ring as deep as fits
+  // the plan's own iterations (a batch of one) and the apply-inverse launch
   {
-    ColParams c = base_col_params(p);
-    const int maxst = col_inverse_max_stages(c, p->storage);
-    const int q = col_inverse_stage_quantum();
-    int st = o.col_stages > 0 ? std::min(o.col_stages, maxst) : maxst;
-    st = std::max(q, st / q * q);  // a positive multiple of the consumer warp count
-    p->col_stages = st;
-    p->col_grid = std::max(1, std::min<int>((int)ncols, p->num_sms));
+    p->eng = new Engine();
+    recon_status st = engine_build(p->eng, &p, 1);
+    if (st != RECON_OK) return cleanup(st);
+    p->eng_inv = new Engine();
+    st = engine_build_inverse(p->eng_inv, p);
+    if (st != RECON_OK) return cleanup(st);
+    p->col_stages = p->eng->stages;
   }
   if (o.profile) {
     const size_t ne = 2 * ((size_t)o.max_iters + 2);
@@ -636,15 +456,14 @@ recon_status recon_solve(recon_plan* p, const float* kspace, float* image, recon
   p->n_col = p->n_tmp = 0;
   p->prof_valid = p->opts.profile != 0;
   if (p->opts.profile) cudaEventRecord(p->ev_solve[0], s);
-  recon_status st = prologue(p, kspace, s);
+  recon_status st = plan_prologue(p, kspace, s);
   if (st != RECON_OK) return st;
-  const float2* res = nullptr;
-  st = iterate(p, s, &res);
+  st = engine_iterate(p->eng, s, p->opts.profile != 0);
   if (st != RECON_OK) return st;
-  st = to_user(p, res, reinterpret_cast<float2*>(image), s);
+  st = plan_to_user(p, plan_result(p), reinterpret_cast<float2*>(image), s);
   if (st != RECON_OK) return st;
   if (p->opts.profile) cudaEventRecord(p->ev_solve[1], s);
-  if (info) return fill_info(p, info, s);
+  if (info) return plan_fill_info(p, info, s);
   return RECON_OK;
 }
 
@@ -691,7 +510,7 @@ recon_status recon_solve_host(recon_plan* p, const float* kspace_host, float* im
                                 nullptr, stream);
   if (st != RECON_OK) return st;
   RC(cudaMemcpyAsync(image_host, p->istage, ibytes, cudaMemcpyDeviceToHost, s));
-  return fill_info(p, info, s);
+  return plan_fill_info(p, info, s);
 }
 
 recon_status recon_get_trace(recon_plan* p, double* J_host, int n) {
@@ -707,15 +526,15 @@ recon_status recon_get_trace(recon_plan* p, double* J_host, int n) {
 recon_status recon_apply_adjoint(recon_plan* p, const float* kspace, float* image, void* stream) {
   if (!p || !kspace || !image) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  recon_status st = adjoint64(p, kspace, p->tmp_b, p->tmp_a, nullptr, s);
+  recon_status st = plan_adjoint64(p, kspace, p->tmp_b, p->tmp_a, nullptr, s);
   if (st != RECON_OK) return st;
-  return to_user(p, p->tmp_a, reinterpret_cast<float2*>(image), s);
+  return plan_to_user(p, p->tmp_a, reinterpret_cast<float2*>(image), s);
 }
 
 recon_status recon_apply_forward(recon_plan* p, const float* image, float* kspace, void* stream) {
   if (!p || !image || !kspace) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  recon_status st = to_internal(p, reinterpret_cast<const float2*>(image), p->tmp_a, s);
+  recon_status st = plan_to_internal(p, reinterpret_cast<const float2*>(image), p->tmp_a, s);
   if (st != RECON_OK) return st;
   RC(launch_forward_cols(p->tmp_a, p->sens, p->tmp_b, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fy, s));
   RC(cudaMemsetAsync(kspace, 0, (size_t)p->Nt * p->Nc * p->Ny * p->Nx * sizeof(float2), s));
@@ -727,16 +546,12 @@ recon_status recon_apply_forward(recon_plan* p, const float* image, float* kspac
 recon_status recon_apply_inverse(recon_plan* p, const float* in, float* out, void* stream) {
   if (!p || !in || !out || in == out) return fail(RECON_ERR_INVALID_ARG, "NULL or aliased argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  recon_status st = to_internal(p, reinterpret_cast<const float2*>(in), p->tmp_a, s);
+  recon_status st = plan_to_internal(p, reinterpret_cast<const float2*>(in), p->tmp_a, s);
   if (st != RECON_OK) return st;
   RC(cudaMemsetAsync(p->flags, 0, FLAG_COUNT * sizeof(int), s));
-  ColParams c = base_col_params(p);
-  c.do_obj = 0;
-  c.base = p->tmp_a; c.add = nullptr; c.coef = 0.f; c.bsrc = p->tmp_a; c.xout = p->tmp_b;
-  c.fid_acc = nullptr;
-  st = run_col(p, c, s);
+  st = engine_apply_inverse(p->eng_inv, s);
   if (st != RECON_OK) return st;
-  return to_user(p, p->tmp_b, reinterpret_cast<float2*>(out), s);
+  return plan_to_user(p, p->tmp_b, reinterpret_cast<float2*>(out), s);
 }
 
 recon_status recon_export_inverse(recon_plan* p, int i, int t, float* dense, void* stream) {

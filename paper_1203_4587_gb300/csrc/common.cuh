@@ -48,12 +48,14 @@ __device__ __forceinline__ void c_fmac(float2& acc, float2 a, float2 b) {
   acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(a.y, b.y, acc.x);
   acc.y = fmaf(a.x, b.y, acc.y); acc.y = fmaf(-a.y, b.x, acc.y);
 }
-__device__ __forceinline__ float c_abs(float2 a) { return hypotf(a.x, a.y); }
+// |a| as the correctly rounded sqrt of the FP32 sum of squares (no overflow
+// or underflow concerns at the magnitudes of the reconstruction)
+__device__ __forceinline__ float c_abs(float2 a) { return __fsqrt_rn(fmaf(a.x, a.x, a.y * a.y)); }
 __device__ __forceinline__ double c_abs2d(float2 a) { return (double)a.x * a.x + (double)a.y * a.y; }
 
 // Complex soft threshold S(a, tau) = (|a| - tau) a / |a| if |a| > tau, else 0.
 __device__ __forceinline__ float2 c_soft(float2 a, float tau) {
-  float mag = hypotf(a.x, a.y);
+  float mag = __fsqrt_rn(fmaf(a.x, a.x, a.y * a.y));
   if (!(mag > tau)) return make_float2(0.f, 0.f);
   float s = (mag - tau) / mag;
   return make_float2(a.x * s, a.y * s);

@@ -1,0 +1,485 @@
+// Launch engine: descriptor sets, work lists and the launch sequence of the
+// ADMM iterations for one plan (a batch of one) or a batch of plans, and the
+// batched C entry points (one launch per step for all slices, replayed from
+// a captured CUDA graph).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <queue>
+#include <vector>
+
+#include "plan.h"
+
+namespace recon {
+
+cudaError_t DevArena::alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e == cudaSuccess) ptrs.push_back(*p);
+  return e;
+}
+
+void DevArena::release() {
+  for (void* p : ptrs) cudaFree(p);
+  ptrs.clear();
+}
+
+namespace {
+
+template <typename T>
+cudaError_t upload(DevArena& a, T** dst, const std::vector<T>& v) {
+  cudaError_t e = a.alloc(reinterpret_cast<void**>(dst), v.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Column work lists: every column of every slice, spread over `grid` CTAs by
+// longest-processing-time-first on the bytes each column streams, then each
+// CTA's list ordered by (slice, column).
+void build_work(recon_plan* const* plans, int n, int grid, std::vector<unsigned>& work, std::vector<int>& off,
+                int& work_max) {
+  struct Col { long long cost; int q, c; };
+  std::vector<Col> cols;
+  for (int q = 0; q < n; ++q) {
+    const recon_plan* p = plans[q];
+    const long long cost = p->pk.col_elems * (long long)p->esize + 4096;
+    for (int c = 0; c < p->Nx * p->Nt; ++c) cols.push_back({cost, q, c});
+  }
+  std::vector<std::vector<int2>> per(grid);
+  if (n == 1) {
+    // equal columns: interleave (column b, b + grid, ...)
+    for (size_t k = 0; k < cols.size(); ++k) per[k % grid].push_back(make_int2(cols[k].q, cols[k].c));
+  } else {
+    std::stable_sort(cols.begin(), cols.end(), [](const Col& a, const Col& b) { return a.cost > b.cost; });
+    using Load = std::pair<long long, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+    for (int b = 0; b < grid; ++b) pq.push({0, b});
+    for (const Col& c : cols) {
+      Load l = pq.top();
+      pq.pop();
+      per[l.second].push_back(make_int2(c.q, c.c));
+      pq.push({l.first + c.cost, l.second});
+    }
+    for (auto& v : per)
+      std::sort(v.begin(), v.end(), [](int2 a, int2 b) { return a.x != b.x ? a.x < b.x : a.y < b.y; });
+  }
+  work.clear();
+  off.assign(grid + 1, 0);
+  work_max = 0;
+  for (int b = 0; b < grid; ++b) {
+    off[b] = (int)work.size();
+    for (int2 w : per[b]) work.push_back(((unsigned)w.x << 24) | (unsigned)w.y);
+    work_max = std::max(work_max, (int)per[b].size());
+  }
+  off[grid] = (int)work.size();
+}
+
+TvSlice tv_desc(recon_plan* p, int k, int K) {
+  TvSlice d{};
+  d.Nt = p->Nt;
+  d.npix = (long long)p->npix();
+  d.tau1 = (float)(p->lam / (2.0 * (p->mu / p->opts.rho)));
+  d.rho = p->opts.rho;
+  d.thomas = p->thomas;
+  d.stop = p->flags + FLAG_STOP;
+  if (k <= K) {  // iteration k (1-based): state of k-1 -> state of k
+    const int in = (k - 1) & 1, out = k & 1;
+    d.m = (k == 1) ? p->b : p->s0[in];
+    d.d1 = (k == 1) ? nullptr : p->s1[in];
+    d.x = (k == 1) ? p->b : p->x;
+    d.p = (k == 1) ? p->b : p->s2[in];
+    d.m_out = p->s0[out];
+    d.d1_out = p->s1[out];
+    d.p_out = p->s2[out];
+    d.write_state = 1;
+    d.prior_acc = p->trace_prior + (k - 1);
+  } else {       // final: only ||D_t x_K||_1
+    d.x = (K == 0) ? p->b : p->x;
+    d.write_state = 0;
+    d.prior_acc = p->trace_prior + K;
+  }
+  return d;
+}
+
+DftSlice dft_desc(recon_plan* p, int k, int K) {
+  DftSlice d{};
+  d.Nt = p->Nt;
+  d.npix = (long long)p->npix();
+  d.b = p->b;
+  d.tau = (float)(p->lam / (2.0 * p->mu));
+  d.mu = p->mu;
+  d.ft = p->ft;
+  d.stop = p->flags + FLAG_STOP;
+  if (k <= K) {
+    const int in = (k - 1) & 1, out = k & 1;
+    d.xh = (k == 1) ? p->b : p->x;
+    d.u = (k == 1) ? nullptr : p->s0[in];
+    d.first = (k == 1);
+    d.u_out = p->s0[out];
+    d.r_out = p->r;
+    d.write_state = 1;
+    d.prior_acc = p->trace_prior + (k - 1);
+  } else {
+    d.xh = (K == 0) ? p->b : p->x;
+    d.first = 1;
+    d.write_state = 0;
+    d.prior_acc = p->trace_prior + K;
+  }
+  return d;
+}
+
+ColSlice col_desc(recon_plan* p, int k, bool fused, int unit_off) {
+  ColSlice c{};
+  c.A = p->A;
+  c.col_elems = p->pk.col_elems;
+  c.Ny = p->Ny;
+  c.nb = p->pk.nb;
+  c.nunits = p->pk.nunits;
+  c.unit_off = unit_off;
+  c.r_tma = ((size_t)p->Ny * sizeof(float2)) % 16 == 0 ? 1 : 0;
+  c.do_obj = fused ? 1 : 0;
+  c.mu = p->mu;
+  c.stop = p->flags + FLAG_STOP;
+  if (p->prior == RECON_PRIOR_TV) {
+    c.base = p->b;
+    c.add = p->s2[k & 1];
+    c.coef = p->mu;
+  } else {
+    c.base = p->r;
+    c.add = nullptr;
+    c.coef = 0.f;
+  }
+  c.bsrc = p->b;
+  c.xout = p->x;
+  c.fid_acc = p->trace_fid + k;
+  return c;
+}
+
+recon_status finish_col_shape(Engine* e, recon_plan* const* plans, int n, int stages_req) {
+  e->nb_max = 0;
+  for (int q = 0; q < n; ++q) e->nb_max = std::max(e->nb_max, plans[q]->pk.nb);
+  const int maxst = col_inverse_max_stages(e->nb_max, e->nunits_all, n, e->work_max);
+  const int qn = col_inverse_stage_quantum();
+  int st = stages_req > 0 ? std::min(stages_req, maxst) : maxst;
+  e->stages = std::max(qn, st / qn * qn);
+  const size_t smem = col_inverse_smem(e->stages, e->nb_max, e->nunits_all, n, e->work_max);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem > (size_t)optin)
+    return fail(RECON_ERR_UNSUPPORTED, "batch too large for one launch (work lists exceed shared memory)");
+  RC(prepare_col_inverse(e->storage, smem));
+  return RECON_OK;
+}
+
+}  // namespace
+
+recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
+  if (n < 1) return fail(RECON_ERR_INVALID_ARG, "empty batch");
+  if (n > 255) return fail(RECON_ERR_UNSUPPORTED, "at most 255 slices per batch");
+  recon_plan* p0 = plans[0];
+  e->plans.assign(plans, plans + n);
+  e->n = n;
+  e->K = p0->opts.max_iters;
+  e->tv = p0->prior == RECON_PRIOR_TV;
+  e->storage = p0->storage;
+  e->obj = p0->opts.objective != 0 || p0->opts.tol > 0.0;
+  e->fused = e->obj && p0->opts.objective != 2 && p0->storage == 0;
+  for (int q = 1; q < n; ++q) {
+    const recon_plan* p = plans[q];
+    if (p->prior != p0->prior || p->opts.max_iters != e->K || p->storage != e->storage ||
+        (p->opts.objective != 0 || p->opts.tol > 0.0) != e->obj || (p->opts.objective == 2) != (p0->opts.objective == 2))
+      return fail(RECON_ERR_INVALID_ARG, "batched plans must share prior, max_iters, storage and objective mode");
+    if (p->device != p0->device) return fail(RECON_ERR_INVALID_ARG, "batched plans must be on one device");
+  }
+  const int K = e->K;
+  // unit tables
+  std::vector<int4> units;
+  std::vector<int> unit_off(n);
+  for (int q = 0; q < n; ++q) {
+    unit_off[q] = (int)units.size();
+    units.insert(units.end(), plans[q]->h_units.begin(), plans[q]->h_units.end());
+  }
+  e->nunits_all = (int)units.size();
+  RC(upload(e->arena, &e->d_units, units));
+  // column descriptors, K sets (at least one so the layout is valid at K = 0)
+  std::vector<ColSlice> cols((size_t)std::max(K, 1) * n);
+  for (int k = 1; k <= std::max(K, 1); ++k)
+    for (int q = 0; q < n; ++q) cols[(size_t)(k - 1) * n + q] = col_desc(plans[q], k, e->fused, unit_off[q]);
+  RC(upload(e->arena, &e->d_col, cols));
+  // temporal descriptors, K+1 sets
+  e->Nt_max = 0;
+  for (int q = 0; q < n; ++q) e->Nt_max = std::max(e->Nt_max, plans[q]->Nt);
+  e->tile_px = e->tv ? tv_tile_px(e->Nt_max) : dft_tile_px();
+  std::vector<int> tile0(n);
+  int blocks = 0;
+  for (int q = 0; q < n; ++q) {
+    tile0[q] = blocks;
+    blocks += (int)((plans[q]->npix() + e->tile_px - 1) / e->tile_px);
+  }
+  e->tmp_blocks = blocks;
+  if (e->tv) {
+    std::vector<TvSlice> t((size_t)(K + 1) * n);
+    for (int k = 1; k <= K + 1; ++k)
+      for (int q = 0; q < n; ++q) {
+        TvSlice d = tv_desc(plans[q], k, K);
+        d.tile0 = tile0[q];
+        t[(size_t)(k - 1) * n + q] = d;
+      }
+    RC(upload(e->arena, reinterpret_cast<TvSlice**>(&e->d_tmp), t));
+    RC(prepare_tv_temporal(e->Nt_max));
+  } else {
+    std::vector<DftSlice> t((size_t)(K + 1) * n);
+    for (int k = 1; k <= K + 1; ++k)
+      for (int q = 0; q < n; ++q) {
+        DftSlice d = dft_desc(plans[q], k, K);
+        d.tile0 = tile0[q];
+        t[(size_t)(k - 1) * n + q] = d;
+      }
+    RC(upload(e->arena, reinterpret_cast<DftSlice**>(&e->d_tmp), t));
+    RC(prepare_dft_temporal(e->Nt_max));
+  }
+  // finalize descriptors
+  std::vector<FinSlice> fin(n);
+  for (int q = 0; q < n; ++q) {
+    recon_plan* p = plans[q];
+    fin[q].fid = p->trace_fid;
+    fin[q].prior = p->trace_prior;
+    fin[q].yy = e->fused ? p->yy : nullptr;
+    fin[q].J = p->trace_J;
+    fin[q].flags = p->flags;
+    fin[q].lam = p->lam;
+    fin[q].tol = p->opts.tol;
+  }
+  RC(upload(e->arena, &e->d_fin, fin));
+  // work lists and launch shape
+  e->grid = std::max(1, p0->num_sms);
+  std::vector<unsigned> work;
+  std::vector<int> off;
+  build_work(plans, n, e->grid, work, off, e->work_max);
+  RC(upload(e->arena, &e->d_work, work));
+  RC(upload(e->arena, &e->d_work_off, off));
+  if (n == 1) {
+    e->d_err = p0->flags + FLAG_ERR;
+  } else {
+    RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_err), sizeof(int)));
+    RC(cudaMemset(e->d_err, 0, sizeof(int)));
+  }
+  return finish_col_shape(e, plans, n, p0->opts.col_stages);
+}
+
+recon_status engine_build_inverse(Engine* e, recon_plan* p) {
+  e->plans = {p};
+  e->n = 1;
+  e->K = 1;
+  e->storage = p->storage;
+  e->obj = e->fused = false;
+  RC(upload(e->arena, &e->d_units, p->h_units));
+  e->nunits_all = (int)p->h_units.size();
+  ColSlice c = col_desc(p, 1, false, 0);
+  c.base = p->tmp_a;
+  c.add = nullptr;
+  c.coef = 0.f;
+  c.bsrc = p->tmp_a;
+  c.xout = p->tmp_b;
+  c.fid_acc = nullptr;
+  c.stop = nullptr;
+  RC(upload(e->arena, &e->d_col, std::vector<ColSlice>{c}));
+  e->grid = std::max(1, p->num_sms);
+  std::vector<unsigned> work;
+  std::vector<int> off;
+  recon_plan* pl[1] = {p};
+  build_work(pl, 1, e->grid, work, off, e->work_max);
+  RC(upload(e->arena, &e->d_work, work));
+  RC(upload(e->arena, &e->d_work_off, off));
+  e->d_err = p->flags + FLAG_ERR;
+  return finish_col_shape(e, pl, 1, p->opts.col_stages);
+}
+
+static recon_status launch_col_set(Engine* e, int set, cudaStream_t s) {
+  ColLaunch L{};
+  L.slices = e->d_col + (size_t)set * e->n;
+  L.nslices = e->n;
+  L.units = e->d_units;
+  L.nunits_all = e->nunits_all;
+  L.work = e->d_work;
+  L.work_off = e->d_work_off;
+  L.work_max = e->work_max;
+  L.nb_max = e->nb_max;
+  L.stages = e->stages;
+  L.err = e->d_err;
+  RC(launch_col_inverse(L, e->storage, e->grid, s));
+  return RECON_OK;
+}
+
+static recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s) {
+  TemporalLaunch L{};
+  L.nslices = e->n;
+  L.nblocks = e->tmp_blocks;
+  L.Nt_max = e->Nt_max;
+  L.tile_px = e->tile_px;
+  if (e->tv) {
+    L.slices = static_cast<TvSlice*>(e->d_tmp) + (size_t)set * e->n;
+    RC(launch_tv_temporal(L, s));
+  } else {
+    L.slices = static_cast<DftSlice*>(e->d_tmp) + (size_t)set * e->n;
+    RC(launch_dft_temporal(L, s));
+  }
+  return RECON_OK;
+}
+
+recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
+  const int K = e->K;
+  const size_t nt = (size_t)K + 2;
+  recon_plan* p0 = e->plans[0];
+  const bool prof = profile && e->n == 1;
+  for (recon_plan* p : e->plans) {
+    RC(cudaMemsetAsync(p->flags, 0, FLAG_COUNT * sizeof(int), s));
+    RC(cudaMemsetAsync(p->trace_fid, 0, nt * sizeof(double), s));
+    RC(cudaMemsetAsync(p->trace_prior, 0, nt * sizeof(double), s));
+    RC(cudaMemsetAsync(p->trace_J, 0xff, nt * sizeof(double), s));  // NaN
+  }
+  if (e->n > 1) RC(cudaMemsetAsync(e->d_err, 0, sizeof(int), s));
+  recon_status st;
+  if (e->obj)
+    for (recon_plan* p : e->plans)
+      if ((st = plan_objective(p, p->b, p->trace_fid, s)) != RECON_OK) return st;
+  for (int k = 1; k <= K; ++k) {
+    if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, true, s);
+    if ((st = launch_tmp_set(e, k - 1, s)) != RECON_OK) return st;
+    if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, false, s);
+    if (e->obj) RC(launch_finalize(e->d_fin, e->n, k - 1, s));
+    if (prof) p0->mark(p0->ev_col, p0->n_col, true, s);
+    if ((st = launch_col_set(e, k - 1, s)) != RECON_OK) return st;
+    if (prof) p0->mark(p0->ev_col, p0->n_col, false, s);
+    if (e->obj && !e->fused)
+      for (recon_plan* p : e->plans)
+        if ((st = plan_objective(p, p->x, p->trace_fid + k, s)) != RECON_OK) return st;
+  }
+  if (e->obj) {
+    if ((st = launch_tmp_set(e, K, s)) != RECON_OK) return st;
+    RC(launch_finalize(e->d_fin, e->n, K, s));
+  }
+  return RECON_OK;
+}
+
+recon_status engine_apply_inverse(Engine* e, cudaStream_t s) { return launch_col_set(e, 0, s); }
+
+const float2* plan_result(const recon_plan* p) { return p->opts.max_iters == 0 ? p->b : p->x; }
+
+}  // namespace recon
+
+// ---------------------------------------------------------------------------
+// batched entry points
+// ---------------------------------------------------------------------------
+using namespace recon;
+
+recon_batch::~recon_batch() {
+  if (graph) cudaGraphExecDestroy(graph);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+}
+
+namespace {
+
+recon_status batch_enqueue(recon_batch* b, const float* const* kspace, float* const* image, cudaStream_t s) {
+  recon_status st;
+  for (int q = 0; q < b->eng.n; ++q)
+    if ((st = plan_prologue(b->eng.plans[q], kspace[q], s)) != RECON_OK) return st;
+  if ((st = engine_iterate(&b->eng, s, false)) != RECON_OK) return st;
+  for (int q = 0; q < b->eng.n; ++q) {
+    recon_plan* p = b->eng.plans[q];
+    if ((st = plan_to_user(p, plan_result(p), reinterpret_cast<float2*>(image[q]), s)) != RECON_OK) return st;
+  }
+  return RECON_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+recon_status recon_batch_create(recon_batch** out, recon_plan* const* plans, int n) {
+  if (!out || !plans || n < 1) return fail(RECON_ERR_INVALID_ARG, "bad argument");
+  *out = nullptr;
+  for (int q = 0; q < n; ++q)
+    if (!plans[q]) return fail(RECON_ERR_INVALID_ARG, "NULL plan in batch");
+  auto* b = new recon_batch();
+  recon_status st = engine_build(&b->eng, plans, n);
+  if (st != RECON_OK) {
+    delete b;
+    return st;
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "cudaStreamCreateWithFlags");
+  }
+  *out = b;
+  return RECON_OK;
+}
+
+recon_status recon_batch_solve(recon_batch* b, const float* const* kspace, float* const* image, void* stream) {
+  if (!b || !kspace || !image) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  const int n = b->eng.n;
+  std::vector<const void*> key;
+  for (int q = 0; q < n; ++q) {
+    if (!kspace[q] || !image[q]) return fail(RECON_ERR_INVALID_ARG, "NULL buffer in batch");
+    key.push_back(kspace[q]);
+    key.push_back(image[q]);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (recon_plan* p : b->eng.plans) p->last_stream = s;
+  if (b->graph && key == b->key) {
+    RC(cudaGraphLaunch(b->graph, s));
+    return RECON_OK;
+  }
+  // first call with these buffers: run directly (sets every kernel attribute),
+  // then capture the same sequence for the next calls
+  recon_status st = batch_enqueue(b, kspace, image, s);
+  if (st != RECON_OK) return st;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  RC(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  st = batch_enqueue(b, kspace, image, b->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &g);
+  if (st != RECON_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+  ce = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ce != cudaSuccess) {
+    b->graph = nullptr;
+    return cuda_fail(ce, "cudaGraphInstantiate");
+  }
+  b->key = key;
+  return RECON_OK;
+}
+
+recon_status recon_batch_info(recon_batch* b, recon_info* info, void* stream) {
+  if (!b || !info) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  recon_status worst = RECON_OK;
+  for (int q = 0; q < b->eng.n; ++q) {
+    recon_status st = plan_fill_info(b->eng.plans[q], &info[q], s);
+    if (st != RECON_OK && worst == RECON_OK) worst = st;
+  }
+  int err = 0;
+  if (b->eng.n > 1) RC(cudaMemcpy(&err, b->eng.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err & DEV_ERR_TIMEOUT) return fail(RECON_ERR_TIMEOUT, "a bounded device-side wait timed out");
+  return worst;
+}
+
+recon_status recon_batch_destroy(recon_batch* b) {
+  if (!b) return RECON_OK;
+  for (recon_plan* p : b->eng.plans)
+    if (p && p->last_stream) cudaStreamSynchronize(p->last_stream);
+  delete b;
+  return RECON_OK;
+}
+
+}  // extern "C"

@@ -175,9 +175,9 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a -
 constexpr int kRSlots = 2;  // double-buffered r inputs / partial sums
 
 struct ColLayout {
-  size_t bars, ring, ycopy, rvec, bvec, rslot, units, total;
+  size_t bars, ring, ycopy, rvec, bvec, rslot, units, slices, skip, work, total;
 };
-__host__ __device__ inline ColLayout col_layout(int stages, int nb, int nunits) {
+__host__ __device__ inline ColLayout col_layout(int stages, int nb, int nunits, int nslices, int work_max) {
   ColLayout L;
   const size_t ny32 = (size_t)(nb + 1) * 32;
   size_t o = 0;
@@ -191,12 +191,17 @@ __host__ __device__ inline ColLayout col_layout(int stages, int nb, int nunits) 
   L.bvec = o; o += (size_t)kRSlots * ny32 * 8;
   L.rslot = o; o += (size_t)kRSlots * 3 * ny32 * 8;   // [slot][base, add, b][ny32]
   L.units = o; o += (size_t)nunits * 16;
+  L.slices = o; o += (size_t)nslices * sizeof(ColSlice);
+  o = align_up(o, 16);
+  L.skip = o; o += (size_t)nslices * 4;
+  L.work = o; o += (size_t)work_max * 4;
   L.total = align_up(o, 128);
   return L;
 }
 
-// Persistent column-inverse kernel, warp-specialised and free of block-wide
-// barriers in the main loop (all hand-offs are bounded mbarrier waits):
+// Persistent column-inverse kernel over a work list of (slice, column) pairs,
+// warp-specialised and free of block-wide barriers in the main loop (all
+// hand-offs are bounded mbarrier waits):
 //   warp 8   producer: streams the packed inverses with the TMA engine
 //            (cp.async.bulk, L2 evict_first) into a ring of S stages
 //   warp 9   r loader: bulk-copies each column's right-hand-side inputs
@@ -205,11 +210,12 @@ __host__ __device__ inline ColLayout col_layout(int stages, int nb, int nunits) 
 //            objective dot products, clear the partials
 //   warps 0-7 consumers: Hermitian matvec of each unit into their own
 //            partial y vector of buffer n&1, column after column
+// Columns of slices whose stop flag is set are dropped from the work list
+// (every role reads the same snapshot of the flags).
 template <typename E>
-__global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColParams P) {
+__global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
   extern __shared__ __align__(128) unsigned char smem[];
-  if (P.flags[FLAG_STOP]) return;
-  const ColLayout L = col_layout(P.stages, P.nb, P.nunits);
+  const ColLayout L = col_layout(P.stages, P.nb_max, P.nunits_all, P.nslices, P.work_max);
   const int S = P.stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
   uint64_t* empty = full + S;
@@ -219,20 +225,31 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColParams P) {
   uint64_t* yc_empty = rv_full + kRSlots;
   uint64_t* col_done = yc_empty + kRSlots;
   unsigned char* ring = smem + L.ring;
-  const int ny32 = (P.nb + 1) * 32;
+  const int ny32m = (P.nb_max + 1) * 32;   // buffer stride (largest slice)
   float2* ycopy = reinterpret_cast<float2*>(smem + L.ycopy);
   float2* rvec = reinterpret_cast<float2*>(smem + L.rvec);
   float2* bvec = reinterpret_cast<float2*>(smem + L.bvec);
   float2* rslot = reinterpret_cast<float2*>(smem + L.rslot);
   int4* units = reinterpret_cast<int4*>(smem + L.units);
+  ColSlice* sl = reinterpret_cast<ColSlice*>(smem + L.slices);
+  int* skip = reinterpret_cast<int*>(smem + L.skip);
+  unsigned* wl = reinterpret_cast<unsigned*>(smem + L.work);   // this CTA's work list
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int u = tid; u < P.nunits; u += blockDim.x) units[u] = P.units[u];
-  for (int j = tid; j < kRSlots * kConsumerWarps * ny32; j += blockDim.x) ycopy[j] = make_float2(0.f, 0.f);
+  for (int u = tid; u < P.nunits_all; u += blockDim.x) units[u] = P.units[u];
+  for (int q = tid; q < P.nslices; q += blockDim.x) {
+    sl[q] = P.slices[q];
+    skip[q] = P.slices[q].stop ? *P.slices[q].stop : 0;
+  }
+  for (int j = tid; j < kRSlots * kConsumerWarps * ny32m; j += blockDim.x) ycopy[j] = make_float2(0.f, 0.f);
+  {
+    const int a = P.work_off[blockIdx.x], b = P.work_off[blockIdx.x + 1];
+    for (int w = a + tid; w < b; w += blockDim.x) wl[w - a] = P.work[w];
+  }
   if (tid == 0) {
     for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int s = 0; s < kRSlots; ++s) {
-      mbar_init(&rfull[s], P.r_tma ? 1 : 32);
+      mbar_init(&rfull[s], 1);
       mbar_init(&rempty[s], 1);
       mbar_init(&rv_full[s], 1);
       mbar_init(&yc_empty[s], 1);
@@ -242,22 +259,26 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColParams P) {
   }
   __syncthreads();
   constexpr int ES = Elem<E>::bytes;
-  const bool sep_b = P.do_obj && P.bsrc != P.base;
+  const int w0 = 0, w1 = P.work_off[blockIdx.x + 1] - P.work_off[blockIdx.x];
+  // work entry: slice in the high byte, column in the low 24 bits
+#define WSL(w) ((int)(wl[w] >> 24))
+#define WCOL(w) ((int)(wl[w] & 0xFFFFFFu))
 
   if (warp == kConsumerWarps) {
     // ---------------- producer: stream packed inverses into the ring --------
     if (lane == 0) {
       const uint64_t pol = policy_evict_first();
-      const unsigned char* Ab = reinterpret_cast<const unsigned char*>(P.A);
       // stage st of the ring, wraps = completed passes over the ring (no
       // divisions on the issue path)
       int st = 0, wraps = 0;
       bool ok = true;
-      for (int col = blockIdx.x; col < P.ncols && ok; col += gridDim.x) {
-        const unsigned char* cb = Ab + (size_t)col * (size_t)P.col_elems * ES;
-        for (int u = 0; u < P.nunits; ++u) {
-          if (wraps > 0 && !mbar_wait(&empty[st], (uint32_t)((wraps - 1) & 1), P.flags)) { ok = false; break; }
-          const int4 un = units[u];
+      for (int w = w0; w < w1 && ok; ++w) {
+        if (skip[WSL(w)]) continue;
+        const ColSlice& c = sl[WSL(w)];
+        const unsigned char* cb = reinterpret_cast<const unsigned char*>(c.A) + (size_t)WCOL(w) * (size_t)c.col_elems * ES;
+        for (int u = 0; u < c.nunits; ++u) {
+          if (wraps > 0 && !mbar_wait(&empty[st], (uint32_t)((wraps - 1) & 1), P.err)) { ok = false; break; }
+          const int4 un = units[c.unit_off + u];
           const uint32_t bytes = (uint32_t)((un.x == UNIT_TILE ? kTileElems : kRectElems) * ES);
           mbar_arrive_expect_tx(&full[st], bytes);
           bulk_g2s(ring + (size_t)st * kStageBytes, cb + (size_t)un.w * ES, bytes, &full[st], pol);
@@ -279,50 +300,56 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColParams P) {
   }
   if (warp == kConsumerWarps + 1) {
     // ---------------- r loader: each column's inputs into a slot -------------
-    // With 16-byte aligned columns (Ny even) one lane moves them with the TMA
-    // engine; otherwise all lanes load them (unrolled) and arrive.
+    // With 16-byte aligned columns (Ny even) lane 0 moves them with the TMA
+    // engine; otherwise all lanes load them and lane 0 arrives after a warp
+    // sync (the slot barrier always expects one arrival).
     int n = 0;
-    for (int col = blockIdx.x; col < P.ncols; col += gridDim.x, ++n) {
-      const int sl = n % kRSlots;
-      if (n >= kRSlots && !mbar_wait(&rempty[sl], (uint32_t)(((n / kRSlots) - 1) & 1), P.flags)) break;
-      float2* d = rslot + (size_t)sl * 3 * ny32;
-      const size_t cofs = (size_t)col * P.Ny;
-      if (P.r_tma) {
+    for (int w = w0; w < w1; ++w) {
+      if (skip[WSL(w)]) continue;
+      const ColSlice& c = sl[WSL(w)];
+      const bool sep_b = c.do_obj && c.bsrc != c.base;
+      const int slt = n % kRSlots;
+      if (n >= kRSlots && !mbar_wait(&rempty[slt], (uint32_t)(((n / kRSlots) - 1) & 1), P.err)) break;
+      float2* d = rslot + (size_t)slt * 3 * ny32m;
+      const size_t cofs = (size_t)WCOL(w) * c.Ny;
+      if (c.r_tma) {
         if (lane == 0) {
-          const uint32_t bytes = (uint32_t)P.Ny * 8u;
-          const uint32_t total = bytes * (1u + (P.add ? 1u : 0u) + (sep_b ? 1u : 0u));
+          const uint32_t bytes = (uint32_t)c.Ny * 8u;
+          const uint32_t total = bytes * (1u + (c.add ? 1u : 0u) + (sep_b ? 1u : 0u));
           const uint64_t pol = policy_evict_first();
-          mbar_arrive_expect_tx(&rfull[sl], total);
-          bulk_g2s(d, P.base + cofs, bytes, &rfull[sl], pol);
-          if (P.add) bulk_g2s(d + ny32, P.add + cofs, bytes, &rfull[sl], pol);
-          if (sep_b) bulk_g2s(d + 2 * ny32, P.bsrc + cofs, bytes, &rfull[sl], pol);
+          mbar_arrive_expect_tx(&rfull[slt], total);
+          bulk_g2s(d, c.base + cofs, bytes, &rfull[slt], pol);
+          if (c.add) bulk_g2s(d + ny32m, c.add + cofs, bytes, &rfull[slt], pol);
+          if (sep_b) bulk_g2s(d + 2 * ny32m, c.bsrc + cofs, bytes, &rfull[slt], pol);
         }
       } else {
-        for (int j0 = 0; j0 < P.Ny; j0 += 32 * 8) {
+        for (int j0 = 0; j0 < c.Ny; j0 += 32 * 8) {
           float2 va[8], vb[8], vc[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const int j = j0 + q * 32 + lane;
-            if (j < P.Ny) {
-              va[q] = P.base[cofs + j];
-              if (P.add) vb[q] = P.add[cofs + j];
-              if (sep_b) vc[q] = P.bsrc[cofs + j];
+            if (j < c.Ny) {
+              va[q] = c.base[cofs + j];
+              if (c.add) vb[q] = c.add[cofs + j];
+              if (sep_b) vc[q] = c.bsrc[cofs + j];
             }
           }
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const int j = j0 + q * 32 + lane;
-            if (j < P.Ny) {
+            if (j < c.Ny) {
               d[j] = va[q];
-              if (P.add) d[ny32 + j] = vb[q];
-              if (sep_b) d[2 * ny32 + j] = vc[q];
+              if (c.add) d[ny32m + j] = vb[q];
+              if (sep_b) d[2 * ny32m + j] = vc[q];
             }
           }
         }
-        mbar_arrive(&rfull[sl]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&rfull[slt]);
       }
+      ++n;
     }
-    if (P.r_tma && lane == 0) {
+    if (lane == 0) {
       // copies of the last slots may still be in flight if the kernel quits early
       for (int h = (n > kRSlots ? n - kRSlots : 0); h < n; ++h) {
         unsigned long long t0 = global_ns();
@@ -331,59 +358,87 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColParams P) {
     }
     return;
   }
+
+  // the columns this CTA processes (after dropping stopped slices)
+  int ncol = 0;
+  for (int w = w0; w < w1; ++w) ncol += skip[WSL(w)] ? 0 : 1;
+
   if (warp == kConsumerWarps + 2) {
     // ---------------- column manager -----------------------------------------
+    // walks the work list twice, in step: `wp` for prepare(n), `we` for the epilogue
+    int wp = w0, we = w0;
+    auto next_col = [&](int& w) -> int2 {
+      while (skip[WSL(w)]) ++w;
+      const int2 r = make_int2(WSL(w), WCOL(w));
+      ++w;
+      return r;
+    };
     // prepare(n): rvec[n&1] = base + coef*add (zero padded), bvec[n&1] = b
     auto prepare = [&](int n) -> bool {
-      const int sl = n % kRSlots;
-      if (!mbar_wait(&rfull[sl], (uint32_t)((n / kRSlots) & 1), P.flags)) return false;
-      const float2* d = rslot + (size_t)sl * 3 * ny32;
-      float2* rv = rvec + (size_t)(n & 1) * ny32;
-      float2* bv = bvec + (size_t)(n & 1) * ny32;
+      const int2 wk = next_col(wp);
+      const ColSlice& c = sl[wk.x];
+      const bool sep_b = c.do_obj && c.bsrc != c.base;
+      const int ny32 = (c.nb + 1) * 32;
+      const int slt = n % kRSlots;
+      if (!mbar_wait(&rfull[slt], (uint32_t)((n / kRSlots) & 1), P.err)) return false;
+      const float2* d = rslot + (size_t)slt * 3 * ny32m;
+      float2* rv = rvec + (size_t)(n & 1) * ny32m;
+      float2* bv = bvec + (size_t)(n & 1) * ny32m;
       for (int j = lane; j < ny32; j += 32) {
         float2 v = make_float2(0.f, 0.f), bb = make_float2(0.f, 0.f);
-        if (j < P.Ny) {
+        if (j < c.Ny) {
           v = d[j];
-          bb = sep_b ? d[2 * ny32 + j] : v;
-          if (P.add) {
-            const float2 a = d[ny32 + j];
-            v.x = fmaf(P.coef, a.x, v.x); v.y = fmaf(P.coef, a.y, v.y);
+          bb = sep_b ? d[2 * ny32m + j] : v;
+          if (c.add) {
+            const float2 a = d[ny32m + j];
+            v.x = fmaf(c.coef, a.x, v.x); v.y = fmaf(c.coef, a.y, v.y);
           }
         }
         rv[j] = v;
         bv[j] = bb;
       }
       __syncwarp();
-      if (lane == 0) { mbar_arrive(&rempty[sl]); mbar_arrive(&rv_full[n & 1]); }
+      if (lane == 0) { mbar_arrive(&rempty[slt]); mbar_arrive(&rv_full[n & 1]); }
       return true;
     };
-    int ncol = 0;
-    for (int col = blockIdx.x; col < P.ncols; col += gridDim.x) ++ncol;
     double fid = 0.0;
+    int fid_slice = -1;
     bool ok = true;
     for (int n = 0; n < ncol && n < kRSlots && ok; ++n) ok = prepare(n);
     for (int n = 0; n < ncol && ok; ++n) {
       const int bb = n & 1;
-      if (!mbar_wait(&col_done[bb], (uint32_t)((n >> 1) & 1), P.flags)) break;
-      const size_t cofs = (size_t)(blockIdx.x + (size_t)n * gridDim.x) * P.Ny;
-      float2* yc = ycopy + (size_t)bb * kConsumerWarps * ny32;
-      const float2* rv = rvec + (size_t)bb * ny32;
-      const float2* bv = bvec + (size_t)bb * ny32;
+      const int2 wk = next_col(we);
+      const ColSlice& c = sl[wk.x];
+      if (!mbar_wait(&col_done[bb], (uint32_t)((n >> 1) & 1), P.err)) break;
+      if (wk.x != fid_slice) {
+        // results of one slice go to that slice's accumulator
+        if (fid_slice >= 0 && sl[fid_slice].do_obj) {
+          const double f = warp_sum(fid);
+          if (lane == 0) atomicAdd(sl[fid_slice].fid_acc, f);
+        }
+        fid = 0.0;
+        fid_slice = wk.x;
+      }
+      const int ny32 = (c.nb + 1) * 32;
+      const size_t cofs = (size_t)wk.y * c.Ny;
+      float2* yc = ycopy + (size_t)bb * kConsumerWarps * ny32m;
+      const float2* rv = rvec + (size_t)bb * ny32m;
+      const float2* bv = bvec + (size_t)bb * ny32m;
       for (int j = lane; j < ny32; j += 32) {
         float2 x = yc[j];
         yc[j] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int w = 1; w < kConsumerWarps; ++w) {
-          x = c_add(x, yc[(size_t)w * ny32 + j]);
-          yc[(size_t)w * ny32 + j] = make_float2(0.f, 0.f);
+          x = c_add(x, yc[(size_t)w * ny32m + j]);
+          yc[(size_t)w * ny32m + j] = make_float2(0.f, 0.f);
         }
-        if (j < P.Ny) {
-          P.xout[cofs + j] = x;
-          if (P.do_obj) {
+        if (j < c.Ny) {
+          c.xout[cofs + j] = x;
+          if (c.do_obj) {
             const float2 r = rv[j], b = bv[j];
             // -2 Re<b, x> + Re<x, r> - mu |x|^2
             fid += -2.0 * ((double)b.x * x.x + (double)b.y * x.y) + ((double)x.x * r.x + (double)x.y * r.y) -
-                   (double)P.mu * ((double)x.x * x.x + (double)x.y * x.y);
+                   (double)c.mu * ((double)x.x * x.x + (double)x.y * x.y);
           }
         }
       }
@@ -391,9 +446,9 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColParams P) {
       if (lane == 0) mbar_arrive(&yc_empty[bb]);
       if (n + kRSlots < ncol) ok = prepare(n + kRSlots);
     }
-    if (P.do_obj) {
+    if (fid_slice >= 0 && sl[fid_slice].do_obj) {
       fid = warp_sum(fid);
-      if (lane == 0) atomicAdd(P.fid_acc, fid);
+      if (lane == 0) atomicAdd(sl[fid_slice].fid_acc, fid);
     }
     return;
   }
@@ -406,20 +461,22 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColParams P) {
   // wait is at most one phase ahead of its barrier.  Every column's rv/yc
   // barriers are waited on (and col_done arrived at) even when the warp has
   // no unit in that column, for the same reason.
-  int ncol = 0;
-  for (int col = blockIdx.x; col < P.ncols; col += gridDim.x) ++ncol;
   int u = warp, st = warp;
   uint32_t ph = 0;
+  int w = w0;
   for (int n = 0; n < ncol; ++n) {
+    while (skip[WSL(w)]) ++w;
+    const ColSlice& c = sl[WSL(w)];
+    ++w;
     const int bb = n & 1;
-    if (!mbar_wait(&rv_full[bb], (uint32_t)((n >> 1) & 1), P.flags)) break;
-    if (n >= 2 && !mbar_wait(&yc_empty[bb], (uint32_t)(((n >> 1) - 1) & 1), P.flags)) break;
-    const float2* rv = rvec + (size_t)bb * ny32;
-    float2* yw = ycopy + ((size_t)bb * kConsumerWarps + warp) * ny32;
+    if (!mbar_wait(&rv_full[bb], (uint32_t)((n >> 1) & 1), P.err)) break;
+    if (n >= 2 && !mbar_wait(&yc_empty[bb], (uint32_t)(((n >> 1) - 1) & 1), P.err)) break;
+    const float2* rv = rvec + (size_t)bb * ny32m;
+    float2* yw = ycopy + ((size_t)bb * kConsumerWarps + warp) * ny32m;
     bool failed = false;
-    for (; u < P.nunits; u += kConsumerWarps) {
-      if (!mbar_wait(&full[st], ph, P.flags)) { failed = true; break; }
-      const int4 un = units[u];
+    for (; u < c.nunits; u += kConsumerWarps) {
+      if (!mbar_wait(&full[st], ph, P.err)) { failed = true; break; }
+      const int4 un = units[c.unit_off + u];
       const E* tl = reinterpret_cast<const E*>(ring + (size_t)st * kStageBytes);
       if (un.x == UNIT_TILE) proc_tile<E>(tl, rv, yw, un.y, un.z, lane);
       else proc_rect<E>(tl, rv, yw, un.y, un.z, lane);
@@ -428,24 +485,26 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColParams P) {
       if (st >= S) { st -= S; ph ^= 1u; }
     }
     if (failed) break;
-    u -= P.nunits;
+    u -= c.nunits;
     if (lane == 0) mbar_arrive(&col_done[bb]);
   }
+#undef WSL
+#undef WCOL
 }
 
-size_t col_inverse_smem(const ColParams& p, int) { return col_layout(p.stages, p.nb, p.nunits).total; }
+size_t col_inverse_smem(int stages, int nb_max, int nunits_all, int nslices, int work_max) {
+  return col_layout(stages, nb_max, nunits_all, nslices, work_max).total;
+}
 
 // Largest ring depth that fits, a multiple of the consumer warp count (the
 // parity waits rely on it; see the consumer loop).
-int col_inverse_max_stages(const ColParams& p, int storage) {
+int col_inverse_max_stages(int nb_max, int nunits_all, int nslices, int work_max) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   int s = 4 * kConsumerWarps;
   while (s > kConsumerWarps) {
-    ColParams q = p;
-    q.stages = s;
-    if (col_inverse_smem(q, storage) + 1024 <= (size_t)optin) break;
+    if (col_inverse_smem(s, nb_max, nunits_all, nslices, work_max) + 1024 <= (size_t)optin) break;
     s -= kConsumerWarps;
   }
   return s;
@@ -454,125 +513,186 @@ int col_inverse_max_stages(const ColParams& p, int storage) {
 int col_inverse_stage_quantum() { return kConsumerWarps; }
 
 template <typename E>
-static cudaError_t launch_col_t(const ColParams& p, int grid, size_t smem, cudaStream_t s) {
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_col_inverse<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
-  k_col_inverse<E><<<grid, kColThreads, smem, s>>>(p); note_launch();
-  return cudaGetLastError();
+static size_t& col_configured() {
+  static size_t v = 0;
+  return v;
 }
 
-cudaError_t launch_col_inverse(const ColParams& p, int storage, int grid, size_t smem, cudaStream_t s) {
+cudaError_t prepare_col_inverse(int storage, size_t smem) {
+  auto go = [&](auto kern, size_t& conf) -> cudaError_t {
+    if (smem <= conf) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) conf = smem;
+    return e;
+  };
   switch (storage) {
-    case 0: return launch_col_t<float2>(p, grid, smem, s);
-    case 1: return launch_col_t<__half2>(p, grid, smem, s);
-    case 2: return launch_col_t<__nv_bfloat162>(p, grid, smem, s);
+    case 0: return go(k_col_inverse<float2>, col_configured<float2>());
+    case 1: return go(k_col_inverse<__half2>, col_configured<__half2>());
+    case 2: return go(k_col_inverse<__nv_bfloat162>, col_configured<__nv_bfloat162>());
     default: return cudaErrorInvalidValue;
   }
 }
 
+cudaError_t launch_col_inverse(const ColLaunch& p, int storage, int grid, cudaStream_t s) {
+  const size_t smem = col_inverse_smem(p.stages, p.nb_max, p.nunits_all, p.nslices, p.work_max);
+  cudaError_t e = prepare_col_inverse(storage, smem);
+  if (e != cudaSuccess) return e;
+  switch (storage) {
+    case 0: k_col_inverse<float2><<<grid, kColThreads, smem, s>>>(p); break;
+    case 1: k_col_inverse<__half2><<<grid, kColThreads, smem, s>>>(p); break;
+    case 2: k_col_inverse<__nv_bfloat162><<<grid, kColThreads, smem, s>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Slice of a temporal launch's block (binary search over the slices' first blocks).
+template <typename SliceT>
+__device__ __forceinline__ int find_slice(const SliceT* sl, int n, int blk) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sl[mid].tile0 <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // ---------------------------------------------------------------------------
-// Algorithm 2 temporal step, one thread per pixel over a tile of kTvPix
-// pixels (column layout keeps a tile's pixels contiguous for every t):
+// Algorithm 2 temporal step on a tile of px pixels x Nt frames (column
+// layout keeps a tile's pixels contiguous for every t):
 //   v  = S(D_t m + d1, lambda/(2 mu1))
 //   m' = (rho I + D_t'D_t)^{-1} [D_t'(v - d1) + rho (x + d2)]    (Thomas)
 //   d1' = d1 - (v - D_t m')
 // with d2 = x - p, and p' = m' - d2 handed to the inverse step, which forms
 // r = H'y + mu2 (m' - d2) = b + mu2 p'.  The next d2 is then x' - p'.
-// The tile's inputs are staged in shared memory with asynchronous copies
-// (all in flight at once), then both sweeps run from shared memory.  Also
+// Phase 1 (all threads, every (t, pixel)): stage the tile with asynchronous
+// copies, then e = d1 - v, rhs and f = p - x.  Phase 2 (one thread per pixel):
+// the two tridiagonal sweeps only.  Phase 3 (all threads): outputs.  Also
 // accumulates ||D_t x||_1 of the incoming x (the prior term of J).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(64) k_tv_temporal(TvParams P) {
+constexpr int kTvThreads = 256;
+
+template <int PX>
+__global__ void __launch_bounds__(kTvThreads) k_tv_temporal(TemporalLaunch L) {
   extern __shared__ __align__(16) float2 sm_tv[];
   __shared__ double red[32];
-  if (P.flags[FLAG_STOP]) return;
-  const int tid = threadIdx.x, PX = blockDim.x, Nt = P.Nt;
+  const TvSlice* sls = static_cast<const TvSlice*>(L.slices);
+  const TvSlice& P = sls[find_slice(sls, L.nslices, (int)blockIdx.x)];
+  if (P.stop && *P.stop) return;
+  constexpr int TS = kTvThreads / PX;   // t-stride of a thread
+  const int tid = threadIdx.x, Nt = P.Nt;
+  const int pp = tid % PX, t0 = tid / PX;  // this thread: pixel pp, frames t0, t0+TS, ...
   const long long N = P.npix;
-  const long long pix0 = (long long)blockIdx.x * PX;
+  const long long pix0 = (long long)(blockIdx.x - P.tile0) * PX;
   const int npx = (int)min((long long)PX, N - pix0);
-  // [Nt][PX] tiles: m, d1, x (later e = d1 - v), p (later f = p - x), d'
+  const bool mine = pp < npx;
+  const int T = Nt * PX;
+  // [Nt][PX] tiles: m (then m'), d1 (then e), x (then rhs), p (then f)
   float2* sm_m = sm_tv;
-  float2* sm_d1 = sm_m + (size_t)Nt * PX;
-  float2* sm_x = sm_d1 + (size_t)Nt * PX;
-  float2* sm_p = sm_x + (size_t)Nt * PX;
-  float2* sm_dp = sm_p + (size_t)Nt * PX;
-  if (tid < npx) {
-    for (int t = 0; t < Nt; ++t) {
-      const long long g = t * N + pix0 + tid;
-      cp_async8(&sm_x[t * PX + tid], P.x + g);
+  float2* sm_d1 = sm_m + T;
+  float2* sm_x = sm_d1 + T;
+  float2* sm_p = sm_x + T;
+  if (mine) {
+    const float2* gx = P.x + pix0 + pp;
+    for (int t = t0; t < Nt; t += TS) {
+      const long long g = t * N;
+      const int idx = t * PX + pp;
+      cp_async8(&sm_x[idx], gx + g);
       if (P.write_state) {
-        cp_async8(&sm_m[t * PX + tid], P.m + g);
-        cp_async8(&sm_p[t * PX + tid], P.p + g);
-        if (P.d1 && t + 1 < Nt) cp_async8(&sm_d1[t * PX + tid], P.d1 + g);
+        cp_async8(&sm_m[idx], P.m + pix0 + pp + g);
+        cp_async8(&sm_p[idx], P.p + pix0 + pp + g);
+        if (P.d1 && t + 1 < Nt) cp_async8(&sm_d1[idx], P.d1 + pix0 + pp + g);
       }
     }
   }
   cp_async_wait_all();
+  __syncthreads();
   double tv = 0.0;
-  if (tid < npx) {
-    float2 x_prev = sm_x[tid];
-    for (int t = 1; t < Nt; ++t) {
-      const float2 x_t = sm_x[t * PX + tid];
-      tv += (double)c_abs(c_sub(x_t, x_prev));
-      x_prev = x_t;
-    }
-    if (P.write_state) {
-      float2 m_t = sm_m[tid];
-      float2 e_prev = make_float2(0.f, 0.f), d_prev = make_float2(0.f, 0.f);
-      for (int t = 0; t < Nt; ++t) {
-        const float2 x_t = sm_x[t * PX + tid], p_t = sm_p[t * PX + tid];
-        float2 e_t = make_float2(0.f, 0.f), m_n = make_float2(0.f, 0.f);
+  if (mine)
+    for (int t = t0; t + 1 < Nt; t += TS) tv += (double)c_abs(c_sub(sm_x[(t + 1) * PX + pp], sm_x[t * PX + pp]));
+  if (P.write_state) {
+    // e_t = d1_t - S(m_{t+1} - m_t + d1_t) for t < Nt-1 (0 at t = Nt-1)
+    if (mine)
+      for (int t = t0; t < Nt; t += TS) {
+        const int idx = t * PX + pp;
+        float2 e = make_float2(0.f, 0.f);
         if (t + 1 < Nt) {
-          m_n = sm_m[(t + 1) * PX + tid];
-          const float2 d1_t = P.d1 ? sm_d1[t * PX + tid] : make_float2(0.f, 0.f);
-          const float2 v = c_soft(c_add(c_sub(m_n, m_t), d1_t), P.tau1);
-          e_t = c_sub(d1_t, v);
+          const float2 d1_t = P.d1 ? sm_d1[idx] : make_float2(0.f, 0.f);
+          const float2 v = c_soft(c_add(c_sub(sm_m[idx + PX], sm_m[idx]), d1_t), P.tau1);
+          e = c_sub(d1_t, v);
         }
-        // rhs = D'(v - d1) + rho (x + d2),  (D'u)_t = u_{t-1} - u_t,  u = -e
-        float2 rhs = c_sub(e_t, e_prev);
+        sm_d1[idx] = e;  // d1 is not needed any more
+      }
+    __syncthreads();
+    // rhs_t = e_t - e_{t-1} + rho (2 x_t - p_t);  f_t = p_t - x_t
+    if (mine)
+      for (int t = t0; t < Nt; t += TS) {
+        const int idx = t * PX + pp;
+        const float2 x_t = sm_x[idx], p_t = sm_p[idx];
+        float2 rhs = sm_d1[idx];
+        if (t > 0) rhs = c_sub(rhs, sm_d1[idx - PX]);
         rhs.x = fmaf(P.rho, 2.f * x_t.x - p_t.x, rhs.x);
         rhs.y = fmaf(P.rho, 2.f * x_t.y - p_t.y, rhs.y);
+        sm_x[idx] = rhs;
+        sm_p[idx] = c_sub(p_t, x_t);
+      }
+    __syncthreads();
+    // phase 2: Thomas sweeps, one thread per pixel; m' into the m tile
+    if (tid < npx) {
+      float2 d_prev = make_float2(0.f, 0.f);
+      for (int t = 0; t < Nt; ++t) {
         const float inv = __ldg(P.thomas + t);
-        const float2 dp = c_scale(c_add(rhs, d_prev), inv);
-        sm_dp[t * PX + tid] = dp;
-        sm_x[t * PX + tid] = e_t;               // x no longer needed: keep e
-        sm_p[t * PX + tid] = c_sub(p_t, x_t);   // keep f = p - x
-        d_prev = dp; e_prev = e_t; m_t = m_n;
+        d_prev = c_scale(c_add(sm_x[t * PX + tid], d_prev), inv);
+        sm_m[t * PX + tid] = d_prev;
       }
       float2 mnext = make_float2(0.f, 0.f);
       for (int t = Nt - 1; t >= 0; --t) {
         const float inv = __ldg(P.thomas + t);
-        const float2 dp = sm_dp[t * PX + tid];
-        const float2 mt = make_float2(fmaf(inv, mnext.x, dp.x), fmaf(inv, mnext.y, dp.y));
-        const long long g = t * N + pix0 + tid;
-        if (t + 1 < Nt) P.d1_out[g] = c_add(sm_x[t * PX + tid], c_sub(mnext, mt));
-        P.p_out[g] = c_add(mt, sm_p[t * PX + tid]);
-        P.m_out[g] = mt;
-        mnext = mt;
+        const float2 dp = sm_m[t * PX + tid];
+        mnext = make_float2(fmaf(inv, mnext.x, dp.x), fmaf(inv, mnext.y, dp.y));
+        sm_m[t * PX + tid] = mnext;
       }
     }
+    __syncthreads();
+    // phase 3: m', d1' = e + D m', p' = m' + f
+    if (mine)
+      for (int t = t0; t < Nt; t += TS) {
+        const int idx = t * PX + pp;
+        const long long g = t * N + pix0 + pp;
+        const float2 mt = sm_m[idx];
+        P.m_out[g] = mt;
+        P.p_out[g] = c_add(mt, sm_p[idx]);
+        if (t + 1 < Nt) P.d1_out[g] = c_add(sm_d1[idx], c_sub(sm_m[idx + PX], mt));
+      }
   }
-  const double s = group_sum(tv, red, tid, PX, BlockBar());
+  const double s = group_sum(tv, red, tid, kTvThreads, BlockBar());
   if (tid == 0) atomicAdd(P.prior_acc, s);
 }
 
-cudaError_t launch_tv_temporal(const TvParams& p, cudaStream_t s) {
-  // five [Nt][PX] complex tiles must fit (Nt <= 128)
-  int px = 64;
-  while (px > 32 && 5 * (size_t)p.Nt * px * sizeof(float2) > 200 * 1024) px >>= 1;
-  const size_t smem = 5 * (size_t)p.Nt * px * sizeof(float2);
+// four [Nt][px] complex tiles: px = 64 up to Nt = 96, else 32 (Nt <= 128)
+int tv_tile_px(int Nt_max) { return Nt_max <= 96 ? 64 : 32; }
+
+cudaError_t prepare_tv_temporal(int Nt_max) {
   static size_t configured = 0;
+  const size_t smem = 4 * (size_t)Nt_max * tv_tile_px(Nt_max) * sizeof(float2);
   if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_tv_temporal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_tv_temporal<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tv_temporal<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  const long long grid = (p.npix + px - 1) / px;
-  k_tv_temporal<<<(unsigned)grid, px, smem, s>>>(p); note_launch();
+  return cudaSuccess;
+}
+
+cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s) {
+  cudaError_t e = prepare_tv_temporal(p.Nt_max);
+  if (e != cudaSuccess) return e;
+  const size_t smem = 4 * (size_t)p.Nt_max * p.tile_px * sizeof(float2);
+  if (p.tile_px == 64) k_tv_temporal<64><<<p.nblocks, kTvThreads, smem, s>>>(p);
+  else k_tv_temporal<32><<<p.nblocks, kTvThreads, smem, s>>>(p);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -586,16 +706,20 @@ cudaError_t launch_tv_temporal(const TvParams& p, cudaStream_t s) {
 // accumulates ||w||_1 (the prior term of J at the incoming iterate).
 // ---------------------------------------------------------------------------
 constexpr int kDftPix = 64;
-__global__ void __launch_bounds__(256) k_dft_temporal(DftParams P) {
+int dft_tile_px() { return kDftPix; }
+
+__global__ void __launch_bounds__(256) k_dft_temporal(TemporalLaunch L) {
   extern __shared__ float2 sm_dft[];
   __shared__ double red[32];
-  if (P.flags[FLAG_STOP]) return;
+  const DftSlice* sls = static_cast<const DftSlice*>(L.slices);
+  const DftSlice& P = sls[find_slice(sls, L.nslices, (int)blockIdx.x)];
+  if (P.stop && *P.stop) return;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Nt = P.Nt;
   float2* A = sm_dft;
   float2* B = sm_dft + (size_t)Nt * kDftPix;
   const long long N = P.npix;
-  const long long pix0 = (long long)blockIdx.x * kDftPix;
+  const long long pix0 = (long long)(blockIdx.x - P.tile0) * kDftPix;
   const int npx = (int)min((long long)kDftPix, N - pix0);
   for (int idx = tid; idx < Nt * kDftPix; idx += nth) {
     const int t = idx / kDftPix, pp = idx - t * kDftPix;
@@ -641,16 +765,22 @@ __global__ void __launch_bounds__(256) k_dft_temporal(DftParams P) {
   if (tid == 0) atomicAdd(P.prior_acc, s);
 }
 
-cudaError_t launch_dft_temporal(const DftParams& p, cudaStream_t s) {
-  const size_t smem = 2 * (size_t)p.Nt * kDftPix * sizeof(float2);
+cudaError_t prepare_dft_temporal(int Nt_max) {
   static size_t configured = 0;
+  const size_t smem = 2 * (size_t)Nt_max * kDftPix * sizeof(float2);
   if (smem > 48 * 1024 && smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(k_dft_temporal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  const long long grid = (p.npix + kDftPix - 1) / kDftPix;
-  k_dft_temporal<<<(unsigned)grid, 256, smem, s>>>(p); note_launch();
+  return cudaSuccess;
+}
+
+cudaError_t launch_dft_temporal(const TemporalLaunch& p, cudaStream_t s) {
+  cudaError_t e = prepare_dft_temporal(p.Nt_max);
+  if (e != cudaSuccess) return e;
+  const size_t smem = 2 * (size_t)p.Nt_max * kDftPix * sizeof(float2);
+  k_dft_temporal<<<p.nblocks, 256, smem, s>>>(p); note_launch();
   return cudaGetLastError();
 }
 
@@ -687,28 +817,29 @@ cudaError_t launch_objective(const ObjParams& p, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// J(k) = ||y - Hx||^2 + lambda * prior, Delta(k) (Eq. r_ratio) and the stop
-// flag: later launches see flags[FLAG_STOP] and return at once.
+// Per slice: J(k) = ||y - Hx||^2 + lambda * prior, Delta(k) (Eq. r_ratio) and
+// the stop flag; later launches see the flag and skip that slice.
 // ---------------------------------------------------------------------------
-__global__ void k_finalize(const double* fid, const double* prior, const double* yy, double* J, int k, float lam,
-                           double tol, int* flags) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void k_finalize(const FinSlice* fins, int n, int k) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const FinSlice f = fins[q];
+  int* flags = f.flags;
   if (flags[FLAG_STOP]) return;
-  const double Jk = fid[k] + (yy ? *yy : 0.0) + (double)lam * prior[k];
-  J[k] = Jk;
+  const double Jk = f.fid[k] + ((f.yy && k > 0) ? *f.yy : 0.0) + (double)f.lam * f.prior[k];
+  f.J[k] = Jk;
   if (!isfinite(Jk)) atomicOr(&flags[FLAG_ERR], DEV_ERR_NONFINITE);
-  if (tol > 0.0 && k >= 1) {
-    const double d = (J[k - 1] - Jk) / Jk;
-    if (d >= 0.0 && d < tol) {
+  if (f.tol > 0.0 && k >= 1) {
+    const double d = (f.J[k - 1] - Jk) / Jk;
+    if (d >= 0.0 && d < f.tol) {
       flags[FLAG_ITERS] = k;
       flags[FLAG_STOP] = 1;
     }
   }
 }
 
-cudaError_t launch_finalize(const double* fid, const double* prior, const double* yy, double* J, int k, float lam,
-                            double tol, int* flags, cudaStream_t s) {
-  k_finalize<<<1, 32, 0, s>>>(fid, prior, yy, J, k, lam, tol, flags); note_launch();
+cudaError_t launch_finalize(const FinSlice* fins, int nslices, int k, cudaStream_t s) {
+  k_finalize<<<(nslices + 127) / 128, 128, 0, s>>>(fins, nslices, k); note_launch();
   return cudaGetLastError();
 }
 

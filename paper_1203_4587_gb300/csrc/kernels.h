@@ -49,31 +49,47 @@ void fill_twiddles_host(int n, float2* host_tw);           // exp(-2 pi i k/n)
 void fill_twiddles_host64(int n, double2* host_tw);
 
 // ---- kernel parameter blocks ----------------------------------------------
-struct ColParams {           // data-consistency inverse x = A r, per column
+// The per-iteration kernels take arrays of per-problem ("slice") descriptors:
+// a single reconstruction is a batch of one, and a batch of uneven slices
+// runs in one launch per step.  The host builds one descriptor set per
+// iteration once (the buffers a slice uses never move), so an iteration's
+// launches only point at set k and a whole solve can be captured as a graph.
+
+struct ColSlice {            // data-consistency inverse x = A r of one slice
   const void* A;             // packed stream base
   long long col_elems;
-  int nunits;
-  const int4* units;         // {kind, p, q, elem offset}
-  int Nx, Ny, Nt, nb;
-  int ncols;
-  int stages;                // ring depth
+  int Ny, nb;
+  int nunits, unit_off;      // this slice's unit table inside ColLaunch::units
+  int r_tma;                 // 1: r inputs move by bulk copy (Ny*8 a multiple of 16)
+  int do_obj;
   const float2* base;        // r = base + coef * add   ([Nt][Nx][Ny])
   const float2* add;         // may be null
-  float coef;
   const float2* bsrc;        // H'y for the objective term (may equal base)
-  int r_tma;                 // 1: r inputs move by bulk copy (Ny*8 a multiple of 16)
   float2* xout;
+  float coef;
+  float mu;
   // data term of J for the new x, with (mu I + H'H) x = r:
   //   ||y - Hx||^2 = ||y||^2 - 2 Re<H'y, x> + Re<x, r> - mu ||x||^2
   // the kernel adds the last three terms to *fid_acc (||y||^2 comes from the
   // prologue).
-  int do_obj;
-  float mu;
   double* fid_acc;
-  int* flags;
+  const int* stop;           // the slice's stop flag: its columns are skipped when set
 };
 
-struct TvParams {            // temporal step of Algorithm 2 (R = D_t)
+struct ColLaunch {
+  const ColSlice* slices;
+  int nslices;
+  const int4* units;         // concatenated unit tables {kind, p, q, elem offset}
+  int nunits_all;
+  const unsigned* work;      // (slice << 24) | column, in processing order
+  const int* work_off;       // [gridDim.x + 1]: CTA b processes work[work_off[b] .. work_off[b+1])
+  int work_max;              // longest per-CTA list (staged in shared memory)
+  int nb_max;                // largest block count of any slice (shared-memory sizing)
+  int stages;                // ring depth (a multiple of the consumer warp count)
+  int* err;                  // device error bits of the launch
+};
+
+struct TvSlice {             // temporal step of Algorithm 2 (R = D_t) of one slice
   int Nt;
   long long npix;            // Nx*Ny
   const float2* m;           // [Nt][npix]
@@ -88,10 +104,11 @@ struct TvParams {            // temporal step of Algorithm 2 (R = D_t)
   const float* thomas;       // [Nt] pivots of (rho I + D'D)
   int write_state;           // 0: only the prior term
   double* prior_acc;         // += ||D_t x||_1
-  const int* flags;
+  const int* stop;
+  int tile0;                 // first block of this slice in the launch
 };
 
-struct DftParams {           // temporal step of Algorithm 1 (Psi = temporal DFT)
+struct DftSlice {            // temporal step of Algorithm 1 (Psi = temporal DFT) of one slice
   int Nt;
   long long npix;
   const float2* xh;          // xhat = A r of the previous iteration (b at k=1)
@@ -105,7 +122,26 @@ struct DftParams {           // temporal step of Algorithm 1 (Psi = temporal DFT
   int write_state;
   FftPlanDev ft;
   double* prior_acc;         // += ||w||_1
-  const int* flags;
+  const int* stop;
+  int tile0;
+};
+
+struct TemporalLaunch {      // one launch over the tiles of several slices
+  const void* slices;        // TvSlice[] or DftSlice[]
+  int nslices;
+  int nblocks;
+  int Nt_max;                // shared-memory sizing
+  int tile_px;               // pixels per block (TV)
+};
+
+struct FinSlice {            // J(k), Delta(k) and the stop flag of one slice
+  const double* fid;
+  const double* prior;
+  const double* yy;          // ||y||^2 (fused objective) or null
+  double* J;
+  int* flags;
+  float lam;
+  double tol;
 };
 
 struct ObjParams {           // ||y - H x||^2 of a given field (no inverse)
@@ -126,16 +162,20 @@ void note_launch();
 void set_last_error(const std::string& why);
 
 // ---- launchers (return cudaGetLastError()) ---------------------------------
-cudaError_t launch_col_inverse(const ColParams& p, int storage, int grid, size_t smem, cudaStream_t s);
-size_t col_inverse_smem(const ColParams& p, int storage);
-int col_inverse_max_stages(const ColParams& p, int storage);
+cudaError_t launch_col_inverse(const ColLaunch& p, int storage, int grid, cudaStream_t s);
+size_t col_inverse_smem(int stages, int nb_max, int nunits_all, int nslices, int work_max);
+int col_inverse_max_stages(int nb_max, int nunits_all, int nslices, int work_max);
 int col_inverse_stage_quantum();  // ring depth must be a positive multiple of this
-cudaError_t launch_tv_temporal(const TvParams& p, cudaStream_t s);
-cudaError_t launch_dft_temporal(const DftParams& p, cudaStream_t s);
+cudaError_t prepare_tv_temporal(int Nt_max);   // shared-memory attribute, outside any capture
+cudaError_t prepare_dft_temporal(int Nt_max);
+cudaError_t prepare_col_inverse(int storage, size_t smem);
+int tv_tile_px(int Nt_max);
+int dft_tile_px();
+cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s);
+cudaError_t launch_dft_temporal(const TemporalLaunch& p, cudaStream_t s);
 cudaError_t launch_objective(const ObjParams& p, cudaStream_t s);
-// J(k) = fid[k] + (yy ? *yy : 0) + lambda prior[k]; Delta(k); stop flag.
-cudaError_t launch_finalize(const double* fid, const double* prior, const double* yy, double* J, int k, float lam,
-                            double tol, int* flags, cudaStream_t s);
+// per slice: J(k) = fid[k] + (yy ? *yy : 0) + lambda prior[k]; Delta(k); stop flag.
+cudaError_t launch_finalize(const FinSlice* fins, int nslices, int k, cudaStream_t s);
 
 // prologue / operators
 cudaError_t launch_hybrid_rows(const void* kspace, int kdtype, const float* kscale, float2* yhat, const int* rows,

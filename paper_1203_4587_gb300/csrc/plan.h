@@ -1,0 +1,153 @@
+// Internal host-side structures: the plan behind recon_plan*, and the
+// engine that launches the ADMM iterations of one plan or of a batch.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/recon.h"
+#include "kernels.h"
+
+namespace recon {
+
+// Device buffers owned by one engine (freed with it).
+struct DevArena {
+  std::vector<void*> ptrs;
+  cudaError_t alloc(void** p, size_t bytes);
+  void release();
+  ~DevArena() { release(); }
+};
+
+// Launch data for the iterations of a set of plans: one descriptor set per
+// iteration, built once (the buffers of a plan never move), so iteration k
+// only points at set k and a whole solve can be captured as a graph.
+struct Engine {
+  std::vector<recon_plan*> plans;
+  int n = 0;               // number of slices
+  int K = 0;               // iterations (the same for every slice)
+  bool tv = true;          // prior (the same for every slice)
+  bool fused = false;      // objective data term inside the inverse kernel
+  bool obj = false;        // objective on
+  int storage = 0;
+  // temporal launches: K+1 descriptor sets (k = 1..K, then the final prior term)
+  void* d_tmp = nullptr;
+  int tmp_blocks = 0, Nt_max = 0, tile_px = 0;
+  // column-inverse launches: K descriptor sets
+  ColSlice* d_col = nullptr;
+  int4* d_units = nullptr;
+  int nunits_all = 0;
+  unsigned* d_work = nullptr;
+  int* d_work_off = nullptr;
+  int grid = 0, nb_max = 0, stages = 0, work_max = 0;
+  int* d_err = nullptr;    // error word shared by the engine's launches
+  FinSlice* d_fin = nullptr;
+  DevArena arena;
+};
+
+}  // namespace recon
+
+struct recon_plan {
+  int Nx = 0, Ny = 0, Nt = 0, Nc = 0;
+  recon_prior prior = RECON_PRIOR_TV;
+  float lam = 0.f, mu = 0.f;
+  recon_opts opts{};
+  int device = 0, num_sms = 0;
+  cudaStream_t last_stream = nullptr;
+  recon::PackInfo pk{};
+  int storage = 0;
+  size_t esize = 8;
+  std::vector<int> h_rows, h_rowoff;
+  std::vector<int4> h_units;
+  int maxm = 0, total_rows = 0;
+  // device memory
+  std::vector<void*> allocs;
+  void* A = nullptr;
+  float2* sens = nullptr;
+  int* rows = nullptr;
+  int* rowoff = nullptr;
+  float2 *tw_x = nullptr, *tw_y = nullptr, *tw_t = nullptr;
+  double2 *tw64_x = nullptr, *tw64_y = nullptr;
+  double2* yhat64 = nullptr;           // FP64 hybrid data of the prologue
+  float* thomas = nullptr;
+  float2* yhat = nullptr;
+  float2* b = nullptr;
+  float2* s0[2] = {nullptr, nullptr};  // TV: m;  DFT: u
+  float2* s1[2] = {nullptr, nullptr};  // TV: d1
+  float2* s2[2] = {nullptr, nullptr};  // TV: p
+  float2* x = nullptr;                 // TV: x; DFT: xhat
+  float2* r = nullptr;                 // DFT: r
+  float2* tmp_a = nullptr;             // operator entry points
+  float2* tmp_b = nullptr;
+  float2* kstage = nullptr;            // host-solve staging
+  float2* istage = nullptr;
+  double* trace_fid = nullptr;
+  double* trace_prior = nullptr;
+  double* trace_J = nullptr;
+  double* yy = nullptr;                // ||y||^2 over the sampled entries (FP64)
+  int* flags = nullptr;
+  recon::FftPlanDev fx{}, fy{}, ft{};
+  recon::FftPlanDev64 fx64{}, fy64{};
+  int col_stages = 0;
+  int last_iters = 0;
+  recon::Engine* eng = nullptr;        // the plan's own iterations (a batch of one)
+  recon::Engine* eng_inv = nullptr;    // recon_apply_inverse (tmp_a -> tmp_b)
+  // opts.profile: event pairs around every inverse / temporal launch of a solve
+  std::vector<cudaEvent_t> ev_col, ev_tmp;
+  cudaEvent_t ev_solve[2] = {nullptr, nullptr};
+  int n_col = 0, n_tmp = 0;
+  bool prof_valid = false;
+
+  cudaError_t alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) allocs.push_back(*p);
+    return e;
+  }
+  ~recon_plan();
+  void mark(std::vector<cudaEvent_t>& v, int& n, bool begin, cudaStream_t s) {
+    if (!opts.profile) return;
+    const size_t idx = 2 * (size_t)n + (begin ? 0 : 1);
+    if (idx < v.size()) cudaEventRecord(v[idx], s);
+    if (!begin) ++n;
+  }
+  size_t npix() const { return (size_t)Nx * Ny; }
+  size_t nimg() const { return (size_t)Nx * Ny * Nt; }
+};
+
+struct recon_batch {
+  recon::Engine eng;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<const void*> key;        // buffers the captured graph reads / writes
+  cudaStream_t cap_stream = nullptr;
+  ~recon_batch();
+};
+
+namespace recon {
+
+recon_status fail(recon_status st, const std::string& why);
+recon_status cuda_fail(cudaError_t e, const char* where);
+
+#define RC(call)                                                \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return recon::cuda_fail(e_, #call);  \
+  } while (0)
+
+// engine.cu
+recon_status engine_build(Engine* e, recon_plan* const* plans, int n);
+recon_status engine_build_inverse(Engine* e, recon_plan* p);   // tmp_a -> tmp_b, no objective
+// Resets traces/flags, J(0), K iterations and the final prior term of every
+// slice (prologues must have run).  `profile` records the plan's events (n = 1).
+recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile);
+recon_status engine_apply_inverse(Engine* e, cudaStream_t s);
+const float2* plan_result(const recon_plan* p);   // image (internal layout) after K iterations
+recon_status plan_prologue(recon_plan* p, const float* kspace, cudaStream_t s);
+recon_status plan_to_user(recon_plan* p, const float2* in, float2* out, cudaStream_t s);
+recon_status plan_to_internal(recon_plan* p, const float2* in, float2* out, cudaStream_t s);
+recon_status plan_adjoint64(recon_plan* p, const float* kspace, float2* yhat32, float2* b, double* yy,
+                            cudaStream_t s);
+recon_status plan_objective(recon_plan* p, const float2* x, double* acc, cudaStream_t s);
+recon_status plan_fill_info(recon_plan* p, recon_info* info, cudaStream_t s);
+
+}  // namespace recon

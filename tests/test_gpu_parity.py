@@ -256,3 +256,40 @@ def test_reduced_precision_storage_error_is_reported(storage, tol):
     prob = oracle.Problem(case.kspace, case.sens, case.mask, case.mu)
     J_of_x = oracle.objective_tv(host(x), case.lam, prob.fid)
     assert abs(info.J - J_of_x) / J_of_x < 1e-5
+
+
+BATCH = [
+    dict(Nx=24, Ny=64, Nt=6, Nc=3, R=4, seed=11),
+    dict(Nx=40, Ny=40, Nt=8, Nc=4, R=3, seed=12),     # ragged Ny (padded block)
+    dict(Nx=16, Ny=96, Nt=5, Nc=2, R=4, seed=13),     # odd block count
+    dict(Nx=33, Ny=128, Nt=7, Nc=3, R=6, seed=14),
+]
+
+
+@pytest.mark.parametrize("prior", ["tv", "dft"])
+def test_batched_solve_matches_single_solves(prior):
+    """Uneven slices in one batch: one launch per step, then a graph replay."""
+    from paper_1203_4587_gb300 import Batch
+    iters = 15
+    cases = [make("tiny", **{k: v for k, v in sh.items()}) for sh in BATCH]
+    plans = [plan_for(c, prior=prior, max_iters=iters) for c in cases]
+    singles = []
+    for c, p in zip(cases, plans):
+        x, info = p.solve(gpu(c.kspace))
+        singles.append((host(x), info.J))
+    batch = Batch(plans)
+    ks = [gpu(c.kspace) for c in cases]
+    for call in range(2):          # direct run, then graph replay
+        outs = batch.solve(ks)
+        infos = batch.info()
+        for q, (c, (xs, Js)) in enumerate(zip(cases, singles)):
+            xb = host(outs[q])
+            # same arithmetic, different unit-to-warp assignment (rounding order)
+            assert rel(xb, xs) < TOL, (call, q)
+            assert infos[q].iters == iters
+            # fused objective: absolute error about 2 eps ||x||^2 either way
+            assert abs(infos[q].J - Js) <= 4 * 2.0 ** -24 * np.linalg.norm(xs) ** 2 + 1e-6 * Js
+            if call == 0:
+                xr, _ = _oracle_solve(c, prior, iters)
+                assert rel(xb, xr) < TOL, q
+    batch.close()
