@@ -17,6 +17,13 @@ Extra keys on the JSON line:
   cpu_baseline  the FP64 oracle on a bounded sample (a subset of columns,
                 single-threaded), scaled to the full workload
   variants      the synthesis prior (Algorithm 1) and lambda=0.02
+  batched       64 uneven slices in one batched solve (graph replay)
+  precision     384x384x48 frames x16 coils, R=6: FP32 / FP16 / BF16 storage
+                (inverses and hybrid coil data; 16-bit k-space for the 16-bit
+                runs), iters/s and the inverse kernel's HBM fraction each
+  grad          differentiable unrolled Algorithm 2: forward and backward
+                (dL/dy, dL/dlambda, dL/dmu) of 4 slices 192x192x24x8,
+                20 iterations, checkpoints every 5
 
 Run:  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 For N>1 (torchrun) each rank solves its own slice (weak scaling, no
@@ -59,6 +66,10 @@ def parse():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-slices", type=int, default=64)
+    ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--grad-only", action="store_true",
+                    help="only the differentiable-form measurement (one JSON line with its numbers)")
     return ap.parse_args()
 
 
@@ -269,6 +280,103 @@ def measure_batched(nslices, storage, steps=3):
                      "from a captured CUDA graph; plan (FP64 factorisation) reported separately")}
 
 
+def measure_precision(steps=3):
+    """The precision workload with FP32, FP16 and BF16 storage, J(k) every iteration."""
+    import numpy as np
+    import torch
+
+    import synthdata
+    from paper_1203_4587_gb300 import Plan
+    from paper_1203_4587_gb300.binding import quantize_kspace
+    c = synthdata.make_case("precision")
+    sens = torch.from_numpy(c.sens.astype(np.complex64)).cuda()
+    k = torch.from_numpy(c.kspace.astype(np.complex64)).cuda()
+    mask = c.mask.astype(np.uint8)
+    Nt, Ny, Nx = c.x_true.shape
+    peak, peak_kind = hbm_peak()
+    out = {"workload": "384x384x48 frames x16 coils, R=6, TV, lambda=0.005, mu=0.1, 100 iterations, "
+                       "J(k) every iteration (fused for FP32, explicit FFTs for 16-bit)",
+           "peak_source": f"{peak_kind} hbm_gbs (copy)"}
+    stream = torch.cuda.current_stream()
+    for storage in ("fp32", "fp16", "bf16"):
+        t0 = time.perf_counter()
+        p = Plan(mask, sens, c.lam, c.mu, prior="tv", rho=c.rho, max_iters=c.iters, storage=storage, profile=1)
+        torch.cuda.synchronize()
+        plan_s = time.perf_counter() - t0
+        q = quantize_kspace(k, storage) if storage != "fp32" else None
+        img = torch.empty((Nt, Ny, Nx), dtype=torch.complex64, device="cuda")
+
+        def run():
+            if q is None:
+                p.solve(k, img, info=False)
+            else:
+                p.solve_quantized(q, img, info=False)
+        for _ in range(2):
+            run()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            run()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        prof = p.profile()
+        A_bytes = p.inverse_bytes
+        col_ms = prof.inverse_ms / max(prof.inverse_launches, 1)
+        bytes_launch = A_bytes + 3 * 8 * Nx * Ny * Nt
+        out[storage] = {"iters_per_s": c.iters / (ms / 1e3), "ms_per_solve": ms, "plan_s": plan_s,
+                        "inverse_bytes": A_bytes, "inverse_avg_ms": col_ms,
+                        "inverse_gbs": bytes_launch / (col_ms / 1e3) / 1e9,
+                        "inverse_frac": bytes_launch / (col_ms / 1e3) / 1e9 / peak,
+                        "inverse_share": prof.inverse_ms / max(prof.solve_ms, 1e-9)}
+        p.close()
+        del q
+        torch.cuda.empty_cache()
+    return out
+
+
+def measure_grad(storage, steps=5):
+    """Forward and backward of unrolled Algorithm 2 over a batch of 4 slices."""
+    import numpy as np
+    import torch
+
+    import synthdata
+    from paper_1203_4587_gb300 import Grad, Plan
+    cases = [synthdata.make_case("diff", seed=q) for q in range(4)]
+    iters = cases[0].iters
+    plans = [Plan(c.mask.astype(np.uint8), torch.from_numpy(c.sens.astype(np.complex64)).cuda(), c.lam, c.mu,
+                  prior="tv", rho=c.rho, max_iters=iters, objective=0, storage=storage) for c in cases]
+    ks = [torch.from_numpy(c.kspace.astype(np.complex64)).cuda() for c in cases]
+    xt = [torch.from_numpy(c.x_true.astype(np.complex64)).cuda() for c in cases]
+    g = Grad(plans, checkpoint_every=5)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    fwd, bwd = [], []
+    for s in range(2 + steps):
+        ev[0].record(stream)
+        xs = g.forward(ks)
+        ev[1].record(stream)
+        gi = [2.0 * (x - t) for x, t in zip(xs, xt)]
+        ev[2].record(stream)
+        g.backward(gi)      # fills dL/dlambda, dL/dmu: synchronises
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        if s >= 2:
+            fwd.append(ev[0].elapsed_time(ev[1]))
+            bwd.append(ev[2].elapsed_time(ev[3]))
+    g.close()
+    for p in plans:
+        p.close()
+    f, b = statistics.median(fwd), statistics.median(bwd)
+    return {"forward_ms": f, "backward_ms": b, "backward_over_forward": b / f, "slices": 4,
+            "iters": iters, "checkpoint_every": 5,
+            "note": ("192x192x24 frames x8 coils, R=8, TV, lambda=0.005, mu=0.1, rho=0.5; forward = H'y + 20 "
+                     "steps keeping checkpoints; backward = segment recomputation + reverse steps + dL/dy = H b_bar "
+                     "+ the lambda/mu gradients (host read)")}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -431,6 +539,20 @@ def run_native(args):
         except Exception as e:  # report, never fake
             line["batched"] = {"error": str(e)[:300]}
 
+    if not args.no_precision and rank == 0:
+        torch.cuda.empty_cache()
+        try:
+            line["precision"] = measure_precision()
+        except Exception as e:  # report, never fake
+            line["precision"] = {"error": str(e)[:300]}
+
+    if not args.no_grad and rank == 0:
+        torch.cuda.empty_cache()
+        try:
+            line["grad"] = measure_grad(args.storage)
+        except Exception as e:  # report, never fake
+            line["grad"] = {"error": str(e)[:300]}
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             res = oracle_sample(args.prior, ncols=2, budget=10.0)
@@ -449,6 +571,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.grad_only:
+        print(json.dumps({"grad": measure_grad(args.storage, steps=args.steps)}), flush=True)
+        return 0
     return run_native(args)
 
 

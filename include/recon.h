@@ -64,21 +64,32 @@ typedef enum {
   RECON_ERR_UNSUPPORTED = 7         /* valid request this build does not support */
 } recon_status;
 
+/* Storage of the data a solve keeps in device memory.  For a plan (opts.storage):
+ *   FP32  packed inverses and hybrid coil data F_h'y in complex64; the H'y
+ *         prologue in FP64, rounded once.
+ *   FP16 / BF16  packed inverses (FP64 factorisation rounded once) and the
+ *         hybrid coil data (per-frame power-of-two scales) as 16-bit (re, im)
+ *         pairs; FFT butterflies, products and accumulation in FP32; the
+ *         objective and the stopping test reduce in FP64.
+ * For k-space (recon_kspace.storage): complex64, or 16-bit pairs with
+ * per-frame scales (recon_quantize_kspace).  Any k-space storage goes with
+ * any plan storage. */
 typedef enum {
-  RECON_STORAGE_FP32 = 0, /* inverses stored as complex64 */
-  RECON_STORAGE_FP16 = 1, /* inverses stored as 2 x fp16, arithmetic in FP32 */
-  RECON_STORAGE_BF16 = 2  /* inverses stored as 2 x bf16, arithmetic in FP32 */
+  RECON_STORAGE_FP32 = 0,
+  RECON_STORAGE_FP16 = 1,
+  RECON_STORAGE_BF16 = 2
 } recon_storage;
 
 typedef struct {
   float rho;        /* mu2 / mu1 for Algorithm 2 (default 0.5, Section V); ignored for DFT */
   int max_iters;    /* iterations K (default 50); 0 returns H'y */
   double tol;       /* stop when 0 <= Delta(k) < tol (Eq. r_ratio); 0 = run K iterations */
-  int storage;      /* recon_storage of the packed inverses (default FP32) */
+  int storage;      /* recon_storage of the inverses and hybrid coil data (default FP32) */
   int objective;    /* J(k) every iteration: 0 = off (tol must be 0), 1 = fused (default), 2 = exact.
                        Fused: the data term ||y - Hx||^2 = ||y||^2 - 2Re<H'y,x> + Re<x,r> - mu||x||^2
                        uses (mu I + H'H) x = r of the inverse step, in the inverse kernel; its absolute
-                       error is about 2 eps ||x||^2 (eps = 2^-24), adequate for Delta(k) (Eq. r_ratio).
+                       error is <x, e>, e the FP32 residual of that system, at most about
+                       2 (1 + mu) sqrt(Ny) eps ||x||^2 (eps = 2^-24), adequate for Delta(k) (Eq. r_ratio).
                        Exact: ||y - Hx||^2 by explicit FFTs after each inverse step.  16-bit storage
                        always uses the exact form. */
   int mask_full;    /* 1 = mask is [Nt][Ny][Nx] and must be constant along kx (default 0) */
@@ -177,6 +188,73 @@ recon_status recon_batch_info(recon_batch* b, recon_info* info, void* stream);
 
 /* Frees the batch (not its plans).  NULL-safe. */
 recon_status recon_batch_destroy(recon_batch* b);
+
+/* ---- differentiable unrolled Algorithm 2 -----------------------------------
+ * Reverse mode of K = max_iters steps of Algorithm 2 (temporal TV), so that
+ * the reconstruction can sit inside a learned pipeline.  The paper gives no
+ * derivative; the adjoint of each step is written out by hand:
+ *   x' = (mu I + H'H)^{-1} r (Eq. eigen_mu) is self-adjoint and
+ *   d/dmu (mu I + H'H)^{-1} = -(mu I + H'H)^{-2};
+ *   the Thomas solve with the symmetric (rho I + D_t'D_t) is self-adjoint;
+ *   the complex soft threshold S(a, tau) has, for |a| > tau, the Jacobian
+ *   (1 - tau/|a|) I + (tau/|a|) n n^T (n = a/|a| as a real 2-vector), and
+ *   dS/dtau = -n; for |a| <= tau both are 0.
+ * Parameters: mu2 = mu (the plan's mu), mu1 = mu / rho with rho fixed, so
+ * the threshold is lambda rho / (2 mu).  Gradients of the complex inputs
+ * follow dL/dRe + i dL/dIm (a real loss L of the image).  The forward keeps
+ * the state (x, m, d1, d2) every `checkpoint_every` steps (and the last);
+ * the backward recomputes each segment from its checkpoint and then walks it
+ * backwards: memory is (K / checkpoint_every + checkpoint_every + 3) states of
+ * 4 image fields per slice. */
+typedef struct recon_grad recon_grad; /* opaque, owned by the library */
+
+/* Prepares the forward/backward pair over `n` plans (borrowed, 1 <= n <= 255;
+ * TV prior, equal max_iters >= 1 and storage).  checkpoint_every <= 0 means 5.
+ * The plans' H'y buffers hold the forward's input until the backward ran:
+ * do not solve with these plans in between.  Errors: INVALID_ARG,
+ * UNSUPPORTED, OOM, CUDA. */
+recon_status recon_grad_create(recon_grad** out, recon_plan* const* plans, int n, int checkpoint_every);
+
+/* image[q] = x_K of slice q from kspace[q] (device buffers laid out as for
+ * recon_solve; no objective, no early stop).  Enqueues on `stream`. */
+recon_status recon_grad_forward(recon_grad* g, const float* const* kspace, float* const* image, void* stream);
+
+/* Given grad_image[q] = dL/dx_K (device complex64 [Nt][Ny][Nx]), writes
+ * grad_kspace[q] = dL/dy (device complex64 [Nt][Nc][Ny][Nx], 0 on unsampled
+ * rows) and, when the pointers are non-NULL, grad_lambda[q] = dL/dlambda and
+ * grad_mu[q] = dL/dmu (host double arrays of n entries; filling them
+ * synchronises `stream`).  Must follow recon_grad_forward with the same
+ * plans; may be called again for another grad_image.  Errors: INVALID_ARG,
+ * TIMEOUT (a bounded device-side wait expired), CUDA. */
+recon_status recon_grad_backward(recon_grad* g, const float* const* grad_image, float* const* grad_kspace,
+                                 double* grad_lambda, double* grad_mu, void* stream);
+
+/* Frees the gradient state (not its plans).  NULL-safe. */
+recon_status recon_grad_destroy(recon_grad* g);
+
+/* ---- reduced-precision k-space ----------------------------------------------
+ * k-space in device memory as complex64, or as 16-bit (re, im) pairs scaled
+ * per frame: entry (t, c, ky, kx) is data[t][c][ky][kx] * frame_scale[t]. */
+typedef struct {
+  const void* data;          /* device [Nt][Nc][Ny][Nx]: complex64, or 2 x fp16 / 2 x bf16 */
+  int storage;               /* recon_storage of `data` */
+  const float* frame_scale;  /* device [Nt]; NULL = all 1 */
+} recon_kspace;
+
+/* recon_solve with a recon_kspace input (same behaviour otherwise). */
+recon_status recon_solve_kspace(recon_plan* plan, const recon_kspace* kspace, float* image, recon_info* info,
+                                void* stream);
+
+/* Quantises complex64 k-space (device [Nt][Nc][Ny][Nx]) to 16-bit pairs
+ * (storage FP16 or BF16) with per-frame power-of-two scales: frame_scale[t]
+ * (device [Nt], written) = 2^e with max_component_t / 2^e in [2^14, 2^15)
+ * (1 for an all-zero frame), out[t] = k[t] / frame_scale[t] rounded once
+ * to nearest.  FP16 then holds every frame's values with an 11-bit
+ * significand down to 2^-29 of the frame's largest component.  `out` is
+ * device memory of Nt*Nc*Ny*Nx*4 bytes.  Enqueued on `stream`.
+ * Errors: INVALID_ARG, CUDA. */
+recon_status recon_quantize_kspace(int Nx, int Ny, int Nt, int Nc, const float* kspace, int storage, void* out,
+                                   float* frame_scale, void* stream);
 
 /* Frees the plan and all its device memory.  NULL-safe. */
 recon_status recon_destroy(recon_plan* plan);

@@ -17,14 +17,18 @@ Lagrangian and Parallel Processing":
   temporal TV), step by step in the paper's order
 * objective J and the convergence ratio Delta(k) (Section V, Eq. r_ratio)
 * the reverse-mode gradient of unrolled Algorithm 2 (``grad.py``)
+* the 16-bit storage encoding with per-frame power-of-two scales
+  (``precision.py``)
 
 Every function here is pinned by a ``-m "not gpu"`` test in
-``tests/test_oracle_pins.py`` and ``tests/test_oracle_grad.py`` against closed
+``tests/test_oracle_pins.py``, ``tests/test_oracle_grad.py`` and
+``tests/test_oracle_precision.py`` against closed
 forms, brute force, finite differences or invariants.
 """
 
 from .admm import *  # noqa: F401,F403
 from .admm import __all__ as _admm_all
 from .grad import unrolled_tv_adjoint, unrolled_tv_forward, unrolled_tv_loss_and_grad  # noqa: F401
+from . import precision  # noqa: F401
 
 __all__ = list(_admm_all) + ["unrolled_tv_forward", "unrolled_tv_adjoint", "unrolled_tv_loss_and_grad"]

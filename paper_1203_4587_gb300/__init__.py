@@ -4,9 +4,10 @@ Bilen, Wang & Selesnick's augmented-Lagrangian method for Cartesian ky-t
 undersampled multi-coil dynamic MRI: Algorithm 1 (synthesis prior, temporal
 DFT) and Algorithm 2 (analysis prior, temporal TV) with the exact per-column
 data-consistency inverse of Section IV-C.  The C ABI is in
-``include/recon.h``; ``binding`` is its ctypes wrapper.
+``include/recon.h``; ``binding`` is its ctypes wrapper, with ``unrolled_tv``
+the differentiable (autograd) form of K steps of Algorithm 2.
 """
 
-from .binding import Batch, Plan, ReconError, load, default_opts  # noqa: F401
+from .binding import Batch, Grad, Plan, ReconError, default_opts, load, unrolled_tv  # noqa: F401
 
-__all__ = ["Batch", "Plan", "ReconError", "load", "default_opts"]
+__all__ = ["Batch", "Grad", "Plan", "ReconError", "load", "default_opts", "unrolled_tv"]

@@ -16,6 +16,8 @@ import ctypes as C
 import math
 import os
 
+import numpy as np
+
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -31,7 +33,9 @@ EXPORTS = ["recon_default_opts", "recon_plan_create", "recon_solve", "recon_solv
            "recon_destroy", "recon_apply_adjoint", "recon_apply_forward", "recon_apply_inverse",
            "recon_export_inverse", "recon_inverse_bytes", "recon_status_string", "recon_last_error",
            "recon_get_profile", "recon_kernel_launches", "recon_gram_inverse_noalloc",
-           "recon_batch_create", "recon_batch_solve", "recon_batch_info", "recon_batch_destroy"]
+           "recon_batch_create", "recon_batch_solve", "recon_batch_info", "recon_batch_destroy",
+           "recon_grad_create", "recon_grad_forward", "recon_grad_backward", "recon_grad_destroy",
+           "recon_solve_kspace", "recon_quantize_kspace"]
 
 
 class Opts(C.Structure):
@@ -42,6 +46,10 @@ class Opts(C.Structure):
 class Info(C.Structure):
     _fields_ = [("iters", C.c_int), ("J", C.c_double), ("J0", C.c_double), ("delta", C.c_double),
                 ("stopped", C.c_int)]
+
+
+class KSpace(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("storage", C.c_int), ("frame_scale", C.c_void_p)]
 
 
 class Profile(C.Structure):
@@ -104,6 +112,19 @@ def load(path: str = LIB_PATH):
     lib.recon_batch_info.restype = i
     lib.recon_batch_destroy.argtypes = [vp]
     lib.recon_batch_destroy.restype = i
+    lib.recon_grad_create.argtypes = [C.POINTER(vp), C.POINTER(vp), i, i]
+    lib.recon_grad_create.restype = i
+    lib.recon_grad_forward.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), vp]
+    lib.recon_grad_forward.restype = i
+    lib.recon_grad_backward.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double), vp]
+    lib.recon_grad_backward.restype = i
+    lib.recon_grad_destroy.argtypes = [vp]
+    lib.recon_grad_destroy.restype = i
+    lib.recon_solve_kspace.argtypes = [vp, C.POINTER(KSpace), fp, C.POINTER(Info), vp]
+    lib.recon_solve_kspace.restype = i
+    lib.recon_quantize_kspace.argtypes = [i, i, i, i, fp, i, vp, fp, vp]
+    lib.recon_quantize_kspace.restype = i
     _lib = lib
     return lib
 
@@ -191,6 +212,16 @@ class Plan:
         _check(st)
         return out, inf
 
+    def solve_quantized(self, q, out=None, info=True, stream=None):
+        """Runs the reconstruction from 16-bit k-space ``q`` (a QuantizedKspace)."""
+        out = self._img() if out is None else out
+        inf = Info() if info else None
+        y = KSpace(q.data.data_ptr(), STORAGE[q.storage], q.frame_scale.data_ptr())
+        st = load().recon_solve_kspace(self._h, C.byref(y), _ptr(out), C.byref(inf) if info else None,
+                                       _stream(stream))
+        _check(st)
+        return out, inf
+
     def solve_host(self, kspace_host, image_host, stream=None):
         """Host buffers in and out (copies inside the call); returns Info."""
         inf = Info()
@@ -272,6 +303,109 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Grad:
+    """Differentiable unrolled Algorithm 2 over plans (recon_grad_*).
+
+    ``forward`` runs the plans' max_iters steps keeping checkpoints;
+    ``backward`` takes dL/dx_K per slice and returns dL/dy per slice and
+    dL/dlambda, dL/dmu (NumPy float64 arrays, one entry per slice).  The plans
+    must not be solved with between the two calls.
+    """
+
+    def __init__(self, plans, checkpoint_every=5):
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        self._h = C.c_void_p()
+        _check(load().recon_grad_create(C.byref(self._h), arr, len(self.plans), int(checkpoint_every)))
+
+    def forward(self, kspaces, stream=None):
+        ks = [_c64(k, "cuda") for k in kspaces]
+        outs = [p._img() for p in self.plans]
+        ka = (C.c_void_p * len(ks))(*[k.data_ptr() for k in ks])
+        oa = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+        _check(load().recon_grad_forward(self._h, ka, oa, _stream(stream)))
+        return outs
+
+    def backward(self, grad_images, stream=None):
+        gs = [_c64(g, "cuda") for g in grad_images]
+        outs = [p._ksp() for p in self.plans]
+        n = len(self.plans)
+        ga = (C.c_void_p * n)(*[g.data_ptr() for g in gs])
+        oa = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+        gl = (C.c_double * n)()
+        gm = (C.c_double * n)()
+        _check(load().recon_grad_backward(self._h, ga, oa, gl, gm, _stream(stream)))
+        return outs, np.array(gl[:], dtype=np.float64), np.array(gm[:], dtype=np.float64)
+
+    def close(self):
+        if self._h:
+            load().recon_grad_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _UnrolledTV(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, grad, lam, mu, *kspaces):
+        ctx.grad = grad
+        return tuple(grad.forward(kspaces))
+
+    @staticmethod
+    def backward(ctx, *grad_images):
+        g = [torch.zeros_like(p._img()) if gi is None else gi for p, gi in zip(ctx.grad.plans, grad_images)]
+        gk, gl, gm = ctx.grad.backward(g)
+        return (None, torch.from_numpy(gl), torch.from_numpy(gm), *gk)
+
+
+def unrolled_tv(grad, kspaces, lam, mu):
+    """Images x_K of every slice as a differentiable function of the k-space
+    data and of lambda, mu (float64 tensors with one entry per slice).
+
+    lam and mu must equal the plans' values (the plans hold the inverses for
+    their mu); their gradients are dL/dlambda and dL/dmu at those values.
+    """
+    lam = torch.as_tensor(lam, dtype=torch.float64)
+    mu = torch.as_tensor(mu, dtype=torch.float64)
+    lv, mv = lam.detach().reshape(-1).tolist(), mu.detach().reshape(-1).tolist()
+    for q, p in enumerate(grad.plans):
+        if abs(lv[q] - p.lam) > 1e-6 * abs(p.lam) or abs(mv[q] - p.mu) > 1e-6 * abs(p.mu):
+            raise ValueError(f"slice {q}: lambda/mu differ from the plan's")
+    return list(_UnrolledTV.apply(grad, lam, mu, *kspaces))
+
+
+class QuantizedKspace:
+    """16-bit k-space with per-frame power-of-two scales (recon_quantize_kspace).
+
+    ``data`` int32 [Nt, Nc, Ny, Nx] holding (re, im) 16-bit pairs, ``frame_scale``
+    float32 [Nt]; entry = pair * frame_scale[t].
+    """
+
+    def __init__(self, data, storage, frame_scale):
+        self.data, self.storage, self.frame_scale = data, storage, frame_scale
+
+    def to_complex(self):
+        """Dequantised complex64 copy (for inspection and tests)."""
+        dt = torch.float16 if self.storage == "fp16" else torch.bfloat16
+        pairs = self.data.view(dt).view(*self.data.shape, 2).float()
+        return torch.complex(pairs[..., 0], pairs[..., 1]) * self.frame_scale.view(-1, 1, 1, 1)
+
+
+def quantize_kspace(kspace, storage="fp16", stream=None):
+    """complex64 [Nt, Nc, Ny, Nx] on the GPU -> QuantizedKspace (fp16 or bf16)."""
+    k = _c64(kspace, "cuda")
+    Nt, Nc, Ny, Nx = k.shape
+    data = torch.empty((Nt, Nc, Ny, Nx), dtype=torch.int32, device="cuda")
+    scale = torch.empty((Nt,), dtype=torch.float32, device="cuda")
+    _check(load().recon_quantize_kspace(int(Nx), int(Ny), int(Nt), int(Nc), _ptr(k), STORAGE[storage], _ptr(data),
+                                        _ptr(scale), _stream(stream)))
+    return QuantizedKspace(data, storage, scale)
 
 
 def gram_inverse_noalloc(mask_rows, sens_cols, mu, out=None, stream=None):

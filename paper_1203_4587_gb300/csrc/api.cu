@@ -186,7 +186,10 @@ namespace recon {
 recon_status plan_objective(recon_plan* p, const float2* x, double* acc, cudaStream_t s) {
   ObjParams o{};
   o.Nx = p->Nx; o.Ny = p->Ny; o.Nt = p->Nt; o.Nc = p->Nc; o.ncg = coil_group_for(p->Nc, p->Ny);
-  o.x = x; o.sens = p->sens; o.yhat = p->yhat; o.rows = p->rows; o.rowoff = p->rowoff; o.fy = p->fy;
+  o.x = x; o.sens = p->sens; o.rows = p->rows; o.rowoff = p->rowoff; o.fy = p->fy;
+  o.yhat = p->storage ? p->yhat_lp : static_cast<const void*>(p->yhat);
+  o.ystorage = p->storage;
+  o.yscale = p->yscale;
   o.fid_acc = acc; o.flags = p->flags;
   RC(launch_objective(o, s));
   return RECON_OK;
@@ -204,17 +207,26 @@ recon_status plan_to_user(recon_plan* p, const float2* in, float2* out, cudaStre
 
 // H'y in FP64 (rounded once to FP32), the FP32 hybrid data for J(k) and
 // ||y||^2 (into *yy, which must be zeroed first).
-recon_status plan_adjoint64(recon_plan* p, const float* kspace, float2* yhat32, float2* b, double* yy,
-                            cudaStream_t s) {
-  RC(launch_hybrid_rows64(reinterpret_cast<const float2*>(kspace), p->yhat64, yhat32, yy, p->rows, p->rowoff,
-                          p->maxm, p->Nx, p->Ny, p->Nt, p->Nc, p->fx64, s));
+recon_status plan_adjoint64(recon_plan* p, const void* kspace, int kstorage, const float* kscale, float2* yhat32,
+                            float2* b, double* yy, cudaStream_t s) {
+  RC(launch_hybrid_rows64(kspace, kstorage, kscale, p->yhat64, yhat32, yy, p->rows, p->rowoff, p->maxm, p->Nx, p->Ny,
+                          p->Nt, p->Nc, p->fx64, s));
   RC(launch_adjoint_combine64(p->yhat64, p->sens, b, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fy64, s));
   return RECON_OK;
 }
 
-recon_status plan_prologue(recon_plan* p, const float* kspace, cudaStream_t s) {
+// FP32 storage: the FP64 prologue above (the 1e-5 bar needs it).  16-bit
+// storage: FP32 butterflies and accumulation, the hybrid data kept in 16 bits
+// with per-frame power-of-two scales (its FP32 values pass through tmp_b).
+recon_status plan_prologue(recon_plan* p, const void* kspace, int kstorage, const float* kscale, cudaStream_t s) {
   RC(cudaMemsetAsync(p->yy, 0, sizeof(double), s));
-  return plan_adjoint64(p, kspace, p->yhat, p->b, p->yy, s);
+  if (p->storage == 0) return plan_adjoint64(p, kspace, kstorage, kscale, p->yhat, p->b, p->yy, s);
+  RC(cudaMemsetAsync(p->ymax, 0, (size_t)p->Nt * sizeof(unsigned), s));
+  RC(launch_hybrid_rows(kspace, kstorage, kscale, p->tmp_b, p->yy, p->ymax, p->rows, p->rowoff, p->maxm, p->Nx, p->Ny,
+                        p->Nt, p->Nc, p->fx, s));
+  RC(launch_adjoint_combine(p->tmp_b, p->sens, p->b, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fy,
+                            p->storage, p->yhat_lp, p->ymax, p->yscale, s));
+  return RECON_OK;
 }
 
 recon_status plan_fill_info(recon_plan* p, recon_info* info, cudaStream_t s) {
@@ -333,7 +345,14 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
   PC(p->alloc((void**)&p->tw64_y, Ny * sizeof(double2)));
   PC(p->alloc((void**)&p->yhat64, std::max<size_t>(1, (size_t)p->total_rows * Nx * Nc) * sizeof(double2)));
   PC(p->alloc((void**)&p->thomas, Nt * sizeof(float)));
-  PC(p->alloc((void**)&p->yhat, std::max<size_t>(1, (size_t)p->total_rows * Nx * Nc) * sizeof(float2)));
+  const size_t nyhat = std::max<size_t>(1, (size_t)p->total_rows * Nx * Nc);
+  if (o.storage == RECON_STORAGE_FP32) {
+    PC(p->alloc((void**)&p->yhat, nyhat * sizeof(float2)));
+  } else {  // 16-bit hybrid data with per-frame scales
+    PC(p->alloc(&p->yhat_lp, nyhat * 4));
+    PC(p->alloc((void**)&p->ymax, Nt * sizeof(unsigned)));
+    PC(p->alloc((void**)&p->yscale, Nt * sizeof(float)));
+  }
   PC(p->alloc((void**)&p->b, nimg * sizeof(float2)));
   for (int k = 0; k < 2; ++k) {
     PC(p->alloc((void**)&p->s0[k], nimg * sizeof(float2)));
@@ -448,15 +467,17 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
 #undef PC
 }
 
-recon_status recon_solve(recon_plan* p, const float* kspace, float* image, recon_info* info, void* stream) {
+recon_status recon_solve_kspace(recon_plan* p, const recon_kspace* y, float* image, recon_info* info, void* stream) {
   g_last_error.clear();
-  if (!p || !kspace || !image) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  if (!p || !y || !y->data || !image) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  if (y->storage < RECON_STORAGE_FP32 || y->storage > RECON_STORAGE_BF16)
+    return fail(RECON_ERR_INVALID_ARG, "k-space storage must be a recon_storage value");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   p->last_stream = s;
   p->n_col = p->n_tmp = 0;
   p->prof_valid = p->opts.profile != 0;
   if (p->opts.profile) cudaEventRecord(p->ev_solve[0], s);
-  recon_status st = plan_prologue(p, kspace, s);
+  recon_status st = plan_prologue(p, y->data, y->storage, y->frame_scale, s);
   if (st != RECON_OK) return st;
   st = engine_iterate(p->eng, s, p->opts.profile != 0);
   if (st != RECON_OK) return st;
@@ -464,6 +485,23 @@ recon_status recon_solve(recon_plan* p, const float* kspace, float* image, recon
   if (st != RECON_OK) return st;
   if (p->opts.profile) cudaEventRecord(p->ev_solve[1], s);
   if (info) return plan_fill_info(p, info, s);
+  return RECON_OK;
+}
+
+recon_status recon_solve(recon_plan* p, const float* kspace, float* image, recon_info* info, void* stream) {
+  const recon_kspace y{kspace, RECON_STORAGE_FP32, nullptr};
+  return recon_solve_kspace(p, &y, image, info, stream);
+}
+
+recon_status recon_quantize_kspace(int Nx, int Ny, int Nt, int Nc, const float* kspace, int storage, void* out,
+                                   float* frame_scale, void* stream) {
+  g_last_error.clear();
+  if (Nx < 1 || Ny < 1 || Nt < 1 || Nc < 1 || !kspace || !out || !frame_scale)
+    return fail(RECON_ERR_INVALID_ARG, "bad argument");
+  if (storage != RECON_STORAGE_FP16 && storage != RECON_STORAGE_BF16)
+    return fail(RECON_ERR_INVALID_ARG, "storage must be RECON_STORAGE_FP16 or RECON_STORAGE_BF16");
+  RC(launch_quantize_kspace(reinterpret_cast<const float2*>(kspace), (long long)Nc * Ny * Nx, Nt, storage, out,
+                            frame_scale, static_cast<cudaStream_t>(stream)));
   return RECON_OK;
 }
 
@@ -526,7 +564,7 @@ recon_status recon_get_trace(recon_plan* p, double* J_host, int n) {
 recon_status recon_apply_adjoint(recon_plan* p, const float* kspace, float* image, void* stream) {
   if (!p || !kspace || !image) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  recon_status st = plan_adjoint64(p, kspace, p->tmp_b, p->tmp_a, nullptr, s);
+  recon_status st = plan_adjoint64(p, kspace, 0, nullptr, p->tmp_b, p->tmp_a, nullptr, s);
   if (st != RECON_OK) return st;
   return plan_to_user(p, p->tmp_a, reinterpret_cast<float2*>(image), s);
 }

@@ -94,6 +94,19 @@ __device__ __forceinline__ float2 to_f2(float2 z) { return z; }
 template <typename T> __device__ __forceinline__ T from_f2(float2 v);
 template <> __device__ __forceinline__ float2 from_f2<float2>(float2 v) { return v; }
 template <> __device__ __forceinline__ double2 from_f2<double2>(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ double c_abs2d(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// Per-frame scale of 16-bit storage: the power of two 2^e with
+// maxabs / 2^e in [2^14, 2^15), so the largest component keeps the full FP16
+// mantissa and cannot overflow (FP16 max 65504), and dividing by the scale is
+// exact.  maxabs <= 0 or non-finite gives 1.
+__host__ __device__ inline float pow2_frame_scale(float maxabs) {
+  if (!(maxabs > 0.f) || !(maxabs < 3.0e38f)) return 1.f;
+  int e = 0;
+  frexpf(maxabs, &e);          // maxabs = f 2^e, f in [0.5, 1)
+  if (e < -100) e = -100;
+  return ldexpf(1.f, e - 15);
+}
 
 // ---- storage element types (FP32 complex, or 16-bit complex pairs) --------
 struct c32 { float2 v; };
@@ -109,6 +122,7 @@ template <> struct Elem<float2> {
     a = make_float2(q.x, q.y); b = make_float2(q.z, q.w);
   }
   __device__ __forceinline__ static float2 cvt(double2 z) { return make_float2((float)z.x, (float)z.y); }
+  __device__ __forceinline__ static float2 cvt(float2 z) { return z; }
 };
 template <> struct Elem<__half2> {
   static constexpr int bytes = 4;
@@ -118,7 +132,10 @@ template <> struct Elem<__half2> {
     __half2 h0 = *reinterpret_cast<__half2*>(&q.x), h1 = *reinterpret_cast<__half2*>(&q.y);
     a = __half22float2(h0); b = __half22float2(h1);
   }
-  __device__ __forceinline__ static __half2 cvt(double2 z) { return __floats2half2_rn((float)z.x, (float)z.y); }
+  __device__ __forceinline__ static __half2 cvt(double2 z) {   // one rounding from FP64
+    return __halves2half2(__double2half(z.x), __double2half(z.y));
+  }
+  __device__ __forceinline__ static __half2 cvt(float2 z) { return __floats2half2_rn(z.x, z.y); }
 };
 template <> struct Elem<__nv_bfloat162> {
   static constexpr int bytes = 4;
@@ -128,7 +145,10 @@ template <> struct Elem<__nv_bfloat162> {
     __nv_bfloat162 h0 = *reinterpret_cast<__nv_bfloat162*>(&q.x), h1 = *reinterpret_cast<__nv_bfloat162*>(&q.y);
     a = __bfloat1622float2(h0); b = __bfloat1622float2(h1);
   }
-  __device__ __forceinline__ static __nv_bfloat162 cvt(double2 z) { return __floats2bfloat162_rn((float)z.x, (float)z.y); }
+  __device__ __forceinline__ static __nv_bfloat162 cvt(double2 z) {   // one rounding from FP64
+    return __halves2bfloat162(__double2bfloat16(z.x), __double2bfloat16(z.y));
+  }
+  __device__ __forceinline__ static __nv_bfloat162 cvt(float2 z) { return __floats2bfloat162_rn(z.x, z.y); }
 };
 
 // ---- timers, barriers ------------------------------------------------------

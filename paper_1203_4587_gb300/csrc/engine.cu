@@ -37,8 +37,10 @@ cudaError_t upload(DevArena& a, T** dst, const std::vector<T>& v) {
 // Column work lists: every column of every slice, spread over `grid` CTAs by
 // longest-processing-time-first on the bytes each column streams, then each
 // CTA's list ordered by (slice, column).
-void build_work(recon_plan* const* plans, int n, int grid, std::vector<unsigned>& work, std::vector<int>& off,
-                int& work_max) {
+}  // namespace
+
+void build_col_work(recon_plan* const* plans, int n, int grid, std::vector<unsigned>& work, std::vector<int>& off,
+                    int& work_max) {
   struct Col { long long cost; int q, c; };
   std::vector<Col> cols;
   for (int q = 0; q < n; ++q) {
@@ -74,6 +76,8 @@ void build_work(recon_plan* const* plans, int n, int grid, std::vector<unsigned>
   }
   off[grid] = (int)work.size();
 }
+
+namespace {
 
 TvSlice tv_desc(recon_plan* p, int k, int K) {
   TvSlice d{};
@@ -140,6 +144,9 @@ ColSlice col_desc(recon_plan* p, int k, bool fused, int unit_off) {
   c.r_tma = ((size_t)p->Ny * sizeof(float2)) % 16 == 0 ? 1 : 0;
   c.do_obj = fused ? 1 : 0;
   c.mu = p->mu;
+  c.w_bx = -2.f;
+  c.w_xr = 1.f;
+  c.w_xx = -p->mu;
   c.stop = p->flags + FLAG_STOP;
   if (p->prior == RECON_PRIOR_TV) {
     c.base = p->b;
@@ -155,6 +162,8 @@ ColSlice col_desc(recon_plan* p, int k, bool fused, int unit_off) {
   c.fid_acc = p->trace_fid + k;
   return c;
 }
+
+}  // namespace
 
 recon_status finish_col_shape(Engine* e, recon_plan* const* plans, int n, int stages_req) {
   e->nb_max = 0;
@@ -172,8 +181,6 @@ recon_status finish_col_shape(Engine* e, recon_plan* const* plans, int n, int st
   RC(prepare_col_inverse(e->storage, smem));
   return RECON_OK;
 }
-
-}  // namespace
 
 recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
   if (n < 1) return fail(RECON_ERR_INVALID_ARG, "empty batch");
@@ -257,7 +264,7 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
   e->grid = std::max(1, p0->num_sms);
   std::vector<unsigned> work;
   std::vector<int> off;
-  build_work(plans, n, e->grid, work, off, e->work_max);
+  build_col_work(plans, n, e->grid, work, off, e->work_max);
   RC(upload(e->arena, &e->d_work, work));
   RC(upload(e->arena, &e->d_work_off, off));
   if (n == 1) {
@@ -290,14 +297,14 @@ recon_status engine_build_inverse(Engine* e, recon_plan* p) {
   std::vector<unsigned> work;
   std::vector<int> off;
   recon_plan* pl[1] = {p};
-  build_work(pl, 1, e->grid, work, off, e->work_max);
+  build_col_work(pl, 1, e->grid, work, off, e->work_max);
   RC(upload(e->arena, &e->d_work, work));
   RC(upload(e->arena, &e->d_work_off, off));
   e->d_err = p->flags + FLAG_ERR;
   return finish_col_shape(e, pl, 1, p->opts.col_stages);
 }
 
-static recon_status launch_col_set(Engine* e, int set, cudaStream_t s) {
+recon_status launch_col_set(Engine* e, int set, cudaStream_t s) {
   ColLaunch L{};
   L.slices = e->d_col + (size_t)set * e->n;
   L.nslices = e->n;
@@ -313,7 +320,7 @@ static recon_status launch_col_set(Engine* e, int set, cudaStream_t s) {
   return RECON_OK;
 }
 
-static recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s) {
+recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s) {
   TemporalLaunch L{};
   L.nslices = e->n;
   L.nblocks = e->tmp_blocks;
@@ -385,7 +392,7 @@ namespace {
 recon_status batch_enqueue(recon_batch* b, const float* const* kspace, float* const* image, cudaStream_t s) {
   recon_status st;
   for (int q = 0; q < b->eng.n; ++q)
-    if ((st = plan_prologue(b->eng.plans[q], kspace[q], s)) != RECON_OK) return st;
+    if ((st = plan_prologue(b->eng.plans[q], kspace[q], RECON_STORAGE_FP32, nullptr, s)) != RECON_OK) return st;
   if ((st = engine_iterate(&b->eng, s, false)) != RECON_OK) return st;
   for (int q = 0; q < b->eng.n; ++q) {
     recon_plan* p = b->eng.plans[q];

@@ -137,15 +137,16 @@ __device__ __forceinline__ void proc_rect(const E* __restrict__ tl, const float2
 // for each coil, z = F_v(s_c . x) (unitary, batched FFT of `ncg` coils at a
 // time) compared with the hybrid data F_h'y on the sampled rows.  By
 // Parseval on F_h this is the column's share of ||y - Hx||^2.
-template <class Bar>
+template <class YE, class Bar>
 __device__ double column_fid(const float2* xcol, int i, int t, int Nx, int Ny, int Nc, int ncg,
-                             const float2* __restrict__ sens, const float2* __restrict__ yhat,
+                             const float2* __restrict__ sens, const YE* __restrict__ yhat, const float* yscale,
                              const int* __restrict__ rows, const int* __restrict__ rowoff, const FftPlanDev& fy,
                              float scl, float2* fa, float2* fb, int tid, int nthr, Bar bar) {
   const int r0 = rowoff[t], mt = rowoff[t + 1] - r0;
   const int* rw = rows + r0;
-  const float2* yh = yhat + (size_t)r0 * Nx * Nc + (size_t)i * Nc * mt;
+  const YE* yh = yhat + (size_t)r0 * Nx * Nc + (size_t)i * Nc * mt;
   const float2* sc = sens + (size_t)i * Nc * Ny;
+  const float ys = yscale ? yscale[t] : 1.f;
   double acc = 0.0;
   for (int c0 = 0; c0 < Nc; c0 += ncg) {
     const int cg = min(ncg, Nc - c0);
@@ -158,7 +159,7 @@ __device__ double column_fid(const float2* xcol, int i, int t, int Nx, int Ny, i
     for (int idx = tid; idx < cg * mt; idx += nthr) {
       const int c = idx / mt, m = idx - c * mt;
       float2 z = c_scale(res[c * Ny + rw[m]], scl);
-      float2 d = c_sub(__ldg(yh + (size_t)(c0 + c) * mt + m), z);
+      float2 d = c_sub(c_scale(Elem<YE>::load(yh + (size_t)(c0 + c) * mt + m), ys), z);
       acc += c_abs2d(d);
     }
     bar();
@@ -436,9 +437,10 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
           c.xout[cofs + j] = x;
           if (c.do_obj) {
             const float2 r = rv[j], b = bv[j];
-            // -2 Re<b, x> + Re<x, r> - mu |x|^2
-            fid += -2.0 * ((double)b.x * x.x + (double)b.y * x.y) + ((double)x.x * r.x + (double)x.y * r.y) -
-                   (double)c.mu * ((double)x.x * x.x + (double)x.y * x.y);
+            // w_bx Re<b, x> + w_xr Re<x, r> + w_xx |x|^2
+            fid += (double)c.w_bx * ((double)b.x * x.x + (double)b.y * x.y) +
+                   (double)c.w_xr * ((double)x.x * r.x + (double)x.y * r.y) +
+                   (double)c.w_xx * ((double)x.x * x.x + (double)x.y * x.y);
           }
         }
       }
@@ -676,7 +678,7 @@ int tv_tile_px(int Nt_max) { return Nt_max <= 96 ? 64 : 32; }
 cudaError_t prepare_tv_temporal(int Nt_max) {
   static size_t configured = 0;
   const size_t smem = 4 * (size_t)Nt_max * tv_tile_px(Nt_max) * sizeof(float2);
-  if (smem > 48 * 1024 && smem > configured) {
+  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
     cudaError_t e = cudaFuncSetAttribute(k_tv_temporal<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_tv_temporal<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -768,7 +770,7 @@ __global__ void __launch_bounds__(256) k_dft_temporal(TemporalLaunch L) {
 cudaError_t prepare_dft_temporal(int Nt_max) {
   static size_t configured = 0;
   const size_t smem = 2 * (size_t)Nt_max * kDftPix * sizeof(float2);
-  if (smem > 48 * 1024 && smem > configured) {
+  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
     cudaError_t e = cudaFuncSetAttribute(k_dft_temporal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
@@ -787,6 +789,7 @@ cudaError_t launch_dft_temporal(const TemporalLaunch& p, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // ||y - H x||^2 of a whole field, one block per column.
 // ---------------------------------------------------------------------------
+template <class YE>
 __global__ void __launch_bounds__(256) k_objective(ObjParams P) {
   extern __shared__ float2 sm_obj[];
   __shared__ double red[32];
@@ -798,22 +801,32 @@ __global__ void __launch_bounds__(256) k_objective(ObjParams P) {
   float2* fb = fa + (size_t)P.ncg * P.Ny;
   for (int j = tid; j < P.Ny; j += blockDim.x) xc[j] = P.x[(size_t)col * P.Ny + j];
   __syncthreads();
-  const double f = column_fid(xc, i, t, P.Nx, P.Ny, P.Nc, P.ncg, P.sens, P.yhat, P.rows, P.rowoff, P.fy,
-                              rsqrtf((float)P.Ny), fa, fb, tid, blockDim.x, BlockBar());
+  const double f = column_fid(xc, i, t, P.Nx, P.Ny, P.Nc, P.ncg, P.sens, static_cast<const YE*>(P.yhat), P.yscale,
+                              P.rows, P.rowoff, P.fy, rsqrtf((float)P.Ny), fa, fb, tid, blockDim.x, BlockBar());
   const double s = group_sum(f, red, tid, blockDim.x, BlockBar());
   if (tid == 0) atomicAdd(P.fid_acc, s);
 }
 
-cudaError_t launch_objective(const ObjParams& p, cudaStream_t s) {
+template <class YE>
+static cudaError_t launch_objective_t(const ObjParams& p, cudaStream_t s) {
   const size_t smem = ((size_t)p.Ny + 2 * (size_t)p.ncg * p.Ny) * sizeof(float2);
   static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_objective, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
+    cudaError_t e = cudaFuncSetAttribute(k_objective<YE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  k_objective<<<p.Nx * p.Nt, 256, smem, s>>>(p); note_launch();
+  k_objective<YE><<<p.Nx * p.Nt, 256, smem, s>>>(p); note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_objective(const ObjParams& p, cudaStream_t s) {
+  switch (p.ystorage) {
+    case 0: return launch_objective_t<float2>(p, s);
+    case 1: return launch_objective_t<__half2>(p, s);
+    case 2: return launch_objective_t<__nv_bfloat162>(p, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -68,10 +68,13 @@ struct ColSlice {            // data-consistency inverse x = A r of one slice
   float2* xout;
   float coef;
   float mu;
-  // data term of J for the new x, with (mu I + H'H) x = r:
+  // dot products of the new x accumulated into *fid_acc:
+  //   w_bx Re<bsrc, x> + w_xr Re<x, r> + w_xx ||x||^2
+  // The data term of J uses w = (-2, 1, -mu), since with (mu I + H'H) x = r
   //   ||y - Hx||^2 = ||y||^2 - 2 Re<H'y, x> + Re<x, r> - mu ||x||^2
-  // the kernel adds the last three terms to *fid_acc (||y||^2 comes from the
-  // prologue).
+  // (||y||^2 comes from the prologue); the adjoint pass uses w_bx = -1 for
+  // the dA/dmu term of the mu gradient.
+  float w_bx, w_xr, w_xx;
   double* fid_acc;
   const int* stop;           // the slice's stop flag: its columns are skipped when set
 };
@@ -134,6 +137,35 @@ struct TemporalLaunch {      // one launch over the tiles of several slices
   int tile_px;               // pixels per block (TV)
 };
 
+struct TvBwdSlice {          // reverse of one Algorithm 2 step (see grad.cu), one slice
+  int Nt;
+  long long npix;
+  // adjoints of the step's outputs (x', m', d1', d2') and r_bar = A (x_bar' + d2_bar')
+  const float2* xb;
+  const float2* mb;
+  const float2* d1b;         // null at the last step (zero)
+  const float2* d2b;
+  const float2* rb;
+  // forward state of the step's input (x, m, d1, p with d2 = x - p) and m'
+  const float2* x0;
+  const float2* m0;
+  const float2* d10;         // null at the first step
+  const float2* p0;
+  const float2* m1;
+  // adjoints of the step's inputs
+  float2* xb_out;
+  float2* mb_out;
+  float2* d1b_out;
+  float2* d2b_out;
+  float2* bbar;              // += r_bar (and x_bar + m_bar of the initial state when `first`)
+  float tau1, rho, mu;
+  const float* thomas;
+  int first;                 // step 1: its input state is x = m = H'y
+  double* mu_acc;            // += Re<r_bar, m' - d2>
+  double* tau_acc;           // += dL/dtau1
+  int tile0;
+};
+
 struct FinSlice {            // J(k), Delta(k) and the stop flag of one slice
   const double* fid;
   const double* prior;
@@ -148,7 +180,9 @@ struct ObjParams {           // ||y - H x||^2 of a given field (no inverse)
   int Nx, Ny, Nt, Nc, ncg;
   const float2* x;           // [Nt][Nx][Ny]
   const float2* sens;
-  const float2* yhat;
+  const void* yhat;          // hybrid data: complex64, or 16-bit pairs times yscale[t]
+  int ystorage;              // recon_storage of yhat
+  const float* yscale;       // [Nt] (16-bit yhat only)
   const int* rows;
   const int* rowoff;
   FftPlanDev fy;
@@ -178,21 +212,31 @@ cudaError_t launch_objective(const ObjParams& p, cudaStream_t s);
 cudaError_t launch_finalize(const FinSlice* fins, int nslices, int k, cudaStream_t s);
 
 // prologue / operators
-cudaError_t launch_hybrid_rows(const void* kspace, int kdtype, const float* kscale, float2* yhat, const int* rows,
-                               const int* rowoff, int maxm, int Nx, int Ny, int Nt, int Nc, FftPlanDev fx,
-                               cudaStream_t s);
+// yhat = F_h' y (FP32 butterflies), k-space complex64 or 16-bit pairs
+// (kstorage = recon_storage) times kscale[t] (may be null); ymax[t] receives
+// the largest |component| of frame t's yhat (float bits, may be null).
+cudaError_t launch_hybrid_rows(const void* kspace, int kstorage, const float* kscale, float2* yhat, double* yy,
+                               unsigned* ymax, const int* rows, const int* rowoff, int maxm, int Nx, int Ny, int Nt,
+                               int Nc, FftPlanDev fx, cudaStream_t s);
+// b = H'y from yhat (FP32); ystorage 1/2 also writes the 16-bit copy ylp of
+// yhat with per-frame power-of-two scales yscale[t] from ymax.
 cudaError_t launch_adjoint_combine(const float2* yhat, const float2* sens, float2* b, const int* rows,
-                                   const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, cudaStream_t s);
+                                   const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, int ystorage,
+                                   void* ylp, const unsigned* ymax, float* yscale, cudaStream_t s);
 // FP64 H'y prologue: the solution of the iterations is ~100x more sensitive to
 // errors in H'y than to rounding elsewhere, so H'y is formed in FP64 and
 // rounded once.  yhat32 receives the FP32 rounding of the hybrid data; *yy
 // accumulates ||y||^2 over the sampled entries (may be null).
-cudaError_t launch_hybrid_rows64(const float2* kspace, double2* yhat64, float2* yhat32, double* yy, const int* rows,
-                                 const int* rowoff, int maxm, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fx,
-                                 cudaStream_t s);
+cudaError_t launch_hybrid_rows64(const void* kspace, int kstorage, const float* kscale, double2* yhat64,
+                                 float2* yhat32, double* yy, const int* rows, const int* rowoff, int maxm, int Nx,
+                                 int Ny, int Nt, int Nc, FftPlanDev64 fx, cudaStream_t s);
 cudaError_t launch_adjoint_combine64(const double2* yhat64, const float2* sens, float2* b, const int* rows,
                                      const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fy,
                                      cudaStream_t s);
+// 16-bit k-space (storage 1 = FP16, 2 = BF16 pairs) with per-frame
+// power-of-two scales: out = k / frame_scale[t], one rounding.
+cudaError_t launch_quantize_kspace(const float2* k, long long per_frame, int Nt, int storage, void* out,
+                                  float* frame_scale, cudaStream_t s);
 cudaError_t launch_forward_cols(const float2* x, const float2* sens, float2* zhat, const int* rows,
                                 const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, cudaStream_t s);
 cudaError_t launch_forward_rows(const float2* zhat, float2* kspace, const int* rows, const int* rowoff, int maxm,

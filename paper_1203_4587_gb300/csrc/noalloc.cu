@@ -186,7 +186,7 @@ extern "C" recon_status recon_gram_inverse_noalloc(int Ny, int Nc, int nblk, con
   const int per = (int)((kScratchBytes - kScratchStatusBytes) / ws);
   const int grid = nblk < per ? nblk : per;
   e = cudaMemsetAsync(base, 0, sizeof(int), s);  // status word of this call
-  if (e == cudaSuccess && smem > 48 * 1024)
+  if (e == cudaSuccess)   // always: static shared memory counts toward the 48 KB default
     e = cudaFuncSetAttribute(k_gram_inverse_static, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) {
     k_gram_inverse_static<<<grid, kNoAllocThreads, smem, s>>>(mask, reinterpret_cast<const float2*>(sens), Ny, Nc,

@@ -10,6 +10,9 @@
 //   k_forward_cols    zhat = M F_v (s_c . x), per column (sampled rows only)
 //   k_forward_rows    y = F_h zhat on the sampled rows
 //   k_transpose       layout changes between [..][Ny][Nx] and [..][Nx][Ny]
+#include <algorithm>
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace recon {
@@ -24,11 +27,16 @@ static int row_group(int Nx) {
   return g;
 }
 
-// yhat = F_h' y on the sampled rows.  T = double2 computes in FP64 and also
-// writes the FP32 rounding (yhat32) used by the objective.
-template <typename T>
-__global__ void __launch_bounds__(256) k_hybrid_rows(const float2* __restrict__ ksp, T* __restrict__ yhat,
-                                                     float2* __restrict__ yhat32, double* __restrict__ yy,
+// yhat = F_h' y on the sampled rows.  The k-space arrives as complex64 or as
+// 16-bit pairs KIn with a per-frame scale (value = stored * kscale[t]); it is
+// widened exactly and the FFT runs in T (double2: FP64, with the FP32
+// rounding also written to yhat32 for the objective; float2: FP32).  *yy
+// accumulates ||y||^2 over the sampled entries and ymax[t] the largest
+// |component| of frame t's output (float bits; both optional).
+template <typename T, typename KIn>
+__global__ void __launch_bounds__(256) k_hybrid_rows(const KIn* __restrict__ ksp, const float* __restrict__ kscale,
+                                                     T* __restrict__ yhat, float2* __restrict__ yhat32,
+                                                     double* __restrict__ yy, unsigned* __restrict__ ymax,
                                                      const int* __restrict__ rows,
                                                      const int* __restrict__ rowoff, int Nx, int Ny, int Nt, int Nc,
                                                      int G, FftPlanT<T> fx, double scl) {
@@ -43,13 +51,15 @@ __global__ void __launch_bounds__(256) k_hybrid_rows(const float2* __restrict__ 
   T* A = sm_rows;
   T* B = sm_rows + (size_t)G * ss;
   const int tid = threadIdx.x, nth = blockDim.x;
+  const float ks = kscale ? kscale[t] : 1.f;
   double e2 = 0.0;  // ||y||^2 over these sampled rows
   for (int idx = tid; idx < g * Nx; idx += nth) {
     const int gg = idx / Nx, kx = idx - gg * Nx;
     const int row = rows[r0 + m0 + gg];
-    const float2 v = ksp[(((size_t)t * Nc + c) * Ny + row) * Nx + kx];
+    T v = from_f2<T>(Elem<KIn>::load(ksp + (((size_t)t * Nc + c) * Ny + row) * Nx + kx));
+    if (kscale) v = c_scale(v, ks);
     e2 += c_abs2d(v);
-    A[gg * ss + kx] = from_f2<T>(v);
+    A[gg * ss + kx] = v;
   }
   __syncthreads();
   if (yy) {
@@ -59,59 +69,84 @@ __global__ void __launch_bounds__(256) k_hybrid_rows(const float2* __restrict__ 
   const BlockBar bar;
   T* R = fft_run(A, B, g, ss, 1, fx, true, tid, nth, bar);
   const size_t base = (size_t)r0 * Nx * Nc;
+  float mx = 0.f;
   for (int idx = tid; idx < g * Nx; idx += nth) {
     const int i = idx / g, gg = idx - i * g;
     const size_t o = base + ((size_t)i * Nc + c) * mt + m0 + gg;
     const T v = c_scale(R[gg * ss + i], scl);
     yhat[o] = v;
     if (yhat32) yhat32[o] = to_f2(v);
+    const float2 f = to_f2(v);
+    mx = fmaxf(mx, fmaxf(fabsf(f.x), fabsf(f.y)));
+  }
+  if (ymax) {
+    const unsigned w = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));   // non-negative: bits order as values
+    if ((tid & 31) == 0) atomicMax(ymax + t, w);
   }
 }
 
-template <typename T>
-static cudaError_t launch_rows_t(const float2* ksp, T* yhat, float2* yhat32, double* yy, const int* rows,
-                                 const int* rowoff, int maxm, int Nx, int Ny, int Nt, int Nc, const FftPlanT<T>& fx,
-                                 cudaStream_t s) {
+template <typename T, typename KIn>
+static cudaError_t launch_rows_t(const KIn* ksp, const float* kscale, T* yhat, float2* yhat32, double* yy,
+                                 unsigned* ymax, const int* rows, const int* rowoff, int maxm, int Nx, int Ny, int Nt,
+                                 int Nc, const FftPlanT<T>& fx, cudaStream_t s) {
   if (maxm <= 0) return cudaSuccess;
   const int G = row_group<T>(Nx);
   const size_t smem = 2 * (size_t)G * (Nx + 1) * sizeof(T);
   static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_hybrid_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
+    cudaError_t e = cudaFuncSetAttribute(k_hybrid_rows<T, KIn>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
   dim3 grid((maxm + G - 1) / G, Nc, Nt);
-  k_hybrid_rows<T><<<grid, 256, smem, s>>>(ksp, yhat, yhat32, yy, rows, rowoff, Nx, Ny, Nt, Nc, G, fx,
-                                           1.0 / sqrt((double)Nx)); note_launch();
+  k_hybrid_rows<T, KIn><<<grid, 256, smem, s>>>(ksp, kscale, yhat, yhat32, yy, ymax, rows, rowoff, Nx, Ny, Nt, Nc,
+                                                G, fx, 1.0 / sqrt((double)Nx)); note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_hybrid_rows(const void* kspace, int kdtype, const float* kscale, float2* yhat, const int* rows,
-                               const int* rowoff, int maxm, int Nx, int Ny, int Nt, int Nc, FftPlanDev fx,
-                               cudaStream_t s) {
-  (void)kscale;
-  if (kdtype != 0) return cudaErrorInvalidValue;
-  return launch_rows_t<float2>(static_cast<const float2*>(kspace), yhat, nullptr, nullptr, rows, rowoff, maxm, Nx,
-                               Ny, Nt, Nc, fx, s);
+template <typename T, typename Plan>
+static cudaError_t rows_dispatch(const void* kspace, int kstorage, const float* kscale, T* yhat, float2* yhat32,
+                                 double* yy, unsigned* ymax, const int* rows, const int* rowoff, int maxm, int Nx,
+                                 int Ny, int Nt, int Nc, const Plan& fx, cudaStream_t s) {
+  switch (kstorage) {
+    case 0: return launch_rows_t<T, float2>(static_cast<const float2*>(kspace), kscale, yhat, yhat32, yy, ymax,
+                                            rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, s);
+    case 1: return launch_rows_t<T, __half2>(static_cast<const __half2*>(kspace), kscale, yhat, yhat32, yy, ymax,
+                                             rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, s);
+    case 2: return launch_rows_t<T, __nv_bfloat162>(static_cast<const __nv_bfloat162*>(kspace), kscale, yhat,
+                                                    yhat32, yy, ymax, rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-cudaError_t launch_hybrid_rows64(const float2* kspace, double2* yhat64, float2* yhat32, double* yy, const int* rows,
-                                 const int* rowoff, int maxm, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fx,
-                                 cudaStream_t s) {
-  return launch_rows_t<double2>(kspace, yhat64, yhat32, yy, rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, s);
+cudaError_t launch_hybrid_rows(const void* kspace, int kstorage, const float* kscale, float2* yhat, double* yy,
+                               unsigned* ymax, const int* rows, const int* rowoff, int maxm, int Nx, int Ny, int Nt,
+                               int Nc, FftPlanDev fx, cudaStream_t s) {
+  return rows_dispatch<float2>(kspace, kstorage, kscale, yhat, nullptr, yy, ymax, rows, rowoff, maxm, Nx, Ny, Nt,
+                               Nc, fx, s);
+}
+
+cudaError_t launch_hybrid_rows64(const void* kspace, int kstorage, const float* kscale, double2* yhat64,
+                                 float2* yhat32, double* yy, const int* rows, const int* rowoff, int maxm, int Nx,
+                                 int Ny, int Nt, int Nc, FftPlanDev64 fx, cudaStream_t s) {
+  return rows_dispatch<double2>(kspace, kstorage, kscale, yhat64, yhat32, yy, nullptr, rows, rowoff, maxm, Nx, Ny,
+                                Nt, Nc, fx, s);
 }
 
 constexpr int kCoilGroupMax = 8;
 
 // b = sum_c conj(s_c) . F_v'(zero-filled yhat_c), accumulated in T and rounded
-// once to FP32.
-template <typename T>
+// once to FP32.  With YS != void, also writes ylp = yhat / scale_t in 16 bits
+// (the stored coil data of the objective), scale_t = pow2_frame_scale(ymax[t]),
+// and yscale[t] = scale_t.
+template <typename T, typename YS>
 __global__ void __launch_bounds__(256) k_adjoint_combine(const T* __restrict__ yhat,
                                                          const float2* __restrict__ sens, float2* __restrict__ b,
                                                          const int* __restrict__ rows,
                                                          const int* __restrict__ rowoff, int Nx, int Ny, int Nt,
-                                                         int Nc, int ncg, FftPlanT<T> fy, double scl) {
+                                                         int Nc, int ncg, FftPlanT<T> fy, double scl, YS* ylp,
+                                                         const unsigned* __restrict__ ymax, float* yscale) {
   extern __shared__ __align__(16) unsigned char sm_adj_raw[];
   T* sm_adj = reinterpret_cast<T*>(sm_adj_raw);
   const int i = blockIdx.x, t = blockIdx.y;
@@ -119,6 +154,12 @@ __global__ void __launch_bounds__(256) k_adjoint_combine(const T* __restrict__ y
   const int r0 = rowoff[t], mt = rowoff[t + 1] - r0;
   const T* yh = yhat + (size_t)r0 * Nx * Nc + (size_t)i * Nc * mt;
   const float2* sc = sens + (size_t)i * Nc * Ny;
+  float yinv = 1.f;
+  if constexpr (!std::is_same<YS, void>::value) {
+    const float ysc = pow2_frame_scale(__uint_as_float(ymax[t]));
+    yinv = 1.f / ysc;   // exact: a power of two
+    if (i == 0 && tid == 0) yscale[t] = ysc;
+  }
   T* A = sm_adj;
   T* B = sm_adj + (size_t)ncg * Ny;
   T acc[4];
@@ -131,7 +172,13 @@ __global__ void __launch_bounds__(256) k_adjoint_combine(const T* __restrict__ y
     __syncthreads();
     for (int idx = tid; idx < cg * mt; idx += nth) {
       const int c = idx / mt, m = idx - c * mt;
-      A[c * Ny + rows[r0 + m]] = yh[(size_t)(c0 + c) * mt + m];
+      const T v = yh[(size_t)(c0 + c) * mt + m];
+      A[c * Ny + rows[r0 + m]] = v;
+      if constexpr (!std::is_same<YS, void>::value) {
+        const float2 f = to_f2(v);
+        ylp[(size_t)r0 * Nx * Nc + (size_t)i * Nc * mt + (size_t)(c0 + c) * mt + m] =
+            Elem<YS>::cvt(make_float2(f.x * yinv, f.y * yinv));
+      }
     }
     __syncthreads();
     T* R = fft_run(A, B, cg, Ny, 1, fy, true, tid, nth, bar);
@@ -158,33 +205,96 @@ static int coil_group(int Nc, int Ny) {
   return g < Nc ? g : Nc;
 }
 
-template <typename T>
+template <typename T, typename YS>
 static cudaError_t launch_combine_t(const T* yhat, const float2* sens, float2* b, const int* rows, const int* rowoff,
-                                    int Nx, int Ny, int Nt, int Nc, const FftPlanT<T>& fy, cudaStream_t s) {
+                                    int Nx, int Ny, int Nt, int Nc, const FftPlanT<T>& fy, YS* ylp,
+                                    const unsigned* ymax, float* yscale, cudaStream_t s) {
   if (Ny > 1024) return cudaErrorInvalidValue;
   const int ncg = coil_group<T>(Nc, Ny);
   const size_t smem = 2 * (size_t)ncg * Ny * sizeof(T);
   static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_adjoint_combine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
+    cudaError_t e = cudaFuncSetAttribute(k_adjoint_combine<T, YS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  k_adjoint_combine<T><<<dim3(Nx, Nt), 256, smem, s>>>(yhat, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, ncg, fy,
-                                                       1.0 / sqrt((double)Ny)); note_launch();
+  k_adjoint_combine<T, YS><<<dim3(Nx, Nt), 256, smem, s>>>(yhat, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, ncg, fy,
+                                                           1.0 / sqrt((double)Ny), ylp, ymax, yscale);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_combine(const float2* yhat, const float2* sens, float2* b, const int* rows,
-                                   const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, cudaStream_t s) {
-  return launch_combine_t<float2>(yhat, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, fy, s);
+                                   const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, int ystorage,
+                                   void* ylp, const unsigned* ymax, float* yscale, cudaStream_t s) {
+  switch (ystorage) {
+    case 0: return launch_combine_t<float2, void>(yhat, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, fy, nullptr, nullptr,
+                                                  nullptr, s);
+    case 1: return launch_combine_t<float2, __half2>(yhat, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, fy,
+                                                     static_cast<__half2*>(ylp), ymax, yscale, s);
+    case 2: return launch_combine_t<float2, __nv_bfloat162>(yhat, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, fy,
+                                                            static_cast<__nv_bfloat162*>(ylp), ymax, yscale, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_adjoint_combine64(const double2* yhat64, const float2* sens, float2* b, const int* rows,
                                      const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fy,
                                      cudaStream_t s) {
-  return launch_combine_t<double2>(yhat64, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, fy, s);
+  return launch_combine_t<double2, void>(yhat64, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, fy, nullptr, nullptr,
+                                         nullptr, s);
+}
+
+// ---- 16-bit k-space with per-frame scales ----------------------------------
+// Three launches: the largest |component| of every frame (float bits into
+// the scale array), the quantisation q = k / scale_t (one rounding: the
+// scale is a power of two), and the bits replaced by the scale values.
+__global__ void k_frame_absmax(const float2* __restrict__ k, long long per_frame, unsigned* mx) {
+  const int t = blockIdx.y;
+  const float2* kf = k + (size_t)t * per_frame;
+  float m = 0.f;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < per_frame;
+       e += (long long)gridDim.x * blockDim.x) {
+    const float2 v = kf[e];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  const unsigned w = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+  if ((threadIdx.x & 31) == 0) atomicMax(mx + t, w);
+}
+
+template <typename E>
+__global__ void k_quantize_frames(const float2* __restrict__ k, long long per_frame, const unsigned* __restrict__ mx,
+                                  E* __restrict__ out) {
+  const int t = blockIdx.y;
+  const float inv = 1.f / pow2_frame_scale(__uint_as_float(mx[t]));
+  const size_t o = (size_t)t * per_frame;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < per_frame;
+       e += (long long)gridDim.x * blockDim.x) {
+    const float2 v = k[o + e];
+    out[o + e] = Elem<E>::cvt(make_float2(v.x * inv, v.y * inv));
+  }
+}
+
+__global__ void k_bits_to_scale(float* scale, int Nt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < Nt) scale[t] = pow2_frame_scale(__uint_as_float(reinterpret_cast<unsigned*>(scale)[t]));
+}
+
+cudaError_t launch_quantize_kspace(const float2* k, long long per_frame, int Nt, int storage, void* out,
+                                   float* frame_scale, cudaStream_t s) {
+  if (storage != 1 && storage != 2) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(frame_scale, 0, (size_t)Nt * sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  const int bx = (int)std::min<long long>(64, (per_frame + 255) / 256);
+  const dim3 grid(std::max(bx, 1), Nt);
+  unsigned* bits = reinterpret_cast<unsigned*>(frame_scale);
+  k_frame_absmax<<<grid, 256, 0, s>>>(k, per_frame, bits); note_launch();
+  if (storage == 1) k_quantize_frames<__half2><<<grid, 256, 0, s>>>(k, per_frame, bits, static_cast<__half2*>(out));
+  else k_quantize_frames<__nv_bfloat162><<<grid, 256, 0, s>>>(k, per_frame, bits, static_cast<__nv_bfloat162*>(out));
+  note_launch();
+  k_bits_to_scale<<<(Nt + 127) / 128, 128, 0, s>>>(frame_scale, Nt); note_launch();
+  return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(256) k_forward_cols(const float2* __restrict__ x, const float2* __restrict__ sens,
@@ -224,7 +334,7 @@ cudaError_t launch_forward_cols(const float2* x, const float2* sens, float2* zha
   const int ncg = coil_group<float2>(Nc, Ny);
   const size_t smem = ((size_t)Ny + 2 * (size_t)ncg * Ny) * sizeof(float2);
   static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
+  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
     cudaError_t e = cudaFuncSetAttribute(k_forward_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
@@ -266,7 +376,7 @@ cudaError_t launch_forward_rows(const float2* zhat, float2* kspace, const int* r
   if (maxm <= 0) return cudaSuccess;
   const size_t smem = 2 * (size_t)kRowGroup * (Nx + 1) * sizeof(float2);
   static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
+  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
     cudaError_t e = cudaFuncSetAttribute(k_forward_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;

@@ -69,7 +69,10 @@ struct recon_plan {
   double2 *tw64_x = nullptr, *tw64_y = nullptr;
   double2* yhat64 = nullptr;           // FP64 hybrid data of the prologue
   float* thomas = nullptr;
-  float2* yhat = nullptr;
+  float2* yhat = nullptr;               // FP32 hybrid data (FP32 storage)
+  void* yhat_lp = nullptr;             // 16-bit storage: hybrid data / yscale[t], 16-bit pairs
+  unsigned* ymax = nullptr;            // [Nt] largest |component| of the hybrid data (float bits)
+  float* yscale = nullptr;             // [Nt] power-of-two frame scales of yhat_lp
   float2* b = nullptr;
   float2* s0[2] = {nullptr, nullptr};  // TV: m;  DFT: u
   float2* s1[2] = {nullptr, nullptr};  // TV: d1
@@ -135,6 +138,11 @@ recon_status cuda_fail(cudaError_t e, const char* where);
   } while (0)
 
 // engine.cu
+void build_col_work(recon_plan* const* plans, int n, int grid, std::vector<unsigned>& work, std::vector<int>& off,
+                    int& work_max);
+recon_status finish_col_shape(Engine* e, recon_plan* const* plans, int n, int stages_req);
+recon_status launch_col_set(Engine* e, int set, cudaStream_t s);   // descriptor set `set` of d_col
+recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s);   // descriptor set `set` of d_tmp
 recon_status engine_build(Engine* e, recon_plan* const* plans, int n);
 recon_status engine_build_inverse(Engine* e, recon_plan* p);   // tmp_a -> tmp_b, no objective
 // Resets traces/flags, J(0), K iterations and the final prior term of every
@@ -142,11 +150,13 @@ recon_status engine_build_inverse(Engine* e, recon_plan* p);   // tmp_a -> tmp_b
 recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile);
 recon_status engine_apply_inverse(Engine* e, cudaStream_t s);
 const float2* plan_result(const recon_plan* p);   // image (internal layout) after K iterations
-recon_status plan_prologue(recon_plan* p, const float* kspace, cudaStream_t s);
+// H'y (into p->b), the hybrid data kept for J(k) and ||y||^2.  kspace is
+// complex64 (kstorage 0) or 16-bit pairs times kscale[t] (kscale may be null).
+recon_status plan_prologue(recon_plan* p, const void* kspace, int kstorage, const float* kscale, cudaStream_t s);
 recon_status plan_to_user(recon_plan* p, const float2* in, float2* out, cudaStream_t s);
 recon_status plan_to_internal(recon_plan* p, const float2* in, float2* out, cudaStream_t s);
-recon_status plan_adjoint64(recon_plan* p, const float* kspace, float2* yhat32, float2* b, double* yy,
-                            cudaStream_t s);
+recon_status plan_adjoint64(recon_plan* p, const void* kspace, int kstorage, const float* kscale, float2* yhat32,
+                            float2* b, double* yy, cudaStream_t s);
 recon_status plan_objective(recon_plan* p, const float2* x, double* acc, cudaStream_t s);
 recon_status plan_fill_info(recon_plan* p, recon_info* info, cudaStream_t s);
 
