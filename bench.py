@@ -21,6 +21,9 @@ Extra keys on the JSON line:
   precision     384x384x48 frames x16 coils, R=6: FP32 / FP16 / BF16 storage
                 (inverses and hybrid coil data; 16-bit k-space for the 16-bit
                 runs), iters/s and the inverse kernel's HBM fraction each
+  library_comparison  the same TV iteration written with stock PyTorch ops
+                (cuFFT for the objective, cuBLAS batched matmul with dense
+                per-column inverses from torch.linalg.inv), timed only
   grad          differentiable unrolled Algorithm 2: forward and backward
                 (dL/dy, dL/dlambda, dL/dmu) of 4 slices 192x192x24x8,
                 20 iterations, checkpoints every 5
@@ -68,6 +71,7 @@ def parse():
     ap.add_argument("--batched-slices", type=int, default=64)
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-comparison", action="store_true")
     ap.add_argument("--grad-only", action="store_true",
                     help="only the differentiable-form measurement (one JSON line with its numbers)")
     return ap.parse_args()
@@ -337,6 +341,83 @@ def measure_precision(steps=3):
     return out
 
 
+def measure_library_comparison(case, iters=10):
+    """Algorithm 2 with stock PyTorch CUDA ops on the cardiac workload: the
+    objective through cuFFT (torch.fft), the inverse as a cuBLAS batched
+    matrix-vector product with dense per-column inverses (torch.linalg.inv of
+    mu I + C_t (.) K_i), the m-update as a dense (rho I + D'D)^{-1} product.
+    Timed only: the comparison arm, not part of the library."""
+    import numpy as np
+    import torch
+    dev = "cuda"
+    w = WORKLOAD
+    Nt, Ny, Nx, Nc = w["Nt"], w["Ny"], w["Nx"], w["Nc"]
+    lam, mu, rho = w["lam"], w["mu"], w["rho"]
+    t0 = time.perf_counter()
+    sens = torch.from_numpy(case.sens.astype(np.complex64)).to(dev)           # [Nc, Ny, Nx]
+    mask = torch.from_numpy(case.mask).to(dev)                                # [Nt, Ny]
+    y = torch.from_numpy(case.kspace.astype(np.complex64)).to(dev) * mask[:, None, :, None]
+    # per-column Gram blocks and inverses
+    Kc = torch.einsum("cji,cki->ijk", sens.conj(), sens)                      # [Nx, Ny, Ny]
+    P = mask.to(torch.complex64)
+    Fv = torch.fft.fft(torch.eye(Ny, dtype=torch.complex64, device=dev), norm="ortho", dim=0)
+    Ct = torch.einsum("aj,ta,ak->tjk", Fv.conj(), P, Fv)                       # F_v' P_t F_v  [Nt, Ny, Ny]
+    A = torch.empty((Nt, Nx, Ny, Ny), dtype=torch.complex64, device=dev)
+    eye = torch.eye(Ny, dtype=torch.complex64, device=dev)
+    for t in range(Nt):
+        A[t] = torch.linalg.inv(mu * eye + Ct[t][None] * Kc)
+    D = torch.zeros((Nt - 1, Nt), dtype=torch.float32, device=dev)
+    idx = torch.arange(Nt - 1, device=dev)
+    D[idx, idx] = -1.0
+    D[idx, idx + 1] = 1.0
+    Minv = torch.linalg.inv(rho * torch.eye(Nt, device=dev) + D.T @ D).to(torch.complex64)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+
+    def Hop(x):   # [Nt, Ny, Nx] -> [Nt, Nc, Ny, Nx]
+        return torch.fft.fft2(sens[None] * x[:, None], norm="ortho") * mask[:, None, :, None]
+
+    b = (sens.conj()[None] * torch.fft.ifft2(y, norm="ortho")).sum(1)        # H'y
+    tau = lam * rho / (2 * mu)
+
+    def step(st):
+        x, m, d1, d2 = st
+        a = m[1:] - m[:-1] + d1
+        mag = a.abs()
+        v = torch.where(mag > tau, a * (1 - tau / mag.clamp_min(1e-30)), torch.zeros_like(a))
+        u = v - d1
+        rhs = rho * (x + d2)
+        rhs[:-1] -= u
+        rhs[1:] += u
+        mn = torch.tensordot(Minv, rhs, dims=([1], [0]))
+        r = b + mu * (mn - d2)
+        xn = torch.matmul(A, r.permute(0, 2, 1).unsqueeze(-1)).squeeze(-1).permute(0, 2, 1)
+        d1 = d1 - v + (mn[1:] - mn[:-1])
+        d2 = d2 - mn + xn
+        J = torch.sum(torch.abs(y - Hop(xn)) ** 2) + lam * torch.sum(torch.abs(xn[1:] - xn[:-1]))
+        return (xn, mn, d1, d2), J
+
+    st = (b.clone(), b.clone(), torch.zeros((Nt - 1, Ny, Nx), dtype=torch.complex64, device=dev), torch.zeros_like(b))
+    for _ in range(2):
+        st, J = step(st)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        st, J = step(st)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    out = {"iters_per_s": 1e3 / ms, "ms_per_iter": ms, "setup_s": setup_s,
+           "dense_inverse_bytes": int(A.numel() * 8),
+           "note": ("cardiac TV iteration in stock PyTorch: dense per-column inverses (cuBLAS batched matvec), "
+                    "dense m-update, J through cuFFT every iteration; timed only")}
+    del A, Kc, Ct
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_grad(storage, steps=5):
     """Forward and backward of unrolled Algorithm 2 over a batch of 4 slices."""
     import numpy as np
@@ -538,6 +619,13 @@ def run_native(args):
             line["batched"] = measure_batched(args.batched_slices, args.storage)
         except Exception as e:  # report, never fake
             line["batched"] = {"error": str(e)[:300]}
+
+    if not args.no_comparison and rank == 0:
+        torch.cuda.empty_cache()
+        try:
+            line["library_comparison"] = measure_library_comparison(case)
+        except Exception as e:  # report, never fake
+            line["library_comparison"] = {"error": str(e)[:300]}
 
     if not args.no_precision and rank == 0:
         torch.cuda.empty_cache()

@@ -256,6 +256,33 @@ recon_status recon_solve_kspace(recon_plan* plan, const recon_kspace* kspace, fl
 recon_status recon_quantize_kspace(int Nx, int Ny, int Nt, int Nc, const float* kspace, int storage, void* out,
                                    float* frame_scale, void* stream);
 
+/* ---- launch-shape autotuner ---------------------------------------------------
+ * Times every candidate tile shape of the kernels below on the plan's (or
+ * batch's) own device buffers with CUDA events and keeps the fastest.  The
+ * buffers are overwritten with a pattern (a later solve re-initialises every
+ * state it reads).  Results are cached per problem shape for the process, so
+ * a plan of a shape already tuned takes the cached choice at once.  Not part
+ * of the paper; it only picks launch shapes, never the arithmetic. */
+typedef struct {
+  int temporal_tile_px;   /* pixels per block of the temporal kernel (TV 32/64/128, DFT 16..128) */
+  int col_stages;         /* ring depth of the column-inverse kernel */
+  int rows_per_block;     /* k-space rows per block of the prologue's row FFTs (1..8) */
+  int combine_coils;      /* coils per pass of the prologue's column FFTs and coil combine (1..8) */
+  int objective_coils;    /* coils per pass of the explicit objective; 0 when the plan does not use it */
+  float temporal_ms, col_ms, rows_ms, combine_ms, objective_ms;   /* time per launch of the chosen shape */
+  int from_cache;         /* 1 when the plan took a cached result */
+} recon_tuning;
+
+/* Tunes every kernel of a plan (synchronises `stream`).  out may be NULL.
+ * Errors: INVALID_ARG, CUDA, OOM. */
+recon_status recon_autotune(recon_plan* plan, recon_tuning* out, void* stream);
+
+/* Tunes the batch's temporal tile width and ring depth over all of its slices
+ * (synchronises `stream`; drops a captured graph, which is re-captured at the
+ * next recon_batch_solve).  Fills temporal_tile_px, col_stages and their
+ * times.  Errors: INVALID_ARG, CUDA. */
+recon_status recon_batch_autotune(recon_batch* batch, recon_tuning* out, void* stream);
+
 /* Frees the plan and all its device memory.  NULL-safe. */
 recon_status recon_destroy(recon_plan* plan);
 

@@ -35,7 +35,7 @@ EXPORTS = ["recon_default_opts", "recon_plan_create", "recon_solve", "recon_solv
            "recon_get_profile", "recon_kernel_launches", "recon_gram_inverse_noalloc",
            "recon_batch_create", "recon_batch_solve", "recon_batch_info", "recon_batch_destroy",
            "recon_grad_create", "recon_grad_forward", "recon_grad_backward", "recon_grad_destroy",
-           "recon_solve_kspace", "recon_quantize_kspace"]
+           "recon_solve_kspace", "recon_quantize_kspace", "recon_autotune", "recon_batch_autotune"]
 
 
 class Opts(C.Structure):
@@ -50,6 +50,16 @@ class Info(C.Structure):
 
 class KSpace(C.Structure):
     _fields_ = [("data", C.c_void_p), ("storage", C.c_int), ("frame_scale", C.c_void_p)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("temporal_tile_px", C.c_int), ("col_stages", C.c_int), ("rows_per_block", C.c_int),
+                ("combine_coils", C.c_int), ("objective_coils", C.c_int), ("temporal_ms", C.c_float),
+                ("col_ms", C.c_float), ("rows_ms", C.c_float), ("combine_ms", C.c_float),
+                ("objective_ms", C.c_float), ("from_cache", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Profile(C.Structure):
@@ -125,6 +135,10 @@ def load(path: str = LIB_PATH):
     lib.recon_solve_kspace.restype = i
     lib.recon_quantize_kspace.argtypes = [i, i, i, i, fp, i, vp, fp, vp]
     lib.recon_quantize_kspace.restype = i
+    lib.recon_autotune.argtypes = [vp, C.POINTER(Tuning), vp]
+    lib.recon_autotune.restype = i
+    lib.recon_batch_autotune.argtypes = [vp, C.POINTER(Tuning), vp]
+    lib.recon_batch_autotune.restype = i
     _lib = lib
     return lib
 
@@ -212,6 +226,12 @@ class Plan:
         _check(st)
         return out, inf
 
+    def autotune(self, stream=None) -> Tuning:
+        """Picks the kernels' launch shapes by timing them (recon_autotune)."""
+        t = Tuning()
+        _check(load().recon_autotune(self._h, C.byref(t), _stream(stream)))
+        return t
+
     def solve_quantized(self, q, out=None, info=True, stream=None):
         """Runs the reconstruction from 16-bit k-space ``q`` (a QuantizedKspace)."""
         out = self._img() if out is None else out
@@ -287,6 +307,12 @@ class Batch:
         oa = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
         _check(load().recon_batch_solve(self._h, ka, oa, _stream(stream)))
         return outs
+
+    def autotune(self, stream=None) -> Tuning:
+        """Temporal tile width and ring depth for this batch (recon_batch_autotune)."""
+        t = Tuning()
+        _check(load().recon_batch_autotune(self._h, C.byref(t), _stream(stream)))
+        return t
 
     def info(self, stream=None):
         arr = (Info * len(self.plans))()

@@ -179,13 +179,18 @@ int coil_group_for(int Nc, int Ny) {
 }  // namespace
 
 namespace recon {
+int objective_coils_max(int Nc, int Ny) { return coil_group_for(Nc, Ny); }
+}  // namespace recon
+
+namespace recon {
 
 // ||y - H x||^2 of a field by explicit FFTs (J(0), and every J(k) in the
 // exact objective mode or with 16-bit inverses, where (mu I + H'H) x = r
 // holds only to the storage precision).
 recon_status plan_objective(recon_plan* p, const float2* x, double* acc, cudaStream_t s) {
   ObjParams o{};
-  o.Nx = p->Nx; o.Ny = p->Ny; o.Nt = p->Nt; o.Nc = p->Nc; o.ncg = coil_group_for(p->Nc, p->Ny);
+  o.Nx = p->Nx; o.Ny = p->Ny; o.Nt = p->Nt; o.Nc = p->Nc;
+  o.ncg = p->obj_coils > 0 ? std::min(p->obj_coils, coil_group_for(p->Nc, p->Ny)) : coil_group_for(p->Nc, p->Ny);
   o.x = x; o.sens = p->sens; o.rows = p->rows; o.rowoff = p->rowoff; o.fy = p->fy;
   o.yhat = p->storage ? p->yhat_lp : static_cast<const void*>(p->yhat);
   o.ystorage = p->storage;
@@ -210,8 +215,9 @@ recon_status plan_to_user(recon_plan* p, const float2* in, float2* out, cudaStre
 recon_status plan_adjoint64(recon_plan* p, const void* kspace, int kstorage, const float* kscale, float2* yhat32,
                             float2* b, double* yy, cudaStream_t s) {
   RC(launch_hybrid_rows64(kspace, kstorage, kscale, p->yhat64, yhat32, yy, p->rows, p->rowoff, p->maxm, p->Nx, p->Ny,
-                          p->Nt, p->Nc, p->fx64, s));
-  RC(launch_adjoint_combine64(p->yhat64, p->sens, b, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fy64, s));
+                          p->Nt, p->Nc, p->fx64, p->rows_per_block, s));
+  RC(launch_adjoint_combine64(p->yhat64, p->sens, b, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fy64,
+                              p->combine_coils, s));
   return RECON_OK;
 }
 
@@ -223,9 +229,9 @@ recon_status plan_prologue(recon_plan* p, const void* kspace, int kstorage, cons
   if (p->storage == 0) return plan_adjoint64(p, kspace, kstorage, kscale, p->yhat, p->b, p->yy, s);
   RC(cudaMemsetAsync(p->ymax, 0, (size_t)p->Nt * sizeof(unsigned), s));
   RC(launch_hybrid_rows(kspace, kstorage, kscale, p->tmp_b, p->yy, p->ymax, p->rows, p->rowoff, p->maxm, p->Nx, p->Ny,
-                        p->Nt, p->Nc, p->fx, s));
+                        p->Nt, p->Nc, p->fx, p->rows_per_block, s));
   RC(launch_adjoint_combine(p->tmp_b, p->sens, p->b, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fy,
-                            p->storage, p->yhat_lp, p->ymax, p->yscale, s));
+                            p->storage, p->yhat_lp, p->ymax, p->yscale, p->combine_coils, s));
   return RECON_OK;
 }
 

@@ -116,6 +116,7 @@ struct c16b { __nv_bfloat162 v; };
 template <typename E> struct Elem;
 template <> struct Elem<float2> {
   static constexpr int bytes = 8;
+  __device__ __forceinline__ static float2 widen(float2 v) { return v; }
   __device__ __forceinline__ static float2 load(const float2* p) { return *p; }
   __device__ __forceinline__ static void load2(const float2* p, float2& a, float2& b) {
     float4 q = *reinterpret_cast<const float4*>(p);
@@ -126,6 +127,7 @@ template <> struct Elem<float2> {
 };
 template <> struct Elem<__half2> {
   static constexpr int bytes = 4;
+  __device__ __forceinline__ static float2 widen(__half2 v) { return __half22float2(v); }
   __device__ __forceinline__ static float2 load(const __half2* p) { return __half22float2(*p); }
   __device__ __forceinline__ static void load2(const __half2* p, float2& a, float2& b) {
     uint2 q = *reinterpret_cast<const uint2*>(p);
@@ -139,6 +141,7 @@ template <> struct Elem<__half2> {
 };
 template <> struct Elem<__nv_bfloat162> {
   static constexpr int bytes = 4;
+  __device__ __forceinline__ static float2 widen(__nv_bfloat162 v) { return __bfloat1622float2(v); }
   __device__ __forceinline__ static float2 load(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
   __device__ __forceinline__ static void load2(const __nv_bfloat162* p, float2& a, float2& b) {
     uint2 q = *reinterpret_cast<const uint2*>(p);

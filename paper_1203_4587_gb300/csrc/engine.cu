@@ -20,6 +20,14 @@ cudaError_t DevArena::alloc(void** p, size_t bytes) {
   return e;
 }
 
+void DevArena::free(void* p) {
+  auto it = std::find(ptrs.begin(), ptrs.end(), p);
+  if (it != ptrs.end()) {
+    cudaFree(p);
+    ptrs.erase(it);
+  }
+}
+
 void DevArena::release() {
   for (void* p : ptrs) cudaFree(p);
   ptrs.clear();
@@ -168,11 +176,12 @@ ColSlice col_desc(recon_plan* p, int k, bool fused, int unit_off) {
 recon_status finish_col_shape(Engine* e, recon_plan* const* plans, int n, int stages_req) {
   e->nb_max = 0;
   for (int q = 0; q < n; ++q) e->nb_max = std::max(e->nb_max, plans[q]->pk.nb);
-  const int maxst = col_inverse_max_stages(e->nb_max, e->nunits_all, n, e->work_max);
+  const int es = e->storage ? 4 : 8;
+  const int maxst = col_inverse_max_stages(e->nb_max, e->nunits_all, n, e->work_max, es);
   const int qn = col_inverse_stage_quantum();
   int st = stages_req > 0 ? std::min(stages_req, maxst) : maxst;
   e->stages = std::max(qn, st / qn * qn);
-  const size_t smem = col_inverse_smem(e->stages, e->nb_max, e->nunits_all, n, e->work_max);
+  const size_t smem = col_inverse_smem(e->stages, e->nb_max, e->nunits_all, n, e->work_max, es);
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -218,35 +227,10 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
   // temporal descriptors, K+1 sets
   e->Nt_max = 0;
   for (int q = 0; q < n; ++q) e->Nt_max = std::max(e->Nt_max, plans[q]->Nt);
-  e->tile_px = e->tv ? tv_tile_px(e->Nt_max) : dft_tile_px();
-  std::vector<int> tile0(n);
-  int blocks = 0;
-  for (int q = 0; q < n; ++q) {
-    tile0[q] = blocks;
-    blocks += (int)((plans[q]->npix() + e->tile_px - 1) / e->tile_px);
-  }
-  e->tmp_blocks = blocks;
-  if (e->tv) {
-    std::vector<TvSlice> t((size_t)(K + 1) * n);
-    for (int k = 1; k <= K + 1; ++k)
-      for (int q = 0; q < n; ++q) {
-        TvSlice d = tv_desc(plans[q], k, K);
-        d.tile0 = tile0[q];
-        t[(size_t)(k - 1) * n + q] = d;
-      }
-    RC(upload(e->arena, reinterpret_cast<TvSlice**>(&e->d_tmp), t));
-    RC(prepare_tv_temporal(e->Nt_max));
-  } else {
-    std::vector<DftSlice> t((size_t)(K + 1) * n);
-    for (int k = 1; k <= K + 1; ++k)
-      for (int q = 0; q < n; ++q) {
-        DftSlice d = dft_desc(plans[q], k, K);
-        d.tile0 = tile0[q];
-        t[(size_t)(k - 1) * n + q] = d;
-      }
-    RC(upload(e->arena, reinterpret_cast<DftSlice**>(&e->d_tmp), t));
-    RC(prepare_dft_temporal(e->Nt_max));
-  }
+  // a single plan uses its own tuning; a batch starts from the default (recon_batch_autotune)
+  const int px = (n == 1 && p0->tile_px > 0) ? p0->tile_px : (e->tv ? tv_tile_px(e->Nt_max) : dft_tile_px());
+  recon_status st = engine_set_tile(e, px);
+  if (st != RECON_OK) return st;
   // finalize descriptors
   std::vector<FinSlice> fin(n);
   for (int q = 0; q < n; ++q) {
@@ -273,7 +257,48 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
     RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_err), sizeof(int)));
     RC(cudaMemset(e->d_err, 0, sizeof(int)));
   }
-  return finish_col_shape(e, plans, n, p0->opts.col_stages);
+  return finish_col_shape(e, plans, n,
+                          (n == 1 && p0->col_stages_tuned > 0) ? p0->col_stages_tuned : p0->opts.col_stages);
+}
+
+// (Re)builds the K+1 temporal descriptor sets for tiles of `px` pixels.
+recon_status engine_set_tile(Engine* e, int px) {
+  const int K = e->K, n = e->n;
+  int cand[4];
+  const int nc = e->tv ? tv_tile_candidates(e->Nt_max, cand) : dft_tile_candidates(e->Nt_max, cand);
+  if (std::find(cand, cand + nc, px) == cand + nc) return fail(RECON_ERR_INVALID_ARG, "temporal tile width does not fit");
+  std::vector<int> tile0(n);
+  int blocks = 0;
+  for (int q = 0; q < n; ++q) {
+    tile0[q] = blocks;
+    blocks += (int)((e->plans[q]->npix() + px - 1) / px);
+  }
+  void* old = e->d_tmp;
+  if (e->tv) {
+    std::vector<TvSlice> t((size_t)(K + 1) * n);
+    for (int k = 1; k <= K + 1; ++k)
+      for (int q = 0; q < n; ++q) {
+        TvSlice d = tv_desc(e->plans[q], k, K);
+        d.tile0 = tile0[q];
+        t[(size_t)(k - 1) * n + q] = d;
+      }
+    RC(upload(e->arena, reinterpret_cast<TvSlice**>(&e->d_tmp), t));
+    RC(prepare_tv_temporal(e->Nt_max, px));
+  } else {
+    std::vector<DftSlice> t((size_t)(K + 1) * n);
+    for (int k = 1; k <= K + 1; ++k)
+      for (int q = 0; q < n; ++q) {
+        DftSlice d = dft_desc(e->plans[q], k, K);
+        d.tile0 = tile0[q];
+        t[(size_t)(k - 1) * n + q] = d;
+      }
+    RC(upload(e->arena, reinterpret_cast<DftSlice**>(&e->d_tmp), t));
+    RC(prepare_dft_temporal(e->Nt_max, px));
+  }
+  if (old) e->arena.free(old);
+  e->tile_px = px;
+  e->tmp_blocks = blocks;
+  return RECON_OK;
 }
 
 recon_status engine_build_inverse(Engine* e, recon_plan* p) {

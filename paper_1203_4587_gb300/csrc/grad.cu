@@ -327,7 +327,7 @@ recon_status recon_grad_create(recon_grad** out, recon_plan* const* plans, int n
   recon_status st = finish_col_shape(&g->fwd, plans, n, plans[0]->opts.col_stages);
   if (st == RECON_OK) st = finish_col_shape(&g->bwd, plans, n, plans[0]->opts.col_stages);
   if (st != RECON_OK) return bail(st);
-  if (prepare_tv_temporal(Nt_max) != cudaSuccess) return bail(fail(RECON_ERR_CUDA, "temporal kernel attributes"));
+  if (prepare_tv_temporal(Nt_max, px) != cudaSuccess) return bail(fail(RECON_ERR_CUDA, "temporal kernel attributes"));
   *out = g;
   return RECON_OK;
 }

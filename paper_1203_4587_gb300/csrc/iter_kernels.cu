@@ -15,7 +15,9 @@ namespace recon {
 constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kColThreads = kConsumers + 96;  // + producer, r loader, column manager
-constexpr int kStageBytes = kRectElems * 8;   // largest unit (FP32 rect)
+// A ring stage holds the largest unit of the storage type: kRectElems
+// elements of esize bytes (8 FP32, 4 FP16/BF16; both multiples of 16 bytes).
+__host__ __device__ constexpr int stage_bytes(int esize) { return kRectElems * esize; }
 
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
   return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
@@ -27,8 +29,19 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
 // lanes sharing lc, by butterfly exchanges that leave one total per lane.
 template <typename E>
 __device__ __forceinline__ void proc_tile(const E* __restrict__ tl, const float2* __restrict__ r,
-                                          float2* __restrict__ yw, int p, int q, int lane) {
+                                          float2* __restrict__ yw, int p, int q, int lane, uint64_t* release) {
   const int lr = lane >> 2, lc = lane & 3;
+  // the whole unit into registers first, then the ring stage goes back to the
+  // producer while this warp computes
+  E el[32];
+#pragma unroll
+  for (int qq = 0; qq < 16; ++qq) {
+    const E* src = tl + qq * 64 + lane * 2;
+    el[2 * qq] = src[0];
+    el[2 * qq + 1] = src[1];
+  }
+  __syncwarp();
+  if (lane == 0) mbar_arrive(release);
   float2 rv[4], cv[8];
   {
     const float4* r4 = reinterpret_cast<const float4*>(r + p * 32 + lr * 4);
@@ -49,8 +62,7 @@ __device__ __forceinline__ void proc_tile(const E* __restrict__ tl, const float2
   for (int k = 0; k < 8; ++k) colp[k] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int qq = 0; qq < 16; ++qq) {
-    float2 e0, e1;
-    Elem<E>::load2(tl + qq * 64 + lane * 2, e0, e1);
+    const float2 e0 = Elem<E>::widen(el[2 * qq]), e1 = Elem<E>::widen(el[2 * qq + 1]);
     const int ri = qq >> 2, c0 = (qq & 3) * 2;
     c_fma(rowp[ri], e0, cv[c0]);
     c_fma(rowp[ri], e1, cv[c0 + 1]);
@@ -95,28 +107,35 @@ __device__ __forceinline__ void proc_tile(const E* __restrict__ tl, const float2
 // makes both passes free of bank conflicts.
 template <typename E>
 __device__ __forceinline__ void proc_rect(const E* __restrict__ tl, const float2* __restrict__ r,
-                                          float2* __restrict__ yw, int p, int q, int lane) {
+                                          float2* __restrict__ yw, int p, int q, int lane, uint64_t* release) {
   const float2* rP = r + p * 32;
   const float2* rQ = r + q * 32;
+  // pass 1 from registers; the stage is released once pass 2's cells are loaded
+  E e1[33];
+#pragma unroll
+  for (int b = 0; b < 33; ++b) e1[b] = tl[b * 32 + ((lane + b) & 31)];
   float2 rowP = make_float2(0.f, 0.f), colQ = make_float2(0.f, 0.f);
-#pragma unroll 11
+#pragma unroll
   for (int b = 0; b < 33; ++b) {
-    float2 e = Elem<E>::load(tl + b * 32 + ((lane + b) & 31));
+    const float2 e = Elem<E>::widen(e1[b]);
     if (b > lane) c_fma(rowP, e, rP[b - 1]);      // P[lane][b-1], b-1 >= lane
     else c_fmac(colQ, e, rQ[b]);                   // Q[b][lane], b <= lane
   }
+  const float2 c00 = Elem<E>::widen(e1[0]);       // cell (lane, 0) = Q[0][lane]
+  E e2[32];
+#pragma unroll
+  for (int a = 0; a < 32; ++a) e2[a] = tl[(lane + 1) * 32 + ((a + lane + 1) & 31)];
+  __syncwarp();
+  if (lane == 0) mbar_arrive(release);
   float2 colP = make_float2(0.f, 0.f), rowQ = make_float2(0.f, 0.f);
-#pragma unroll 8
+#pragma unroll
   for (int a = 0; a < 32; ++a) {
-    float2 e = Elem<E>::load(tl + (lane + 1) * 32 + ((a + lane + 1) & 31));
+    const float2 e = Elem<E>::widen(e2[a]);
     if (a < lane) c_fmac(colP, e, rP[a]);          // P[a][lane], a < lane
     else if (a > lane + 1) c_fma(rowQ, e, rQ[a]);  // Q[lane+1][a], a > lane+1
   }
   float2 t0 = make_float2(0.f, 0.f);
-  {
-    float2 e = Elem<E>::load(tl + lane);           // cell (lane, 0) = Q[0][lane]
-    if (lane > 0) t0 = c_mul(e, rQ[lane]);
-  }
+  if (lane > 0) t0 = c_mul(c00, rQ[lane]);
   t0 = warp_sum2(t0);
   float2* y1 = yw + p * 32 + lane;
   *y1 = c_add(*y1, c_add(rowP, colP));
@@ -178,14 +197,15 @@ constexpr int kRSlots = 2;  // double-buffered r inputs / partial sums
 struct ColLayout {
   size_t bars, ring, ycopy, rvec, bvec, rslot, units, slices, skip, work, total;
 };
-__host__ __device__ inline ColLayout col_layout(int stages, int nb, int nunits, int nslices, int work_max) {
+__host__ __device__ inline ColLayout col_layout(int stages, int nb, int nunits, int nslices, int work_max,
+                                                int esize) {
   ColLayout L;
   const size_t ny32 = (size_t)(nb + 1) * 32;
   size_t o = 0;
   // full[S], empty[S], rfull[2], rempty[2], rv_full[2], yc_empty[2], col_done[2]
   L.bars = o; o += (2 * (size_t)stages + 5 * kRSlots) * 8;
   o = align_up(o, 128);
-  L.ring = o; o += (size_t)stages * kStageBytes;
+  L.ring = o; o += (size_t)stages * stage_bytes(esize);
   o = align_up(o, 16);
   L.ycopy = o; o += (size_t)kRSlots * kConsumerWarps * ny32 * 8;   // [buf][warp][ny32]
   L.rvec = o; o += (size_t)kRSlots * ny32 * 8;
@@ -216,7 +236,8 @@ __host__ __device__ inline ColLayout col_layout(int stages, int nb, int nunits, 
 template <typename E>
 __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const ColLayout L = col_layout(P.stages, P.nb_max, P.nunits_all, P.nslices, P.work_max);
+  constexpr int kStage = stage_bytes(Elem<E>::bytes);
+  const ColLayout L = col_layout(P.stages, P.nb_max, P.nunits_all, P.nslices, P.work_max, Elem<E>::bytes);
   const int S = P.stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
   uint64_t* empty = full + S;
@@ -282,7 +303,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
           const int4 un = units[c.unit_off + u];
           const uint32_t bytes = (uint32_t)((un.x == UNIT_TILE ? kTileElems : kRectElems) * ES);
           mbar_arrive_expect_tx(&full[st], bytes);
-          bulk_g2s(ring + (size_t)st * kStageBytes, cb + (size_t)un.w * ES, bytes, &full[st], pol);
+          bulk_g2s(ring + (size_t)st * kStage, cb + (size_t)un.w * ES, bytes, &full[st], pol);
           if (++st == S) { st = 0; ++wraps; }
         }
       }
@@ -425,6 +446,10 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
       float2* yc = ycopy + (size_t)bb * kConsumerWarps * ny32m;
       const float2* rv = rvec + (size_t)bb * ny32m;
       const float2* bv = bvec + (size_t)bb * ny32m;
+      // per element in FP32 (GB300's FP64 rate is a small fraction of FP32),
+      // summed per lane over the column in FP32 and added once to the FP64
+      // accumulator: w_bx Re<b, x> + w_xr Re<x, r> + w_xx |x|^2
+      float fcol = 0.f;
       for (int j = lane; j < ny32; j += 32) {
         float2 x = yc[j];
         yc[j] = make_float2(0.f, 0.f);
@@ -437,13 +462,14 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
           c.xout[cofs + j] = x;
           if (c.do_obj) {
             const float2 r = rv[j], b = bv[j];
-            // w_bx Re<b, x> + w_xr Re<x, r> + w_xx |x|^2
-            fid += (double)c.w_bx * ((double)b.x * x.x + (double)b.y * x.y) +
-                   (double)c.w_xr * ((double)x.x * r.x + (double)x.y * r.y) +
-                   (double)c.w_xx * ((double)x.x * x.x + (double)x.y * x.y);
+            float f = c.w_bx * fmaf(b.x, x.x, b.y * x.y);
+            f = fmaf(c.w_xr, fmaf(x.x, r.x, x.y * r.y), f);
+            f = fmaf(c.w_xx, fmaf(x.x, x.x, x.y * x.y), f);
+            fcol += f;
           }
         }
       }
+      fid += (double)fcol;
       __syncwarp();
       if (lane == 0) mbar_arrive(&yc_empty[bb]);
       if (n + kRSlots < ncol) ok = prepare(n + kRSlots);
@@ -479,10 +505,9 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
     for (; u < c.nunits; u += kConsumerWarps) {
       if (!mbar_wait(&full[st], ph, P.err)) { failed = true; break; }
       const int4 un = units[c.unit_off + u];
-      const E* tl = reinterpret_cast<const E*>(ring + (size_t)st * kStageBytes);
-      if (un.x == UNIT_TILE) proc_tile<E>(tl, rv, yw, un.y, un.z, lane);
-      else proc_rect<E>(tl, rv, yw, un.y, un.z, lane);
-      if (lane == 0) mbar_arrive(&empty[st]);
+      const E* tl = reinterpret_cast<const E*>(ring + (size_t)st * kStage);
+      if (un.x == UNIT_TILE) proc_tile<E>(tl, rv, yw, un.y, un.z, lane, &empty[st]);
+      else proc_rect<E>(tl, rv, yw, un.y, un.z, lane, &empty[st]);
       st += kConsumerWarps;
       if (st >= S) { st -= S; ph ^= 1u; }
     }
@@ -494,19 +519,19 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
 #undef WCOL
 }
 
-size_t col_inverse_smem(int stages, int nb_max, int nunits_all, int nslices, int work_max) {
-  return col_layout(stages, nb_max, nunits_all, nslices, work_max).total;
+size_t col_inverse_smem(int stages, int nb_max, int nunits_all, int nslices, int work_max, int esize) {
+  return col_layout(stages, nb_max, nunits_all, nslices, work_max, esize).total;
 }
 
 // Largest ring depth that fits, a multiple of the consumer warp count (the
 // parity waits rely on it; see the consumer loop).
-int col_inverse_max_stages(int nb_max, int nunits_all, int nslices, int work_max) {
+int col_inverse_max_stages(int nb_max, int nunits_all, int nslices, int work_max, int esize) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  int s = 4 * kConsumerWarps;
+  int s = 8 * kConsumerWarps;
   while (s > kConsumerWarps) {
-    if (col_inverse_smem(s, nb_max, nunits_all, nslices, work_max) + 1024 <= (size_t)optin) break;
+    if (col_inverse_smem(s, nb_max, nunits_all, nslices, work_max, esize) + 1024 <= (size_t)optin) break;
     s -= kConsumerWarps;
   }
   return s;
@@ -536,7 +561,7 @@ cudaError_t prepare_col_inverse(int storage, size_t smem) {
 }
 
 cudaError_t launch_col_inverse(const ColLaunch& p, int storage, int grid, cudaStream_t s) {
-  const size_t smem = col_inverse_smem(p.stages, p.nb_max, p.nunits_all, p.nslices, p.work_max);
+  const size_t smem = col_inverse_smem(p.stages, p.nb_max, p.nunits_all, p.nslices, p.work_max, storage ? 4 : 8);
   cudaError_t e = prepare_col_inverse(storage, smem);
   if (e != cudaSuccess) return e;
   switch (storage) {
@@ -672,28 +697,41 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_temporal(TemporalLaunch L) {
   if (tid == 0) atomicAdd(P.prior_acc, s);
 }
 
-// four [Nt][px] complex tiles: px = 64 up to Nt = 96, else 32 (Nt <= 128)
+// four [Nt][px] complex tiles; px in {32, 64, 128} (the widest that fits is
+// the default: 64 up to Nt = 96, else 32; 128 needs Nt <= 55)
+constexpr size_t kSmemOptin = 227 * 1024;
+static size_t tv_smem(int Nt_max, int px) { return 4 * (size_t)Nt_max * px * sizeof(float2); }
 int tv_tile_px(int Nt_max) { return Nt_max <= 96 ? 64 : 32; }
+int tv_tile_candidates(int Nt_max, int* out) {
+  int n = 0;
+  for (int px : {32, 64, 128})
+    if (tv_smem(Nt_max, px) + 1024 <= kSmemOptin) out[n++] = px;
+  return n;
+}
 
-cudaError_t prepare_tv_temporal(int Nt_max) {
-  static size_t configured = 0;
-  const size_t smem = 4 * (size_t)Nt_max * tv_tile_px(Nt_max) * sizeof(float2);
-  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
-    cudaError_t e = cudaFuncSetAttribute(k_tv_temporal<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_tv_temporal<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t prepare_tv_temporal(int Nt_max, int px) {
+  static size_t configured[3] = {0, 0, 0};
+  const size_t smem = tv_smem(Nt_max, px);
+  const int k = px == 32 ? 0 : px == 64 ? 1 : px == 128 ? 2 : -1;
+  if (k < 0) return cudaErrorInvalidValue;
+  if (smem > configured[k]) {   // also below 48 KB: static shared memory counts toward that limit
+    cudaError_t e = cudaSuccess;
+    if (px == 32) e = cudaFuncSetAttribute(k_tv_temporal<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (px == 64) e = cudaFuncSetAttribute(k_tv_temporal<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (px == 128) e = cudaFuncSetAttribute(k_tv_temporal<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
+    configured[k] = smem;
   }
   return cudaSuccess;
 }
 
 cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s) {
-  cudaError_t e = prepare_tv_temporal(p.Nt_max);
+  cudaError_t e = prepare_tv_temporal(p.Nt_max, p.tile_px);
   if (e != cudaSuccess) return e;
-  const size_t smem = 4 * (size_t)p.Nt_max * p.tile_px * sizeof(float2);
+  const size_t smem = tv_smem(p.Nt_max, p.tile_px);
   if (p.tile_px == 64) k_tv_temporal<64><<<p.nblocks, kTvThreads, smem, s>>>(p);
-  else k_tv_temporal<32><<<p.nblocks, kTvThreads, smem, s>>>(p);
+  else if (p.tile_px == 32) k_tv_temporal<32><<<p.nblocks, kTvThreads, smem, s>>>(p);
+  else k_tv_temporal<128><<<p.nblocks, kTvThreads, smem, s>>>(p);
   note_launch();
   return cudaGetLastError();
 }
@@ -707,9 +745,16 @@ cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s) {
 // Psi is unitary, the (I - Psi Psi') term of the w-update is zero.  Also
 // accumulates ||w||_1 (the prior term of J at the incoming iterate).
 // ---------------------------------------------------------------------------
-constexpr int kDftPix = 64;
-int dft_tile_px() { return kDftPix; }
+static size_t dft_smem(int Nt_max, int px) { return 2 * (size_t)Nt_max * px * sizeof(float2); }
+int dft_tile_px() { return 64; }
+int dft_tile_candidates(int Nt_max, int* out) {
+  int n = 0;
+  for (int px : {16, 32, 64, 128})
+    if (dft_smem(Nt_max, px) + 1024 <= kSmemOptin) out[n++] = px;
+  return n;
+}
 
+template <int kDftPix>
 __global__ void __launch_bounds__(256) k_dft_temporal(TemporalLaunch L) {
   extern __shared__ float2 sm_dft[];
   __shared__ double red[32];
@@ -767,22 +812,35 @@ __global__ void __launch_bounds__(256) k_dft_temporal(TemporalLaunch L) {
   if (tid == 0) atomicAdd(P.prior_acc, s);
 }
 
-cudaError_t prepare_dft_temporal(int Nt_max) {
-  static size_t configured = 0;
-  const size_t smem = 2 * (size_t)Nt_max * kDftPix * sizeof(float2);
-  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
-    cudaError_t e = cudaFuncSetAttribute(k_dft_temporal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t prepare_dft_temporal(int Nt_max, int px) {
+  static size_t configured[4] = {0, 0, 0, 0};
+  const size_t smem = dft_smem(Nt_max, px);
+  const int k = px == 16 ? 0 : px == 32 ? 1 : px == 64 ? 2 : px == 128 ? 3 : -1;
+  if (k < 0) return cudaErrorInvalidValue;
+  if (smem > configured[k]) {   // also below 48 KB: static shared memory counts toward that limit
+    cudaError_t e = cudaSuccess;
+    const int b = (int)smem;
+    if (px == 16) e = cudaFuncSetAttribute(k_dft_temporal<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (px == 32) e = cudaFuncSetAttribute(k_dft_temporal<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (px == 64) e = cudaFuncSetAttribute(k_dft_temporal<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (px == 128) e = cudaFuncSetAttribute(k_dft_temporal<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e != cudaSuccess) return e;
-    configured = smem;
+    configured[k] = smem;
   }
   return cudaSuccess;
 }
 
 cudaError_t launch_dft_temporal(const TemporalLaunch& p, cudaStream_t s) {
-  cudaError_t e = prepare_dft_temporal(p.Nt_max);
+  cudaError_t e = prepare_dft_temporal(p.Nt_max, p.tile_px);
   if (e != cudaSuccess) return e;
-  const size_t smem = 2 * (size_t)p.Nt_max * kDftPix * sizeof(float2);
-  k_dft_temporal<<<p.nblocks, 256, smem, s>>>(p); note_launch();
+  const size_t smem = dft_smem(p.Nt_max, p.tile_px);
+  switch (p.tile_px) {
+    case 16: k_dft_temporal<16><<<p.nblocks, 256, smem, s>>>(p); break;
+    case 32: k_dft_temporal<32><<<p.nblocks, 256, smem, s>>>(p); break;
+    case 64: k_dft_temporal<64><<<p.nblocks, 256, smem, s>>>(p); break;
+    default: k_dft_temporal<128><<<p.nblocks, 256, smem, s>>>(p); break;
+  }
+  note_launch();
   return cudaGetLastError();
 }
 

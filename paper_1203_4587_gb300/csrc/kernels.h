@@ -197,14 +197,17 @@ void set_last_error(const std::string& why);
 
 // ---- launchers (return cudaGetLastError()) ---------------------------------
 cudaError_t launch_col_inverse(const ColLaunch& p, int storage, int grid, cudaStream_t s);
-size_t col_inverse_smem(int stages, int nb_max, int nunits_all, int nslices, int work_max);
-int col_inverse_max_stages(int nb_max, int nunits_all, int nslices, int work_max);
+// esize: bytes per stored element (8 FP32, 4 FP16/BF16)
+size_t col_inverse_smem(int stages, int nb_max, int nunits_all, int nslices, int work_max, int esize);
+int col_inverse_max_stages(int nb_max, int nunits_all, int nslices, int work_max, int esize);
 int col_inverse_stage_quantum();  // ring depth must be a positive multiple of this
-cudaError_t prepare_tv_temporal(int Nt_max);   // shared-memory attribute, outside any capture
-cudaError_t prepare_dft_temporal(int Nt_max);
+cudaError_t prepare_tv_temporal(int Nt_max, int px);   // shared-memory attribute, outside any capture
+cudaError_t prepare_dft_temporal(int Nt_max, int px);
 cudaError_t prepare_col_inverse(int storage, size_t smem);
-int tv_tile_px(int Nt_max);
+int tv_tile_px(int Nt_max);                         // default pixels per block
 int dft_tile_px();
+int tv_tile_candidates(int Nt_max, int* out);       // tile widths that fit (<= 4 entries)
+int dft_tile_candidates(int Nt_max, int* out);
 cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s);
 cudaError_t launch_dft_temporal(const TemporalLaunch& p, cudaStream_t s);
 cudaError_t launch_objective(const ObjParams& p, cudaStream_t s);
@@ -215,24 +218,27 @@ cudaError_t launch_finalize(const FinSlice* fins, int nslices, int k, cudaStream
 // yhat = F_h' y (FP32 butterflies), k-space complex64 or 16-bit pairs
 // (kstorage = recon_storage) times kscale[t] (may be null); ymax[t] receives
 // the largest |component| of frame t's yhat (float bits, may be null).
+// G (rows per block) and ncg (coils per pass) below: 0 = the largest that fits.
 cudaError_t launch_hybrid_rows(const void* kspace, int kstorage, const float* kscale, float2* yhat, double* yy,
                                unsigned* ymax, const int* rows, const int* rowoff, int maxm, int Nx, int Ny, int Nt,
-                               int Nc, FftPlanDev fx, cudaStream_t s);
+                               int Nc, FftPlanDev fx, int G, cudaStream_t s);
 // b = H'y from yhat (FP32); ystorage 1/2 also writes the 16-bit copy ylp of
 // yhat with per-frame power-of-two scales yscale[t] from ymax.
 cudaError_t launch_adjoint_combine(const float2* yhat, const float2* sens, float2* b, const int* rows,
                                    const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, int ystorage,
-                                   void* ylp, const unsigned* ymax, float* yscale, cudaStream_t s);
+                                   void* ylp, const unsigned* ymax, float* yscale, int ncg, cudaStream_t s);
 // FP64 H'y prologue: the solution of the iterations is ~100x more sensitive to
 // errors in H'y than to rounding elsewhere, so H'y is formed in FP64 and
 // rounded once.  yhat32 receives the FP32 rounding of the hybrid data; *yy
 // accumulates ||y||^2 over the sampled entries (may be null).
 cudaError_t launch_hybrid_rows64(const void* kspace, int kstorage, const float* kscale, double2* yhat64,
                                  float2* yhat32, double* yy, const int* rows, const int* rowoff, int maxm, int Nx,
-                                 int Ny, int Nt, int Nc, FftPlanDev64 fx, cudaStream_t s);
+                                 int Ny, int Nt, int Nc, FftPlanDev64 fx, int G, cudaStream_t s);
 cudaError_t launch_adjoint_combine64(const double2* yhat64, const float2* sens, float2* b, const int* rows,
-                                     const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fy,
+                                     const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fy, int ncg,
                                      cudaStream_t s);
+int row_group_max(int Nx, bool fp64);              // largest rows-per-block of the row FFTs
+int coil_group_max(int Nc, int Ny, bool fp64);     // largest coils-per-pass of the combine
 // 16-bit k-space (storage 1 = FP16, 2 = BF16 pairs) with per-frame
 // power-of-two scales: out = k / frame_scale[t], one rounding.
 cudaError_t launch_quantize_kspace(const float2* k, long long per_frame, int Nt, int storage, void* out,

@@ -88,9 +88,9 @@ __global__ void __launch_bounds__(256) k_hybrid_rows(const KIn* __restrict__ ksp
 template <typename T, typename KIn>
 static cudaError_t launch_rows_t(const KIn* ksp, const float* kscale, T* yhat, float2* yhat32, double* yy,
                                  unsigned* ymax, const int* rows, const int* rowoff, int maxm, int Nx, int Ny, int Nt,
-                                 int Nc, const FftPlanT<T>& fx, cudaStream_t s) {
+                                 int Nc, const FftPlanT<T>& fx, int G_req, cudaStream_t s) {
   if (maxm <= 0) return cudaSuccess;
-  const int G = row_group<T>(Nx);
+  const int G = G_req > 0 ? std::min(G_req, row_group<T>(Nx)) : row_group<T>(Nx);
   const size_t smem = 2 * (size_t)G * (Nx + 1) * sizeof(T);
   static size_t configured = 0;
   if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
@@ -108,30 +108,30 @@ static cudaError_t launch_rows_t(const KIn* ksp, const float* kscale, T* yhat, f
 template <typename T, typename Plan>
 static cudaError_t rows_dispatch(const void* kspace, int kstorage, const float* kscale, T* yhat, float2* yhat32,
                                  double* yy, unsigned* ymax, const int* rows, const int* rowoff, int maxm, int Nx,
-                                 int Ny, int Nt, int Nc, const Plan& fx, cudaStream_t s) {
+                                 int Ny, int Nt, int Nc, const Plan& fx, int G, cudaStream_t s) {
   switch (kstorage) {
     case 0: return launch_rows_t<T, float2>(static_cast<const float2*>(kspace), kscale, yhat, yhat32, yy, ymax,
-                                            rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, s);
+                                            rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, G, s);
     case 1: return launch_rows_t<T, __half2>(static_cast<const __half2*>(kspace), kscale, yhat, yhat32, yy, ymax,
-                                             rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, s);
+                                             rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, G, s);
     case 2: return launch_rows_t<T, __nv_bfloat162>(static_cast<const __nv_bfloat162*>(kspace), kscale, yhat,
-                                                    yhat32, yy, ymax, rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, s);
+                                                    yhat32, yy, ymax, rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, G, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_hybrid_rows(const void* kspace, int kstorage, const float* kscale, float2* yhat, double* yy,
                                unsigned* ymax, const int* rows, const int* rowoff, int maxm, int Nx, int Ny, int Nt,
-                               int Nc, FftPlanDev fx, cudaStream_t s) {
+                               int Nc, FftPlanDev fx, int G, cudaStream_t s) {
   return rows_dispatch<float2>(kspace, kstorage, kscale, yhat, nullptr, yy, ymax, rows, rowoff, maxm, Nx, Ny, Nt,
-                               Nc, fx, s);
+                               Nc, fx, G, s);
 }
 
 cudaError_t launch_hybrid_rows64(const void* kspace, int kstorage, const float* kscale, double2* yhat64,
                                  float2* yhat32, double* yy, const int* rows, const int* rowoff, int maxm, int Nx,
-                                 int Ny, int Nt, int Nc, FftPlanDev64 fx, cudaStream_t s) {
+                                 int Ny, int Nt, int Nc, FftPlanDev64 fx, int G, cudaStream_t s) {
   return rows_dispatch<double2>(kspace, kstorage, kscale, yhat64, yhat32, yy, nullptr, rows, rowoff, maxm, Nx, Ny,
-                                Nt, Nc, fx, s);
+                                Nt, Nc, fx, G, s);
 }
 
 constexpr int kCoilGroupMax = 8;
@@ -208,9 +208,9 @@ static int coil_group(int Nc, int Ny) {
 template <typename T, typename YS>
 static cudaError_t launch_combine_t(const T* yhat, const float2* sens, float2* b, const int* rows, const int* rowoff,
                                     int Nx, int Ny, int Nt, int Nc, const FftPlanT<T>& fy, YS* ylp,
-                                    const unsigned* ymax, float* yscale, cudaStream_t s) {
+                                    const unsigned* ymax, float* yscale, int ncg_req, cudaStream_t s) {
   if (Ny > 1024) return cudaErrorInvalidValue;
-  const int ncg = coil_group<T>(Nc, Ny);
+  const int ncg = ncg_req > 0 ? std::min(ncg_req, coil_group<T>(Nc, Ny)) : coil_group<T>(Nc, Ny);
   const size_t smem = 2 * (size_t)ncg * Ny * sizeof(T);
   static size_t configured = 0;
   if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
@@ -227,24 +227,27 @@ static cudaError_t launch_combine_t(const T* yhat, const float2* sens, float2* b
 
 cudaError_t launch_adjoint_combine(const float2* yhat, const float2* sens, float2* b, const int* rows,
                                    const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, int ystorage,
-                                   void* ylp, const unsigned* ymax, float* yscale, cudaStream_t s) {
+                                   void* ylp, const unsigned* ymax, float* yscale, int ncg, cudaStream_t s) {
   switch (ystorage) {
     case 0: return launch_combine_t<float2, void>(yhat, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, fy, nullptr, nullptr,
-                                                  nullptr, s);
+                                                  nullptr, ncg, s);
     case 1: return launch_combine_t<float2, __half2>(yhat, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, fy,
-                                                     static_cast<__half2*>(ylp), ymax, yscale, s);
+                                                     static_cast<__half2*>(ylp), ymax, yscale, ncg, s);
     case 2: return launch_combine_t<float2, __nv_bfloat162>(yhat, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, fy,
-                                                            static_cast<__nv_bfloat162*>(ylp), ymax, yscale, s);
+                                                            static_cast<__nv_bfloat162*>(ylp), ymax, yscale, ncg, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_adjoint_combine64(const double2* yhat64, const float2* sens, float2* b, const int* rows,
-                                     const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fy,
+                                     const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fy, int ncg,
                                      cudaStream_t s) {
   return launch_combine_t<double2, void>(yhat64, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, fy, nullptr, nullptr,
-                                         nullptr, s);
+                                         nullptr, ncg, s);
 }
+
+int row_group_max(int Nx, bool fp64) { return fp64 ? row_group<double2>(Nx) : row_group<float2>(Nx); }
+int coil_group_max(int Nc, int Ny, bool fp64) { return fp64 ? coil_group<double2>(Nc, Ny) : coil_group<float2>(Nc, Ny); }
 
 // ---- 16-bit k-space with per-frame scales ----------------------------------
 // Three launches: the largest |component| of every frame (float bits into

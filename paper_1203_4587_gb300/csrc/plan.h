@@ -14,6 +14,7 @@ namespace recon {
 struct DevArena {
   std::vector<void*> ptrs;
   cudaError_t alloc(void** p, size_t bytes);
+  void free(void* p);
   void release();
   ~DevArena() { release(); }
 };
@@ -92,6 +93,12 @@ struct recon_plan {
   recon::FftPlanDev64 fx64{}, fy64{};
   int col_stages = 0;
   int last_iters = 0;
+  // tuned launch shapes (0 = the built-in default); see autotune.cu
+  int tile_px = 0;                     // temporal kernel pixels per block
+  int col_stages_tuned = 0;            // ring depth of the inverse kernel
+  int obj_coils = 0;                   // coils per pass of the explicit objective
+  int rows_per_block = 0;              // k-space rows per block of the prologue's row FFTs
+  int combine_coils = 0;               // coils per pass of the prologue's column FFTs
   recon::Engine* eng = nullptr;        // the plan's own iterations (a batch of one)
   recon::Engine* eng_inv = nullptr;    // recon_apply_inverse (tmp_a -> tmp_b)
   // opts.profile: event pairs around every inverse / temporal launch of a solve
@@ -144,6 +151,7 @@ recon_status finish_col_shape(Engine* e, recon_plan* const* plans, int n, int st
 recon_status launch_col_set(Engine* e, int set, cudaStream_t s);   // descriptor set `set` of d_col
 recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s);   // descriptor set `set` of d_tmp
 recon_status engine_build(Engine* e, recon_plan* const* plans, int n);
+recon_status engine_set_tile(Engine* e, int px);   // temporal tile width (rebuilds its descriptor sets)
 recon_status engine_build_inverse(Engine* e, recon_plan* p);   // tmp_a -> tmp_b, no objective
 // Resets traces/flags, J(0), K iterations and the final prior term of every
 // slice (prologues must have run).  `profile` records the plan's events (n = 1).
@@ -159,5 +167,6 @@ recon_status plan_adjoint64(recon_plan* p, const void* kspace, int kstorage, con
                             float2* b, double* yy, cudaStream_t s);
 recon_status plan_objective(recon_plan* p, const float2* x, double* acc, cudaStream_t s);
 recon_status plan_fill_info(recon_plan* p, recon_info* info, cudaStream_t s);
+int objective_coils_max(int Nc, int Ny);   // largest coils-per-pass of the explicit objective
 
 }  // namespace recon
