@@ -14,7 +14,8 @@ namespace recon {
 
 constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;
-constexpr int kColThreads = kConsumers + 96;  // + producer, r loader, column manager
+constexpr int kProducers = 2;                 // producer warps (one issuing thread each)
+constexpr int kColThreads = kConsumers + 32 * (kProducers + 2);  // + producers, r loader, column manager
 // A ring stage holds the largest unit of the storage type: kRectElems
 // elements of esize bytes (8 FP32, 4 FP16/BF16; both multiples of 16 bytes).
 __host__ __device__ constexpr int stage_bytes(int esize) { return kRectElems * esize; }
@@ -223,10 +224,10 @@ __host__ __device__ inline ColLayout col_layout(int stages, int nb, int nunits, 
 // Persistent column-inverse kernel over a work list of (slice, column) pairs,
 // warp-specialised and free of block-wide barriers in the main loop (all
 // hand-offs are bounded mbarrier waits):
-//   warp 8   producer: streams the packed inverses with the TMA engine
+//   warps 8-9  producers: stream the packed inverses with the TMA engine
 //            (cp.async.bulk, L2 evict_first) into a ring of S stages
-//   warp 9   r loader: bulk-copies each column's right-hand-side inputs
-//   warp 10  column manager: r = base + coef*add into rvec[n&1]; after the
+//   warp 10  r loader: bulk-copies each column's right-hand-side inputs
+//   warp 11  column manager: r = base + coef*add into rvec[n&1]; after the
 //            consumers are done, x = sum of the 8 partial y vectors, store,
 //            objective dot products, clear the partials
 //   warps 0-7 consumers: Hermitian matvec of each unit into their own
@@ -286,33 +287,48 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
 #define WSL(w) ((int)(wl[w] >> 24))
 #define WCOL(w) ((int)(wl[w] & 0xFFFFFFu))
 
-  if (warp == kConsumerWarps) {
-    // ---------------- producer: stream packed inverses into the ring --------
+  if (warp >= kConsumerWarps && warp < kConsumerWarps + kProducers) {
+    // ---------------- producers: stream packed inverses into the ring -------
+    // Producer p issues the units whose index (counted across this CTA's
+    // columns) is p mod kProducers, into stage (index mod S): one issuing
+    // thread streams a bulk copy every ~150 ns at best, which limits 4 KB
+    // (16-bit) units, so the issue work is split.  S is a multiple of
+    // kProducers, so each producer owns a fixed set of stages.
     if (lane == 0) {
+      const int p = warp - kConsumerWarps;
       const uint64_t pol = policy_evict_first();
       // stage st of the ring, wraps = completed passes over the ring (no
       // divisions on the issue path)
-      int st = 0, wraps = 0;
+      int st = p, wraps = 0, gu = 0, issued = 0;
       bool ok = true;
       for (int w = w0; w < w1 && ok; ++w) {
         if (skip[WSL(w)]) continue;
         const ColSlice& c = sl[WSL(w)];
         const unsigned char* cb = reinterpret_cast<const unsigned char*>(c.A) + (size_t)WCOL(w) * (size_t)c.col_elems * ES;
-        for (int u = 0; u < c.nunits; ++u) {
+        // first unit of this column whose global index is p mod kProducers
+        int u = p - gu % kProducers;
+        if (u < 0) u += kProducers;
+        for (; u < c.nunits; u += kProducers) {
           if (wraps > 0 && !mbar_wait(&empty[st], (uint32_t)((wraps - 1) & 1), P.err)) { ok = false; break; }
           const int4 un = units[c.unit_off + u];
           const uint32_t bytes = (uint32_t)((un.x == UNIT_TILE ? kTileElems : kRectElems) * ES);
           mbar_arrive_expect_tx(&full[st], bytes);
           bulk_g2s(ring + (size_t)st * kStage, cb + (size_t)un.w * ES, bytes, &full[st], pol);
-          if (++st == S) { st = 0; ++wraps; }
+          ++issued;
+          st += kProducers;
+          if (st >= S) { st -= S; ++wraps; }
         }
+        gu += c.nunits;
       }
       if (!ok) {
-        // error path: let every copy still in flight land before the CTA exits
-        const long long g = (long long)wraps * S + st;
-        for (long long h = (g > S ? g - S : 0); h < g; ++h) {
-          uint64_t* bb = &full[h % S];
-          const uint32_t par = (uint32_t)((h / S) & 1);
+        // error path: let this producer's copies still in flight land before
+        // the CTA exits (its k-th copy filled stage (p + k*P) mod S for the
+        // ((p + k*P) / S)-th time)
+        const int per = S / kProducers;
+        for (int k = (issued > per ? issued - per : 0); k < issued; ++k) {
+          const long long gi = p + (long long)k * kProducers;
+          uint64_t* bb = &full[gi % S];
+          const uint32_t par = (uint32_t)((gi / S) & 1);
           unsigned long long t0 = global_ns();
           while (!mbar_try_wait(bb, par) && global_ns() - t0 < kWaitLimitNs) {}
         }
@@ -320,7 +336,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
     }
     return;
   }
-  if (warp == kConsumerWarps + 1) {
+  if (warp == kConsumerWarps + kProducers) {
     // ---------------- r loader: each column's inputs into a slot -------------
     // With 16-byte aligned columns (Ny even) lane 0 moves them with the TMA
     // engine; otherwise all lanes load them and lane 0 arrives after a warp
@@ -385,7 +401,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
   int ncol = 0;
   for (int w = w0; w < w1; ++w) ncol += skip[WSL(w)] ? 0 : 1;
 
-  if (warp == kConsumerWarps + 2) {
+  if (warp == kConsumerWarps + kProducers + 1) {
     // ---------------- column manager -----------------------------------------
     // walks the work list twice, in step: `wp` for prepare(n), `we` for the epilogue
     int wp = w0, we = w0;

@@ -1,7 +1,8 @@
 """CPU model of the column-inverse kernel's mbarrier protocol (no GPU).
 
-k_col_inverse hands data between warps with mbarriers and parity waits: a
-producer streams units into a ring of S stages (full/empty barriers), a
+k_col_inverse hands data between warps with mbarriers and parity waits:
+producers (units alternate between two issuing threads) stream units into
+a ring of S stages (full/empty barriers), a
 loader fills two r slots, a manager prepares r and reduces partial sums, and
 eight consumers walk units g = warp, warp+8, ...  A parity wait is only exact
 when the waiter is at most one phase ahead of the barrier.  This model runs
@@ -47,7 +48,7 @@ class Bar:
         return (self.phase & 1) != parity
 
 
-def simulate(S, nunits, ncols, seed, W=8, per_column_mapping=False):
+def simulate(S, nunits, ncols, seed, W=8, per_column_mapping=False, producers=1):
     rnd = random.Random(seed)
     full = [Bar(1) for _ in range(S)]
     empty = [Bar(1) for _ in range(S)]
@@ -94,20 +95,21 @@ def simulate(S, nunits, ncols, seed, W=8, per_column_mapping=False):
                 u -= nunits
             col_done[bb].arrive()
 
-    def producer():
-        st = wraps = 0
-        for _ in range(ncols * nunits):
+    def producer(p):
+        # producer p issues units g = p, p + P, ... into stage g mod S
+        st, wraps = p, 0
+        for g in range(p, ncols * nunits, producers):
             if wraps > 0:
                 while not empty[st].try_wait((wraps - 1) & 1):
                     yield
             assert busy[st] is None, "copy issued into a stage still in use"
-            g = wraps * S + st
+            assert g == wraps * S + st
             busy[st] = g
             full[st].expect_tx(1)
             inflight.append([rnd.randint(1, 30), st, g])
-            st += 1
-            if st == S:
-                st, wraps = 0, wraps + 1
+            st += producers
+            if st >= S:
+                st, wraps = st - S, wraps + 1
             yield
 
     def loader():
@@ -137,7 +139,7 @@ def simulate(S, nunits, ncols, seed, W=8, per_column_mapping=False):
             if n + 2 < ncols:
                 yield from prepare(n + 2)
 
-    alive = [consumer(w) for w in range(W)] + [producer(), loader(), manager()]
+    alive = [consumer(w) for w in range(W)] + [producer(p) for p in range(producers)] + [loader(), manager()]
     steps = 0
     while alive:
         steps += 1
@@ -162,12 +164,14 @@ def simulate(S, nunits, ncols, seed, W=8, per_column_mapping=False):
     assert processed == set(range(ncols * nunits))
 
 
-@pytest.mark.parametrize("S", [8, 16, 24])
+@pytest.mark.parametrize("producers", [1, 2])
+@pytest.mark.parametrize("S", [8, 16, 24, 32])
 @pytest.mark.parametrize("nunits", [1, 2, 3, 13, 32, 36])
-def test_protocol_holds_for_ring_depths_multiple_of_8(S, nunits):
+def test_protocol_holds_for_ring_depths_multiple_of_8(S, nunits, producers):
+    """The kernel runs two producers (units alternate between them)."""
     for ncols in (1, 2, 5):
         for seed in range(3):
-            simulate(S, nunits, ncols, seed)
+            simulate(S, nunits, ncols, seed, producers=producers)
 
 
 def test_per_column_unit_mapping_breaks_parity_waits():
