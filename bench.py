@@ -255,6 +255,9 @@ def measure_batched(nslices, storage, steps=3):
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
     batch = Batch(plans)
+    t0 = time.perf_counter()
+    tuning = batch.autotune().as_dict()
+    tuning["tune_s"] = time.perf_counter() - t0
     outs = [p._img() for p in plans]
     stream = torch.cuda.current_stream()
     batch.solve(ks, outs)            # direct run + graph capture
@@ -277,7 +280,7 @@ def measure_batched(nslices, storage, steps=3):
     return {"value": nslices / (ms / 1e3), "unit": "recons/s", "slices": nslices,
             "iters_per_slice": shapes[0]["iters"], "ms_per_batch": ms,
             "recons_per_s_with_plan": nslices / (ms / 1e3 + plan_s), "plan_s_total": plan_s,
-            "input_gen_s": gen_s, "iters_done": iters, "inverse_bytes_total": A_bytes,
+            "input_gen_s": gen_s, "iters_done": iters, "inverse_bytes_total": A_bytes, "tuning": tuning,
             "hbm_gbs_inverse_stream": A_bytes * shapes[0]["iters"] / (ms / 1e3) / 1e9,
             "note": ("Nx, Ny in {128,160,192,256}, Nt in {16,24,32,40}, Nc in {8,12,16}, R in {4,6,8}, TV, "
                      "lambda=0.005, mu=0.1; all slices in one launch per step, the batched solve replayed "
@@ -307,6 +310,7 @@ def measure_precision(steps=3):
         p = Plan(mask, sens, c.lam, c.mu, prior="tv", rho=c.rho, max_iters=c.iters, storage=storage, profile=1)
         torch.cuda.synchronize()
         plan_s = time.perf_counter() - t0
+        tn = p.autotune()
         q = quantize_kspace(k, storage) if storage != "fp32" else None
         img = torch.empty((Nt, Ny, Nx), dtype=torch.complex64, device="cuda")
 
@@ -334,7 +338,9 @@ def measure_precision(steps=3):
                         "inverse_bytes": A_bytes, "inverse_avg_ms": col_ms,
                         "inverse_gbs": bytes_launch / (col_ms / 1e3) / 1e9,
                         "inverse_frac": bytes_launch / (col_ms / 1e3) / 1e9 / peak,
-                        "inverse_share": prof.inverse_ms / max(prof.solve_ms, 1e-9)}
+                        "inverse_share": prof.inverse_ms / max(prof.solve_ms, 1e-9),
+                        "tuning": {"col_stages": tn.col_stages, "temporal_tile_px": tn.temporal_tile_px,
+                                   "objective_coils": tn.objective_coils}}
         p.close()
         del q
         torch.cuda.empty_cache()
@@ -510,6 +516,9 @@ def run_native(args):
     plan = Plan(mask, sens, w["lam"], w["mu"], prior=args.prior, rho=w["rho"], max_iters=w["iters"],
                 profile=1, storage=args.storage)
     plan_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tuning = plan.autotune().as_dict()       # launch shapes, picked by timing them
+    tuning["tune_s"] = time.perf_counter() - t0
     out = torch.empty((w["Nt"], w["Ny"], w["Nx"]), dtype=torch.complex64, device="cuda")
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
@@ -568,7 +577,7 @@ def run_native(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_obj(args.prior, args.storage), "roofline": roofline, "clocks": clocks,
-            "gpu_launches": launches, "plan_s": plan_s,
+            "gpu_launches": launches, "plan_s": plan_s, "tuning": tuning,
             "check": {"iters": info.iters, "J0": info.J0, "J": info.J}}
 
     # end to end through the public API with host buffers

@@ -144,18 +144,6 @@ PackInfo make_pack(int Ny) {
   return pk;
 }
 
-std::vector<int4> make_units(const PackInfo& pk) {
-  std::vector<int4> u;
-  long long off = 0;
-  for (int bk = 0; bk < pk.nb; ++bk)
-    for (int bj = 0; bj < bk; ++bj) { u.push_back(make_int4(UNIT_TILE, bj, bk, (int)off)); off += kTileElems; }
-  for (int q = 0; q < (pk.nb + 1) / 2; ++q) {
-    u.push_back(make_int4(UNIT_RECT, 2 * q, 2 * q + 1, (int)off));
-    off += kRectElems;
-  }
-  return u;
-}
-
 // Pivots of the tridiagonal (rho I + D_t'D_t) for the Thomas sweep: with
 // sub/super-diagonal -1, inv_t = 1 / (b_t - inv_{t-1}), b_t = rho + deg_t.
 std::vector<float> thomas_pivots(int Nt, double rho) {
@@ -340,7 +328,6 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
   const size_t nimg = p->nimg();
   const size_t ncols = (size_t)Nx * Nt;
   PC(p->alloc(&p->A, (size_t)p->pk.col_elems * p->esize * ncols));
-  p->h_units = make_units(p->pk);
   PC(p->alloc((void**)&p->sens, (size_t)Nx * Nc * Ny * sizeof(float2)));
   PC(p->alloc((void**)&p->rows, std::max<size_t>(1, p->h_rows.size()) * sizeof(int)));
   PC(p->alloc((void**)&p->rowoff, (Nt + 1) * sizeof(int)));

@@ -116,6 +116,11 @@ struct c16b { __nv_bfloat162 v; };
 template <typename E> struct Elem;
 template <> struct Elem<float2> {
   static constexpr int bytes = 8;
+  // two adjacent elements in one 16-byte load (p 16-byte aligned), not widened
+  __device__ __forceinline__ static void load2raw(const float2* p, float2& a, float2& b) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    a = make_float2(q.x, q.y); b = make_float2(q.z, q.w);
+  }
   __device__ __forceinline__ static float2 widen(float2 v) { return v; }
   __device__ __forceinline__ static float2 load(const float2* p) { return *p; }
   __device__ __forceinline__ static void load2(const float2* p, float2& a, float2& b) {
@@ -127,6 +132,10 @@ template <> struct Elem<float2> {
 };
 template <> struct Elem<__half2> {
   static constexpr int bytes = 4;
+  __device__ __forceinline__ static void load2raw(const __half2* p, __half2& a, __half2& b) {
+    const uint2 q = *reinterpret_cast<const uint2*>(p);
+    a = *reinterpret_cast<const __half2*>(&q.x); b = *reinterpret_cast<const __half2*>(&q.y);
+  }
   __device__ __forceinline__ static float2 widen(__half2 v) { return __half22float2(v); }
   __device__ __forceinline__ static float2 load(const __half2* p) { return __half22float2(*p); }
   __device__ __forceinline__ static void load2(const __half2* p, float2& a, float2& b) {
@@ -141,6 +150,10 @@ template <> struct Elem<__half2> {
 };
 template <> struct Elem<__nv_bfloat162> {
   static constexpr int bytes = 4;
+  __device__ __forceinline__ static void load2raw(const __nv_bfloat162* p, __nv_bfloat162& a, __nv_bfloat162& b) {
+    const uint2 q = *reinterpret_cast<const uint2*>(p);
+    a = *reinterpret_cast<const __nv_bfloat162*>(&q.x); b = *reinterpret_cast<const __nv_bfloat162*>(&q.y);
+  }
   __device__ __forceinline__ static float2 widen(__nv_bfloat162 v) { return __bfloat1622float2(v); }
   __device__ __forceinline__ static float2 load(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
   __device__ __forceinline__ static void load2(const __nv_bfloat162* p, float2& a, float2& b) {

@@ -141,14 +141,13 @@ DftSlice dft_desc(recon_plan* p, int k, int K) {
   return d;
 }
 
-ColSlice col_desc(recon_plan* p, int k, bool fused, int unit_off) {
+ColSlice col_desc(recon_plan* p, int k, bool fused) {
   ColSlice c{};
   c.A = p->A;
   c.col_elems = p->pk.col_elems;
   c.Ny = p->Ny;
   c.nb = p->pk.nb;
   c.nunits = p->pk.nunits;
-  c.unit_off = unit_off;
   c.r_tma = ((size_t)p->Ny * sizeof(float2)) % 16 == 0 ? 1 : 0;
   c.do_obj = fused ? 1 : 0;
   c.mu = p->mu;
@@ -177,11 +176,11 @@ recon_status finish_col_shape(Engine* e, recon_plan* const* plans, int n, int st
   e->nb_max = 0;
   for (int q = 0; q < n; ++q) e->nb_max = std::max(e->nb_max, plans[q]->pk.nb);
   const int es = e->storage ? 4 : 8;
-  const int maxst = col_inverse_max_stages(e->nb_max, e->nunits_all, n, e->work_max, es);
+  const int maxst = col_inverse_max_stages(e->nb_max, n, e->work_max, es);
   const int qn = col_inverse_stage_quantum();
   int st = stages_req > 0 ? std::min(stages_req, maxst) : maxst;
   e->stages = std::max(qn, st / qn * qn);
-  const size_t smem = col_inverse_smem(e->stages, e->nb_max, e->nunits_all, n, e->work_max, es);
+  const size_t smem = col_inverse_smem(e->stages, e->nb_max, n, e->work_max, es);
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -210,19 +209,10 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
     if (p->device != p0->device) return fail(RECON_ERR_INVALID_ARG, "batched plans must be on one device");
   }
   const int K = e->K;
-  // unit tables
-  std::vector<int4> units;
-  std::vector<int> unit_off(n);
-  for (int q = 0; q < n; ++q) {
-    unit_off[q] = (int)units.size();
-    units.insert(units.end(), plans[q]->h_units.begin(), plans[q]->h_units.end());
-  }
-  e->nunits_all = (int)units.size();
-  RC(upload(e->arena, &e->d_units, units));
   // column descriptors, K sets (at least one so the layout is valid at K = 0)
   std::vector<ColSlice> cols((size_t)std::max(K, 1) * n);
   for (int k = 1; k <= std::max(K, 1); ++k)
-    for (int q = 0; q < n; ++q) cols[(size_t)(k - 1) * n + q] = col_desc(plans[q], k, e->fused, unit_off[q]);
+    for (int q = 0; q < n; ++q) cols[(size_t)(k - 1) * n + q] = col_desc(plans[q], k, e->fused);
   RC(upload(e->arena, &e->d_col, cols));
   // temporal descriptors, K+1 sets
   e->Nt_max = 0;
@@ -307,9 +297,7 @@ recon_status engine_build_inverse(Engine* e, recon_plan* p) {
   e->K = 1;
   e->storage = p->storage;
   e->obj = e->fused = false;
-  RC(upload(e->arena, &e->d_units, p->h_units));
-  e->nunits_all = (int)p->h_units.size();
-  ColSlice c = col_desc(p, 1, false, 0);
+  ColSlice c = col_desc(p, 1, false);
   c.base = p->tmp_a;
   c.add = nullptr;
   c.coef = 0.f;
@@ -333,8 +321,6 @@ recon_status launch_col_set(Engine* e, int set, cudaStream_t s) {
   ColLaunch L{};
   L.slices = e->d_col + (size_t)set * e->n;
   L.nslices = e->n;
-  L.units = e->d_units;
-  L.nunits_all = e->nunits_all;
   L.work = e->d_work;
   L.work_off = e->d_work_off;
   L.work_max = e->work_max;

@@ -207,13 +207,6 @@ recon_status recon_grad_create(recon_grad** out, recon_plan* const* plans, int n
         g->arena.alloc((void**)&gs.acc, 4 * sizeof(double)) != cudaSuccess)
       return bail(fail(RECON_ERR_OOM, "gradient buffers"));
   }
-  // unit tables shared by both engines
-  std::vector<int4> units;
-  std::vector<int> unit_off(n);
-  for (int q = 0; q < n; ++q) {
-    unit_off[q] = (int)units.size();
-    units.insert(units.end(), plans[q]->h_units.begin(), plans[q]->h_units.end());
-  }
   std::vector<unsigned> work;
   std::vector<int> off;
   int work_max = 0;
@@ -227,13 +220,10 @@ recon_status recon_grad_create(recon_grad** out, recon_plan* const* plans, int n
     e->storage = plans[0]->storage;
     e->grid = grid;
     e->work_max = work_max;
-    e->nunits_all = (int)units.size();
-    if (e->arena.alloc((void**)&e->d_units, units.size() * sizeof(int4)) != cudaSuccess ||
-        e->arena.alloc((void**)&e->d_work, work.size() * sizeof(unsigned)) != cudaSuccess ||
+    if (e->arena.alloc((void**)&e->d_work, work.size() * sizeof(unsigned)) != cudaSuccess ||
         e->arena.alloc((void**)&e->d_work_off, off.size() * sizeof(int)) != cudaSuccess ||
         e->arena.alloc((void**)&e->d_err, sizeof(int)) != cudaSuccess)
       return bail(fail(RECON_ERR_OOM, "gradient launch data"));
-    cudaMemcpy(e->d_units, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice);
     cudaMemcpy(e->d_work, work.data(), work.size() * sizeof(unsigned), cudaMemcpyHostToDevice);
     cudaMemcpy(e->d_work_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice);
     cudaMemset(e->d_err, 0, sizeof(int));
@@ -278,7 +268,6 @@ recon_status recon_grad_create(recon_grad** out, recon_plan* const* plans, int n
       c.Ny = p->Ny;
       c.nb = p->pk.nb;
       c.nunits = p->pk.nunits;
-      c.unit_off = unit_off[q];
       c.r_tma = ((size_t)p->Ny * sizeof(float2)) % 16 == 0 ? 1 : 0;
       c.mu = p->mu;
       c.stop = nullptr;

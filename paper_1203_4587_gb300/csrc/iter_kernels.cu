@@ -36,11 +36,7 @@ __device__ __forceinline__ void proc_tile(const E* __restrict__ tl, const float2
   // producer while this warp computes
   E el[32];
 #pragma unroll
-  for (int qq = 0; qq < 16; ++qq) {
-    const E* src = tl + qq * 64 + lane * 2;
-    el[2 * qq] = src[0];
-    el[2 * qq + 1] = src[1];
-  }
+  for (int qq = 0; qq < 16; ++qq) Elem<E>::load2raw(tl + qq * 64 + lane * 2, el[2 * qq], el[2 * qq + 1]);
   __syncwarp();
   if (lane == 0) mbar_arrive(release);
   float2 rv[4], cv[8];
@@ -195,11 +191,43 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a -
 
 constexpr int kRSlots = 2;  // double-buffered r inputs / partial sums
 
+// Units of the n-th column a CTA processes are taken in an order rotated by
+// 3n: with few units per column the diagonal-pair units (the slowest, at
+// the end of a column's stream) would otherwise fall on the same consumer
+// warps in every column and set the pace.  Producers and consumers agree on
+// the order; the unit -> warp / stage mapping by position is unchanged.
+__device__ __forceinline__ int unit_rotation(int n, int nunits) { return (int)((3ll * n) % nunits); }
+
+// Unit m of a column with nb blocks, in stream order: {kind, p, q, element
+// offset}.  Off-diagonal tiles (bj, bk), bj < bk, bk-major (an order that
+// does not depend on nb, so one table of (bj | bk << 8) for the largest nb
+// of a launch serves every slice), then the diagonal pairs (2r, 2r+1) (the
+// packed layout of kernels.h).
+__device__ __forceinline__ int tile_pq(int m) {   // the table's entry m, computed once per launch
+  int bk = (int)((1.f + sqrtf(1.f + 8.f * (float)m)) * 0.5f);   // bk(bk-1)/2 <= m < bk(bk+1)/2
+  while (bk * (bk - 1) / 2 > m) --bk;
+  while ((bk + 1) * bk / 2 <= m) ++bk;
+  return (m - bk * (bk - 1) / 2) | (bk << 8);
+}
+__device__ __forceinline__ int4 decode_unit(int m, int nb, const int* tiles) {
+  const int ntiles = nb * (nb - 1) / 2;
+  if (m < ntiles) {
+    const int pq = tiles[m];
+    return make_int4(UNIT_TILE, pq & 0xff, pq >> 8, m * kTileElems);
+  }
+  const int r = m - ntiles;
+  return make_int4(UNIT_RECT, 2 * r, 2 * r + 1, ntiles * kTileElems + r * kRectElems);
+}
+
+__device__ __forceinline__ int rotated_unit(int pos, int rot, int nunits) {
+  const int u = pos + rot;
+  return u >= nunits ? u - nunits : u;
+}
+
 struct ColLayout {
-  size_t bars, ring, ycopy, rvec, bvec, rslot, units, slices, skip, work, total;
+  size_t bars, ring, ycopy, rvec, bvec, rslot, tiles, slices, skip, work, total;
 };
-__host__ __device__ inline ColLayout col_layout(int stages, int nb, int nunits, int nslices, int work_max,
-                                                int esize) {
+__host__ __device__ inline ColLayout col_layout(int stages, int nb, int nslices, int work_max, int esize) {
   ColLayout L;
   const size_t ny32 = (size_t)(nb + 1) * 32;
   size_t o = 0;
@@ -212,7 +240,8 @@ __host__ __device__ inline ColLayout col_layout(int stages, int nb, int nunits, 
   L.rvec = o; o += (size_t)kRSlots * ny32 * 8;
   L.bvec = o; o += (size_t)kRSlots * ny32 * 8;
   L.rslot = o; o += (size_t)kRSlots * 3 * ny32 * 8;   // [slot][base, add, b][ny32]
-  L.units = o; o += (size_t)nunits * 16;
+  L.tiles = o; o += (size_t)(nb * (nb - 1) / 2) * 4;   // (bj | bk << 8) of the off-diagonal tiles
+  o = align_up(o, 16);
   L.slices = o; o += (size_t)nslices * sizeof(ColSlice);
   o = align_up(o, 16);
   L.skip = o; o += (size_t)nslices * 4;
@@ -238,7 +267,7 @@ template <typename E>
 __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int kStage = stage_bytes(Elem<E>::bytes);
-  const ColLayout L = col_layout(P.stages, P.nb_max, P.nunits_all, P.nslices, P.work_max, Elem<E>::bytes);
+  const ColLayout L = col_layout(P.stages, P.nb_max, P.nslices, P.work_max, Elem<E>::bytes);
   const int S = P.stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
   uint64_t* empty = full + S;
@@ -253,13 +282,13 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
   float2* rvec = reinterpret_cast<float2*>(smem + L.rvec);
   float2* bvec = reinterpret_cast<float2*>(smem + L.bvec);
   float2* rslot = reinterpret_cast<float2*>(smem + L.rslot);
-  int4* units = reinterpret_cast<int4*>(smem + L.units);
   ColSlice* sl = reinterpret_cast<ColSlice*>(smem + L.slices);
+  int* tiles = reinterpret_cast<int*>(smem + L.tiles);
   int* skip = reinterpret_cast<int*>(smem + L.skip);
   unsigned* wl = reinterpret_cast<unsigned*>(smem + L.work);   // this CTA's work list
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int u = tid; u < P.nunits_all; u += blockDim.x) units[u] = P.units[u];
+  for (int m = tid; m < P.nb_max * (P.nb_max - 1) / 2; m += blockDim.x) tiles[m] = tile_pq(m);
   for (int q = tid; q < P.nslices; q += blockDim.x) {
     sl[q] = P.slices[q];
     skip[q] = P.slices[q].stop ? *P.slices[q].stop : 0;
@@ -299,18 +328,19 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
       const uint64_t pol = policy_evict_first();
       // stage st of the ring, wraps = completed passes over the ring (no
       // divisions on the issue path)
-      int st = p, wraps = 0, gu = 0, issued = 0;
+      int st = p, wraps = 0, gu = 0, issued = 0, ncolumn = 0;
       bool ok = true;
       for (int w = w0; w < w1 && ok; ++w) {
         if (skip[WSL(w)]) continue;
         const ColSlice& c = sl[WSL(w)];
         const unsigned char* cb = reinterpret_cast<const unsigned char*>(c.A) + (size_t)WCOL(w) * (size_t)c.col_elems * ES;
-        // first unit of this column whose global index is p mod kProducers
+        const int rot = unit_rotation(ncolumn++, c.nunits);
+        // first position of this column whose global index is p mod kProducers
         int u = p - gu % kProducers;
         if (u < 0) u += kProducers;
         for (; u < c.nunits; u += kProducers) {
           if (wraps > 0 && !mbar_wait(&empty[st], (uint32_t)((wraps - 1) & 1), P.err)) { ok = false; break; }
-          const int4 un = units[c.unit_off + u];
+          const int4 un = decode_unit(rotated_unit(u, rot, c.nunits), c.nb, tiles);
           const uint32_t bytes = (uint32_t)((un.x == UNIT_TILE ? kTileElems : kRectElems) * ES);
           mbar_arrive_expect_tx(&full[st], bytes);
           bulk_g2s(ring + (size_t)st * kStage, cb + (size_t)un.w * ES, bytes, &full[st], pol);
@@ -422,18 +452,20 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
       const float2* d = rslot + (size_t)slt * 3 * ny32m;
       float2* rv = rvec + (size_t)(n & 1) * ny32m;
       float2* bv = bvec + (size_t)(n & 1) * ny32m;
-      for (int j = lane; j < ny32; j += 32) {
-        float2 v = make_float2(0.f, 0.f), bb = make_float2(0.f, 0.f);
-        if (j < c.Ny) {
-          v = d[j];
-          bb = sep_b ? d[2 * ny32m + j] : v;
-          if (c.add) {
-            const float2 a = d[ny32m + j];
-            v.x = fmaf(c.coef, a.x, v.x); v.y = fmaf(c.coef, a.y, v.y);
-          }
+      // two elements per lane and 16-byte accesses (all buffers are 16-byte
+      // aligned and ny32 is even); elements past Ny are zero padding
+      for (int j = 2 * lane; j < ny32; j += 64) {
+        float4 v = *reinterpret_cast<const float4*>(d + j);
+        float4 bb = sep_b ? *reinterpret_cast<const float4*>(d + 2 * ny32m + j) : v;
+        if (c.add) {
+          const float4 a = *reinterpret_cast<const float4*>(d + ny32m + j);
+          v.x = fmaf(c.coef, a.x, v.x); v.y = fmaf(c.coef, a.y, v.y);
+          v.z = fmaf(c.coef, a.z, v.z); v.w = fmaf(c.coef, a.w, v.w);
         }
-        rv[j] = v;
-        bv[j] = bb;
+        if (j >= c.Ny) { v.x = v.y = 0.f; bb.x = bb.y = 0.f; }
+        if (j + 1 >= c.Ny) { v.z = v.w = 0.f; bb.z = bb.w = 0.f; }
+        *reinterpret_cast<float4*>(rv + j) = v;
+        *reinterpret_cast<float4*>(bv + j) = bb;
       }
       __syncwarp();
       if (lane == 0) { mbar_arrive(&rempty[slt]); mbar_arrive(&rv_full[n & 1]); }
@@ -466,23 +498,31 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
       // summed per lane over the column in FP32 and added once to the FP64
       // accumulator: w_bx Re<b, x> + w_xr Re<x, r> + w_xx |x|^2
       float fcol = 0.f;
-      for (int j = lane; j < ny32; j += 32) {
-        float2 x = yc[j];
-        yc[j] = make_float2(0.f, 0.f);
+      const bool vec_out = ((cofs & 1) == 0);   // 16-byte aligned pairs of x
+      for (int j = 2 * lane; j < ny32; j += 64) {
+        float4 x = *reinterpret_cast<const float4*>(yc + j);
+        *reinterpret_cast<float4*>(yc + j) = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int w = 1; w < kConsumerWarps; ++w) {
-          x = c_add(x, yc[(size_t)w * ny32m + j]);
-          yc[(size_t)w * ny32m + j] = make_float2(0.f, 0.f);
+          float4* pw = reinterpret_cast<float4*>(yc + (size_t)w * ny32m + j);
+          const float4 t = *pw;
+          x.x += t.x; x.y += t.y; x.z += t.z; x.w += t.w;
+          *pw = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (j < c.Ny) {
-          c.xout[cofs + j] = x;
-          if (c.do_obj) {
-            const float2 r = rv[j], b = bv[j];
-            float f = c.w_bx * fmaf(b.x, x.x, b.y * x.y);
-            f = fmaf(c.w_xr, fmaf(x.x, r.x, x.y * r.y), f);
-            f = fmaf(c.w_xx, fmaf(x.x, x.x, x.y * x.y), f);
-            fcol += f;
-          }
+        if (j + 1 < c.Ny && vec_out) {
+          *reinterpret_cast<float4*>(c.xout + cofs + j) = x;
+        } else {
+          if (j < c.Ny) c.xout[cofs + j] = make_float2(x.x, x.y);
+          if (j + 1 < c.Ny) c.xout[cofs + j + 1] = make_float2(x.z, x.w);
+        }
+        if (c.do_obj) {   // only elements < Ny (r and b are zero past Ny; x need not be)
+          if (j >= c.Ny) x.x = x.y = 0.f;
+          if (j + 1 >= c.Ny) x.z = x.w = 0.f;
+          const float4 r = *reinterpret_cast<const float4*>(rv + j), b = *reinterpret_cast<const float4*>(bv + j);
+          float f = c.w_bx * fmaf(b.x, x.x, fmaf(b.y, x.y, fmaf(b.z, x.z, b.w * x.w)));
+          f = fmaf(c.w_xr, fmaf(x.x, r.x, fmaf(x.y, r.y, fmaf(x.z, r.z, x.w * r.w))), f);
+          f = fmaf(c.w_xx, fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, x.w * x.w))), f);
+          fcol += f;
         }
       }
       fid += (double)fcol;
@@ -518,9 +558,10 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
     const float2* rv = rvec + (size_t)bb * ny32m;
     float2* yw = ycopy + ((size_t)bb * kConsumerWarps + warp) * ny32m;
     bool failed = false;
+    const int rot = unit_rotation(n, c.nunits);
     for (; u < c.nunits; u += kConsumerWarps) {
       if (!mbar_wait(&full[st], ph, P.err)) { failed = true; break; }
-      const int4 un = units[c.unit_off + u];
+      const int4 un = decode_unit(rotated_unit(u, rot, c.nunits), c.nb, tiles);
       const E* tl = reinterpret_cast<const E*>(ring + (size_t)st * kStage);
       if (un.x == UNIT_TILE) proc_tile<E>(tl, rv, yw, un.y, un.z, lane, &empty[st]);
       else proc_rect<E>(tl, rv, yw, un.y, un.z, lane, &empty[st]);
@@ -535,19 +576,19 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
 #undef WCOL
 }
 
-size_t col_inverse_smem(int stages, int nb_max, int nunits_all, int nslices, int work_max, int esize) {
-  return col_layout(stages, nb_max, nunits_all, nslices, work_max, esize).total;
+size_t col_inverse_smem(int stages, int nb_max, int nslices, int work_max, int esize) {
+  return col_layout(stages, nb_max, nslices, work_max, esize).total;
 }
 
 // Largest ring depth that fits, a multiple of the consumer warp count (the
 // parity waits rely on it; see the consumer loop).
-int col_inverse_max_stages(int nb_max, int nunits_all, int nslices, int work_max, int esize) {
+int col_inverse_max_stages(int nb_max, int nslices, int work_max, int esize) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   int s = 8 * kConsumerWarps;
   while (s > kConsumerWarps) {
-    if (col_inverse_smem(s, nb_max, nunits_all, nslices, work_max, esize) + 1024 <= (size_t)optin) break;
+    if (col_inverse_smem(s, nb_max, nslices, work_max, esize) + 1024 <= (size_t)optin) break;
     s -= kConsumerWarps;
   }
   return s;
@@ -577,7 +618,7 @@ cudaError_t prepare_col_inverse(int storage, size_t smem) {
 }
 
 cudaError_t launch_col_inverse(const ColLaunch& p, int storage, int grid, cudaStream_t s) {
-  const size_t smem = col_inverse_smem(p.stages, p.nb_max, p.nunits_all, p.nslices, p.work_max, storage ? 4 : 8);
+  const size_t smem = col_inverse_smem(p.stages, p.nb_max, p.nslices, p.work_max, storage ? 4 : 8);
   cudaError_t e = prepare_col_inverse(storage, smem);
   if (e != cudaSuccess) return e;
   switch (storage) {

@@ -59,7 +59,7 @@ struct ColSlice {            // data-consistency inverse x = A r of one slice
   const void* A;             // packed stream base
   long long col_elems;
   int Ny, nb;
-  int nunits, unit_off;      // this slice's unit table inside ColLaunch::units
+  int nunits;                // units per column (decoded from the index and nb)
   int r_tma;                 // 1: r inputs move by bulk copy (Ny*8 a multiple of 16)
   int do_obj;
   const float2* base;        // r = base + coef * add   ([Nt][Nx][Ny])
@@ -82,8 +82,6 @@ struct ColSlice {            // data-consistency inverse x = A r of one slice
 struct ColLaunch {
   const ColSlice* slices;
   int nslices;
-  const int4* units;         // concatenated unit tables {kind, p, q, elem offset}
-  int nunits_all;
   const unsigned* work;      // (slice << 24) | column, in processing order
   const int* work_off;       // [gridDim.x + 1]: CTA b processes work[work_off[b] .. work_off[b+1])
   int work_max;              // longest per-CTA list (staged in shared memory)
@@ -198,8 +196,8 @@ void set_last_error(const std::string& why);
 // ---- launchers (return cudaGetLastError()) ---------------------------------
 cudaError_t launch_col_inverse(const ColLaunch& p, int storage, int grid, cudaStream_t s);
 // esize: bytes per stored element (8 FP32, 4 FP16/BF16)
-size_t col_inverse_smem(int stages, int nb_max, int nunits_all, int nslices, int work_max, int esize);
-int col_inverse_max_stages(int nb_max, int nunits_all, int nslices, int work_max, int esize);
+size_t col_inverse_smem(int stages, int nb_max, int nslices, int work_max, int esize);
+int col_inverse_max_stages(int nb_max, int nslices, int work_max, int esize);
 int col_inverse_stage_quantum();  // ring depth must be a positive multiple of this
 cudaError_t prepare_tv_temporal(int Nt_max, int px);   // shared-memory attribute, outside any capture
 cudaError_t prepare_dft_temporal(int Nt_max, int px);

@@ -35,8 +35,6 @@ struct Engine {
   int tmp_blocks = 0, Nt_max = 0, tile_px = 0;
   // column-inverse launches: K descriptor sets
   ColSlice* d_col = nullptr;
-  int4* d_units = nullptr;
-  int nunits_all = 0;
   unsigned* d_work = nullptr;
   int* d_work_off = nullptr;
   int grid = 0, nb_max = 0, stages = 0, work_max = 0;
@@ -58,7 +56,6 @@ struct recon_plan {
   int storage = 0;
   size_t esize = 8;
   std::vector<int> h_rows, h_rowoff;
-  std::vector<int4> h_units;
   int maxm = 0, total_rows = 0;
   // device memory
   std::vector<void*> allocs;
