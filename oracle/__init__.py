@@ -13,16 +13,17 @@ Lagrangian and Parallel Processing":
 * complex soft threshold (Section III, definition of S(a, tau))
 * per-column Gram blocks and the exact inverse (mu I + H'H)^{-1}
   (Section IV-C, Eqs. HconjH, separate_x, eigen_mu)
-* Algorithm 1 (synthesis prior, temporal DFT) and Algorithm 2 (analysis prior,
-  temporal TV), step by step in the paper's order
+* Algorithm 1 (synthesis prior, temporal DFT, or the undecimated temporal Haar
+  frame, a redundant tight frame) and Algorithm 2 (analysis prior, temporal
+  TV), step by step in the paper's order
 * objective J and the convergence ratio Delta(k) (Section V, Eq. r_ratio)
 * the reverse-mode gradient of unrolled Algorithm 2 (``grad.py``)
 * the 16-bit storage encoding with per-frame power-of-two scales
   (``precision.py``)
 
 Every function here is pinned by a ``-m "not gpu"`` test in
-``tests/test_oracle_pins.py``, ``tests/test_oracle_grad.py`` and
-``tests/test_oracle_precision.py`` against closed
+``tests/test_oracle_pins.py``, ``tests/test_oracle_grad.py``,
+``tests/test_oracle_frame.py`` and ``tests/test_oracle_precision.py`` against closed
 forms, brute force, finite differences or invariants.
 """
 

@@ -39,7 +39,7 @@ __all__ = [
     "gram_blocks", "inverse_blocks", "ColumnInverse", "tv_D", "tv_Dadj",
     "tv_m_matrix", "data_residual", "data_residual_columns", "objective_tv",
     "objective_dft", "delta_ratio", "admm_analysis_tv", "admm_synthesis_dft",
-    "psi_dft", "psi_dft_adj", "Problem", "make_problem",
+    "psi_dft", "psi_dft_adj", "psi_haar", "psi_haar_adj", "Problem", "make_problem",
 ]
 
 
@@ -219,6 +219,41 @@ def psi_dft_adj(w):
     return np.fft.ifft(w, axis=0, norm="ortho")
 
 
+def psi_haar(x, levels):
+    """Undecimated temporal Haar frame (a redundant tight frame, Psi'Psi = I).
+
+    Along t with circular shifts: a_0 = x and, for level j = 1..levels with
+    shift s = 2^(j-1) (mod Nt),
+        a_j[t] = (a_{j-1}[t] + a_{j-1}[t+s]) / 2,   d_j[t] = (a_{j-1}[t] - a_{j-1}[t+s]) / 2.
+    Coefficients stacked as [d_1, ..., d_levels, a_levels] on a new axis 0.
+    Section IV-A allows any tight frame for Psi; this is one with
+    Psi Psi' != I, so the (1/mu)(I - Psi Psi') term of the lemma is active.
+    """
+    a = np.asarray(x, dtype=np.complex128)
+    Nt = a.shape[0]
+    out = []
+    for j in range(1, levels + 1):
+        sh = (2 ** (j - 1)) % Nt
+        nxt = np.roll(a, -sh, axis=0)              # nxt[t] = a[t + s]
+        out.append((a - nxt) / 2.0)
+        a = (a + nxt) / 2.0
+    out.append(a)
+    return np.stack(out)
+
+
+def psi_haar_adj(w, levels):
+    """Synthesis Psi' of ``psi_haar`` (its adjoint; psi_haar_adj(psi_haar(x)) = x)."""
+    w = np.asarray(w, dtype=np.complex128)
+    Nt = w.shape[1]
+    a = w[levels].copy()
+    for j in range(levels, 0, -1):
+        sh = (2 ** (j - 1)) % Nt
+        d = w[j - 1]
+        # adjoint of a -> ((a + S a)/2, (a - S a)/2) with (S a)[t] = a[t + s]
+        a = (a + np.roll(a, sh, axis=0)) / 2.0 + (d - np.roll(d, sh, axis=0)) / 2.0
+    return a
+
+
 # ---------------------------------------------------------------------------
 # Algorithm 2: ADMM for the analysis prior (R = D_t, temporal TV)
 # ---------------------------------------------------------------------------
@@ -320,12 +355,17 @@ class Problem:
     def fid(self, x_cols):
         return data_residual_columns(x_cols, self.yhat, self.sens, self.mask, self.cols)
 
-    def solve(self, prior, lam, mu, rho=0.5, iters=50, tol=0.0, objective=True):
+    def solve(self, prior, lam, mu, rho=0.5, iters=50, tol=0.0, objective=True, levels=2):
+        """prior: "tv" (Algorithm 2), "dft" (Algorithm 1, unitary temporal DFT) or
+        "haar" (Algorithm 1, undecimated temporal Haar frame of ``levels`` levels)."""
         fid = self.fid if objective else None
         if prior == "tv":
             return admm_analysis_tv(self.b, self.inv, lam, mu, rho, iters, fid=fid, tol=tol)
         if prior == "dft":
             return admm_synthesis_dft(self.b, self.inv, lam, mu, iters, fid=fid, tol=tol)
+        if prior == "haar":
+            return admm_synthesis_dft(self.b, self.inv, lam, mu, iters, fid=fid, tol=tol,
+                                      psi=lambda z: psi_haar(z, levels), psi_adj=lambda z: psi_haar_adj(z, levels))
         raise ValueError(prior)
 
 
