@@ -49,8 +49,15 @@ extern "C" {
 typedef struct recon_plan recon_plan; /* opaque, owned by the library */
 
 typedef enum {
-  RECON_PRIOR_TV = 0,  /* Algorithm 2: analysis prior, R = D_t (non-circular temporal differences) */
-  RECON_PRIOR_DFT = 1  /* Algorithm 1: synthesis prior, Psi = unitary temporal DFT */
+  RECON_PRIOR_TV = 0,   /* Algorithm 2: analysis prior, R = D_t (non-circular temporal differences) */
+  RECON_PRIOR_DFT = 1,  /* Algorithm 1: synthesis prior, Psi = unitary temporal DFT */
+  RECON_PRIOR_HAAR = 2  /* Algorithm 1: synthesis prior, Psi = undecimated temporal Haar frame of
+                           opts.frame_levels levels with circular shifts: a_0 = x and for level j
+                           (shift s = 2^(j-1) mod Nt) a_j[t] = (a_{j-1}[t] + a_{j-1}[t+s]) / 2,
+                           d_j[t] = (a_{j-1}[t] - a_{j-1}[t+s]) / 2; coefficients d_1..d_L, a_L.
+                           A redundant tight frame (Psi'Psi = I, Psi Psi' != I): the w-update
+                           keeps the (1/mu)(I - Psi Psi') term of the lemma in Section IV-A,
+                           w = u + Psi (A (H'y + mu Psi'u) - Psi'u) with u = v + d. */
 } recon_prior;
 
 typedef enum {
@@ -96,6 +103,7 @@ typedef struct {
   int col_stages;   /* ring depth of the inverse kernel, rounded down to a multiple of 8
                        (min 8) and capped by shared memory; 0 = deepest that fits (default) */
   int profile;      /* 1 = time every kernel of a solve with CUDA events (default 0) */
+  int frame_levels; /* levels L of RECON_PRIOR_HAAR, 1..6 (default 2); the frame has L+1 channels */
 } recon_opts;
 
 typedef struct {

@@ -99,6 +99,7 @@ void recon_default_opts(recon_opts* o) {
   o->mask_full = 0;
   o->col_stages = 0;
   o->profile = 0;
+  o->frame_levels = 2;
 }
 
 const char* recon_status_string(recon_status s) {
@@ -267,12 +268,13 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
   if (!valid_ptr(mask) || !valid_ptr(sens)) return fail(RECON_ERR_INVALID_ARG, "mask or sens is NULL");
   if (!(mu > 0.f) || !std::isfinite(mu)) return fail(RECON_ERR_INVALID_ARG, "mu must be > 0");
   if (!(lambda >= 0.f) || !std::isfinite(lambda)) return fail(RECON_ERR_INVALID_ARG, "lambda must be >= 0");
-  if (prior != RECON_PRIOR_TV && prior != RECON_PRIOR_DFT) return fail(RECON_ERR_INVALID_ARG, "unknown prior");
+  if (prior != RECON_PRIOR_TV && prior != RECON_PRIOR_DFT && prior != RECON_PRIOR_HAAR)
+    return fail(RECON_ERR_INVALID_ARG, "unknown prior");
   recon_opts o;
   recon_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.rho > 0.f) || o.max_iters < 0 || !(o.tol >= 0.0) || o.storage < 0 || o.storage > 2 || o.col_stages < 0 ||
-      o.objective < 0 || o.objective > 2)
+      o.objective < 0 || o.objective > 2 || (prior == RECON_PRIOR_HAAR && (o.frame_levels < 1 || o.frame_levels > 6)))
     return fail(RECON_ERR_INVALID_ARG, "invalid options");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
@@ -347,15 +349,18 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
     PC(p->alloc((void**)&p->yscale, Nt * sizeof(float)));
   }
   PC(p->alloc((void**)&p->b, nimg * sizeof(float2)));
+  // TV: m, d1, p;  DFT: u = v + d;  Haar: u ((L+1) channels) and s = Psi'u
+  const size_t nu = (prior == RECON_PRIOR_HAAR) ? (size_t)(o.frame_levels + 1) * nimg : nimg;
   for (int k = 0; k < 2; ++k) {
-    PC(p->alloc((void**)&p->s0[k], nimg * sizeof(float2)));
+    PC(p->alloc((void**)&p->s0[k], nu * sizeof(float2)));
     if (prior == RECON_PRIOR_TV) {
       PC(p->alloc((void**)&p->s1[k], nimg * sizeof(float2)));
       PC(p->alloc((void**)&p->s2[k], nimg * sizeof(float2)));
     }
+    if (prior == RECON_PRIOR_HAAR) PC(p->alloc((void**)&p->s1[k], nimg * sizeof(float2)));
   }
   PC(p->alloc((void**)&p->x, nimg * sizeof(float2)));
-  if (prior == RECON_PRIOR_DFT) PC(p->alloc((void**)&p->r, nimg * sizeof(float2)));
+  if (prior != RECON_PRIOR_TV) PC(p->alloc((void**)&p->r, nimg * sizeof(float2)));
   PC(p->alloc((void**)&p->tmp_a, nimg * sizeof(float2)));
   PC(p->alloc((void**)&p->tmp_b, std::max<size_t>(nimg, (size_t)p->total_rows * Nx * Nc) * sizeof(float2)));
   const size_t nt = (size_t)o.max_iters + 2;

@@ -120,7 +120,7 @@ recon_status prepare_buffers(recon_plan* p, cudaStream_t s) {
 recon_status tune_engine(Engine* e, cudaStream_t s, recon_tuning* t) {
   if (e->K < 1) return RECON_OK;
   int cand[4];
-  const int nc = e->tv ? tv_tile_candidates(e->Nt_max, cand) : dft_tile_candidates(e->Nt_max, cand);
+  const int nc = engine_tile_candidates(e, cand);
   int best_px = e->tile_px;
   float best = 3.4e38f;
   for (int i = 0; i < nc; ++i) {

@@ -141,6 +141,38 @@ DftSlice dft_desc(recon_plan* p, int k, int K) {
   return d;
 }
 
+HaarSlice haar_desc(recon_plan* p, int k, int K) {
+  HaarSlice d{};
+  d.Nt = p->Nt;
+  d.npix = (long long)p->npix();
+  d.levels = p->opts.frame_levels;
+  d.b = p->b;
+  d.tau = (float)(p->lam / (2.0 * p->mu));
+  d.mu = p->mu;
+  d.stop = p->flags + FLAG_STOP;
+  if (k <= K) {
+    const int in = (k - 1) & 1, out = k & 1;
+    d.xh = (k == 1) ? p->b : p->x;
+    d.u = (k == 1) ? nullptr : p->s0[in];
+    d.s = (k == 1) ? nullptr : p->s1[in];
+    d.first = (k == 1);
+    d.u_out = p->s0[out];
+    d.s_out = p->s1[out];
+    d.r_out = p->r;
+    d.write_state = 1;
+    d.prior_acc = p->trace_prior + (k - 1);
+  } else {       // final: only ||w_K||_1 with w_K = u + Psi(xhat - Psi'u)
+    const int in = K & 1;
+    d.xh = (K == 0) ? p->b : p->x;
+    d.u = (K == 0) ? nullptr : p->s0[in];
+    d.s = (K == 0) ? nullptr : p->s1[in];
+    d.first = (K == 0);
+    d.write_state = 0;
+    d.prior_acc = p->trace_prior + K;
+  }
+  return d;
+}
+
 ColSlice col_desc(recon_plan* p, int k, bool fused) {
   ColSlice c{};
   c.A = p->A;
@@ -197,13 +229,16 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
   e->plans.assign(plans, plans + n);
   e->n = n;
   e->K = p0->opts.max_iters;
+  e->prior = p0->prior;
   e->tv = p0->prior == RECON_PRIOR_TV;
+  e->levels = p0->opts.frame_levels;
   e->storage = p0->storage;
   e->obj = p0->opts.objective != 0 || p0->opts.tol > 0.0;
   e->fused = e->obj && p0->opts.objective != 2 && p0->storage == 0;
   for (int q = 1; q < n; ++q) {
     const recon_plan* p = plans[q];
     if (p->prior != p0->prior || p->opts.max_iters != e->K || p->storage != e->storage ||
+        (p->prior == RECON_PRIOR_HAAR && p->opts.frame_levels != p0->opts.frame_levels) ||
         (p->opts.objective != 0 || p->opts.tol > 0.0) != e->obj || (p->opts.objective == 2) != (p0->opts.objective == 2))
       return fail(RECON_ERR_INVALID_ARG, "batched plans must share prior, max_iters, storage and objective mode");
     if (p->device != p0->device) return fail(RECON_ERR_INVALID_ARG, "batched plans must be on one device");
@@ -218,7 +253,7 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
   e->Nt_max = 0;
   for (int q = 0; q < n; ++q) e->Nt_max = std::max(e->Nt_max, plans[q]->Nt);
   // a single plan uses its own tuning; a batch starts from the default (recon_batch_autotune)
-  const int px = (n == 1 && p0->tile_px > 0) ? p0->tile_px : (e->tv ? tv_tile_px(e->Nt_max) : dft_tile_px());
+  const int px = (n == 1 && p0->tile_px > 0) ? p0->tile_px : engine_default_tile(e);
   recon_status st = engine_set_tile(e, px);
   if (st != RECON_OK) return st;
   // finalize descriptors
@@ -251,11 +286,23 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
                           (n == 1 && p0->col_stages_tuned > 0) ? p0->col_stages_tuned : p0->opts.col_stages);
 }
 
+int engine_tile_candidates(const Engine* e, int* out) {
+  if (e->tv) return tv_tile_candidates(e->Nt_max, out);
+  if (e->prior == RECON_PRIOR_HAAR) return haar_tile_candidates(e->Nt_max, e->levels, out);
+  return dft_tile_candidates(e->Nt_max, out);
+}
+
+int engine_default_tile(const Engine* e) {
+  if (e->tv) return tv_tile_px(e->Nt_max);
+  if (e->prior == RECON_PRIOR_HAAR) return haar_tile_px(e->Nt_max, e->levels);
+  return dft_tile_px();
+}
+
 // (Re)builds the K+1 temporal descriptor sets for tiles of `px` pixels.
 recon_status engine_set_tile(Engine* e, int px) {
   const int K = e->K, n = e->n;
   int cand[4];
-  const int nc = e->tv ? tv_tile_candidates(e->Nt_max, cand) : dft_tile_candidates(e->Nt_max, cand);
+  const int nc = engine_tile_candidates(e, cand);
   if (std::find(cand, cand + nc, px) == cand + nc) return fail(RECON_ERR_INVALID_ARG, "temporal tile width does not fit");
   std::vector<int> tile0(n);
   int blocks = 0;
@@ -274,6 +321,16 @@ recon_status engine_set_tile(Engine* e, int px) {
       }
     RC(upload(e->arena, reinterpret_cast<TvSlice**>(&e->d_tmp), t));
     RC(prepare_tv_temporal(e->Nt_max, px));
+  } else if (e->prior == RECON_PRIOR_HAAR) {
+    std::vector<HaarSlice> t((size_t)(K + 1) * n);
+    for (int k = 1; k <= K + 1; ++k)
+      for (int q = 0; q < n; ++q) {
+        HaarSlice d = haar_desc(e->plans[q], k, K);
+        d.tile0 = tile0[q];
+        t[(size_t)(k - 1) * n + q] = d;
+      }
+    RC(upload(e->arena, reinterpret_cast<HaarSlice**>(&e->d_tmp), t));
+    RC(prepare_haar_temporal(e->Nt_max, e->levels, px));
   } else {
     std::vector<DftSlice> t((size_t)(K + 1) * n);
     for (int k = 1; k <= K + 1; ++k)
@@ -340,6 +397,9 @@ recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s) {
   if (e->tv) {
     L.slices = static_cast<TvSlice*>(e->d_tmp) + (size_t)set * e->n;
     RC(launch_tv_temporal(L, s));
+  } else if (e->prior == RECON_PRIOR_HAAR) {
+    L.slices = static_cast<HaarSlice*>(e->d_tmp) + (size_t)set * e->n;
+    RC(launch_haar_temporal(L, e->levels, s));
   } else {
     L.slices = static_cast<DftSlice*>(e->d_tmp) + (size_t)set * e->n;
     RC(launch_dft_temporal(L, s));

@@ -902,6 +902,172 @@ cudaError_t launch_dft_temporal(const TemporalLaunch& p, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// Algorithm 1 with the undecimated temporal Haar frame (a redundant tight
+// frame; Section IV-A's lemma with its (1/mu)(I - Psi Psi') term), on a tile
+// of PX pixels x Nt frames held in shared memory:
+//   w = u_prev + Psi (xhat - Psi'u_prev)   (w = Psi b at k = 1)
+//   d = u_prev - w (0 at k = 1);  v = S(w - d, lambda/(2 mu));  u = v + d
+//   s = Psi'u;  r = b + mu s  (the inverse step then gives xhat = A r)
+// Psi: a_0 = z, a_j[t] = (a_{j-1}[t] + a_{j-1}[t+s]) / 2,
+//      d_j[t] = (a_{j-1}[t] - a_{j-1}[t+s]) / 2 with s = 2^(j-1) mod Nt;
+// Psi': a_{j-1}[t] = (a_j[t] + a_j[t-s]) / 2 + (d_j[t] - d_j[t-s]) / 2.
+// Also accumulates ||w||_1 (the prior term of J).
+// ---------------------------------------------------------------------------
+static size_t haar_smem(int Nt_max, int levels, int px) {
+  return (size_t)(levels + 3) * Nt_max * px * sizeof(float2);   // L+1 channels, two approximations
+}
+int haar_tile_candidates(int Nt_max, int levels, int* out) {
+  int n = 0;
+  for (int px : {16, 32, 64})
+    if (haar_smem(Nt_max, levels, px) + 1024 <= kSmemOptin) out[n++] = px;
+  return n;
+}
+int haar_tile_px(int Nt_max, int levels) {
+  int c[4];
+  const int n = haar_tile_candidates(Nt_max, levels, c);
+  for (int i = n - 1; i >= 0; --i)
+    if (c[i] <= 32) return c[i];
+  return n ? c[0] : 16;
+}
+
+template <int PX>
+__global__ void __launch_bounds__(256) k_haar_temporal(TemporalLaunch L, int levels) {
+  extern __shared__ __align__(16) float2 sm_h[];
+  __shared__ double red[32];
+  const HaarSlice* sls = static_cast<const HaarSlice*>(L.slices);
+  const HaarSlice& P = sls[find_slice(sls, L.nslices, (int)blockIdx.x)];
+  if (P.stop && *P.stop) return;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int Nt = P.Nt, T = Nt * PX, nch = levels + 1;
+  const long long N = P.npix;
+  const long long pix0 = (long long)(blockIdx.x - P.tile0) * PX;
+  const int npx = (int)min((long long)PX, N - pix0);
+  float2* W = sm_h;                          // [L+1][Nt][PX] channels
+  float2* A0 = W + (size_t)nch * T;          // approximations (ping-pong)
+  float2* A1 = A0 + T;
+  const BlockBar bar;
+  // z = xhat - Psi'u_prev (b at k = 1)
+  for (int idx = tid; idx < T; idx += nth) {
+    const int t = idx / PX, pp = idx - t * PX;
+    float2 z = make_float2(0.f, 0.f);
+    if (pp < npx) {
+      const long long g = t * N + pix0 + pp;
+      z = P.first ? P.b[g] : c_sub(P.xh[g], P.s[g]);
+    }
+    A0[idx] = z;
+  }
+  bar();
+  // analysis into W
+  float2* a = A0;
+  float2* an = A1;
+  int sh = 1 % Nt;
+  for (int j = 1; j <= levels; ++j) {
+    for (int idx = tid; idx < T; idx += nth) {
+      const int t = idx / PX, pp = idx - t * PX;
+      int tn = t + sh;
+      if (tn >= Nt) tn -= Nt;
+      const float2 cur = a[idx], nxt = a[tn * PX + pp];
+      W[(size_t)(j - 1) * T + idx] = c_scale(c_sub(cur, nxt), 0.5f);
+      an[idx] = c_scale(c_add(cur, nxt), 0.5f);
+    }
+    bar();
+    float2* tmp = a; a = an; an = tmp;
+    sh = (2 * sh) % Nt;
+  }
+  for (int idx = tid; idx < T; idx += nth) W[(size_t)levels * T + idx] = a[idx];
+  bar();
+  // w, ||w||_1, the v- and d-updates
+  double l1 = 0.0;
+  const size_t NU = (size_t)Nt * N;          // one channel of u in global memory
+  for (int idx = tid; idx < nch * T; idx += nth) {
+    const int c = idx / T, rem = idx - c * T;
+    const int t = rem / PX, pp = rem - t * PX;
+    float2 uo = make_float2(0.f, 0.f);
+    if (pp < npx) {
+      const size_t g = (size_t)c * NU + (size_t)t * N + pix0 + pp;
+      const float2 up = P.first ? make_float2(0.f, 0.f) : P.u[g];
+      const float2 w = c_add(up, W[idx]);
+      l1 += (double)c_abs(w);
+      if (P.write_state) {
+        const float2 d = P.first ? make_float2(0.f, 0.f) : c_sub(up, w);
+        const float2 v = c_soft(c_sub(w, d), P.tau);
+        uo = c_add(v, d);
+        P.u_out[g] = uo;
+      }
+    }
+    W[idx] = uo;
+  }
+  bar();
+  if (P.write_state) {
+    // synthesis s = Psi'u from the channels now holding u
+    a = A0;
+    an = A1;
+    for (int idx = tid; idx < T; idx += nth) a[idx] = W[(size_t)levels * T + idx];
+    int shl = 1 % Nt;
+    for (int j = 1; j < levels; ++j) shl = (2 * shl) % Nt;   // shift of level L
+    bar();
+    for (int j = levels; j >= 1; --j) {
+      const float2* dj = W + (size_t)(j - 1) * T;
+      for (int idx = tid; idx < T; idx += nth) {
+        const int t = idx / PX, pp = idx - t * PX;
+        int tp = t - shl;
+        if (tp < 0) tp += Nt;
+        const int jdx = tp * PX + pp;
+        const float2 lo = c_scale(c_add(a[idx], a[jdx]), 0.5f);
+        const float2 hi = c_scale(c_sub(dj[idx], dj[jdx]), 0.5f);
+        an[idx] = c_add(lo, hi);
+      }
+      bar();
+      float2* tmp = a; a = an; an = tmp;
+      // shift of level j-1 (2^(j-2) mod Nt), recomputed from 1 to stay exact mod Nt
+      shl = 1 % Nt;
+      for (int k = 1; k < j - 1; ++k) shl = (2 * shl) % Nt;
+    }
+    const float ms = P.mu;
+    for (int idx = tid; idx < T; idx += nth) {
+      const int t = idx / PX, pp = idx - t * PX;
+      if (pp < npx) {
+        const long long g = t * N + pix0 + pp;
+        const float2 sv = a[idx], bb = P.b[g];
+        P.s_out[g] = sv;
+        P.r_out[g] = make_float2(fmaf(ms, sv.x, bb.x), fmaf(ms, sv.y, bb.y));
+      }
+    }
+  }
+  const double sum = group_sum(l1, red, tid, nth, bar);
+  if (tid == 0) atomicAdd(P.prior_acc, sum);
+}
+
+cudaError_t prepare_haar_temporal(int Nt_max, int levels, int px) {
+  static size_t configured[3] = {0, 0, 0};
+  const size_t smem = haar_smem(Nt_max, levels, px);
+  const int k = px == 16 ? 0 : px == 32 ? 1 : px == 64 ? 2 : -1;
+  if (k < 0 || smem + 1024 > kSmemOptin) return cudaErrorInvalidValue;
+  if (smem > configured[k]) {
+    cudaError_t e = cudaSuccess;
+    if (px == 16) e = cudaFuncSetAttribute(k_haar_temporal<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (px == 32) e = cudaFuncSetAttribute(k_haar_temporal<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (px == 64) e = cudaFuncSetAttribute(k_haar_temporal<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured[k] = smem;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_haar_temporal(const TemporalLaunch& p, int levels, cudaStream_t s) {
+  cudaError_t e = prepare_haar_temporal(p.Nt_max, levels, p.tile_px);
+  if (e != cudaSuccess) return e;
+  const size_t smem = haar_smem(p.Nt_max, levels, p.tile_px);
+  switch (p.tile_px) {
+    case 16: k_haar_temporal<16><<<p.nblocks, 256, smem, s>>>(p, levels); break;
+    case 32: k_haar_temporal<32><<<p.nblocks, 256, smem, s>>>(p, levels); break;
+    default: k_haar_temporal<64><<<p.nblocks, 256, smem, s>>>(p, levels); break;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // ||y - H x||^2 of a whole field, one block per column.
 // ---------------------------------------------------------------------------
 template <class YE>

@@ -127,8 +127,28 @@ struct DftSlice {            // temporal step of Algorithm 1 (Psi = temporal DFT
   int tile0;
 };
 
+struct HaarSlice {           // temporal step of Algorithm 1 with the undecimated Haar frame, one slice
+  int Nt;
+  long long npix;
+  int levels;                // L; L + 1 coefficient channels
+  const float2* xh;          // xhat = A r of the previous iteration (b at k = 1)
+  const float2* u;           // u = v + d of the previous iteration, [L+1][Nt][npix] (unused at k = 1)
+  const float2* s;           // Psi'u of the previous iteration (unused at k = 1)
+  const float2* b;
+  float2* u_out;
+  float2* s_out;             // Psi'u
+  float2* r_out;             // r = b + mu Psi'u
+  float tau;                 // lambda / (2 mu)
+  float mu;
+  int first;                 // k == 1: w = Psi b, d = 0
+  int write_state;           // 0: only ||w||_1 of the final w
+  double* prior_acc;         // += ||w||_1
+  const int* stop;
+  int tile0;
+};
+
 struct TemporalLaunch {      // one launch over the tiles of several slices
-  const void* slices;        // TvSlice[] or DftSlice[]
+  const void* slices;        // TvSlice[], DftSlice[] or HaarSlice[]
   int nslices;
   int nblocks;
   int Nt_max;                // shared-memory sizing
@@ -208,6 +228,10 @@ int tv_tile_candidates(int Nt_max, int* out);       // tile widths that fit (<= 
 int dft_tile_candidates(int Nt_max, int* out);
 cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s);
 cudaError_t launch_dft_temporal(const TemporalLaunch& p, cudaStream_t s);
+cudaError_t launch_haar_temporal(const TemporalLaunch& p, int levels, cudaStream_t s);
+cudaError_t prepare_haar_temporal(int Nt_max, int levels, int px);
+int haar_tile_px(int Nt_max, int levels);
+int haar_tile_candidates(int Nt_max, int levels, int* out);
 cudaError_t launch_objective(const ObjParams& p, cudaStream_t s);
 // per slice: J(k) = fid[k] + (yy ? *yy : 0) + lambda prior[k]; Delta(k); stop flag.
 cudaError_t launch_finalize(const FinSlice* fins, int nslices, int k, cudaStream_t s);

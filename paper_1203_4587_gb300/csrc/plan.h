@@ -26,7 +26,9 @@ struct Engine {
   std::vector<recon_plan*> plans;
   int n = 0;               // number of slices
   int K = 0;               // iterations (the same for every slice)
-  bool tv = true;          // prior (the same for every slice)
+  bool tv = true;          // prior is TV (the same for every slice)
+  recon_prior prior = RECON_PRIOR_TV;
+  int levels = 0;          // frame levels of the Haar prior
   bool fused = false;      // objective data term inside the inverse kernel
   bool obj = false;        // objective on
   int storage = 0;
@@ -72,11 +74,11 @@ struct recon_plan {
   unsigned* ymax = nullptr;            // [Nt] largest |component| of the hybrid data (float bits)
   float* yscale = nullptr;             // [Nt] power-of-two frame scales of yhat_lp
   float2* b = nullptr;
-  float2* s0[2] = {nullptr, nullptr};  // TV: m;  DFT: u
-  float2* s1[2] = {nullptr, nullptr};  // TV: d1
+  float2* s0[2] = {nullptr, nullptr};  // TV: m;  DFT: u;  Haar: u, [L+1][Nt][Nx][Ny]
+  float2* s1[2] = {nullptr, nullptr};  // TV: d1;  Haar: s = Psi'u
   float2* s2[2] = {nullptr, nullptr};  // TV: p
-  float2* x = nullptr;                 // TV: x; DFT: xhat
-  float2* r = nullptr;                 // DFT: r
+  float2* x = nullptr;                 // TV: x; DFT, Haar: xhat
+  float2* r = nullptr;                 // DFT, Haar: r
   float2* tmp_a = nullptr;             // operator entry points
   float2* tmp_b = nullptr;
   float2* kstage = nullptr;            // host-solve staging
@@ -149,6 +151,8 @@ recon_status launch_col_set(Engine* e, int set, cudaStream_t s);   // descriptor
 recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s);   // descriptor set `set` of d_tmp
 recon_status engine_build(Engine* e, recon_plan* const* plans, int n);
 recon_status engine_set_tile(Engine* e, int px);   // temporal tile width (rebuilds its descriptor sets)
+int engine_tile_candidates(const Engine* e, int* out);   // temporal tile widths that fit
+int engine_default_tile(const Engine* e);
 recon_status engine_build_inverse(Engine* e, recon_plan* p);   // tmp_a -> tmp_b, no objective
 // Resets traces/flags, J(0), K iterations and the final prior term of every
 // slice (prologues must have run).  `profile` records the plan's events (n = 1).
