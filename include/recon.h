@@ -135,6 +135,39 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
                                const float* sens, float lambda, float mu, recon_prior prior,
                                const recon_opts* opts, void* stream);
 
+/* ---- sequential reconstruction along the horizontal axis ---------------------
+ * Every step of the method is separable over the image columns i once the
+ * k-space rows are inverse-transformed along x (Section IV-C), so a problem
+ * can be solved a slab of columns at a time with the memory of one slab's
+ * inverses (Section V notes this remedy for the memory of the inverses).
+ *
+ * A slab plan covers columns i0 .. i0+width-1 of an Nx-wide problem.  It
+ * takes the same arguments as recon_plan_create (mask, sens and, at solve
+ * time, kspace and image are the whole Nx-wide arrays) and builds only its
+ * columns' inverses.  Its solve reads the whole k-space rows (row IFFTs over
+ * the full width, its columns kept), iterates on its columns and writes only
+ * those columns of `image`.  J(k) and the stopping test are the slab's own:
+ * J of the whole problem is the sum over slabs.  recon_apply_adjoint /
+ * recon_apply_forward and recon_grad_* need whole plans (UNSUPPORTED);
+ * recon_apply_inverse and recon_export_inverse use the slab's columns (the
+ * column index of recon_export_inverse is relative to i0).  Errors: as
+ * recon_plan_create; INVALID_ARG when the slab leaves the image. */
+recon_status recon_plan_create_slab(recon_plan** out, int Nx, int Ny, int Nt, int Nc, const uint8_t* mask,
+                                    const float* sens, float lambda, float mu, recon_prior prior,
+                                    const recon_opts* opts, int i0, int width, void* stream);
+
+/* Solves the whole problem slab after slab (slabs of `width` columns, the last
+ * one narrower), holding one slab plan at a time: peak memory is one slab's
+ * inverses plus the k-space and image.  kspace and image are device arrays as
+ * for recon_solve.  J_trace (host, max_iters + 1 entries, may be NULL)
+ * receives the sum over slabs of J(k) (meaningful with tol = 0: with a
+ * tolerance each slab stops on its own); info (host, may be NULL) gets the
+ * largest iteration count and the summed J, J0.  Synchronises `stream`.  Each
+ * slab's plan (its factorisation) is built inside the call. */
+recon_status recon_solve_slabs(int Nx, int Ny, int Nt, int Nc, const uint8_t* mask, const float* sens, float lambda,
+                               float mu, recon_prior prior, const recon_opts* opts, int width, const float* kspace,
+                               float* image, double* J_trace, recon_info* info, void* stream);
+
 /* Runs the reconstruction: H'y prologue (batched row/column IFFTs and coil
  * combine), K ADMM iterations, and writes the image.
  *   kspace  device complex64 [Nt][Nc][Ny][Nx]; entries on unsampled rows are ignored

@@ -35,7 +35,8 @@ EXPORTS = ["recon_default_opts", "recon_plan_create", "recon_solve", "recon_solv
            "recon_get_profile", "recon_kernel_launches", "recon_gram_inverse_noalloc",
            "recon_batch_create", "recon_batch_solve", "recon_batch_info", "recon_batch_destroy",
            "recon_grad_create", "recon_grad_forward", "recon_grad_backward", "recon_grad_destroy",
-           "recon_solve_kspace", "recon_quantize_kspace", "recon_autotune", "recon_batch_autotune"]
+           "recon_solve_kspace", "recon_quantize_kspace", "recon_autotune", "recon_batch_autotune",
+           "recon_plan_create_slab", "recon_solve_slabs"]
 
 
 class Opts(C.Structure):
@@ -136,6 +137,11 @@ def load(path: str = LIB_PATH):
     lib.recon_solve_kspace.restype = i
     lib.recon_quantize_kspace.argtypes = [i, i, i, i, fp, i, vp, fp, vp]
     lib.recon_quantize_kspace.restype = i
+    lib.recon_plan_create_slab.argtypes = [C.POINTER(vp), i, i, i, i, vp, fp, f, f, i, C.POINTER(Opts), i, i, vp]
+    lib.recon_plan_create_slab.restype = i
+    lib.recon_solve_slabs.argtypes = [i, i, i, i, vp, fp, f, f, i, C.POINTER(Opts), i, fp, fp, C.POINTER(d),
+                                      C.POINTER(Info), vp]
+    lib.recon_solve_slabs.restype = i
     lib.recon_autotune.argtypes = [vp, C.POINTER(Tuning), vp]
     lib.recon_autotune.restype = i
     lib.recon_batch_autotune.argtypes = [vp, C.POINTER(Tuning), vp]
@@ -181,7 +187,8 @@ def default_opts(**over) -> Opts:
 class Plan:
     """Owns one ``recon_plan``: geometry, sensitivities, mask and the packed inverses."""
 
-    def __init__(self, mask, sens, lam, mu, prior="tv", stream=None, **opts):
+    def __init__(self, mask, sens, lam, mu, prior="tv", stream=None, slab=None, **opts):
+        """slab=(i0, width): a plan over columns i0 .. i0+width-1 (recon_plan_create_slab)."""
         lib = load()
         sens = _c64(sens, "cuda")
         Nc, Ny, Nx = sens.shape
@@ -194,10 +201,16 @@ class Plan:
         self.prior, self.lam, self.mu, self.opts = prior, float(lam), float(mu), o
         self._h = C.c_void_p()
         mdev = mask.cuda() if mask.device.type != "cuda" else mask
-        st = lib.recon_plan_create(C.byref(self._h), int(Nx), int(Ny), int(Nt), int(Nc), _ptr(mdev), _ptr(sens),
-                                   float(lam), float(mu), PRIOR[prior], C.byref(o), _stream(stream))
+        if slab is None:
+            st = lib.recon_plan_create(C.byref(self._h), int(Nx), int(Ny), int(Nt), int(Nc), _ptr(mdev), _ptr(sens),
+                                       float(lam), float(mu), PRIOR[prior], C.byref(o), _stream(stream))
+        else:
+            st = lib.recon_plan_create_slab(C.byref(self._h), int(Nx), int(Ny), int(Nt), int(Nc), _ptr(mdev),
+                                            _ptr(sens), float(lam), float(mu), PRIOR[prior], C.byref(o),
+                                            int(slab[0]), int(slab[1]), _stream(stream))
         _check(st)
         self._keep = (mdev, sens)
+        self.slab = slab
 
     def close(self):
         if self._h:
@@ -212,7 +225,8 @@ class Plan:
 
     def _img(self):
         s = self.shape
-        return torch.empty((s["Nt"], s["Ny"], s["Nx"]), dtype=torch.complex64, device="cuda")
+        alloc = torch.zeros if getattr(self, "slab", None) is not None else torch.empty   # a slab writes its columns only
+        return alloc((s["Nt"], s["Ny"], s["Nx"]), dtype=torch.complex64, device="cuda")
 
     def _ksp(self):
         s = self.shape
@@ -449,6 +463,28 @@ def gram_inverse_noalloc(mask_rows, sens_cols, mu, out=None, stream=None):
     _check(load().recon_gram_inverse_noalloc(int(Ny), int(Nc), int(nblk), _ptr(m), _ptr(s), float(mu), _ptr(out),
                                              _stream(stream)))
     return out
+
+
+def solve_slabs(mask, sens, lam, mu, kspace, width, prior="tv", out=None, stream=None, **opts):
+    """The whole problem solved slab after slab of `width` columns
+    (recon_solve_slabs); returns (image, Info, J trace as a list)."""
+    lib = load()
+    s = _c64(sens, "cuda")
+    k = _c64(kspace, "cuda")
+    Nc, Ny, Nx = s.shape
+    m = torch.as_tensor(mask).to(torch.uint8).contiguous()
+    o = default_opts(**opts)
+    if m.dim() == 3:
+        o.mask_full = 1
+    Nt = m.shape[0]
+    mdev = m.cuda() if m.device.type != "cuda" else m
+    out = torch.empty((Nt, Ny, Nx), dtype=torch.complex64, device="cuda") if out is None else out
+    tr = (C.c_double * (o.max_iters + 1))()
+    inf = Info()
+    _check(lib.recon_solve_slabs(int(Nx), int(Ny), int(Nt), int(Nc), _ptr(mdev), _ptr(s), float(lam), float(mu),
+                                 PRIOR[prior], C.byref(o), int(width), _ptr(k), _ptr(out), tr, C.byref(inf),
+                                 _stream(stream)))
+    return out, inf, list(tr)
 
 
 def kernel_launches() -> int:

@@ -189,13 +189,15 @@ recon_status plan_objective(recon_plan* p, const float2* x, double* acc, cudaStr
   return RECON_OK;
 }
 
-// user layout [Nt][Ny][Nx] -> internal [Nt][Nx][Ny]
+// user layout [Nt][Ny][Nx_full] (the plan's columns i0 .. i0+Nx-1) -> internal [Nt][Nx][Ny]
 recon_status plan_to_internal(recon_plan* p, const float2* in, float2* out, cudaStream_t s) {
-  RC(launch_transpose(in, out, p->Nt, p->Ny, p->Nx, (long long)p->npix(), (long long)p->npix(), p->Ny, s));
+  const long long uframe = (long long)p->Ny * p->Nx_full;
+  RC(launch_transpose(in + p->i0, out, p->Nt, p->Ny, p->Nx, uframe, (long long)p->npix(), p->Ny, s, p->Nx_full));
   return RECON_OK;
 }
 recon_status plan_to_user(recon_plan* p, const float2* in, float2* out, cudaStream_t s) {
-  RC(launch_transpose(in, out, p->Nt, p->Nx, p->Ny, (long long)p->npix(), (long long)p->npix(), p->Nx, s));
+  const long long uframe = (long long)p->Ny * p->Nx_full;
+  RC(launch_transpose(in, out + p->i0, p->Nt, p->Nx, p->Ny, (long long)p->npix(), uframe, p->Nx_full, s));
   return RECON_OK;
 }
 
@@ -203,8 +205,8 @@ recon_status plan_to_user(recon_plan* p, const float2* in, float2* out, cudaStre
 // ||y||^2 (into *yy, which must be zeroed first).
 recon_status plan_adjoint64(recon_plan* p, const void* kspace, int kstorage, const float* kscale, float2* yhat32,
                             float2* b, double* yy, cudaStream_t s) {
-  RC(launch_hybrid_rows64(kspace, kstorage, kscale, p->yhat64, yhat32, yy, p->rows, p->rowoff, p->maxm, p->Nx, p->Ny,
-                          p->Nt, p->Nc, p->fx64, p->rows_per_block, s));
+  RC(launch_hybrid_rows64(kspace, kstorage, kscale, p->yhat64, yhat32, yy, p->rows, p->rowoff, p->maxm, p->Nx_full,
+                          p->Ny, p->Nt, p->Nc, p->fx64, p->rows_per_block, s, p->i0, p->Nx));
   RC(launch_adjoint_combine64(p->yhat64, p->sens, b, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fy64,
                               p->combine_coils, s));
   return RECON_OK;
@@ -217,8 +219,8 @@ recon_status plan_prologue(recon_plan* p, const void* kspace, int kstorage, cons
   RC(cudaMemsetAsync(p->yy, 0, sizeof(double), s));
   if (p->storage == 0) return plan_adjoint64(p, kspace, kstorage, kscale, p->yhat, p->b, p->yy, s);
   RC(cudaMemsetAsync(p->ymax, 0, (size_t)p->Nt * sizeof(unsigned), s));
-  RC(launch_hybrid_rows(kspace, kstorage, kscale, p->tmp_b, p->yy, p->ymax, p->rows, p->rowoff, p->maxm, p->Nx, p->Ny,
-                        p->Nt, p->Nc, p->fx, p->rows_per_block, s));
+  RC(launch_hybrid_rows(kspace, kstorage, kscale, p->tmp_b, p->yy, p->ymax, p->rows, p->rowoff, p->maxm, p->Nx_full,
+                        p->Ny, p->Nt, p->Nc, p->fx, p->rows_per_block, s, p->i0, p->Nx));
   RC(launch_adjoint_combine(p->tmp_b, p->sens, p->b, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fy,
                             p->storage, p->yhat_lp, p->ymax, p->yscale, p->combine_coils, s));
   return RECON_OK;
@@ -251,18 +253,20 @@ namespace {
 
 bool valid_ptr(const void* p) { return p != nullptr; }
 
-}  // namespace
-
-extern "C" {
-
-recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc, const uint8_t* mask,
-                               const float* sens, float lambda, float mu, recon_prior prior, const recon_opts* opts,
-                               void* stream) {
+// A plan over columns i0 .. i0+W-1 of an Nxf-wide problem (W = Nxf, i0 = 0
+// for a whole plan).  Inside, Nx is the plan's own width W; the k-space rows
+// (and the row FFTs of the prologue), the mask and the sensitivities the
+// caller passes are Nxf wide.
+recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc, const uint8_t* mask,
+                              const float* sens, float lambda, float mu, recon_prior prior, const recon_opts* opts,
+                              int i0, int W, void* stream) {
   g_last_error.clear();
   if (!out) return fail(RECON_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (Nx < 1 || Ny < 1 || Nt < 1 || Nc < 1) return fail(RECON_ERR_INVALID_ARG, "dimensions must be >= 1");
-  if (Ny > 1024 || Nx > 1024 || Nt > 128 || Nc > 64 || (size_t)(Nc + 1) * Ny * 16 > 200 * 1024)
+  const int Nx = W;
+  if (Nxf < 1 || Ny < 1 || Nt < 1 || Nc < 1) return fail(RECON_ERR_INVALID_ARG, "dimensions must be >= 1");
+  if (W < 1 || i0 < 0 || i0 + W > Nxf) return fail(RECON_ERR_INVALID_ARG, "slab outside the image");
+  if (Ny > 1024 || Nxf > 1024 || Nt > 128 || Nc > 64 || (size_t)(Nc + 1) * Ny * 16 > 200 * 1024)
     return fail(RECON_ERR_UNSUPPORTED,
                 "size beyond supported limits (Nx, Ny <= 1024, Nt <= 128, Nc <= 64, (Nc+1)*Ny <= 12800)");
   if (!valid_ptr(mask) || !valid_ptr(sens)) return fail(RECON_ERR_INVALID_ARG, "mask or sens is NULL");
@@ -279,7 +283,7 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   // mask -> sampled row lists (host)
-  const size_t mcount = o.mask_full ? (size_t)Nt * Ny * Nx : (size_t)Nt * Ny;
+  const size_t mcount = o.mask_full ? (size_t)Nt * Ny * Nxf : (size_t)Nt * Ny;
   std::vector<uint8_t> hm(mcount);
   {
     cudaError_t e = cudaMemcpy(hm.data(), mask, mcount, cudaMemcpyDefault);
@@ -287,6 +291,7 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
   }
   auto* p = new recon_plan();
   p->Nx = Nx; p->Ny = Ny; p->Nt = Nt; p->Nc = Nc;
+  p->Nx_full = Nxf; p->i0 = i0;
   p->prior = prior; p->lam = lambda; p->mu = mu; p->opts = o;
   p->storage = o.storage;
   p->esize = (o.storage == 0) ? 8 : 4;
@@ -297,9 +302,9 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
     for (int j = 0; j < Ny; ++j) {
       bool on;
       if (o.mask_full) {
-        const uint8_t* rowp = &hm[((size_t)t * Ny + j) * Nx];
+        const uint8_t* rowp = &hm[((size_t)t * Ny + j) * Nxf];
         on = rowp[0] != 0;
-        for (int i = 1; i < Nx; ++i) {
+        for (int i = 1; i < Nxf; ++i) {
           if ((rowp[i] != 0) != on) {
             delete p;
             return fail(RECON_ERR_MASK_NOT_CARTESIAN, "mask differs along kx (row " + std::to_string(j) +
@@ -333,10 +338,10 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
   PC(p->alloc((void**)&p->sens, (size_t)Nx * Nc * Ny * sizeof(float2)));
   PC(p->alloc((void**)&p->rows, std::max<size_t>(1, p->h_rows.size()) * sizeof(int)));
   PC(p->alloc((void**)&p->rowoff, (Nt + 1) * sizeof(int)));
-  PC(p->alloc((void**)&p->tw_x, Nx * sizeof(float2)));
+  PC(p->alloc((void**)&p->tw_x, Nxf * sizeof(float2)));
   PC(p->alloc((void**)&p->tw_y, Ny * sizeof(float2)));
   PC(p->alloc((void**)&p->tw_t, Nt * sizeof(float2)));
-  PC(p->alloc((void**)&p->tw64_x, Nx * sizeof(double2)));
+  PC(p->alloc((void**)&p->tw64_x, Nxf * sizeof(double2)));
   PC(p->alloc((void**)&p->tw64_y, Ny * sizeof(double2)));
   PC(p->alloc((void**)&p->yhat64, std::max<size_t>(1, (size_t)p->total_rows * Nx * Nc) * sizeof(double2)));
   PC(p->alloc((void**)&p->thomas, Nt * sizeof(float)));
@@ -371,23 +376,23 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
   PC(p->alloc((void**)&p->yy, sizeof(double)));
 
   // tables
-  std::vector<float2> tw(std::max(std::max(Nx, Ny), Nt));
-  fill_twiddles_host(Nx, tw.data());
-  PC(cudaMemcpy(p->tw_x, tw.data(), Nx * sizeof(float2), cudaMemcpyHostToDevice));
+  std::vector<float2> tw(std::max(std::max(Nxf, Ny), Nt));
+  fill_twiddles_host(Nxf, tw.data());
+  PC(cudaMemcpy(p->tw_x, tw.data(), Nxf * sizeof(float2), cudaMemcpyHostToDevice));
   fill_twiddles_host(Ny, tw.data());
   PC(cudaMemcpy(p->tw_y, tw.data(), Ny * sizeof(float2), cudaMemcpyHostToDevice));
   fill_twiddles_host(Nt, tw.data());
   PC(cudaMemcpy(p->tw_t, tw.data(), Nt * sizeof(float2), cudaMemcpyHostToDevice));
   {
-    std::vector<double2> tw64(std::max(Nx, Ny));
-    fill_twiddles_host64(Nx, tw64.data());
-    PC(cudaMemcpy(p->tw64_x, tw64.data(), Nx * sizeof(double2), cudaMemcpyHostToDevice));
+    std::vector<double2> tw64(std::max(Nxf, Ny));
+    fill_twiddles_host64(Nxf, tw64.data());
+    PC(cudaMemcpy(p->tw64_x, tw64.data(), Nxf * sizeof(double2), cudaMemcpyHostToDevice));
     fill_twiddles_host64(Ny, tw64.data());
     PC(cudaMemcpy(p->tw64_y, tw64.data(), Ny * sizeof(double2), cudaMemcpyHostToDevice));
-    p->fx64 = make_fft_plan_host64(Nx, p->tw64_x);
+    p->fx64 = make_fft_plan_host64(Nxf, p->tw64_x);
     p->fy64 = make_fft_plan_host64(Ny, p->tw64_y);
   }
-  p->fx = make_fft_plan_host(Nx, p->tw_x);
+  p->fx = make_fft_plan_host(Nxf, p->tw_x);
   p->fy = make_fft_plan_host(Ny, p->tw_y);
   p->ft = make_fft_plan_host(Nt, p->tw_t);
   std::vector<float> th = thomas_pivots(Nt, o.rho);
@@ -403,7 +408,10 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
     const size_t sbytes = (size_t)Nc * Ny * Nx * sizeof(float2);
     PC(cudaMalloc(&tmp, sbytes));
     stage = static_cast<float2*>(tmp);
-    cudaError_t e = cudaMemcpyAsync(stage, sens, sbytes, cudaMemcpyDefault, s);
+    // the plan's columns i0 .. i0+Nx-1 of the caller's [Nc][Ny][Nxf] array
+    cudaError_t e = cudaMemcpy2DAsync(stage, (size_t)Nx * sizeof(float2), sens + 2 * (size_t)i0,
+                                      (size_t)Nxf * sizeof(float2), (size_t)Nx * sizeof(float2), (size_t)Nc * Ny,
+                                      cudaMemcpyDefault, s);
     if (e == cudaSuccess)
       e = launch_transpose(stage, p->sens, Nc, Ny, Nx, (long long)Ny * Nx, (long long)Ny, (long long)Nc * Ny, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -463,6 +471,56 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
   *out = p;
   return RECON_OK;
 #undef PC
+}
+
+}  // namespace
+
+extern "C" {
+
+recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc, const uint8_t* mask,
+                               const float* sens, float lambda, float mu, recon_prior prior, const recon_opts* opts,
+                               void* stream) {
+  return plan_create_impl(out, Nx, Ny, Nt, Nc, mask, sens, lambda, mu, prior, opts, 0, Nx, stream);
+}
+
+recon_status recon_plan_create_slab(recon_plan** out, int Nx, int Ny, int Nt, int Nc, const uint8_t* mask,
+                                    const float* sens, float lambda, float mu, recon_prior prior,
+                                    const recon_opts* opts, int i0, int width, void* stream) {
+  return plan_create_impl(out, Nx, Ny, Nt, Nc, mask, sens, lambda, mu, prior, opts, i0, width, stream);
+}
+
+recon_status recon_solve_slabs(int Nx, int Ny, int Nt, int Nc, const uint8_t* mask, const float* sens, float lambda,
+                               float mu, recon_prior prior, const recon_opts* opts, int width, const float* kspace,
+                               float* image, double* J_trace, recon_info* info, void* stream) {
+  if (width < 1 || !kspace || !image) return fail(RECON_ERR_INVALID_ARG, "bad argument");
+  recon_opts o;
+  recon_default_opts(&o);
+  if (opts) o = *opts;
+  const int K = std::max(o.max_iters, 0);
+  std::vector<double> acc((size_t)K + 1, 0.0), tr((size_t)K + 1);
+  recon_info tot{};
+  tot.J = tot.J0 = 0.0;
+  for (int i0 = 0; i0 < Nx; i0 += width) {
+    const int W = std::min(width, Nx - i0);
+    recon_plan* p = nullptr;
+    recon_status st = plan_create_impl(&p, Nx, Ny, Nt, Nc, mask, sens, lambda, mu, prior, &o, i0, W, stream);
+    if (st != RECON_OK) return st;
+    recon_info si{};
+    st = recon_solve(p, kspace, image, &si, stream);
+    if (st == RECON_OK && J_trace) st = recon_get_trace(p, tr.data(), K + 1);
+    recon_destroy(p);
+    if (st != RECON_OK) return st;
+    for (int k = 0; k <= K; ++k) acc[k] += tr[k];
+    tot.iters = std::max(tot.iters, si.iters);
+    tot.stopped |= si.stopped;
+    tot.J += si.J;
+    tot.J0 += si.J0;
+  }
+  if (J_trace)
+    for (int k = 0; k <= K; ++k) J_trace[k] = acc[k];
+  tot.delta = (J_trace && K >= 1) ? (acc[K - 1] - acc[K]) / acc[K] : NAN;
+  if (info) *info = tot;
+  return RECON_OK;
 }
 
 recon_status recon_solve_kspace(recon_plan* p, const recon_kspace* y, float* image, recon_info* info, void* stream) {
@@ -537,15 +595,21 @@ recon_status recon_solve_host(recon_plan* p, const float* kspace_host, float* im
   g_last_error.clear();
   if (!p || !kspace_host || !image_host) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t kbytes = (size_t)p->Nt * p->Nc * p->Ny * p->Nx * sizeof(float2);
-  const size_t ibytes = p->nimg() * sizeof(float2);
+  const size_t kbytes = (size_t)p->Nt * p->Nc * p->Ny * p->Nx_full * sizeof(float2);
+  const size_t ibytes = (size_t)p->Nt * p->Ny * p->Nx_full * sizeof(float2);
   if (!p->kstage) RC(p->alloc((void**)&p->kstage, kbytes));
   if (!p->istage) RC(p->alloc((void**)&p->istage, ibytes));
   RC(cudaMemcpyAsync(p->kstage, kspace_host, kbytes, cudaMemcpyHostToDevice, s));
   recon_status st = recon_solve(p, reinterpret_cast<const float*>(p->kstage), reinterpret_cast<float*>(p->istage),
                                 nullptr, stream);
   if (st != RECON_OK) return st;
-  RC(cudaMemcpyAsync(image_host, p->istage, ibytes, cudaMemcpyDeviceToHost, s));
+  if (p->Nx == p->Nx_full) {
+    RC(cudaMemcpyAsync(image_host, p->istage, ibytes, cudaMemcpyDeviceToHost, s));
+  } else {  // only the plan's columns of the caller's image
+    const size_t pitch = (size_t)p->Nx_full * sizeof(float2);
+    RC(cudaMemcpy2DAsync(reinterpret_cast<float2*>(image_host) + p->i0, pitch, p->istage + p->i0, pitch,
+                         (size_t)p->Nx * sizeof(float2), (size_t)p->Nt * p->Ny, cudaMemcpyDeviceToHost, s));
+  }
   return plan_fill_info(p, info, s);
 }
 
@@ -561,6 +625,7 @@ recon_status recon_get_trace(recon_plan* p, double* J_host, int n) {
 
 recon_status recon_apply_adjoint(recon_plan* p, const float* kspace, float* image, void* stream) {
   if (!p || !kspace || !image) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  if (p->Nx != p->Nx_full) return fail(RECON_ERR_UNSUPPORTED, "H' of a slab plan: use a whole plan");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   recon_status st = plan_adjoint64(p, kspace, 0, nullptr, p->tmp_b, p->tmp_a, nullptr, s);
   if (st != RECON_OK) return st;
@@ -569,6 +634,7 @@ recon_status recon_apply_adjoint(recon_plan* p, const float* kspace, float* imag
 
 recon_status recon_apply_forward(recon_plan* p, const float* image, float* kspace, void* stream) {
   if (!p || !image || !kspace) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  if (p->Nx != p->Nx_full) return fail(RECON_ERR_UNSUPPORTED, "H of a slab plan: use a whole plan");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   recon_status st = plan_to_internal(p, reinterpret_cast<const float2*>(image), p->tmp_a, s);
   if (st != RECON_OK) return st;

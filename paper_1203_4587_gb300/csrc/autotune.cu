@@ -71,13 +71,13 @@ recon_status time_ms(F&& launch, cudaStream_t s, float* out) {
   return st;
 }
 
-using Key = std::tuple<int, int, int, int, int, int, int, int>;   // Nx Ny Nt Nc prior storage objective K>0
+using Key = std::tuple<int, int, int, int, int, int, int, int, int>;   // Nx Nx_full Ny Nt Nc prior storage objective K>0
 std::mutex g_mu;
 std::map<Key, recon_tuning> g_cache;
 
 Key key_of(const recon_plan* p) {
   const int objmode = (p->opts.objective != 0 || p->opts.tol > 0.0) ? (p->opts.objective == 2 ? 2 : 1) : 0;
-  return Key{p->Nx, p->Ny, p->Nt, p->Nc, (int)p->prior, p->storage, objmode, p->opts.max_iters > 0 ? 1 : 0};
+  return Key{p->Nx, p->Nx_full, p->Ny, p->Nt, p->Nc, (int)p->prior, p->storage, objmode, p->opts.max_iters > 0 ? 1 : 0};
 }
 
 // Candidate ring depths: multiples of the quantum up to the largest that fits.
@@ -152,7 +152,7 @@ recon_status tune_plan(recon_plan* p, cudaStream_t s, recon_tuning* t) {
   recon_status st = prepare_buffers(p, s);
   if (st != RECON_OK) return st;
   // prologue: a patterned complex64 k-space
-  const size_t nk = (size_t)p->Nt * p->Nc * p->Ny * p->Nx;
+  const size_t nk = (size_t)p->Nt * p->Nc * p->Ny * p->Nx_full;
   void* k = nullptr;
   RC(cudaMalloc(&k, nk * sizeof(float2)));
   struct Free { void* q; ~Free() { cudaFree(q); } } guard{k};
@@ -161,16 +161,16 @@ recon_status tune_plan(recon_plan* p, cudaStream_t s, recon_tuning* t) {
   float best = 3.4e38f;
   int best_g = 0;
   for (int g : {1, 2, 4, 8}) {
-    if (g > row_group_max(p->Nx, fp64)) break;
+    if (g > row_group_max(p->Nx_full, fp64)) break;
     p->rows_per_block = g;
     float ms = 0.f;
     auto run = [&]() -> recon_status {
       if (fp64) {
-        RC(launch_hybrid_rows64(k, 0, nullptr, p->yhat64, p->yhat, nullptr, p->rows, p->rowoff, p->maxm, p->Nx, p->Ny,
-                                p->Nt, p->Nc, p->fx64, g, s));
+        RC(launch_hybrid_rows64(k, 0, nullptr, p->yhat64, p->yhat, nullptr, p->rows, p->rowoff, p->maxm, p->Nx_full,
+                                p->Ny, p->Nt, p->Nc, p->fx64, g, s, p->i0, p->Nx));
       } else {
-        RC(launch_hybrid_rows(k, 0, nullptr, p->tmp_b, nullptr, p->ymax, p->rows, p->rowoff, p->maxm, p->Nx, p->Ny,
-                              p->Nt, p->Nc, p->fx, g, s));
+        RC(launch_hybrid_rows(k, 0, nullptr, p->tmp_b, nullptr, p->ymax, p->rows, p->rowoff, p->maxm, p->Nx_full,
+                              p->Ny, p->Nt, p->Nc, p->fx, g, s, p->i0, p->Nx));
       }
       return RECON_OK;
     };

@@ -168,6 +168,7 @@ recon_status recon_grad_create(recon_grad** out, recon_plan* const* plans, int n
     const recon_plan* p = plans[q];
     if (!p) return fail(RECON_ERR_INVALID_ARG, "NULL plan");
     if (p->prior != RECON_PRIOR_TV) return fail(RECON_ERR_UNSUPPORTED, "the adjoint is implemented for the TV prior");
+    if (p->Nx != p->Nx_full) return fail(RECON_ERR_UNSUPPORTED, "the adjoint needs whole plans (dL/dy spans all columns)");
     if (p->opts.max_iters != K || p->storage != plans[0]->storage)
       return fail(RECON_ERR_INVALID_ARG, "plans must share max_iters and storage");
   }

@@ -241,9 +241,11 @@ cudaError_t launch_finalize(const FinSlice* fins, int nslices, int k, cudaStream
 // (kstorage = recon_storage) times kscale[t] (may be null); ymax[t] receives
 // the largest |component| of frame t's yhat (float bits, may be null).
 // G (rows per block) and ncg (coils per pass) below: 0 = the largest that fits.
+// Nx is the full row length of the k-space (and the FFT length); i0, W keep
+// columns i0 .. i0+W-1 of the result (a slab plan), W = 0 keeps all.
 cudaError_t launch_hybrid_rows(const void* kspace, int kstorage, const float* kscale, float2* yhat, double* yy,
                                unsigned* ymax, const int* rows, const int* rowoff, int maxm, int Nx, int Ny, int Nt,
-                               int Nc, FftPlanDev fx, int G, cudaStream_t s);
+                               int Nc, FftPlanDev fx, int G, cudaStream_t s, int i0 = 0, int W = 0);
 // b = H'y from yhat (FP32); ystorage 1/2 also writes the 16-bit copy ylp of
 // yhat with per-frame power-of-two scales yscale[t] from ymax.
 cudaError_t launch_adjoint_combine(const float2* yhat, const float2* sens, float2* b, const int* rows,
@@ -255,7 +257,8 @@ cudaError_t launch_adjoint_combine(const float2* yhat, const float2* sens, float
 // accumulates ||y||^2 over the sampled entries (may be null).
 cudaError_t launch_hybrid_rows64(const void* kspace, int kstorage, const float* kscale, double2* yhat64,
                                  float2* yhat32, double* yy, const int* rows, const int* rowoff, int maxm, int Nx,
-                                 int Ny, int Nt, int Nc, FftPlanDev64 fx, int G, cudaStream_t s);
+                                 int Ny, int Nt, int Nc, FftPlanDev64 fx, int G, cudaStream_t s, int i0 = 0,
+                                 int W = 0);
 cudaError_t launch_adjoint_combine64(const double2* yhat64, const float2* sens, float2* b, const int* rows,
                                      const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fy, int ncg,
                                      cudaStream_t s);
@@ -269,9 +272,9 @@ cudaError_t launch_forward_cols(const float2* x, const float2* sens, float2* zha
                                 const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, cudaStream_t s);
 cudaError_t launch_forward_rows(const float2* zhat, float2* kspace, const int* rows, const int* rowoff, int maxm,
                                 int Nx, int Ny, int Nt, int Nc, FftPlanDev fx, cudaStream_t s);
-// out[b*obs + c*ors + r] = in[b*ibs + r*C + c], for r < R, c < C, b < B
+// out[b*obs + c*ors + r] = in[b*ibs + r*irs + c], for r < R, c < C, b < B (irs = 0: C)
 cudaError_t launch_transpose(const float2* in, float2* out, int B, int R, int C, long long ibs, long long obs,
-                             long long ors, cudaStream_t s);
+                             long long ors, cudaStream_t s, long long irs = 0);
 
 // plan
 cudaError_t launch_circulant(const int* rows, const int* rowoff, const double2* w64, double2* circ, int Ny, int Nt,

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) k_hybrid_rows(const KIn* __restrict__ ksp
                                                      double* __restrict__ yy, unsigned* __restrict__ ymax,
                                                      const int* __restrict__ rows,
                                                      const int* __restrict__ rowoff, int Nx, int Ny, int Nt, int Nc,
-                                                     int G, FftPlanT<T> fx, double scl) {
+                                                     int G, FftPlanT<T> fx, double scl, int i0, int W) {
   __shared__ double red[32];
   extern __shared__ __align__(16) unsigned char sm_rows_raw[];
   T* sm_rows = reinterpret_cast<T*>(sm_rows_raw);
@@ -52,32 +52,33 @@ __global__ void __launch_bounds__(256) k_hybrid_rows(const KIn* __restrict__ ksp
   T* B = sm_rows + (size_t)G * ss;
   const int tid = threadIdx.x, nth = blockDim.x;
   const float ks = kscale ? kscale[t] : 1.f;
-  double e2 = 0.0;  // ||y||^2 over these sampled rows
   for (int idx = tid; idx < g * Nx; idx += nth) {
     const int gg = idx / Nx, kx = idx - gg * Nx;
     const int row = rows[r0 + m0 + gg];
     T v = from_f2<T>(Elem<KIn>::load(ksp + (((size_t)t * Nc + c) * Ny + row) * Nx + kx));
     if (kscale) v = c_scale(v, ks);
-    e2 += c_abs2d(v);
     A[gg * ss + kx] = v;
   }
   __syncthreads();
-  if (yy) {
-    const double s2 = group_sum(e2, red, tid, nth, BlockBar());
-    if (tid == 0) atomicAdd(yy, s2);
-  }
   const BlockBar bar;
   T* R = fft_run(A, B, g, ss, 1, fx, true, tid, nth, bar);
-  const size_t base = (size_t)r0 * Nx * Nc;
+  // keep columns i0 .. i0+W-1 (a slab; all columns for a whole plan)
+  const size_t base = (size_t)r0 * W * Nc;
   float mx = 0.f;
-  for (int idx = tid; idx < g * Nx; idx += nth) {
+  double e2 = 0.0;  // ||yhat||^2 of the kept columns (= ||y||^2 of these rows for a whole plan)
+  for (int idx = tid; idx < g * W; idx += nth) {
     const int i = idx / g, gg = idx - i * g;
     const size_t o = base + ((size_t)i * Nc + c) * mt + m0 + gg;
-    const T v = c_scale(R[gg * ss + i], scl);
+    const T v = c_scale(R[gg * ss + i0 + i], scl);
     yhat[o] = v;
     if (yhat32) yhat32[o] = to_f2(v);
     const float2 f = to_f2(v);
     mx = fmaxf(mx, fmaxf(fabsf(f.x), fabsf(f.y)));
+    e2 += c_abs2d(v);
+  }
+  if (yy) {
+    const double s2 = group_sum(e2, red, tid, nth, bar);
+    if (tid == 0) atomicAdd(yy, s2);
   }
   if (ymax) {
     const unsigned w = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));   // non-negative: bits order as values
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(256) k_hybrid_rows(const KIn* __restrict__ ksp
 template <typename T, typename KIn>
 static cudaError_t launch_rows_t(const KIn* ksp, const float* kscale, T* yhat, float2* yhat32, double* yy,
                                  unsigned* ymax, const int* rows, const int* rowoff, int maxm, int Nx, int Ny, int Nt,
-                                 int Nc, const FftPlanT<T>& fx, int G_req, cudaStream_t s) {
+                                 int Nc, const FftPlanT<T>& fx, int G_req, int i0, int W, cudaStream_t s) {
   if (maxm <= 0) return cudaSuccess;
   const int G = G_req > 0 ? std::min(G_req, row_group<T>(Nx)) : row_group<T>(Nx);
   const size_t smem = 2 * (size_t)G * (Nx + 1) * sizeof(T);
@@ -101,37 +102,39 @@ static cudaError_t launch_rows_t(const KIn* ksp, const float* kscale, T* yhat, f
   }
   dim3 grid((maxm + G - 1) / G, Nc, Nt);
   k_hybrid_rows<T, KIn><<<grid, 256, smem, s>>>(ksp, kscale, yhat, yhat32, yy, ymax, rows, rowoff, Nx, Ny, Nt, Nc,
-                                                G, fx, 1.0 / sqrt((double)Nx)); note_launch();
+                                                G, fx, 1.0 / sqrt((double)Nx), i0, W > 0 ? W : Nx);
+  note_launch();
   return cudaGetLastError();
 }
 
 template <typename T, typename Plan>
 static cudaError_t rows_dispatch(const void* kspace, int kstorage, const float* kscale, T* yhat, float2* yhat32,
                                  double* yy, unsigned* ymax, const int* rows, const int* rowoff, int maxm, int Nx,
-                                 int Ny, int Nt, int Nc, const Plan& fx, int G, cudaStream_t s) {
+                                 int Ny, int Nt, int Nc, const Plan& fx, int G, int i0, int W, cudaStream_t s) {
   switch (kstorage) {
     case 0: return launch_rows_t<T, float2>(static_cast<const float2*>(kspace), kscale, yhat, yhat32, yy, ymax,
-                                            rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, G, s);
+                                            rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, G, i0, W, s);
     case 1: return launch_rows_t<T, __half2>(static_cast<const __half2*>(kspace), kscale, yhat, yhat32, yy, ymax,
-                                             rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, G, s);
+                                             rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, G, i0, W, s);
     case 2: return launch_rows_t<T, __nv_bfloat162>(static_cast<const __nv_bfloat162*>(kspace), kscale, yhat,
-                                                    yhat32, yy, ymax, rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, G, s);
+                                                    yhat32, yy, ymax, rows, rowoff, maxm, Nx, Ny, Nt, Nc, fx, G, i0,
+                                                    W, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_hybrid_rows(const void* kspace, int kstorage, const float* kscale, float2* yhat, double* yy,
                                unsigned* ymax, const int* rows, const int* rowoff, int maxm, int Nx, int Ny, int Nt,
-                               int Nc, FftPlanDev fx, int G, cudaStream_t s) {
+                               int Nc, FftPlanDev fx, int G, cudaStream_t s, int i0, int W) {
   return rows_dispatch<float2>(kspace, kstorage, kscale, yhat, nullptr, yy, ymax, rows, rowoff, maxm, Nx, Ny, Nt,
-                               Nc, fx, G, s);
+                               Nc, fx, G, i0, W, s);
 }
 
 cudaError_t launch_hybrid_rows64(const void* kspace, int kstorage, const float* kscale, double2* yhat64,
                                  float2* yhat32, double* yy, const int* rows, const int* rowoff, int maxm, int Nx,
-                                 int Ny, int Nt, int Nc, FftPlanDev64 fx, int G, cudaStream_t s) {
+                                 int Ny, int Nt, int Nc, FftPlanDev64 fx, int G, cudaStream_t s, int i0, int W) {
   return rows_dispatch<double2>(kspace, kstorage, kscale, yhat64, yhat32, yy, nullptr, rows, rowoff, maxm, Nx, Ny,
-                                Nt, Nc, fx, G, s);
+                                Nt, Nc, fx, G, i0, W, s);
 }
 
 constexpr int kCoilGroupMax = 8;
@@ -392,14 +395,14 @@ cudaError_t launch_forward_rows(const float2* zhat, float2* kspace, const int* r
 
 // out[b*obs + c*ors + r] = in[b*ibs + r*C + c]
 __global__ void k_transpose(const float2* __restrict__ in, float2* __restrict__ out, int R, int C, long long ibs,
-                            long long obs, long long ors) {
+                            long long irs, long long obs, long long ors) {
   __shared__ float2 tile[32][33];
   const int b = blockIdx.z;
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   for (int k = ty; k < 32; k += 8) {
     const int r = r0 + k, c = c0 + tx;
-    if (r < R && c < C) tile[k][tx] = in[b * ibs + (long long)r * C + c];
+    if (r < R && c < C) tile[k][tx] = in[b * ibs + (long long)r * irs + c];
   }
   __syncthreads();
   for (int k = ty; k < 32; k += 8) {
@@ -409,9 +412,9 @@ __global__ void k_transpose(const float2* __restrict__ in, float2* __restrict__ 
 }
 
 cudaError_t launch_transpose(const float2* in, float2* out, int B, int R, int C, long long ibs, long long obs,
-                             long long ors, cudaStream_t s) {
+                             long long ors, cudaStream_t s, long long irs) {
   dim3 grid((C + 31) / 32, (R + 31) / 32, B);
-  k_transpose<<<grid, dim3(32, 8), 0, s>>>(in, out, R, C, ibs, obs, ors); note_launch();
+  k_transpose<<<grid, dim3(32, 8), 0, s>>>(in, out, R, C, ibs, irs > 0 ? irs : C, obs, ors); note_launch();
   return cudaGetLastError();
 }
 

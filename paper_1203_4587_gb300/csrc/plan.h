@@ -48,7 +48,8 @@ struct Engine {
 }  // namespace recon
 
 struct recon_plan {
-  int Nx = 0, Ny = 0, Nt = 0, Nc = 0;
+  int Nx = 0, Ny = 0, Nt = 0, Nc = 0;  // Nx: the plan's own columns (a slab's width)
+  int Nx_full = 0, i0 = 0;             // the caller's image width and this plan's first column
   recon_prior prior = RECON_PRIOR_TV;
   float lam = 0.f, mu = 0.f;
   recon_opts opts{};
