@@ -78,6 +78,21 @@ def parse():
     return ap.parse_args()
 
 
+def reduce_max(x, dist, device):
+    """The largest of every rank's x (the whole job is as slow as its slowest rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(world, steps, iters_per_step, ms):
+    """Whole-job iterations/s: every rank runs `steps` solves of its own slice."""
+    return world * steps * iters_per_step / (ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -173,15 +188,14 @@ yhat = oracle.hybrid_data(case.kspace, case.mask)
 t_pro = time.perf_counter() - t0
 cols = (col0 + np.arange(ncols)) % w["Nx"]
 P = oracle.Problem(case.kspace, case.sens, case.mask, case.mu, cols)
+# size the sample from a 2-iteration probe so that one solve takes about `budget` seconds
 t0 = time.perf_counter()
-n = 0
-while True:
-    n += 1
-    _, info = P.solve(prior, case.lam, case.mu, case.rho, n)
-    el = time.perf_counter() - t0
-    if el > budget or n >= w["iters"]:
-        break
-    t0 = time.perf_counter()
+P.solve(prior, case.lam, case.mu, case.rho, 2)
+probe = (time.perf_counter() - t0) / 2
+n = int(max(2, min(w["iters"], budget / max(probe, 1e-9))))
+t0 = time.perf_counter()
+_, info = P.solve(prior, case.lam, case.mu, case.rho, n)
+el = time.perf_counter() - t0
 per_iter_full = el / n * (w["Nx"] / ncols)
 solve_s = t_pro + w["iters"] * per_iter_full
 print(json.dumps(dict(iters_per_s=w["iters"] / solve_s, prologue_s=t_pro, per_iter_full_s=per_iter_full,
@@ -572,13 +586,8 @@ def run_native(args):
     barrier()
     clocks = sampler.stop() if sampler else None
     launches = binding.kernel_launches() - launches0
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    iters_total = world * args.steps * w["iters"]
-    value = iters_total / (ms / 1e3)
+    ms = reduce_max(e0.elapsed_time(e1), dist, "cuda")
+    value = weak_value(world, args.steps, w["iters"], ms)
     prof = plan.profile()
     _, info = plan.solve(kspace, out, info=True)
 
@@ -623,12 +632,8 @@ def run_native(args):
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             plan.solve_host(kh, ih)
-        el = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        line["e2e"] = {"value": world * n_e2e * w["iters"] / el, "unit": UNIT,
+        el = reduce_max(time.perf_counter() - t0, dist, "cuda")
+        line["e2e"] = {"value": weak_value(world, n_e2e, w["iters"], el * 1e3), "unit": UNIT,
                        "h2d_bytes_per_step": int(kh.numel() * 8), "d2h_bytes_per_step": int(ih.numel() * 8),
                        "step": "recon_solve_host: k-space H2D (pinned), prologue, 100 iterations, image D2H"}
 
