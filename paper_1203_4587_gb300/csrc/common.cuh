@@ -116,6 +116,9 @@ struct c16b { __nv_bfloat162 v; };
 template <typename E> struct Elem;
 template <> struct Elem<float2> {
   static constexpr int bytes = 8;
+  using S = float;   // one component
+  __device__ __forceinline__ static S cvt1(double v) { return (float)v; }
+  __device__ __forceinline__ static float widen1(S v) { return v; }
   // two adjacent elements in one 16-byte load (p 16-byte aligned), not widened
   __device__ __forceinline__ static void load2raw(const float2* p, float2& a, float2& b) {
     const float4 q = *reinterpret_cast<const float4*>(p);
@@ -132,6 +135,9 @@ template <> struct Elem<float2> {
 };
 template <> struct Elem<__half2> {
   static constexpr int bytes = 4;
+  using S = __half;
+  __device__ __forceinline__ static S cvt1(double v) { return __double2half(v); }
+  __device__ __forceinline__ static float widen1(S v) { return __half2float(v); }
   __device__ __forceinline__ static void load2raw(const __half2* p, __half2& a, __half2& b) {
     const uint2 q = *reinterpret_cast<const uint2*>(p);
     a = *reinterpret_cast<const __half2*>(&q.x); b = *reinterpret_cast<const __half2*>(&q.y);
@@ -150,6 +156,9 @@ template <> struct Elem<__half2> {
 };
 template <> struct Elem<__nv_bfloat162> {
   static constexpr int bytes = 4;
+  using S = __nv_bfloat16;
+  __device__ __forceinline__ static S cvt1(double v) { return __double2bfloat16(v); }
+  __device__ __forceinline__ static float widen1(S v) { return __bfloat162float(v); }
   __device__ __forceinline__ static void load2raw(const __nv_bfloat162* p, __nv_bfloat162& a, __nv_bfloat162& b) {
     const uint2 q = *reinterpret_cast<const uint2*>(p);
     a = *reinterpret_cast<const __nv_bfloat162*>(&q.x); b = *reinterpret_cast<const __nv_bfloat162*>(&q.y);
@@ -166,6 +175,25 @@ template <> struct Elem<__nv_bfloat162> {
   }
   __device__ __forceinline__ static __nv_bfloat162 cvt(float2 z) { return __floats2bfloat162_rn(z.x, z.y); }
 };
+
+// Packed FP32x2 arithmetic on pairs held in one 64-bit register (two
+// independent round-to-nearest operations per instruction).
+struct f32x2 { unsigned long long v; };
+__device__ __forceinline__ f32x2 pack2(float a, float b) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(f32x2 a) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a.v));
+  return r;
+}
+__device__ __forceinline__ f32x2 ffma2(f32x2 a, f32x2 b, f32x2 c) {   // a * b + c
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return d;
+}
 
 // ---- timers, barriers ------------------------------------------------------
 __device__ __forceinline__ unsigned long long global_ns() {

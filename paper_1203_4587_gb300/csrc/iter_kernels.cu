@@ -52,19 +52,45 @@ __device__ __forceinline__ void proc_tile(const E* __restrict__ tl, const float2
       cv[2 * k] = make_float2(c.x, c.y); cv[2 * k + 1] = make_float2(c.z, c.w);
     }
   }
-  float2 rowp[4], colp[8];
+  // Planar pairs: el[2qq] = (re_c, re_c+1), el[2qq+1] = (im_c, im_c+1) of row
+  // ri = qq/4, columns c = 2(qq%4), c+1.  Packed FP32x2 FMAs accumulate
+  //   row ri:         e_c cv_c over the two columns  (Re = re cx - im cy, Im = re cy + im cx)
+  //   columns c, c+1: conj(e_c) rv_ri                (Re = re rv.x + im rv.y, Im = re rv.y - im rv.x)
+  // with the subtracted products in their own accumulators.
+  f32x2 cx[4], cy[4], rx[4], ry[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) rowp[k] = make_float2(0.f, 0.f);
+  for (int k = 0; k < 4; ++k) {
+    cx[k] = pack2(cv[2 * k].x, cv[2 * k + 1].x);
+    cy[k] = pack2(cv[2 * k].y, cv[2 * k + 1].y);
+    rx[k] = pack2(rv[k].x, rv[k].x);
+    ry[k] = pack2(rv[k].y, rv[k].y);
+  }
+  const f32x2 z2 = pack2(0.f, 0.f);
+  f32x2 rre[4], rren[4], rim[4], cre[4], cim[4], cimn[4];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) colp[k] = make_float2(0.f, 0.f);
+  for (int k = 0; k < 4; ++k) { rre[k] = rren[k] = rim[k] = cre[k] = cim[k] = cimn[k] = z2; }
 #pragma unroll
   for (int qq = 0; qq < 16; ++qq) {
-    const float2 e0 = Elem<E>::widen(el[2 * qq]), e1 = Elem<E>::widen(el[2 * qq + 1]);
-    const int ri = qq >> 2, c0 = (qq & 3) * 2;
-    c_fma(rowp[ri], e0, cv[c0]);
-    c_fma(rowp[ri], e1, cv[c0 + 1]);
-    c_fmac(colp[c0], e0, rv[ri]);
-    c_fmac(colp[c0 + 1], e1, rv[ri]);
+    const float2 ref = Elem<E>::widen(el[2 * qq]), imf = Elem<E>::widen(el[2 * qq + 1]);
+    const f32x2 re = pack2(ref.x, ref.y), im = pack2(imf.x, imf.y);
+    const int ri = qq >> 2, cp = qq & 3;
+    rre[ri] = ffma2(re, cx[cp], rre[ri]);
+    rren[ri] = ffma2(im, cy[cp], rren[ri]);
+    rim[ri] = ffma2(re, cy[cp], rim[ri]);
+    rim[ri] = ffma2(im, cx[cp], rim[ri]);
+    cre[cp] = ffma2(re, rx[ri], cre[cp]);
+    cre[cp] = ffma2(im, ry[ri], cre[cp]);
+    cim[cp] = ffma2(re, ry[ri], cim[cp]);
+    cimn[cp] = ffma2(im, rx[ri], cimn[cp]);
+  }
+  float2 rowp[4], colp[8];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 a = unpack2(rre[k]), an = unpack2(rren[k]), b = unpack2(rim[k]);
+    rowp[k] = make_float2((a.x - an.x) + (a.y - an.y), b.x + b.y);
+    const float2 c = unpack2(cre[k]), d = unpack2(cim[k]), dn = unpack2(cimn[k]);
+    colp[2 * k] = make_float2(c.x, d.x - dn.x);
+    colp[2 * k + 1] = make_float2(c.y, d.y - dn.y);
   }
   // rows: lanes differing in bits 0,1
   const bool b1 = (lc & 2) != 0, b0 = (lc & 1) != 0;

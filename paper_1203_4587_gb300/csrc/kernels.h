@@ -23,8 +23,11 @@ namespace recon {
 // Ny is padded to Nyp = 32*nb.  The upper triangle is cut into 32x32 blocks.
 // Units, in stream order:
 //   * every off-diagonal block (bj < bk), bk-major: 1024 elements in the
-//     order the matvec lanes read them: element (R, C) of the block sits at
-//     ((R%4)*4 + (C%8)/2)*64 + ((R/4)*4 + C/8)*2 + C%2.
+//     order the matvec lanes read them: the pair (R, C), (R, C+1), C even,
+//     sits at complex position ((R%4)*4 + (C%8)/2)*64 + ((R/4)*4 + C/8)*2 and
+//     is stored planar, components (re_C, re_C+1, im_C, im_C+1), so one
+//     16-byte (8-byte at 16 bit) load gives a lane a real pair and an
+//     imaginary pair for packed FP32x2 arithmetic.
 //   * diagonal blocks in pairs (2q, 2q+1): 32 x 33 = 1056 elements.  Cell
 //     (a, b) holds P[a][b-1] for b > a (upper triangle of block 2q, row a)
 //     and Q[b][a] for b <= a (upper triangle of block 2q+1, column a); it is

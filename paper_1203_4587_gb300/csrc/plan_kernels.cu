@@ -53,6 +53,34 @@ __host__ __device__ inline long long packed_pos(int R, int C, int ntiles) {
   return base + b * 32 + ((a + b) & 31);
 }
 
+// Element (R, C), R <= C, of a packed column: tiles are planar per column
+// pair (see kernels.h), diagonal pairs hold (re, im) per element.
+template <typename E>
+__device__ __forceinline__ void packed_store(E* Ac, int R, int C, int ntiles, double2 v) {
+  using S = typename Elem<E>::S;
+  S* sc = reinterpret_cast<S*>(Ac);
+  if ((R >> 5) < (C >> 5)) {
+    const long long b = 2 * packed_pos(R, C & ~1, ntiles);
+    sc[b + (C & 1)] = Elem<E>::cvt1(v.x);
+    sc[b + 2 + (C & 1)] = Elem<E>::cvt1(v.y);
+  } else {
+    const long long b = 2 * packed_pos(R, C, ntiles);
+    sc[b] = Elem<E>::cvt1(v.x);
+    sc[b + 1] = Elem<E>::cvt1(v.y);
+  }
+}
+template <typename E>
+__device__ __forceinline__ float2 packed_load(const E* Ac, int R, int C, int ntiles) {
+  using S = typename Elem<E>::S;
+  const S* sc = reinterpret_cast<const S*>(Ac);
+  if ((R >> 5) < (C >> 5)) {
+    const long long b = 2 * packed_pos(R, C & ~1, ntiles);
+    return make_float2(Elem<E>::widen1(sc[b + (C & 1)]), Elem<E>::widen1(sc[b + 2 + (C & 1)]));
+  }
+  const long long b = 2 * packed_pos(R, C, ntiles);
+  return make_float2(Elem<E>::widen1(sc[b]), Elem<E>::widen1(sc[b + 1]));
+}
+
 constexpr int kPlanThreads = 256;
 
 template <typename E>
@@ -146,7 +174,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_inverse(const float2* __r
           double2 s = make_double2(0.0, 0.0);
           for (int l = k; l < n; ++l) z_fmac(s, W[(size_t)l * n + j], W[(size_t)l * n + k]);
           if (j == k) s.y = 0.0;  // Hermitian: exact real diagonal
-          Ac[packed_pos(j, k, ntiles)] = Elem<E>::cvt(s);
+          packed_store(Ac, j, k, ntiles, s);
         }
       }
     }
@@ -185,8 +213,8 @@ __global__ void k_unpack(const E* __restrict__ A, long long col_elems, int ntile
        idx += (long long)gridDim.x * blockDim.x) {
     const int R = (int)(idx / Ny), C = (int)(idx - (long long)R * Ny);
     float2 v;
-    if (R <= C) v = Elem<E>::load(Ac + packed_pos(R, C, ntiles));
-    else v = c_conj(Elem<E>::load(Ac + packed_pos(C, R, ntiles)));
+    if (R <= C) v = packed_load(Ac, R, C, ntiles);
+    else v = c_conj(packed_load(Ac, C, R, ntiles));
     dense[idx] = v;
   }
 }
