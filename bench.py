@@ -320,14 +320,18 @@ def measure_batched(nslices, storage, steps=3):
     ms = a.elapsed_time(b) / steps
     infos = batch.info()
     iters = sum(i.iters for i in infos)
-    A_bytes = sum(p.inverse_bytes for p in plans)
+    esize = 8 if storage == "fp32" else 4
+    # algorithmic bytes: the Hermitian triangle Ny(Ny+1)/2 of every column (i, t)
+    A_bytes = sum(esize * sh["Nx"] * sh["Nt"] * sh["Ny"] * (sh["Ny"] + 1) // 2 for sh in shapes)
+    A_stored = sum(p.inverse_bytes for p in plans)
     batch.close()
     for p in plans:
         p.close()
     return {"value": nslices / (ms / 1e3), "unit": "recons/s", "slices": nslices,
             "iters_per_slice": shapes[0]["iters"], "ms_per_batch": ms,
             "recons_per_s_with_plan": nslices / (ms / 1e3 + plan_s), "plan_s_total": plan_s,
-            "input_gen_s": gen_s, "iters_done": iters, "inverse_bytes_total": A_bytes, "tuning": tuning,
+            "input_gen_s": gen_s, "iters_done": iters, "inverse_bytes_total": A_bytes,
+            "inverse_bytes_stored": A_stored, "tuning": tuning,
             "hbm_gbs_inverse_stream": A_bytes * shapes[0]["iters"] / (ms / 1e3) / 1e9,
             "note": ("Nx, Ny in {128,160,192,256}, Nt in {16,24,32,40}, Nc in {8,12,16}, R in {4,6,8}, TV, "
                      "lambda=0.005, mu=0.1; all slices in one launch per step, the batched solve replayed "
@@ -378,11 +382,11 @@ def measure_precision(steps=3):
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / steps
         prof = p.profile()
-        A_bytes = p.inverse_bytes
+        A_bytes = (8 if storage == "fp32" else 4) * Nx * Nt * Ny * (Ny + 1) // 2   # algorithmic
         col_ms = prof.inverse_ms / max(prof.inverse_launches, 1)
         bytes_launch = A_bytes + 3 * 8 * Nx * Ny * Nt
         out[storage] = {"iters_per_s": c.iters / (ms / 1e3), "ms_per_solve": ms, "plan_s": plan_s,
-                        "inverse_bytes": A_bytes, "inverse_avg_ms": col_ms,
+                        "inverse_bytes": A_bytes, "inverse_bytes_stored": p.inverse_bytes, "inverse_avg_ms": col_ms,
                         "inverse_gbs": bytes_launch / (col_ms / 1e3) / 1e9,
                         "inverse_frac": bytes_launch / (col_ms / 1e3) / 1e9 / peak,
                         "inverse_share": prof.inverse_ms / max(prof.solve_ms, 1e-9),

@@ -139,9 +139,8 @@ PackInfo make_pack(int Ny) {
   PackInfo pk{};
   pk.nb = (Ny + 31) / 32;
   pk.ntiles = pk.nb * (pk.nb - 1) / 2;
-  const int nrect = (pk.nb + 1) / 2;
-  pk.nunits = pk.ntiles + nrect;
-  pk.col_elems = (long long)pk.ntiles * kTileElems + (long long)nrect * kRectElems;
+  pk.nunits = pk.ntiles + pk.nb;
+  pk.col_elems = (long long)pk.ntiles * kTileElems + (long long)pk.nb * kDiagElems;
   return pk;
 }
 

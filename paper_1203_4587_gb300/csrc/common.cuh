@@ -117,6 +117,7 @@ template <typename E> struct Elem;
 template <> struct Elem<float2> {
   static constexpr int bytes = 8;
   using S = float;   // one component
+  __device__ __forceinline__ static float2 zero() { return make_float2(0.f, 0.f); }
   __device__ __forceinline__ static S cvt1(double v) { return (float)v; }
   __device__ __forceinline__ static float widen1(S v) { return v; }
   // two adjacent elements in one 16-byte load (p 16-byte aligned), not widened
@@ -136,6 +137,7 @@ template <> struct Elem<float2> {
 template <> struct Elem<__half2> {
   static constexpr int bytes = 4;
   using S = __half;
+  __device__ __forceinline__ static __half2 zero() { return __float2half2_rn(0.f); }
   __device__ __forceinline__ static S cvt1(double v) { return __double2half(v); }
   __device__ __forceinline__ static float widen1(S v) { return __half2float(v); }
   __device__ __forceinline__ static void load2raw(const __half2* p, __half2& a, __half2& b) {
@@ -157,6 +159,7 @@ template <> struct Elem<__half2> {
 template <> struct Elem<__nv_bfloat162> {
   static constexpr int bytes = 4;
   using S = __nv_bfloat16;
+  __device__ __forceinline__ static __nv_bfloat162 zero() { return __float2bfloat162_rn(0.f); }
   __device__ __forceinline__ static S cvt1(double v) { return __double2bfloat16(v); }
   __device__ __forceinline__ static float widen1(S v) { return __bfloat162float(v); }
   __device__ __forceinline__ static void load2raw(const __nv_bfloat162* p, __nv_bfloat162& a, __nv_bfloat162& b) {

@@ -16,27 +16,37 @@ constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kProducers = 2;                 // producer warps (one issuing thread each)
 constexpr int kColThreads = kConsumers + 32 * (kProducers + 2);  // + producers, r loader, column manager
-// A ring stage holds the largest unit of the storage type: kRectElems
+// A ring stage holds the largest unit of the storage type: kTileElems
 // elements of esize bytes (8 FP32, 4 FP16/BF16; both multiples of 16 bytes).
-__host__ __device__ constexpr int stage_bytes(int esize) { return kRectElems * esize; }
+__host__ __device__ constexpr int stage_bytes(int esize) { return kTileElems * esize; }
 
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
   return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
-// One off-diagonal 32x32 block (rows p*32.., cols q*32..): lane (lr, lc)
-// holds rows lr*4..+3 and cols lc*8..+7.  Row sums are reduced over the 4
-// lanes sharing lr, column sums (with conj, the lower triangle) over the 8
+// One 32x32 block (rows p*32.., cols q*32..): lane (lr, lc) holds rows
+// lr*4..+3 and cols lc*8..+7, and each element e at (R, C) adds e r_C to
+// y_R and conj(e) r_R to y_C.  For an off-diagonal block (p < q) that is its
+// product and the product of its conjugate transpose (the lower triangle);
+// for a diagonal block (p == q, zeros below the diagonal, the diagonal
+// halved, 12 lanes without elements) it is the block's Hermitian product.
+// Row sums are reduced over the 4 lanes sharing lr, column sums over the 8
 // lanes sharing lc, by butterfly exchanges that leave one total per lane.
+// Lane data of pair qq sit at qq*qstride + loff (kernels.h).
 template <typename E>
 __device__ __forceinline__ void proc_tile(const E* __restrict__ tl, const float2* __restrict__ r,
-                                          float2* __restrict__ yw, int p, int q, int lane, uint64_t* release) {
+                                          float2* __restrict__ yw, int p, int q, int lane, uint64_t* release,
+                                          int qstride, int loff, bool has) {
   const int lr = lane >> 2, lc = lane & 3;
   // the whole unit into registers first, then the ring stage goes back to the
   // producer while this warp computes
   E el[32];
 #pragma unroll
-  for (int qq = 0; qq < 16; ++qq) Elem<E>::load2raw(tl + qq * 64 + lane * 2, el[2 * qq], el[2 * qq + 1]);
+  for (int k = 0; k < 32; ++k) el[k] = Elem<E>::zero();
+  if (has) {
+#pragma unroll
+    for (int qq = 0; qq < 16; ++qq) Elem<E>::load2raw(tl + qq * qstride + loff, el[2 * qq], el[2 * qq + 1]);
+  }
   __syncwarp();
   if (lane == 0) mbar_arrive(release);
   float2 rv[4], cv[8];
@@ -123,58 +133,6 @@ __device__ __forceinline__ void proc_tile(const E* __restrict__ tl, const float2
   __syncwarp();
 }
 
-// A pair of diagonal blocks P = block p, Q = block q in one 32 x 33 cell
-// array (see kernels.h).  Pass 1: lane a walks row a (row sums of P, column
-// sums of Q).  Pass 2: lane l walks column l+1 (column sums of P, row sums of
-// Q); column 0 (row 0 of Q) is reduced across the warp.  The skewed layout
-// makes both passes free of bank conflicts.
-template <typename E>
-__device__ __forceinline__ void proc_rect(const E* __restrict__ tl, const float2* __restrict__ r,
-                                          float2* __restrict__ yw, int p, int q, int lane, uint64_t* release) {
-  const float2* rP = r + p * 32;
-  const float2* rQ = r + q * 32;
-  // pass 1 from registers; the stage is released once pass 2's cells are loaded
-  E e1[33];
-#pragma unroll
-  for (int b = 0; b < 33; ++b) e1[b] = tl[b * 32 + ((lane + b) & 31)];
-  float2 rowP = make_float2(0.f, 0.f), colQ = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int b = 0; b < 33; ++b) {
-    const float2 e = Elem<E>::widen(e1[b]);
-    if (b > lane) c_fma(rowP, e, rP[b - 1]);      // P[lane][b-1], b-1 >= lane
-    else c_fmac(colQ, e, rQ[b]);                   // Q[b][lane], b <= lane
-  }
-  const float2 c00 = Elem<E>::widen(e1[0]);       // cell (lane, 0) = Q[0][lane]
-  E e2[32];
-#pragma unroll
-  for (int a = 0; a < 32; ++a) e2[a] = tl[(lane + 1) * 32 + ((a + lane + 1) & 31)];
-  __syncwarp();
-  if (lane == 0) mbar_arrive(release);
-  float2 colP = make_float2(0.f, 0.f), rowQ = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int a = 0; a < 32; ++a) {
-    const float2 e = Elem<E>::widen(e2[a]);
-    if (a < lane) c_fmac(colP, e, rP[a]);          // P[a][lane], a < lane
-    else if (a > lane + 1) c_fma(rowQ, e, rQ[a]);  // Q[lane+1][a], a > lane+1
-  }
-  float2 t0 = make_float2(0.f, 0.f);
-  if (lane > 0) t0 = c_mul(c00, rQ[lane]);
-  t0 = warp_sum2(t0);
-  float2* y1 = yw + p * 32 + lane;
-  *y1 = c_add(*y1, c_add(rowP, colP));
-  __syncwarp();
-  float2 add = colQ;
-  if (lane == 0) add = c_add(add, t0);
-  float2* y2 = yw + q * 32 + lane;
-  *y2 = c_add(*y2, add);
-  __syncwarp();
-  if (lane < 31) {
-    float2* y3 = yw + q * 32 + lane + 1;
-    *y3 = c_add(*y3, rowQ);
-  }
-  __syncwarp();
-}
-
 // ||y - H x||^2 of one column (i, t) whose values are in shared memory:
 // for each coil, z = F_v(s_c . x) (unitary, batched FFT of `ncg` coils at a
 // time) compared with the hybrid data F_h'y on the sampled rows.  By
@@ -218,17 +176,17 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a -
 constexpr int kRSlots = 2;  // double-buffered r inputs / partial sums
 
 // Units of the n-th column a CTA processes are taken in an order rotated by
-// 3n: with few units per column the diagonal-pair units (the slowest, at
-// the end of a column's stream) would otherwise fall on the same consumer
-// warps in every column and set the pace.  Producers and consumers agree on
-// the order; the unit -> warp / stage mapping by position is unchanged.
+// 3n: with few units per column the diagonal units (the smaller ones, at the
+// end of a column's stream) would otherwise fall on the same consumer warps
+// in every column.  Producers and consumers agree on the order; the unit ->
+// warp / stage mapping by position is unchanged.
 __device__ __forceinline__ int unit_rotation(int n, int nunits) { return (int)((3ll * n) % nunits); }
 
 // Unit m of a column with nb blocks, in stream order: {kind, p, q, element
 // offset}.  Off-diagonal tiles (bj, bk), bj < bk, bk-major (an order that
 // does not depend on nb, so one table of (bj | bk << 8) for the largest nb
-// of a launch serves every slice), then the diagonal pairs (2r, 2r+1) (the
-// packed layout of kernels.h).
+// of a launch serves every slice), then the diagonal blocks (the packed
+// layout of kernels.h).
 __device__ __forceinline__ int tile_pq(int m) {   // the table's entry m, computed once per launch
   int bk = (int)((1.f + sqrtf(1.f + 8.f * (float)m)) * 0.5f);   // bk(bk-1)/2 <= m < bk(bk+1)/2
   while (bk * (bk - 1) / 2 > m) --bk;
@@ -241,8 +199,8 @@ __device__ __forceinline__ int4 decode_unit(int m, int nb, const int* tiles) {
     const int pq = tiles[m];
     return make_int4(UNIT_TILE, pq & 0xff, pq >> 8, m * kTileElems);
   }
-  const int r = m - ntiles;
-  return make_int4(UNIT_RECT, 2 * r, 2 * r + 1, ntiles * kTileElems + r * kRectElems);
+  const int d = m - ntiles;
+  return make_int4(UNIT_DIAG, d, d, ntiles * kTileElems + d * kDiagElems);
 }
 
 __device__ __forceinline__ int rotated_unit(int pos, int rot, int nunits) {
@@ -255,7 +213,7 @@ struct ColLayout {
 };
 __host__ __device__ inline ColLayout col_layout(int stages, int nb, int nslices, int work_max, int esize) {
   ColLayout L;
-  const size_t ny32 = (size_t)(nb + 1) * 32;
+  const size_t ny32 = (size_t)nb * 32;
   size_t o = 0;
   // full[S], empty[S], rfull[2], rempty[2], rv_full[2], yc_empty[2], col_done[2]
   L.bars = o; o += (2 * (size_t)stages + 5 * kRSlots) * 8;
@@ -303,7 +261,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
   uint64_t* yc_empty = rv_full + kRSlots;
   uint64_t* col_done = yc_empty + kRSlots;
   unsigned char* ring = smem + L.ring;
-  const int ny32m = (P.nb_max + 1) * 32;   // buffer stride (largest slice)
+  const int ny32m = P.nb_max * 32;   // buffer stride (largest slice)
   float2* ycopy = reinterpret_cast<float2*>(smem + L.ycopy);
   float2* rvec = reinterpret_cast<float2*>(smem + L.rvec);
   float2* bvec = reinterpret_cast<float2*>(smem + L.bvec);
@@ -367,7 +325,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
         for (; u < c.nunits; u += kProducers) {
           if (wraps > 0 && !mbar_wait(&empty[st], (uint32_t)((wraps - 1) & 1), P.err)) { ok = false; break; }
           const int4 un = decode_unit(rotated_unit(u, rot, c.nunits), c.nb, tiles);
-          const uint32_t bytes = (uint32_t)((un.x == UNIT_TILE ? kTileElems : kRectElems) * ES);
+          const uint32_t bytes = (uint32_t)((un.x == UNIT_TILE ? kTileElems : kDiagElems) * ES);
           mbar_arrive_expect_tx(&full[st], bytes);
           bulk_g2s(ring + (size_t)st * kStage, cb + (size_t)un.w * ES, bytes, &full[st], pol);
           ++issued;
@@ -472,7 +430,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
       const int2 wk = next_col(wp);
       const ColSlice& c = sl[wk.x];
       const bool sep_b = c.do_obj && c.bsrc != c.base;
-      const int ny32 = (c.nb + 1) * 32;
+      const int ny32 = c.nb * 32;
       const int slt = n % kRSlots;
       if (!mbar_wait(&rfull[slt], (uint32_t)((n / kRSlots) & 1), P.err)) return false;
       const float2* d = rslot + (size_t)slt * 3 * ny32m;
@@ -515,7 +473,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
         fid = 0.0;
         fid_slice = wk.x;
       }
-      const int ny32 = (c.nb + 1) * 32;
+      const int ny32 = c.nb * 32;
       const size_t cofs = (size_t)wk.y * c.Ny;
       float2* yc = ycopy + (size_t)bb * kConsumerWarps * ny32m;
       const float2* rv = rvec + (size_t)bb * ny32m;
@@ -571,6 +529,11 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
   // wait is at most one phase ahead of its barrier.  Every column's rv/yc
   // barriers are waited on (and col_done arrived at) even when the warp has
   // no unit in that column, for the same reason.
+  // this lane's place in a diagonal unit: patch (lr, lc) is stored when it
+  // meets the upper triangle
+  const int dlr = lane >> 2, dlc = lane & 3;
+  const bool diag_has = dlr <= 2 * dlc + 1;
+  const int diag_off = diag_has ? (dlc * (dlc + 1) + dlr) * 2 : 0;
   int u = warp, st = warp;
   uint32_t ph = 0;
   int w = w0;
@@ -589,8 +552,8 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
       if (!mbar_wait(&full[st], ph, P.err)) { failed = true; break; }
       const int4 un = decode_unit(rotated_unit(u, rot, c.nunits), c.nb, tiles);
       const E* tl = reinterpret_cast<const E*>(ring + (size_t)st * kStage);
-      if (un.x == UNIT_TILE) proc_tile<E>(tl, rv, yw, un.y, un.z, lane, &empty[st]);
-      else proc_rect<E>(tl, rv, yw, un.y, un.z, lane, &empty[st]);
+      if (un.x == UNIT_TILE) proc_tile<E>(tl, rv, yw, un.y, un.z, lane, &empty[st], 64, lane * 2, true);
+      else proc_tile<E>(tl, rv, yw, un.y, un.z, lane, &empty[st], 2 * kDiagLanes, diag_off, diag_has);
       st += kConsumerWarps;
       if (st >= S) { st -= S; ph ^= 1u; }
     }

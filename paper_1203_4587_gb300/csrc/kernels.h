@@ -20,23 +20,27 @@
 namespace recon {
 
 // ---- packed Hermitian storage of A_{i,t} = (mu I + G_{i,t})^{-1} -------------
-// Ny is padded to Nyp = 32*nb.  The upper triangle is cut into 32x32 blocks.
-// Units, in stream order:
-//   * every off-diagonal block (bj < bk), bk-major: 1024 elements in the
-//     order the matvec lanes read them: the pair (R, C), (R, C+1), C even,
-//     sits at complex position ((R%4)*4 + (C%8)/2)*64 + ((R/4)*4 + C/8)*2 and
-//     is stored planar, components (re_C, re_C+1, im_C, im_C+1), so one
-//     16-byte (8-byte at 16 bit) load gives a lane a real pair and an
-//     imaginary pair for packed FP32x2 arithmetic.
-//   * diagonal blocks in pairs (2q, 2q+1): 32 x 33 = 1056 elements.  Cell
-//     (a, b) holds P[a][b-1] for b > a (upper triangle of block 2q, row a)
-//     and Q[b][a] for b <= a (upper triangle of block 2q+1, column a); it is
-//     stored at b*32 + ((a+b) & 31).  With nb odd the last pair has no Q
-//     block (zeros).
-// This is exactly Ny(Ny+1)/2 elements when Ny is a multiple of 64.
-enum UnitKind : int { UNIT_TILE = 0, UNIT_RECT = 1 };
+// Ny is padded to Nyp = 32*nb.  The upper triangle is cut into 32x32 blocks,
+// and every block is read by one warp whose lane (lr, lc) = (lane/4, lane%4)
+// owns rows 4lr..4lr+3 and columns 8lc..8lc+7 of it.  Units, in stream order:
+//   * every off-diagonal block (bj < bk), bk-major: 1024 elements.  The pair
+//     (R, C), (R, C+1), C even, sits at complex position
+//     ((R%4)*4 + (C%8)/2)*64 + ((R/4)*4 + C/8)*2 and is stored planar,
+//     components (re_C, re_C+1, im_C, im_C+1), so one 16-byte (8-byte at
+//     16 bit) load gives a lane a real pair and an imaginary pair for packed
+//     FP32x2 arithmetic.
+//   * every diagonal block: 640 elements, the same planar pairs for the 20
+//     lanes whose 4x8 patch meets the upper triangle (lr <= 2lc+1), at
+//     ((R%4)*4 + (C%8)/2)*40 + (lc*(lc+1) + lr)*2.  Entries below the
+//     diagonal inside those patches are zero, and the diagonal is stored
+//     halved: every stored element e at (R, C) then adds e r_C to y_R and
+//     conj(e) r_R to y_C, the off-diagonal rule, and the two halves of the
+//     (real) diagonal make A_RR r_R.
+// The diagonal blocks carry 112 padding elements each over the triangle.
+enum UnitKind : int { UNIT_TILE = 0, UNIT_DIAG = 1 };
 constexpr int kTileElems = 1024;
-constexpr int kRectElems = 1056;
+constexpr int kDiagElems = 640;
+constexpr int kDiagLanes = 20;   // lanes of a diagonal block with stored elements
 
 struct PackInfo {
   int nb;          // 32-blocks per column

@@ -39,46 +39,36 @@ cudaError_t launch_circulant(const int* rows, const int* rowoff, const double2* 
   return cudaGetLastError();
 }
 
-// Position of A[R][C] (R <= C, both < Nyp) inside one column's packed stream.
+// Complex position of the planar pair holding A[R][C] (R <= C, both < Nyp,
+// C even) inside one column's packed stream (layout in kernels.h).
 __host__ __device__ inline long long packed_pos(int R, int C, int ntiles) {
   const int bj = R >> 5, bk = C >> 5, rr = R & 31, cc = C & 31;
+  const int qq = (rr & 3) * 4 + (cc & 7) / 2, lr = rr >> 2, lc = cc >> 3;
   if (bj < bk) {
     const long long u = (long long)bk * (bk - 1) / 2 + bj;
-    return u * kTileElems + ((rr & 3) * 4 + (cc & 7) / 2) * 64 + ((rr >> 2) * 4 + (cc >> 3)) * 2 + (cc & 1);
+    return u * kTileElems + qq * 64 + (lr * 4 + lc) * 2;
   }
-  const long long base = (long long)ntiles * kTileElems + (long long)(bj >> 1) * kRectElems;
-  int a, b;
-  if ((bj & 1) == 0) { a = rr; b = cc + 1; }   // block P of the pair: P[rr][cc], cc >= rr
-  else { a = cc; b = rr; }                     // block Q of the pair: Q[rr][cc], cc >= rr
-  return base + b * 32 + ((a + b) & 31);
+  return (long long)ntiles * kTileElems + (long long)bj * kDiagElems + qq * 2 * kDiagLanes + (lc * (lc + 1) + lr) * 2;
 }
 
-// Element (R, C), R <= C, of a packed column: tiles are planar per column
-// pair (see kernels.h), diagonal pairs hold (re, im) per element.
+// Element (R, C), R <= C, of a packed column as planar pairs (components
+// re_C, re_C+1, im_C, im_C+1); diagonal entries are stored halved.
 template <typename E>
 __device__ __forceinline__ void packed_store(E* Ac, int R, int C, int ntiles, double2 v) {
   using S = typename Elem<E>::S;
   S* sc = reinterpret_cast<S*>(Ac);
-  if ((R >> 5) < (C >> 5)) {
-    const long long b = 2 * packed_pos(R, C & ~1, ntiles);
-    sc[b + (C & 1)] = Elem<E>::cvt1(v.x);
-    sc[b + 2 + (C & 1)] = Elem<E>::cvt1(v.y);
-  } else {
-    const long long b = 2 * packed_pos(R, C, ntiles);
-    sc[b] = Elem<E>::cvt1(v.x);
-    sc[b + 1] = Elem<E>::cvt1(v.y);
-  }
+  if (R == C) v = make_double2(0.5 * v.x, 0.0);
+  const long long b = 2 * packed_pos(R, C & ~1, ntiles);
+  sc[b + (C & 1)] = Elem<E>::cvt1(v.x);
+  sc[b + 2 + (C & 1)] = Elem<E>::cvt1(v.y);
 }
 template <typename E>
 __device__ __forceinline__ float2 packed_load(const E* Ac, int R, int C, int ntiles) {
   using S = typename Elem<E>::S;
   const S* sc = reinterpret_cast<const S*>(Ac);
-  if ((R >> 5) < (C >> 5)) {
-    const long long b = 2 * packed_pos(R, C & ~1, ntiles);
-    return make_float2(Elem<E>::widen1(sc[b + (C & 1)]), Elem<E>::widen1(sc[b + 2 + (C & 1)]));
-  }
-  const long long b = 2 * packed_pos(R, C, ntiles);
-  return make_float2(Elem<E>::widen1(sc[b]), Elem<E>::widen1(sc[b + 1]));
+  const long long b = 2 * packed_pos(R, C & ~1, ntiles);
+  const float2 v = make_float2(Elem<E>::widen1(sc[b + (C & 1)]), Elem<E>::widen1(sc[b + 2 + (C & 1)]));
+  return R == C ? make_float2(2.f * v.x, 0.f) : v;
 }
 
 constexpr int kPlanThreads = 256;
