@@ -14,8 +14,11 @@ namespace recon {
 
 constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;
-constexpr int kProducers = 2;                 // producer warps (one issuing thread each)
-constexpr int kColThreads = kConsumers + 32 * (kProducers + 2);  // + producers, r loader, column manager
+// producer warps (one issuing thread each): 2 for 8-byte elements, 4 for
+// the half-size units of 16-bit storage (more copies per byte)
+__host__ __device__ constexpr int col_producers(int esize) { return esize == 8 ? 2 : 4; }
+// consumers + producers + r loader + column manager
+__host__ __device__ constexpr int col_threads(int esize) { return kConsumers + 32 * (col_producers(esize) + 2); }
 // A ring stage holds the largest unit of the storage type: kTileElems
 // elements of esize bytes (8 FP32, 4 FP16/BF16; both multiples of 16 bytes).
 __host__ __device__ constexpr int stage_bytes(int esize) { return kTileElems * esize; }
@@ -237,10 +240,11 @@ __host__ __device__ inline ColLayout col_layout(int stages, int nb, int nslices,
 // Persistent column-inverse kernel over a work list of (slice, column) pairs,
 // warp-specialised and free of block-wide barriers in the main loop (all
 // hand-offs are bounded mbarrier waits):
-//   warps 8-9  producers: stream the packed inverses with the TMA engine
-//            (cp.async.bulk, L2 evict_first) into a ring of S stages
-//   warp 10  r loader: bulk-copies each column's right-hand-side inputs
-//   warp 11  column manager: r = base + coef*add into rvec[n&1]; after the
+//   warps 8..8+P-1  producers (P = 2 at FP32, 4 at 16 bit): stream the
+//            packed inverses with the TMA engine (cp.async.bulk, L2
+//            evict_first) into a ring of S stages
+//   warp 8+P  r loader: bulk-copies each column's right-hand-side inputs
+//   warp 9+P  column manager: r = base + coef*add into rvec[n&1]; after the
 //            consumers are done, x = sum of the 8 partial y vectors, store,
 //            objective dot products, clear the partials
 //   warps 0-7 consumers: Hermitian matvec of each unit into their own
@@ -248,8 +252,9 @@ __host__ __device__ inline ColLayout col_layout(int stages, int nb, int nslices,
 // Columns of slices whose stop flag is set are dropped from the work list
 // (every role reads the same snapshot of the flags).
 template <typename E>
-__global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
+__global__ void __launch_bounds__(col_threads(Elem<E>::bytes), 1) k_col_inverse(ColLaunch P) {
   extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int kProducers = col_producers(Elem<E>::bytes);
   constexpr int kStage = stage_bytes(Elem<E>::bytes);
   const ColLayout L = col_layout(P.stages, P.nb_max, P.nslices, P.work_max, Elem<E>::bytes);
   const int S = P.stages;
@@ -304,9 +309,9 @@ __global__ void __launch_bounds__(kColThreads, 1) k_col_inverse(ColLaunch P) {
     // ---------------- producers: stream packed inverses into the ring -------
     // Producer p issues the units whose index (counted across this CTA's
     // columns) is p mod kProducers, into stage (index mod S): one issuing
-    // thread streams a bulk copy every ~150 ns at best, which limits 4 KB
-    // (16-bit) units, so the issue work is split.  S is a multiple of
-    // kProducers, so each producer owns a fixed set of stages.
+    // thread streams a bulk copy every ~150 ns at best, which would limit
+    // the 2.5-4 KB units of 16-bit storage, so the issue work is split.  S is
+    // a multiple of kProducers, so each producer owns a fixed set of stages.
     if (lane == 0) {
       const int p = warp - kConsumerWarps;
       const uint64_t pol = policy_evict_first();
@@ -611,9 +616,9 @@ cudaError_t launch_col_inverse(const ColLaunch& p, int storage, int grid, cudaSt
   cudaError_t e = prepare_col_inverse(storage, smem);
   if (e != cudaSuccess) return e;
   switch (storage) {
-    case 0: k_col_inverse<float2><<<grid, kColThreads, smem, s>>>(p); break;
-    case 1: k_col_inverse<__half2><<<grid, kColThreads, smem, s>>>(p); break;
-    case 2: k_col_inverse<__nv_bfloat162><<<grid, kColThreads, smem, s>>>(p); break;
+    case 0: k_col_inverse<float2><<<grid, col_threads(8), smem, s>>>(p); break;
+    case 1: k_col_inverse<__half2><<<grid, col_threads(4), smem, s>>>(p); break;
+    case 2: k_col_inverse<__nv_bfloat162><<<grid, col_threads(4), smem, s>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   note_launch();

@@ -1,7 +1,7 @@
 """CPU model of the column-inverse kernel's mbarrier protocol (no GPU).
 
 k_col_inverse hands data between warps with mbarriers and parity waits:
-producers (units alternate between two issuing threads) stream units into
+producers (units go round four issuing threads) stream units into
 a ring of S stages (full/empty barriers), a
 loader fills two r slots, a manager prepares r and reduces partial sums, and
 eight consumers walk units g = warp, warp+8, ...  A parity wait is only exact
@@ -164,11 +164,11 @@ def simulate(S, nunits, ncols, seed, W=8, per_column_mapping=False, producers=1)
     assert processed == set(range(ncols * nunits))
 
 
-@pytest.mark.parametrize("producers", [1, 2])
+@pytest.mark.parametrize("producers", [1, 2, 4])
 @pytest.mark.parametrize("S", [8, 16, 24, 32])
 @pytest.mark.parametrize("nunits", [1, 2, 3, 13, 32, 36])
 def test_protocol_holds_for_ring_depths_multiple_of_8(S, nunits, producers):
-    """The kernel runs two producers (units alternate between them)."""
+    """The kernel runs four producers (units go round them)."""
     for ncols in (1, 2, 5):
         for seed in range(3):
             simulate(S, nunits, ncols, seed, producers=producers)
