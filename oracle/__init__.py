@@ -15,7 +15,8 @@ Lagrangian and Parallel Processing":
   (Section IV-C, Eqs. HconjH, separate_x, eigen_mu)
 * Algorithm 1 (synthesis prior, temporal DFT, or the undecimated temporal Haar
   frame, a redundant tight frame) and Algorithm 2 (analysis prior, temporal
-  TV), step by step in the paper's order
+  TV; or spatio-temporal differences with a conjugate-gradient m-update,
+  ``stv.py``), step by step in the paper's order
 * objective J and the convergence ratio Delta(k) (Section V, Eq. r_ratio)
 * the reverse-mode gradient of unrolled Algorithm 2 (``grad.py``)
 * the 16-bit storage encoding with per-frame power-of-two scales
@@ -23,7 +24,8 @@ Lagrangian and Parallel Processing":
 
 Every function here is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_pins.py``, ``tests/test_oracle_grad.py``,
-``tests/test_oracle_frame.py`` and ``tests/test_oracle_precision.py`` against closed
+``tests/test_oracle_frame.py``, ``tests/test_oracle_precision.py`` and
+``tests/test_oracle_stv.py`` against closed
 forms, brute force, finite differences or invariants.
 """
 
@@ -31,5 +33,7 @@ from .admm import *  # noqa: F401,F403
 from .admm import __all__ as _admm_all
 from .grad import unrolled_tv_adjoint, unrolled_tv_forward, unrolled_tv_loss_and_grad  # noqa: F401
 from . import precision  # noqa: F401
+from .stv import admm_analysis_stv, cg_steps, objective_stv, stv_M, stv_R, stv_Radj  # noqa: F401
 
-__all__ = list(_admm_all) + ["unrolled_tv_forward", "unrolled_tv_adjoint", "unrolled_tv_loss_and_grad"]
+__all__ = list(_admm_all) + ["unrolled_tv_forward", "unrolled_tv_adjoint", "unrolled_tv_loss_and_grad",
+                             "admm_analysis_stv", "cg_steps", "objective_stv", "stv_M", "stv_R", "stv_Radj"]

@@ -355,10 +355,17 @@ class Problem:
     def fid(self, x_cols):
         return data_residual_columns(x_cols, self.yhat, self.sens, self.mask, self.cols)
 
-    def solve(self, prior, lam, mu, rho=0.5, iters=50, tol=0.0, objective=True, levels=2):
-        """prior: "tv" (Algorithm 2), "dft" (Algorithm 1, unitary temporal DFT) or
-        "haar" (Algorithm 1, undecimated temporal Haar frame of ``levels`` levels)."""
+    def solve(self, prior, lam, mu, rho=0.5, iters=50, tol=0.0, objective=True, levels=2, ws=1.0, cg=5):
+        """prior: "tv" (Algorithm 2), "dft" (Algorithm 1, unitary temporal DFT),
+        "haar" (Algorithm 1, undecimated temporal Haar frame of ``levels`` levels)
+        or "stv" (Algorithm 2 with spatio-temporal differences of spatial weight
+        ``ws`` and a ``cg``-step CG m-update; needs every column)."""
         fid = self.fid if objective else None
+        if prior == "stv":
+            from .stv import admm_analysis_stv
+            if len(self.cols) != self.sens.shape[2]:
+                raise ValueError("the spatio-temporal prior couples columns: solve on all of them")
+            return admm_analysis_stv(self.b, self.inv, lam, mu, rho, iters, ws=ws, cg=cg, fid=fid, tol=tol)
         if prior == "tv":
             return admm_analysis_tv(self.b, self.inv, lam, mu, rho, iters, fid=fid, tol=tol)
         if prior == "dft":

@@ -1,0 +1,177 @@
+"""Pins of the oracle's spatio-temporal analysis operator, its CG m-update and
+Algorithm 2 with it (CPU, no GPU).
+
+None of these re-derive the code under test:
+* R and R' are adjoint (inner products on random fields, several shapes,
+  including length-1 axes);
+* (rho I + R'R) equals a dense matrix assembled from Kronecker products of
+  one-dimensional difference matrices;
+* CG reaches the dense solve once it has taken as many steps as the system
+  has unknowns, and converges to the closed form given by the DCT-II, which
+  diagonalises every non-circular difference Laplacian D'D (eigenvalues
+  2 - 2 cos(pi k / n));
+* CG's error in the energy norm never grows from step to step;
+* with w = 0 and enough CG steps, Algorithm 2 reduces to the temporal-TV
+  oracle (Thomas / dense m-update);
+* the converged ADMM point satisfies the KKT conditions of
+  lambda ||R x||_1 + ||y - H x||^2 on a tiny problem.
+"""
+
+import numpy as np
+import pytest
+import scipy.fft
+
+import oracle
+from test_oracle_pins import _small_case
+
+
+def _rand(rng, shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def _D(n):
+    D = np.zeros((max(n - 1, 0), n))
+    for k in range(n - 1):
+        D[k, k], D[k, k + 1] = -1.0, 1.0
+    return D
+
+
+def _dense_M(shape, rho, ws):
+    """rho I + R'R for x[t, j, i] flattened C-order, from Kronecker products."""
+    Nt, Ny, Nx = shape
+    It, Iy, Ix = np.eye(Nt), np.eye(Ny), np.eye(Nx)
+    Lt, Ly, Lx = (_D(n).T @ _D(n) for n in (Nt, Ny, Nx))
+    L = np.kron(np.kron(Lt, Iy), Ix) + ws ** 2 * (np.kron(np.kron(It, Ly), Ix) + np.kron(np.kron(It, Iy), Lx))
+    return rho * np.eye(Nt * Ny * Nx) + L
+
+
+@pytest.mark.parametrize("shape", [(4, 5, 6), (1, 3, 4), (5, 1, 3), (3, 4, 1), (2, 2, 2)])
+@pytest.mark.parametrize("ws", [1.0, 0.37])
+def test_R_adjoint(shape, ws):
+    rng = np.random.default_rng(sum(shape))
+    x = _rand(rng, shape)
+    Rx = oracle.stv_R(x, ws)
+    u = tuple(_rand(rng, c.shape) for c in Rx)
+    lhs = sum(np.vdot(a, b) for a, b in zip(Rx, u))
+    rhs = np.vdot(x, oracle.stv_Radj(u, ws, shape))
+    assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5), (1, 3, 2), (4, 1, 3)])
+@pytest.mark.parametrize("ws", [1.0, 0.5, 0.0])
+def test_M_equals_kronecker_assembly(shape, ws):
+    rho = 0.5
+    n = int(np.prod(shape))
+    cols = []
+    for k in range(n):
+        e = np.zeros(n, complex)
+        e[k] = 1.0
+        cols.append(oracle.stv_M(e.reshape(shape), rho, ws).ravel())
+    np.testing.assert_allclose(np.stack(cols, axis=1), _dense_M(shape, rho, ws), atol=1e-14)
+
+
+def test_cg_exact_after_n_steps():
+    shape, rho, ws = (2, 3, 4), 0.5, 1.0
+    rng = np.random.default_rng(3)
+    rhs, m0 = _rand(rng, shape), _rand(rng, shape)
+    exact = np.linalg.solve(_dense_M(shape, rho, ws), rhs.ravel()).reshape(shape)
+    m = oracle.cg_steps(lambda a: oracle.stv_M(a, rho, ws), rhs, m0, int(np.prod(shape)))
+    np.testing.assert_allclose(m, exact, atol=1e-10 * np.abs(exact).max())
+
+
+def _dct_solve(rhs, rho, ws):
+    """(rho I + R'R)^{-1} rhs by the DCT-II diagonalisation of each D'D."""
+    Nt, Ny, Nx = rhs.shape
+    lam = [2.0 - 2.0 * np.cos(np.pi * np.arange(n) / n) for n in (Nt, Ny, Nx)]
+    den = rho + lam[0][:, None, None] + ws ** 2 * (lam[1][None, :, None] + lam[2][None, None, :])
+    c = scipy.fft.dctn(rhs, type=2, norm="ortho")
+    return scipy.fft.idctn(c / den, type=2, norm="ortho")
+
+
+@pytest.mark.parametrize("ws", [1.0, 0.3])
+def test_cg_converges_to_dct_closed_form(ws):
+    shape, rho = (7, 6, 9), 0.5
+    rng = np.random.default_rng(4)
+    rhs = _rand(rng, shape)
+    m = oracle.cg_steps(lambda a: oracle.stv_M(a, rho, ws), rhs, np.zeros(shape, complex), 120)
+    exact = _dct_solve(rhs, rho, ws)
+    np.testing.assert_allclose(m, exact, atol=1e-9 * np.abs(exact).max())
+
+
+def test_cg_energy_error_never_grows():
+    shape, rho, ws = (6, 8, 8), 0.5, 1.0
+    rng = np.random.default_rng(5)
+    rhs, m0 = _rand(rng, shape), _rand(rng, shape)
+    exact = _dct_solve(rhs, rho, ws)
+
+    def energy(m):
+        e = m - exact
+        return np.vdot(e, oracle.stv_M(e, rho, ws)).real
+
+    errs = [energy(oracle.cg_steps(lambda a: oracle.stv_M(a, rho, ws), rhs, m0, s)) for s in range(0, 12)]
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-3 * errs[0]
+
+
+def test_zero_spatial_weight_is_temporal_tv():
+    x, sens, mask, y = _small_case(Nx=5, Ny=6, Nt=5, Nc=2, R=2, noise=0.02, seed=21)
+    lam, mu, rho, iters = 0.02, 0.1, 0.5, 15
+    P = oracle.Problem(y, sens, mask, mu)
+    xt, it = oracle.admm_analysis_tv(P.b, P.inv, lam, mu, rho, iters, fid=P.fid)
+    # global CG on a system that decouples per pixel: at most Nt distinct eigenvalues
+    xs, is_ = oracle.admm_analysis_stv(P.b, P.inv, lam, mu, rho, iters, ws=0.0, cg=x.shape[0] + 1, fid=P.fid)
+    np.testing.assert_allclose(xs, xt, atol=1e-10 * np.abs(xt).max())
+    np.testing.assert_allclose(is_["J"], it["J"], rtol=1e-10)
+
+
+def _stv_converged():
+    x, sens, mask, y = _small_case(Nx=4, Ny=4, Nt=4, Nc=2, R=2, noise=0.05, seed=18)
+    lam, mu, rho, ws = 0.05, 0.1, 0.5, 0.8
+    P = oracle.Problem(y, sens, mask, mu)
+    xr, info = oracle.admm_analysis_stv(P.b, P.inv, lam, mu, rho, 3000, ws=ws, cg=70)
+    return x, sens, mask, y, lam, mu, rho, ws, xr, info
+
+
+def test_kkt_stv_on_tiny_problem():
+    """2 H'(Hx - y) + lambda R' g = 0, g = 2 mu1 d1 / lambda in the subdifferential of ||.||_1 at R x."""
+    x, sens, mask, y, lam, mu, rho, ws, xr, info = _stv_converged()
+    _, m, d1, d2 = info["state"]
+    np.testing.assert_allclose(m, xr, atol=1e-9)                      # the split is tight at convergence
+    mu1 = mu / rho
+    g = tuple(2 * mu1 * d / lam for d in d1)
+    Rx = oracle.stv_R(xr, ws)
+    for gc, rc in zip(g, Rx):
+        assert np.abs(gc).max() <= 1 + 1e-8
+        # the sign condition on the clearly nonzero differences (the zeros sit at
+        # |R x| ~ 1e-10; a few small ones near 1e-3 converge more slowly)
+        big = np.abs(rc) > 1e-3
+        assert big.sum() > 20
+        np.testing.assert_allclose(gc[big], rc[big] / np.abs(rc[big]), atol=1e-6)
+    grad = 2 * oracle.adjoint_op(oracle.forward_op(xr, sens, mask) - y, sens, mask)
+    stat = grad + lam * oracle.stv_Radj(g, ws, xr.shape)
+    assert np.linalg.norm(stat) < 1e-8 * max(1.0, np.linalg.norm(grad))
+
+
+def test_objective_is_lambda_l1_plus_fidelity():
+    x, sens, mask, y = _small_case(Nx=3, Ny=4, Nt=3, Nc=2, R=2, seed=22)
+    P = oracle.Problem(y, sens, mask, 0.1)
+    ws = 0.6
+    J = oracle.objective_stv(x, 0.3, ws, P.fid)
+    l1 = 0.0
+    for t in range(3):                                   # element by element, every difference
+        for j in range(4):
+            for i in range(3):
+                if t + 1 < 3:
+                    l1 += abs(x[t + 1, j, i] - x[t, j, i])
+                if i + 1 < 3:
+                    l1 += ws * abs(x[t, j, i + 1] - x[t, j, i])
+                if j + 1 < 4:
+                    l1 += ws * abs(x[t, j + 1, i] - x[t, j, i])
+    assert abs(J - (0.3 * l1 + oracle.data_residual(x, y, sens, mask))) < 1e-10 * J
+
+
+def test_column_subset_refused():
+    x, sens, mask, y = _small_case(Nx=4, Ny=4, Nt=2, Nc=2, R=2, seed=23)
+    P = oracle.Problem(y, sens, mask, 0.1, cols=[0, 2])
+    with pytest.raises(ValueError):
+        P.solve("stv", 0.01, 0.1, iters=2)
