@@ -17,7 +17,9 @@ Extra keys on the JSON line:
   cpu_baseline  the FP64 oracle on a bounded sample (a subset of columns,
                 single-threaded), scaled to the full workload
   variants      the synthesis prior (Algorithm 1: temporal DFT, and the
-                undecimated temporal Haar frame with 2 levels) and lambda=0.02
+                undecimated temporal Haar frame with 2 levels), lambda=0.02,
+                and Algorithm 2 with spatio-temporal differences (w = 1) and a
+                5-step CG m-update
   batched       64 uneven slices in one batched solve (graph replay)
   precision     384x384x48 frames x16 coils, R=6: FP32 / FP16 / BF16 storage
                 (inverses and hybrid coil data; 16-bit k-space for the 16-bit
@@ -644,11 +646,12 @@ def run_native(args):
     if not args.no_variants and rank == 0:
         var = {}
         for name, prior, lam in (("dft_lambda0.005", "dft", 0.005), ("tv_lambda0.02", "tv", 0.02),
-                                 ("dft_lambda0.02", "dft", 0.02), ("haar2_lambda0.005", "haar", 0.005)):
+                                 ("dft_lambda0.02", "dft", 0.02), ("haar2_lambda0.005", "haar", 0.005),
+                                 ("stv_w1_cg5_lambda0.005", "stv", 0.005)):
             if prior == args.prior and lam == w["lam"]:
                 continue
             p2 = Plan(mask, sens, lam, w["mu"], prior=prior, rho=w["rho"], max_iters=w["iters"],
-                      storage=args.storage, frame_levels=2)
+                      storage=args.storage, frame_levels=2, spatial_weight=1.0, cg_steps=5)
             p2.autotune()
             for _ in range(2):
                 p2.solve(kspace, out, info=False)

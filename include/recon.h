@@ -51,13 +51,19 @@ typedef struct recon_plan recon_plan; /* opaque, owned by the library */
 typedef enum {
   RECON_PRIOR_TV = 0,   /* Algorithm 2: analysis prior, R = D_t (non-circular temporal differences) */
   RECON_PRIOR_DFT = 1,  /* Algorithm 1: synthesis prior, Psi = unitary temporal DFT */
-  RECON_PRIOR_HAAR = 2  /* Algorithm 1: synthesis prior, Psi = undecimated temporal Haar frame of
+  RECON_PRIOR_HAAR = 2, /* Algorithm 1: synthesis prior, Psi = undecimated temporal Haar frame of
                            opts.frame_levels levels with circular shifts: a_0 = x and for level j
                            (shift s = 2^(j-1) mod Nt) a_j[t] = (a_{j-1}[t] + a_{j-1}[t+s]) / 2,
                            d_j[t] = (a_{j-1}[t] - a_{j-1}[t+s]) / 2; coefficients d_1..d_L, a_L.
                            A redundant tight frame (Psi'Psi = I, Psi Psi' != I): the w-update
                            keeps the (1/mu)(I - Psi Psi') term of the lemma in Section IV-A,
                            w = u + Psi (A (H'y + mu Psi'u) - Psi'u) with u = v + d. */
+  RECON_PRIOR_STV = 3   /* Algorithm 2: analysis prior, R x = (D_t x, w D_x x, w D_y x): non-circular
+                           differences along t, the horizontal and the vertical axis, spatial weight
+                           w = opts.spatial_weight; l1 over all three components (anisotropic).  The
+                           m-update (mu2/mu1 I + R'R) m = R'(v - d1) + mu2/mu1 (x + d2) takes
+                           opts.cg_steps conjugate-gradient steps from the previous m (Section IV-B:
+                           CG where no closed form is used).  Couples columns: no slab plans. */
 } recon_prior;
 
 typedef enum {
@@ -104,6 +110,8 @@ typedef struct {
                        (min 8) and capped by shared memory; 0 = deepest that fits (default) */
   int profile;      /* 1 = time every kernel of a solve with CUDA events (default 0) */
   int frame_levels; /* levels L of RECON_PRIOR_HAAR, 1..6 (default 2); the frame has L+1 channels */
+  float spatial_weight; /* w of RECON_PRIOR_STV, >= 0 (default 1) */
+  int cg_steps;     /* CG steps per iteration of RECON_PRIOR_STV, 1..64 (default 5) */
 } recon_opts;
 
 typedef struct {

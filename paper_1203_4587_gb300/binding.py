@@ -23,7 +23,7 @@ import torch
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "lib", "librecon.so")
 
-PRIOR = {"tv": 0, "dft": 1, "haar": 2}
+PRIOR = {"tv": 0, "dft": 1, "haar": 2, "stv": 3}
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 STATUS = {0: "RECON_OK", 1: "RECON_ERR_INVALID_ARG", 2: "RECON_ERR_MASK_NOT_CARTESIAN", 3: "RECON_ERR_OOM",
           4: "RECON_ERR_CUDA", 5: "RECON_ERR_TIMEOUT", 6: "RECON_ERR_NONFINITE", 7: "RECON_ERR_UNSUPPORTED"}
@@ -42,7 +42,7 @@ EXPORTS = ["recon_default_opts", "recon_plan_create", "recon_solve", "recon_solv
 class Opts(C.Structure):
     _fields_ = [("rho", C.c_float), ("max_iters", C.c_int), ("tol", C.c_double), ("storage", C.c_int),
                 ("objective", C.c_int), ("mask_full", C.c_int), ("col_stages", C.c_int), ("profile", C.c_int),
-                ("frame_levels", C.c_int)]
+                ("frame_levels", C.c_int), ("spatial_weight", C.c_float), ("cg_steps", C.c_int)]
 
 
 class Info(C.Structure):
@@ -177,7 +177,10 @@ def _c64(t: torch.Tensor, dev=None) -> torch.Tensor:
 def default_opts(**over) -> Opts:
     o = Opts()
     load().recon_default_opts(C.byref(o))
+    names = {f for f, _ in Opts._fields_}
     for k, v in over.items():
+        if k not in names:
+            raise TypeError(f"unknown option {k!r}")
         if k == "storage" and isinstance(v, str):
             v = STORAGE[v]
         setattr(o, k, v)

@@ -100,6 +100,8 @@ void recon_default_opts(recon_opts* o) {
   o->col_stages = 0;
   o->profile = 0;
   o->frame_levels = 2;
+  o->spatial_weight = 1.f;
+  o->cg_steps = 5;
 }
 
 const char* recon_status_string(recon_status s) {
@@ -271,13 +273,17 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
   if (!valid_ptr(mask) || !valid_ptr(sens)) return fail(RECON_ERR_INVALID_ARG, "mask or sens is NULL");
   if (!(mu > 0.f) || !std::isfinite(mu)) return fail(RECON_ERR_INVALID_ARG, "mu must be > 0");
   if (!(lambda >= 0.f) || !std::isfinite(lambda)) return fail(RECON_ERR_INVALID_ARG, "lambda must be >= 0");
-  if (prior != RECON_PRIOR_TV && prior != RECON_PRIOR_DFT && prior != RECON_PRIOR_HAAR)
+  if (prior != RECON_PRIOR_TV && prior != RECON_PRIOR_DFT && prior != RECON_PRIOR_HAAR && prior != RECON_PRIOR_STV)
     return fail(RECON_ERR_INVALID_ARG, "unknown prior");
+  if (prior == RECON_PRIOR_STV && (i0 != 0 || W != Nxf))
+    return fail(RECON_ERR_UNSUPPORTED, "the spatio-temporal prior couples columns: no slab plans");
   recon_opts o;
   recon_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.rho > 0.f) || o.max_iters < 0 || !(o.tol >= 0.0) || o.storage < 0 || o.storage > 2 || o.col_stages < 0 ||
-      o.objective < 0 || o.objective > 2 || (prior == RECON_PRIOR_HAAR && (o.frame_levels < 1 || o.frame_levels > 6)))
+      o.objective < 0 || o.objective > 2 || (prior == RECON_PRIOR_HAAR && (o.frame_levels < 1 || o.frame_levels > 6)) ||
+      (prior == RECON_PRIOR_STV && (!(o.spatial_weight >= 0.f) || !std::isfinite(o.spatial_weight) ||
+                                    o.cg_steps < 1 || o.cg_steps > 64)))
     return fail(RECON_ERR_INVALID_ARG, "invalid options");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
@@ -353,7 +359,9 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
     PC(p->alloc((void**)&p->yscale, Nt * sizeof(float)));
   }
   PC(p->alloc((void**)&p->b, nimg * sizeof(float2)));
-  // TV: m, d1, p;  DFT: u = v + d;  Haar: u ((L+1) channels) and s = Psi'u
+  // TV: m, d1, p;  DFT: u = v + d;  Haar: u ((L+1) channels) and s = Psi'u;
+  // STV: m and q (s0), d1 and e with three components (s1), p and the CG
+  // residual (s2), the CG directions (r, cgd)
   const size_t nu = (prior == RECON_PRIOR_HAAR) ? (size_t)(o.frame_levels + 1) * nimg : nimg;
   for (int k = 0; k < 2; ++k) {
     PC(p->alloc((void**)&p->s0[k], nu * sizeof(float2)));
@@ -362,7 +370,12 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
       PC(p->alloc((void**)&p->s2[k], nimg * sizeof(float2)));
     }
     if (prior == RECON_PRIOR_HAAR) PC(p->alloc((void**)&p->s1[k], nimg * sizeof(float2)));
+    if (prior == RECON_PRIOR_STV) {
+      PC(p->alloc((void**)&p->s1[k], 3 * nimg * sizeof(float2)));
+      PC(p->alloc((void**)&p->s2[k], nimg * sizeof(float2)));
+    }
   }
+  if (prior == RECON_PRIOR_STV) PC(p->alloc((void**)&p->cgd, nimg * sizeof(float2)));
   PC(p->alloc((void**)&p->x, nimg * sizeof(float2)));
   if (prior != RECON_PRIOR_TV) PC(p->alloc((void**)&p->r, nimg * sizeof(float2)));
   PC(p->alloc((void**)&p->tmp_a, nimg * sizeof(float2)));

@@ -173,6 +173,35 @@ HaarSlice haar_desc(recon_plan* p, int k, int K) {
   return d;
 }
 
+// Iteration k (1-based) of the spatio-temporal prior; k = K+1 is the final
+// prior term.  The state buffers are updated in place (m by the CG steps,
+// d1 and p by the finishing kernel); a solve starts from m = p = x = H'y, d1 = 0.
+StvSlice stv_desc(recon_plan* p, int k, int K, double* red) {
+  StvSlice d{};
+  d.Nx = p->Nx;
+  d.Ny = p->Ny;
+  d.Nt = p->Nt;
+  d.n = (int)p->nimg();
+  d.cg = p->opts.cg_steps;
+  d.tau1 = (float)(p->lam / (2.0 * (p->mu / p->opts.rho)));
+  d.rho = p->opts.rho;
+  d.ws = p->opts.spatial_weight;
+  d.m = p->s0[0];
+  d.q = p->s0[1];
+  d.d1 = p->s1[0];
+  d.e = p->s1[1];
+  d.p = p->s2[0];
+  d.r = p->s2[1];
+  d.pc[0] = p->r;
+  d.pc[1] = p->cgd;
+  d.x = p->x;
+  d.stop = p->flags + FLAG_STOP;
+  d.write_state = k <= K ? 1 : 0;
+  d.red = red + (size_t)(std::min(k, std::max(K, 1)) - 1) * (2 * d.cg + 1);
+  d.prior_acc = p->trace_prior + (k - 1);
+  return d;
+}
+
 ColSlice col_desc(recon_plan* p, int k, bool fused) {
   ColSlice c{};
   c.A = p->A;
@@ -190,6 +219,10 @@ ColSlice col_desc(recon_plan* p, int k, bool fused) {
   if (p->prior == RECON_PRIOR_TV) {
     c.base = p->b;
     c.add = p->s2[k & 1];
+    c.coef = p->mu;
+  } else if (p->prior == RECON_PRIOR_STV) {   // r = H'y + mu2 p, p = m' - d2 (in place)
+    c.base = p->b;
+    c.add = p->s2[0];
     c.coef = p->mu;
   } else {
     c.base = p->r;
@@ -242,6 +275,19 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
         (p->opts.objective != 0 || p->opts.tol > 0.0) != e->obj || (p->opts.objective == 2) != (p0->opts.objective == 2))
       return fail(RECON_ERR_INVALID_ARG, "batched plans must share prior, max_iters, storage and objective mode");
     if (p->device != p0->device) return fail(RECON_ERR_INVALID_ARG, "batched plans must be on one device");
+    if (p->prior == RECON_PRIOR_STV && p->opts.cg_steps != p0->opts.cg_steps)
+      return fail(RECON_ERR_INVALID_ARG, "batched spatio-temporal plans must share cg_steps");
+  }
+  if (e->prior == RECON_PRIOR_STV) {
+    e->cg = p0->opts.cg_steps;
+    const size_t per = (size_t)std::max(e->K, 1) * (2 * e->cg + 1);
+    e->stv_red.assign(n, nullptr);
+    for (int q = 0; q < n; ++q) RC(e->arena.alloc(reinterpret_cast<void**>(&e->stv_red[q]), per * sizeof(double)));
+    RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_stv_count), (size_t)n * sizeof(unsigned)));
+    RC(cudaMemset(e->d_stv_count, 0, (size_t)n * sizeof(unsigned)));
+    int blocks = 0;
+    for (int q = 0; q < n; ++q) blocks += (int)((plans[q]->nimg() + kStvBlockElems - 1) / kStvBlockElems);
+    RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_stv_part), (size_t)std::max(blocks, 1) * sizeof(double)));
   }
   const int K = e->K;
   // column descriptors, K sets (at least one so the layout is valid at K = 0)
@@ -287,12 +333,17 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
 }
 
 int engine_tile_candidates(const Engine* e, int* out) {
+  if (e->prior == RECON_PRIOR_STV) {   // fixed elements per block
+    out[0] = kStvBlockElems;
+    return 1;
+  }
   if (e->tv) return tv_tile_candidates(e->Nt_max, out);
   if (e->prior == RECON_PRIOR_HAAR) return haar_tile_candidates(e->Nt_max, e->levels, out);
   return dft_tile_candidates(e->Nt_max, out);
 }
 
 int engine_default_tile(const Engine* e) {
+  if (e->prior == RECON_PRIOR_STV) return kStvBlockElems;
   if (e->tv) return tv_tile_px(e->Nt_max);
   if (e->prior == RECON_PRIOR_HAAR) return haar_tile_px(e->Nt_max, e->levels);
   return dft_tile_px();
@@ -308,10 +359,24 @@ recon_status engine_set_tile(Engine* e, int px) {
   int blocks = 0;
   for (int q = 0; q < n; ++q) {
     tile0[q] = blocks;
-    blocks += (int)((e->plans[q]->npix() + px - 1) / px);
+    // temporal kernels tile pixels; the spatio-temporal kernels tile all elements
+    const size_t units = e->prior == RECON_PRIOR_STV ? e->plans[q]->nimg() : e->plans[q]->npix();
+    blocks += (int)((units + px - 1) / px);
   }
   void* old = e->d_tmp;
-  if (e->tv) {
+  if (e->prior == RECON_PRIOR_STV) {
+    std::vector<StvSlice> t((size_t)(K + 1) * n);
+    for (int k = 1; k <= K + 1; ++k)
+      for (int q = 0; q < n; ++q) {
+        StvSlice d = stv_desc(e->plans[q], k, K, e->stv_red[q]);
+        d.tile0 = tile0[q];
+        d.nblk = (int)((e->plans[q]->nimg() + px - 1) / px);
+        d.part = e->d_stv_part;
+        d.count = e->d_stv_count + q;
+        t[(size_t)(k - 1) * n + q] = d;
+      }
+    RC(upload(e->arena, reinterpret_cast<StvSlice**>(&e->d_tmp), t));
+  } else if (e->tv) {
     std::vector<TvSlice> t((size_t)(K + 1) * n);
     for (int k = 1; k <= K + 1; ++k)
       for (int q = 0; q < n; ++q) {
@@ -394,7 +459,13 @@ recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s) {
   L.nblocks = e->tmp_blocks;
   L.Nt_max = e->Nt_max;
   L.tile_px = e->tile_px;
-  if (e->tv) {
+  if (e->prior == RECON_PRIOR_STV) {   // the prior / threshold kernel of the set
+    StvLaunch S{};
+    S.slices = static_cast<StvSlice*>(e->d_tmp) + (size_t)set * e->n;
+    S.nslices = e->n;
+    S.nblocks = e->tmp_blocks;
+    RC(launch_stv_prior(S, s));
+  } else if (e->tv) {
     L.slices = static_cast<TvSlice*>(e->d_tmp) + (size_t)set * e->n;
     RC(launch_tv_temporal(L, s));
   } else if (e->prior == RECON_PRIOR_HAAR) {
@@ -404,6 +475,23 @@ recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s) {
     L.slices = static_cast<DftSlice*>(e->d_tmp) + (size_t)set * e->n;
     RC(launch_dft_temporal(L, s));
   }
+  return RECON_OK;
+}
+
+// Spatio-temporal prior, after the threshold kernel of set `set`: the CG
+// m-update and the d1 / p updates.
+recon_status launch_stv_m_update(Engine* e, int set, cudaStream_t s) {
+  StvLaunch S{};
+  S.slices = static_cast<StvSlice*>(e->d_tmp) + (size_t)set * e->n;
+  S.nslices = e->n;
+  S.nblocks = e->tmp_blocks;
+  RC(launch_stv_rhs(S, s));
+  for (int j = 0; j < e->cg; ++j) {
+    S.step = j;
+    RC(launch_stv_dir(S, s));
+    RC(launch_stv_update(S, s));
+  }
+  RC(launch_stv_finish(S, s));
   return RECON_OK;
 }
 
@@ -419,6 +507,16 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
     RC(cudaMemsetAsync(p->trace_J, 0xff, nt * sizeof(double), s));  // NaN
   }
   if (e->n > 1) RC(cudaMemsetAsync(e->d_err, 0, sizeof(int), s));
+  if (e->prior == RECON_PRIOR_STV) {   // m = p = x = H'y, d1 = 0
+    for (recon_plan* p : e->plans) {
+      const size_t bytes = p->nimg() * sizeof(float2);
+      RC(cudaMemcpyAsync(p->s0[0], p->b, bytes, cudaMemcpyDeviceToDevice, s));
+      RC(cudaMemcpyAsync(p->s2[0], p->b, bytes, cudaMemcpyDeviceToDevice, s));
+      RC(cudaMemcpyAsync(p->x, p->b, bytes, cudaMemcpyDeviceToDevice, s));
+      RC(cudaMemsetAsync(p->s1[0], 0, 3 * bytes, s));
+    }
+    RC(cudaMemsetAsync(e->d_stv_count, 0, (size_t)e->n * sizeof(unsigned), s));
+  }
   recon_status st;
   if (e->obj)
     for (recon_plan* p : e->plans)
@@ -426,6 +524,7 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
   for (int k = 1; k <= K; ++k) {
     if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, true, s);
     if ((st = launch_tmp_set(e, k - 1, s)) != RECON_OK) return st;
+    if (e->prior == RECON_PRIOR_STV && (st = launch_stv_m_update(e, k - 1, s)) != RECON_OK) return st;
     if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, false, s);
     if (e->obj) RC(launch_finalize(e->d_fin, e->n, k - 1, s));
     if (prof) p0->mark(p0->ev_col, p0->n_col, true, s);

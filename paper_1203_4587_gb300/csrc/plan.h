@@ -42,6 +42,12 @@ struct Engine {
   int grid = 0, nb_max = 0, stages = 0, work_max = 0;
   int* d_err = nullptr;    // error word shared by the engine's launches
   FinSlice* d_fin = nullptr;
+  // spatio-temporal prior: CG steps, per-block partial sums, per-slice block
+  // counters and reduction slots (K sets of 2 cg + 1 per slice)
+  int cg = 0;
+  double* d_stv_part = nullptr;
+  unsigned* d_stv_count = nullptr;
+  std::vector<double*> stv_red;
   DevArena arena;
 };
 
@@ -79,7 +85,8 @@ struct recon_plan {
   float2* s1[2] = {nullptr, nullptr};  // TV: d1;  Haar: s = Psi'u
   float2* s2[2] = {nullptr, nullptr};  // TV: p
   float2* x = nullptr;                 // TV: x; DFT, Haar: xhat
-  float2* r = nullptr;                 // DFT, Haar: r
+  float2* r = nullptr;                 // DFT, Haar: r;  STV: CG direction 0
+  float2* cgd = nullptr;               // STV: CG direction 1
   float2* tmp_a = nullptr;             // operator entry points
   float2* tmp_b = nullptr;
   float2* kstage = nullptr;            // host-solve staging

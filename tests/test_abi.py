@@ -51,6 +51,7 @@ def test_invalid_arguments_rejected_before_any_cuda_call(libpath):
     o = binding.Opts()
     lib.recon_default_opts(C.byref(o))
     assert o.rho == pytest.approx(0.5) and o.max_iters == 50 and o.storage == 0 and o.objective == 1
+    assert o.frame_levels == 2 and o.spatial_weight == pytest.approx(1.0) and o.cg_steps == 5
     cases = [
         (0, 4, 2, 1, 0.01, 0.1, 0),       # Nx = 0
         (4, 4, 2, 1, 0.01, 0.0, 0),       # mu = 0
@@ -69,9 +70,31 @@ def test_invalid_arguments_rejected_before_any_cuda_call(libpath):
     st = lib.recon_plan_create(C.byref(h), 4, 4, 2, 1, C.cast(mask, C.c_void_p), C.cast(sens, C.c_void_p),
                                0.01, 0.1, 0, C.byref(bad), None)
     assert st == 1
+    for field, value in (("cg_steps", 0), ("cg_steps", 65), ("spatial_weight", -0.5)):   # spatio-temporal prior
+        bad = binding.Opts()
+        lib.recon_default_opts(C.byref(bad))
+        setattr(bad, field, value)
+        st = lib.recon_plan_create(C.byref(h), 4, 4, 2, 1, C.cast(mask, C.c_void_p), C.cast(sens, C.c_void_p),
+                                   0.01, 0.1, 3, C.byref(bad), None)
+        assert st == 1, field
     st = lib.recon_plan_create(C.byref(h), 4, 4096, 2, 1, C.cast(mask, C.c_void_p), C.cast(sens, C.c_void_p),
                                0.01, 0.1, 0, None, None)
     assert st == 7  # unsupported size
+    st = lib.recon_plan_create_slab(C.byref(h), 8, 4, 2, 1, C.cast(mask, C.c_void_p), C.cast(sens, C.c_void_p),
+                                    0.01, 0.1, 3, None, 0, 4, None)
+    assert st == 7  # the spatio-temporal prior couples columns: no slab plans
     assert lib.recon_destroy(None) == 0
     assert lib.recon_solve(None, None, None, None, None) == 1
     assert lib.recon_status_string(2) == b"RECON_ERR_MASK_NOT_CARTESIAN"
+
+
+def test_opts_struct_matches_header():
+    """binding.Opts lists recon_opts' fields in the header's order and types."""
+    import re
+    from paper_1203_4587_gb300 import binding
+    text = open(os.path.join(ROOT, "include", "recon.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} recon_opts;", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(float|int|double)\s+(\w+)\s*;", body)
+    ctype = {"float": C.c_float, "int": C.c_int, "double": C.c_double}
+    assert [(n, ctype[t]) for t, n in fields] == list(binding.Opts._fields_)
