@@ -175,7 +175,8 @@ HaarSlice haar_desc(recon_plan* p, int k, int K) {
 
 // Iteration k (1-based) of the spatio-temporal prior; k = K+1 is the final
 // prior term.  The state buffers are updated in place (m by the CG steps,
-// d1 and p by the finishing kernel); a solve starts from m = p = x = H'y, d1 = 0.
+// e = d1 - v and p by the finishing kernel); a solve starts from
+// m = p = x = H'y, d1 = 0.
 StvSlice stv_desc(recon_plan* p, int k, int K, double* red) {
   StvSlice d{};
   d.Nx = p->Nx;
@@ -188,15 +189,13 @@ StvSlice stv_desc(recon_plan* p, int k, int K, double* red) {
   d.ws = p->opts.spatial_weight;
   d.m = p->s0[0];
   d.q = p->s0[1];
-  d.d1 = p->s1[0];
-  d.e = p->s1[1];
+  d.e = p->s1[0];
   d.p = p->s2[0];
   d.r = p->s2[1];
   d.pc[0] = p->r;
   d.pc[1] = p->cgd;
   d.x = p->x;
   d.stop = p->flags + FLAG_STOP;
-  d.write_state = k <= K ? 1 : 0;
   d.red = red + (size_t)(std::min(k, std::max(K, 1)) - 1) * (2 * d.cg + 1);
   d.prior_acc = p->trace_prior + (k - 1);
   return d;
@@ -286,7 +285,7 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
     RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_stv_count), (size_t)n * sizeof(unsigned)));
     RC(cudaMemset(e->d_stv_count, 0, (size_t)n * sizeof(unsigned)));
     int blocks = 0;
-    for (int q = 0; q < n; ++q) blocks += (int)((plans[q]->nimg() + kStvBlockElems - 1) / kStvBlockElems);
+    for (int q = 0; q < n; ++q) blocks += (plans[q]->Nt * plans[q]->Nx + kStvRows - 1) / kStvRows;
     RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_stv_part), (size_t)std::max(blocks, 1) * sizeof(double)));
   }
   const int K = e->K;
@@ -333,8 +332,8 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
 }
 
 int engine_tile_candidates(const Engine* e, int* out) {
-  if (e->prior == RECON_PRIOR_STV) {   // fixed elements per block
-    out[0] = kStvBlockElems;
+  if (e->prior == RECON_PRIOR_STV) {   // fixed image columns per block
+    out[0] = kStvRows;
     return 1;
   }
   if (e->tv) return tv_tile_candidates(e->Nt_max, out);
@@ -343,7 +342,7 @@ int engine_tile_candidates(const Engine* e, int* out) {
 }
 
 int engine_default_tile(const Engine* e) {
-  if (e->prior == RECON_PRIOR_STV) return kStvBlockElems;
+  if (e->prior == RECON_PRIOR_STV) return kStvRows;
   if (e->tv) return tv_tile_px(e->Nt_max);
   if (e->prior == RECON_PRIOR_HAAR) return haar_tile_px(e->Nt_max, e->levels);
   return dft_tile_px();
@@ -359,8 +358,9 @@ recon_status engine_set_tile(Engine* e, int px) {
   int blocks = 0;
   for (int q = 0; q < n; ++q) {
     tile0[q] = blocks;
-    // temporal kernels tile pixels; the spatio-temporal kernels tile all elements
-    const size_t units = e->prior == RECON_PRIOR_STV ? e->plans[q]->nimg() : e->plans[q]->npix();
+    // temporal kernels tile pixels; the spatio-temporal kernels tile image columns (t, i)
+    const size_t units = e->prior == RECON_PRIOR_STV ? (size_t)e->plans[q]->Nt * e->plans[q]->Nx
+                                                     : e->plans[q]->npix();
     blocks += (int)((units + px - 1) / px);
   }
   void* old = e->d_tmp;
@@ -370,7 +370,7 @@ recon_status engine_set_tile(Engine* e, int px) {
       for (int q = 0; q < n; ++q) {
         StvSlice d = stv_desc(e->plans[q], k, K, e->stv_red[q]);
         d.tile0 = tile0[q];
-        d.nblk = (int)((e->plans[q]->nimg() + px - 1) / px);
+        d.nblk = (e->plans[q]->Nt * e->plans[q]->Nx + px - 1) / px;
         d.part = e->d_stv_part;
         d.count = e->d_stv_count + q;
         t[(size_t)(k - 1) * n + q] = d;
@@ -459,7 +459,7 @@ recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s) {
   L.nblocks = e->tmp_blocks;
   L.Nt_max = e->Nt_max;
   L.tile_px = e->tile_px;
-  if (e->prior == RECON_PRIOR_STV) {   // the prior / threshold kernel of the set
+  if (e->prior == RECON_PRIOR_STV) {   // the prior term of set `set` (the final one in a solve)
     StvLaunch S{};
     S.slices = static_cast<StvSlice*>(e->d_tmp) + (size_t)set * e->n;
     S.nslices = e->n;
@@ -478,9 +478,9 @@ recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s) {
   return RECON_OK;
 }
 
-// Spatio-temporal prior, after the threshold kernel of set `set`: the CG
-// m-update and the d1 / p updates.
-recon_status launch_stv_m_update(Engine* e, int set, cudaStream_t s) {
+// Spatio-temporal prior, iteration set+1 up to the inverse step: r and the
+// prior term of J, the CG m-update, the d1 / p updates and the next threshold.
+recon_status launch_stv_step(Engine* e, int set, cudaStream_t s) {
   StvLaunch S{};
   S.slices = static_cast<StvSlice*>(e->d_tmp) + (size_t)set * e->n;
   S.nslices = e->n;
@@ -513,9 +513,13 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
       RC(cudaMemcpyAsync(p->s0[0], p->b, bytes, cudaMemcpyDeviceToDevice, s));
       RC(cudaMemcpyAsync(p->s2[0], p->b, bytes, cudaMemcpyDeviceToDevice, s));
       RC(cudaMemcpyAsync(p->x, p->b, bytes, cudaMemcpyDeviceToDevice, s));
-      RC(cudaMemsetAsync(p->s1[0], 0, 3 * bytes, s));
     }
     RC(cudaMemsetAsync(e->d_stv_count, 0, (size_t)e->n * sizeof(unsigned), s));
+    StvLaunch S{};   // e = -S(R m), d1 = 0
+    S.slices = static_cast<StvSlice*>(e->d_tmp);
+    S.nslices = e->n;
+    S.nblocks = e->tmp_blocks;
+    RC(launch_stv_init(S, s));
   }
   recon_status st;
   if (e->obj)
@@ -523,8 +527,9 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
       if ((st = plan_objective(p, p->b, p->trace_fid, s)) != RECON_OK) return st;
   for (int k = 1; k <= K; ++k) {
     if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, true, s);
-    if ((st = launch_tmp_set(e, k - 1, s)) != RECON_OK) return st;
-    if (e->prior == RECON_PRIOR_STV && (st = launch_stv_m_update(e, k - 1, s)) != RECON_OK) return st;
+    if (e->prior == RECON_PRIOR_STV) st = launch_stv_step(e, k - 1, s);
+    else st = launch_tmp_set(e, k - 1, s);
+    if (st != RECON_OK) return st;
     if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, false, s);
     if (e->obj) RC(launch_finalize(e->d_fin, e->n, k - 1, s));
     if (prof) p0->mark(p0->ev_col, p0->n_col, true, s);

@@ -156,7 +156,7 @@ struct HaarSlice {           // temporal step of Algorithm 1 with the undecimate
 
 // Algorithm 2 with R = (D_t, w D_x, w D_y) (spatio-temporal differences) and a
 // CG m-update, one slice.  Fields [Nt][Nx][Ny] (n elements); the three
-// difference components of d1 and e are stored padded, [3][n], with zeros
+// difference components of e = d1 - v are stored padded, [3][n], with zeros
 // where a difference leaves the grid.  Reduction slots of one iteration:
 // red[0..cg] = gamma_0..gamma_cg (<r, r>), red[cg+1+j] = <p_j, q_j>.
 struct StvSlice {
@@ -167,7 +167,6 @@ struct StvSlice {
   float rho;                 // mu2 / mu1
   float ws;                  // spatial weight w
   float2* m;                 // m (updated in place by the CG steps)
-  float2* d1;                // [3][n]
   float2* e;                 // [3][n]: d1 - v
   float2* p;                 // p = m - d2 (so d2 = x - p); the inverse step reads r = b + mu2 p
   const float2* x;
@@ -177,11 +176,10 @@ struct StvSlice {
   double* red;               // this iteration's reduction slots
   double* part;              // per-block partial sums (indexed by the launch's block)
   unsigned* count;           // blocks done, for the last-block sum (reset by that block)
-  int write_state;           // 0: only the prior term
   double* prior_acc;         // += ||R x||_1 of the incoming x
   const int* stop;
   int tile0;                 // first block of this slice in the launch
-  int nblk;                  // blocks of this slice
+  int nblk;                  // blocks of this slice (kStvRows image columns each)
 };
 
 struct StvLaunch {
@@ -277,15 +275,16 @@ cudaError_t prepare_haar_temporal(int Nt_max, int levels, int px);
 int haar_tile_px(int Nt_max, int levels);
 int haar_tile_candidates(int Nt_max, int levels, int* out);
 cudaError_t launch_objective(const ObjParams& p, cudaStream_t s);
-// spatio-temporal Algorithm 2 (stv_kernels.cu); elements per block:
+// spatio-temporal Algorithm 2 (stv_kernels.cu): a block walks kStvRows image
+// columns (t, i) of Ny elements
 constexpr int kStvThreads = 256;
-constexpr int kStvPerThread = 4;
-constexpr int kStvBlockElems = kStvThreads * kStvPerThread;
-cudaError_t launch_stv_prior(const StvLaunch& L, cudaStream_t s);    // v, e = d1 - v; ||R x||_1
-cudaError_t launch_stv_rhs(const StvLaunch& L, cudaStream_t s);      // r = rhs - M m, gamma_0
+constexpr int kStvRows = 4;
+cudaError_t launch_stv_init(const StvLaunch& L, cudaStream_t s);     // e = -S(R m) (d1 = 0)
+cudaError_t launch_stv_prior(const StvLaunch& L, cudaStream_t s);    // ||R x||_1
+cudaError_t launch_stv_rhs(const StvLaunch& L, cudaStream_t s);      // r = rhs - M m, gamma_0, ||R x||_1
 cudaError_t launch_stv_dir(const StvLaunch& L, cudaStream_t s);      // p_j, q = M p_j, <p_j, q>
 cudaError_t launch_stv_update(const StvLaunch& L, cudaStream_t s);   // m, r, gamma_{j+1}
-cudaError_t launch_stv_finish(const StvLaunch& L, cudaStream_t s);   // d1 = e + R m, p = m + p - x
+cudaError_t launch_stv_finish(const StvLaunch& L, cudaStream_t s);   // d1 = e + R m, p, next e
 // per slice: J(k) = fid[k] + (yy ? *yy : 0) + lambda prior[k]; Delta(k); stop flag.
 cudaError_t launch_finalize(const FinSlice* fins, int nslices, int k, cudaStream_t s);
 

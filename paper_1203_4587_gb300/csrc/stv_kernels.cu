@@ -2,65 +2,100 @@
 //   R x = (D_t x, w D_x x, w D_y x)
 // (non-circular differences along t, the horizontal index i and the vertical
 // index j) and an m-update by conjugate gradients, as Section IV-B suggests
-// when (mu2/mu1 I + R'R)^{-1} is not used in closed form:
+// when (mu2/mu1 I + R'R)^{-1} is not used in closed form.  With e = d1 - v
+// and p = m - d2 (so d2 = x - p), iteration k is
 //
-//   v   = S(R m + d1, lambda / (2 mu1))                      k_stv_prior
-//   rhs = R'(v - d1) + rho (x + d2),  r = rhs - M m           k_stv_rhs
-//   cg steps on M = rho I + R'R from m:                       k_stv_dir, k_stv_update
+//   rhs = R'(v - d1) + rho (x + d2) = -R'e + rho (2x - p),
+//   r = rhs - M m (M = rho I + R'R)                            k_stv_rhs
+//   cg steps from m:                                           k_stv_dir, k_stv_update
 //     p_j = r_j + (gamma_j / gamma_{j-1}) p_{j-1},  q = M p_j
 //     alpha = gamma_j / <p_j, q>,  m += alpha p_j,  r -= alpha q,  gamma_{j+1} = <r, r>
-//   d1' = d1 - (v - R m'),  p' = m' - d2                      k_stv_finish
+//   d1' = e + R m'  (= d1 - (v - R m')),  p' = m' - d2 = m' + p - x,
+//   and already the next threshold step on (m', d1'):
+//   v' = S(R m' + d1', lambda/(2 mu1)),  e' = d1' - v'          k_stv_finish
 //
-// then the inverse step forms x' = A (H'y + mu2 p') (k_col_inverse), and the
-// next d2 is x' - p' (the same bookkeeping as the temporal TV step).
+// after which the inverse step forms x' = A (H'y + mu2 p') (k_col_inverse);
+// the next d2 is x' - p'.  d1 itself is never stored.  A solve starts from
+// m = p = x = H'y, d1 = 0: k_stv_init forms e = -S(R m).  The prior term
+// ||R x||_1 of J at the incoming x is summed by k_stv_rhs (k_stv_prior for
+// the final x).
 //
-// Fields are [Nt][Nx][Ny]; element idx = (t Nx + i) Ny + j has its
-// neighbours at idx +- 1 (j), +- Ny (i) and +- Nx Ny (t).  d1 and e = d1 - v
-// keep the three components padded to the grid, with zeros where a
-// difference leaves it; those stay zero (S(0 + 0) = 0), so the adjoint
-// R'u = D_t'u_t + w D_x'u_x + w D_y'u_y needs no boundary cases beyond the
-// first index of each axis.
+// Fields are [Nt][Nx][Ny]; a "row" is one image column (t, i) of Ny
+// elements, with neighbours at +-1 (j), +-Ny (i) and +-Nx Ny (t).  A block
+// walks kStvRows consecutive rows; (t, i) of its first row is found once and
+// stepped, and an element's row within the block comes from an FP32
+// reciprocal that is exact at these sizes (see row_of).  e keeps its three
+// components padded to the grid, with zeros where a difference leaves it
+// (they stay zero: S(0) = 0), so R'e needs no cases beyond the first index of
+// each axis.
 //
-// The CG inner products are sums over the whole slice: every block writes
-// its partial sum, and the last block of the slice to finish (a counter
-// taken with an atomic after a fence) adds the partials in block order, so
-// the result does not depend on scheduling.  alpha and beta are formed in
-// FP64 from those sums.
+// CG inner products are sums over the whole slice.  A thread adds its few
+// elements (kStvRows * Ny / 256 of them, at most 16) in FP32; the block sums
+// its threads in FP64 and writes a partial, and the last block of the slice
+// to finish (an atomic counter after a fence) adds the partials in block
+// order, so results do not depend on scheduling.  alpha and beta are formed
+// in FP64 from those sums.  (GB300's FP64 pipe runs at 1/64 of FP32: FP64
+// products per element would cost more than the memory traffic.)
 #include "kernels.h"
 
 namespace recon {
 
 namespace {
 
-struct Pos {
-  int t, i, j;
+// Where the threads of this block are: rows [row0, row0 + nrows) of the slice.
+struct Blk {
+  int row0, nrows;
+  int t0, i0;      // (t, i) of row0
+  float inv_ny;
 };
 
-__device__ __forceinline__ Pos pos_of(const StvSlice& P, int idx) {
-  const int st = P.Nx * P.Ny;
+__device__ __forceinline__ Blk blk_of(const StvSlice& P) {
+  Blk b;
+  b.row0 = ((int)blockIdx.x - P.tile0) * kStvRows;
+  b.nrows = min(kStvRows, P.Nt * P.Nx - b.row0);
+  b.t0 = b.row0 / P.Nx;
+  b.i0 = b.row0 - b.t0 * P.Nx;
+  b.inv_ny = 1.f / (float)P.Ny;
+  return b;
+}
+
+// Row within the block of local element e < kStvRows * Ny: (e + 1/2)/Ny has
+// fractional part >= 1/(2 Ny) >= 2^-11 away from an integer, and its FP32
+// rounding error is below 2^12 * 2^-24, so the truncation is exact.
+__device__ __forceinline__ int row_of(const Blk& b, int e) {
+  return __float2int_rz(((float)e + 0.5f) * b.inv_ny);
+}
+
+struct Pos {
+  int idx, t, i, j;
+};
+
+__device__ __forceinline__ Pos pos_of(const StvSlice& P, const Blk& b, int e) {
+  const int r = row_of(b, e);
   Pos q;
-  q.t = idx / st;
-  const int rem = idx - q.t * st;
-  q.i = rem / P.Ny;
-  q.j = rem - q.i * P.Ny;
+  q.j = e - r * P.Ny;
+  q.i = b.i0 + r;
+  q.t = b.t0;
+  while (q.i >= P.Nx) { q.i -= P.Nx; ++q.t; }   // at most kStvRows steps
+  q.idx = (b.row0 + r) * P.Ny + q.j;
   return q;
 }
 
-// (D_t f, w D_x f, w D_y f) at idx, zero where the difference leaves the grid
-__device__ __forceinline__ void diffs(const StvSlice& P, const float2* __restrict__ f, int idx, Pos q,
+// (D_t f, w D_x f, w D_y f) at q, zero where the difference leaves the grid
+__device__ __forceinline__ void diffs(const StvSlice& P, const float2* __restrict__ f, const Pos& q,
                                       float2& dt, float2& dx, float2& dy) {
-  const float2 c = f[idx];
+  const float2 c = f[q.idx];
   const float2 z = make_float2(0.f, 0.f);
-  dt = (q.t + 1 < P.Nt) ? c_sub(f[idx + P.Nx * P.Ny], c) : z;
-  dx = (q.i + 1 < P.Nx) ? c_scale(c_sub(f[idx + P.Ny], c), P.ws) : z;
-  dy = (q.j + 1 < P.Ny) ? c_scale(c_sub(f[idx + 1], c), P.ws) : z;
+  dt = (q.t + 1 < P.Nt) ? c_sub(f[q.idx + P.Nx * P.Ny], c) : z;
+  dx = (q.i + 1 < P.Nx) ? c_scale(c_sub(f[q.idx + P.Ny], c), P.ws) : z;
+  dy = (q.j + 1 < P.Ny) ? c_scale(c_sub(f[q.idx + 1], c), P.ws) : z;
 }
 
-// (D'D f)_t + w^2 ((D'D f)_x + (D'D f)_y) at idx: the 7-point operator R'R
+// (D'D f)_t + w^2 ((D'D f)_x + (D'D f)_y) at q: the 7-point operator R'R
 template <class F>
-__device__ __forceinline__ float2 rtr(const StvSlice& P, F f, int idx, Pos q) {
+__device__ __forceinline__ float2 rtr(const StvSlice& P, F f, const Pos& q) {
+  const int idx = q.idx, st = P.Nx * P.Ny;
   const float2 c = f(idx);
-  const int st = P.Nx * P.Ny;
   float2 lt = make_float2(0.f, 0.f), ls = make_float2(0.f, 0.f);
   if (q.t > 0) lt = c_add(lt, c_sub(c, f(idx - st)));
   if (q.t + 1 < P.Nt) lt = c_sub(lt, c_sub(f(idx + st), c));
@@ -104,50 +139,69 @@ __device__ void slice_sum(const StvSlice& P, double v, double* slot) {
   }
 }
 
+__device__ __forceinline__ float rx_l1(const StvSlice& P, const Pos& q) {
+  float2 a, b, c;
+  diffs(P, P.x, q, a, b, c);
+  return c_abs(a) + c_abs(b) + c_abs(c);
+}
+
+// e = d1 - S(R m + d1) into the three padded components
+__device__ __forceinline__ void threshold(const StvSlice& P, const Pos& q, float2 d0, float2 d1, float2 d2) {
+  float2 a, b, c;
+  diffs(P, P.m, q, a, b, c);
+  // d1' = e + R m arrives here as (d0, d1, d2) + (a, b, c) when called from
+  // k_stv_finish; from k_stv_init d1 = 0
+  const float2 rm[3] = {a, b, c};
+  const float2 dd[3] = {c_add(d0, a), c_add(d1, b), c_add(d2, c)};
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    P.e[(long long)k * P.n + q.idx] = c_sub(dd[k], c_soft(c_add(rm[k], dd[k]), P.tau1));
+}
+
+__global__ void __launch_bounds__(kStvThreads) k_stv_init(StvLaunch L) {
+  const StvSlice& P = slice_of(L);
+  if (P.stop && *P.stop) return;
+  const Blk b = blk_of(P);
+  const float2 z = make_float2(0.f, 0.f);
+  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
+    const Pos q = pos_of(P, b, e);
+    float2 a, bb, c;
+    diffs(P, P.m, q, a, bb, c);
+    // d1 = 0: e = -S(R m)
+    P.e[q.idx] = c_sub(z, c_soft(a, P.tau1));
+    P.e[(long long)P.n + q.idx] = c_sub(z, c_soft(bb, P.tau1));
+    P.e[2 * (long long)P.n + q.idx] = c_sub(z, c_soft(c, P.tau1));
+  }
+}
+
 __global__ void __launch_bounds__(kStvThreads) k_stv_prior(StvLaunch L) {
   __shared__ double red[32];
   const StvSlice& P = slice_of(L);
   if (P.stop && *P.stop) return;
-  const int base = ((int)blockIdx.x - P.tile0) * kStvBlockElems;
-  double l1 = 0.0;
-#pragma unroll
-  for (int k = 0; k < kStvPerThread; ++k) {
-    const int idx = base + k * kStvThreads + (int)threadIdx.x;
-    if (idx >= P.n) break;
-    const Pos q = pos_of(P, idx);
-    float2 a, b, c;
-    diffs(P, P.x, idx, q, a, b, c);
-    l1 += (double)(c_abs(a) + c_abs(b) + c_abs(c));
-    if (P.write_state) {
-      diffs(P, P.m, idx, q, a, b, c);
-      const float2 rm[3] = {a, b, c};
-#pragma unroll
-      for (int comp = 0; comp < 3; ++comp) {
-        const long long o = (long long)comp * P.n + idx;
-        const float2 d = P.d1[o];
-        P.e[o] = c_sub(d, c_soft(c_add(rm[comp], d), P.tau1));
-      }
-    }
-  }
-  const double s = group_sum(l1, red, threadIdx.x, kStvThreads, BlockBar());
+  const Blk b = blk_of(P);
+  float l1 = 0.f;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) l1 += rx_l1(P, pos_of(P, b, e));
+  const double s = group_sum((double)l1, red, threadIdx.x, kStvThreads, BlockBar());
   if (threadIdx.x == 0) atomicAdd(P.prior_acc, s);
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_rhs(StvLaunch L) {
+  __shared__ double red[32];
   const StvSlice& P = slice_of(L);
   if (P.stop && *P.stop) return;
-  const int base = ((int)blockIdx.x - P.tile0) * kStvBlockElems;
+  const Blk b = blk_of(P);
   const int st = P.Nx * P.Ny;
   const float2* et = P.e;
   const float2* ex = P.e + P.n;
   const float2* ey = P.e + 2 * (long long)P.n;
   const float2* m = P.m;
-  double g = 0.0;
-#pragma unroll
-  for (int k = 0; k < kStvPerThread; ++k) {
-    const int idx = base + k * kStvThreads + (int)threadIdx.x;
-    if (idx >= P.n) break;
-    const Pos q = pos_of(P, idx);
+  float g = 0.f, l1 = 0.f;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
+    const Pos q = pos_of(P, b, e);
+    const int idx = q.idx;
+    l1 += rx_l1(P, q);
     // R'e (the padded components are zero past the last index)
     float2 rt = make_float2(-et[idx].x, -et[idx].y), rs = make_float2(-ex[idx].x - ey[idx].x, -ex[idx].y - ey[idx].y);
     if (q.t > 0) rt = c_add(rt, et[idx - st]);
@@ -155,91 +209,85 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_rhs(StvLaunch L) {
     if (q.j > 0) rs = c_add(rs, ey[idx - 1]);
     const float2 rte = make_float2(fmaf(P.ws, rs.x, rt.x), fmaf(P.ws, rs.y, rt.y));
     const float2 xv = P.x[idx], pv = P.p[idx], mv = m[idx];
-    const float2 mm = rtr(P, [m](int o) { return m[o]; }, idx, q);
+    const float2 mm = rtr(P, [m](int o) { return m[o]; }, q);
     // r = -R'e + rho (2x - p) - (rho m + R'R m)
     float2 r;
     r.x = fmaf(P.rho, 2.f * xv.x - pv.x - mv.x, -rte.x - mm.x);
     r.y = fmaf(P.rho, 2.f * xv.y - pv.y - mv.y, -rte.y - mm.y);
     P.r[idx] = r;
-    g += (double)r.x * r.x + (double)r.y * r.y;
+    g = fmaf(r.x, r.x, fmaf(r.y, r.y, g));
   }
-  slice_sum(P, g, P.red);
+  const double s = group_sum((double)l1, red, threadIdx.x, kStvThreads, BlockBar());
+  if (threadIdx.x == 0) atomicAdd(P.prior_acc, s);
+  slice_sum(P, (double)g, P.red);
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_dir(StvLaunch L) {
   const StvSlice& P = slice_of(L);
   if (P.stop && *P.stop) return;
   const int j = L.step;
-  const int base = ((int)blockIdx.x - P.tile0) * kStvBlockElems;
+  const Blk b = blk_of(P);
   double beta = 0.0;
   if (j > 0 && P.red[j - 1] > 0.0) beta = P.red[j] / P.red[j - 1];
-  const float b = (float)beta;
+  const float be = (float)beta;
   const float2* r = P.r;
   const float2* po = P.pc[(j + 1) & 1];
   float2* pn = P.pc[j & 1];
-  auto dir = [r, po, b, j](int o) {
+  auto dir = [r, po, be, j](int o) {
     const float2 rv = r[o];
     if (j == 0) return rv;
     const float2 pv = po[o];
-    return make_float2(fmaf(b, pv.x, rv.x), fmaf(b, pv.y, rv.y));
+    return make_float2(fmaf(be, pv.x, rv.x), fmaf(be, pv.y, rv.y));
   };
-  double pq = 0.0;
-#pragma unroll
-  for (int k = 0; k < kStvPerThread; ++k) {
-    const int idx = base + k * kStvThreads + (int)threadIdx.x;
-    if (idx >= P.n) break;
-    const Pos q = pos_of(P, idx);
-    const float2 pv = dir(idx);
-    const float2 l = rtr(P, dir, idx, q);
+  float pq = 0.f;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
+    const Pos q = pos_of(P, b, e);
+    const float2 pv = dir(q.idx);
+    const float2 l = rtr(P, dir, q);
     const float2 qv = make_float2(fmaf(P.rho, pv.x, l.x), fmaf(P.rho, pv.y, l.y));
-    pn[idx] = pv;
-    P.q[idx] = qv;
-    pq += (double)pv.x * qv.x + (double)pv.y * qv.y;
+    pn[q.idx] = pv;
+    P.q[q.idx] = qv;
+    pq = fmaf(pv.x, qv.x, fmaf(pv.y, qv.y, pq));
   }
-  slice_sum(P, pq, P.red + P.cg + 1 + j);
+  slice_sum(P, (double)pq, P.red + P.cg + 1 + j);
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_update(StvLaunch L) {
   const StvSlice& P = slice_of(L);
   if (P.stop && *P.stop) return;
   const int j = L.step;
-  const int base = ((int)blockIdx.x - P.tile0) * kStvBlockElems;
+  const Blk b = blk_of(P);
   const double gam = P.red[j], pq = P.red[P.cg + 1 + j];
   const float alpha = (pq > 0.0 && gam > 0.0) ? (float)(gam / pq) : 0.f;
   const float2* pn = P.pc[j & 1];
-  double g = 0.0;
-#pragma unroll
-  for (int k = 0; k < kStvPerThread; ++k) {
-    const int idx = base + k * kStvThreads + (int)threadIdx.x;
-    if (idx >= P.n) break;
+  const int base = b.row0 * P.Ny;
+  float g = 0.f;
+  // element-wise: no neighbours, so no (t, i, j)
+#pragma unroll 4
+  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
+    const int idx = base + e;
     const float2 pv = pn[idx], qv = P.q[idx];
     float2 mv = P.m[idx], rv = P.r[idx];
     mv.x = fmaf(alpha, pv.x, mv.x); mv.y = fmaf(alpha, pv.y, mv.y);
     rv.x = fmaf(-alpha, qv.x, rv.x); rv.y = fmaf(-alpha, qv.y, rv.y);
     P.m[idx] = mv;
     P.r[idx] = rv;
-    g += (double)rv.x * rv.x + (double)rv.y * rv.y;
+    g = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, g));
   }
-  slice_sum(P, g, P.red + j + 1);
+  slice_sum(P, (double)g, P.red + j + 1);
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_finish(StvLaunch L) {
   const StvSlice& P = slice_of(L);
   if (P.stop && *P.stop) return;
-  const int base = ((int)blockIdx.x - P.tile0) * kStvBlockElems;
-#pragma unroll
-  for (int k = 0; k < kStvPerThread; ++k) {
-    const int idx = base + k * kStvThreads + (int)threadIdx.x;
-    if (idx >= P.n) break;
-    const Pos q = pos_of(P, idx);
-    float2 a, b, c;
-    diffs(P, P.m, idx, q, a, b, c);
-    const float2 rm[3] = {a, b, c};
-#pragma unroll
-    for (int comp = 0; comp < 3; ++comp) {
-      const long long o = (long long)comp * P.n + idx;
-      P.d1[o] = c_add(P.e[o], rm[comp]);
-    }
+  const Blk b = blk_of(P);
+#pragma unroll 4
+  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
+    const Pos q = pos_of(P, b, e);
+    const int idx = q.idx;
+    // e (the previous threshold's d1 - v) is read and replaced element by element
+    threshold(P, q, P.e[idx], P.e[(long long)P.n + idx], P.e[2 * (long long)P.n + idx]);
     P.p[idx] = c_add(P.m[idx], c_sub(P.p[idx], P.x[idx]));
   }
 }
@@ -254,6 +302,7 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_finish(StvLaunch L) {
     return cudaGetLastError();                                           \
   } while (0)
 
+cudaError_t launch_stv_init(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_init); }
 cudaError_t launch_stv_prior(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_prior); }
 cudaError_t launch_stv_rhs(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_rhs); }
 cudaError_t launch_stv_dir(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_dir); }
