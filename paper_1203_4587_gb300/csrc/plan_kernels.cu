@@ -7,12 +7,14 @@
 // (The paper prints sum_c s_c s_c'; the operator form S_c' F~' F~ S_c gives
 // conj(s_j) s_k, which is used here.)  Each block is inverted exactly,
 // A_{i,t} = (mu I + G_{i,t})^{-1} (Eq. eigen_mu: the eigendecomposition and a
-// Cholesky factorisation give the same matrix), in FP64:
+// Cholesky factorisation give the same matrix), in double-float arithmetic
+// (df64.cuh, about 48 significant bits on the FP32 pipe):
 //   1. M = mu I + G (lower triangle)
 //   2. M = L L'                 (right-looking Cholesky)
 //   3. Z = L^{-1}               (row by row)
 //   4. A = Z' Z                 (upper triangle), rounded once to the storage
 //      type and scattered into the packed stream (kernels.h).
+#include "df64.cuh"
 #include "kernels.h"
 
 namespace recon {
@@ -73,64 +75,78 @@ __device__ __forceinline__ float2 packed_load(const E* Ac, int R, int C, int nti
 
 constexpr int kPlanThreads = 256;
 
+// The factorisation in double-float arithmetic (df64.cuh): about 48
+// significant bits on the FP32 pipe, which GB300 runs at 64 times its FP64
+// rate; the result is rounded once to the storage type.  W holds one complex
+// double-float per element as (re.hi, re.lo, im.hi, im.lo).
+__device__ __forceinline__ dc ldw(const float4* W, size_t o) { return dc_unpack(W[o]); }
+__device__ __forceinline__ void stw(float4* W, size_t o, dc v) { W[o] = dc_pack(v); }
+
 template <typename E>
 __global__ void __launch_bounds__(kPlanThreads) k_plan_inverse(const float2* __restrict__ sens,
-                                                               const double2* __restrict__ circ, double mu, int Nx,
+                                                               const double2* __restrict__ circ, float mu, int Nx,
                                                                int Ny, int Nt, int Nc, E* __restrict__ A,
                                                                long long col_elems, int ntiles,
-                                                               double2* __restrict__ scratch, int* flags) {
-  extern __shared__ double2 zs[];
+                                                               float4* __restrict__ scratch, int* flags) {
+  extern __shared__ float4 zs[];
   const int n = Ny, tid = threadIdx.x;
-  double2* sc = zs;                  // [Nc][n] sensitivities of column i (FP64)
-  double2* cb = zs + (size_t)Nc * n; // [n] cached column / row
-  double2* W = scratch + (size_t)blockIdx.x * n * n;  // row-major n x n
+  float2* sc = reinterpret_cast<float2*>(zs);   // [Nc][n] sensitivities of column i (exact FP32 inputs)
+  float4* cb = zs + ((size_t)Nc * n + 1) / 2;   // [n] cached column / row
+  float4* W = scratch + (size_t)blockIdx.x * n * n;  // row-major n x n
   const long long nmat = (long long)Nx * Nt;
   const int ty = tid >> 4, tx = tid & 15;
   for (long long mat = blockIdx.x; mat < nmat; mat += gridDim.x) {
     const int t = (int)(mat / Nx), i = (int)(mat - (long long)t * Nx);
-    for (int idx = tid; idx < Nc * n; idx += kPlanThreads) {
-      const float2 v = sens[(size_t)i * Nc * n + idx];
-      sc[idx] = make_double2(v.x, v.y);
-    }
+    for (int idx = tid; idx < Nc * n; idx += kPlanThreads) sc[idx] = sens[(size_t)i * Nc * n + idx];
     __syncthreads();
-    // 1. M = mu I + C_t (.) K_i, lower triangle
+    // 1. M = mu I + C_t (.) K_i, lower triangle; K = sum_c conj(s_j) s_k, every
+    //    product exact in double length
     for (long long idx = tid; idx < (long long)n * n; idx += kPlanThreads) {
       const int j = (int)(idx / n), k = (int)(idx - (long long)j * n);
       if (k > j) continue;
-      double2 K = make_double2(0.0, 0.0);
-      for (int c = 0; c < Nc; ++c) z_fmac(K, sc[c * n + j], sc[c * n + k]);  // conj(s_j) s_k
-      double2 g = z_mul(circ[(size_t)t * n + (j - k)], K);
-      if (j == k) g.x += mu;
-      W[(size_t)j * n + k] = g;
+      df kr = df_make(0.f), ki = df_make(0.f);
+      for (int c = 0; c < Nc; ++c) {
+        const float2 a = sc[c * n + j], b = sc[c * n + k];
+        kr = df_fma_ff(df_fma_ff(kr, a.x, b.x), a.y, b.y);     // Re conj(a) b
+        ki = df_fma_ff(df_fma_ff(ki, a.x, b.y), -a.y, b.x);    // Im conj(a) b
+      }
+      const double2 cz = circ[(size_t)t * n + (j - k)];
+      const df cr = df_from_double(cz.x), ci = df_from_double(cz.y);
+      dc g;
+      g.re = df_sub(df_mul(cr, kr), df_mul(ci, ki));
+      g.im = df_add(df_mul(cr, ki), df_mul(ci, kr));
+      if (j == k) g.re = df_add(g.re, df_make(mu));
+      stw(W, (size_t)j * n + k, g);
     }
     __syncthreads();
     // 2. Cholesky, right-looking
     bool bad = false;
     for (int k = 0; k < n; ++k) {
-      double d = W[(size_t)k * n + k].x;
-      if (!(d > 0.0)) { bad = true; d = 1.0; }
-      d = sqrt(d);
-      const double inv = 1.0 / d;
+      df d = ldw(W, (size_t)k * n + k).re;
+      if (!(d.hi > 0.f)) { bad = true; d = df_make(1.f); }
+      d = df_sqrt(d);
+      const df inv = df_rcp(d);
       for (int j = k + 1 + tid; j < n; j += kPlanThreads) {
-        double2 v = W[(size_t)j * n + k];
-        v.x *= inv; v.y *= inv;
-        W[(size_t)j * n + k] = v;
-        cb[j] = v;
+        dc v = ldw(W, (size_t)j * n + k);
+        v.re = df_mul(v.re, inv);
+        v.im = df_mul(v.im, inv);
+        stw(W, (size_t)j * n + k, v);
+        cb[j] = dc_pack(v);
       }
       __syncthreads();
-      if (tid == 0) W[(size_t)k * n + k] = make_double2(d, 0.0);
+      if (tid == 0) stw(W, (size_t)k * n + k, dc{d, df_make(0.f)});
       const int m = n - k - 1;
       for (int jb = 0; jb < m; jb += 16) {
         for (int lb = 0; lb <= jb; lb += 16) {
           const int jj = jb + ty, ll = lb + tx;
           if (jj < m && ll <= jj) {
             const int j = k + 1 + jj, l = k + 1 + ll;
-            double2 w = W[(size_t)j * n + l];
-            const double2 a = cb[j], b = cb[l];
+            dc w = ldw(W, (size_t)j * n + l);
+            const dc a = dc_unpack(cb[j]), b = dc_unpack(cb[l]);
             // w -= a * conj(b)
-            w.x -= fma(a.x, b.x, a.y * b.y);
-            w.y -= fma(a.y, b.x, -a.x * b.y);
-            W[(size_t)j * n + l] = w;
+            w.re = df_fma(df_fma(w.re, df_neg(a.re), b.re), df_neg(a.im), b.im);
+            w.im = df_fma(df_fma(w.im, df_neg(a.im), b.re), a.re, b.im);
+            stw(W, (size_t)j * n + l, w);
           }
         }
       }
@@ -141,30 +157,39 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_inverse(const float2* __r
     for (int j = 0; j < n; ++j) {
       for (int l = tid; l <= j; l += kPlanThreads) cb[l] = W[(size_t)j * n + l];
       __syncthreads();
-      const double ljj = cb[j].x;
+      const df rl = df_rcp(dc_unpack(cb[j]).re);
       for (int c = tid; c <= j; c += kPlanThreads) {
-        double2 z;
+        dc z;
         if (c == j) {
-          z = make_double2(1.0 / ljj, 0.0);
+          z = dc{rl, df_make(0.f)};
         } else {
-          double2 s = make_double2(0.0, 0.0);
-          for (int l = c; l < j; ++l) z_fma(s, cb[l], W[(size_t)l * n + c]);
-          z = make_double2(-s.x / ljj, -s.y / ljj);
+          df sr = df_make(0.f), si = df_make(0.f);
+          for (int l = c; l < j; ++l) {
+            const dc a = dc_unpack(cb[l]), b = ldw(W, (size_t)l * n + c);
+            sr = df_fma(df_fma(sr, a.re, b.re), df_neg(a.im), b.im);
+            si = df_fma(df_fma(si, a.re, b.im), a.im, b.re);
+          }
+          z = dc{df_neg(df_mul(sr, rl)), df_neg(df_mul(si, rl))};
         }
-        W[(size_t)j * n + c] = z;
+        stw(W, (size_t)j * n + c, z);
       }
       __syncthreads();
     }
-    // 4. A = Z' Z, upper triangle: A[j][k] = sum_{l >= k} conj(Z[l][j]) Z[l][k]
+    // 4. A = Z' Z, upper triangle: A[j][k] = sum_{l >= k} conj(Z[l][j]) Z[l][k],
+    //    rounded once to the storage type
     E* Ac = A + (size_t)mat * col_elems;
     for (int jb = 0; jb < n; jb += 16) {
       for (int kb = jb; kb < n; kb += 16) {
         const int j = jb + ty, k = kb + tx;
         if (j < n && k < n && j <= k) {
-          double2 s = make_double2(0.0, 0.0);
-          for (int l = k; l < n; ++l) z_fmac(s, W[(size_t)l * n + j], W[(size_t)l * n + k]);
-          if (j == k) s.y = 0.0;  // Hermitian: exact real diagonal
-          packed_store(Ac, j, k, ntiles, s);
+          df sr = df_make(0.f), si = df_make(0.f);
+          for (int l = k; l < n; ++l) {
+            const dc a = ldw(W, (size_t)l * n + j), b = ldw(W, (size_t)l * n + k);
+            sr = df_fma(df_fma(sr, a.re, b.re), a.im, b.im);           // Re conj(a) b
+            si = df_fma(df_fma(si, a.re, b.im), df_neg(a.im), b.re);   // Im conj(a) b
+          }
+          double2 v = make_double2(df_to_double(sr), j == k ? 0.0 : df_to_double(si));  // Hermitian: real diagonal
+          packed_store(Ac, j, k, ntiles, v);
         }
       }
     }
@@ -176,11 +201,12 @@ template <typename E>
 static cudaError_t launch_plan_t(const float2* sens, const double2* circ, double mu, int Nx, int Ny, int Nt, int Nc,
                                  void* A, const PackInfo& pk, double2* scratch, int grid, int* flags,
                                  cudaStream_t s) {
-  const size_t smem = ((size_t)Nc * Ny + Ny) * sizeof(double2);
+  const size_t smem = (((size_t)Nc * Ny + 1) / 2 + Ny) * sizeof(float4);
   cudaError_t e = cudaFuncSetAttribute(k_plan_inverse<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_plan_inverse<E><<<grid, kPlanThreads, smem, s>>>(sens, circ, mu, Nx, Ny, Nt, Nc, static_cast<E*>(A),
-                                                     pk.col_elems, pk.ntiles, scratch, flags); note_launch();
+  k_plan_inverse<E><<<grid, kPlanThreads, smem, s>>>(sens, circ, (float)mu, Nx, Ny, Nt, Nc, static_cast<E*>(A),
+                                                     pk.col_elems, pk.ntiles, reinterpret_cast<float4*>(scratch),
+                                                     flags); note_launch();
   return cudaGetLastError();
 }
 

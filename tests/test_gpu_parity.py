@@ -108,6 +108,29 @@ def test_packed_inverse_blocks(shape):
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(str(s[k]) for k in ("Nx", "Ny", "Nt", "Nc")))
+def test_inverse_rounded_once(shape):
+    """The factorisation (double-float, about 48 bits) is rounded once: every
+    element is within half an FP32 ulp of the FP64 oracle's value plus
+    2^-36 max|A|, and the larger elements equal its FP32 rounding."""
+    case = make("tiny", **shape)
+    P = plan_for(case, max_iters=1)
+    Nt, Ny, Nx = case.x_true.shape
+    mu32 = float(np.float32(case.mu))   # the plan holds mu as an FP32 value (recon_plan_create takes float)
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        i, t = int(rng.integers(Nx)), int(rng.integers(Nt))
+        Aref = oracle.inverse_blocks(oracle.gram_blocks(case.sens, case.mask, [i])[t, 0], mu32)
+        A = P.export_inverse(i, t).cpu().numpy()
+        top = np.abs(Aref).max()
+        for part in (np.real, np.imag):
+            a, r = part(A).astype(np.float64), part(Aref)
+            ulp = np.spacing(np.abs(r).astype(np.float32)).astype(np.float64)
+            assert np.all(np.abs(a - r) <= 0.5 * ulp + 2.0 ** -36 * top)
+            big = np.abs(r) > 1e-2 * top
+            assert np.mean(a[big] == r[big].astype(np.float32)) > 0.999
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(str(s[k]) for k in ("Nx", "Ny", "Nt", "Nc")))
 def test_apply_inverse(shape):
     case = make("tiny", **shape)
     P = plan_for(case, max_iters=1)
