@@ -439,7 +439,9 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
       w64[k] = make_double2(std::cos(a), std::sin(a));
     }
     void *d_w64 = nullptr, *d_circ = nullptr, *d_scr = nullptr;
-    int grid = std::max(1, std::min<int>((int)ncols, 2 * p->num_sms));
+    // one CTA per SM (the sweep holds ~200 KB of shared memory): the scratch
+    // triangles of all CTAs then stay in L2 up to Ny = 256
+    int grid = std::max(1, std::min<int>((int)ncols, p->num_sms));
     cudaError_t e = cudaMalloc(&d_w64, Ny * sizeof(double2));
     if (e == cudaSuccess) e = cudaMalloc(&d_circ, (size_t)Nt * Ny * sizeof(double2));
     if (e == cudaSuccess) e = cudaMalloc(&d_scr, (size_t)grid * Ny * Ny * sizeof(double2));

@@ -7,13 +7,10 @@
 // (The paper prints sum_c s_c s_c'; the operator form S_c' F~' F~ S_c gives
 // conj(s_j) s_k, which is used here.)  Each block is inverted exactly,
 // A_{i,t} = (mu I + G_{i,t})^{-1} (Eq. eigen_mu: the eigendecomposition and a
-// Cholesky factorisation give the same matrix), in double-float arithmetic
-// (df64.cuh, about 48 significant bits on the FP32 pipe):
-//   1. M = mu I + G (lower triangle)
-//   2. M = L L'                 (right-looking Cholesky)
-//   3. Z = L^{-1}               (row by row)
-//   4. A = Z' Z                 (upper triangle), rounded once to the storage
-//      type and scattered into the packed stream (kernels.h).
+// direct inversion give the same matrix), in double-float arithmetic
+// (df64.cuh, about 48 significant bits on the FP32 pipe) by a blocked sweep
+// (below), rounded once to the storage type and scattered into the packed
+// stream (kernels.h).
 #include "df64.cuh"
 #include "kernels.h"
 
@@ -75,32 +72,70 @@ __device__ __forceinline__ float2 packed_load(const E* Ac, int R, int C, int nti
 
 constexpr int kPlanThreads = 256;
 
-// The factorisation in double-float arithmetic (df64.cuh): about 48
+// The inversion runs in double-float arithmetic (df64.cuh): about 48
 // significant bits on the FP32 pipe, which GB300 runs at 64 times its FP64
 // rate; the result is rounded once to the storage type.  W holds one complex
 // double-float per element as (re.hi, re.lo, im.hi, im.lo).
+//
+// M is inverted in place by the sweep operator (Goodnight 1979), blocked over
+// B pivots at a time: with P the pivot block, R the other indices,
+//   M[B][B] <- -P^{-1},   M[R][B] <- M[R][B] P^{-1},
+//   M[R][R] <- M[R][R] - M[R][B] P^{-1} M[B][R],
+// and after every pivot has been swept M holds -M^{-1}.  Sweeping the
+// pivots of a Hermitian positive definite matrix in order divides by the
+// diagonals of its Schur complements, which are positive, as in a Cholesky
+// factorisation; it takes about n^3/2 complex multiply-adds and touches W
+// once per block of B pivots.  Only the lower triangle is stored.  P^{-1} comes
+// from sweeping the B x B block itself in shared memory.
 __device__ __forceinline__ dc ldw(const float4* W, size_t o) { return dc_unpack(W[o]); }
 __device__ __forceinline__ void stw(float4* W, size_t o, dc v) { W[o] = dc_pack(v); }
+__device__ __forceinline__ dc dc_conj(dc a) { return {a.re, df_neg(a.im)}; }
+__device__ __forceinline__ dc dc_neg(dc a) { return {df_neg(a.re), df_neg(a.im)}; }
+__device__ __forceinline__ dc dc_zero() { return {df_make(0.f), df_make(0.f)}; }
+// acc + a b
+__device__ __forceinline__ dc dc_fma(dc acc, dc a, dc b) {
+  acc.re = df_fma(df_fma(acc.re, a.re, b.re), df_neg(a.im), b.im);
+  acc.im = df_fma(df_fma(acc.im, a.re, b.im), a.im, b.re);
+  return acc;
+}
+// acc - a conj(b)
+__device__ __forceinline__ dc dc_fms_conj(dc acc, dc a, dc b) {
+  acc.re = df_fma(df_fma(acc.re, df_neg(a.re), b.re), df_neg(a.im), b.im);
+  acc.im = df_fma(df_fma(acc.im, df_neg(a.im), b.re), a.re, b.im);
+  return acc;
+}
+__device__ __forceinline__ dc dc_scale(dc a, df s) { return {df_mul(a.re, s), df_mul(a.im, s)}; }
 
-template <typename E>
-__global__ void __launch_bounds__(kPlanThreads) k_plan_inverse(const float2* __restrict__ sens,
-                                                               const double2* __restrict__ circ, float mu, int Nx,
-                                                               int Ny, int Nt, int Nc, E* __restrict__ A,
-                                                               long long col_elems, int ntiles,
-                                                               float4* __restrict__ scratch, int* flags) {
+template <int B>
+__host__ __device__ constexpr size_t plan_smem_f4(int n, int Nc) {
+  // max(sensitivities [Nc][n] float2, panel [n][B] + T [n][B] + pivot block [B][B])
+  return ((size_t)Nc * n + 1) / 2 > (size_t)2 * n * B + B * B ? ((size_t)Nc * n + 1) / 2
+                                                                : (size_t)2 * n * B + B * B;
+}
+
+template <typename E, int B>
+__global__ void __launch_bounds__(kPlanThreads, 1) k_plan_inverse(const float2* __restrict__ sens,
+                                                                  const double2* __restrict__ circ, float mu, int Nx,
+                                                                  int Ny, int Nt, int Nc, E* __restrict__ A,
+                                                                  long long col_elems, int ntiles,
+                                                                  float4* __restrict__ scratch, int* flags) {
+  static_assert(B * B <= kPlanThreads, "one pivot-block entry per thread");
   extern __shared__ float4 zs[];
   const int n = Ny, tid = threadIdx.x;
-  float2* sc = reinterpret_cast<float2*>(zs);   // [Nc][n] sensitivities of column i (exact FP32 inputs)
-  float4* cb = zs + ((size_t)Nc * n + 1) / 2;   // [n] cached column / row
-  float4* W = scratch + (size_t)blockIdx.x * n * n;  // row-major n x n
+  float2* sc = reinterpret_cast<float2*>(zs);   // [Nc][n] sensitivities of column i (Gram phase only)
+  float4* pan = zs;                              // [n][B]  M(i, k0 + c)
+  float4* Tm = zs + (size_t)n * B;               // [n][B]  M(i, k0 + c) P^{-1}
+  float4* Pq = zs + (size_t)2 * n * B;           // [B][B]  pivot block, swept to -P^{-1}
+  float4* W = scratch + (size_t)blockIdx.x * n * n;  // row-major n x n, lower triangle used
   const long long nmat = (long long)Nx * Nt;
   const int ty = tid >> 4, tx = tid & 15;
+  bool bad = false;
   for (long long mat = blockIdx.x; mat < nmat; mat += gridDim.x) {
     const int t = (int)(mat / Nx), i = (int)(mat - (long long)t * Nx);
     for (int idx = tid; idx < Nc * n; idx += kPlanThreads) sc[idx] = sens[(size_t)i * Nc * n + idx];
     __syncthreads();
-    // 1. M = mu I + C_t (.) K_i, lower triangle; K = sum_c conj(s_j) s_k, every
-    //    product exact in double length
+    // M = mu I + C_t (.) K_i, lower triangle; K = sum_c conj(s_j) s_k, every
+    // product exact in double length
     for (long long idx = tid; idx < (long long)n * n; idx += kPlanThreads) {
       const int j = (int)(idx / n), k = (int)(idx - (long long)j * n);
       if (k > j) continue;
@@ -118,96 +153,122 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_inverse(const float2* __r
       if (j == k) g.re = df_add(g.re, df_make(mu));
       stw(W, (size_t)j * n + k, g);
     }
-    __syncthreads();
-    // 2. Cholesky, right-looking
-    bool bad = false;
-    for (int k = 0; k < n; ++k) {
-      df d = ldw(W, (size_t)k * n + k).re;
-      if (!(d.hi > 0.f)) { bad = true; d = df_make(1.f); }
-      d = df_sqrt(d);
-      const df inv = df_rcp(d);
-      for (int j = k + 1 + tid; j < n; j += kPlanThreads) {
-        dc v = ldw(W, (size_t)j * n + k);
-        v.re = df_mul(v.re, inv);
-        v.im = df_mul(v.im, inv);
-        stw(W, (size_t)j * n + k, v);
-        cb[j] = dc_pack(v);
+    __syncthreads();   // sc is overwritten by the panel below
+    for (int k0 = 0; k0 < n; k0 += B) {
+      const int bb = min(B, n - k0);
+      // panel M(i, k0 + c) for every i (the upper part from the stored lower one)
+      for (int idx = tid; idx < n * B; idx += kPlanThreads) {
+        const int r = idx / B, c = idx - r * B;
+        dc v = dc_zero();
+        if (c < bb) v = (r >= k0 + c) ? ldw(W, (size_t)r * n + k0 + c) : dc_conj(ldw(W, (size_t)(k0 + c) * n + r));
+        pan[idx] = dc_pack(v);
       }
       __syncthreads();
-      if (tid == 0) stw(W, (size_t)k * n + k, dc{d, df_make(0.f)});
-      const int m = n - k - 1;
-      for (int jb = 0; jb < m; jb += 16) {
-        for (int lb = 0; lb <= jb; lb += 16) {
-          const int jj = jb + ty, ll = lb + tx;
-          if (jj < m && ll <= jj) {
-            const int j = k + 1 + jj, l = k + 1 + ll;
-            dc w = ldw(W, (size_t)j * n + l);
-            const dc a = dc_unpack(cb[j]), b = dc_unpack(cb[l]);
-            // w -= a * conj(b)
-            w.re = df_fma(df_fma(w.re, df_neg(a.re), b.re), df_neg(a.im), b.im);
-            w.im = df_fma(df_fma(w.im, df_neg(a.im), b.re), a.re, b.im);
-            stw(W, (size_t)j * n + l, w);
+      // pivot block, swept in place: pivot k, entry (r, c)
+      const int pr = tid / B, pc = tid - (tid / B) * B;
+      const bool pv = tid < B * B && pr < bb && pc < bb;
+      if (tid < B * B) Pq[tid] = pv ? pan[(size_t)(k0 + pr) * B + pc] : dc_pack(dc_zero());
+      __syncthreads();
+      for (int k = 0; k < bb; ++k) {
+        df d = dc_unpack(Pq[k * B + k]).re;
+        if (!(d.hi > 0.f)) { bad = true; d = df_make(1.f); }
+        const df rd = df_rcp(d);
+        dc rk = dc_zero(), kc = dc_zero(), old = dc_zero();
+        if (pv) { rk = dc_unpack(Pq[pr * B + k]); kc = dc_unpack(Pq[k * B + pc]); old = dc_unpack(Pq[tid]); }
+        __syncthreads();
+        if (pv) {
+          dc v;
+          if (pr == k && pc == k) v = dc{df_neg(rd), df_make(0.f)};
+          else if (pr == k) v = dc_scale(kc, rd);
+          else if (pc == k) v = dc_scale(rk, rd);
+          else v = dc_fms_conj(old, dc_scale(rk, rd), dc_conj(kc));   // old - rk kc / d
+          Pq[tid] = dc_pack(v);
+        }
+        __syncthreads();
+      }
+      // T(i, c) = M(i, k0 + c) P^{-1} = -sum_d M(i, k0 + d) Pq(d, c), i outside the block
+      for (int idx = tid; idx < n * B; idx += kPlanThreads) {
+        const int r = idx / B, c = idx - r * B;
+        if (c >= bb || (r >= k0 && r < k0 + bb)) continue;
+        dc acc = dc_zero();
+#pragma unroll
+        for (int d = 0; d < B; ++d)
+          if (d < bb) acc = dc_fma(acc, dc_unpack(pan[(size_t)r * B + d]), dc_unpack(Pq[d * B + c]));
+        Tm[idx] = dc_pack(dc_neg(acc));
+      }
+      __syncthreads();
+      // the sweep of the block over the stored lower triangle
+      for (int ib = 0; ib < n; ib += 16) {
+        const int r = ib + ty;
+        const bool rin = r >= k0 && r < k0 + bb;
+        for (int jb = 0; jb <= ib; jb += 16) {
+          const int c = jb + tx;
+          if (r >= n || c > r) continue;
+          const bool cin = c >= k0 && c < k0 + bb;
+          const size_t o = (size_t)r * n + c;
+          if (!rin && !cin) {          // M[R][R] - T(r) conj(M(c, block))
+            dc w = ldw(W, o);
+#pragma unroll
+            for (int q = 0; q < B; ++q)
+              if (q < bb) w = dc_fms_conj(w, dc_unpack(Tm[(size_t)r * B + q]), dc_unpack(pan[(size_t)c * B + q]));
+            stw(W, o, w);
+          } else if (!rin) {           // (r, c) with c in the block, r below it
+            W[o] = Tm[(size_t)r * B + (c - k0)];
+          } else if (!cin) {           // r in the block, c left of it: conj of (c, r)
+            W[o] = dc_pack(dc_conj(dc_unpack(Tm[(size_t)c * B + (r - k0)])));
+          } else {                     // inside the block
+            W[o] = Pq[(r - k0) * B + (c - k0)];
           }
         }
       }
       __syncthreads();
     }
-    if (bad && tid == 0) atomicOr(&flags[FLAG_ERR], DEV_ERR_NOT_PD);
-    // 3. Z = L^{-1}, row j from rows < j:  Z[j][c] = -(1/L[j][j]) sum_{l=c}^{j-1} L[j][l] Z[l][c]
-    for (int j = 0; j < n; ++j) {
-      for (int l = tid; l <= j; l += kPlanThreads) cb[l] = W[(size_t)j * n + l];
-      __syncthreads();
-      const df rl = df_rcp(dc_unpack(cb[j]).re);
-      for (int c = tid; c <= j; c += kPlanThreads) {
-        dc z;
-        if (c == j) {
-          z = dc{rl, df_make(0.f)};
-        } else {
-          df sr = df_make(0.f), si = df_make(0.f);
-          for (int l = c; l < j; ++l) {
-            const dc a = dc_unpack(cb[l]), b = ldw(W, (size_t)l * n + c);
-            sr = df_fma(df_fma(sr, a.re, b.re), df_neg(a.im), b.im);
-            si = df_fma(df_fma(si, a.re, b.im), a.im, b.re);
-          }
-          z = dc{df_neg(df_mul(sr, rl)), df_neg(df_mul(si, rl))};
-        }
-        stw(W, (size_t)j * n + c, z);
-      }
-      __syncthreads();
-    }
-    // 4. A = Z' Z, upper triangle: A[j][k] = sum_{l >= k} conj(Z[l][j]) Z[l][k],
-    //    rounded once to the storage type
+    // W = -M^{-1}: A[j][k] = -conj(W[k][j]) for j <= k, rounded once
     E* Ac = A + (size_t)mat * col_elems;
     for (int jb = 0; jb < n; jb += 16) {
       for (int kb = jb; kb < n; kb += 16) {
         const int j = jb + ty, k = kb + tx;
         if (j < n && k < n && j <= k) {
-          df sr = df_make(0.f), si = df_make(0.f);
-          for (int l = k; l < n; ++l) {
-            const dc a = ldw(W, (size_t)l * n + j), b = ldw(W, (size_t)l * n + k);
-            sr = df_fma(df_fma(sr, a.re, b.re), a.im, b.im);           // Re conj(a) b
-            si = df_fma(df_fma(si, a.re, b.im), df_neg(a.im), b.re);   // Im conj(a) b
-          }
-          double2 v = make_double2(df_to_double(sr), j == k ? 0.0 : df_to_double(si));  // Hermitian: real diagonal
-          packed_store(Ac, j, k, ntiles, v);
+          const dc w = ldw(W, (size_t)k * n + j);
+          // Hermitian: exact real diagonal
+          packed_store(Ac, j, k, ntiles, make_double2(-df_to_double(w.re), j == k ? 0.0 : df_to_double(w.im)));
         }
       }
     }
     __syncthreads();
   }
+  if (bad) atomicOr(&flags[FLAG_ERR], DEV_ERR_NOT_PD);
+}
+
+// pivot block width: 16 while the panel and T fit in shared memory, else 8 or 4
+static int plan_block(int n, int Nc) {
+  if (plan_smem_f4<16>(n, Nc) * sizeof(float4) <= 220 * 1024) return 16;
+  if (plan_smem_f4<8>(n, Nc) * sizeof(float4) <= 220 * 1024) return 8;
+  return 4;
+}
+
+template <typename E, int B>
+static cudaError_t launch_plan_tb(const float2* sens, const double2* circ, double mu, int Nx, int Ny, int Nt, int Nc,
+                                  void* A, const PackInfo& pk, double2* scratch, int grid, int* flags,
+                                  cudaStream_t s) {
+  const size_t smem = plan_smem_f4<B>(Ny, Nc) * sizeof(float4);
+  cudaError_t e = cudaFuncSetAttribute(k_plan_inverse<E, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_plan_inverse<E, B><<<grid, kPlanThreads, smem, s>>>(sens, circ, (float)mu, Nx, Ny, Nt, Nc, static_cast<E*>(A),
+                                                        pk.col_elems, pk.ntiles, reinterpret_cast<float4*>(scratch),
+                                                        flags); note_launch();
+  return cudaGetLastError();
 }
 
 template <typename E>
 static cudaError_t launch_plan_t(const float2* sens, const double2* circ, double mu, int Nx, int Ny, int Nt, int Nc,
                                  void* A, const PackInfo& pk, double2* scratch, int grid, int* flags,
                                  cudaStream_t s) {
-  const size_t smem = (((size_t)Nc * Ny + 1) / 2 + Ny) * sizeof(float4);
-  cudaError_t e = cudaFuncSetAttribute(k_plan_inverse<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_plan_inverse<E><<<grid, kPlanThreads, smem, s>>>(sens, circ, (float)mu, Nx, Ny, Nt, Nc, static_cast<E*>(A),
-                                                     pk.col_elems, pk.ntiles, reinterpret_cast<float4*>(scratch),
-                                                     flags); note_launch();
-  return cudaGetLastError();
+  switch (plan_block(Ny, Nc)) {
+    case 16: return launch_plan_tb<E, 16>(sens, circ, mu, Nx, Ny, Nt, Nc, A, pk, scratch, grid, flags, s);
+    case 8: return launch_plan_tb<E, 8>(sens, circ, mu, Nx, Ny, Nt, Nc, A, pk, scratch, grid, flags, s);
+    default: return launch_plan_tb<E, 4>(sens, circ, mu, Nx, Ny, Nt, Nc, A, pk, scratch, grid, flags, s);
+  }
 }
 
 cudaError_t launch_plan_inverse(const float2* sens, const double2* circ, double mu, int Nx, int Ny, int Nt, int Nc,
