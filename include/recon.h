@@ -128,8 +128,10 @@ void recon_default_opts(recon_opts* opts);
 /* Builds a plan: validates the mask, copies sensitivities and the sampled row
  * lists into plan-owned device memory and computes every packed inverse
  * A_{i,t} = (mu2 I + G_{i,t})^{-1}, G_{i,t} = C_t (.) sum_c conj(s_{.,i,c}) s_{.,i,c}^T
- * (Section IV-C; C_t = F_v' P_t F_v is circulant).  The factorisation runs in
- * FP64 on the GPU and is rounded once to the storage type.
+ * (Section IV-C; C_t = F_v' P_t F_v is circulant).  The inversion runs on
+ * the GPU in double-float arithmetic (pairs of FP32 numbers, about 48
+ * significant bits; a blocked Hermitian sweep) and is rounded once to the
+ * storage type.
  *   out     receives the plan (set to NULL on failure)
  *   Nx, Ny, Nt, Nc >= 1
  *   mask    host or device uint8, nonzero = sampled row (see opts.mask_full)
@@ -142,6 +144,18 @@ void recon_default_opts(recon_opts* opts);
 recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc, const uint8_t* mask,
                                const float* sens, float lambda, float mu, recon_prior prior,
                                const recon_opts* opts, void* stream);
+
+/* Changes mu (mu2 of Algorithm 2) of an existing plan: recomputes every packed
+ * inverse (mu I + G_{i,t})^{-1} from the plan's device-resident sensitivities
+ * and row lists (Eq. eigen_mu with the new mu) and every launch descriptor
+ * that carries mu, keeping the allocations and the tuned launch shapes.
+ * Blocks until done.  Batches and gradient engines built from the plan
+ * before the call refuse to run afterwards (INVALID_ARG): build them again.
+ * If the recomputation fails, the plan keeps its old mu but is unusable
+ * (every later call on it returns INVALID_ARG) and must be destroyed.
+ * Errors: INVALID_ARG (NULL plan, mu <= 0 or not finite), OOM, CUDA,
+ * NONFINITE. */
+recon_status recon_plan_set_mu(recon_plan* plan, float mu, void* stream);
 
 /* ---- sequential reconstruction along the horizontal axis ---------------------
  * Every step of the method is separable over the image columns i once the

@@ -36,7 +36,7 @@ EXPORTS = ["recon_default_opts", "recon_plan_create", "recon_solve", "recon_solv
            "recon_batch_create", "recon_batch_solve", "recon_batch_info", "recon_batch_destroy",
            "recon_grad_create", "recon_grad_forward", "recon_grad_backward", "recon_grad_destroy",
            "recon_solve_kspace", "recon_quantize_kspace", "recon_autotune", "recon_batch_autotune",
-           "recon_plan_create_slab", "recon_solve_slabs"]
+           "recon_plan_create_slab", "recon_solve_slabs", "recon_plan_set_mu"]
 
 
 class Opts(C.Structure):
@@ -142,6 +142,8 @@ def load(path: str = LIB_PATH):
     lib.recon_solve_slabs.argtypes = [i, i, i, i, vp, fp, f, f, i, C.POINTER(Opts), i, fp, fp, C.POINTER(d),
                                       C.POINTER(Info), vp]
     lib.recon_solve_slabs.restype = i
+    lib.recon_plan_set_mu.argtypes = [vp, f, vp]
+    lib.recon_plan_set_mu.restype = i
     lib.recon_autotune.argtypes = [vp, C.POINTER(Tuning), vp]
     lib.recon_autotune.restype = i
     lib.recon_batch_autotune.argtypes = [vp, C.POINTER(Tuning), vp]
@@ -214,6 +216,11 @@ class Plan:
         _check(st)
         self._keep = (mdev, sens)
         self.slab = slab
+
+    def set_mu(self, mu, stream=None):
+        """Recomputes the inverses for a new mu (recon_plan_set_mu)."""
+        _check(load().recon_plan_set_mu(self._h, float(mu), _stream(stream)))
+        self.mu = float(mu)
 
     def close(self):
         if self._h:

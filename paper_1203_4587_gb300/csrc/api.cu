@@ -87,6 +87,10 @@ recon_plan::~recon_plan() {
   for (void* q : allocs) cudaFree(q);
 }
 
+namespace {
+recon_status plan_invert(recon_plan* p, cudaStream_t s);   // below
+}  // namespace
+
 extern "C" {
 
 void recon_default_opts(recon_opts* o) {
@@ -125,6 +129,43 @@ size_t recon_inverse_bytes(const recon_plan* p) {
   return (size_t)p->pk.col_elems * p->esize * (size_t)p->Nx * p->Nt;
 }
 
+recon_status recon_plan_set_mu(recon_plan* p, float mu, void* stream) {
+  g_last_error.clear();
+  if (!p) return fail(RECON_ERR_INVALID_ARG, "NULL plan");
+  if (!(mu > 0.f) || !std::isfinite(mu)) return fail(RECON_ERR_INVALID_ARG, "mu must be > 0");
+  cudaSetDevice(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const float old = p->mu;
+  p->mu = mu;
+  ++p->generation;   // batches and gradient engines built on the old mu refuse to run
+  recon_status st = plan_invert(p, s);
+  if (st == RECON_OK) {
+    // every descriptor that carries mu (thresholds, r = b + mu p, J weights)
+    Engine* e = new Engine();
+    st = engine_build(e, &p, 1);
+    if (st == RECON_OK && p->tile_px > 0 && p->opts.max_iters > 0) st = engine_set_tile(e, p->tile_px);
+    if (st == RECON_OK) {
+      delete p->eng;
+      p->eng = e;
+      Engine* ei = new Engine();
+      st = engine_build_inverse(ei, p);
+      if (st == RECON_OK) {
+        delete p->eng_inv;
+        p->eng_inv = ei;
+      } else {
+        delete ei;
+      }
+    } else {
+      delete e;
+    }
+  }
+  if (st != RECON_OK) {   // the inverses may be half-written: the plan stays unusable
+    p->mu = old;
+    p->broken = true;
+  }
+  return st;
+}
+
 recon_status recon_destroy(recon_plan* p) {
   if (!p) return RECON_OK;
   cudaSetDevice(p->device);
@@ -136,6 +177,41 @@ recon_status recon_destroy(recon_plan* p) {
 }  // extern "C"
 
 namespace {
+
+// A_{i,t} = (mu I + G_{i,t})^{-1} for every column of the plan, from its
+// device-resident sensitivities and row lists (Section IV-C), rounded once
+// into the packed stream.
+recon_status plan_invert(recon_plan* p, cudaStream_t s) {
+  const int Nx = p->Nx, Ny = p->Ny, Nt = p->Nt, Nc = p->Nc;
+  const size_t ncols = (size_t)Nx * Nt;
+  std::vector<double2> w64(Ny);
+  for (int k = 0; k < Ny; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)Ny;
+    w64[k] = make_double2(std::cos(a), std::sin(a));
+  }
+  void *d_w64 = nullptr, *d_circ = nullptr, *d_scr = nullptr;
+  // one CTA per SM (the sweep holds ~200 KB of shared memory): the scratch
+  // triangles of all CTAs then stay in L2 up to Ny = 256
+  const int grid = std::max(1, std::min<int>((int)ncols, p->num_sms));
+  cudaError_t e = cudaMalloc(&d_w64, Ny * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&d_circ, (size_t)Nt * Ny * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&d_scr, (size_t)grid * Ny * Ny * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMemcpy(d_w64, w64.data(), Ny * sizeof(double2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->flags, 0, FLAG_COUNT * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->A, 0, (size_t)p->pk.col_elems * p->esize * ncols, s);
+  if (e == cudaSuccess)
+    e = launch_circulant(p->rows, p->rowoff, static_cast<double2*>(d_w64), static_cast<double2*>(d_circ), Ny, Nt, s);
+  if (e == cudaSuccess)
+    e = launch_plan_inverse(p->sens, static_cast<double2*>(d_circ), (double)p->mu, Nx, Ny, Nt, Nc, p->A, p->storage,
+                            p->pk, static_cast<double2*>(d_scr), grid, p->flags, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_w64); cudaFree(d_circ); cudaFree(d_scr);
+  if (e != cudaSuccess) return cuda_fail(e, "plan inverse");
+  int fl[FLAG_COUNT];
+  RC(cudaMemcpy(fl, p->flags, sizeof(fl), cudaMemcpyDeviceToHost));
+  if (fl[FLAG_ERR] & DEV_ERR_NOT_PD) return fail(RECON_ERR_NONFINITE, "a Gram block is not positive definite");
+  return RECON_OK;
+}
 
 PackInfo make_pack(int Ny) {
   PackInfo pk{};
@@ -431,35 +507,10 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "sensitivity upload"));
   }
 
-  // packed inverses (FP64 factorisation, rounded once)
+  // packed inverses (double-float inversion, rounded once)
   {
-    std::vector<double2> w64(Ny);
-    for (int k = 0; k < Ny; ++k) {
-      const double a = 2.0 * M_PI * (double)k / (double)Ny;
-      w64[k] = make_double2(std::cos(a), std::sin(a));
-    }
-    void *d_w64 = nullptr, *d_circ = nullptr, *d_scr = nullptr;
-    // one CTA per SM (the sweep holds ~200 KB of shared memory): the scratch
-    // triangles of all CTAs then stay in L2 up to Ny = 256
-    int grid = std::max(1, std::min<int>((int)ncols, p->num_sms));
-    cudaError_t e = cudaMalloc(&d_w64, Ny * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMalloc(&d_circ, (size_t)Nt * Ny * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMalloc(&d_scr, (size_t)grid * Ny * Ny * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMemcpy(d_w64, w64.data(), Ny * sizeof(double2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->flags, 0, FLAG_COUNT * sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->A, 0, (size_t)p->pk.col_elems * p->esize * ncols, s);
-    if (e == cudaSuccess)
-      e = launch_circulant(p->rows, p->rowoff, static_cast<double2*>(d_w64), static_cast<double2*>(d_circ), Ny, Nt,
-                           s);
-    if (e == cudaSuccess)
-      e = launch_plan_inverse(p->sens, static_cast<double2*>(d_circ), (double)mu, Nx, Ny, Nt, Nc, p->A, p->storage,
-                              p->pk, static_cast<double2*>(d_scr), grid, p->flags, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(d_w64); cudaFree(d_circ); cudaFree(d_scr);
-    if (e != cudaSuccess) return cleanup(cuda_fail(e, "plan inverse"));
-    int fl[FLAG_COUNT];
-    PC(cudaMemcpy(fl, p->flags, sizeof(fl), cudaMemcpyDeviceToHost));
-    if (fl[FLAG_ERR] & DEV_ERR_NOT_PD) return cleanup(fail(RECON_ERR_NONFINITE, "a Gram block is not positive definite"));
+    recon_status st = plan_invert(p, s);
+    if (st != RECON_OK) return cleanup(st);
   }
 
   // the plan's own iterations (a batch of one) and the apply-inverse launch
@@ -540,6 +591,7 @@ recon_status recon_solve_slabs(int Nx, int Ny, int Nt, int Nc, const uint8_t* ma
 recon_status recon_solve_kspace(recon_plan* p, const recon_kspace* y, float* image, recon_info* info, void* stream) {
   g_last_error.clear();
   if (!p || !y || !y->data || !image) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  if (p->broken) return fail(RECON_ERR_INVALID_ARG, "the plan failed recon_plan_set_mu and is unusable");
   if (y->storage < RECON_STORAGE_FP32 || y->storage > RECON_STORAGE_BF16)
     return fail(RECON_ERR_INVALID_ARG, "k-space storage must be a recon_storage value");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -608,6 +660,7 @@ recon_status recon_solve_host(recon_plan* p, const float* kspace_host, float* im
                               void* stream) {
   g_last_error.clear();
   if (!p || !kspace_host || !image_host) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  if (p->broken) return fail(RECON_ERR_INVALID_ARG, "the plan failed recon_plan_set_mu and is unusable");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t kbytes = (size_t)p->Nt * p->Nc * p->Ny * p->Nx_full * sizeof(float2);
   const size_t ibytes = (size_t)p->Nt * p->Ny * p->Nx_full * sizeof(float2);
@@ -661,6 +714,7 @@ recon_status recon_apply_forward(recon_plan* p, const float* image, float* kspac
 
 recon_status recon_apply_inverse(recon_plan* p, const float* in, float* out, void* stream) {
   if (!p || !in || !out || in == out) return fail(RECON_ERR_INVALID_ARG, "NULL or aliased argument");
+  if (p->broken) return fail(RECON_ERR_INVALID_ARG, "the plan failed recon_plan_set_mu and is unusable");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   recon_status st = plan_to_internal(p, reinterpret_cast<const float2*>(in), p->tmp_a, s);
   if (st != RECON_OK) return st;
@@ -672,6 +726,7 @@ recon_status recon_apply_inverse(recon_plan* p, const float* in, float* out, voi
 
 recon_status recon_export_inverse(recon_plan* p, int i, int t, float* dense, void* stream) {
   if (!p || !dense || i < 0 || i >= p->Nx || t < 0 || t >= p->Nt) return fail(RECON_ERR_INVALID_ARG, "bad argument");
+  if (p->broken) return fail(RECON_ERR_INVALID_ARG, "the plan failed recon_plan_set_mu and is unusable");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   RC(launch_unpack(p->A, p->storage, p->pk, (long long)t * p->Nx + i, p->Ny, reinterpret_cast<float2*>(dense), s));
   return RECON_OK;

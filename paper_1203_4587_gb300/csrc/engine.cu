@@ -260,6 +260,11 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
   recon_plan* p0 = plans[0];
   e->plans.assign(plans, plans + n);
   e->n = n;
+  e->gens.resize(n);
+  for (int q = 0; q < n; ++q) {
+    if (plans[q]->broken) return fail(RECON_ERR_INVALID_ARG, "a plan failed recon_plan_set_mu and is unusable");
+    e->gens[q] = plans[q]->generation;
+  }
   e->K = p0->opts.max_iters;
   e->prior = p0->prior;
   e->tv = p0->prior == RECON_PRIOR_TV;
@@ -548,6 +553,16 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
 
 recon_status engine_apply_inverse(Engine* e, cudaStream_t s) { return launch_col_set(e, 0, s); }
 
+recon_status engine_check(const Engine* e) {
+  for (int q = 0; q < e->n; ++q) {
+    const recon_plan* p = e->plans[q];
+    if (p->broken) return fail(RECON_ERR_INVALID_ARG, "a plan failed recon_plan_set_mu and is unusable");
+    if (q < (int)e->gens.size() && p->generation != e->gens[q])
+      return fail(RECON_ERR_INVALID_ARG, "a plan's mu changed (recon_plan_set_mu) after this batch was built: rebuild it");
+  }
+  return RECON_OK;
+}
+
 const float2* plan_result(const recon_plan* p) { return p->opts.max_iters == 0 ? p->b : p->x; }
 
 }  // namespace recon
@@ -602,6 +617,10 @@ recon_status recon_batch_create(recon_batch** out, recon_plan* const* plans, int
 
 recon_status recon_batch_solve(recon_batch* b, const float* const* kspace, float* const* image, void* stream) {
   if (!b || !kspace || !image) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  {
+    recon_status st = engine_check(&b->eng);
+    if (st != RECON_OK) return st;
+  }
   const int n = b->eng.n;
   std::vector<const void*> key;
   for (int q = 0; q < n; ++q) {

@@ -213,9 +213,13 @@ recon_status recon_grad_create(recon_grad** out, recon_plan* const* plans, int n
   int work_max = 0;
   const int grid = std::max(1, plans[0]->num_sms);
   build_col_work(plans, n, grid, work, off, work_max);
+  for (int q = 0; q < n; ++q)
+    if (plans[q]->broken) return bail(fail(RECON_ERR_INVALID_ARG, "a plan failed recon_plan_set_mu and is unusable"));
   for (Engine* e : {&g->fwd, &g->bwd}) {
     e->plans.assign(plans, plans + n);
     e->n = n;
+    e->gens.resize(n);
+    for (int q = 0; q < n; ++q) e->gens[q] = plans[q]->generation;
     e->K = K;
     e->tv = true;
     e->storage = plans[0]->storage;
@@ -324,6 +328,10 @@ recon_status recon_grad_create(recon_grad** out, recon_plan* const* plans, int n
 
 recon_status recon_grad_forward(recon_grad* g, const float* const* kspace, float* const* image, void* stream) {
   if (!g || !kspace || !image) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  {
+    recon_status st0 = engine_check(&g->fwd);
+    if (st0 != RECON_OK) return st0;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   recon_status st;
   for (recon_plan* p : g->fwd.plans) p->last_stream = s;
@@ -344,6 +352,10 @@ recon_status recon_grad_forward(recon_grad* g, const float* const* kspace, float
 recon_status recon_grad_backward(recon_grad* g, const float* const* grad_image, float* const* grad_kspace,
                                  double* grad_lambda, double* grad_mu, void* stream) {
   if (!g || !grad_image || !grad_kspace) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
+  {
+    recon_status st0 = engine_check(&g->fwd);
+    if (st0 != RECON_OK) return st0;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int K = g->K, n = g->n;
   recon_status st;

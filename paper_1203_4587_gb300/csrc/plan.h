@@ -48,6 +48,7 @@ struct Engine {
   double* d_stv_part = nullptr;
   unsigned* d_stv_count = nullptr;
   std::vector<double*> stv_red;
+  std::vector<unsigned> gens;   // each plan's generation when this engine was built
   DevArena arena;
 };
 
@@ -100,6 +101,8 @@ struct recon_plan {
   recon::FftPlanDev64 fx64{}, fy64{};
   int col_stages = 0;
   int last_iters = 0;
+  unsigned generation = 0;             // bumped by recon_plan_set_mu: engines built before refuse to run
+  bool broken = false;                 // a recon_plan_set_mu failed half-way: the inverses are not valid
   // tuned launch shapes (0 = the built-in default); see autotune.cu
   int tile_px = 0;                     // temporal kernel pixels per block
   int col_stages_tuned = 0;            // ring depth of the inverse kernel
@@ -166,6 +169,8 @@ recon_status engine_build_inverse(Engine* e, recon_plan* p);   // tmp_a -> tmp_b
 // slice (prologues must have run).  `profile` records the plan's events (n = 1).
 recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile);
 recon_status engine_apply_inverse(Engine* e, cudaStream_t s);
+// RECON_OK while every plan of the engine is usable and unchanged since the build
+recon_status engine_check(const Engine* e);
 const float2* plan_result(const recon_plan* p);   // image (internal layout) after K iterations
 // H'y (into p->b), the hybrid data kept for J(k) and ||y||^2.  kspace is
 // complex64 (kstorage 0) or 16-bit pairs times kscale[t] (kscale may be null).

@@ -70,7 +70,10 @@ __device__ __forceinline__ float2 packed_load(const E* Ac, int R, int C, int nti
   return R == C ? make_float2(2.f * v.x, 0.f) : v;
 }
 
-constexpr int kPlanThreads = 256;
+// 16 warps: a thread's double-float update chains are long and dependent, so
+// the SM needs many warps in flight to hide their latency
+constexpr int kPlanThreads = 512;
+constexpr int kPlanRows = kPlanThreads / 16;   // rows of a 16-column tile
 
 // The inversion runs in double-float arithmetic (df64.cuh): about 48
 // significant bits on the FP32 pipe, which GB300 runs at 64 times its FP64
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan_inverse(const float2* 
   float4* Pq = zs + (size_t)2 * n * B;           // [B][B]  pivot block, swept to -P^{-1}
   float4* W = scratch + (size_t)blockIdx.x * n * n;  // row-major n x n, lower triangle used
   const long long nmat = (long long)Nx * Nt;
-  const int ty = tid >> 4, tx = tid & 15;
+  const int ty = tid >> 4, tx = tid & 15;   // kPlanRows x 16 tiles
   bool bad = false;
   for (long long mat = blockIdx.x; mat < nmat; mat += gridDim.x) {
     const int t = (int)(mat / Nx), i = (int)(mat - (long long)t * Nx);
@@ -198,10 +201,10 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan_inverse(const float2* 
       }
       __syncthreads();
       // the sweep of the block over the stored lower triangle
-      for (int ib = 0; ib < n; ib += 16) {
+      for (int ib = 0; ib < n; ib += kPlanRows) {
         const int r = ib + ty;
         const bool rin = r >= k0 && r < k0 + bb;
-        for (int jb = 0; jb <= ib; jb += 16) {
+        for (int jb = 0; jb < ib + kPlanRows; jb += 16) {
           const int c = jb + tx;
           if (r >= n || c > r) continue;
           const bool cin = c >= k0 && c < k0 + bb;
@@ -225,8 +228,8 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan_inverse(const float2* 
     }
     // W = -M^{-1}: A[j][k] = -conj(W[k][j]) for j <= k, rounded once
     E* Ac = A + (size_t)mat * col_elems;
-    for (int jb = 0; jb < n; jb += 16) {
-      for (int kb = jb; kb < n; kb += 16) {
+    for (int jb = 0; jb < n; jb += kPlanRows) {
+      for (int kb = jb / 16 * 16; kb < n; kb += 16) {
         const int j = jb + ty, k = kb + tx;
         if (j < n && k < n && j <= k) {
           const dc w = ldw(W, (size_t)k * n + j);
