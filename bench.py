@@ -338,7 +338,7 @@ def measure_batched(nslices, storage, steps=3):
             "hbm_gbs_inverse_stream": A_bytes * shapes[0]["iters"] / (ms / 1e3) / 1e9,
             "note": ("Nx, Ny in {128,160,192,256}, Nt in {16,24,32,40}, Nc in {8,12,16}, R in {4,6,8}, TV, "
                      "lambda=0.005, mu=0.1; all slices in one launch per step, the batched solve replayed "
-                     "from a captured CUDA graph; plan (FP64 factorisation) reported separately")}
+                     "from a captured CUDA graph; plan (double-float inversion) reported separately")}
 
 
 def measure_precision(steps=3):

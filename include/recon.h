@@ -80,7 +80,7 @@ typedef enum {
 /* Storage of the data a solve keeps in device memory.  For a plan (opts.storage):
  *   FP32  packed inverses and hybrid coil data F_h'y in complex64; the H'y
  *         prologue in FP64, rounded once.
- *   FP16 / BF16  packed inverses (FP64 factorisation rounded once) and the
+ *   FP16 / BF16  packed inverses (double-float inversion rounded once) and the
  *         hybrid coil data (per-frame power-of-two scales) as 16-bit (re, im)
  *         pairs; FFT butterflies, products and accumulation in FP32; the
  *         objective and the stopping test reduce in FP64.
