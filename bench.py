@@ -659,7 +659,8 @@ def run_native(args):
             if prior == args.prior and lam == w["lam"]:
                 continue
             p2 = Plan(mask, sens, lam, w["mu"], prior=prior, rho=w["rho"], max_iters=w["iters"],
-                      storage=args.storage, frame_levels=2, spatial_weight=1.0, cg_steps=5)
+                      storage=args.storage, frame_levels=2, spatial_weight=1.0, cg_steps=5,
+                      profile=1 if prior == "stv" else 0)
             p2.autotune()
             for _ in range(2):
                 p2.solve(kspace, out, info=False)
@@ -672,6 +673,17 @@ def run_native(args):
             b.record(stream)
             torch.cuda.synchronize()
             var[name] = 3 * w["iters"] / (a.elapsed_time(b) / 1e3)
+            if prior == "stv":
+                # the spatio-temporal step (r, 5 CG steps, finish) against HBM: per iteration it
+                # moves 67 fields of N complex64 at minimum (rhs 7, each CG step 10, finish 10)
+                pr = p2.profile()
+                step_ms = pr.temporal_ms / max(pr.temporal_launches, 1)
+                nbytes = 67 * 8 * w["Nx"] * w["Ny"] * w["Nt"]
+                gbs = nbytes / (step_ms / 1e3) / 1e9
+                peak, _ = hbm_peak()
+                line["stv_step"] = {"ms_per_iter": step_ms, "algorithmic_bytes": nbytes, "gbs": gbs,
+                                    "frac_hbm": gbs / peak, "inverse_ms_per_iter":
+                                    pr.inverse_ms / max(pr.inverse_launches, 1)}
             p2.close()
         line["variants"] = var
 
