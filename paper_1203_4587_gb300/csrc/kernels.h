@@ -278,7 +278,7 @@ cudaError_t launch_objective(const ObjParams& p, cudaStream_t s);
 // spatio-temporal Algorithm 2 (stv_kernels.cu): a block walks kStvRows image
 // columns (t, i) of Ny elements
 constexpr int kStvThreads = 256;
-constexpr int kStvRows = 4;
+constexpr int kStvRows = 16;
 cudaError_t launch_stv_init(const StvLaunch& L, cudaStream_t s);     // e = -S(R m) (d1 = 0)
 cudaError_t launch_stv_prior(const StvLaunch& L, cudaStream_t s);    // ||R x||_1
 cudaError_t launch_stv_rhs(const StvLaunch& L, cudaStream_t s);      // r = rhs - M m, gamma_0, ||R x||_1

@@ -29,8 +29,9 @@
 // (they stay zero: S(0) = 0), so R'e needs no cases beyond the first index of
 // each axis.
 //
-// CG inner products are sums over the whole slice.  A thread adds its few
-// elements (kStvRows * Ny / 256 of them, at most 16) in FP32; the block sums
+// CG inner products are sums over the whole slice.  A thread adds its
+// elements (kStvRows * Ny / 256 of them, at most 64) in FP32 with Kahan's
+// compensated summation (error about 2 eps, not n eps); the block sums
 // its threads in FP64 and writes a partial, and the last block of the slice
 // to finish (an atomic counter after a fence) adds the partials in block
 // order, so results do not depend on scheduling.  alpha and beta are formed
@@ -61,7 +62,7 @@ __device__ __forceinline__ Blk blk_of(const StvSlice& P) {
 
 // Row within the block of local element e < kStvRows * Ny: (e + 1/2)/Ny has
 // fractional part >= 1/(2 Ny) >= 2^-11 away from an integer, and its FP32
-// rounding error is below 2^12 * 2^-24, so the truncation is exact.
+// rounding error is below 2^14 * 2^-24, so the truncation is exact.
 __device__ __forceinline__ int row_of(const Blk& b, int e) {
   return __float2int_rz(((float)e + 0.5f) * b.inv_ny);
 }
@@ -139,6 +140,17 @@ __device__ void slice_sum(const StvSlice& P, double v, double* slot) {
   }
 }
 
+// Kahan's compensated sum of FP32 terms
+struct KSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float y) {
+    const float t = y - c;
+    const float u = s + t;
+    c = (u - s) - t;
+    s = u;
+  }
+};
+
 __device__ __forceinline__ float rx_l1(const StvSlice& P, const Pos& q) {
   float2 a, b, c;
   diffs(P, P.x, q, a, b, c);
@@ -179,10 +191,10 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_prior(StvLaunch L) {
   const StvSlice& P = slice_of(L);
   if (P.stop && *P.stop) return;
   const Blk b = blk_of(P);
-  float l1 = 0.f;
+  KSum l1;
 #pragma unroll 4
-  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) l1 += rx_l1(P, pos_of(P, b, e));
-  const double s = group_sum((double)l1, red, threadIdx.x, kStvThreads, BlockBar());
+  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) l1.add(rx_l1(P, pos_of(P, b, e)));
+  const double s = group_sum((double)l1.s, red, threadIdx.x, kStvThreads, BlockBar());
   if (threadIdx.x == 0) atomicAdd(P.prior_acc, s);
 }
 
@@ -196,12 +208,12 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_rhs(StvLaunch L) {
   const float2* ex = P.e + P.n;
   const float2* ey = P.e + 2 * (long long)P.n;
   const float2* m = P.m;
-  float g = 0.f, l1 = 0.f;
+  KSum g, l1;
 #pragma unroll 4
   for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
     const Pos q = pos_of(P, b, e);
     const int idx = q.idx;
-    l1 += rx_l1(P, q);
+    l1.add(rx_l1(P, q));
     // R'e (the padded components are zero past the last index)
     float2 rt = make_float2(-et[idx].x, -et[idx].y), rs = make_float2(-ex[idx].x - ey[idx].x, -ex[idx].y - ey[idx].y);
     if (q.t > 0) rt = c_add(rt, et[idx - st]);
@@ -215,11 +227,11 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_rhs(StvLaunch L) {
     r.x = fmaf(P.rho, 2.f * xv.x - pv.x - mv.x, -rte.x - mm.x);
     r.y = fmaf(P.rho, 2.f * xv.y - pv.y - mv.y, -rte.y - mm.y);
     P.r[idx] = r;
-    g = fmaf(r.x, r.x, fmaf(r.y, r.y, g));
+    g.add(fmaf(r.x, r.x, r.y * r.y));
   }
-  const double s = group_sum((double)l1, red, threadIdx.x, kStvThreads, BlockBar());
+  const double s = group_sum((double)l1.s, red, threadIdx.x, kStvThreads, BlockBar());
   if (threadIdx.x == 0) atomicAdd(P.prior_acc, s);
-  slice_sum(P, (double)g, P.red);
+  slice_sum(P, (double)g.s, P.red);
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_dir(StvLaunch L) {
@@ -239,7 +251,7 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_dir(StvLaunch L) {
     const float2 pv = po[o];
     return make_float2(fmaf(be, pv.x, rv.x), fmaf(be, pv.y, rv.y));
   };
-  float pq = 0.f;
+  KSum pq;
 #pragma unroll 4
   for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
     const Pos q = pos_of(P, b, e);
@@ -248,9 +260,9 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_dir(StvLaunch L) {
     const float2 qv = make_float2(fmaf(P.rho, pv.x, l.x), fmaf(P.rho, pv.y, l.y));
     pn[q.idx] = pv;
     P.q[q.idx] = qv;
-    pq = fmaf(pv.x, qv.x, fmaf(pv.y, qv.y, pq));
+    pq.add(fmaf(pv.x, qv.x, pv.y * qv.y));
   }
-  slice_sum(P, (double)pq, P.red + P.cg + 1 + j);
+  slice_sum(P, (double)pq.s, P.red + P.cg + 1 + j);
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_update(StvLaunch L) {
@@ -262,7 +274,7 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_update(StvLaunch L) {
   const float alpha = (pq > 0.0 && gam > 0.0) ? (float)(gam / pq) : 0.f;
   const float2* pn = P.pc[j & 1];
   const int base = b.row0 * P.Ny;
-  float g = 0.f;
+  KSum g;
   // element-wise: no neighbours, so no (t, i, j)
 #pragma unroll 4
   for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
@@ -273,9 +285,9 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_update(StvLaunch L) {
     rv.x = fmaf(-alpha, qv.x, rv.x); rv.y = fmaf(-alpha, qv.y, rv.y);
     P.m[idx] = mv;
     P.r[idx] = rv;
-    g = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, g));
+    g.add(fmaf(rv.x, rv.x, rv.y * rv.y));
   }
-  slice_sum(P, (double)g, P.red + j + 1);
+  slice_sum(P, (double)g.s, P.red + j + 1);
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_finish(StvLaunch L) {
