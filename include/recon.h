@@ -145,6 +145,18 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
                                const float* sens, float lambda, float mu, recon_prior prior,
                                const recon_opts* opts, void* stream);
 
+/* Self-test of the failure path of the bounded device-side waits (no fault
+ * involved): one CTA waits, through the same bounded mbarrier wait the
+ * persistent kernels use, on a barrier phase that nothing completes, with a
+ * wall-clock limit of limit_us microseconds (1..2000000; the kernels' own
+ * limit is 2 s).  The wait gives up, records DEV_ERR_TIMEOUT in the launch's
+ * error word and returns, and the call reports RECON_ERR_TIMEOUT, the status
+ * a solve returns when one of its waits gives up; the CUDA context stays
+ * usable.  *waited_ms (may be NULL) receives the host-measured time of the
+ * launch.  Any other status means the path is broken: RECON_ERR_CUDA when the
+ * wait came back without reporting, INVALID_ARG for a bad limit. */
+recon_status recon_selftest_wait_timeout(int limit_us, double* waited_ms, void* stream);
+
 /* Changes mu (mu2 of Algorithm 2) of an existing plan: recomputes every packed
  * inverse (mu I + G_{i,t})^{-1} from the plan's device-resident sensitivities
  * and row lists (Eq. eigen_mu with the new mu) and every launch descriptor

@@ -36,7 +36,7 @@ EXPORTS = ["recon_default_opts", "recon_plan_create", "recon_solve", "recon_solv
            "recon_batch_create", "recon_batch_solve", "recon_batch_info", "recon_batch_destroy",
            "recon_grad_create", "recon_grad_forward", "recon_grad_backward", "recon_grad_destroy",
            "recon_solve_kspace", "recon_quantize_kspace", "recon_autotune", "recon_batch_autotune",
-           "recon_plan_create_slab", "recon_solve_slabs", "recon_plan_set_mu"]
+           "recon_plan_create_slab", "recon_solve_slabs", "recon_plan_set_mu", "recon_selftest_wait_timeout"]
 
 
 class Opts(C.Structure):
@@ -142,6 +142,8 @@ def load(path: str = LIB_PATH):
     lib.recon_solve_slabs.argtypes = [i, i, i, i, vp, fp, f, f, i, C.POINTER(Opts), i, fp, fp, C.POINTER(d),
                                       C.POINTER(Info), vp]
     lib.recon_solve_slabs.restype = i
+    lib.recon_selftest_wait_timeout.argtypes = [i, C.POINTER(d), vp]
+    lib.recon_selftest_wait_timeout.restype = i
     lib.recon_plan_set_mu.argtypes = [vp, f, vp]
     lib.recon_plan_set_mu.restype = i
     lib.recon_autotune.argtypes = [vp, C.POINTER(Tuning), vp]
@@ -495,6 +497,13 @@ def solve_slabs(mask, sens, lam, mu, kspace, width, prior="tv", out=None, stream
                                  PRIOR[prior], C.byref(o), int(width), _ptr(k), _ptr(out), tr, C.byref(inf),
                                  _stream(stream)))
     return out, inf, list(tr)
+
+
+def selftest_wait_timeout(limit_us, stream=None):
+    """Runs recon_selftest_wait_timeout: returns (status, host-measured ms)."""
+    ms = C.c_double(0.0)
+    st = load().recon_selftest_wait_timeout(int(limit_us), C.byref(ms), _stream(stream))
+    return st, ms.value
 
 
 def kernel_launches() -> int:

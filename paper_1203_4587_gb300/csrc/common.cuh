@@ -231,14 +231,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Bounded wait on an mbarrier phase.  Returns false (and sets DEV_ERR_TIMEOUT)
 // when the wall-clock limit passes, or false when another CTA already
 // reported an error.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* flags) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* flags,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   unsigned long long t0 = global_ns();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 0) {
       if (*((volatile int*)&flags[FLAG_ERR]) != 0) return false;
-      if (global_ns() - t0 > kWaitLimitNs) { atomicOr(&flags[FLAG_ERR], DEV_ERR_TIMEOUT); return false; }
+      if (global_ns() - t0 > limit_ns) { atomicOr(&flags[FLAG_ERR], DEV_ERR_TIMEOUT); return false; }
     }
   }
 }
