@@ -200,27 +200,49 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan_inverse(const float2* 
         Tm[idx] = dc_pack(dc_neg(acc));
       }
       __syncthreads();
-      // the sweep of the block over the stored lower triangle
+      // the sweep of the block over the stored lower triangle; a thread takes
+      // columns c and c + 16 of its row, so one T(r) serves two elements and
+      // two independent chains interleave
       for (int ib = 0; ib < n; ib += kPlanRows) {
         const int r = ib + ty;
         const bool rin = r >= k0 && r < k0 + bb;
-        for (int jb = 0; jb < ib + kPlanRows; jb += 16) {
-          const int c = jb + tx;
-          if (r >= n || c > r) continue;
-          const bool cin = c >= k0 && c < k0 + bb;
-          const size_t o = (size_t)r * n + c;
-          if (!rin && !cin) {          // M[R][R] - T(r) conj(M(c, block))
-            dc w = ldw(W, o);
+        for (int jb = 0; jb < ib + kPlanRows; jb += 32) {
+          const int c0 = jb + tx, c1 = c0 + 16;
+          const bool v0 = r < n && c0 <= r, v1 = r < n && c1 <= r;
+          const bool in0 = c0 >= k0 && c0 < k0 + bb, in1 = c1 >= k0 && c1 < k0 + bb;
+          if (v0 && v1 && !rin && !in0 && !in1) {   // M[R][R] - T(r) conj(M(c, block)), two columns
+            const size_t o0 = (size_t)r * n + c0, o1 = o0 + 16;
+            dc w0 = ldw(W, o0), w1 = ldw(W, o1);
 #pragma unroll
             for (int q = 0; q < B; ++q)
-              if (q < bb) w = dc_fms_conj(w, dc_unpack(Tm[(size_t)r * B + q]), dc_unpack(pan[(size_t)c * B + q]));
-            stw(W, o, w);
-          } else if (!rin) {           // (r, c) with c in the block, r below it
-            W[o] = Tm[(size_t)r * B + (c - k0)];
-          } else if (!cin) {           // r in the block, c left of it: conj of (c, r)
-            W[o] = dc_pack(dc_conj(dc_unpack(Tm[(size_t)c * B + (r - k0)])));
-          } else {                     // inside the block
-            W[o] = Pq[(r - k0) * B + (c - k0)];
+              if (q < bb) {
+                const dc t = dc_unpack(Tm[(size_t)r * B + q]);
+                w0 = dc_fms_conj(w0, t, dc_unpack(pan[(size_t)c0 * B + q]));
+                w1 = dc_fms_conj(w1, t, dc_unpack(pan[(size_t)c1 * B + q]));
+              }
+            stw(W, o0, w0);
+            stw(W, o1, w1);
+            continue;
+          }
+#pragma unroll 1
+          for (int h = 0; h < 2; ++h) {
+            const int c = h ? c1 : c0;
+            if (!(h ? v1 : v0)) continue;
+            const bool cin = h ? in1 : in0;
+            const size_t o = (size_t)r * n + c;
+            if (!rin && !cin) {          // M[R][R] - T(r) conj(M(c, block))
+              dc w = ldw(W, o);
+#pragma unroll
+              for (int q = 0; q < B; ++q)
+                if (q < bb) w = dc_fms_conj(w, dc_unpack(Tm[(size_t)r * B + q]), dc_unpack(pan[(size_t)c * B + q]));
+              stw(W, o, w);
+            } else if (!rin) {           // (r, c) with c in the block, r below it
+              W[o] = Tm[(size_t)r * B + (c - k0)];
+            } else if (!cin) {           // r in the block, c left of it: conj of (c, r)
+              W[o] = dc_pack(dc_conj(dc_unpack(Tm[(size_t)c * B + (r - k0)])));
+            } else {                     // inside the block
+              W[o] = Pq[(r - k0) * B + (c - k0)];
+            }
           }
         }
       }
