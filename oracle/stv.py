@@ -36,7 +36,8 @@ import numpy as np
 
 from .admm import delta_ratio, soft
 
-__all__ = ["stv_R", "stv_Radj", "stv_M", "cg_steps", "objective_stv", "admm_analysis_stv"]
+__all__ = ["stv_R", "stv_Radj", "stv_M", "cg_steps", "objective_stv", "admm_analysis_stv",
+           "stv_R_vol", "stv_Radj_vol", "stv_M_vol", "objective_stv_vol", "admm_analysis_stv_volume"]
 
 
 def stv_R(x, ws):
@@ -148,3 +149,71 @@ def admm_analysis_stv(b, inv, lam, mu, rho, iters, ws=1.0, cg=5, fid=None, tol=0
                 if 0.0 <= dk < tol:
                     break
     return x, dict(J=J, iters=k_done, state=(x, m, d1, d2))
+
+
+# ---------------------------------------------------------------------------
+# 3D volumes (Section II-A: the model extends from 2D slices to volumes).
+# With kz fully sampled, an inverse FFT along z separates the volume into
+# slices, each with its own ky-t mask, coil profiles and per-column inverses
+# (Section IV-C holds slice by slice).  The slices are then coupled only by a
+# z-difference in R:
+#     R x = (D_t x, w D_x x, w D_y x, w_z D_z x),   x[z, t, j, i],
+# and the m-update's CG runs on the whole volume (inner products over every
+# slice).  A volume of one slice is the 2D algorithm above.
+# ---------------------------------------------------------------------------
+def stv_R_vol(x, ws, wz):
+    """R x for x[z, t, j, i]: (D_t, w D_x, w D_y, w_z D_z), non-circular."""
+    x = np.asarray(x)
+    return (x[:, 1:] - x[:, :-1], ws * (x[:, :, :, 1:] - x[:, :, :, :-1]), ws * (x[:, :, 1:, :] - x[:, :, :-1, :]),
+            wz * (x[1:] - x[:-1]))
+
+
+def stv_Radj_vol(u, ws, wz, shape):
+    ut, ux, uy, uz = u
+    Nz, Nt, Ny, Nx = shape
+    return (_diff_adj(ut, 1, Nt) + ws * _diff_adj(ux, 3, Nx) + ws * _diff_adj(uy, 2, Ny)
+            + wz * _diff_adj(uz, 0, Nz))
+
+
+def stv_M_vol(m, rho, ws, wz):
+    return rho * m + stv_Radj_vol(stv_R_vol(m, ws, wz), ws, wz, m.shape)
+
+
+def objective_stv_vol(x, lam, ws, wz, fids):
+    """J = lambda ||R x||_1 + sum_z ||y_z - H_z x_z||^2."""
+    return lam * float(sum(np.abs(c).sum() for c in stv_R_vol(x, ws, wz))) + sum(f(xz) for f, xz in zip(fids, x))
+
+
+def admm_analysis_stv_volume(bs, invs, lam, mu, rho, iters, ws=1.0, wz=1.0, cg=5, fids=None):
+    """Algorithm 2 on a volume of slices: bs[z] = H_z'y_z, invs[z] the slice's
+    column inverses; the same steps as ``admm_analysis_stv`` with the 4-component
+    R above and one CG over the volume.  Returns (x[z, t, j, i], info)."""
+    b = np.stack([np.asarray(v, dtype=np.complex128) for v in bs])
+    shape = b.shape
+    mu2 = mu
+    mu1 = mu / rho
+    r2 = mu2 / mu1
+
+    def M(a):
+        return stv_M_vol(a, r2, ws, wz)
+
+    def inverse(r):
+        return np.stack([inv.apply(rz) for inv, rz in zip(invs, r)])
+
+    x = b.copy()
+    m = x.copy()
+    d1 = tuple(np.zeros_like(c) for c in stv_R_vol(x, ws, wz))
+    d2 = np.zeros_like(b)
+    J = [objective_stv_vol(x, lam, ws, wz, fids)] if fids is not None else []
+    for _ in range(iters):
+        Rm = stv_R_vol(m, ws, wz)
+        v = tuple(soft(a + d, lam / (2.0 * mu1)) for a, d in zip(Rm, d1))
+        rhs = stv_Radj_vol(tuple(a - d for a, d in zip(v, d1)), ws, wz, shape) + r2 * (x + d2)
+        m = cg_steps(M, rhs, m, cg)
+        x = inverse(b + mu2 * (m - d2))
+        Rm = stv_R_vol(m, ws, wz)
+        d1 = tuple(d - (a - c) for d, a, c in zip(d1, v, Rm))
+        d2 = d2 - (m - x)
+        if fids is not None:
+            J.append(objective_stv_vol(x, lam, ws, wz, fids))
+    return x, dict(J=J, iters=iters, state=(x, m, d1, d2))

@@ -175,3 +175,81 @@ def test_column_subset_refused():
     P = oracle.Problem(y, sens, mask, 0.1, cols=[0, 2])
     with pytest.raises(ValueError):
         P.solve("stv", 0.01, 0.1, iters=2)
+
+
+# --- 3D volumes: slices coupled by a z-difference --------------------------------------------
+
+def _dense_M_vol(shape, rho, ws, wz):
+    Nz, Nt, Ny, Nx = shape
+    I = [np.eye(n) for n in shape]
+    Lz, Lt, Ly, Lx = (_D(n).T @ _D(n) for n in shape)
+
+    def k4(a, b, c, d):
+        return np.kron(np.kron(np.kron(a, b), c), d)
+    L = (k4(I[0], Lt, I[2], I[3]) + ws ** 2 * (k4(I[0], I[1], Ly, I[3]) + k4(I[0], I[1], I[2], Lx))
+         + wz ** 2 * k4(Lz, I[1], I[2], I[3]))
+    return rho * np.eye(int(np.prod(shape))) + L
+
+
+@pytest.mark.parametrize("shape", [(3, 2, 4, 5), (1, 3, 2, 2), (4, 1, 3, 1)])
+def test_volume_R_adjoint(shape):
+    rng = np.random.default_rng(sum(shape) + 7)
+    x = _rand(rng, shape)
+    Rx = oracle.stv_R_vol(x, 0.7, 1.3)
+    u = tuple(_rand(rng, c.shape) for c in Rx)
+    lhs = sum(np.vdot(a, b) for a, b in zip(Rx, u))
+    rhs = np.vdot(x, oracle.stv_Radj_vol(u, 0.7, 1.3, shape))
+    assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+
+
+@pytest.mark.parametrize("wz", [1.0, 0.4, 0.0])
+def test_volume_M_equals_kronecker_assembly(wz):
+    shape, rho, ws = (3, 2, 3, 2), 0.5, 0.8
+    n = int(np.prod(shape))
+    cols = []
+    for k in range(n):
+        e = np.zeros(n, complex)
+        e[k] = 1.0
+        cols.append(oracle.stv_M_vol(e.reshape(shape), rho, ws, wz).ravel())
+    np.testing.assert_allclose(np.stack(cols, axis=1), _dense_M_vol(shape, rho, ws, wz), atol=1e-14)
+
+
+def test_volume_cg_converges_to_dct_closed_form():
+    shape, rho, ws, wz = (4, 5, 6, 7), 0.5, 1.0, 0.6
+    rng = np.random.default_rng(9)
+    rhs = _rand(rng, shape)
+    m = oracle.cg_steps(lambda a: oracle.stv_M_vol(a, rho, ws, wz), rhs, np.zeros(shape, complex), 150)
+    lam = [2.0 - 2.0 * np.cos(np.pi * np.arange(n) / n) for n in shape]
+    den = (rho + wz ** 2 * lam[0][:, None, None, None] + lam[1][None, :, None, None]
+           + ws ** 2 * (lam[2][None, None, :, None] + lam[3][None, None, None, :]))
+    exact = scipy.fft.idctn(scipy.fft.dctn(rhs, type=2, norm="ortho") / den, type=2, norm="ortho")
+    np.testing.assert_allclose(m, exact, atol=1e-9 * np.abs(exact).max())
+
+
+def test_volume_of_one_slice_is_the_2d_algorithm():
+    x, sens, mask, y = _small_case(Nx=5, Ny=6, Nt=4, Nc=2, R=2, noise=0.02, seed=24)
+    lam, mu, rho, iters = 0.02, 0.1, 0.5, 10
+    P = oracle.Problem(y, sens, mask, mu)
+    x2, i2 = oracle.admm_analysis_stv(P.b, P.inv, lam, mu, rho, iters, ws=0.9, cg=4, fid=P.fid)
+    xv, iv = oracle.admm_analysis_stv_volume([P.b], [P.inv], lam, mu, rho, iters, ws=0.9, wz=2.0, cg=4,
+                                             fids=[P.fid])
+    np.testing.assert_allclose(xv[0], x2, atol=1e-12 * np.abs(x2).max())
+    np.testing.assert_allclose(iv["J"], i2["J"], rtol=1e-12)
+
+
+def test_kkt_volume_on_tiny_problem():
+    """sum_z 2 H_z'(H_z x_z - y_z) + lambda R' g = 0 at the converged volume."""
+    cases = [_small_case(Nx=3, Ny=4, Nt=3, Nc=2, R=2, noise=0.05, seed=s) for s in (31, 32)]
+    lam, mu, rho, ws, wz = 0.05, 0.1, 0.5, 0.8, 1.2
+    probs = [oracle.Problem(y, sens, mask, mu) for (_, sens, mask, y) in cases]
+    xv, info = oracle.admm_analysis_stv_volume([p.b for p in probs], [p.inv for p in probs], lam, mu, rho, 3000,
+                                               ws=ws, wz=wz, cg=80)
+    _, m, d1, _ = info["state"]
+    np.testing.assert_allclose(m, xv, atol=1e-9)
+    g = tuple(2 * (mu / rho) * d / lam for d in d1)
+    for gc in g:
+        assert np.abs(gc).max() <= 1 + 1e-8
+    grad = np.stack([2 * oracle.adjoint_op(oracle.forward_op(xz, sens, mask) - y, sens, mask)
+                     for xz, (_, sens, mask, y) in zip(xv, cases)])
+    stat = grad + lam * oracle.stv_Radj_vol(g, ws, wz, xv.shape)
+    assert np.linalg.norm(stat) < 1e-8 * max(1.0, np.linalg.norm(grad))
