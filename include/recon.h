@@ -252,6 +252,21 @@ typedef struct recon_batch recon_batch; /* opaque, owned by the library */
  * on one device.  Errors: INVALID_ARG, OOM, CUDA. */
 recon_status recon_batch_create(recon_batch** out, recon_plan* const* plans, int n);
 
+/* A 3D volume as a batch: slices stacked along z, after an inverse FFT
+ * along a fully sampled kz, each with its own ky-t mask, coil profiles and
+ * per-column inverses (Section II-A: the model extends to volumes; Section
+ * IV-C holds slice by slice).  The plans must be RECON_PRIOR_STV with equal
+ * Nx, Ny, Nt, cg_steps, max_iters, storage and objective mode, and tol = 0.
+ * plans[0..nz-1] are in z order.  R gains a z-difference,
+ * R x = (D_t x, w D_x x, w D_y x, w_z D_z x), non-circular along z, and the
+ * m-update's CG runs over the whole volume (its inner products sum every
+ * slice).  The result is a recon_batch: solve, info and destroy as for a
+ * batch.  Each slice's J(k) carries the z-differences to the slice above it;
+ * the volume's J is the sum over slices.  A volume of one slice is the 2D
+ * solve.  Errors: INVALID_ARG (NULL, wz < 0 or not finite, mixed plans),
+ * OOM, CUDA. */
+recon_status recon_volume_create(recon_batch** out, recon_plan* const* plans, int nz, float wz);
+
 /* Solves every slice: kspace[q] and image[q] are device buffers laid out as
  * for recon_solve.  The first call with a given set of buffers runs the
  * launches directly and captures them into a graph; later calls with the same

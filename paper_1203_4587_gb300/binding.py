@@ -36,7 +36,8 @@ EXPORTS = ["recon_default_opts", "recon_plan_create", "recon_solve", "recon_solv
            "recon_batch_create", "recon_batch_solve", "recon_batch_info", "recon_batch_destroy",
            "recon_grad_create", "recon_grad_forward", "recon_grad_backward", "recon_grad_destroy",
            "recon_solve_kspace", "recon_quantize_kspace", "recon_autotune", "recon_batch_autotune",
-           "recon_plan_create_slab", "recon_solve_slabs", "recon_plan_set_mu", "recon_selftest_wait_timeout"]
+           "recon_plan_create_slab", "recon_solve_slabs", "recon_plan_set_mu", "recon_selftest_wait_timeout",
+           "recon_volume_create"]
 
 
 class Opts(C.Structure):
@@ -142,6 +143,8 @@ def load(path: str = LIB_PATH):
     lib.recon_solve_slabs.argtypes = [i, i, i, i, vp, fp, f, f, i, C.POINTER(Opts), i, fp, fp, C.POINTER(d),
                                       C.POINTER(Info), vp]
     lib.recon_solve_slabs.restype = i
+    lib.recon_volume_create.argtypes = [C.POINTER(vp), C.POINTER(vp), i, f]
+    lib.recon_volume_create.restype = i
     lib.recon_selftest_wait_timeout.argtypes = [i, C.POINTER(d), vp]
     lib.recon_selftest_wait_timeout.restype = i
     lib.recon_plan_set_mu.argtypes = [vp, f, vp]
@@ -356,6 +359,17 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Volume(Batch):
+    """Slices of a 3D volume in z order, coupled by w_z D_z in the spatio-temporal
+    prior (recon_volume_create); solved like a batch."""
+
+    def __init__(self, plans, wz):
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        self._h = C.c_void_p()
+        _check(load().recon_volume_create(C.byref(self._h), arr, len(self.plans), float(wz)))
 
 
 class Grad:

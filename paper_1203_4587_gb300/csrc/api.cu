@@ -436,8 +436,8 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
   }
   PC(p->alloc((void**)&p->b, nimg * sizeof(float2)));
   // TV: m, d1, p;  DFT: u = v + d;  Haar: u ((L+1) channels) and s = Psi'u;
-  // STV: m and q (s0), e = d1 - v with three components (s1[0]), p and the
-  // CG residual (s2), the CG directions (r, cgd)
+  // STV: m and q (s0), e = d1 - v with four components (s1[0]; z in a
+  // volume), p and the CG residual (s2), the CG directions (r, cgd)
   const size_t nu = (prior == RECON_PRIOR_HAAR) ? (size_t)(o.frame_levels + 1) * nimg : nimg;
   for (int k = 0; k < 2; ++k) {
     PC(p->alloc((void**)&p->s0[k], nu * sizeof(float2)));
@@ -447,7 +447,7 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
     }
     if (prior == RECON_PRIOR_HAAR) PC(p->alloc((void**)&p->s1[k], nimg * sizeof(float2)));
     if (prior == RECON_PRIOR_STV) {
-      if (k == 0) PC(p->alloc((void**)&p->s1[k], 3 * nimg * sizeof(float2)));
+      if (k == 0) PC(p->alloc((void**)&p->s1[k], 4 * nimg * sizeof(float2)));   // t, x, y, z
       PC(p->alloc((void**)&p->s2[k], nimg * sizeof(float2)));
     }
   }

@@ -286,7 +286,11 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
     e->cg = p0->opts.cg_steps;
     const size_t per = (size_t)std::max(e->K, 1) * (2 * e->cg + 1);
     e->stv_red.assign(n, nullptr);
-    for (int q = 0; q < n; ++q) RC(e->arena.alloc(reinterpret_cast<void**>(&e->stv_red[q]), per * sizeof(double)));
+    // a volume shares one set of slots (its sums run over every slice)
+    for (int q = 0; q < (e->volume ? 1 : n); ++q)
+      RC(e->arena.alloc(reinterpret_cast<void**>(&e->stv_red[q]), per * sizeof(double)));
+    if (e->volume)
+      for (int q = 1; q < n; ++q) e->stv_red[q] = e->stv_red[0];
     RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_stv_count), (size_t)n * sizeof(unsigned)));
     RC(cudaMemset(e->d_stv_count, 0, (size_t)n * sizeof(unsigned)));
     int blocks = 0;
@@ -377,7 +381,18 @@ recon_status engine_set_tile(Engine* e, int px) {
         d.tile0 = tile0[q];
         d.nblk = (e->plans[q]->Nt * e->plans[q]->Nx + px - 1) / px;
         d.part = e->d_stv_part;
-        d.count = e->d_stv_count + q;
+        if (e->volume) {   // neighbours at q -1 / q + 1, one sum over every slice
+          d.wz = e->wz;
+          d.zprev = q > 0;
+          d.znext = q + 1 < n;
+          d.count = e->d_stv_count;
+          d.red0 = 0;
+          d.rednblk = blocks;
+        } else {
+          d.count = e->d_stv_count + q;
+          d.red0 = d.tile0;
+          d.rednblk = d.nblk;
+        }
         t[(size_t)(k - 1) * n + q] = d;
       }
     RC(upload(e->arena, reinterpret_cast<StvSlice**>(&e->d_tmp), t));
@@ -602,6 +617,36 @@ recon_status recon_batch_create(recon_batch** out, recon_plan* const* plans, int
     if (!plans[q]) return fail(RECON_ERR_INVALID_ARG, "NULL plan in batch");
   auto* b = new recon_batch();
   recon_status st = engine_build(&b->eng, plans, n);
+  if (st != RECON_OK) {
+    delete b;
+    return st;
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "cudaStreamCreateWithFlags");
+  }
+  *out = b;
+  return RECON_OK;
+}
+
+recon_status recon_volume_create(recon_batch** out, recon_plan* const* plans, int nz, float wz) {
+  if (!out || !plans || nz < 1) return fail(RECON_ERR_INVALID_ARG, "bad argument");
+  *out = nullptr;
+  if (!(wz >= 0.f) || !std::isfinite(wz)) return fail(RECON_ERR_INVALID_ARG, "wz must be >= 0");
+  for (int q = 0; q < nz; ++q) {
+    const recon_plan* p = plans[q];
+    if (!p) return fail(RECON_ERR_INVALID_ARG, "NULL plan in volume");
+    if (p->prior != RECON_PRIOR_STV) return fail(RECON_ERR_INVALID_ARG, "a volume takes spatio-temporal plans");
+    if (p->Nx != plans[0]->Nx || p->Ny != plans[0]->Ny || p->Nt != plans[0]->Nt)
+      return fail(RECON_ERR_INVALID_ARG, "the slices of a volume share Nx, Ny and Nt");
+    if (p->opts.tol > 0.0)
+      return fail(RECON_ERR_INVALID_ARG, "a volume runs a fixed number of iterations (tol = 0)");
+  }
+  auto* b = new recon_batch();
+  b->eng.volume = true;
+  b->eng.wz = wz;
+  recon_status st = engine_build(&b->eng, plans, nz);
   if (st != RECON_OK) {
     delete b;
     return st;

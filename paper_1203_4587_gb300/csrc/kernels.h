@@ -155,10 +155,13 @@ struct HaarSlice {           // temporal step of Algorithm 1 with the undecimate
 };
 
 // Algorithm 2 with R = (D_t, w D_x, w D_y) (spatio-temporal differences) and a
-// CG m-update, one slice.  Fields [Nt][Nx][Ny] (n elements); the three
-// difference components of e = d1 - v are stored padded, [3][n], with zeros
+// CG m-update, one slice.  Fields [Nt][Nx][Ny] (n elements); the difference
+// components of e = d1 - v are stored padded, [4][n] (t, x, y, z), with zeros
 // where a difference leaves the grid.  Reduction slots of one iteration:
 // red[0..cg] = gamma_0..gamma_cg (<r, r>), red[cg+1+j] = <p_j, q_j>.
+// In a volume (slices stacked along z, coupled by w_z D_z) the slices of a
+// launch are in z order, the neighbours of slice q are descriptors q-1 and
+// q+1, and every slice shares one reduction range, counter and slot array.
 struct StvSlice {
   int Nx, Ny, Nt;
   int n;                     // Nt*Nx*Ny
@@ -166,8 +169,10 @@ struct StvSlice {
   float tau1;                // lambda / (2 mu1)
   float rho;                 // mu2 / mu1
   float ws;                  // spatial weight w
+  float wz;                  // z weight w_z (volumes; 0 otherwise)
+  int zprev, znext;          // 1 when the slice has a neighbour below / above in z
   float2* m;                 // m (updated in place by the CG steps)
-  float2* e;                 // [3][n]: d1 - v
+  float2* e;                 // [4][n]: d1 - v
   float2* p;                 // p = m - d2 (so d2 = x - p); the inverse step reads r = b + mu2 p
   const float2* x;
   float2* r;                 // CG residual
@@ -176,6 +181,7 @@ struct StvSlice {
   double* red;               // this iteration's reduction slots
   double* part;              // per-block partial sums (indexed by the launch's block)
   unsigned* count;           // blocks done, for the last-block sum (reset by that block)
+  int red0, rednblk;         // the blocks whose partials make one sum (the slice, or the volume)
   double* prior_acc;         // += ||R x||_1 of the incoming x
   const int* stop;
   int tile0;                 // first block of this slice in the launch

@@ -45,6 +45,8 @@ struct Engine {
   // spatio-temporal prior: CG steps, per-block partial sums, per-slice block
   // counters and reduction slots (K sets of 2 cg + 1 per slice)
   int cg = 0;
+  bool volume = false;     // the slices are a volume in z order, coupled by w_z D_z
+  float wz = 0.f;
   double* d_stv_part = nullptr;
   unsigned* d_stv_count = nullptr;
   std::vector<double*> stv_red;

@@ -29,7 +29,13 @@
 // (they stay zero: S(0) = 0), so R'e needs no cases beyond the first index of
 // each axis.
 //
-// CG inner products are sums over the whole slice.  A thread adds its
+// 3D volumes: slices stacked along z (each with its own mask, coils and
+// inverses) add w_z D_z to R.  The slices of a volume are consecutive
+// descriptors of one launch; an element's z-neighbours are the same element
+// of the neighbouring descriptors' fields, and e carries a fourth component.
+// A volume of one slice runs exactly the 2D arithmetic.
+//
+// CG inner products are sums over the whole slice (over the whole volume).  A thread adds its
 // elements (kStvRows * Ny / 256 of them, at most 64) in FP32 with Kahan's
 // compensated summation (error about 2 eps, not n eps); the block sums
 // its threads in FP64 and writes a partial, and the last block of the slice
@@ -82,21 +88,28 @@ __device__ __forceinline__ Pos pos_of(const StvSlice& P, const Blk& b, int e) {
   return q;
 }
 
-// (D_t f, w D_x f, w D_y f) at q, zero where the difference leaves the grid
-__device__ __forceinline__ void diffs(const StvSlice& P, const float2* __restrict__ f, const Pos& q,
-                                      float2& dt, float2& dx, float2& dy) {
+// (D_t f, w D_x f, w D_y f, w_z D_z f) at q, zero where the difference leaves
+// the grid; fz is the same field of the slice above (null: none)
+__device__ __forceinline__ void diffs(const StvSlice& P, const float2* __restrict__ f, const float2* fz,
+                                      const Pos& q, float2 (&d)[4]) {
   const float2 c = f[q.idx];
   const float2 z = make_float2(0.f, 0.f);
-  dt = (q.t + 1 < P.Nt) ? c_sub(f[q.idx + P.Nx * P.Ny], c) : z;
-  dx = (q.i + 1 < P.Nx) ? c_scale(c_sub(f[q.idx + P.Ny], c), P.ws) : z;
-  dy = (q.j + 1 < P.Ny) ? c_scale(c_sub(f[q.idx + 1], c), P.ws) : z;
+  d[0] = (q.t + 1 < P.Nt) ? c_sub(f[q.idx + P.Nx * P.Ny], c) : z;
+  d[1] = (q.i + 1 < P.Nx) ? c_scale(c_sub(f[q.idx + P.Ny], c), P.ws) : z;
+  d[2] = (q.j + 1 < P.Ny) ? c_scale(c_sub(f[q.idx + 1], c), P.ws) : z;
+  d[3] = fz ? c_scale(c_sub(fz[q.idx], c), P.wz) : z;
 }
 
-// (D'D f)_t + w^2 ((D'D f)_x + (D'D f)_y) at q: the 7-point operator R'R
-template <class F>
-__device__ __forceinline__ float2 rtr(const StvSlice& P, F f, const Pos& q) {
+// (D'D f)_t + w^2 ((D'D f)_x + (D'D f)_y) + w_z^2 (D'D f)_z at q: the 7-point
+// (9-point in a volume) operator R'R; fp / fn give f of the slices below /
+// above (used only when the slice has them)
+template <class F, class Fp, class Fn>
+__device__ __forceinline__ float2 rtr(const StvSlice& P, F f, Fp fp, Fn fn, const Pos& q) {
   const int idx = q.idx, st = P.Nx * P.Ny;
   const float2 c = f(idx);
+  float2 lz = make_float2(0.f, 0.f);
+  if (P.zprev) lz = c_add(lz, c_sub(c, fp(idx)));
+  if (P.znext) lz = c_sub(lz, c_sub(fn(idx), c));
   float2 lt = make_float2(0.f, 0.f), ls = make_float2(0.f, 0.f);
   if (q.t > 0) lt = c_add(lt, c_sub(c, f(idx - st)));
   if (q.t + 1 < P.Nt) lt = c_sub(lt, c_sub(f(idx + st), c));
@@ -104,20 +117,28 @@ __device__ __forceinline__ float2 rtr(const StvSlice& P, F f, const Pos& q) {
   if (q.i + 1 < P.Nx) ls = c_sub(ls, c_sub(f(idx + P.Ny), c));
   if (q.j > 0) ls = c_add(ls, c_sub(c, f(idx - 1)));
   if (q.j + 1 < P.Ny) ls = c_sub(ls, c_sub(f(idx + 1), c));
-  const float w2 = P.ws * P.ws;
-  return make_float2(fmaf(w2, ls.x, lt.x), fmaf(w2, ls.y, lt.y));
+  const float w2 = P.ws * P.ws, z2 = P.wz * P.wz;
+  return make_float2(fmaf(z2, lz.x, fmaf(w2, ls.x, lt.x)), fmaf(z2, lz.y, fmaf(w2, ls.y, lt.y)));
 }
 
-__device__ __forceinline__ const StvSlice& slice_of(const StvLaunch& L) {
+__device__ __forceinline__ int slice_of(const StvLaunch& L) {
   int lo = 0, hi = L.nslices - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (L.slices[mid].tile0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
   }
-  return L.slices[lo];
+  return lo;
+}
+// the slices below / above in a volume (null: none)
+__device__ __forceinline__ const StvSlice* below(const StvLaunch& L, int si) {
+  return L.slices[si].zprev ? &L.slices[si - 1] : nullptr;
+}
+__device__ __forceinline__ const StvSlice* above(const StvLaunch& L, int si) {
+  return L.slices[si].znext ? &L.slices[si + 1] : nullptr;
 }
 
-// Sum of v over the slice into *slot (deterministic order); see the file comment.
+// Sum of v over the slice (the volume) into *slot (deterministic order); see
+// the file comment.
 __device__ void slice_sum(const StvSlice& P, double v, double* slot) {
   __shared__ double red[32];
   __shared__ int last;
@@ -126,13 +147,13 @@ __device__ void slice_sum(const StvSlice& P, double v, double* slot) {
   if (tid == 0) {
     P.part[blockIdx.x] = s;
     __threadfence();
-    last = (atomicAdd(P.count, 1u) == (unsigned)(P.nblk - 1));
+    last = (atomicAdd(P.count, 1u) == (unsigned)(P.rednblk - 1));
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   double a = 0.0;
-  for (int b = tid; b < P.nblk; b += kStvThreads) a += __ldcg(P.part + P.tile0 + b);
+  for (int b = tid; b < P.rednblk; b += kStvThreads) a += __ldcg(P.part + P.red0 + b);
   const double tot = group_sum(a, red, tid, kStvThreads, BlockBar());
   if (tid == 0) {
     *slot = tot;
@@ -151,77 +172,87 @@ struct KSum {
   }
 };
 
-__device__ __forceinline__ float rx_l1(const StvSlice& P, const Pos& q) {
-  float2 a, b, c;
-  diffs(P, P.x, q, a, b, c);
-  return c_abs(a) + c_abs(b) + c_abs(c);
+__device__ __forceinline__ float rx_l1(const StvSlice& P, const StvSlice* Pn, const Pos& q) {
+  float2 d[4];
+  diffs(P, P.x, Pn ? Pn->x : nullptr, q, d);
+  return c_abs(d[0]) + c_abs(d[1]) + c_abs(d[2]) + c_abs(d[3]);
 }
 
-// e = d1 - S(R m + d1) into the three padded components
-__device__ __forceinline__ void threshold(const StvSlice& P, const Pos& q, float2 d0, float2 d1, float2 d2) {
-  float2 a, b, c;
-  diffs(P, P.m, q, a, b, c);
-  // d1' = e + R m arrives here as (d0, d1, d2) + (a, b, c) when called from
-  // k_stv_finish; from k_stv_init d1 = 0
-  const float2 rm[3] = {a, b, c};
-  const float2 dd[3] = {c_add(d0, a), c_add(d1, b), c_add(d2, c)};
+// e = d1 - S(R m + d1) into the padded components, with d1 = e + R m (the
+// previous e, from k_stv_finish) or d1 = 0 (first = true, from k_stv_init)
+__device__ __forceinline__ void threshold(const StvSlice& P, const StvSlice* Pn, const Pos& q, bool first) {
+  float2 rm[4];
+  diffs(P, P.m, Pn ? Pn->m : nullptr, q, rm);
+  const int nc = (P.zprev || P.znext) ? 4 : 3;
 #pragma unroll
-  for (int k = 0; k < 3; ++k)
-    P.e[(long long)k * P.n + q.idx] = c_sub(dd[k], c_soft(c_add(rm[k], dd[k]), P.tau1));
+  for (int k = 0; k < 4; ++k) {
+    if (k >= nc) break;
+    const long long o = (long long)k * P.n + q.idx;
+    const float2 dd = first ? make_float2(0.f, 0.f) : c_add(P.e[o], rm[k]);
+    P.e[o] = c_sub(dd, c_soft(c_add(rm[k], dd), P.tau1));
+  }
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_init(StvLaunch L) {
-  const StvSlice& P = slice_of(L);
+  const int si = slice_of(L);
+  const StvSlice& P = L.slices[si];
   if (P.stop && *P.stop) return;
+  const StvSlice* Pn = above(L, si);
   const Blk b = blk_of(P);
-  const float2 z = make_float2(0.f, 0.f);
-  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
-    const Pos q = pos_of(P, b, e);
-    float2 a, bb, c;
-    diffs(P, P.m, q, a, bb, c);
-    // d1 = 0: e = -S(R m)
-    P.e[q.idx] = c_sub(z, c_soft(a, P.tau1));
-    P.e[(long long)P.n + q.idx] = c_sub(z, c_soft(bb, P.tau1));
-    P.e[2 * (long long)P.n + q.idx] = c_sub(z, c_soft(c, P.tau1));
-  }
+  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) threshold(P, Pn, pos_of(P, b, e), true);
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_prior(StvLaunch L) {
   __shared__ double red[32];
-  const StvSlice& P = slice_of(L);
+  const int si = slice_of(L);
+  const StvSlice& P = L.slices[si];
   if (P.stop && *P.stop) return;
+  const StvSlice* Pn = above(L, si);
   const Blk b = blk_of(P);
   KSum l1;
 #pragma unroll 4
-  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) l1.add(rx_l1(P, pos_of(P, b, e)));
+  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) l1.add(rx_l1(P, Pn, pos_of(P, b, e)));
   const double s = group_sum((double)l1.s, red, threadIdx.x, kStvThreads, BlockBar());
   if (threadIdx.x == 0) atomicAdd(P.prior_acc, s);
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_rhs(StvLaunch L) {
   __shared__ double red[32];
-  const StvSlice& P = slice_of(L);
+  const int si = slice_of(L);
+  const StvSlice& P = L.slices[si];
   if (P.stop && *P.stop) return;
+  const StvSlice* Pp = below(L, si);
+  const StvSlice* Pn = above(L, si);
   const Blk b = blk_of(P);
   const int st = P.Nx * P.Ny;
   const float2* et = P.e;
   const float2* ex = P.e + P.n;
   const float2* ey = P.e + 2 * (long long)P.n;
   const float2* m = P.m;
+  const float2* mp = Pp ? Pp->m : m;
+  const float2* mn = Pn ? Pn->m : m;
+  const float2* ez = P.e + 3 * (long long)P.n;
+  const float2* ezp = Pp ? Pp->e + 3 * (long long)Pp->n : ez;
   KSum g, l1;
 #pragma unroll 4
   for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
     const Pos q = pos_of(P, b, e);
     const int idx = q.idx;
-    l1.add(rx_l1(P, q));
+    l1.add(rx_l1(P, Pn, q));
     // R'e (the padded components are zero past the last index)
     float2 rt = make_float2(-et[idx].x, -et[idx].y), rs = make_float2(-ex[idx].x - ey[idx].x, -ex[idx].y - ey[idx].y);
     if (q.t > 0) rt = c_add(rt, et[idx - st]);
     if (q.i > 0) rs = c_add(rs, ex[idx - P.Ny]);
     if (q.j > 0) rs = c_add(rs, ey[idx - 1]);
-    const float2 rte = make_float2(fmaf(P.ws, rs.x, rt.x), fmaf(P.ws, rs.y, rt.y));
+    float2 rte = make_float2(fmaf(P.ws, rs.x, rt.x), fmaf(P.ws, rs.y, rt.y));
+    if (P.zprev || P.znext) {   // w_z D_z' e_z: e_z of the slice below minus this slice's
+      float2 rz = make_float2(-ez[idx].x, -ez[idx].y);
+      if (P.zprev) rz = c_add(rz, ezp[idx]);
+      rte = make_float2(fmaf(P.wz, rz.x, rte.x), fmaf(P.wz, rz.y, rte.y));
+    }
     const float2 xv = P.x[idx], pv = P.p[idx], mv = m[idx];
-    const float2 mm = rtr(P, [m](int o) { return m[o]; }, q);
+    const float2 mm = rtr(P, [m](int o) { return m[o]; }, [mp](int o) { return mp[o]; },
+                          [mn](int o) { return mn[o]; }, q);
     // r = -R'e + rho (2x - p) - (rho m + R'R m)
     float2 r;
     r.x = fmaf(P.rho, 2.f * xv.x - pv.x - mv.x, -rte.x - mm.x);
@@ -235,8 +266,11 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_rhs(StvLaunch L) {
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_dir(StvLaunch L) {
-  const StvSlice& P = slice_of(L);
+  const int si = slice_of(L);
+  const StvSlice& P = L.slices[si];
   if (P.stop && *P.stop) return;
+  const StvSlice* Pp = below(L, si);
+  const StvSlice* Pn = above(L, si);
   const int j = L.step;
   const Blk b = blk_of(P);
   double beta = 0.0;
@@ -245,18 +279,25 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_dir(StvLaunch L) {
   const float2* r = P.r;
   const float2* po = P.pc[(j + 1) & 1];
   float2* pn = P.pc[j & 1];
-  auto dir = [r, po, be, j](int o) {
-    const float2 rv = r[o];
+  auto dir_of = [be, j](const float2* rr, const float2* pp, int o) {
+    const float2 rv = rr[o];
     if (j == 0) return rv;
-    const float2 pv = po[o];
+    const float2 pv = pp[o];
     return make_float2(fmaf(be, pv.x, rv.x), fmaf(be, pv.y, rv.y));
   };
+  auto dir = [&](int o) { return dir_of(r, po, o); };
+  const float2* rp = Pp ? Pp->r : r;
+  const float2* pop = Pp ? Pp->pc[(j + 1) & 1] : po;
+  const float2* rn = Pn ? Pn->r : r;
+  const float2* pon = Pn ? Pn->pc[(j + 1) & 1] : po;
+  auto dirp = [&](int o) { return dir_of(rp, pop, o); };
+  auto dirn = [&](int o) { return dir_of(rn, pon, o); };
   KSum pq;
 #pragma unroll 4
   for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
     const Pos q = pos_of(P, b, e);
     const float2 pv = dir(q.idx);
-    const float2 l = rtr(P, dir, q);
+    const float2 l = rtr(P, dir, dirp, dirn, q);
     const float2 qv = make_float2(fmaf(P.rho, pv.x, l.x), fmaf(P.rho, pv.y, l.y));
     pn[q.idx] = pv;
     P.q[q.idx] = qv;
@@ -266,7 +307,7 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_dir(StvLaunch L) {
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_update(StvLaunch L) {
-  const StvSlice& P = slice_of(L);
+  const StvSlice& P = L.slices[slice_of(L)];
   if (P.stop && *P.stop) return;
   const int j = L.step;
   const Blk b = blk_of(P);
@@ -291,15 +332,17 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_update(StvLaunch L) {
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_finish(StvLaunch L) {
-  const StvSlice& P = slice_of(L);
+  const int si = slice_of(L);
+  const StvSlice& P = L.slices[si];
   if (P.stop && *P.stop) return;
+  const StvSlice* Pn = above(L, si);
   const Blk b = blk_of(P);
 #pragma unroll 4
   for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
     const Pos q = pos_of(P, b, e);
     const int idx = q.idx;
     // e (the previous threshold's d1 - v) is read and replaced element by element
-    threshold(P, q, P.e[idx], P.e[(long long)P.n + idx], P.e[2 * (long long)P.n + idx]);
+    threshold(P, Pn, q, false);
     P.p[idx] = c_add(P.m[idx], c_sub(P.p[idx], P.x[idx]));
   }
 }
