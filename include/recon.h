@@ -106,8 +106,9 @@ typedef struct {
                        Exact: ||y - Hx||^2 by explicit FFTs after each inverse step.  16-bit storage
                        always uses the exact form. */
   int mask_full;    /* 1 = mask is [Nt][Ny][Nx] and must be constant along kx (default 0) */
-  int col_stages;   /* ring depth of the inverse kernel, rounded down to a multiple of 8
-                       (min 8) and capped by shared memory; 0 = deepest that fits (default) */
+  int col_stages;   /* ring depth of the inverse kernel, rounded down to a multiple of its consumer
+                       warp count (8 at FP32 storage, 12 at 16 bit; at least that count) and
+                       capped by shared memory; 0 = deepest that fits (default) */
   int profile;      /* 1 = time every kernel of a solve with CUDA events (default 0) */
   int frame_levels; /* levels L of RECON_PRIOR_HAAR, 1..6 (default 2); the frame has L+1 channels */
   float spatial_weight; /* w of RECON_PRIOR_STV, >= 0 (default 1) */

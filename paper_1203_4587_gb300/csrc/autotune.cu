@@ -82,7 +82,7 @@ Key key_of(const recon_plan* p) {
 
 // Candidate ring depths: multiples of the quantum up to the largest that fits.
 std::vector<int> stage_candidates(const Engine* e) {
-  const int q = col_inverse_stage_quantum();
+  const int q = col_inverse_stage_quantum(e->storage ? 4 : 8);
   const int mx = col_inverse_max_stages(e->nb_max, e->n, e->work_max, e->storage ? 4 : 8);
   std::vector<int> out;
   for (int st = q; st <= mx; st += q) out.push_back(st);

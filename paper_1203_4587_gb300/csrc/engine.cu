@@ -241,7 +241,7 @@ recon_status finish_col_shape(Engine* e, recon_plan* const* plans, int n, int st
   for (int q = 0; q < n; ++q) e->nb_max = std::max(e->nb_max, plans[q]->pk.nb);
   const int es = e->storage ? 4 : 8;
   const int maxst = col_inverse_max_stages(e->nb_max, n, e->work_max, es);
-  const int qn = col_inverse_stage_quantum();
+  const int qn = col_inverse_stage_quantum(es);
   int st = stages_req > 0 ? std::min(stages_req, maxst) : maxst;
   e->stages = std::max(qn, st / qn * qn);
   const size_t smem = col_inverse_smem(e->stages, e->nb_max, n, e->work_max, es);

@@ -12,13 +12,17 @@
 
 namespace recon {
 
-constexpr int kConsumerWarps = 8;
-constexpr int kConsumers = kConsumerWarps * 32;
+// consumer warps: 8 at FP32; 12 for the 16-bit streams, whose consumers do
+// the same arithmetic per element on half the bytes and need more warps in
+// flight to hide their latency (the smaller ring leaves the shared memory)
+__host__ __device__ constexpr int col_consumer_warps(int esize) { return esize == 8 ? 8 : 12; }
 // producer warps (one issuing thread each): 2 for 8-byte elements, 4 for
 // the half-size units of 16-bit storage (more copies per byte)
 __host__ __device__ constexpr int col_producers(int esize) { return esize == 8 ? 2 : 4; }
 // consumers + producers + r loader + column manager
-__host__ __device__ constexpr int col_threads(int esize) { return kConsumers + 32 * (col_producers(esize) + 2); }
+__host__ __device__ constexpr int col_threads(int esize) {
+  return 32 * (col_consumer_warps(esize) + col_producers(esize) + 2);
+}
 // A ring stage holds the largest unit of the storage type: kTileElems
 // elements of esize bytes (8 FP32, 4 FP16/BF16; both multiples of 16 bytes).
 __host__ __device__ constexpr int stage_bytes(int esize) { return kTileElems * esize; }
@@ -170,10 +174,6 @@ __device__ double column_fid(const float2* xcol, int i, int t, int Nx, int Ny, i
   return acc;
 }
 
-struct ConsumerBar {
-  __device__ __forceinline__ void operator()() const { named_bar_sync(1, kConsumers); }
-};
-
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 constexpr int kRSlots = 2;  // double-buffered r inputs / partial sums
@@ -223,7 +223,7 @@ __host__ __device__ inline ColLayout col_layout(int stages, int nb, int nslices,
   o = align_up(o, 128);
   L.ring = o; o += (size_t)stages * stage_bytes(esize);
   o = align_up(o, 16);
-  L.ycopy = o; o += (size_t)kRSlots * kConsumerWarps * ny32 * 8;   // [buf][warp][ny32]
+  L.ycopy = o; o += (size_t)kRSlots * col_consumer_warps(esize) * ny32 * 8;   // [buf][warp][ny32]
   L.rvec = o; o += (size_t)kRSlots * ny32 * 8;
   L.bvec = o; o += (size_t)kRSlots * ny32 * 8;
   L.rslot = o; o += (size_t)kRSlots * 3 * ny32 * 8;   // [slot][base, add, b][ny32]
@@ -240,21 +240,23 @@ __host__ __device__ inline ColLayout col_layout(int stages, int nb, int nslices,
 // Persistent column-inverse kernel over a work list of (slice, column) pairs,
 // warp-specialised and free of block-wide barriers in the main loop (all
 // hand-offs are bounded mbarrier waits):
-//   warps 8..8+P-1  producers (P = 2 at FP32, 4 at 16 bit): stream the
+//   warps 0..C-1  consumers (C = 8 at FP32, 12 at 16 bit): Hermitian matvec
+//            of each unit into their own partial y vector of buffer n&1,
+//            column after column
+//   warps C..C+P-1  producers (P = 2 at FP32, 4 at 16 bit): stream the
 //            packed inverses with the TMA engine (cp.async.bulk, L2
 //            evict_first) into a ring of S stages
-//   warp 8+P  r loader: bulk-copies each column's right-hand-side inputs
-//   warp 9+P  column manager: r = base + coef*add into rvec[n&1]; after the
-//            consumers are done, x = sum of the 8 partial y vectors, store,
-//            objective dot products, clear the partials
-//   warps 0-7 consumers: Hermitian matvec of each unit into their own
-//            partial y vector of buffer n&1, column after column
+//   warp C+P  r loader: bulk-copies each column's right-hand-side inputs
+//   warp C+P+1  column manager: r = base + coef*add into rvec[n&1]; after
+//            the consumers are done, x = sum of the C partial y vectors,
+//            store, objective dot products, clear the partials
 // Columns of slices whose stop flag is set are dropped from the work list
 // (every role reads the same snapshot of the flags).
 template <typename E>
 __global__ void __launch_bounds__(col_threads(Elem<E>::bytes), 1) k_col_inverse(ColLaunch P) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int kProducers = col_producers(Elem<E>::bytes);
+  constexpr int kConsumerWarps = col_consumer_warps(Elem<E>::bytes);
   constexpr int kStage = stage_bytes(Elem<E>::bytes);
   const ColLayout L = col_layout(P.stages, P.nb_max, P.nslices, P.work_max, Elem<E>::bytes);
   const int S = P.stages;
@@ -526,10 +528,10 @@ __global__ void __launch_bounds__(col_threads(Elem<E>::bytes), 1) k_col_inverse(
     return;
   }
 
-  // ---------------- consumers (8 warps) --------------------------------------
-  // Unit g (counted across this CTA's columns) belongs to warp g mod 8, so a
-  // warp walks g = warp, warp+8, ...: within column n that is unit index u,
-  // and its ring stage advances by 8 per unit.  With S a multiple of 8 the
+  // ---------------- consumers (C warps) --------------------------------------
+  // Unit g (counted across this CTA's columns) belongs to warp g mod C, so a
+  // warp walks g = warp, warp+C, ...: within column n that is unit index u,
+  // and its ring stage advances by C per unit.  With S a multiple of C the
   // previous fill of a stage was consumed by this same warp, so every parity
   // wait is at most one phase ahead of its barrier.  Every column's rv/yc
   // barriers are waited on (and col_done arrived at) even when the warp has
@@ -580,15 +582,16 @@ int col_inverse_max_stages(int nb_max, int nslices, int work_max, int esize) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  int s = 8 * kConsumerWarps;
-  while (s > kConsumerWarps) {
+  const int q = col_consumer_warps(esize);
+  int s = 8 * q;
+  while (s > q) {
     if (col_inverse_smem(s, nb_max, nslices, work_max, esize) + 1024 <= (size_t)optin) break;
-    s -= kConsumerWarps;
+    s -= q;
   }
   return s;
 }
 
-int col_inverse_stage_quantum() { return kConsumerWarps; }
+int col_inverse_stage_quantum(int esize) { return col_consumer_warps(esize); }
 
 template <typename E>
 static size_t& col_configured() {

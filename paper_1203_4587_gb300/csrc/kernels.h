@@ -266,7 +266,7 @@ cudaError_t launch_col_inverse(const ColLaunch& p, int storage, int grid, cudaSt
 // esize: bytes per stored element (8 FP32, 4 FP16/BF16)
 size_t col_inverse_smem(int stages, int nb_max, int nslices, int work_max, int esize);
 int col_inverse_max_stages(int nb_max, int nslices, int work_max, int esize);
-int col_inverse_stage_quantum();  // ring depth must be a positive multiple of this
+int col_inverse_stage_quantum(int esize);  // ring depth must be a positive multiple of this
 cudaError_t prepare_tv_temporal(int Nt_max, int px);   // shared-memory attribute, outside any capture
 cudaError_t prepare_dft_temporal(int Nt_max, int px);
 cudaError_t prepare_col_inverse(int storage, size_t smem);

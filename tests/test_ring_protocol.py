@@ -1,10 +1,10 @@
 """CPU model of the column-inverse kernel's mbarrier protocol (no GPU).
 
 k_col_inverse hands data between warps with mbarriers and parity waits:
-producers (units go round four issuing threads) stream units into
-a ring of S stages (full/empty barriers), a
-loader fills two r slots, a manager prepares r and reduces partial sums, and
-eight consumers walk units g = warp, warp+8, ...  A parity wait is only exact
+producers (units go round two issuing threads at FP32 storage, four at 16 bit)
+stream units into a ring of S stages (full/empty barriers), a loader fills
+two r slots, a manager prepares r and reduces partial sums, and C consumers
+(8 at FP32, 12 at 16 bit) walk units g = warp, warp+C, ...  A parity wait is only exact
 when the waiter is at most one phase ahead of the barrier.  This model runs
 the same protocol under random timings and checks that every successful wait
 is for data that has landed, that no copy is issued into a busy stage, that
@@ -168,10 +168,19 @@ def simulate(S, nunits, ncols, seed, W=8, per_column_mapping=False, producers=1)
 @pytest.mark.parametrize("S", [8, 16, 24, 32])
 @pytest.mark.parametrize("nunits", [1, 2, 3, 13, 32, 36])
 def test_protocol_holds_for_ring_depths_multiple_of_8(S, nunits, producers):
-    """The kernel runs four producers (units go round them)."""
+    """FP32 storage: 8 consumer warps, two producers (units go round them)."""
     for ncols in (1, 2, 5):
         for seed in range(3):
             simulate(S, nunits, ncols, seed, producers=producers)
+
+
+@pytest.mark.parametrize("S", [12, 24, 36])
+@pytest.mark.parametrize("nunits", [1, 5, 13, 36, 78])
+def test_protocol_holds_with_twelve_consumers(S, nunits):
+    """16-bit storage: 12 consumer warps, four producers, S a multiple of 12."""
+    for ncols in (1, 2, 5):
+        for seed in range(3):
+            simulate(S, nunits, ncols, seed, W=12, producers=4)
 
 
 def test_per_column_unit_mapping_breaks_parity_waits():
