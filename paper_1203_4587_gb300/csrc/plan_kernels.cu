@@ -200,43 +200,60 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan_inverse(const float2* 
         Tm[idx] = dc_pack(dc_neg(acc));
       }
       __syncthreads();
-      // the sweep of the block over the stored lower triangle; a thread takes
-      // columns c and c + 16 of its row, so one T(r) serves two elements and
-      // two independent chains interleave
-      for (int ib = 0; ib < n; ib += kPlanRows) {
-        const int r = ib + ty;
-        const bool rin = r >= k0 && r < k0 + bb;
-        for (int jb = 0; jb < ib + kPlanRows; jb += 32) {
-          const int c0 = jb + tx, c1 = c0 + 16;
-          const bool v0 = r < n && c0 <= r, v1 = r < n && c1 <= r;
-          const bool in0 = c0 >= k0 && c0 < k0 + bb, in1 = c1 >= k0 && c1 < k0 + bb;
-          if (v0 && v1 && !rin && !in0 && !in1) {   // M[R][R] - T(r) conj(M(c, block)), two columns
-            const size_t o0 = (size_t)r * n + c0, o1 = o0 + 16;
-            dc w0 = ldw(W, o0), w1 = ldw(W, o1);
+      // the sweep of the block over the stored lower triangle.  A thread takes
+      // rows r, r + kPlanRows and columns c, c + 16 of a 64 x 32 tile: one T
+      // load serves two columns, one panel load two rows, and four
+      // independent double-float chains interleave
+      for (int ib = 0; ib < n; ib += 2 * kPlanRows) {
+        for (int jb = 0; jb < ib + 2 * kPlanRows; jb += 32) {
+          const int rr[2] = {ib + ty, ib + ty + kPlanRows}, cc[2] = {jb + tx, jb + tx + 16};
+          // (R, R) entries get the rank-bb update; the four run together, an
+          // entry outside the triangle or in the block's rows / columns only
+          // masked (its operand rows clamped in range, its result not stored)
+          bool upd[2][2], any = false;
+#pragma unroll
+          for (int a2 = 0; a2 < 2; ++a2)
+#pragma unroll
+            for (int b2 = 0; b2 < 2; ++b2) {
+              const int r = rr[a2], c = cc[b2];
+              const bool inr = r >= k0 && r < k0 + bb, inc = c >= k0 && c < k0 + bb;
+              upd[a2][b2] = r < n && c <= r && !inr && !inc;
+              any = any || upd[a2][b2];
+            }
+          if (any) {
+            const int r0 = min(rr[0], n - 1), r1 = min(rr[1], n - 1);
+            const int c0 = min(cc[0], n - 1), c1 = min(cc[1], n - 1);
+            dc w[2][2];
+#pragma unroll
+            for (int a2 = 0; a2 < 2; ++a2)
+#pragma unroll
+              for (int b2 = 0; b2 < 2; ++b2)
+                w[a2][b2] = upd[a2][b2] ? ldw(W, (size_t)rr[a2] * n + cc[b2]) : dc_zero();
 #pragma unroll
             for (int q = 0; q < B; ++q)
               if (q < bb) {
-                const dc t = dc_unpack(Tm[(size_t)r * B + q]);
-                w0 = dc_fms_conj(w0, t, dc_unpack(pan[(size_t)c0 * B + q]));
-                w1 = dc_fms_conj(w1, t, dc_unpack(pan[(size_t)c1 * B + q]));
+                const dc t0 = dc_unpack(Tm[(size_t)r0 * B + q]), t1 = dc_unpack(Tm[(size_t)r1 * B + q]);
+                const dc p0 = dc_unpack(pan[(size_t)c0 * B + q]), p1 = dc_unpack(pan[(size_t)c1 * B + q]);
+                w[0][0] = dc_fms_conj(w[0][0], t0, p0);
+                w[0][1] = dc_fms_conj(w[0][1], t0, p1);
+                w[1][0] = dc_fms_conj(w[1][0], t1, p0);
+                w[1][1] = dc_fms_conj(w[1][1], t1, p1);
               }
-            stw(W, o0, w0);
-            stw(W, o1, w1);
-            continue;
-          }
-#pragma unroll 1
-          for (int h = 0; h < 2; ++h) {
-            const int c = h ? c1 : c0;
-            if (!(h ? v1 : v0)) continue;
-            const bool cin = h ? in1 : in0;
-            const size_t o = (size_t)r * n + c;
-            if (!rin && !cin) {          // M[R][R] - T(r) conj(M(c, block))
-              dc w = ldw(W, o);
 #pragma unroll
-              for (int q = 0; q < B; ++q)
-                if (q < bb) w = dc_fms_conj(w, dc_unpack(Tm[(size_t)r * B + q]), dc_unpack(pan[(size_t)c * B + q]));
-              stw(W, o, w);
-            } else if (!rin) {           // (r, c) with c in the block, r below it
+            for (int a2 = 0; a2 < 2; ++a2)
+#pragma unroll
+              for (int b2 = 0; b2 < 2; ++b2)
+                if (upd[a2][b2]) stw(W, (size_t)rr[a2] * n + cc[b2], w[a2][b2]);
+          }
+          // the entries of the block's rows and columns take T, its conjugate or -P^{-1}
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const int r = rr[h >> 1], c = cc[h & 1];
+            if (r >= n || c > r) continue;
+            const bool rin = r >= k0 && r < k0 + bb, cin = c >= k0 && c < k0 + bb;
+            if (!rin && !cin) continue;   // updated above
+            const size_t o = (size_t)r * n + c;
+            if (!rin) {                  // (r, c) with c in the block, r below it
               W[o] = Tm[(size_t)r * B + (c - k0)];
             } else if (!cin) {           // r in the block, c left of it: conj of (c, r)
               W[o] = dc_pack(dc_conj(dc_unpack(Tm[(size_t)c * B + (r - k0)])));
