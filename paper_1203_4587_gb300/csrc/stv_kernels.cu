@@ -315,18 +315,40 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_update(StvLaunch L) {
   const float alpha = (pq > 0.0 && gam > 0.0) ? (float)(gam / pq) : 0.f;
   const float2* pn = P.pc[j & 1];
   const int base = b.row0 * P.Ny;
+  const int ne = b.nrows * P.Ny;
   KSum g;
-  // element-wise: no neighbours, so no (t, i, j)
+  // element-wise: no neighbours, so no (t, i, j).  With Ny even the block's
+  // elements start on a 16-byte boundary and go two per access.
+  if ((P.Ny & 1) == 0) {
+    const float4* p4 = reinterpret_cast<const float4*>(pn + base);
+    const float4* q4 = reinterpret_cast<const float4*>(P.q + base);
+    float4* m4 = reinterpret_cast<float4*>(P.m + base);
+    float4* r4 = reinterpret_cast<float4*>(P.r + base);
 #pragma unroll 4
-  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
-    const int idx = base + e;
-    const float2 pv = pn[idx], qv = P.q[idx];
-    float2 mv = P.m[idx], rv = P.r[idx];
-    mv.x = fmaf(alpha, pv.x, mv.x); mv.y = fmaf(alpha, pv.y, mv.y);
-    rv.x = fmaf(-alpha, qv.x, rv.x); rv.y = fmaf(-alpha, qv.y, rv.y);
-    P.m[idx] = mv;
-    P.r[idx] = rv;
-    g.add(fmaf(rv.x, rv.x, rv.y * rv.y));
+    for (int e = threadIdx.x; e < ne / 2; e += kStvThreads) {
+      const float4 pv = p4[e], qv = q4[e];
+      float4 mv = m4[e], rv = r4[e];
+      mv.x = fmaf(alpha, pv.x, mv.x); mv.y = fmaf(alpha, pv.y, mv.y);
+      mv.z = fmaf(alpha, pv.z, mv.z); mv.w = fmaf(alpha, pv.w, mv.w);
+      rv.x = fmaf(-alpha, qv.x, rv.x); rv.y = fmaf(-alpha, qv.y, rv.y);
+      rv.z = fmaf(-alpha, qv.z, rv.z); rv.w = fmaf(-alpha, qv.w, rv.w);
+      m4[e] = mv;
+      r4[e] = rv;
+      g.add(fmaf(rv.x, rv.x, rv.y * rv.y));
+      g.add(fmaf(rv.z, rv.z, rv.w * rv.w));
+    }
+  } else {
+#pragma unroll 4
+    for (int e = threadIdx.x; e < ne; e += kStvThreads) {
+      const int idx = base + e;
+      const float2 pv = pn[idx], qv = P.q[idx];
+      float2 mv = P.m[idx], rv = P.r[idx];
+      mv.x = fmaf(alpha, pv.x, mv.x); mv.y = fmaf(alpha, pv.y, mv.y);
+      rv.x = fmaf(-alpha, qv.x, rv.x); rv.y = fmaf(-alpha, qv.y, rv.y);
+      P.m[idx] = mv;
+      P.r[idx] = rv;
+      g.add(fmaf(rv.x, rv.x, rv.y * rv.y));
+    }
   }
   slice_sum(P, (double)g.s, P.red + j + 1);
 }
