@@ -5,10 +5,14 @@
  * Reconstruction in Dynamic Parallel MRI Using Augmented Lagrangian and
  * Parallel Processing".  The library solves
  *
- *   analysis prior   (Eq. L1an_pri, R = temporal TV, Algorithm 2)
- *       min_x  lambda ||D_t x||_1 + ||y - H x||^2
- *   synthesis prior  (Eq. L1unconst, Psi = unitary temporal DFT, Algorithm 1)
- *       min_w  lambda ||w||_1 + ||y - H Psi' w||^2,   x = Psi' w
+ *   analysis prior   (Eq. L1an_pri, Algorithm 2)
+ *       min_x  lambda ||R x||_1 + ||y - H x||^2,
+ *       R = D_t (temporal TV), or R = (D_t, w D_x, w D_y) with a
+ *       conjugate-gradient m-update (RECON_PRIOR_STV; plus w_z D_z across the
+ *       slices of a 3D volume, recon_volume_create)
+ *   synthesis prior  (Eq. L1unconst, Algorithm 1)
+ *       min_w  lambda ||w||_1 + ||y - H Psi' w||^2,   x = Psi' w,
+ *       Psi = unitary temporal DFT, or an undecimated temporal Haar frame
  *
  * for Cartesian ky-t undersampled multi-coil data, y_{t,c} = M_{v,t} F_h F_v
  * (s_c . x_t) + n (Eqs. mri_csmcoill, H_1, S, F).  The data-consistency
@@ -146,18 +150,6 @@ recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc,
                                const float* sens, float lambda, float mu, recon_prior prior,
                                const recon_opts* opts, void* stream);
 
-/* Self-test of the failure path of the bounded device-side waits (no fault
- * involved): one CTA waits, through the same bounded mbarrier wait the
- * persistent kernels use, on a barrier phase that nothing completes, with a
- * wall-clock limit of limit_us microseconds (1..2000000; the kernels' own
- * limit is 2 s).  The wait gives up, records DEV_ERR_TIMEOUT in the launch's
- * error word and returns, and the call reports RECON_ERR_TIMEOUT, the status
- * a solve returns when one of its waits gives up; the CUDA context stays
- * usable.  *waited_ms (may be NULL) receives the host-measured time of the
- * launch.  Any other status means the path is broken: RECON_ERR_CUDA when the
- * wait came back without reporting, INVALID_ARG for a bad limit. */
-recon_status recon_selftest_wait_timeout(int limit_us, double* waited_ms, void* stream);
-
 /* Changes mu (mu2 of Algorithm 2) of an existing plan: recomputes every packed
  * inverse (mu I + G_{i,t})^{-1} from the plan's device-resident sensitivities
  * and row lists (Eq. eigen_mu with the new mu) and every launch descriptor
@@ -237,6 +229,18 @@ recon_status recon_get_profile(recon_plan* plan, recon_profile* out);
 
 /* Number of CUDA kernels this library has launched in this process. */
 unsigned long long recon_kernel_launches(void);
+
+/* Self-test of the failure path of the bounded device-side waits (no fault
+ * involved): one CTA waits, through the same bounded mbarrier wait the
+ * persistent kernels use, on a barrier phase that nothing completes, with a
+ * wall-clock limit of limit_us microseconds (1..2000000; the kernels' own
+ * limit is 2 s).  The wait gives up, records DEV_ERR_TIMEOUT in the launch's
+ * error word and returns, and the call reports RECON_ERR_TIMEOUT, the status
+ * a solve returns when one of its waits gives up; the CUDA context stays
+ * usable.  *waited_ms (may be NULL) receives the host-measured time of the
+ * launch.  Any other status means the path is broken: RECON_ERR_CUDA when the
+ * wait came back without reporting, INVALID_ARG for a bad limit. */
+recon_status recon_selftest_wait_timeout(int limit_us, double* waited_ms, void* stream);
 
 /* ---- batched solves --------------------------------------------------------
  * Many independent slices (plans of uneven Nx, Ny, Nt, Nc) solved together:
