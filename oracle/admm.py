@@ -38,7 +38,7 @@ __all__ = [
     "soft", "unitary_dft_matrix", "forward_op", "adjoint_op", "hybrid_data",
     "gram_blocks", "inverse_blocks", "ColumnInverse", "tv_D", "tv_Dadj",
     "tv_m_matrix", "data_residual", "data_residual_columns", "objective_tv",
-    "objective_dft", "delta_ratio", "admm_analysis_tv", "admm_synthesis_dft",
+    "objective_dft", "delta_ratio", "admm_analysis_tv", "admm_synthesis_dft", "tv_residuals",
     "psi_dft", "psi_dft_adj", "psi_haar", "psi_haar_adj", "Problem", "make_problem",
 ]
 
@@ -268,6 +268,7 @@ def admm_analysis_tv(b, inv, lam, mu, rho, iters, fid=None, tol=0.0, state=None)
     mu2 = mu
     mu1 = mu / rho
     Minv = tv_m_matrix(Nt, mu2 / mu1)
+    m_prev = None
     if state is None:
         x = b.copy()                                            # x = H'y
         m = x.copy()                                            # m = x
@@ -278,6 +279,7 @@ def admm_analysis_tv(b, inv, lam, mu, rho, iters, fid=None, tol=0.0, state=None)
     J = [objective_tv(x, lam, fid)] if fid is not None else []
     k_done = 0
     for k in range(1, iters + 1):
+        m_prev = m
         # v <- S(R m + d1, lambda / (2 mu1))
         v = soft(tv_D(m) + d1, lam / (2.0 * mu1))
         # m <- (mu2/mu1 I + R'R)^{-1} [R'(v - d1) + mu2/mu1 (x + d2)]
@@ -295,7 +297,23 @@ def admm_analysis_tv(b, inv, lam, mu, rho, iters, fid=None, tol=0.0, state=None)
                 dk = delta_ratio(J[-2], J[-1])
                 if 0.0 <= dk < tol:
                     break
-    return x, dict(J=J, iters=k_done, state=(x, m, d1, d2))
+    info = dict(J=J, iters=k_done, state=(x, m, d1, d2))
+    if m_prev is not None:
+        info["primal_res"], info["dual_res"] = tv_residuals(x, m, v, m_prev, mu1, mu2)
+    return x, info
+
+
+def tv_residuals(x, m, v, m_prev, mu1, mu2):
+    """ADMM residuals of Algorithm 2 after an iteration, in the stacked form of
+    Boyd et al. (Distributed Optimization and Statistical Learning via ADMM,
+    2011, Sec. 3.3) for its two splits, v = D_t m (penalty mu1) and m = x
+    (penalty mu2), with m the variable updated second:
+      primal = sqrt(||v - D_t m||^2 + ||m - x||^2)
+      dual   = sqrt(mu1^2 ||D_t (m - m_prev)||^2 + mu2^2 ||m - m_prev||^2)."""
+    rp = np.vdot(v - tv_D(m), v - tv_D(m)).real + np.vdot(m - x, m - x).real
+    dm = m - m_prev
+    rd = mu1 ** 2 * np.vdot(tv_D(dm), tv_D(dm)).real + mu2 ** 2 * np.vdot(dm, dm).real
+    return float(np.sqrt(rp)), float(np.sqrt(rd))
 
 
 # ---------------------------------------------------------------------------

@@ -48,7 +48,7 @@ class Opts(C.Structure):
 
 class Info(C.Structure):
     _fields_ = [("iters", C.c_int), ("J", C.c_double), ("J0", C.c_double), ("delta", C.c_double),
-                ("stopped", C.c_int)]
+                ("stopped", C.c_int), ("primal_res", C.c_double), ("dual_res", C.c_double)]
 
 
 class KSpace(C.Structure):

@@ -318,6 +318,15 @@ recon_status plan_fill_info(recon_plan* p, recon_info* info, cudaStream_t s) {
     info->J = J[iters];
     info->J0 = J[0];
     info->delta = (iters >= 1) ? (J[iters - 1] - J[iters]) / J[iters] : NAN;
+    // ADMM residuals (temporal TV, a solve that ran all K iterations)
+    info->primal_res = info->dual_res = NAN;
+    if (p->prior == RECON_PRIOR_TV && K >= 1 && !fl[FLAG_STOP]) {
+      double a[4];
+      RC(cudaMemcpy(a, p->res_acc, sizeof(a), cudaMemcpyDeviceToHost));
+      const double mu2 = p->mu, mu1 = p->mu / p->opts.rho;
+      info->primal_res = std::sqrt(a[0] + a[1]);
+      info->dual_res = std::sqrt(mu1 * mu1 * a[3] + mu2 * mu2 * a[2]);
+    }
   }
   if (fl[FLAG_ERR] & DEV_ERR_TIMEOUT) return fail(RECON_ERR_TIMEOUT, "a bounded device-side wait timed out");
   if (fl[FLAG_ERR] & DEV_ERR_NONFINITE) return fail(RECON_ERR_NONFINITE, "non-finite objective value");
@@ -462,6 +471,7 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
   PC(p->alloc((void**)&p->trace_J, nt * sizeof(double)));
   PC(p->alloc((void**)&p->flags, FLAG_COUNT * sizeof(int)));
   PC(p->alloc((void**)&p->yy, sizeof(double)));
+  PC(p->alloc((void**)&p->res_acc, 4 * sizeof(double)));
 
   // tables
   std::vector<float2> tw(std::max(std::max(Nxf, Ny), Nt));

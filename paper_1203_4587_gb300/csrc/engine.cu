@@ -563,6 +563,8 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
     if ((st = launch_tmp_set(e, K, s)) != RECON_OK) return st;
     RC(launch_finalize(e->d_fin, e->n, K, s));
   }
+  for (recon_plan* p : e->plans)
+    if ((st = launch_tv_residuals(p, s)) != RECON_OK) return st;
   return RECON_OK;
 }
 

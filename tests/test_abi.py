@@ -90,13 +90,14 @@ def test_invalid_arguments_rejected_before_any_cuda_call(libpath):
     assert lib.recon_status_string(2) == b"RECON_ERR_MASK_NOT_CARTESIAN"
 
 
-def test_opts_struct_matches_header():
-    """binding.Opts lists recon_opts' fields in the header's order and types."""
+@pytest.mark.parametrize("name,cls", [("recon_opts", "Opts"), ("recon_info", "Info")])
+def test_struct_matches_header(name, cls):
+    """The binding's ctypes structs list the header's fields in order and type."""
     import re
     from paper_1203_4587_gb300 import binding
     text = open(os.path.join(ROOT, "include", "recon.h")).read()
-    body = re.search(r"typedef struct \{(.*?)\} recon_opts;", text, re.S).group(1)
+    body = re.search(r"typedef struct \{((?:(?!typedef struct).)*?)\} " + name + ";", text, re.S).group(1)
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = re.findall(r"\b(float|int|double)\s+(\w+)\s*;", body)
     ctype = {"float": C.c_float, "int": C.c_int, "double": C.c_double}
-    assert [(n, ctype[t]) for t, n in fields] == list(binding.Opts._fields_)
+    assert [(n, ctype[t]) for t, n in fields] == list(getattr(binding, cls)._fields_)

@@ -1,0 +1,73 @@
+"""GPU parity of the ADMM residuals recon_info reports for Algorithm 2
+(temporal TV): primal sqrt(||v - D_t m||^2 + ||m - x||^2) and dual
+sqrt(mu1^2 ||D_t dm||^2 + mu2^2 ||dm||^2), dm = m_K - m_{K-1}, against the FP64
+oracle (oracle.tv_residuals on its own iterates).
+
+Bound: the GPU state matches the oracle's to 1e-5 relative (the parity bar),
+and each residual is a norm of differences of state fields, so it may differ
+by a few times 1e-5 of the fields' norms: |r - r_ref| <= 4e-5 (||x|| + ||m||) +
+1e-4 r_ref.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synthdata
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def gpu(x):
+    return torch.from_numpy(np.asarray(x, dtype=np.complex64)).cuda()
+
+
+def case64(name="tiny", **over):
+    c = synthdata.make_case(name, **over)
+    c.kspace = np.asarray(c.kspace, dtype=np.complex64).astype(np.complex128)
+    c.sens = np.asarray(c.sens, dtype=np.complex64).astype(np.complex128)
+    return c
+
+
+def check(info, oinfo, xr, mu):
+    _, m, _, _ = oinfo["state"]
+    scale = np.linalg.norm(xr) + np.linalg.norm(m)
+    for got, ref, w in ((info.primal_res, oinfo["primal_res"], 1.0), (info.dual_res, oinfo["dual_res"], mu)):
+        assert np.isfinite(got)
+        assert abs(got - ref) <= 4e-5 * w * 4 * scale + 1e-4 * ref, (got, ref)
+
+
+@pytest.mark.parametrize("iters", [1, 2, 50])
+def test_tv_residuals_match_oracle(iters):
+    from paper_1203_4587_gb300 import Plan
+    c = case64("tiny")
+    P = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="tv", rho=c.rho, max_iters=iters)
+    _, info = P.solve(gpu(c.kspace))
+    prob = oracle.Problem(c.kspace, c.sens, c.mask, c.mu)
+    xr, oinfo = prob.solve("tv", c.lam, c.mu, c.rho, iters, objective=False)
+    check(info, oinfo, xr, c.mu / c.rho)
+
+
+def test_batched_tv_residuals_per_slice():
+    from paper_1203_4587_gb300 import Batch, Plan
+    cases = [case64("tiny", Nx=24, Ny=32, Nt=4, Nc=2, seed=81), case64("tiny", Nx=40, Ny=48, Nt=6, Nc=3, seed=82)]
+    plans = [Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="tv", rho=c.rho, max_iters=10)
+             for c in cases]
+    b = Batch(plans)
+    b.solve([gpu(c.kspace) for c in cases])
+    for c, info in zip(cases, b.info()):
+        prob = oracle.Problem(c.kspace, c.sens, c.mask, c.mu)
+        xr, oinfo = prob.solve("tv", c.lam, c.mu, c.rho, 10, objective=False)
+        check(info, oinfo, xr, c.mu / c.rho)
+
+
+def test_residuals_nan_where_not_defined():
+    from paper_1203_4587_gb300 import Plan
+    c = case64("tiny", Nx=24, Ny=32, Nt=4, Nc=2, seed=83)
+    P = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="dft", max_iters=5)
+    _, info = P.solve(gpu(c.kspace))
+    assert np.isnan(info.primal_res) and np.isnan(info.dual_res)
+    Q = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="tv", rho=c.rho, max_iters=200, tol=1e-2)
+    _, info = Q.solve(gpu(c.kspace))
+    assert info.stopped == 1 and np.isnan(info.primal_res) and np.isnan(info.dual_res)

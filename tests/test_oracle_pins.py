@@ -395,3 +395,22 @@ def test_synthdata_structure():
     assert case.mask[:, central].all()
     assert np.all(case.kspace[~np.broadcast_to(case.mask[:, None, :, None], case.kspace.shape)] == 0)
     assert len({tuple(np.nonzero(case.mask[t])[0]) for t in range(Nt)}) > 1
+
+
+def test_tv_residuals_vanish_at_convergence_and_follow_the_duals():
+    """Algorithm 2's residuals: v - D_t m equals d1_prev - d1 (the d1-update), both
+    residuals shrink to ~0 at the ADMM fixed point, and they are positive early on."""
+    x, sens, mask, y = _small_case(Nx=4, Ny=4, Nt=4, Nc=2, R=2, noise=0.05, seed=19)
+    lam, mu, rho = 0.05, 0.1, 0.5
+    P = oracle.Problem(y, sens, mask, mu)
+    _, early = oracle.admm_analysis_tv(P.b, P.inv, lam, mu, rho, 3)
+    assert early["primal_res"] > 1e-6 and early["dual_res"] > 1e-6
+    # the v - D_t m part equals the change of d1 in the last iteration
+    _, i4 = oracle.admm_analysis_tv(P.b, P.inv, lam, mu, rho, 4)
+    _, i5 = oracle.admm_analysis_tv(P.b, P.inv, lam, mu, rho, 5)
+    x5, m5, d1_5, _ = i5["state"]
+    d1_4 = i4["state"][2]
+    part = np.sqrt(np.vdot(d1_4 - d1_5, d1_4 - d1_5).real + np.vdot(m5 - x5, m5 - x5).real)
+    assert abs(part - i5["primal_res"]) <= 1e-12 * max(part, 1e-30)
+    _, late = oracle.admm_analysis_tv(P.b, P.inv, lam, mu, rho, 3000)
+    assert late["primal_res"] < 1e-8 and late["dual_res"] < 1e-8
