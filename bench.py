@@ -634,7 +634,8 @@ def run_native(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_obj(args.prior, args.storage), "roofline": roofline, "clocks": clocks,
             "gpu_launches": launches, "plan_s": plan_s, "set_mu_s": set_mu_s, "tuning": tuning,
-            "check": {"iters": info.iters, "J0": info.J0, "J": info.J}}
+            "check": {"iters": info.iters, "J0": info.J0, "J": info.J, "primal_res": info.primal_res,
+                      "dual_res": info.dual_res}}
 
     # end to end through the public API with host buffers
     if not args.no_e2e:
