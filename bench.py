@@ -41,6 +41,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -79,6 +80,17 @@ def parse():
     ap.add_argument("--grad-only", action="store_true",
                     help="only the differentiable-form measurement (one JSON line with its numbers)")
     return ap.parse_args()
+
+
+def finite_json(v):
+    """The line with every non-finite float replaced by null (strict JSON has no NaN)."""
+    if isinstance(v, float):
+        return v if math.isfinite(v) else None
+    if isinstance(v, dict):
+        return {k: finite_json(x) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [finite_json(x) for x in v]
+    return v
 
 
 def reduce_max(x, dist, device):
@@ -542,7 +554,7 @@ def run_reference(args):
             "cpu_baseline": cpu_baseline_obj(last, args.prior) | {"value": value},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t_start}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(finite_json(line)), flush=True)
     return 0
 
 
@@ -731,7 +743,7 @@ def run_native(args):
         except Exception as e:  # report, never fake
             line["cpu_baseline_all_cores"] = {"error": str(e)[:300]}
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(finite_json(line)), flush=True)
     plan.close()
     if dist is not None:
         dist.destroy_process_group()
