@@ -9,6 +9,7 @@
 // FP32 (Kahan) and across threads in FP64.
 #include <algorithm>
 
+#include "kahan.cuh"
 #include "plan.h"
 
 namespace recon {
@@ -16,16 +17,6 @@ namespace recon {
 namespace {
 
 constexpr int kResThreads = 256;
-
-struct KahanF {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float y) {
-    const float t = y - c;
-    const float u = s + t;
-    c = (u - s) - t;
-    s = u;
-  }
-};
 
 // acc[0] += ||m - x||^2, acc[1] += ||d1p - d1||^2, acc[2] += ||dm||^2,
 // acc[3] += ||D_t dm||^2 (dm = m - mp); fields [Nt][npix], d1 [Nt-1][npix]
@@ -36,7 +27,7 @@ __global__ void __launch_bounds__(kResThreads) k_tv_residuals(const float2* __re
                                                               double* acc) {
   __shared__ double red[32];
   const long long n = npix * Nt;
-  KahanF a0, a1, a2, a3;
+  KahanSum a0, a1, a2, a3;
   for (long long idx = (long long)blockIdx.x * kResThreads + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * kResThreads) {
     const float2 mv = m[idx], xv = x[idx], pv = mp[idx];

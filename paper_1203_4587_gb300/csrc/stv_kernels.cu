@@ -43,6 +43,7 @@
 // order, so results do not depend on scheduling.  alpha and beta are formed
 // in FP64 from those sums.  (GB300's FP64 pipe runs at 1/64 of FP32: FP64
 // products per element would cost more than the memory traffic.)
+#include "kahan.cuh"
 #include "kernels.h"
 
 namespace recon {
@@ -161,17 +162,6 @@ __device__ void slice_sum(const StvSlice& P, double v, double* slot) {
   }
 }
 
-// Kahan's compensated sum of FP32 terms
-struct KSum {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float y) {
-    const float t = y - c;
-    const float u = s + t;
-    c = (u - s) - t;
-    s = u;
-  }
-};
-
 __device__ __forceinline__ float rx_l1(const StvSlice& P, const StvSlice* Pn, const Pos& q) {
   float2 d[4];
   diffs(P, P.x, Pn ? Pn->x : nullptr, q, d);
@@ -209,7 +199,7 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_prior(StvLaunch L) {
   if (P.stop && *P.stop) return;
   const StvSlice* Pn = above(L, si);
   const Blk b = blk_of(P);
-  KSum l1;
+  KahanSum l1;
 #pragma unroll 4
   for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) l1.add(rx_l1(P, Pn, pos_of(P, b, e)));
   const double s = group_sum((double)l1.s, red, threadIdx.x, kStvThreads, BlockBar());
@@ -233,7 +223,7 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_rhs(StvLaunch L) {
   const float2* mn = Pn ? Pn->m : m;
   const float2* ez = P.e + 3 * (long long)P.n;
   const float2* ezp = Pp ? Pp->e + 3 * (long long)Pp->n : ez;
-  KSum g, l1;
+  KahanSum g, l1;
 #pragma unroll 4
   for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
     const Pos q = pos_of(P, b, e);
@@ -292,7 +282,7 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_dir(StvLaunch L) {
   const float2* pon = Pn ? Pn->pc[(j + 1) & 1] : po;
   auto dirp = [&](int o) { return dir_of(rp, pop, o); };
   auto dirn = [&](int o) { return dir_of(rn, pon, o); };
-  KSum pq;
+  KahanSum pq;
 #pragma unroll 4
   for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
     const Pos q = pos_of(P, b, e);
@@ -316,7 +306,7 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_update(StvLaunch L) {
   const float2* pn = P.pc[j & 1];
   const int base = b.row0 * P.Ny;
   const int ne = b.nrows * P.Ny;
-  KSum g;
+  KahanSum g;
   // element-wise: no neighbours, so no (t, i, j).  With Ny even the block's
   // elements start on a 16-byte boundary and go two per access.
   if ((P.Ny & 1) == 0) {
