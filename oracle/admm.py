@@ -39,6 +39,7 @@ __all__ = [
     "gram_blocks", "inverse_blocks", "ColumnInverse", "tv_D", "tv_Dadj",
     "tv_m_matrix", "data_residual", "data_residual_columns", "objective_tv",
     "objective_dft", "delta_ratio", "admm_analysis_tv", "admm_synthesis_dft", "tv_residuals",
+    "synthesis_residuals",
     "psi_dft", "psi_dft_adj", "psi_haar", "psi_haar_adj", "Problem", "make_problem",
 ]
 
@@ -334,7 +335,9 @@ def admm_synthesis_dft(b, inv, lam, mu, iters, fid=None, tol=0.0, state=None,
         w, d = (np.array(a, dtype=np.complex128) for a in state)
     J = [lam * float(np.abs(w).sum()) + fid(psi_adj(w))] if fid is not None else []
     k_done = 0
+    w_prev = v = None
     for k in range(1, iters + 1):
+        w_prev = w
         # v <- S(w - d, lambda / (2 mu))
         v = soft(w - d, lam / (2.0 * mu))
         # w <- (1/mu)(I - Psi Psi')[Psi H'y + mu(v + d)]
@@ -350,7 +353,22 @@ def admm_synthesis_dft(b, inv, lam, mu, iters, fid=None, tol=0.0, state=None,
                 dk = delta_ratio(J[-2], J[-1])
                 if 0.0 <= dk < tol:
                     break
-    return psi_adj(w), dict(J=J, iters=k_done, state=(w, d))
+    info = dict(J=J, iters=k_done, state=(w, d))
+    if w_prev is not None:
+        info["primal_res"], info["dual_res"] = synthesis_residuals(w, v, w_prev, mu)
+    return psi_adj(w), info
+
+
+def synthesis_residuals(w, v, w_prev, mu):
+    """ADMM residuals of Algorithm 1 after an iteration (Boyd et al. 2011,
+    Sec. 3.3) for its one split v = w (penalty mu), w the variable updated
+    second:
+      primal = ||w - v||,   dual = mu ||w - w_prev||.
+    As for Algorithm 2, the paper's penalty weight mu stands where Boyd's
+    scaled form has rho/2."""
+    rp = np.vdot(w - v, w - v).real
+    dw = w - w_prev
+    return float(np.sqrt(rp)), float(mu * np.sqrt(np.vdot(dw, dw).real))
 
 
 # ---------------------------------------------------------------------------

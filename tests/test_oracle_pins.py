@@ -414,3 +414,31 @@ def test_tv_residuals_vanish_at_convergence_and_follow_the_duals():
     assert abs(part - i5["primal_res"]) <= 1e-12 * max(part, 1e-30)
     _, late = oracle.admm_analysis_tv(P.b, P.inv, lam, mu, rho, 3000)
     assert late["primal_res"] < 1e-8 and late["dual_res"] < 1e-8
+
+
+@pytest.mark.parametrize("prior", ["dft", "haar"])
+def test_synthesis_residuals_vanish_at_convergence_and_follow_the_dual(prior):
+    """Algorithm 1's residuals: w - v equals d_prev - d (the d-update), both shrink
+    to ~0 at the ADMM fixed point and are positive early on; for the unitary DFT
+    the dual mu ||w - w_prev|| equals mu ||x - x_prev|| in the image domain
+    (Parseval), the form a GPU path can evaluate without the coefficients."""
+    x, sens, mask, y = _small_case(Nx=4, Ny=4, Nt=4, Nc=2, R=2, noise=0.05, seed=21)
+    lam, mu = 0.05, 0.1
+    P = oracle.Problem(y, sens, mask, mu)
+    kw = {} if prior == "dft" else dict(psi=lambda a: oracle.psi_haar(a, 1), psi_adj=lambda a: oracle.psi_haar_adj(a, 1))
+    _, early = oracle.admm_synthesis_dft(P.b, P.inv, lam, mu, 3, **kw)
+    assert early["primal_res"] > 1e-6 and early["dual_res"] > 1e-6
+    x4, i4 = oracle.admm_synthesis_dft(P.b, P.inv, lam, mu, 4, **kw)
+    x5, i5 = oracle.admm_synthesis_dft(P.b, P.inv, lam, mu, 5, **kw)
+    (w4, d4), (w5, d5) = i4["state"], i5["state"]
+    assert abs(np.linalg.norm(d4 - d5) - i5["primal_res"]) <= 1e-12 * i5["primal_res"]
+    assert abs(mu * np.linalg.norm(w5 - w4) - i5["dual_res"]) <= 1e-12 * i5["dual_res"]
+    if prior == "dft":
+        assert abs(mu * np.linalg.norm(x5 - x4) - i5["dual_res"]) <= 1e-10 * i5["dual_res"]
+    # one iteration: w_0 = Psi H'y, d_0 = 0, so the primal is ||w_1 - v_1|| = ||d_1||
+    _, i1 = oracle.admm_synthesis_dft(P.b, P.inv, lam, mu, 1, **kw)
+    assert abs(np.linalg.norm(i1["state"][1]) - i1["primal_res"]) <= 1e-12 * i1["primal_res"]
+    # the redundant Haar frame converges far more slowly than the unitary DFT
+    _, late = oracle.admm_synthesis_dft(P.b, P.inv, lam, mu, 3000 if prior == "dft" else 12000, **kw)
+    for key in ("primal_res", "dual_res"):
+        assert late[key] < (1e-8 if prior == "dft" else 1e-4 * early[key])
