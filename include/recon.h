@@ -125,11 +125,14 @@ typedef struct {
   double J0;        /* J(0) at the initial point x = H'y */
   double delta;     /* Delta(iters) = (J(iters-1) - J(iters)) / J(iters), NaN if undefined */
   int stopped;      /* 1 when the tolerance test ended the run */
-  double primal_res; /* RECON_PRIOR_TV, a solve of all K iterations: ADMM residuals of the last
-                        iteration for the splits v = D_t m (mu1) and m = x (mu2), stacked as in
-                        Boyd et al. 2011, Sec. 3.3: sqrt(||v - D_t m||^2 + ||m - x||^2) */
-  double dual_res;  /* likewise sqrt(mu1^2 ||D_t (m_K - m_{K-1})||^2 + mu2^2 ||m_K - m_{K-1}||^2);
-                        both NaN for other priors and after an early stop.  Summed in FP64. */
+  double primal_res; /* ADMM residuals of the last iteration of a solve of all K iterations
+                        (Boyd et al. 2011, Sec. 3.3, the paper's penalty weights).
+                        RECON_PRIOR_TV, splits v = D_t m (mu1) and m = x (mu2), stacked:
+                        sqrt(||v - D_t m||^2 + ||m - x||^2).
+                        RECON_PRIOR_DFT, split v = w (mu): ||w - v|| (coefficients w = Psi x) */
+  double dual_res;  /* TV: sqrt(mu1^2 ||D_t (m_K - m_{K-1})||^2 + mu2^2 ||m_K - m_{K-1}||^2);
+                        DFT: mu ||w_K - w_{K-1}||.  Both NaN for the other priors and after an
+                        early stop.  Summed in FP64. */
 } recon_info;
 
 /* Fills `opts` with the defaults listed above.  NULL-safe. */

@@ -552,6 +552,9 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
     if (st != RECON_OK) return st;
     if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, false, s);
     if (e->obj) RC(launch_finalize(e->d_fin, e->n, k - 1, s));
+    if (k == K && K >= 2 && e->prior == RECON_PRIOR_DFT)   // xhat_{K-1} for the residuals
+      for (recon_plan* p : e->plans)
+        RC(cudaMemcpyAsync(p->res_prev, p->x, p->nimg() * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     if (prof) p0->mark(p0->ev_col, p0->n_col, true, s);
     if ((st = launch_col_set(e, k - 1, s)) != RECON_OK) return st;
     if (prof) p0->mark(p0->ev_col, p0->n_col, false, s);
@@ -564,7 +567,7 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
     RC(launch_finalize(e->d_fin, e->n, K, s));
   }
   for (recon_plan* p : e->plans)
-    if ((st = launch_tv_residuals(p, s)) != RECON_OK) return st;
+    if ((st = launch_residuals(p, s)) != RECON_OK) return st;
   return RECON_OK;
 }
 

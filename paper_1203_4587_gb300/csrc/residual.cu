@@ -1,14 +1,30 @@
-// ADMM residuals of Algorithm 2 (temporal TV) at the end of a solve, for
-// recon_info: with the two splits v = D_t m (penalty mu1, scaled dual d1) and
-// m = x (mu2, d2), in the stacked form of Boyd et al. (2011, Sec. 3.3),
+// ADMM residuals at the end of a solve, for recon_info, in the stacked form of
+// Boyd et al. (2011, Sec. 3.3) with the paper's penalty weights.
+//
+// Algorithm 2 (temporal TV), splits v = D_t m (mu1, scaled dual d1) and m = x
+// (mu2, d2):
 //   primal = sqrt(||v_K - D_t m_K||^2 + ||m_K - x_K||^2)
 //   dual   = sqrt(mu1^2 ||D_t (m_K - m_{K-1})||^2 + mu2^2 ||m_K - m_{K-1}||^2),
 // where v_K - D_t m_K = d1_{K-1} - d1_K (the d1-update).  After K iterations
 // the ping-pong state buffers still hold m_K, m_{K-1}, d1_K and d1_{K-1}, so one
-// pass over them gives the four sums; products are FP32, summed per thread in
-// FP32 (Kahan) and across threads in FP64.
+// pass over them gives the four sums.
+//
+// Algorithm 1 (Psi = unitary temporal DFT), split v = w (mu, scaled dual d):
+//   primal = ||w_K - v_K||,   dual = mu ||w_K - w_{K-1}||.
+// The temporal step stores u = v + d (the coefficients it hands to the
+// synthesis) and the inverse step xhat = Psi' w.  With d_{K-1} = u_{K-1} -
+// w_{K-1} and v_K = u_K - d_{K-1},
+//   w_K - v_K = Psi (xhat_K - xhat_{K-1}) - (u_K - u_{K-1})   (K >= 2),
+//   w_1 - v_1 = Psi xhat_1 - u_1                               (d_0 = 0),
+// and ||w_K - w_{K-1}|| = ||xhat_K - xhat_{K-1}|| as Psi is unitary (xhat_0 =
+// H'y).  u_K and u_{K-1} are the two ping-pong buffers; the solve copies
+// xhat_{K-1} aside before the last inverse step overwrites it.
+//
+// Products are FP32, summed per thread in FP32 (Kahan) and across threads in
+// FP64.
 #include <algorithm>
 
+#include "fft.cuh"
 #include "kahan.cuh"
 #include "plan.h"
 
@@ -17,6 +33,7 @@ namespace recon {
 namespace {
 
 constexpr int kResThreads = 256;
+constexpr int kMaxResNt = 128;   // the plans' Nt limit; 2 kMaxResNt kResPix complex64 = 32 KB of shared memory
 
 // acc[0] += ||m - x||^2, acc[1] += ||d1p - d1||^2, acc[2] += ||dm||^2,
 // acc[3] += ||D_t dm||^2 (dm = m - mp); fields [Nt][npix], d1 [Nt-1][npix]
@@ -55,22 +72,88 @@ __global__ void __launch_bounds__(kResThreads) k_tv_residuals(const float2* __re
   }
 }
 
+// acc[0] += ||w_K - v_K||^2, acc[1] += ||xhat_K - xhat_{K-1}||^2 for kResPix
+// pixels per block: the difference tile [Nt][kResPix] is transformed along t
+// in shared memory by the same Stockham stages as the temporal step.
+// xh_prev null: K = 1 (the primal transforms xhat_1 itself, u_prev = 0, and
+// the dual compares with b = H'y).
+constexpr int kResPix = 16;
+
+__global__ void __launch_bounds__(kResThreads) k_dft_residuals(const float2* __restrict__ xh,
+                                                               const float2* __restrict__ xh_prev,
+                                                               const float2* __restrict__ b, const float2* __restrict__ u,
+                                                               const float2* __restrict__ u_prev, long long npix, int Nt,
+                                                               FftPlanDev ft, double* acc) {
+  extern __shared__ float2 sm_res[];
+  __shared__ double red[32];
+  float2* A = sm_res;
+  float2* B = sm_res + (size_t)Nt * kResPix;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const long long pix0 = (long long)blockIdx.x * kResPix;
+  const int npx = (int)min((long long)kResPix, npix - pix0);
+  KahanSum ad, ap;
+  for (int idx = tid; idx < Nt * kResPix; idx += nth) {
+    const int t = idx / kResPix, pp = idx - t * kResPix;
+    float2 a = make_float2(0.f, 0.f);
+    if (pp < npx) {
+      const long long g = (long long)t * npix + pix0 + pp;
+      const float2 xv = xh[g];
+      const float2 dx = c_sub(xv, xh_prev ? xh_prev[g] : b[g]);
+      ad.add(fmaf(dx.x, dx.x, dx.y * dx.y));
+      a = xh_prev ? dx : xv;
+    }
+    A[idx] = a;
+  }
+  __syncthreads();
+  const BlockBar bar;
+  const float2* W = fft_run(A, B, kResPix, 1, kResPix, ft, false, tid, nth, bar);
+  const float sc = rsqrtf((float)Nt);
+  for (int idx = tid; idx < Nt * kResPix; idx += nth) {
+    const int t = idx / kResPix, pp = idx - t * kResPix;
+    if (pp < npx) {
+      const long long g = (long long)t * npix + pix0 + pp;
+      const float2 du = u_prev ? c_sub(u[g], u_prev[g]) : u[g];
+      const float2 e = c_sub(c_scale(W[idx], sc), du);
+      ap.add(fmaf(e.x, e.x, e.y * e.y));
+    }
+  }
+  const double s0 = group_sum((double)ap.s, red, tid, nth, bar);
+  const double s1 = group_sum((double)ad.s, red, tid, nth, bar);
+  if (tid == 0) {
+    atomicAdd(acc + 0, s0);
+    atomicAdd(acc + 1, s1);
+  }
+}
+
 }  // namespace
 
-// The sums of plan p after its K iterations (temporal TV only): the state of
-// iteration K sits at index K & 1 of the ping-pong buffers, that of K-1 at
-// (K-1) & 1 (m_0 = H'y and d1_0 = 0 for K = 1).
-recon_status launch_tv_residuals(recon_plan* p, cudaStream_t s) {
+// The sums of plan p after its K iterations.  TV: the state of iteration K
+// sits at index K & 1 of the ping-pong buffers, that of K-1 at (K-1) & 1 (m_0 =
+// H'y and d1_0 = 0 for K = 1).  DFT: u_K at K & 1, u_{K-1} at (K-1) & 1,
+// xhat_{K-1} in res_prev (K >= 2).  Other priors: nothing (NaN in recon_info).
+recon_status launch_residuals(recon_plan* p, cudaStream_t s) {
   const int K = p->opts.max_iters;
-  if (p->prior != RECON_PRIOR_TV || K < 1) return RECON_OK;
-  RC(cudaMemsetAsync(p->res_acc, 0, 4 * sizeof(double), s));
+  if (K < 1) return RECON_OK;
   const long long npix = (long long)p->npix();
   const long long n = npix * p->Nt;
-  const float2* mp = K == 1 ? p->b : p->s0[(K - 1) & 1];
-  const float2* d1p = K == 1 ? nullptr : p->s1[(K - 1) & 1];
-  const int grid = (int)std::max<long long>(1, std::min<long long>((n + kResThreads - 1) / kResThreads,
-                                                                   4LL * std::max(1, p->num_sms)));
-  k_tv_residuals<<<grid, kResThreads, 0, s>>>(p->x, p->s0[K & 1], mp, p->s1[K & 1], d1p, npix, p->Nt, p->res_acc);
+  if (p->prior == RECON_PRIOR_TV) {
+    RC(cudaMemsetAsync(p->res_acc, 0, 4 * sizeof(double), s));
+    const float2* mp = K == 1 ? p->b : p->s0[(K - 1) & 1];
+    const float2* d1p = K == 1 ? nullptr : p->s1[(K - 1) & 1];
+    const int grid = (int)std::max<long long>(1, std::min<long long>((n + kResThreads - 1) / kResThreads,
+                                                                     4LL * std::max(1, p->num_sms)));
+    k_tv_residuals<<<grid, kResThreads, 0, s>>>(p->x, p->s0[K & 1], mp, p->s1[K & 1], d1p, npix, p->Nt, p->res_acc);
+  } else if (p->prior == RECON_PRIOR_DFT) {
+    if (p->Nt > kMaxResNt) return fail(RECON_ERR_INVALID_ARG, "residuals: Nt above the residual kernel's tile");
+    RC(cudaMemsetAsync(p->res_acc, 0, 4 * sizeof(double), s));
+    const int grid = (int)((npix + kResPix - 1) / kResPix);
+    const size_t smem = 2 * (size_t)p->Nt * kResPix * sizeof(float2);
+    k_dft_residuals<<<grid, kResThreads, smem, s>>>(p->x, K == 1 ? nullptr : p->res_prev, p->b, p->s0[K & 1],
+                                                   K == 1 ? nullptr : p->s0[(K - 1) & 1], npix, p->Nt, p->ft,
+                                                   p->res_acc);
+  } else {
+    return RECON_OK;
+  }
   note_launch();
   RC(cudaGetLastError());
   return RECON_OK;

@@ -1,12 +1,15 @@
-"""GPU parity of the ADMM residuals recon_info reports for Algorithm 2
-(temporal TV): primal sqrt(||v - D_t m||^2 + ||m - x||^2) and dual
-sqrt(mu1^2 ||D_t dm||^2 + mu2^2 ||dm||^2), dm = m_K - m_{K-1}, against the FP64
-oracle (oracle.tv_residuals on its own iterates).
+"""GPU parity of the ADMM residuals recon_info reports, against the FP64 oracle
+on its own iterates.
+
+Algorithm 2 (temporal TV, oracle.tv_residuals): primal sqrt(||v - D_t m||^2 +
+||m - x||^2) and dual sqrt(mu1^2 ||D_t dm||^2 + mu2^2 ||dm||^2), dm = m_K -
+m_{K-1}.  Algorithm 1 (temporal DFT, oracle.synthesis_residuals): primal
+||w - v|| and dual mu ||w_K - w_{K-1}||.
 
 Bound: the GPU state matches the oracle's to 1e-5 relative (the parity bar),
 and each residual is a norm of differences of state fields, so it may differ
-by a few times 1e-5 of the fields' norms: |r - r_ref| <= 4e-5 (||x|| + ||m||) +
-1e-4 r_ref.
+by a few times 1e-5 of the fields' norms: |r - r_ref| <= 4e-5 (sum of the
+fields' norms) + 1e-4 r_ref, the field term scaled by the residual's weight.
 """
 
 import numpy as np
@@ -62,12 +65,46 @@ def test_batched_tv_residuals_per_slice():
         check(info, oinfo, xr, c.mu / c.rho)
 
 
+def check_dft(info, oinfo, xr, mu):
+    w, d = oinfo["state"]
+    scale = np.linalg.norm(xr) + np.linalg.norm(w) + np.linalg.norm(d)
+    for got, ref, wt in ((info.primal_res, oinfo["primal_res"], 1.0), (info.dual_res, oinfo["dual_res"], mu)):
+        assert np.isfinite(got)
+        assert abs(got - ref) <= 4e-5 * wt * 4 * scale + 1e-4 * ref, (got, ref)
+
+
+@pytest.mark.parametrize("iters", [1, 2, 30])
+def test_dft_residuals_match_oracle(iters):
+    from paper_1203_4587_gb300 import Plan
+    c = case64("tiny")
+    P = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="dft", max_iters=iters)
+    _, info = P.solve(gpu(c.kspace))
+    prob = oracle.Problem(c.kspace, c.sens, c.mask, c.mu)
+    xr, oinfo = prob.solve("dft", c.lam, c.mu, iters=iters, objective=False)
+    check_dft(info, oinfo, xr, c.mu)
+
+
+def test_batched_dft_residuals_per_slice_and_odd_frames():
+    """Slices of different sizes in one launch, Nt = 5 and 6 (radix-5 and mixed
+    stages), and a pixel count that is not a multiple of the 16-pixel tile."""
+    from paper_1203_4587_gb300 import Batch, Plan
+    cases = [case64("tiny", Nx=24, Ny=33, Nt=5, Nc=2, seed=84), case64("tiny", Nx=40, Ny=48, Nt=6, Nc=3, seed=85)]
+    plans = [Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="dft", max_iters=7) for c in cases]
+    b = Batch(plans)
+    b.solve([gpu(c.kspace) for c in cases])
+    for c, info in zip(cases, b.info()):
+        prob = oracle.Problem(c.kspace, c.sens, c.mask, c.mu)
+        xr, oinfo = prob.solve("dft", c.lam, c.mu, iters=7, objective=False)
+        check_dft(info, oinfo, xr, c.mu)
+
+
 def test_residuals_nan_where_not_defined():
     from paper_1203_4587_gb300 import Plan
     c = case64("tiny", Nx=24, Ny=32, Nt=4, Nc=2, seed=83)
-    P = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="dft", max_iters=5)
-    _, info = P.solve(gpu(c.kspace))
-    assert np.isnan(info.primal_res) and np.isnan(info.dual_res)
+    for prior in ("haar", "stv"):
+        P = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior=prior, max_iters=5)
+        _, info = P.solve(gpu(c.kspace))
+        assert np.isnan(info.primal_res) and np.isnan(info.dual_res)
     Q = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="tv", rho=c.rho, max_iters=200, tol=1e-2)
     _, info = Q.solve(gpu(c.kspace))
     assert info.stopped == 1 and np.isnan(info.primal_res) and np.isnan(info.dual_res)
