@@ -39,6 +39,10 @@
  *   - Every function returns a recon_status; no function throws or aborts.
  *     recon_last_error() gives a human-readable reason for the last failure
  *     of the calling thread.
+ *   - One device per process: the kernels' raised shared-memory limits are
+ *     set once per process, on the device of the first launch.  Plans on a
+ *     second device in the same process fail at their first large launch
+ *     with RECON_ERR_CUDA (run one process per GPU).
  */
 #ifndef RECON_H
 #define RECON_H
