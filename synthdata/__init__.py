@@ -124,15 +124,20 @@ def make_phantom(Nx, Ny, Nt, rng, moving=3):
     return x * phase[None]
 
 
-def make_sens(Nx, Ny, Nc, rng=None):
-    """Smooth coil sensitivities [Nc, Ny, Nx], normalised sum_c |s_c|^2 = 1."""
+def make_sens(Nx, Ny, Nc, rng=None, phase_y=0.0):
+    """Smooth coil sensitivities [Nc, Ny, Nx], normalised sum_c |s_c|^2 = 1.
+
+    The phase of coil c is th_c + 0.5 x (+ phase_y cos(th_c) y).  With
+    phase_y = 0 it is constant along every image column, so each column's coil
+    Gram sum_c conj(s_j) s_k is real; phase_y != 0 makes it complex, which is
+    what distinguishes conj(s_j) s_k from s_j conj(s_k) (Eq. HconjH)."""
     yy, xx = _grid(Ny, Nx)
     s = np.empty((Nc, Ny, Nx), dtype=np.complex128)
     for c in range(Nc):
         th = 2 * np.pi * c / Nc
         cy, cx = 1.2 * np.sin(th), 1.2 * np.cos(th)
         mag = np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * 0.8 ** 2))
-        s[c] = mag * np.exp(1j * (th + 0.5 * xx))
+        s[c] = mag * np.exp(1j * (th + 0.5 * xx + phase_y * np.cos(th) * yy))
     s /= np.sqrt(np.sum(np.abs(s) ** 2, axis=0, keepdims=True))
     return s
 
@@ -188,7 +193,7 @@ def make_case(name="tiny", seed=None, **over) -> Case:
     rng = np.random.default_rng(cfg["seed"])
     Nx, Ny, Nt, Nc = cfg["Nx"], cfg["Ny"], cfg["Nt"], cfg["Nc"]
     x = make_phantom(Nx, Ny, Nt, rng, moving=cfg.get("moving", 3))
-    sens = make_sens(Nx, Ny, Nc)
+    sens = make_sens(Nx, Ny, Nc, phase_y=cfg.get("phase_y", 0.0))
     mask = cfg.get("mask")
     if mask is None:
         mask = make_mask(Ny, Nt, cfg["R"], rng)

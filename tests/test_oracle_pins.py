@@ -130,9 +130,16 @@ def test_hybrid_residual_equals_full_residual():
 
 
 # --- Section IV-C: Gram blocks and inverse ----------------------------------
-def test_gram_blocks_equal_dense_HtH():
-    """C_t (.) K_i equals the (i,t) block of H'H built column by column."""
+@pytest.mark.parametrize("phase_y", [0.0, 1.5])
+def test_gram_blocks_equal_dense_HtH(phase_y):
+    """C_t (.) K_i equals the (i,t) block of H'H built column by column.  With a
+    coil phase that varies along y, K_i is complex and not symmetric, so the
+    side of the conjugation in Eq. HconjH matters."""
     _, sens, mask, _ = _small_case(Nx=3, Ny=6, Nt=2, Nc=3, R=2, seed=5)
+    sens = synthdata.make_sens(3, 6, 3, phase_y=phase_y)
+    if phase_y:
+        K = np.einsum("cj,ck->jk", np.conj(sens[:, :, 1]), sens[:, :, 1])
+        assert np.abs(K - K.T).max() > 0.1
     Nc, Ny, Nx = sens.shape
     Nt = mask.shape[0]
     Hd = _dense_H(sens, mask)
@@ -355,6 +362,35 @@ def test_objective_and_delta_definitions():
     assert abs(info["J"][0] - oracle.objective_tv(P.b, case.lam, P.fid)) < 1e-12
     full = oracle.data_residual(P.b, case.kspace, case.sens, case.mask)
     assert abs(P.fid(P.b) - full) <= 1e-12 * full
+
+
+def test_objectives_closed_forms():
+    """J on inputs whose terms are known in closed form (Eqs. L1an_pri,
+    L1unconst): noise-free data of x_t = x0 + t c gives a zero data term and
+    ||D_t x||_1 = (Nt - 1) sum |c|; a single temporal frequency x_t = a
+    exp(2 pi i f t / Nt) has one nonzero DFT bin per pixel, of modulus
+    sqrt(Nt) |a|; at x = 0 (w = 0) the data term is ||y||^2."""
+    rng = np.random.default_rng(7)
+    Nt, Ny, Nx, lam = 5, 6, 4, 0.3
+    sens = synthdata.make_sens(Nx, Ny, 2, phase_y=1.0)
+    mask = np.zeros((Nt, Ny), bool)
+    mask[:, ::2] = True
+    x0, c, a = (_rand_c(rng, (Ny, Nx)) for _ in range(3))
+    ramp = x0[None] + np.arange(Nt)[:, None, None] * c[None]
+    y = oracle.forward_op(ramp, sens, mask)
+    fid = lambda z: oracle.data_residual(z, y, sens, mask)
+    ref = lam * (Nt - 1) * np.abs(c).sum()
+    assert abs(oracle.objective_tv(ramp, lam, fid) - ref) <= 1e-12 * ref
+    yy = float(np.vdot(y, y).real)
+    assert abs(oracle.objective_tv(np.zeros_like(ramp), lam, fid) - yy) <= 1e-12 * yy
+    f = 2
+    tone = a[None] * np.exp(2j * np.pi * f * np.arange(Nt) / Nt)[:, None, None]
+    y = oracle.forward_op(tone, sens, mask)
+    fid = lambda z: oracle.data_residual(z, y, sens, mask)
+    ref = lam * np.sqrt(Nt) * np.abs(a).sum()
+    assert abs(oracle.objective_dft(oracle.psi_dft(tone), lam, fid) - ref) <= 1e-12 * ref
+    yy = float(np.vdot(y, y).real)
+    assert abs(oracle.objective_dft(np.zeros_like(tone), lam, fid) - yy) <= 1e-12 * yy
 
 
 def test_column_subset_is_exact():
