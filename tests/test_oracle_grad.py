@@ -72,3 +72,16 @@ def test_gradient_separates_over_columns():
     assert abs(sum(p[1][3] for p in parts) - gm) < 1e-10 * max(1.0, abs(gm))
     for cols, (_, bbc, _, _) in parts:
         np.testing.assert_allclose(bbc, bb[:, :, cols], atol=1e-12)
+
+
+@pytest.mark.parametrize("iters", [1, 4])
+def test_forward_is_algorithm_2(iters):
+    """The unrolled forward runs Algorithm 2 exactly: after K steps its state
+    (x, m, d1, d2) is that of oracle.admm_analysis_tv, which the KKT and
+    closed-form pins fix independently."""
+    case = _case()
+    P = oracle.Problem(case.kspace, case.sens, case.mask, case.mu)
+    states = oracle.unrolled_tv_forward(P.b, P.inv, case.lam, case.mu, case.rho, iters)
+    _, info = oracle.admm_analysis_tv(P.b, P.inv, case.lam, case.mu, case.rho, iters)
+    for a, b in zip(states[-1], info["state"]):
+        np.testing.assert_allclose(a, b, atol=1e-12 * max(1.0, np.abs(b).max()))

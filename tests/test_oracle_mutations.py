@@ -160,7 +160,21 @@ MUTATIONS = [
      [P(ST.test_zero_spatial_weight_is_temporal_tv)]),
     ("volume-z-weight-dropped", "stv", "wz * (x[1:] - x[:-1]))", "(x[1:] - x[:-1]))",
      [P(ST.test_volume_R_adjoint, (3, 2, 4, 5))]),
-    # Differentiable form (reverse pass of unrolled Algorithm 2)
+    ("haar-adjoint-shift-direction", "admm", "a = (a + np.roll(a, sh, axis=0)) / 2.0 + (d - np.roll(d, sh, axis=0)) / 2.0",
+     "a = (a + np.roll(a, -sh, axis=0)) / 2.0 + (d - np.roll(d, -sh, axis=0)) / 2.0",
+     [P(FR.test_tight_and_redundant, 8, 3)]),
+    ("stv-R-weight-dropped", "stv", "ws * (x[:, :, 1:] - x[:, :, :-1])", "(x[:, :, 1:] - x[:, :, :-1])",
+     [P(ST.test_R_adjoint, (4, 5, 6), 0.37)]),
+    ("volume-d1-sign", "stv", "d1 = tuple(d - (a - c) for d, a, c in zip(d1, v, Rm))\n        d2 = d2 - (m - x)\n"
+     "        if fids is not None:",
+     "d1 = tuple(d + (a - c) for d, a, c in zip(d1, v, Rm))\n        d2 = d2 - (m - x)\n"
+     "        if fids is not None:",
+     [P(ST.test_volume_of_one_slice_is_the_2d_algorithm)]),
+    # Differentiable form (unrolled Algorithm 2 and its reverse pass)
+    ("unrolled-threshold-doubled", "grad", "v = soft(tv_D(m) + d1, tau1)", "v = soft(tv_D(m) + d1, 2.0 * tau1)",
+     [P(GR.test_forward_is_algorithm_2, 4)]),
+    ("unrolled-d2-sign", "grad", "d2 = d2 - m_new + x_new", "d2 = d2 + m_new - x_new",
+     [P(GR.test_forward_is_algorithm_2, 4)]),
     ("soft-adjoint-tangent-sign", "grad", "(vbar[on] - n[on] * proj[on])", "(vbar[on] + n[on] * proj[on])",
      [P(GR.test_soft_threshold_adjoint_matches_fd)]),
     ("mu-gradient-stale-iterate", "grad", "mu_bar += float(np.vdot(rb, m1 - d20).real)",
@@ -169,6 +183,10 @@ MUTATIONS = [
     # 16-bit storage encoding
     ("bf16-round-half-up", "precision", "((b + 0x7FFF + lsb) >> 16)", "((b + 0x8000) >> 16)",
      [P(PR.test_rounding_is_nearest_even_by_brute_force, "bf16")]),
+    ("dequantize-scale-dropped", "precision",
+     "return (bits_to_float(re_bits, storage) + 1j * bits_to_float(im_bits, storage)) * s",
+     "return bits_to_float(re_bits, storage) + 1j * bits_to_float(im_bits, storage)",
+     [P(PR.test_round_trip_error_bound, "fp16", 2.0 ** -11)]),
     ("frame-scale-exponent", "precision", "out[t] = 2.0 ** (int(e) - 15)", "out[t] = 2.0 ** (int(e) - 14)",
      [P(PR.test_frame_scales_are_powers_of_two_in_range)]),
 ]
