@@ -133,10 +133,11 @@ typedef struct {
                         (Boyd et al. 2011, Sec. 3.3, the paper's penalty weights).
                         RECON_PRIOR_TV, splits v = D_t m (mu1) and m = x (mu2), stacked:
                         sqrt(||v - D_t m||^2 + ||m - x||^2).
-                        RECON_PRIOR_DFT, split v = w (mu): ||w - v|| (coefficients w = Psi x) */
+                        RECON_PRIOR_DFT and RECON_PRIOR_HAAR, split v = w (mu): ||w - v||
+                        (w the frame coefficients) */
   double dual_res;  /* TV: sqrt(mu1^2 ||D_t (m_K - m_{K-1})||^2 + mu2^2 ||m_K - m_{K-1}||^2);
-                        DFT: mu ||w_K - w_{K-1}||.  Both NaN for the other priors and after an
-                        early stop.  Summed in FP64. */
+                        DFT, Haar: mu ||w_K - w_{K-1}||.  Both NaN for RECON_PRIOR_STV and
+                        after an early stop.  Summed in FP64. */
 } recon_info;
 
 /* Fills `opts` with the defaults listed above.  NULL-safe. */

@@ -552,7 +552,7 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
     if (st != RECON_OK) return st;
     if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, false, s);
     if (e->obj) RC(launch_finalize(e->d_fin, e->n, k - 1, s));
-    if (k == K && K >= 2 && e->prior == RECON_PRIOR_DFT)   // xhat_{K-1} for the residuals
+    if (k == K && K >= 2 && (e->prior == RECON_PRIOR_DFT || e->prior == RECON_PRIOR_HAAR))   // xhat_{K-1}
       for (recon_plan* p : e->plans)
         RC(cudaMemcpyAsync(p->res_prev, p->x, p->nimg() * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     if (prof) p0->mark(p0->ev_col, p0->n_col, true, s);

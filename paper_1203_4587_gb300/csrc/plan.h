@@ -98,8 +98,8 @@ struct recon_plan {
   double* trace_prior = nullptr;
   double* trace_J = nullptr;
   double* yy = nullptr;                // ||y||^2 over the sampled entries (FP64)
-  double* res_acc = nullptr;           // [4] sums of the ADMM residuals (TV, DFT; residual.cu)
-  float2* res_prev = nullptr;          // DFT: xhat_{K-1}, copied before the last inverse step
+  double* res_acc = nullptr;           // [4] sums of the ADMM residuals (TV, DFT, Haar; residual.cu)
+  float2* res_prev = nullptr;          // DFT, Haar: xhat_{K-1}, copied before the last inverse step
   int* flags = nullptr;
   recon::FftPlanDev fx{}, fy{}, ft{};
   recon::FftPlanDev64 fx64{}, fy64{};
@@ -185,7 +185,7 @@ recon_status plan_adjoint64(recon_plan* p, const void* kspace, int kstorage, con
                             float2* b, double* yy, cudaStream_t s);
 recon_status plan_objective(recon_plan* p, const float2* x, double* acc, cudaStream_t s);
 recon_status plan_fill_info(recon_plan* p, recon_info* info, cudaStream_t s);
-// residual.cu: the sums behind recon_info's primal / dual residuals (TV, DFT)
+// residual.cu: the sums behind recon_info's primal / dual residuals (TV, DFT, Haar)
 recon_status launch_residuals(recon_plan* p, cudaStream_t s);
 int objective_coils_max(int Nc, int Ny);   // largest coils-per-pass of the explicit objective
 

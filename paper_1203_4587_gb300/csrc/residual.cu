@@ -20,6 +20,18 @@
 // H'y).  u_K and u_{K-1} are the two ping-pong buffers; the solve copies
 // xhat_{K-1} aside before the last inverse step overwrites it.
 //
+// Algorithm 1 with the undecimated Haar frame (tight, Psi'Psi = I, not
+// unitary): the temporal step keeps u = v + d, s = Psi'u and xhat, with
+// w_k = u_k + Psi(xhat_k - s_k) and d_k = u_k - w_k = -Psi(xhat_k - s_k)
+// (k >= 1; w_0 = Psi H'y, d_0 = 0).  With D = (xhat_K - s_K) - (xhat_{K-1} -
+// s_{K-1}) and Psi'Psi = I,
+//   ||w_K - v_K||^2 = ||d_{K-1} - d_K||^2 = ||D||^2          (K >= 2)
+//   ||w_1 - v_1||^2 = ||d_1||^2 = ||xhat_1 - s_1||^2
+//   ||w_K - w_{K-1}||^2 = ||du||^2 + 2 Re<Psi'du, D> + ||D||^2,  du = u_K - u_{K-1},
+// Psi'du = s_K - s_{K-1}; at K = 1, u_0 = s_0 = 0 and xhat_0 - s_0 stands for
+// H'y (w_0 = Psi H'y).  No transform is needed: all but ||du||^2 are sums
+// over the image, ||du||^2 over the L+1 coefficient channels.
+//
 // Products are FP32, summed per thread in FP32 (Kahan) and across threads in
 // FP64.
 #include <algorithm>
@@ -125,12 +137,49 @@ __global__ void __launch_bounds__(kResThreads) k_dft_residuals(const float2* __r
   }
 }
 
+// acc[0] += the primal sum, acc[1] += ||w_K - w_{K-1}||^2 (Haar frame, as
+// above).  Image fields [Nt][npix]; u [L+1][Nt][npix].  first: K = 1 (xh_prev,
+// s_prev and u_prev unused).
+__global__ void __launch_bounds__(kResThreads) k_haar_residuals(const float2* __restrict__ xh,
+                                                                const float2* __restrict__ xh_prev,
+                                                                const float2* __restrict__ b,
+                                                                const float2* __restrict__ s,
+                                                                const float2* __restrict__ s_prev,
+                                                                const float2* __restrict__ u,
+                                                                const float2* __restrict__ u_prev, long long n,
+                                                                int nch, int first, double* acc) {
+  __shared__ double red[32];
+  KahanSum ap, ad;
+  const long long stride = (long long)gridDim.x * kResThreads;
+  for (long long g = (long long)blockIdx.x * kResThreads + threadIdx.x; g < n; g += stride) {
+    const float2 e = c_sub(xh[g], s[g]);
+    const float2 q = first ? b[g] : c_sub(xh_prev[g], s_prev[g]);
+    const float2 D = c_sub(e, q);
+    const float2 dp = first ? e : D;
+    ap.add(fmaf(dp.x, dp.x, dp.y * dp.y));
+    const float2 ds = first ? s[g] : c_sub(s[g], s_prev[g]);
+    ad.add(fmaf(2.f * ds.x, D.x, fmaf(2.f * ds.y, D.y, fmaf(D.x, D.x, D.y * D.y))));
+  }
+  const long long nu = n * nch;
+  for (long long g = (long long)blockIdx.x * kResThreads + threadIdx.x; g < nu; g += stride) {
+    const float2 du = first ? u[g] : c_sub(u[g], u_prev[g]);
+    ad.add(fmaf(du.x, du.x, du.y * du.y));
+  }
+  const double s0 = group_sum((double)ap.s, red, threadIdx.x, kResThreads, BlockBar());
+  const double s1 = group_sum((double)ad.s, red, threadIdx.x, kResThreads, BlockBar());
+  if (threadIdx.x == 0) {
+    atomicAdd(acc + 0, s0);
+    atomicAdd(acc + 1, s1);
+  }
+}
+
 }  // namespace
 
 // The sums of plan p after its K iterations.  TV: the state of iteration K
 // sits at index K & 1 of the ping-pong buffers, that of K-1 at (K-1) & 1 (m_0 =
-// H'y and d1_0 = 0 for K = 1).  DFT: u_K at K & 1, u_{K-1} at (K-1) & 1,
-// xhat_{K-1} in res_prev (K >= 2).  Other priors: nothing (NaN in recon_info).
+// H'y and d1_0 = 0 for K = 1).  DFT and Haar: u_K (and s_K) at K & 1, u_{K-1}
+// (s_{K-1}) at (K-1) & 1, xhat_{K-1} in res_prev (K >= 2).  The spatio-temporal
+// prior: nothing (NaN in recon_info).
 recon_status launch_residuals(recon_plan* p, cudaStream_t s) {
   const int K = p->opts.max_iters;
   if (K < 1) return RECON_OK;
@@ -151,6 +200,15 @@ recon_status launch_residuals(recon_plan* p, cudaStream_t s) {
     k_dft_residuals<<<grid, kResThreads, smem, s>>>(p->x, K == 1 ? nullptr : p->res_prev, p->b, p->s0[K & 1],
                                                    K == 1 ? nullptr : p->s0[(K - 1) & 1], npix, p->Nt, p->ft,
                                                    p->res_acc);
+  } else if (p->prior == RECON_PRIOR_HAAR) {
+    RC(cudaMemsetAsync(p->res_acc, 0, 4 * sizeof(double), s));
+    const int grid = (int)std::max<long long>(1, std::min<long long>((n + kResThreads - 1) / kResThreads,
+                                                                     4LL * std::max(1, p->num_sms)));
+    const int first = K == 1;
+    k_haar_residuals<<<grid, kResThreads, 0, s>>>(p->x, first ? nullptr : p->res_prev, p->b, p->s1[K & 1],
+                                                  first ? nullptr : p->s1[(K - 1) & 1], p->s0[K & 1],
+                                                  first ? nullptr : p->s0[(K - 1) & 1], n,
+                                                  p->opts.frame_levels + 1, first, p->res_acc);
   } else {
     return RECON_OK;
   }

@@ -3,8 +3,8 @@ on its own iterates.
 
 Algorithm 2 (temporal TV, oracle.tv_residuals): primal sqrt(||v - D_t m||^2 +
 ||m - x||^2) and dual sqrt(mu1^2 ||D_t dm||^2 + mu2^2 ||dm||^2), dm = m_K -
-m_{K-1}.  Algorithm 1 (temporal DFT, oracle.synthesis_residuals): primal
-||w - v|| and dual mu ||w_K - w_{K-1}||.
+m_{K-1}.  Algorithm 1 (temporal DFT or the Haar frame,
+oracle.synthesis_residuals): primal ||w - v|| and dual mu ||w_K - w_{K-1}||.
 
 Bound: the GPU state matches the oracle's to 1e-5 relative (the parity bar),
 and each residual is a norm of differences of state fields, so it may differ
@@ -98,13 +98,25 @@ def test_batched_dft_residuals_per_slice_and_odd_frames():
         check_dft(info, oinfo, xr, c.mu)
 
 
+@pytest.mark.parametrize("iters,levels", [(1, 2), (2, 1), (20, 3)])
+def test_haar_residuals_match_oracle(iters, levels):
+    """The redundant Haar frame: w is not stored, the residuals come from u,
+    s = Psi'u and xhat of the last two iterations (Psi'Psi = I)."""
+    from paper_1203_4587_gb300 import Plan
+    c = case64("tiny", Nx=24, Ny=40, Nt=6, Nc=3, seed=86)
+    P = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="haar", frame_levels=levels, max_iters=iters)
+    _, info = P.solve(gpu(c.kspace))
+    prob = oracle.Problem(c.kspace, c.sens, c.mask, c.mu)
+    xr, oinfo = prob.solve("haar", c.lam, c.mu, iters=iters, objective=False, levels=levels)
+    check_dft(info, oinfo, xr, c.mu)
+
+
 def test_residuals_nan_where_not_defined():
     from paper_1203_4587_gb300 import Plan
     c = case64("tiny", Nx=24, Ny=32, Nt=4, Nc=2, seed=83)
-    for prior in ("haar", "stv"):
-        P = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior=prior, max_iters=5)
-        _, info = P.solve(gpu(c.kspace))
-        assert np.isnan(info.primal_res) and np.isnan(info.dual_res)
+    P = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="stv", max_iters=5)
+    _, info = P.solve(gpu(c.kspace))
+    assert np.isnan(info.primal_res) and np.isnan(info.dual_res)
     Q = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="tv", rho=c.rho, max_iters=200, tol=1e-2)
     _, info = Q.solve(gpu(c.kspace))
     assert info.stopped == 1 and np.isnan(info.primal_res) and np.isnan(info.dual_res)
