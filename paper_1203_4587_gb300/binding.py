@@ -181,6 +181,37 @@ def _c64(t: torch.Tensor, dev=None) -> torch.Tensor:
     return t.contiguous()
 
 
+def _need(t, shape, name, where="cuda"):
+    """Returns ``t`` if it is a contiguous complex64 tensor of ``shape`` on
+    device type ``where`` (None: any); raises otherwise.  The library receives
+    raw pointers and cannot check the sizes of the buffers behind them."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: a torch tensor is expected")
+    if t.dtype != torch.complex64:
+        raise TypeError(f"{name}: complex64 expected, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: a contiguous tensor is expected")
+    if where is not None and t.device.type != where:
+        raise ValueError(f"{name}: a {where} tensor is expected, got {t.device.type}")
+    return t
+
+
+def _need_count(items, n, name):
+    """One entry per plan: the library reads exactly n pointers."""
+    items = list(items)
+    if len(items) != n:
+        raise ValueError(f"{name}: {len(items)} entries for {n} plans")
+    return items
+
+
+def _mask_shape_ok(mshape, Nt_ok, Ny, Nx):
+    """A row mask [Nt][Ny] or a full mask [Nt][Ny][Nx] for images of Ny x Nx."""
+    return Nt_ok and ((len(mshape) == 2 and mshape[1] == Ny) or
+                      (len(mshape) == 3 and mshape[1] == Ny and mshape[2] == Nx))
+
+
 def default_opts(**over) -> Opts:
     o = Opts()
     load().recon_default_opts(C.byref(o))
@@ -201,8 +232,12 @@ class Plan:
         """slab=(i0, width): a plan over columns i0 .. i0+width-1 (recon_plan_create_slab)."""
         lib = load()
         sens = _c64(sens, "cuda")
+        if sens.dim() != 3:
+            raise ValueError(f"sens: [Nc, Ny, Nx] expected, got shape {tuple(sens.shape)}")
         Nc, Ny, Nx = sens.shape
         mask = torch.as_tensor(mask).to(torch.uint8).contiguous()
+        if not _mask_shape_ok(tuple(mask.shape), mask.dim() >= 2 and mask.shape[0] >= 1, Ny, Nx):
+            raise ValueError(f"mask: [Nt, {Ny}] or [Nt, {Ny}, {Nx}] expected, got shape {tuple(mask.shape)}")
         o = default_opts(**opts)
         if mask.dim() == 3:
             o.mask_full = 1
@@ -244,13 +279,24 @@ class Plan:
         return alloc((s["Nt"], s["Ny"], s["Nx"]), dtype=torch.complex64, device="cuda")
 
     def _ksp(self):
+        return torch.empty(self.kshape, dtype=torch.complex64, device="cuda")
+
+    @property
+    def kshape(self):
+        """k-space layout [Nt, Nc, Ny, Nx]."""
         s = self.shape
-        return torch.empty((s["Nt"], s["Nc"], s["Ny"], s["Nx"]), dtype=torch.complex64, device="cuda")
+        return (s["Nt"], s["Nc"], s["Ny"], s["Nx"])
+
+    @property
+    def ishape(self):
+        """image layout [Nt, Ny, Nx]."""
+        s = self.shape
+        return (s["Nt"], s["Ny"], s["Nx"])
 
     def solve(self, kspace, out=None, info=True, stream=None):
         """Runs the reconstruction; returns (image, Info or None)."""
-        k = _c64(kspace, "cuda")
-        out = self._img() if out is None else out
+        k = _need(_c64(kspace, "cuda"), self.kshape, "kspace")
+        out = self._img() if out is None else _need(out, self.ishape, "out")
         inf = Info() if info else None
         st = load().recon_solve(self._h, _ptr(k), _ptr(out), C.byref(inf) if info else None, _stream(stream))
         _check(st)
@@ -264,7 +310,16 @@ class Plan:
 
     def solve_quantized(self, q, out=None, info=True, stream=None):
         """Runs the reconstruction from 16-bit k-space ``q`` (a QuantizedKspace)."""
-        out = self._img() if out is None else out
+        d, fs = q.data, q.frame_scale
+        if (not isinstance(d, torch.Tensor) or d.dtype != torch.int32 or tuple(d.shape) != self.kshape
+                or not d.is_contiguous() or d.device.type != "cuda"):
+            raise ValueError(f"q.data: a contiguous cuda int32 tensor of shape {self.kshape} is expected")
+        if (not isinstance(fs, torch.Tensor) or fs.dtype != torch.float32 or tuple(fs.shape) != (self.kshape[0],)
+                or fs.device.type != "cuda"):
+            raise ValueError(f"q.frame_scale: a cuda float32 tensor of shape ({self.kshape[0]},) is expected")
+        if q.storage not in ("fp16", "bf16"):
+            raise ValueError(f"q.storage: fp16 or bf16 expected, got {q.storage!r}")
+        out = self._img() if out is None else _need(out, self.ishape, "out")
         inf = Info() if info else None
         y = KSpace(q.data.data_ptr(), STORAGE[q.storage], q.frame_scale.data_ptr())
         st = load().recon_solve_kspace(self._h, C.byref(y), _ptr(out), C.byref(inf) if info else None,
@@ -274,6 +329,8 @@ class Plan:
 
     def solve_host(self, kspace_host, image_host, stream=None):
         """Host buffers in and out (copies inside the call); returns Info."""
+        _need(kspace_host, self.kshape, "kspace_host", "cpu")
+        _need(image_host, self.ishape, "image_host", "cpu")
         inf = Info()
         st = load().recon_solve_host(self._h, _ptr(kspace_host), _ptr(image_host), C.byref(inf), _stream(stream))
         _check(st)
@@ -286,19 +343,19 @@ class Plan:
         return [buf[k] for k in range(n)]
 
     def adjoint(self, kspace, stream=None):
-        k = _c64(kspace, "cuda")
+        k = _need(_c64(kspace, "cuda"), self.kshape, "kspace")
         out = self._img()
         _check(load().recon_apply_adjoint(self._h, _ptr(k), _ptr(out), _stream(stream)))
         return out
 
     def forward(self, image, stream=None):
-        x = _c64(image, "cuda")
+        x = _need(_c64(image, "cuda"), self.ishape, "image")
         out = self._ksp()
         _check(load().recon_apply_forward(self._h, _ptr(x), _ptr(out), _stream(stream)))
         return out
 
     def inverse(self, image, stream=None):
-        x = _c64(image, "cuda")
+        x = _need(_c64(image, "cuda"), self.ishape, "image")
         out = self._img()
         _check(load().recon_apply_inverse(self._h, _ptr(x), _ptr(out), _stream(stream)))
         return out
@@ -330,8 +387,14 @@ class Batch:
 
     def solve(self, kspaces, outs=None, stream=None):
         """kspaces: list of device complex64 tensors; returns the list of images."""
-        ks = [_c64(k, "cuda") for k in kspaces]
-        outs = [p._img() for p in self.plans] if outs is None else outs
+        n = len(self.plans)
+        ks = [_need(_c64(k, "cuda"), p.kshape, f"kspaces[{q}]")
+              for q, (k, p) in enumerate(zip(_need_count(kspaces, n, "kspaces"), self.plans))]
+        if outs is None:
+            outs = [p._img() for p in self.plans]
+        else:
+            outs = [_need(o, p.ishape, f"outs[{q}]")
+                    for q, (o, p) in enumerate(zip(_need_count(outs, n, "outs"), self.plans))]
         self._keep = (ks, outs)
         ka = (C.c_void_p * len(ks))(*[k.data_ptr() for k in ks])
         oa = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
@@ -388,7 +451,9 @@ class Grad:
         _check(load().recon_grad_create(C.byref(self._h), arr, len(self.plans), int(checkpoint_every)))
 
     def forward(self, kspaces, stream=None):
-        ks = [_c64(k, "cuda") for k in kspaces]
+        n = len(self.plans)
+        ks = [_need(_c64(k, "cuda"), p.kshape, f"kspaces[{q}]")
+              for q, (k, p) in enumerate(zip(_need_count(kspaces, n, "kspaces"), self.plans))]
         outs = [p._img() for p in self.plans]
         ka = (C.c_void_p * len(ks))(*[k.data_ptr() for k in ks])
         oa = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
@@ -396,9 +461,10 @@ class Grad:
         return outs
 
     def backward(self, grad_images, stream=None):
-        gs = [_c64(g, "cuda") for g in grad_images]
-        outs = [p._ksp() for p in self.plans]
         n = len(self.plans)
+        gs = [_need(_c64(g, "cuda"), p.ishape, f"grad_images[{q}]")
+              for q, (g, p) in enumerate(zip(_need_count(grad_images, n, "grad_images"), self.plans))]
+        outs = [p._ksp() for p in self.plans]
         ga = (C.c_void_p * n)(*[g.data_ptr() for g in gs])
         oa = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
         gl = (C.c_double * n)()
@@ -467,6 +533,10 @@ class QuantizedKspace:
 def quantize_kspace(kspace, storage="fp16", stream=None):
     """complex64 [Nt, Nc, Ny, Nx] on the GPU -> QuantizedKspace (fp16 or bf16)."""
     k = _c64(kspace, "cuda")
+    if k.dim() != 4:
+        raise ValueError(f"kspace: [Nt, Nc, Ny, Nx] expected, got shape {tuple(k.shape)}")
+    if storage not in ("fp16", "bf16"):
+        raise ValueError(f"storage: fp16 or bf16 expected, got {storage!r}")
     Nt, Nc, Ny, Nx = k.shape
     data = torch.empty((Nt, Nc, Ny, Nx), dtype=torch.int32, device="cuda")
     scale = torch.empty((Nt,), dtype=torch.float32, device="cuda")
@@ -483,9 +553,15 @@ def gram_inverse_noalloc(mask_rows, sens_cols, mu, out=None, stream=None):
     """
     m = torch.as_tensor(mask_rows).to(torch.uint8).contiguous()
     s = _c64(sens_cols, "cuda")
+    if s.dim() != 3:
+        raise ValueError(f"sens_cols: [nblk, Nc, Ny] expected, got shape {tuple(s.shape)}")
     nblk, Nc, Ny = s.shape
+    if tuple(m.shape) != (nblk, Ny) or m.device.type != "cuda":
+        raise ValueError(f"mask_rows: a cuda uint8 tensor of shape {(nblk, Ny)} is expected")
     if out is None:
         out = torch.empty((nblk, Ny, Ny), dtype=torch.complex64, device="cuda")
+    else:
+        _need(out, (nblk, Ny, Ny), "out")
     _check(load().recon_gram_inverse_noalloc(int(Ny), int(Nc), int(nblk), _ptr(m), _ptr(s), float(mu), _ptr(out),
                                              _stream(stream)))
     return out
@@ -497,14 +573,22 @@ def solve_slabs(mask, sens, lam, mu, kspace, width, prior="tv", out=None, stream
     lib = load()
     s = _c64(sens, "cuda")
     k = _c64(kspace, "cuda")
+    if s.dim() != 3:
+        raise ValueError(f"sens: [Nc, Ny, Nx] expected, got shape {tuple(s.shape)}")
     Nc, Ny, Nx = s.shape
     m = torch.as_tensor(mask).to(torch.uint8).contiguous()
+    if not _mask_shape_ok(tuple(m.shape), m.dim() >= 2 and m.shape[0] >= 1, Ny, Nx):
+        raise ValueError(f"mask: [Nt, {Ny}] or [Nt, {Ny}, {Nx}] expected, got shape {tuple(m.shape)}")
     o = default_opts(**opts)
     if m.dim() == 3:
         o.mask_full = 1
     Nt = m.shape[0]
+    _need(k, (Nt, Nc, Ny, Nx), "kspace")
     mdev = m.cuda() if m.device.type != "cuda" else m
-    out = torch.empty((Nt, Ny, Nx), dtype=torch.complex64, device="cuda") if out is None else out
+    if out is None:
+        out = torch.empty((Nt, Ny, Nx), dtype=torch.complex64, device="cuda")
+    else:
+        _need(out, (Nt, Ny, Nx), "out")
     tr = (C.c_double * (o.max_iters + 1))()
     inf = Info()
     _check(lib.recon_solve_slabs(int(Nx), int(Ny), int(Nt), int(Nc), _ptr(mdev), _ptr(s), float(lam), float(mu),
