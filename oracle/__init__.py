@@ -34,8 +34,10 @@ from .admm import __all__ as _admm_all
 from .grad import unrolled_tv_adjoint, unrolled_tv_forward, unrolled_tv_loss_and_grad  # noqa: F401
 from . import precision  # noqa: F401
 from .stv import (admm_analysis_stv, admm_analysis_stv_volume, cg_steps, objective_stv,  # noqa: F401
-                  objective_stv_vol, stv_M, stv_M_vol, stv_R, stv_R_vol, stv_Radj, stv_Radj_vol)
+                  objective_stv_vol, stacked_residuals, stv_M, stv_M_vol, stv_R, stv_R_vol, stv_Radj,
+                  stv_Radj_vol)
 
 __all__ = list(_admm_all) + ["unrolled_tv_forward", "unrolled_tv_adjoint", "unrolled_tv_loss_and_grad",
                              "admm_analysis_stv", "cg_steps", "objective_stv", "stv_M", "stv_R", "stv_Radj",
-                             "admm_analysis_stv_volume", "objective_stv_vol", "stv_M_vol", "stv_R_vol", "stv_Radj_vol"]
+                             "admm_analysis_stv_volume", "objective_stv_vol", "stv_M_vol", "stv_R_vol", "stv_Radj_vol",
+                             "stacked_residuals"]

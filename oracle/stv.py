@@ -37,7 +37,8 @@ import numpy as np
 from .admm import delta_ratio, soft
 
 __all__ = ["stv_R", "stv_Radj", "stv_M", "cg_steps", "objective_stv", "admm_analysis_stv",
-           "stv_R_vol", "stv_Radj_vol", "stv_M_vol", "objective_stv_vol", "admm_analysis_stv_volume"]
+           "stv_R_vol", "stv_Radj_vol", "stv_M_vol", "objective_stv_vol", "admm_analysis_stv_volume",
+           "stacked_residuals"]
 
 
 def stv_R(x, ws):
@@ -128,7 +129,9 @@ def admm_analysis_stv(b, inv, lam, mu, rho, iters, ws=1.0, cg=5, fid=None, tol=0
         d1 = tuple(np.array(a, dtype=np.complex128) for a in d1)
     J = [objective_stv(x, lam, ws, fid)] if fid is not None else []
     k_done = 0
+    m_prev = v = None
     for k in range(1, iters + 1):
+        m_prev = m
         # v <- S(R m + d1, lambda / (2 mu1))
         Rm = stv_R(m, ws)
         v = tuple(soft(a + d, lam / (2.0 * mu1)) for a, d in zip(Rm, d1))
@@ -148,7 +151,23 @@ def admm_analysis_stv(b, inv, lam, mu, rho, iters, ws=1.0, cg=5, fid=None, tol=0
                 dk = delta_ratio(J[-2], J[-1])
                 if 0.0 <= dk < tol:
                     break
-    return x, dict(J=J, iters=k_done, state=(x, m, d1, d2))
+    info = dict(J=J, iters=k_done, state=(x, m, d1, d2))
+    if m_prev is not None:
+        info["primal_res"], info["dual_res"] = stacked_residuals(x, m, v, m_prev, mu1, mu2,
+                                                                 lambda a: stv_R(a, ws))
+    return x, info
+
+
+def stacked_residuals(x, m, v, m_prev, mu1, mu2, R):
+    """ADMM residuals of Algorithm 2 with a stacked analysis operator R (a tuple
+    of components), in the stacked form of Boyd et al. (2011, Sec. 3.3) for the
+    splits v = R m (mu1) and m = x (mu2), m updated second:
+      primal = sqrt(sum_c ||v_c - (R m)_c||^2 + ||m - x||^2)
+      dual   = sqrt(mu1^2 sum_c ||(R (m - m_prev))_c||^2 + mu2^2 ||m - m_prev||^2)."""
+    rp = sum(np.vdot(a - b, a - b).real for a, b in zip(v, R(m))) + np.vdot(m - x, m - x).real
+    dm = m - m_prev
+    rd = mu1 ** 2 * sum(np.vdot(c, c).real for c in R(dm)) + mu2 ** 2 * np.vdot(dm, dm).real
+    return float(np.sqrt(rp)), float(np.sqrt(rd))
 
 
 # ---------------------------------------------------------------------------
@@ -205,7 +224,9 @@ def admm_analysis_stv_volume(bs, invs, lam, mu, rho, iters, ws=1.0, wz=1.0, cg=5
     d1 = tuple(np.zeros_like(c) for c in stv_R_vol(x, ws, wz))
     d2 = np.zeros_like(b)
     J = [objective_stv_vol(x, lam, ws, wz, fids)] if fids is not None else []
+    m_prev = v = None
     for _ in range(iters):
+        m_prev = m
         Rm = stv_R_vol(m, ws, wz)
         v = tuple(soft(a + d, lam / (2.0 * mu1)) for a, d in zip(Rm, d1))
         rhs = stv_Radj_vol(tuple(a - d for a, d in zip(v, d1)), ws, wz, shape) + r2 * (x + d2)
@@ -216,4 +237,8 @@ def admm_analysis_stv_volume(bs, invs, lam, mu, rho, iters, ws=1.0, wz=1.0, cg=5
         d2 = d2 - (m - x)
         if fids is not None:
             J.append(objective_stv_vol(x, lam, ws, wz, fids))
-    return x, dict(J=J, iters=iters, state=(x, m, d1, d2))
+    info = dict(J=J, iters=iters, state=(x, m, d1, d2))
+    if m_prev is not None:
+        info["primal_res"], info["dual_res"] = stacked_residuals(x, m, v, m_prev, mu1, mu2,
+                                                                 lambda a: stv_R_vol(a, ws, wz))
+    return x, info

@@ -158,6 +158,12 @@ MUTATIONS = [
     ("stv-rhs-without-rho", "stv", "rhs = stv_Radj(tuple(a - d for a, d in zip(v, d1)), ws, shape) + r2 * (x + d2)",
      "rhs = stv_Radj(tuple(a - d for a, d in zip(v, d1)), ws, shape) + (x + d2)",
      [P(ST.test_zero_spatial_weight_is_temporal_tv)]),
+    ("stv-residual-split-dropped", "stv",
+     "rp = sum(np.vdot(a - b, a - b).real for a, b in zip(v, R(m))) + np.vdot(m - x, m - x).real",
+     "rp = sum(np.vdot(a - b, a - b).real for a, b in zip(v, R(m)))",
+     [P(ST.test_stv_residuals_follow_the_duals_and_vanish)]),
+    ("stv-dual-wrong-weight", "stv", "rd = mu1 ** 2 * sum(", "rd = mu2 ** 2 * sum(",
+     [P(ST.test_zero_spatial_weight_is_temporal_tv)]),
     ("volume-z-weight-dropped", "stv", "wz * (x[1:] - x[:-1]))", "(x[1:] - x[:-1]))",
      [P(ST.test_volume_R_adjoint, (3, 2, 4, 5))]),
     ("haar-adjoint-shift-direction", "admm", "a = (a + np.roll(a, sh, axis=0)) / 2.0 + (d - np.roll(d, sh, axis=0)) / 2.0",

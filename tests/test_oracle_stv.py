@@ -17,6 +17,8 @@ None of these re-derive the code under test:
   lambda ||R x||_1 + ||y - H x||^2 on a tiny problem.
 """
 
+import functools
+
 import numpy as np
 import pytest
 import scipy.fft
@@ -122,8 +124,12 @@ def test_zero_spatial_weight_is_temporal_tv():
     xs, is_ = oracle.admm_analysis_stv(P.b, P.inv, lam, mu, rho, iters, ws=0.0, cg=x.shape[0] + 1, fid=P.fid)
     np.testing.assert_allclose(xs, xt, atol=1e-10 * np.abs(xt).max())
     np.testing.assert_allclose(is_["J"], it["J"], rtol=1e-10)
+    # R = (D_t, 0, 0): the stacked residuals are the temporal-TV ones
+    for key in ("primal_res", "dual_res"):
+        assert abs(is_[key] - it[key]) <= 1e-9 * it[key]
 
 
+@functools.lru_cache(maxsize=1)
 def _stv_converged():
     x, sens, mask, y = _small_case(Nx=4, Ny=4, Nt=4, Nc=2, R=2, noise=0.05, seed=18)
     lam, mu, rho, ws = 0.05, 0.1, 0.5, 0.8
@@ -150,6 +156,38 @@ def test_kkt_stv_on_tiny_problem():
     grad = 2 * oracle.adjoint_op(oracle.forward_op(xr, sens, mask) - y, sens, mask)
     stat = grad + lam * oracle.stv_Radj(g, ws, xr.shape)
     assert np.linalg.norm(stat) < 1e-8 * max(1.0, np.linalg.norm(grad))
+
+
+def test_stv_residuals_follow_the_duals_and_vanish():
+    """Stacked residuals of Algorithm 2 with R = (D_t, w D_x, w D_y): the v - R m
+    part equals the change of d1 in the last iteration (the d1-update), both are
+    positive early on, and both decay towards the fixed point."""
+    x, sens, mask, y = _small_case(Nx=4, Ny=5, Nt=4, Nc=2, R=2, noise=0.05, seed=23)
+    lam, mu, rho, ws = 0.05, 0.1, 0.5, 0.8
+    P = oracle.Problem(y, sens, mask, mu)
+    _, i4 = oracle.admm_analysis_stv(P.b, P.inv, lam, mu, rho, 4, ws=ws, cg=3)
+    _, i5 = oracle.admm_analysis_stv(P.b, P.inv, lam, mu, rho, 5, ws=ws, cg=3)
+    assert i5["primal_res"] > 1e-6 and i5["dual_res"] > 1e-6
+    x5, m5, d1_5, _ = i5["state"]
+    d1_4 = i4["state"][2]
+    part = np.sqrt(sum(np.vdot(a - b, a - b).real for a, b in zip(d1_4, d1_5)) + np.vdot(m5 - x5, m5 - x5).real)
+    assert abs(part - i5["primal_res"]) <= 1e-12 * part
+    # the converged run of the KKT test: a million-fold drop from iteration 5
+    _, sens, mask, y, lam, mu, rho, ws, _, info = _stv_converged()
+    P = oracle.Problem(y, sens, mask, mu)
+    _, early = oracle.admm_analysis_stv(P.b, P.inv, lam, mu, rho, 5, ws=ws, cg=70)
+    for key in ("primal_res", "dual_res"):
+        assert info[key] < 1e-6 * early[key]
+
+
+def test_volume_residuals_of_one_slice_are_the_2d_ones():
+    x, sens, mask, y = _small_case(Nx=4, Ny=5, Nt=4, Nc=2, R=2, noise=0.05, seed=24)
+    lam, mu, rho, ws = 0.05, 0.1, 0.5, 0.7
+    P = oracle.Problem(y, sens, mask, mu)
+    _, i2 = oracle.admm_analysis_stv(P.b, P.inv, lam, mu, rho, 6, ws=ws, cg=4)
+    _, iv = oracle.admm_analysis_stv_volume([P.b], [P.inv], lam, mu, rho, 6, ws=ws, wz=1.3, cg=4)
+    for key in ("primal_res", "dual_res"):
+        assert abs(iv[key] - i2[key]) <= 1e-12 * i2[key]
 
 
 def test_objective_is_lambda_l1_plus_fidelity():
