@@ -36,6 +36,9 @@
  *   - Pointers marked "device" must be device (or managed) memory of the
  *     current device.  The caller owns every buffer it passes; the library
  *     only reads inputs during the call and keeps no reference to them.
+ *   - Buffers must hold at least the elements their stated layout implies:
+ *     the library receives bare pointers and cannot check their sizes (the
+ *     Python binding checks every tensor's shape, dtype and device first).
  *   - Every function returns a recon_status; no function throws or aborts.
  *     recon_last_error() gives a human-readable reason for the last failure
  *     of the calling thread.
