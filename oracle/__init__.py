@@ -26,7 +26,9 @@ Every function here is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_pins.py``, ``tests/test_oracle_grad.py``,
 ``tests/test_oracle_frame.py``, ``tests/test_oracle_precision.py`` and
 ``tests/test_oracle_stv.py`` against closed
-forms, brute force, finite differences or invariants.
+forms, brute force, finite differences or invariants.  The pins are checked
+in turn by ``tests/test_oracle_mutations.py``, which plants plausible slips
+in this package's source one at a time and requires a pin to fail for each.
 """
 
 from .admm import *  # noqa: F401,F403

@@ -27,7 +27,9 @@ stopping early only when gamma = 0 (then m solves the system exactly).
 Parity status: pinned in ``tests/test_oracle_stv.py`` (adjointness of R,
 R'R against a dense brute-force matrix, CG against an exact solve and
 against the DCT-II diagonalisation of the non-circular Laplacians, w = 0
-against the temporal-TV oracle, KKT optimality of the ADMM fixed point).
+against the temporal-TV oracle, KKT optimality of the ADMM fixed point; the
+stacked residuals against the d1 change, the temporal-TV residuals at w = 0,
+a volume of one slice and their decay at the fixed point).
 """
 
 from __future__ import annotations
