@@ -46,6 +46,12 @@
  *     set once per process, on the device of the first launch.  Plans on a
  *     second device in the same process fail at their first large launch
  *     with RECON_ERR_CUDA (run one process per GPU).
+ *   - Host threads: calls on different plans may come from different threads;
+ *     calls that use one plan (or a batch, volume or gradient engine built
+ *     on it) must not overlap.  The limits above are raised without a lock,
+ *     so run one solve of each shape before solving from several threads at
+ *     once (two first launches racing can fail with RECON_ERR_CUDA).  The
+ *     autotuner's cache and the allocation-free workspace are locked.
  */
 #ifndef RECON_H
 #define RECON_H
