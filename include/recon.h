@@ -91,7 +91,7 @@ typedef enum {
   RECON_ERR_CUDA = 4,               /* a CUDA call failed (see recon_last_error) */
   RECON_ERR_TIMEOUT = 5,            /* a bounded device-side wait gave up */
   RECON_ERR_NONFINITE = 6,          /* a non-finite objective or a non-positive-definite block */
-  RECON_ERR_UNSUPPORTED = 7         /* valid request this build does not support */
+  RECON_ERR_UNSUPPORTED = 7         /* valid request the library does not support */
 } recon_status;
 
 /* Storage of the data a solve keeps in device memory.  For a plan (opts.storage):

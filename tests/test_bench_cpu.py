@@ -1,5 +1,5 @@
 """The bench's host-side helpers on CPU: strict-JSON output (no NaN / Infinity)
-and the command-line flags the driver passes."""
+and the command-line flags of the benchmark contract."""
 
 import json
 import math
