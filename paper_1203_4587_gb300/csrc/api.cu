@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "host_logic.h"
 #include "plan.h"
 
 using namespace recon;
@@ -60,15 +61,7 @@ static FftPlanT<T> fft_plan_t(int n, const T* d_tw) {
   FftPlanT<T> P{};
   P.n = n;
   P.tw = d_tw;
-  int m = n, ns = 0;
-  const int pref[] = {4, 2, 3, 5, 7};
-  for (int r : pref) {
-    while (m % r == 0 && ns < kFftMaxStages) { P.radix[ns++] = r; m /= r; }
-  }
-  for (int r = 11; m > 1 && ns < kFftMaxStages; r += 2) {
-    while (m % r == 0) { P.radix[ns++] = r; m /= r; }
-  }
-  P.ns = ns;
+  P.ns = fft_factor(n, P.radix, kFftMaxStages);
   return P;
 }
 

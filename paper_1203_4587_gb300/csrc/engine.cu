@@ -9,6 +9,7 @@
 #include <queue>
 #include <vector>
 
+#include "host_logic.h"
 #include "plan.h"
 
 namespace recon {
@@ -42,47 +43,19 @@ cudaError_t upload(DevArena& a, T** dst, const std::vector<T>& v) {
   return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
-// Column work lists: every column of every slice, spread over `grid` CTAs by
-// longest-processing-time-first on the bytes each column streams, then each
-// CTA's list ordered by (slice, column).
 }  // namespace
 
+// Column work lists of a batch: every column of every slice, by the bytes it
+// streams (host_logic.h: lpt_work_lists).
 void build_col_work(recon_plan* const* plans, int n, int grid, std::vector<unsigned>& work, std::vector<int>& off,
                     int& work_max) {
-  struct Col { long long cost; int q, c; };
-  std::vector<Col> cols;
+  std::vector<long long> cost(n);
+  std::vector<int> ncols(n);
   for (int q = 0; q < n; ++q) {
-    const recon_plan* p = plans[q];
-    const long long cost = p->pk.col_elems * (long long)p->esize + 4096;
-    for (int c = 0; c < p->Nx * p->Nt; ++c) cols.push_back({cost, q, c});
+    cost[q] = plans[q]->pk.col_elems * (long long)plans[q]->esize + 4096;
+    ncols[q] = plans[q]->Nx * plans[q]->Nt;
   }
-  std::vector<std::vector<int2>> per(grid);
-  if (n == 1) {
-    // equal columns: interleave (column b, b + grid, ...)
-    for (size_t k = 0; k < cols.size(); ++k) per[k % grid].push_back(make_int2(cols[k].q, cols[k].c));
-  } else {
-    std::stable_sort(cols.begin(), cols.end(), [](const Col& a, const Col& b) { return a.cost > b.cost; });
-    using Load = std::pair<long long, int>;
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
-    for (int b = 0; b < grid; ++b) pq.push({0, b});
-    for (const Col& c : cols) {
-      Load l = pq.top();
-      pq.pop();
-      per[l.second].push_back(make_int2(c.q, c.c));
-      pq.push({l.first + c.cost, l.second});
-    }
-    for (auto& v : per)
-      std::sort(v.begin(), v.end(), [](int2 a, int2 b) { return a.x != b.x ? a.x < b.x : a.y < b.y; });
-  }
-  work.clear();
-  off.assign(grid + 1, 0);
-  work_max = 0;
-  for (int b = 0; b < grid; ++b) {
-    off[b] = (int)work.size();
-    for (int2 w : per[b]) work.push_back(((unsigned)w.x << 24) | (unsigned)w.y);
-    work_max = std::max(work_max, (int)per[b].size());
-  }
-  off[grid] = (int)work.size();
+  lpt_work_lists(cost, ncols, grid, work, off, work_max);
 }
 
 namespace {
