@@ -385,27 +385,15 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
   p->esize = (o.storage == 0) ? 8 : 4;
   cudaGetDevice(&p->device);
   cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
-  p->h_rowoff.assign(Nt + 1, 0);
-  for (int t = 0; t < Nt; ++t) {
-    for (int j = 0; j < Ny; ++j) {
-      bool on;
-      if (o.mask_full) {
-        const uint8_t* rowp = &hm[((size_t)t * Ny + j) * Nxf];
-        on = rowp[0] != 0;
-        for (int i = 1; i < Nxf; ++i) {
-          if ((rowp[i] != 0) != on) {
-            delete p;
-            return fail(RECON_ERR_MASK_NOT_CARTESIAN, "mask differs along kx (row " + std::to_string(j) +
-                                                          ", frame " + std::to_string(t) + ")");
-          }
-        }
-      } else {
-        on = hm[(size_t)t * Ny + j] != 0;
-      }
-      if (on) p->h_rows.push_back(j);
+  {
+    int bad_t = 0, bad_j = 0;
+    const int maxm = mask_rows(hm.data(), Nt, Ny, Nxf, o.mask_full != 0, p->h_rows, p->h_rowoff, &bad_t, &bad_j);
+    if (maxm < 0) {
+      delete p;
+      return fail(RECON_ERR_MASK_NOT_CARTESIAN, "mask differs along kx (row " + std::to_string(bad_j) +
+                                                    ", frame " + std::to_string(bad_t) + ")");
     }
-    p->h_rowoff[t + 1] = (int)p->h_rows.size();
-    p->maxm = std::max(p->maxm, p->h_rowoff[t + 1] - p->h_rowoff[t]);
+    p->maxm = maxm;
   }
   p->total_rows = (int)p->h_rows.size();
   p->pk = make_pack(Ny);

@@ -4,9 +4,12 @@
 //   fft_factor      the stage radices of the Stockham FFTs (every transform
 //                   of the library: rows, columns and time)
 //   lpt_work_lists  the per-CTA column lists of the column-inverse kernel
+//   mask_rows       the sampled ky rows of each frame of a Cartesian mask
 #pragma once
 
 #include <algorithm>
+#include <cstddef>
+#include <cstdint>
 #include <functional>
 #include <queue>
 #include <utility>
@@ -69,6 +72,41 @@ inline void lpt_work_lists(const std::vector<long long>& cost, const std::vector
     work_max = std::max(work_max, (int)per[b].size());
   }
   off[grid] = (int)work.size();
+}
+
+// Sampled ky rows of a Cartesian ky-t mask (Section II-A: every kx of a
+// sampled row is sampled).  mask is [Nt][Ny] (full = false) or [Nt][Ny][Nx]
+// (full = true, and then each row must be constant along kx).  Frame t's
+// rows, in increasing ky, are rows[rowoff[t] .. rowoff[t+1]).  Returns the
+// largest per-frame count, or -1 with (*bad_t, *bad_j) the first row that
+// differs along kx.
+inline int mask_rows(const uint8_t* mask, int Nt, int Ny, int Nx, bool full, std::vector<int>& rows,
+                     std::vector<int>& rowoff, int* bad_t, int* bad_j) {
+  rows.clear();
+  rowoff.assign(Nt + 1, 0);
+  int maxm = 0;
+  for (int t = 0; t < Nt; ++t) {
+    for (int j = 0; j < Ny; ++j) {
+      bool on;
+      if (full) {
+        const uint8_t* rowp = &mask[((size_t)t * Ny + j) * Nx];
+        on = rowp[0] != 0;
+        for (int i = 1; i < Nx; ++i) {
+          if ((rowp[i] != 0) != on) {
+            *bad_t = t;
+            *bad_j = j;
+            return -1;
+          }
+        }
+      } else {
+        on = mask[(size_t)t * Ny + j] != 0;
+      }
+      if (on) rows.push_back(j);
+    }
+    rowoff[t + 1] = (int)rows.size();
+    maxm = std::max(maxm, rowoff[t + 1] - rowoff[t]);
+  }
+  return maxm;
 }
 
 }  // namespace recon

@@ -1,6 +1,8 @@
-// CPU checks of the library's host-side planning logic (csrc/host_logic.h),
+// CPU checks of the library's host-side planning logic (csrc/host_logic.h):
+// FFT stage radices, mask row lists and batched column work lists,
 // built with the host C++ compiler by tests/test_host_logic.py.  Prints one
 // line per failed property and exits non-zero if any failed.
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <random>
@@ -101,8 +103,54 @@ static void check_work_lists(const std::vector<long long>& cost, const std::vect
   CHECK(hi - lo <= maxcost, "imbalance %lld above one column's cost %lld", hi - lo, maxcost);
 }
 
+// Row lists of random ky-t masks: the sampled rows of every frame in order,
+// offsets and the largest count; a full [Nt][Ny][Nx] mask that is constant
+// along kx gives the same lists, and one flipped entry is reported at its
+// (frame, row) when it is the first row that differs.
+static void check_mask_rows(std::mt19937& rng) {
+  for (int trial = 0; trial < 30; ++trial) {
+    const int Nt = 1 + (int)(rng() % 9), Ny = 1 + (int)(rng() % 40), Nx = 1 + (int)(rng() % 7);
+    std::vector<uint8_t> m((size_t)Nt * Ny), full((size_t)Nt * Ny * Nx);
+    for (auto& v : m) v = (uint8_t)(rng() % 3 == 0 ? (1 + rng() % 255) : 0);   // any nonzero means sampled
+    for (int t = 0; t < Nt; ++t)
+      for (int j = 0; j < Ny; ++j)
+        for (int i = 0; i < Nx; ++i) full[((size_t)t * Ny + j) * Nx + i] = m[(size_t)t * Ny + j] ? 1 : 0;
+    std::vector<int> rows, off, rows_f, off_f;
+    int bt = -1, bj = -1;
+    const int maxm = recon::mask_rows(m.data(), Nt, Ny, Nx, false, rows, off, &bt, &bj);
+    int expect_max = 0;
+    size_t k = 0;
+    for (int t = 0; t < Nt; ++t) {
+      CHECK(off[t] == (int)k, "trial %d offset of frame %d", trial, t);
+      int cnt = 0;
+      for (int j = 0; j < Ny; ++j)
+        if (m[(size_t)t * Ny + j]) {
+          CHECK(k < rows.size() && rows[k] == j, "trial %d frame %d row %d", trial, t, j);
+          ++k;
+          ++cnt;
+        }
+      expect_max = std::max(expect_max, cnt);
+    }
+    CHECK(k == rows.size() && off[Nt] == (int)k, "trial %d row count", trial);
+    CHECK(maxm == expect_max, "trial %d maxm %d, expected %d", trial, maxm, expect_max);
+    const int maxf = recon::mask_rows(full.data(), Nt, Ny, Nx, true, rows_f, off_f, &bt, &bj);
+    CHECK(maxf == maxm && rows_f == rows && off_f == off, "trial %d full mask differs from the row mask", trial);
+    if (Nx > 1) {
+      const int t = (int)(rng() % Nt), j = (int)(rng() % Ny), i = 1 + (int)(rng() % (Nx - 1));
+      full[((size_t)t * Ny + j) * Nx + i] ^= 1;
+      bt = bj = -1;
+      CHECK(recon::mask_rows(full.data(), Nt, Ny, Nx, true, rows_f, off_f, &bt, &bj) == -1 && bt == t && bj == j,
+            "trial %d flipped (%d, %d, %d) reported at (%d, %d)", trial, t, j, i, bt, bj);
+    }
+  }
+}
+
 int main() {
   check_fft_factor();
+  {
+    std::mt19937 rng(7);
+    check_mask_rows(rng);
+  }
   // the cardiac plan alone, and a plan with fewer columns than CTAs
   check_work_lists({2206203904LL / 8192}, {8192}, 152);
   check_work_lists({1000}, {100}, 152);
