@@ -156,8 +156,8 @@ int main() {
   check_work_lists({1000}, {100}, 152);
   // seeded uneven batches (the batched workload's shape mix), up to 255 slices
   std::mt19937 rng(64);
-  for (int trial = 0; trial < 20; ++trial) {
-    const int n = 2 + (int)(rng() % (trial < 18 ? 70 : 254));
+  for (int trial = 0; trial < 10; ++trial) {
+    const int n = 2 + (int)(rng() % (trial < 8 ? 70 : 254));
     std::vector<long long> cost(n);
     std::vector<int> ncols(n);
     const int ny[] = {128, 160, 192, 256}, nt[] = {16, 24, 32, 40};
