@@ -126,6 +126,15 @@ MUTATIONS = [
      [P(FR.test_kkt_alg1_with_redundant_haar_frame)]),
     ("psi-dft-not-unitary", "admm", 'return np.fft.fft(x, axis=0, norm="ortho")', "return np.fft.fft(x, axis=0)",
      [P(PI.test_kkt_dft_on_tiny_problem), P(PI.test_alg1_full_sampling_reaches_soft_threshold_closed_form)]),
+    ("psi-dft-adjoint-not-unitary", "admm", 'return np.fft.ifft(w, axis=0, norm="ortho")',
+     "return np.fft.ifft(w, axis=0)",
+     [P(PI.test_kkt_dft_on_tiny_problem), P(PI.test_objectives_closed_forms)]),
+    ("dft-matrix-sign", "admm", "return np.exp(-2j * np.pi * np.outer(q, q) / n) / np.sqrt(n)",
+     "return np.exp(2j * np.pi * np.outer(q, q) / n) / np.sqrt(n)",
+     [P(PI.test_gram_blocks_equal_dense_HtH, 0.0)]),
+    ("column-subset-wrong-columns", "admm", "self.b = self.b_full[:, :, self.cols]",
+     "self.b = self.b_full[:, :, :len(self.cols)]",
+     [P(PI.test_column_subset_is_exact)]),
     ("haar-detail-scale", "admm", "out.append((a - nxt) / 2.0)", "out.append((a - nxt) / np.sqrt(2.0))",
      [P(FR.test_tight_and_redundant, 8, 3), P(FR.test_channel_frequency_response_closed_form, 8, 2)]),
     # Objective, Eq. r_ratio, residuals
@@ -164,6 +173,9 @@ MUTATIONS = [
      [P(ST.test_stv_residuals_follow_the_duals_and_vanish)]),
     ("stv-dual-wrong-weight", "stv", "rd = mu1 ** 2 * sum(", "rd = mu2 ** 2 * sum(",
      [P(ST.test_zero_spatial_weight_is_temporal_tv)]),
+    ("stv-objective-unweighted", "stv", "return lam * float(sum(np.abs(c).sum() for c in stv_R(x, ws))) + fid(x)",
+     "return lam * float(sum(np.abs(c).sum() for c in stv_R(x, 1.0))) + fid(x)",
+     [P(ST.test_objective_is_lambda_l1_plus_fidelity)]),
     ("volume-z-weight-dropped", "stv", "wz * (x[1:] - x[:-1]))", "(x[1:] - x[:-1]))",
      [P(ST.test_volume_R_adjoint, (3, 2, 4, 5))]),
     ("haar-adjoint-shift-direction", "admm", "a = (a + np.roll(a, sh, axis=0)) / 2.0 + (d - np.roll(d, sh, axis=0)) / 2.0",
