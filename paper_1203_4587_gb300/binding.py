@@ -181,14 +181,16 @@ def _c64(t: torch.Tensor, dev=None) -> torch.Tensor:
     return t.contiguous()
 
 
-def _need(t, shape, name, where="cuda"):
-    """Returns ``t`` if it is a contiguous complex64 tensor of ``shape`` on
-    device type ``where`` (None: any); raises otherwise.  The library receives
-    raw pointers and cannot check the sizes of the buffers behind them."""
+def _need(t, shape, name, where="cuda", dtype=None):
+    """Returns ``t`` if it is a contiguous tensor of ``dtype`` (default
+    complex64) and ``shape`` on device type ``where`` (None: any); raises
+    otherwise.  The library receives raw pointers and cannot check the sizes
+    of the buffers behind them."""
+    dtype = torch.complex64 if dtype is None else dtype
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name}: a torch tensor is expected")
-    if t.dtype != torch.complex64:
-        raise TypeError(f"{name}: complex64 expected, got {t.dtype}")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: {dtype} expected, got {t.dtype}")
     if tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
     if not t.is_contiguous():
@@ -310,13 +312,8 @@ class Plan:
 
     def solve_quantized(self, q, out=None, info=True, stream=None):
         """Runs the reconstruction from 16-bit k-space ``q`` (a QuantizedKspace)."""
-        d, fs = q.data, q.frame_scale
-        if (not isinstance(d, torch.Tensor) or d.dtype != torch.int32 or tuple(d.shape) != self.kshape
-                or not d.is_contiguous() or d.device.type != "cuda"):
-            raise ValueError(f"q.data: a contiguous cuda int32 tensor of shape {self.kshape} is expected")
-        if (not isinstance(fs, torch.Tensor) or fs.dtype != torch.float32 or tuple(fs.shape) != (self.kshape[0],)
-                or fs.device.type != "cuda"):
-            raise ValueError(f"q.frame_scale: a cuda float32 tensor of shape ({self.kshape[0]},) is expected")
+        _need(q.data, self.kshape, "q.data", dtype=torch.int32)
+        _need(q.frame_scale, (self.kshape[0],), "q.frame_scale", dtype=torch.float32)
         if q.storage not in ("fp16", "bf16"):
             raise ValueError(f"q.storage: fp16 or bf16 expected, got {q.storage!r}")
         out = self._img() if out is None else _need(out, self.ishape, "out")
@@ -556,8 +553,7 @@ def gram_inverse_noalloc(mask_rows, sens_cols, mu, out=None, stream=None):
     if s.dim() != 3:
         raise ValueError(f"sens_cols: [nblk, Nc, Ny] expected, got shape {tuple(s.shape)}")
     nblk, Nc, Ny = s.shape
-    if tuple(m.shape) != (nblk, Ny) or m.device.type != "cuda":
-        raise ValueError(f"mask_rows: a cuda uint8 tensor of shape {(nblk, Ny)} is expected")
+    _need(m, (nblk, Ny), "mask_rows", dtype=torch.uint8)
     if out is None:
         out = torch.empty((nblk, Ny, Ny), dtype=torch.complex64, device="cuda")
     else:
