@@ -101,3 +101,43 @@ def test_struct_matches_header(name, cls):
     fields = re.findall(r"\b(float|int|double)\s+(\w+)\s*;", body)
     ctype = {"float": C.c_float, "int": C.c_int, "double": C.c_double}
     assert [(n, ctype[t]) for t, n in fields] == list(getattr(binding, cls)._fields_)
+
+
+def test_every_entry_point_rejects_null_and_empty_arguments(libpath):
+    """recon.h: NULL handles and empty or out-of-range counts give
+    RECON_ERR_INVALID_ARG (1) with a reason, before any device work; the
+    destroy calls are NULL-safe (0)."""
+    from paper_1203_4587_gb300 import binding
+    lib = binding.load(libpath)
+    out = C.c_void_p()
+    one = (C.c_void_p * 1)(None)
+    info = binding.Info()
+    buf = (C.c_double * 4)()
+    calls = {
+        "recon_plan_set_mu": lambda: lib.recon_plan_set_mu(None, 0.1, None),
+        "recon_solve_host": lambda: lib.recon_solve_host(None, None, None, None, None),
+        "recon_solve_kspace": lambda: lib.recon_solve_kspace(None, None, None, None, None),
+        "recon_get_trace": lambda: lib.recon_get_trace(None, buf, 4),
+        "recon_get_profile": lambda: lib.recon_get_profile(None, None),
+        "recon_apply_adjoint": lambda: lib.recon_apply_adjoint(None, None, None, None),
+        "recon_apply_forward": lambda: lib.recon_apply_forward(None, None, None, None),
+        "recon_apply_inverse": lambda: lib.recon_apply_inverse(None, None, None, None),
+        "recon_export_inverse": lambda: lib.recon_export_inverse(None, 0, 0, None, None),
+        "recon_autotune": lambda: lib.recon_autotune(None, None, None),
+        "recon_batch_create (NULL plans)": lambda: lib.recon_batch_create(C.byref(out), None, 1),
+        "recon_batch_create (n = 0)": lambda: lib.recon_batch_create(C.byref(out), one, 0),
+        "recon_volume_create (nz = 0)": lambda: lib.recon_volume_create(C.byref(out), one, 0, 1.0),
+        "recon_batch_solve": lambda: lib.recon_batch_solve(None, None, None, None),
+        "recon_batch_info": lambda: lib.recon_batch_info(None, C.byref(info), None),
+        "recon_batch_autotune": lambda: lib.recon_batch_autotune(None, None, None),
+        "recon_grad_create (n = 0)": lambda: lib.recon_grad_create(C.byref(out), one, 0, 5),
+        "recon_grad_forward": lambda: lib.recon_grad_forward(None, None, None, None),
+        "recon_grad_backward": lambda: lib.recon_grad_backward(None, None, None, None, None, None),
+    }
+    for name, call in calls.items():
+        assert call() == 1, name
+        assert lib.recon_last_error(), name
+    for destroy in (lib.recon_destroy, lib.recon_batch_destroy, lib.recon_grad_destroy):
+        assert destroy(None) == 0
+    for code in range(0, 9):
+        assert lib.recon_status_string(code)
