@@ -2,7 +2,8 @@
 
 The paper prints no worked example, so this fixture is a regression record of
 the oracle on the tiny workload (64x64 pixels, 8 frames, 4 coils, R=4,
-lambda=0.01, mu=0.1, rho=0.5): J(0..K) for both priors and ||x||.
+lambda=0.01, mu=0.1, rho=0.5): J(0..K) for both priors, ||x|| and the ADMM
+residuals of the last iteration.
 Run:  python tests/golden/make_golden.py
 """
 import json
@@ -27,7 +28,8 @@ def main():
                source="oracle (FP64) on synthdata tiny workload, seed 1")
     for prior in ("tv", "dft"):
         x, info = P.solve(prior, case.lam, case.mu, case.rho, iters)
-        out[prior] = dict(J=[float(v) for v in info["J"]], xnorm=float(np.linalg.norm(x)))
+        out[prior] = dict(J=[float(v) for v in info["J"]], xnorm=float(np.linalg.norm(x)),
+                          primal_res=float(info["primal_res"]), dual_res=float(info["dual_res"]))
     with open(os.path.join(HERE, "tiny_oracle.json"), "w") as f:
         json.dump(out, f, indent=1)
 

@@ -417,6 +417,8 @@ def test_golden_tiny_trajectory():
         x, info = P.solve(prior, case.lam, case.mu, iters=g["iters"])
         np.testing.assert_allclose(info["J"], g[prior]["J"], rtol=1e-12)
         assert abs(np.linalg.norm(x) - g[prior]["xnorm"]) < 1e-10 * g[prior]["xnorm"]
+        for key in ("primal_res", "dual_res"):
+            assert abs(info[key] - g[prior][key]) <= 1e-10 * g[prior][key]
 
 
 # --- the input generator ----------------------------------------------------
