@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-comparison", action="store_true")
+    ap.add_argument("--detail", default=None,
+                    help="also write the full record (notes, tunings, every timing) as JSON to this path")
     ap.add_argument("--grad-only", action="store_true",
                     help="only the differentiable-form measurement (one JSON line with its numbers)")
     return ap.parse_args()
@@ -91,6 +93,76 @@ def finite_json(v):
     if isinstance(v, (list, tuple)):
         return [finite_json(x) for x in v]
     return v
+
+
+def sig(v, n=4):
+    """v rounded to n significant digits (ints and non-numbers unchanged)."""
+    if isinstance(v, float) and math.isfinite(v) and v != 0.0:
+        return round(v, max(0, n - 1 - int(math.floor(math.log10(abs(v))))))
+    return v
+
+
+def compact_forms(line):
+    """The forms' headline numbers in a few hundred characters.  The printed
+    JSON line ends with this object, so a reader that keeps only the tail of
+    the output still sees every form's measurement."""
+    out = {}
+    if "variants" in line:
+        out["variants_iters_s"] = {k: sig(v) for k, v in line["variants"].items()}
+    if "stv_step" in line:
+        st = line["stv_step"]
+        out["stv_step"] = {"ms": sig(st["ms_per_iter"]), "frac": sig(st["frac_hbm"], 3)}
+    b = line.get("batched")
+    if b:
+        out["batched"] = ({"error": b["error"][:120]} if "error" in b else
+                          {"recons_s": sig(b["value"]), "ms": sig(b["ms_per_batch"]),
+                           "frac": sig(b["hbm_gbs_inverse_stream"] * 1e9 / b["peak_bps"], 3),
+                           "recons_s_with_plan": sig(b["recons_per_s_with_plan"], 3),
+                           "plan_s": sig(b["plan_s_total"], 3), "slices": b["slices"],
+                           "iters": b["iters_per_slice"]})
+    pr = line.get("precision")
+    if pr:
+        if "error" in pr:
+            out["precision"] = {"error": pr["error"][:120]}
+        else:
+            out["precision"] = {k: {"iters_s": sig(v["iters_per_s"]), "inv_frac": sig(v["inverse_frac"], 3),
+                                    "inv_share": sig(v["inverse_share"], 3)}
+                                for k, v in pr.items() if isinstance(v, dict)}
+    g = line.get("grad")
+    if g:
+        out["grad"] = ({"error": g["error"][:120]} if "error" in g else
+                       {"fwd_ms": sig(g["forward_ms"]), "bwd_ms": sig(g["backward_ms"]),
+                        "bwd_over_fwd": sig(g["backward_over_forward"], 3), "fwd_frac": sig(g["forward_frac"], 3),
+                        "bwd_frac": sig(g["backward_frac"], 3)})
+    lc = line.get("library_comparison")
+    if lc:
+        out["library_iters_s"] = sig(lc["iters_per_s"]) if "iters_per_s" in lc else lc.get("error", "")[:120]
+    ca = line.get("cpu_baseline_all_cores")
+    if ca and "value" in ca:
+        out["cpu_all_cores"] = {"value": sig(ca["value"]), "cores": ca["cores"]}
+    return out
+
+
+def compact_line(line):
+    """The JSON line bench.py prints: the contract's keys, then the forms."""
+    keys = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+            "vs_baseline", "dtype", "data", "gpu_launches", "config", "roofline", "cpu_baseline", "clocks", "e2e",
+            "plan_s", "set_mu_s", "check")
+    out = {k: line[k] for k in keys if k in line}
+    for k in ("value", "ms_per_step", "plan_s", "set_mu_s"):
+        if k in out:
+            out[k] = sig(out[k], 6)
+    if "e2e" in out:
+        out["e2e"] = dict(out["e2e"], value=sig(out["e2e"]["value"], 6))
+    if "check" in out:
+        out["check"] = {k: sig(v, 6) for k, v in out["check"].items()}
+    rf = out.get("roofline")
+    if rf:
+        out["roofline"] = {k: (sig(v) if k != "traffic" else v) for k, v in rf.items()}
+    forms = compact_forms(line)
+    if forms:
+        out["forms"] = forms
+    return out
 
 
 def reduce_max(x, dist, device):
@@ -266,20 +338,16 @@ def oracle_sample_all_cores(prior, ncols=2, budget=10.0):
 
 def cpu_baseline_obj(res, prior):
     return {"value": res["iters_per_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 NumPy oracle, {prior} prior, {res['sample_iters']} iterations on "
-                       f"{res['ncols']} of {WORKLOAD['Nx']} columns (all 32 frames), single thread; "
-                       f"per-iteration time scaled by Nx/{res['ncols']} (columns are independent) plus the "
-                       f"full-size H'y prologue ({res['prologue_s']:.2f} s); plan (eigh) excluded")}
+            "sample": (f"FP64 oracle, 1 thread: {res['sample_iters']} iters on {res['ncols']}/{WORKLOAD['Nx']} "
+                       f"columns x Nx/{res['ncols']}, + full H'y ({res['prologue_s']:.2f} s); plan excluded")}
 
 
 def config_obj(prior, storage):
     w = WORKLOAD
-    return {"workload": (f"cardiac {w['Nx']}x{w['Ny']}x{w['Nt']} frames x{w['Nc']} coils, R={w['R']}, "
-                         f"{prior.upper()} prior, lambda={w['lam']}, mu={w['mu']}, rho={w['rho']}, "
-                         f"{w['iters']} ADMM iterations per solve, objective every iteration"),
-            "Nx": w["Nx"], "Ny": w["Ny"], "Nt": w["Nt"], "Nc": w["Nc"], "R": w["R"], "prior": prior,
-            "iters_per_step": w["iters"], "storage": storage, "parallelism": "replicas (one slice per GPU)",
-            "l2": "inputs larger than L2: 2.16 GB of packed inverses streamed per iteration (L2 126 MB)"}
+    return {"workload": (f"cardiac {w['Nx']}x{w['Ny']}x{w['Nt']}fr x{w['Nc']}coils R={w['R']} {prior.upper()} "
+                         f"lambda={w['lam']} mu={w['mu']} rho={w['rho']}, {w['iters']} iters/solve, J every iter"),
+            "prior": prior, "iters_per_step": w["iters"], "storage": storage, "parallelism": "replicas",
+            "l2": "inputs > L2: 2.16 GB of inverses per iteration"}
 
 
 def make_batched_inputs(nslices, seed=64):
@@ -348,6 +416,7 @@ def measure_batched(nslices, storage, steps=3):
             "input_gen_s": gen_s, "iters_done": iters, "inverse_bytes_total": A_bytes,
             "inverse_bytes_stored": A_stored, "tuning": tuning,
             "hbm_gbs_inverse_stream": A_bytes * shapes[0]["iters"] / (ms / 1e3) / 1e9,
+            "peak_bps": hbm_peak()[0] * 1e9,
             "note": ("Nx, Ny in {128,160,192,256}, Nt in {16,24,32,40}, Nc in {8,12,16}, R in {4,6,8}, TV, "
                      "lambda=0.005, mu=0.1; all slices in one launch per step, the batched solve replayed "
                      "from a captured CUDA graph; plan (double-float inversion) reported separately")}
@@ -503,7 +572,8 @@ def measure_grad(storage, steps=5):
                   prior="tv", rho=c.rho, max_iters=iters, objective=0, storage=storage) for c in cases]
     ks = [torch.from_numpy(c.kspace.astype(np.complex64)).cuda() for c in cases]
     xt = [torch.from_numpy(c.x_true.astype(np.complex64)).cuda() for c in cases]
-    g = Grad(plans, checkpoint_every=5)
+    every = 5
+    g = Grad(plans, checkpoint_every=every)
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     fwd, bwd = [], []
@@ -523,8 +593,19 @@ def measure_grad(storage, steps=5):
     for p in plans:
         p.close()
     f, b = statistics.median(fwd), statistics.median(bwd)
+    # algorithmic bytes: the packed inverses (the Hermitian triangle of every
+    # column) streamed once per inverse launch: K forward steps; K reverse
+    # steps plus K - K/every recomputed steps backward
+    Nt, Ny, Nx = cases[0].x_true.shape
+    a_bytes = len(cases) * (8 if storage == "fp32" else 4) * Nx * Nt * Ny * (Ny + 1) // 2
+    n_fwd, n_bwd = iters, iters + (iters - iters // every)
+    peak, _ = hbm_peak()
+    fgbs = n_fwd * a_bytes / (f / 1e3) / 1e9
+    bgbs = n_bwd * a_bytes / (b / 1e3) / 1e9
     return {"forward_ms": f, "backward_ms": b, "backward_over_forward": b / f, "slices": 4,
-            "iters": iters, "checkpoint_every": 5,
+            "iters": iters, "checkpoint_every": every, "inverse_streams_forward": n_fwd,
+            "inverse_streams_backward": n_bwd, "inverse_bytes_per_stream": a_bytes,
+            "forward_gbs": fgbs, "backward_gbs": bgbs, "forward_frac": fgbs / peak, "backward_frac": bgbs / peak,
             "note": ("192x192x24 frames x8 coils, R=8, TV, lambda=0.005, mu=0.1, rho=0.5; forward = H'y + 20 "
                      "steps keeping checkpoints; backward = segment recomputation + reverse steps + dL/dy = H b_bar "
                      "+ the lambda/mu gradients (host read)")}
@@ -636,7 +717,7 @@ def run_native(args):
     except Exception:
         pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (copy)",
+                "traffic": traffic, "peak_source": f"{peak_kind} copy",
                 "kernel": "k_col_inverse", "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_s * 1e3,
                 "share_of_step": prof.inverse_ms / max(prof.solve_ms, 1e-9),
                 "temporal_avg_ms": prof.temporal_ms / max(prof.temporal_launches, 1)}
@@ -662,13 +743,13 @@ def run_native(args):
         el = reduce_max(time.perf_counter() - t0, dist, "cuda")
         line["e2e"] = {"value": weak_value(world, n_e2e, w["iters"], el * 1e3), "unit": UNIT,
                        "h2d_bytes_per_step": int(kh.numel() * 8), "d2h_bytes_per_step": int(ih.numel() * 8),
-                       "step": "recon_solve_host: k-space H2D (pinned), prologue, 100 iterations, image D2H"}
+                       "step": "recon_solve_host: pinned H2D, solve, D2H"}
 
     if not args.no_variants and rank == 0:
         var = {}
-        for name, prior, lam in (("dft_lambda0.005", "dft", 0.005), ("tv_lambda0.02", "tv", 0.02),
-                                 ("dft_lambda0.02", "dft", 0.02), ("haar2_lambda0.005", "haar", 0.005),
-                                 ("stv_w1_cg5_lambda0.005", "stv", 0.005)):
+        for name, prior, lam in (("dft", "dft", 0.005), ("tv_l0.02", "tv", 0.02),
+                                 ("dft_l0.02", "dft", 0.02), ("haar2", "haar", 0.005),
+                                 ("stv_cg5", "stv", 0.005)):
             if prior == args.prior and lam == w["lam"]:
                 continue
             p2 = Plan(mask, sens, lam, w["mu"], prior=prior, rho=w["rho"], max_iters=w["iters"],
@@ -743,7 +824,10 @@ def run_native(args):
         except Exception as e:  # report, never fake
             line["cpu_baseline_all_cores"] = {"error": str(e)[:300]}
     if rank == 0:
-        print(json.dumps(finite_json(line)), flush=True)
+        if args.detail:
+            with open(args.detail, "w") as f:
+                json.dump(finite_json(line), f, indent=1)
+        print(json.dumps(finite_json(compact_line(line)), separators=(",", ":")), flush=True)
     plan.close()
     if dist is not None:
         dist.destroy_process_group()

@@ -437,14 +437,19 @@ recon_status recon_export_inverse(recon_plan* plan, int i, int t, float* dense, 
  *   sens  device complex64 [nblk][Nc][Ny] (the coil profiles of the block's column)
  *   out   device complex64 [nblk][Ny][Ny], dense Hermitian, written
  * Allocates nothing: the FP64 workspace is a fixed 16 MiB static device array
- * that every GPU loading this library holds until exit.  The first call on a
+ * that every GPU loading this library holds until exit.  It holds
+ * floor((16 MiB - 256) / (16 Ny^2)) workspaces, and that many blocks are
+ * factorised at once, one CTA each (15 at Ny = 256, 3 at Ny = 512); from
+ * Ny = 725 on only one fits, so all blocks run one after another on a single
+ * SM: large Ny is far slower here than in recon_plan_create.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) with the
  * device current; make that first call before any stream capture.  All calls
  * share the array, so calls that overlap on the GPU race; the call
  * synchronises `stream` before returning.
- * Errors: INVALID_ARG; UNSUPPORTED when Ny > 1023 (one Ny x Ny FP64 workspace
- * must fit in the array) or (Nc + 2) * Ny > 12800; NONFINITE for a block that
- * is not positive definite; CUDA. */
+ * Errors: INVALID_ARG (also a non-finite mu); UNSUPPORTED when Ny > 1023 (one
+ * Ny x Ny FP64 workspace must fit in the array) or (Nc + 2) * Ny > 12800;
+ * NONFINITE for a block that is not positive definite or meets a non-finite
+ * pivot (a non-finite coil profile); CUDA. */
 recon_status recon_gram_inverse_noalloc(int Ny, int Nc, int nblk, const uint8_t* mask, const float* sens, float mu,
                                         float* out, void* stream);
 

@@ -8,12 +8,15 @@
 // workspace in a fixed file-scope device array instead.
 //
 // The array is kScratchBytes (16 MiB) per GPU that loads the library and lives
-// until process exit.  It holds one Ny x Ny FP64 complex workspace per
-// resident CTA (Ny = 256: 15 CTAs; Ny = 1023: one), plus a status word.  In
+// until process exit.  It holds one Ny x Ny FP64 complex workspace per CTA
+// plus a status word, so floor((16 MiB - 256) / (16 Ny^2)) blocks are
+// factorised at once (Ny = 256: 15; Ny = 512: 3; Ny >= 725: one CTA, and the
+// blocks then run one after another on a single SM).  In
 // host code the array's name is only a host-side stand-in: the device address
 // is obtained once per device with cudaGetSymbolAddress and passed to the
 // kernel.  Every call shares the array, so calls that overlap on the GPU race
 // on it.
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -75,7 +78,7 @@ __global__ void __launch_bounds__(kNoAllocThreads) k_gram_inverse_static(
     bool bad = false;
     for (int k = 0; k < n; ++k) {
       double d = W[(size_t)k * n + k].x;
-      if (!(d > 0.0)) { bad = true; d = 1.0; }
+      if (!(d > 0.0) || !isfinite(d)) { bad = true; d = 1.0; }   // also NaN and +Inf
       d = sqrt(d);
       const double inv = 1.0 / d;
       for (int j = k + 1 + tid; j < n; j += kNoAllocThreads) {
@@ -155,7 +158,7 @@ using namespace recon;
 
 extern "C" recon_status recon_gram_inverse_noalloc(int Ny, int Nc, int nblk, const uint8_t* mask, const float* sens,
                                                    float mu, float* out, void* stream) {
-  if (Ny < 1 || Nc < 1 || nblk < 0 || !mask || !sens || !out || !(mu > 0.f))
+  if (Ny < 1 || Nc < 1 || nblk < 0 || !mask || !sens || !out || !(mu > 0.f) || !std::isfinite(mu))
     return na_fail(RECON_ERR_INVALID_ARG, "bad argument");
   const size_t ws = (size_t)Ny * Ny * sizeof(double2);
   if (ws > kScratchBytes - kScratchStatusBytes)
@@ -186,7 +189,7 @@ extern "C" recon_status recon_gram_inverse_noalloc(int Ny, int Nc, int nblk, con
   const int per = (int)((kScratchBytes - kScratchStatusBytes) / ws);
   const int grid = nblk < per ? nblk : per;
   e = cudaMemsetAsync(base, 0, sizeof(int), s);  // status word of this call
-  if (e == cudaSuccess)   // always: static shared memory counts toward the 48 KB default
+  if (e == cudaSuccess)   // the dynamic shared-memory limit is a per-device attribute: cheap to set every call
     e = cudaFuncSetAttribute(k_gram_inverse_static, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) {
     k_gram_inverse_static<<<grid, kNoAllocThreads, smem, s>>>(mask, reinterpret_cast<const float2*>(sens), Ny, Nc,

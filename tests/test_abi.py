@@ -83,6 +83,10 @@ def test_invalid_arguments_rejected_before_any_cuda_call(libpath):
     st = lib.recon_plan_create_slab(C.byref(h), 8, 4, 2, 1, C.cast(mask, C.c_void_p), C.cast(sens, C.c_void_p),
                                     0.01, 0.1, 3, None, 0, 4, None)
     assert st == 7  # the spatio-temporal prior couples columns: no slab plans
+    for mu in (0.0, float("inf"), float("nan")):    # the allocation-free inverse checks mu on the host
+        st = lib.recon_gram_inverse_noalloc(8, 1, 1, C.cast(mask, C.c_void_p), C.cast(sens, C.c_void_p), mu,
+                                            C.cast(sens, C.c_void_p), None)
+        assert st == 1, mu
     for bad_limit in (0, 2000001):               # the wait self-test checks its limit before launching
         assert lib.recon_selftest_wait_timeout(bad_limit, None, None) == 1
     assert lib.recon_destroy(None) == 0

@@ -7,7 +7,8 @@ dL/dx_K = 2 (x_K - x_true), so only the reverse pass is under test (the
 forward image is checked separately at the solver tolerance TOL).
 
 The gradient is only piecewise smooth: the soft threshold's Jacobian jumps
-where |a| = tau (reading r7).  The GPU decides |a| > tau on its FP32 states,
+where |a| = tau (the threshold gives exactly 0 for |a| <= tau and its
+derivative there is taken from that zero side).  The GPU decides |a| > tau on its FP32 states,
 the oracle on its FP64 states, and the two trajectories differ by ~1e-6
 relative, so any |a| within about 1e-5 relative of tau may take opposite
 branches on the two sides.  Hence two bounds:

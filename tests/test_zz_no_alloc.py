@@ -39,6 +39,46 @@ def test_noalloc_inverse_matches_plan_twice():
         assert err < 2e-7, (call, err)
 
 
+def test_noalloc_more_blocks_than_workspaces():
+    """Ny = 512: the 16 MiB array holds three 4 MiB workspaces, so five blocks
+    run on three CTAs and two of them factorise a second block in the same
+    workspace (the grid-stride path)."""
+    from paper_1203_4587_gb300 import Plan, binding
+    case = synthdata.make_case("tiny", Nx=5, Ny=512, Nt=1, Nc=3)
+    sens = torch.from_numpy(case.sens.astype(np.complex64)).cuda()
+    plan = Plan(case.mask.astype(np.uint8), sens, case.lam, case.mu, max_iters=1)
+    ref = torch.stack([plan.export_inverse(i, 0) for i in range(5)])
+    mask_rows = torch.from_numpy(np.repeat(case.mask[:1], 5, axis=0).astype(np.uint8)).cuda()
+    sens_cols = torch.stack([sens[:, :, i] for i in range(5)]).contiguous()
+    out = torch.full_like(ref, float("nan"))
+    binding.gram_inverse_noalloc(mask_rows, sens_cols, case.mu, out=out)
+    torch.cuda.synchronize()
+    a = out.cpu().numpy().astype(np.complex128)
+    b = ref.cpu().numpy().astype(np.complex128)
+    for blk in range(5):
+        err = np.linalg.norm(a[blk] - b[blk]) / np.linalg.norm(b[blk])
+        assert err < 2e-7, (blk, err)
+    plan.close()
+
+
+def test_noalloc_reports_a_non_finite_coil_profile():
+    """An infinite coil sample makes a non-finite pivot: the call returns
+    RECON_ERR_NONFINITE (6), and a following call with finite input is fine."""
+    from paper_1203_4587_gb300 import binding
+    lib = binding.load()
+    Ny, Nc = 32, 2
+    m = torch.ones((2, Ny), dtype=torch.uint8, device="cuda")
+    s = torch.full((2, Nc, Ny), 0.5 + 0.0j, dtype=torch.complex64, device="cuda")
+    s[1, 0, 3] = complex(float("inf"), 0.0)
+    o = torch.empty((2, Ny, Ny), dtype=torch.complex64, device="cuda")
+    st = lib.recon_gram_inverse_noalloc(Ny, Nc, 2, binding._ptr(m), binding._ptr(s), 0.1, binding._ptr(o), None)
+    assert st == 6, st
+    s[1, 0, 3] = 0.5
+    st = lib.recon_gram_inverse_noalloc(Ny, Nc, 2, binding._ptr(m), binding._ptr(s), 0.1, binding._ptr(o), None)
+    assert st == 0, lib.recon_last_error()
+    assert torch.isfinite(torch.view_as_real(o)).all()
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     from paper_1203_4587_gb300 import binding
     lib = binding.load()
