@@ -49,10 +49,14 @@ void fill_twiddles_host(int n, float2* tw) {
   }
 }
 
-void fill_twiddles_host64(int n, double2* tw) {
+// (re_hi, re_lo, im_hi, im_lo): each FP64 value split into its FP32 rounding
+// and the FP32 rounding of the remainder
+void fill_twiddles_host_df(int n, float4* tw) {
   for (int k = 0; k < n; ++k) {
     const double a = -2.0 * M_PI * (double)k / (double)n;
-    tw[k] = make_double2(std::cos(a), std::sin(a));
+    const double c = std::cos(a), s = std::sin(a);
+    const float ch = (float)c, sh = (float)s;
+    tw[k] = make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh));
   }
 }
 
@@ -66,7 +70,7 @@ static FftPlanT<T> fft_plan_t(int n, const T* d_tw) {
 }
 
 FftPlanDev make_fft_plan_host(int n, const float2* d_tw) { return fft_plan_t<float2>(n, d_tw); }
-FftPlanDev64 make_fft_plan_host64(int n, const double2* d_tw) { return fft_plan_t<double2>(n, d_tw); }
+FftPlanDf make_fft_plan_host_df(int n, const dc* d_tw) { return fft_plan_t<dc>(n, d_tw); }
 
 }  // namespace recon
 
@@ -250,7 +254,8 @@ recon_status plan_objective(recon_plan* p, const float2* x, double* acc, cudaStr
   ObjParams o{};
   o.Nx = p->Nx; o.Ny = p->Ny; o.Nt = p->Nt; o.Nc = p->Nc;
   o.ncg = p->obj_coils > 0 ? std::min(p->obj_coils, coil_group_for(p->Nc, p->Ny)) : coil_group_for(p->Nc, p->Ny);
-  o.x = x; o.sens = p->sens; o.rows = p->rows; o.rowoff = p->rowoff; o.fy = p->fy;
+  o.x = x; o.sens = p->sens; o.rows = p->rows; o.rowoff = p->rowoff; o.rowidx = p->rowidx; o.fy = p->fy;
+  o.grid = 8 * p->num_sms;
   o.yhat = p->storage ? p->yhat_lp : static_cast<const void*>(p->yhat);
   o.ystorage = p->storage;
   o.yscale = p->yscale;
@@ -271,23 +276,23 @@ recon_status plan_to_user(recon_plan* p, const float2* in, float2* out, cudaStre
   return RECON_OK;
 }
 
-// H'y in FP64 (rounded once to FP32), the FP32 hybrid data for J(k) and
+// H'y in double-float arithmetic (rounded once to FP32), the FP32 hybrid data for J(k) and
 // ||y||^2 (into *yy, which must be zeroed first).
-recon_status plan_adjoint64(recon_plan* p, const void* kspace, int kstorage, const float* kscale, float2* yhat32,
-                            float2* b, double* yy, cudaStream_t s) {
-  RC(launch_hybrid_rows64(kspace, kstorage, kscale, p->yhat64, yhat32, yy, p->rows, p->rowoff, p->maxm, p->Nx_full,
-                          p->Ny, p->Nt, p->Nc, p->fx64, p->rows_per_block, s, p->i0, p->Nx));
-  RC(launch_adjoint_combine64(p->yhat64, p->sens, b, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fy64,
-                              p->combine_coils, s));
+recon_status plan_adjoint_df(recon_plan* p, const void* kspace, int kstorage, const float* kscale,
+                             float2* yhat32, float2* b, double* yy, cudaStream_t s) {
+  RC(launch_hybrid_rows_df(kspace, kstorage, kscale, p->yhat_df, yhat32, yy, p->rows, p->rowoff, p->maxm,
+                           p->Nx_full, p->Ny, p->Nt, p->Nc, p->fxdf, p->rows_per_block, s, p->i0, p->Nx));
+  RC(launch_adjoint_combine_df(p->yhat_df, p->sens, b, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fydf,
+                               p->combine_coils, s));
   return RECON_OK;
 }
 
-// FP32 storage: the FP64 prologue above (the 1e-5 bar needs it).  16-bit
+// FP32 storage: the double-float prologue above (the 1e-5 bar needs it).  16-bit
 // storage: FP32 butterflies and accumulation, the hybrid data kept in 16 bits
 // with per-frame power-of-two scales (its FP32 values pass through tmp_b).
 recon_status plan_prologue(recon_plan* p, const void* kspace, int kstorage, const float* kscale, cudaStream_t s) {
   RC(cudaMemsetAsync(p->yy, 0, sizeof(double), s));
-  if (p->storage == 0) return plan_adjoint64(p, kspace, kstorage, kscale, p->yhat, p->b, p->yy, s);
+  if (p->storage == 0) return plan_adjoint_df(p, kspace, kstorage, kscale, p->yhat, p->b, p->yy, s);
   RC(cudaMemsetAsync(p->ymax, 0, (size_t)p->Nt * sizeof(unsigned), s));
   RC(launch_hybrid_rows(kspace, kstorage, kscale, p->tmp_b, p->yy, p->ymax, p->rows, p->rowoff, p->maxm, p->Nx_full,
                         p->Ny, p->Nt, p->Nc, p->fx, p->rows_per_block, s, p->i0, p->Nx));
@@ -414,12 +419,13 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
   PC(p->alloc((void**)&p->sens, (size_t)Nx * Nc * Ny * sizeof(float2)));
   PC(p->alloc((void**)&p->rows, std::max<size_t>(1, p->h_rows.size()) * sizeof(int)));
   PC(p->alloc((void**)&p->rowoff, (Nt + 1) * sizeof(int)));
+  PC(p->alloc((void**)&p->rowidx, (size_t)Nt * Ny * sizeof(short)));
   PC(p->alloc((void**)&p->tw_x, Nxf * sizeof(float2)));
   PC(p->alloc((void**)&p->tw_y, Ny * sizeof(float2)));
   PC(p->alloc((void**)&p->tw_t, Nt * sizeof(float2)));
-  PC(p->alloc((void**)&p->tw64_x, Nxf * sizeof(double2)));
-  PC(p->alloc((void**)&p->tw64_y, Ny * sizeof(double2)));
-  PC(p->alloc((void**)&p->yhat64, std::max<size_t>(1, (size_t)p->total_rows * Nx * Nc) * sizeof(double2)));
+  PC(p->alloc((void**)&p->twdf_x, Nxf * sizeof(dc)));
+  PC(p->alloc((void**)&p->twdf_y, Ny * sizeof(dc)));
+  PC(p->alloc((void**)&p->yhat_df, std::max<size_t>(1, (size_t)p->total_rows * Nx * Nc) * sizeof(dc)));
   PC(p->alloc((void**)&p->thomas, Nt * sizeof(float)));
   const size_t nyhat = std::max<size_t>(1, (size_t)p->total_rows * Nx * Nc);
   if (o.storage == RECON_STORAGE_FP32) {
@@ -470,13 +476,13 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
   fill_twiddles_host(Nt, tw.data());
   PC(cudaMemcpy(p->tw_t, tw.data(), Nt * sizeof(float2), cudaMemcpyHostToDevice));
   {
-    std::vector<double2> tw64(std::max(Nxf, Ny));
-    fill_twiddles_host64(Nxf, tw64.data());
-    PC(cudaMemcpy(p->tw64_x, tw64.data(), Nxf * sizeof(double2), cudaMemcpyHostToDevice));
-    fill_twiddles_host64(Ny, tw64.data());
-    PC(cudaMemcpy(p->tw64_y, tw64.data(), Ny * sizeof(double2), cudaMemcpyHostToDevice));
-    p->fx64 = make_fft_plan_host64(Nxf, p->tw64_x);
-    p->fy64 = make_fft_plan_host64(Ny, p->tw64_y);
+    std::vector<float4> twd(std::max(Nxf, Ny));
+    fill_twiddles_host_df(Nxf, twd.data());
+    PC(cudaMemcpy(p->twdf_x, twd.data(), Nxf * sizeof(float4), cudaMemcpyHostToDevice));
+    fill_twiddles_host_df(Ny, twd.data());
+    PC(cudaMemcpy(p->twdf_y, twd.data(), Ny * sizeof(float4), cudaMemcpyHostToDevice));
+    p->fxdf = make_fft_plan_host_df(Nxf, p->twdf_x);
+    p->fydf = make_fft_plan_host_df(Ny, p->twdf_y);
   }
   p->fx = make_fft_plan_host(Nxf, p->tw_x);
   p->fy = make_fft_plan_host(Ny, p->tw_y);
@@ -486,6 +492,12 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
   if (!p->h_rows.empty())
     PC(cudaMemcpy(p->rows, p->h_rows.data(), p->h_rows.size() * sizeof(int), cudaMemcpyHostToDevice));
   PC(cudaMemcpy(p->rowoff, p->h_rowoff.data(), (Nt + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  {
+    std::vector<short> ri((size_t)Nt * Ny, (short)-1);
+    for (int t = 0; t < Nt; ++t)
+      for (int m = p->h_rowoff[t]; m < p->h_rowoff[t + 1]; ++m) ri[(size_t)t * Ny + p->h_rows[m]] = (short)(m - p->h_rowoff[t]);
+    PC(cudaMemcpy(p->rowidx, ri.data(), ri.size() * sizeof(short), cudaMemcpyHostToDevice));
+  }
 
   // sensitivities -> [Nx][Nc][Ny]
   {
@@ -692,7 +704,7 @@ recon_status recon_apply_adjoint(recon_plan* p, const float* kspace, float* imag
   if (!p || !kspace || !image) return fail(RECON_ERR_INVALID_ARG, "NULL argument");
   if (p->Nx != p->Nx_full) return fail(RECON_ERR_UNSUPPORTED, "H' of a slab plan: use a whole plan");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  recon_status st = plan_adjoint64(p, kspace, 0, nullptr, p->tmp_b, p->tmp_a, nullptr, s);
+  recon_status st = plan_adjoint_df(p, kspace, 0, nullptr, p->tmp_b, p->tmp_a, nullptr, s);
   if (st != RECON_OK) return st;
   return plan_to_user(p, p->tmp_a, reinterpret_cast<float2*>(image), s);
 }

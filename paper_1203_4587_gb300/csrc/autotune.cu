@@ -157,17 +157,17 @@ recon_status tune_plan(recon_plan* p, cudaStream_t s, recon_tuning* t) {
   RC(cudaMalloc(&k, nk * sizeof(float2)));
   struct Free { void* q; ~Free() { cudaFree(q); } } guard{k};
   RC(fill(k, nk, 11u, s));
-  const bool fp64 = p->storage == 0;
+  const bool wide = p->storage == 0;   // FP32 storage: the double-float prologue
   float best = 3.4e38f;
   int best_g = 0;
   for (int g : {1, 2, 4, 8}) {
-    if (g > row_group_max(p->Nx_full, fp64)) break;
+    if (g > row_group_max(p->Nx_full, wide)) break;
     p->rows_per_block = g;
     float ms = 0.f;
     auto run = [&]() -> recon_status {
-      if (fp64) {
-        RC(launch_hybrid_rows64(k, 0, nullptr, p->yhat64, p->yhat, nullptr, p->rows, p->rowoff, p->maxm, p->Nx_full,
-                                p->Ny, p->Nt, p->Nc, p->fx64, g, s, p->i0, p->Nx));
+      if (wide) {
+        RC(launch_hybrid_rows_df(k, 0, nullptr, p->yhat_df, p->yhat, nullptr, p->rows, p->rowoff, p->maxm,
+                                 p->Nx_full, p->Ny, p->Nt, p->Nc, p->fxdf, g, s, p->i0, p->Nx));
       } else {
         RC(launch_hybrid_rows(k, 0, nullptr, p->tmp_b, nullptr, p->ymax, p->rows, p->rowoff, p->maxm, p->Nx_full,
                               p->Ny, p->Nt, p->Nc, p->fx, g, s, p->i0, p->Nx));
@@ -182,12 +182,12 @@ recon_status tune_plan(recon_plan* p, cudaStream_t s, recon_tuning* t) {
   best = 3.4e38f;
   int best_c = 0;
   for (int c : {1, 2, 4, 8}) {
-    if (c > std::max(1, std::min(p->Nc, coil_group_max(p->Nc, p->Ny, fp64)))) break;
+    if (c > std::max(1, std::min(p->Nc, coil_group_max(p->Nc, p->Ny, wide)))) break;
     float ms = 0.f;
     auto run = [&]() -> recon_status {
-      if (fp64) {
-        RC(launch_adjoint_combine64(p->yhat64, p->sens, p->tmp_a, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc,
-                                    p->fy64, c, s));
+      if (wide) {
+        RC(launch_adjoint_combine_df(p->yhat_df, p->sens, p->tmp_a, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc,
+                                     p->fydf, c, s));
       } else {
         RC(launch_adjoint_combine(p->tmp_b, p->sens, p->tmp_a, p->rows, p->rowoff, p->Nx, p->Ny, p->Nt, p->Nc, p->fy,
                                   p->storage, p->yhat_lp, p->ymax, p->yscale, c, s));

@@ -15,6 +15,8 @@
 
 #include <cuda_runtime.h>
 
+#include "common.cuh"
+
 namespace recon {
 
 struct df {
@@ -89,12 +91,41 @@ __device__ __forceinline__ df df_from_double(double a) {
 }
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
-// complex double-float
-struct dc {
+// complex double-float (16 bytes: one float4 in memory)
+struct __align__(16) dc {
   df re, im;
 };
 
 __device__ __forceinline__ float4 dc_pack(dc a) { return make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
 __device__ __forceinline__ dc dc_unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
+
+// The complex operations under the names the templated FFT and operator
+// kernels use for float2 and double2, so they run unchanged in double-float.
+__device__ __forceinline__ dc c_add(dc a, dc b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ dc c_sub(dc a, dc b) { return {df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+__device__ __forceinline__ dc c_mul(dc a, dc b) {
+  return {df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ void c_fma(dc& acc, dc a, dc b) { acc = c_add(acc, c_mul(a, b)); }
+// acc += conj(a) b
+__device__ __forceinline__ void c_fmac(dc& acc, dc a, dc b) {
+  acc.re = df_add(acc.re, df_add(df_mul(a.re, b.re), df_mul(a.im, b.im)));
+  acc.im = df_add(acc.im, df_sub(df_mul(a.re, b.im), df_mul(a.im, b.re)));
+}
+// scaling by an FP32 number (a power of two in practice: exact) or by an
+// FP64 one (1/sqrt(n), taken to double length first)
+__device__ __forceinline__ dc c_scale(dc a, float s) { return {df_mul(a.re, df_make(s)), df_mul(a.im, df_make(s))}; }
+__device__ __forceinline__ dc c_scale(dc a, double s) {
+  const df f = df_from_double(s);
+  return {df_mul(a.re, f), df_mul(a.im, f)};
+}
+template <> __device__ __forceinline__ dc c_zero<dc>() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+template <> __device__ __forceinline__ dc from_f2<dc>(float2 v) { return {{v.x, 0.f}, {v.y, 0.f}}; }
+// one rounding of the double-length value to FP32 (|lo| <= ulp(hi)/2)
+__device__ __forceinline__ float2 to_f2(dc z) { return make_float2(z.re.hi + z.re.lo, z.im.hi + z.im.lo); }
+__device__ __forceinline__ double c_abs2d(dc a) {
+  const double r = df_to_double(a.re), i = df_to_double(a.im);
+  return r * r + i * i;
+}
 
 }  // namespace recon

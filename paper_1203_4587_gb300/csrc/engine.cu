@@ -244,6 +244,8 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
   e->levels = p0->opts.frame_levels;
   e->storage = p0->storage;
   e->obj = p0->opts.objective != 0 || p0->opts.tol > 0.0;
+  e->stop_test = false;
+  for (int q = 0; q < n; ++q) e->stop_test = e->stop_test || plans[q]->opts.tol > 0.0;
   e->fused = e->obj && p0->opts.objective != 2 && p0->storage == 0;
   for (int q = 1; q < n; ++q) {
     const recon_plan* p = plans[q];
@@ -524,7 +526,7 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
     else st = launch_tmp_set(e, k - 1, s);
     if (st != RECON_OK) return st;
     if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, false, s);
-    if (e->obj) RC(launch_finalize(e->d_fin, e->n, k - 1, s));
+    if (e->stop_test) RC(launch_finalize(e->d_fin, e->n, k - 1, k - 1, s));
     if (k == K && K >= 2 && (e->prior == RECON_PRIOR_DFT || e->prior == RECON_PRIOR_HAAR))   // xhat_{K-1}
       for (recon_plan* p : e->plans)
         RC(cudaMemcpyAsync(p->res_prev, p->x, p->nimg() * sizeof(float2), cudaMemcpyDeviceToDevice, s));
@@ -537,7 +539,8 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
   }
   if (e->obj) {
     if ((st = launch_tmp_set(e, K, s)) != RECON_OK) return st;
-    RC(launch_finalize(e->d_fin, e->n, K, s));
+    // with a fixed iteration count J(0) .. J(K) are formed here, in one launch
+    RC(launch_finalize(e->d_fin, e->n, e->stop_test ? K : 0, K, s));
   }
   for (recon_plan* p : e->plans)
     if ((st = launch_residuals(p, s)) != RECON_OK) return st;

@@ -14,12 +14,14 @@
 // factor (a large prime) uses a direct O(R^2) stage, so every length works.
 //
 // Twiddles come from one table per length, tw[k] = exp(-2 pi i k / N),
-// computed on the host in FP64 (stored as FP32 for float2 transforms).  The
-// transform is templated on the complex type: float2 for the per-iteration
-// work, double2 for the once-per-solve H'y prologue.
+// computed on the host in FP64 (stored as FP32 for float2 transforms, as a
+// double-float pair for dc).  The transform is templated on the complex type:
+// float2 for the per-iteration work, dc (double-float, df64.cuh) for the
+// once-per-solve H'y prologue, double2 where FP64 is wanted.
 #pragma once
 
 #include "common.cuh"
+#include "df64.cuh"
 
 namespace recon {
 
@@ -34,6 +36,7 @@ struct FftPlanT {
 };
 using FftPlanDev = FftPlanT<float2>;
 using FftPlanDev64 = FftPlanT<double2>;
+using FftPlanDf = FftPlanT<dc>;
 
 __device__ __forceinline__ float2 tw_get(const float2* tw, int k, bool inv) {
   float2 w = __ldg(tw + k);
@@ -42,6 +45,22 @@ __device__ __forceinline__ float2 tw_get(const float2* tw, int k, bool inv) {
 __device__ __forceinline__ double2 tw_get(const double2* tw, int k, bool inv) {
   double2 w = __ldg(tw + k);
   return inv ? make_double2(w.x, -w.y) : w;
+}
+__device__ __forceinline__ dc tw_get(const dc* tw, int k, bool inv) {
+  dc w = dc_unpack(__ldg(reinterpret_cast<const float4*>(tw) + k));
+  if (inv) w.im = df_neg(w.im);
+  return w;
+}
+
+// d * (-i) (forward) or d * (+i) (inverse): a swap and a sign, exact
+__device__ __forceinline__ float2 mul_mi(float2 d, bool inv) {
+  return inv ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+}
+__device__ __forceinline__ double2 mul_mi(double2 d, bool inv) {
+  return inv ? make_double2(-d.y, d.x) : make_double2(d.y, -d.x);
+}
+__device__ __forceinline__ dc mul_mi(dc d, bool inv) {
+  return inv ? dc{df_neg(d.im), d.re} : dc{d.im, df_neg(d.re)};
 }
 
 template <int R, typename T>
@@ -60,9 +79,7 @@ __device__ __forceinline__ void bfly_reg(const T* __restrict__ in, T* __restrict
   } else if (R == 4) {
     T a = c_add(v[0], v[2]), b = c_sub(v[0], v[2]);
     T c = c_add(v[1], v[3]), d = c_sub(v[1], v[3]);
-    // forward: d * (-i); inverse: d * (+i)
-    T di = d;
-    if (inv) { di.x = -d.y; di.y = d.x; } else { di.x = d.y; di.y = -d.x; }
+    const T di = mul_mi(d, inv);   // forward: d * (-i); inverse: d * (+i)
     out[od * ks] = c_add(a, c);
     out[(od + Ns) * ks] = c_add(b, di);
     out[(od + 2 * Ns) * ks] = c_sub(a, c);

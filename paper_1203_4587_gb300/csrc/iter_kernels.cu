@@ -640,62 +640,94 @@ __device__ __forceinline__ int find_slice(const SliceT* sl, int n, int blk) {
 }
 
 // ---------------------------------------------------------------------------
-// Algorithm 2 temporal step on a tile of px pixels x Nt frames (column
+// Algorithm 2 temporal step on a tile of PX pixels x Nt frames (the column
 // layout keeps a tile's pixels contiguous for every t):
 //   v  = S(D_t m + d1, lambda/(2 mu1))
-//   m' = (rho I + D_t'D_t)^{-1} [D_t'(v - d1) + rho (x + d2)]    (Thomas)
+//   m' = (rho I + D_t'D_t)^{-1} [D_t'(v - d1) + rho (x + d2)]
 //   d1' = d1 - (v - D_t m')
 // with d2 = x - p, and p' = m' - d2 handed to the inverse step, which forms
-// r = H'y + mu2 (m' - d2) = b + mu2 p'.  The next d2 is then x' - p'.
-// Phase 1 (all threads, every (t, pixel)): stage the tile with asynchronous
-// copies, then e = d1 - v, rhs and f = p - x.  Phase 2 (one thread per pixel):
-// the two tridiagonal sweeps only.  Phase 3 (all threads): outputs.  Also
+// r = H'y + mu2 (m' - d2) = b + mu2 p'.  The next d2 is then x' - p'.  Also
 // accumulates ||D_t x||_1 of the incoming x (the prior term of J).
+//
+// 8 * PX threads; every phase keeps all of them busy:
+//   1. the tile (m, d1, x, p) is staged with 16-byte asynchronous copies;
+//   2. e = d1 - v, then rhs = e_t - e_{t-1} + rho (2 x - p) and f = p - x;
+//   3. the tridiagonal solve by the Thomas recurrences, run as kTvSeg fixed
+//      segments of ceil(Nt / kTvSeg) frames per pixel: each segment composes
+//      its affine recurrence (forward d_t = inv_t (rhs_t + d_{t-1}), backward
+//      m'_t = d_t + inv_t m'_{t+1}), the segments' maps are chained in order,
+//      and each segment then replays its frames from its incoming value.  The
+//      segmentation depends on Nt only, so every tile width gives the same
+//      rounding;
+//   4. m', d1' = e + D m', p' = m' + f stored with 16-byte accesses.
 // ---------------------------------------------------------------------------
-constexpr int kTvThreads = 256;
+constexpr int kTvSeg = 8;
+
+// 16 bytes (two adjacent pixels) when both are in the tile and the frame
+// offsets keep 16-byte alignment (even npix), else 8 bytes per pixel
+__device__ __forceinline__ void tile_load2(float2* dst, const float2* src, bool pair) {
+  if (pair) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(dst)), "l"(src) : "memory");
+  } else {
+    cp_async8(dst, src);
+  }
+}
 
 template <int PX>
-__global__ void __launch_bounds__(kTvThreads) k_tv_temporal(TemporalLaunch L) {
+__global__ void __launch_bounds__(kTvSeg * PX, 1) k_tv_temporal(TemporalLaunch L) {
+  constexpr int NTH = kTvSeg * PX;
   extern __shared__ __align__(16) float2 sm_tv[];
   __shared__ double red[32];
+  __shared__ float2 segB[kTvSeg][PX];
+  __shared__ float segA[kTvSeg][PX];
   const TvSlice* sls = static_cast<const TvSlice*>(L.slices);
   const TvSlice& P = sls[find_slice(sls, L.nslices, (int)blockIdx.x)];
   if (P.stop && *P.stop) return;
-  constexpr int TS = kTvThreads / PX;   // t-stride of a thread
   const int tid = threadIdx.x, Nt = P.Nt;
-  const int pp = tid % PX, t0 = tid / PX;  // this thread: pixel pp, frames t0, t0+TS, ...
   const long long N = P.npix;
   const long long pix0 = (long long)(blockIdx.x - P.tile0) * PX;
   const int npx = (int)min((long long)PX, N - pix0);
-  const bool mine = pp < npx;
+  const bool even = (N & 1) == 0;
   const int T = Nt * PX;
-  // [Nt][PX] tiles: m (then m'), d1 (then e), x (then rhs), p (then f)
+  // [Nt][PX] tiles: m (then d, then m'), d1 (then e), x (then rhs), p (then f)
   float2* sm_m = sm_tv;
   float2* sm_d1 = sm_m + T;
   float2* sm_x = sm_d1 + T;
   float2* sm_p = sm_x + T;
-  if (mine) {
-    const float2* gx = P.x + pix0 + pp;
-    for (int t = t0; t < Nt; t += TS) {
-      const long long g = t * N;
-      const int idx = t * PX + pp;
-      cp_async8(&sm_x[idx], gx + g);
-      if (P.write_state) {
-        cp_async8(&sm_m[idx], P.m + pix0 + pp + g);
-        cp_async8(&sm_p[idx], P.p + pix0 + pp + g);
-        if (P.d1 && t + 1 < Nt) cp_async8(&sm_d1[idx], P.d1 + pix0 + pp + g);
+  // ---- 1. stage: thread -> (frame, pixel pair)
+  {
+    constexpr int PAIRS = PX / 2;
+    for (int idx = tid; idx < Nt * PAIRS; idx += NTH) {
+      const int t = idx / PAIRS, pp = 2 * (idx - t * PAIRS);
+      if (pp >= npx) continue;
+      const bool pair = even && pp + 1 < npx;
+      const long long g = t * N + pix0 + pp;
+      const int o = t * PX + pp;
+      for (int h = 0; h < (pair ? 1 : min(2, npx - pp)); ++h) {
+        tile_load2(&sm_x[o + h], P.x + g + h, pair);
+        if (P.write_state) {
+          tile_load2(&sm_m[o + h], P.m + g + h, pair);
+          tile_load2(&sm_p[o + h], P.p + g + h, pair);
+          if (P.d1 && t + 1 < Nt) tile_load2(&sm_d1[o + h], P.d1 + g + h, pair);
+        }
       }
     }
   }
   cp_async_wait_all();
   __syncthreads();
-  double tv = 0.0;
+  // element phases: thread -> pixel pp = tid % PX, frames t0, t0 + kTvSeg, ...
+  const int pp = tid % PX, t0 = tid / PX;
+  const bool mine = pp < npx;
+  // ||D_t x||_1: at most ceil(Nt / kTvSeg) terms per thread in FP32, then
+  // FP64 across the block (GB300's FP64 pipe is too narrow for per-element use)
+  float tvf = 0.f;
   if (mine)
-    for (int t = t0; t + 1 < Nt; t += TS) tv += (double)c_abs(c_sub(sm_x[(t + 1) * PX + pp], sm_x[t * PX + pp]));
+    for (int t = t0; t + 1 < Nt; t += kTvSeg) tvf += c_abs(c_sub(sm_x[(t + 1) * PX + pp], sm_x[t * PX + pp]));
+  const double tv = (double)tvf;
   if (P.write_state) {
-    // e_t = d1_t - S(m_{t+1} - m_t + d1_t) for t < Nt-1 (0 at t = Nt-1)
+    // ---- 2a. e_t = d1_t - S(m_{t+1} - m_t + d1_t) for t < Nt-1 (0 at t = Nt-1)
     if (mine)
-      for (int t = t0; t < Nt; t += TS) {
+      for (int t = t0; t < Nt; t += kTvSeg) {
         const int idx = t * PX + pp;
         float2 e = make_float2(0.f, 0.f);
         if (t + 1 < Nt) {
@@ -703,12 +735,12 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_temporal(TemporalLaunch L) {
           const float2 v = c_soft(c_add(c_sub(sm_m[idx + PX], sm_m[idx]), d1_t), P.tau1);
           e = c_sub(d1_t, v);
         }
-        sm_d1[idx] = e;  // d1 is not needed any more
+        sm_d1[idx] = e;
       }
     __syncthreads();
-    // rhs_t = e_t - e_{t-1} + rho (2 x_t - p_t);  f_t = p_t - x_t
+    // ---- 2b. rhs_t = e_t - e_{t-1} + rho (2 x_t - p_t);  f_t = p_t - x_t
     if (mine)
-      for (int t = t0; t < Nt; t += TS) {
+      for (int t = t0; t < Nt; t += kTvSeg) {
         const int idx = t * PX + pp;
         const float2 x_t = sm_x[idx], p_t = sm_p[idx];
         float2 rhs = sm_d1[idx];
@@ -719,60 +751,121 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_temporal(TemporalLaunch L) {
         sm_p[idx] = c_sub(p_t, x_t);
       }
     __syncthreads();
-    // phase 2: Thomas sweeps, one thread per pixel; m' into the m tile
-    if (tid < npx) {
-      float2 d_prev = make_float2(0.f, 0.f);
-      for (int t = 0; t < Nt; ++t) {
+    // ---- 3. Thomas recurrences by segments: thread -> (pixel pp, segment t0)
+    const int Ls = (Nt + kTvSeg - 1) / kTvSeg;
+    const int ta = min(Nt, t0 * Ls), tb = min(Nt, ta + Ls);
+    // forward: d_t = inv_t (rhs_t + d_{t-1}); the segment's map d_out = A d_in + B
+    {
+      float A = 1.f;
+      float2 B = make_float2(0.f, 0.f);
+      for (int t = ta; t < tb; ++t) {
         const float inv = __ldg(P.thomas + t);
-        d_prev = c_scale(c_add(sm_x[t * PX + tid], d_prev), inv);
-        sm_m[t * PX + tid] = d_prev;
+        A *= inv;
+        B = c_scale(c_add(sm_x[t * PX + pp], B), inv);
       }
-      float2 mnext = make_float2(0.f, 0.f);
-      for (int t = Nt - 1; t >= 0; --t) {
-        const float inv = __ldg(P.thomas + t);
-        const float2 dp = sm_m[t * PX + tid];
-        mnext = make_float2(fmaf(inv, mnext.x, dp.x), fmaf(inv, mnext.y, dp.y));
-        sm_m[t * PX + tid] = mnext;
+      segA[t0][pp] = A;
+      segB[t0][pp] = B;
+    }
+    __syncthreads();
+    {
+      float2 d = make_float2(0.f, 0.f);
+      for (int q = 0; q < t0; ++q) d = c_add(c_scale(d, segA[q][pp]), segB[q][pp]);
+      for (int t = ta; t < tb; ++t) {
+        d = c_scale(c_add(sm_x[t * PX + pp], d), __ldg(P.thomas + t));
+        sm_m[t * PX + pp] = d;
       }
     }
     __syncthreads();
-    // phase 3: m', d1' = e + D m', p' = m' + f
-    if (mine)
-      for (int t = t0; t < Nt; t += TS) {
-        const int idx = t * PX + pp;
-        const long long g = t * N + pix0 + pp;
-        const float2 mt = sm_m[idx];
-        P.m_out[g] = mt;
-        P.p_out[g] = c_add(mt, sm_p[idx]);
-        if (t + 1 < Nt) P.d1_out[g] = c_add(sm_d1[idx], c_sub(sm_m[idx + PX], mt));
+    // backward: m'_t = d_t + inv_t m'_{t+1}; the segment's map m'_first = A m'_in + B
+    {
+      float A = 1.f;
+      float2 B = make_float2(0.f, 0.f);
+      for (int t = tb - 1; t >= ta; --t) {
+        const float inv = __ldg(P.thomas + t);
+        const float2 dt = sm_m[t * PX + pp];
+        B = make_float2(fmaf(inv, B.x, dt.x), fmaf(inv, B.y, dt.y));
+        A *= inv;
       }
+      segA[t0][pp] = A;
+      segB[t0][pp] = B;
+    }
+    __syncthreads();
+    {
+      float2 mn = make_float2(0.f, 0.f);
+      for (int q = kTvSeg - 1; q > t0; --q) mn = c_add(c_scale(mn, segA[q][pp]), segB[q][pp]);
+      for (int t = tb - 1; t >= ta; --t) {
+        const float inv = __ldg(P.thomas + t);
+        const float2 dt = sm_m[t * PX + pp];
+        mn = make_float2(fmaf(inv, mn.x, dt.x), fmaf(inv, mn.y, dt.y));
+        sm_m[t * PX + pp] = mn;
+      }
+    }
+    __syncthreads();
+    // ---- 4. m', d1' = e + D m', p' = m' + f: thread -> (frame, pixel pair)
+    {
+      constexpr int PAIRS = PX / 2;
+      for (int idx = tid; idx < Nt * PAIRS; idx += NTH) {
+        const int t = idx / PAIRS, q = 2 * (idx - t * PAIRS);
+        if (q >= npx) continue;
+        const int o = t * PX + q;
+        const long long g = t * N + pix0 + q;
+        const float2 m0 = sm_m[o], m1 = sm_m[o + 1];
+        const float2 p0 = c_add(m0, sm_p[o]), p1 = c_add(m1, sm_p[o + 1]);
+        float2 e0 = make_float2(0.f, 0.f), e1 = e0;
+        if (t + 1 < Nt) {
+          e0 = c_add(sm_d1[o], c_sub(sm_m[o + PX], m0));
+          e1 = c_add(sm_d1[o + 1], c_sub(sm_m[o + 1 + PX], m1));
+        }
+        if (even && q + 1 < npx) {
+          *reinterpret_cast<float4*>(P.m_out + g) = make_float4(m0.x, m0.y, m1.x, m1.y);
+          *reinterpret_cast<float4*>(P.p_out + g) = make_float4(p0.x, p0.y, p1.x, p1.y);
+          if (t + 1 < Nt) *reinterpret_cast<float4*>(P.d1_out + g) = make_float4(e0.x, e0.y, e1.x, e1.y);
+        } else {
+          P.m_out[g] = m0;
+          P.p_out[g] = p0;
+          if (t + 1 < Nt) P.d1_out[g] = e0;
+          if (q + 1 < npx) {
+            P.m_out[g + 1] = m1;
+            P.p_out[g + 1] = p1;
+            if (t + 1 < Nt) P.d1_out[g + 1] = e1;
+          }
+        }
+      }
+    }
   }
-  const double s = group_sum(tv, red, tid, kTvThreads, BlockBar());
+  const double s = group_sum(tv, red, tid, NTH, BlockBar());
   if (tid == 0) atomicAdd(P.prior_acc, s);
 }
 
-// four [Nt][px] complex tiles; px in {32, 64, 128} (the widest that fits is
-// the default: 64 up to Nt = 96, else 32; 128 needs Nt <= 55)
+// four [Nt][px] complex tiles; px in {16, 32, 64} (8 px threads); the default
+// is 32, or the widest that fits
 constexpr size_t kSmemOptin = 227 * 1024;
 static size_t tv_smem(int Nt_max, int px) { return 4 * (size_t)Nt_max * px * sizeof(float2); }
-int tv_tile_px(int Nt_max) { return Nt_max <= 96 ? 64 : 32; }
+static size_t tv_static_smem(int px) { return 32 * sizeof(double) + kTvSeg * (size_t)px * (sizeof(float2) + sizeof(float)); }
 int tv_tile_candidates(int Nt_max, int* out) {
   int n = 0;
-  for (int px : {32, 64, 128})
-    if (tv_smem(Nt_max, px) + 1024 <= kSmemOptin) out[n++] = px;
+  for (int px : {16, 32, 64})
+    if (tv_smem(Nt_max, px) + tv_static_smem(px) + 1024 <= kSmemOptin) out[n++] = px;
   return n;
+}
+int tv_tile_px(int Nt_max) {
+  int c[4];
+  const int n = tv_tile_candidates(Nt_max, c);
+  for (int i = n - 1; i >= 0; --i)
+    if (c[i] <= 32) return c[i];
+  return 16;
 }
 
 cudaError_t prepare_tv_temporal(int Nt_max, int px) {
   static size_t configured[3] = {0, 0, 0};
   const size_t smem = tv_smem(Nt_max, px);
-  const int k = px == 32 ? 0 : px == 64 ? 1 : px == 128 ? 2 : -1;
+  const int k = px == 16 ? 0 : px == 32 ? 1 : px == 64 ? 2 : -1;
   if (k < 0) return cudaErrorInvalidValue;
   if (smem > configured[k]) {   // also below 48 KB: static shared memory counts toward that limit
     cudaError_t e = cudaSuccess;
+    if (px == 16) e = cudaFuncSetAttribute(k_tv_temporal<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (px == 32) e = cudaFuncSetAttribute(k_tv_temporal<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (px == 64) e = cudaFuncSetAttribute(k_tv_temporal<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (px == 128) e = cudaFuncSetAttribute(k_tv_temporal<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured[k] = smem;
   }
@@ -783,9 +876,10 @@ cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s) {
   cudaError_t e = prepare_tv_temporal(p.Nt_max, p.tile_px);
   if (e != cudaSuccess) return e;
   const size_t smem = tv_smem(p.Nt_max, p.tile_px);
-  if (p.tile_px == 64) k_tv_temporal<64><<<p.nblocks, kTvThreads, smem, s>>>(p);
-  else if (p.tile_px == 32) k_tv_temporal<32><<<p.nblocks, kTvThreads, smem, s>>>(p);
-  else k_tv_temporal<128><<<p.nblocks, kTvThreads, smem, s>>>(p);
+  if (p.tile_px == 32) k_tv_temporal<32><<<p.nblocks, kTvSeg * 32, smem, s>>>(p);
+  else if (p.tile_px == 16) k_tv_temporal<16><<<p.nblocks, kTvSeg * 16, smem, s>>>(p);
+  else if (p.tile_px == 64) k_tv_temporal<64><<<p.nblocks, kTvSeg * 64, smem, s>>>(p);
+  else return cudaErrorInvalidValue;
   note_launch();
   return cudaGetLastError();
 }
@@ -833,13 +927,13 @@ __global__ void __launch_bounds__(256) k_dft_temporal(TemporalLaunch L) {
   float2* W = fft_run(A, B, kDftPix, 1, kDftPix, P.ft, false, tid, nth, bar);
   float2* O = (W == A) ? B : A;
   const float sc = rsqrtf((float)Nt);
-  double l1 = 0.0;
+  float l1f = 0.f;   // per-thread FP32 partial (a few terms), FP64 across the block
   for (int idx = tid; idx < Nt * kDftPix; idx += nth) {
     const int t = idx / kDftPix, pp = idx - t * kDftPix;
     float2 uo = make_float2(0.f, 0.f);
     if (pp < npx) {
       const float2 w = c_scale(W[idx], sc);
-      l1 += (double)c_abs(w);
+      l1f += c_abs(w);
       if (P.write_state) {
         const float2 d = P.first ? make_float2(0.f, 0.f) : c_sub(P.u[t * N + pix0 + pp], w);
         const float2 v = c_soft(c_sub(w, d), P.tau);
@@ -862,7 +956,7 @@ __global__ void __launch_bounds__(256) k_dft_temporal(TemporalLaunch L) {
       }
     }
   }
-  const double s = group_sum(l1, red, tid, nth, bar);
+  const double s = group_sum((double)l1f, red, tid, nth, bar);
   if (tid == 0) atomicAdd(P.prior_acc, s);
 }
 
@@ -973,8 +1067,8 @@ __global__ void __launch_bounds__(256) k_haar_temporal(TemporalLaunch L, int lev
   }
   for (int idx = tid; idx < T; idx += nth) W[(size_t)levels * T + idx] = a[idx];
   bar();
-  // w, ||w||_1, the v- and d-updates
-  double l1 = 0.0;
+  // w, ||w||_1 (per-thread FP32 partial, FP64 across the block), the v- and d-updates
+  float l1f = 0.f;
   const size_t NU = (size_t)Nt * N;          // one channel of u in global memory
   for (int idx = tid; idx < nch * T; idx += nth) {
     const int c = idx / T, rem = idx - c * T;
@@ -984,7 +1078,7 @@ __global__ void __launch_bounds__(256) k_haar_temporal(TemporalLaunch L, int lev
       const size_t g = (size_t)c * NU + (size_t)t * N + pix0 + pp;
       const float2 up = P.first ? make_float2(0.f, 0.f) : P.u[g];
       const float2 w = c_add(up, W[idx]);
-      l1 += (double)c_abs(w);
+      l1f += c_abs(w);
       if (P.write_state) {
         const float2 d = P.first ? make_float2(0.f, 0.f) : c_sub(up, w);
         const float2 v = c_soft(c_sub(w, d), P.tau);
@@ -1031,7 +1125,7 @@ __global__ void __launch_bounds__(256) k_haar_temporal(TemporalLaunch L, int lev
       }
     }
   }
-  const double sum = group_sum(l1, red, tid, nth, bar);
+  const double sum = group_sum((double)l1f, red, tid, nth, bar);
   if (tid == 0) atomicAdd(P.prior_acc, sum);
 }
 
@@ -1085,8 +1179,148 @@ __global__ void __launch_bounds__(256) k_objective(ObjParams P) {
   if (tid == 0) atomicAdd(P.fid_acc, s);
 }
 
+// ---------------------------------------------------------------------------
+// ||y - H x||^2 of a whole field with one warp per (column, coil): the
+// vertical FFT z = F_v(s_c . x_col) of length Ny = 32 E runs in the warp's
+// registers as a four-step transform, with no shared-memory passes and no
+// block barriers.  Input n = l + 32 k (lane l holds k = 0..E-1), output
+// f = q + E m:
+//   1. an E-point DFT over k in each lane's registers;
+//   2. the twiddle w_Ny^(l q);
+//   3. a 32-point DFT over the lanes for every q (five radix-2
+//      decimation-in-frequency stages with shuffles), after which lane l holds
+//      m = bitrev5(l).
+// Each output on a sampled row is compared with the hybrid data F_h'y.
+// Twiddles w_Ny^j come from the FP64-computed table, staged in shared memory.
+// ---------------------------------------------------------------------------
+template <int N>
+struct SmallestFactor {
+  static constexpr int value = N % 2 == 0 ? 2 : N % 3 == 0 ? 3 : N % 5 == 0 ? 5 : N;
+};
+
+// In-register forward DFT of N values, x[f] = sum_n x[n] w_N^(n f), by
+// recursive decimation in time over the smallest prime factor; w_N^j is
+// tw[j * ts] (tw a table of a length that N divides, ts = length / N).
+template <int N>
+__device__ __forceinline__ void reg_dft(float2 (&x)[N], const float2* __restrict__ tw, int ts) {
+  if constexpr (N > 1) {
+    constexpr int R = SmallestFactor<N>::value, M = N / R;
+    float2 s[R][M];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int m = 0; m < M; ++m) s[r][m] = x[m * R + r];
+#pragma unroll
+    for (int r = 0; r < R; ++r) reg_dft<M>(s[r], tw, ts * R);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = (r == 0 || k == 0) ? s[r][k] : c_mul(s[r][k], tw[r * k * ts]);
+      if constexpr (R == 2) {
+        x[k] = c_add(v[0], v[1]);
+        x[k + M] = c_sub(v[0], v[1]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          float2 acc = v[0];
+#pragma unroll
+          for (int r = 1; r < R; ++r) c_fma(acc, v[r], tw[((q * r) % R) * M * ts]);
+          x[k + q * M] = acc;
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float2 shfl_xor_c(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+template <int E, class YE>
+__global__ void __launch_bounds__(256) k_objective_warp(ObjParams P) {
+  constexpr int Ny = 32 * E;
+  __shared__ float2 tw[Ny];
+  if (P.flags[FLAG_STOP]) return;
+  for (int j = threadIdx.x; j < Ny; j += blockDim.x) tw[j] = __ldg(P.fy.tw + j);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int wglob = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int Nc = P.Nc, Nx = P.Nx;
+  const long long ntask = (long long)P.Nt * Nx * Nc;
+  const float scl = rsqrtf((float)Ny);
+  const int mrow = (int)(__brev((unsigned)lane) >> 27);   // this lane's m after the lane DFT
+  double acc = 0.0;
+  for (long long task = wglob; task < ntask; task += nwarps) {
+    const int c = (int)(task % Nc);
+    const long long col = task / Nc;               // t * Nx + i
+    const int t = (int)(col / Nx), i = (int)(col - (long long)t * Nx);
+    const float2* xc = P.x + col * Ny;
+    const float2* sc = P.sens + ((size_t)i * Nc + c) * Ny;
+    float2 v[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) v[k] = c_mul(__ldg(sc + lane + 32 * k), __ldg(xc + lane + 32 * k));
+    reg_dft<E>(v, tw, 32);
+#pragma unroll
+    for (int q = 1; q < E; ++q) v[q] = c_mul(v[q], tw[lane * q]);
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+      const bool hi = (lane & h) != 0;
+      const float2 w = tw[(lane & (h - 1)) * (Ny / (2 * h))];
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const float2 o = shfl_xor_c(v[q], h);
+        v[q] = hi ? c_mul(c_sub(o, v[q]), w) : c_add(v[q], o);
+      }
+    }
+    const int r0 = P.rowoff[t], mt = P.rowoff[t + 1] - r0;
+    const YE* yh = static_cast<const YE*>(P.yhat) + (size_t)r0 * Nx * Nc + ((size_t)i * Nc + c) * mt;
+    const float ys = P.yscale ? P.yscale[t] : 1.f;
+    const short* ri = P.rowidx + (size_t)t * Ny;
+    float part = 0.f;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int mi = ri[q + E * mrow];
+      if (mi >= 0) {
+        const float2 y = c_scale(Elem<YE>::load(yh + mi), ys);
+        const float dx = y.x - v[q].x * scl, dy = y.y - v[q].y * scl;
+        part = fmaf(dx, dx, fmaf(dy, dy, part));
+      }
+    }
+    acc += (double)part;
+  }
+  acc = warp_sum(acc);
+  if (lane == 0 && acc != 0.0) atomicAdd(P.fid_acc, acc);
+}
+
+// Ny = 32 E with E in this list: the warp kernel; other lengths: the block kernel
+#define RECON_OBJ_WARP_SIZES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(8) X(10) X(12) X(16) X(20) X(24) X(32)
+
+template <class YE>
+static cudaError_t launch_objective_warp(const ObjParams& p, cudaStream_t s, bool* done) {
+  *done = false;
+  if (p.Ny % 32 != 0) return cudaSuccess;
+  const int E = p.Ny / 32;
+  const int grid = p.grid > 0 ? p.grid : 1024;
+  switch (E) {
+#define RECON_OBJ_CASE(e) \
+    case e: k_objective_warp<e, YE><<<grid, 256, 0, s>>>(p); *done = true; break;
+    RECON_OBJ_WARP_SIZES(RECON_OBJ_CASE)
+#undef RECON_OBJ_CASE
+    default: return cudaSuccess;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <class YE>
 static cudaError_t launch_objective_t(const ObjParams& p, cudaStream_t s) {
+  {
+    bool done = false;
+    const cudaError_t e = launch_objective_warp<YE>(p, s, &done);
+    if (e != cudaSuccess || done) return e;
+  }
   const size_t smem = ((size_t)p.Ny + 2 * (size_t)p.ncg * p.Ny) * sizeof(float2);
   static size_t configured = 0;
   if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
@@ -1109,28 +1343,32 @@ cudaError_t launch_objective(const ObjParams& p, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // Per slice: J(k) = ||y - Hx||^2 + lambda * prior, Delta(k) (Eq. r_ratio) and
-// the stop flag; later launches see the flag and skip that slice.
+// the stop flag, for k = k0 .. k1 in order; later launches see the flag and
+// skip that slice.  With the stop test on, the engine calls it once per
+// iteration (k0 = k1); with a fixed iteration count, once after the loop.
 // ---------------------------------------------------------------------------
-__global__ void k_finalize(const FinSlice* fins, int n, int k) {
+__global__ void k_finalize(const FinSlice* fins, int n, int k0, int k1) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const FinSlice f = fins[q];
   int* flags = f.flags;
-  if (flags[FLAG_STOP]) return;
-  const double Jk = f.fid[k] + ((f.yy && k > 0) ? *f.yy : 0.0) + (double)f.lam * f.prior[k];
-  f.J[k] = Jk;
-  if (!isfinite(Jk)) atomicOr(&flags[FLAG_ERR], DEV_ERR_NONFINITE);
-  if (f.tol > 0.0 && k >= 1) {
-    const double d = (f.J[k - 1] - Jk) / Jk;
-    if (d >= 0.0 && d < f.tol) {
-      flags[FLAG_ITERS] = k;
-      flags[FLAG_STOP] = 1;
+  for (int k = k0; k <= k1; ++k) {
+    if (flags[FLAG_STOP]) return;
+    const double Jk = f.fid[k] + ((f.yy && k > 0) ? *f.yy : 0.0) + (double)f.lam * f.prior[k];
+    f.J[k] = Jk;
+    if (!isfinite(Jk)) atomicOr(&flags[FLAG_ERR], DEV_ERR_NONFINITE);
+    if (f.tol > 0.0 && k >= 1) {
+      const double d = (f.J[k - 1] - Jk) / Jk;
+      if (d >= 0.0 && d < f.tol) {
+        flags[FLAG_ITERS] = k;
+        flags[FLAG_STOP] = 1;
+      }
     }
   }
 }
 
-cudaError_t launch_finalize(const FinSlice* fins, int nslices, int k, cudaStream_t s) {
-  k_finalize<<<(nslices + 127) / 128, 128, 0, s>>>(fins, nslices, k); note_launch();
+cudaError_t launch_finalize(const FinSlice* fins, int nslices, int k0, int k1, cudaStream_t s) {
+  k_finalize<<<(nslices + 127) / 128, 128, 0, s>>>(fins, nslices, k0, k1); note_launch();
   return cudaGetLastError();
 }
 

@@ -51,9 +51,9 @@ struct PackInfo {
 
 // ---- FFT plan (host side holds the device twiddle table) -------------------
 FftPlanDev make_fft_plan_host(int n, const float2* d_tw);  // factorisation only
-FftPlanDev64 make_fft_plan_host64(int n, const double2* d_tw);
+FftPlanDf make_fft_plan_host_df(int n, const dc* d_tw);
 void fill_twiddles_host(int n, float2* host_tw);           // exp(-2 pi i k/n)
-void fill_twiddles_host64(int n, double2* host_tw);
+void fill_twiddles_host_df(int n, float4* host_tw);   // exp(-2 pi i k/n) as double-float pairs
 
 // ---- kernel parameter blocks ----------------------------------------------
 // The per-iteration kernels take arrays of per-problem ("slice") descriptors:
@@ -251,9 +251,11 @@ struct ObjParams {           // ||y - H x||^2 of a given field (no inverse)
   const float* yscale;       // [Nt] (16-bit yhat only)
   const int* rows;
   const int* rowoff;
+  const short* rowidx;       // [Nt][Ny]: index of row j among frame t's sampled rows, or -1
   FftPlanDev fy;
   double* fid_acc;
   const int* flags;
+  int grid;                  // blocks of the warp-per-(column, coil) kernel
 };
 
 // Counts kernel launches of this library (process-wide); every launcher calls it.
@@ -291,8 +293,8 @@ cudaError_t launch_stv_rhs(const StvLaunch& L, cudaStream_t s);      // r = rhs 
 cudaError_t launch_stv_dir(const StvLaunch& L, cudaStream_t s);      // p_j, q = M p_j, <p_j, q>
 cudaError_t launch_stv_update(const StvLaunch& L, cudaStream_t s);   // m, r, gamma_{j+1}
 cudaError_t launch_stv_finish(const StvLaunch& L, cudaStream_t s);   // d1 = e + R m, p, next e
-// per slice: J(k) = fid[k] + (yy ? *yy : 0) + lambda prior[k]; Delta(k); stop flag.
-cudaError_t launch_finalize(const FinSlice* fins, int nslices, int k, cudaStream_t s);
+// per slice, for k = k0 .. k1: J(k) = fid[k] + (yy ? *yy : 0) + lambda prior[k]; Delta(k); stop flag.
+cudaError_t launch_finalize(const FinSlice* fins, int nslices, int k0, int k1, cudaStream_t s);
 
 // prologue / operators
 // yhat = F_h' y (FP32 butterflies), k-space complex64 or 16-bit pairs
@@ -309,19 +311,20 @@ cudaError_t launch_hybrid_rows(const void* kspace, int kstorage, const float* ks
 cudaError_t launch_adjoint_combine(const float2* yhat, const float2* sens, float2* b, const int* rows,
                                    const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, int ystorage,
                                    void* ylp, const unsigned* ymax, float* yscale, int ncg, cudaStream_t s);
-// FP64 H'y prologue: the solution of the iterations is ~100x more sensitive to
-// errors in H'y than to rounding elsewhere, so H'y is formed in FP64 and
-// rounded once.  yhat32 receives the FP32 rounding of the hybrid data; *yy
-// accumulates ||y||^2 over the sampled entries (may be null).
-cudaError_t launch_hybrid_rows64(const void* kspace, int kstorage, const float* kscale, double2* yhat64,
-                                 float2* yhat32, double* yy, const int* rows, const int* rowoff, int maxm, int Nx,
-                                 int Ny, int Nt, int Nc, FftPlanDev64 fx, int G, cudaStream_t s, int i0 = 0,
-                                 int W = 0);
-cudaError_t launch_adjoint_combine64(const double2* yhat64, const float2* sens, float2* b, const int* rows,
-                                     const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fy, int ncg,
-                                     cudaStream_t s);
-int row_group_max(int Nx, bool fp64);              // largest rows-per-block of the row FFTs
-int coil_group_max(int Nc, int Ny, bool fp64);     // largest coils-per-pass of the combine
+// Double-float H'y prologue: the solution of the iterations is ~100x more
+// sensitive to errors in H'y than to rounding elsewhere, so H'y is formed in
+// double-float arithmetic (about 48 bits, on the FP32 pipe) and rounded once.
+// yhat32 receives the FP32 rounding of the hybrid data; *yy accumulates
+// ||y||^2 over the sampled entries (may be null).
+cudaError_t launch_hybrid_rows_df(const void* kspace, int kstorage, const float* kscale, dc* yhat_df,
+                                  float2* yhat32, double* yy, const int* rows, const int* rowoff, int maxm, int Nx,
+                                  int Ny, int Nt, int Nc, FftPlanDf fx, int G, cudaStream_t s, int i0 = 0,
+                                  int W = 0);
+cudaError_t launch_adjoint_combine_df(const dc* yhat_df, const float2* sens, float2* b, const int* rows,
+                                      const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDf fy, int ncg,
+                                      cudaStream_t s);
+int row_group_max(int Nx, bool wide);              // largest rows-per-block of the row FFTs (wide: double-float)
+int coil_group_max(int Nc, int Ny, bool wide);     // largest coils-per-pass of the combine
 // 16-bit k-space (storage 1 = FP16, 2 = BF16 pairs) with per-frame
 // power-of-two scales: out = k / frame_scale[t], one rounding.
 cudaError_t launch_quantize_kspace(const float2* k, long long per_frame, int Nt, int storage, void* out,

@@ -29,8 +29,9 @@ static int row_group(int Nx) {
 
 // yhat = F_h' y on the sampled rows.  The k-space arrives as complex64 or as
 // 16-bit pairs KIn with a per-frame scale (value = stored * kscale[t]); it is
-// widened exactly and the FFT runs in T (double2: FP64, with the FP32
-// rounding also written to yhat32 for the objective; float2: FP32).  *yy
+// widened exactly and the FFT runs in T (dc: double-float, about 48 bits on
+// the FP32 pipe, with the FP32 rounding also written to yhat32 for the
+// objective; float2: FP32).  *yy
 // accumulates ||y||^2 over the sampled entries and ymax[t] the largest
 // |component| of frame t's output (float bits; both optional).
 template <typename T, typename KIn>
@@ -130,11 +131,11 @@ cudaError_t launch_hybrid_rows(const void* kspace, int kstorage, const float* ks
                                Nc, fx, G, i0, W, s);
 }
 
-cudaError_t launch_hybrid_rows64(const void* kspace, int kstorage, const float* kscale, double2* yhat64,
-                                 float2* yhat32, double* yy, const int* rows, const int* rowoff, int maxm, int Nx,
-                                 int Ny, int Nt, int Nc, FftPlanDev64 fx, int G, cudaStream_t s, int i0, int W) {
-  return rows_dispatch<double2>(kspace, kstorage, kscale, yhat64, yhat32, yy, nullptr, rows, rowoff, maxm, Nx, Ny,
-                                Nt, Nc, fx, G, i0, W, s);
+cudaError_t launch_hybrid_rows_df(const void* kspace, int kstorage, const float* kscale, dc* yhat_df,
+                                  float2* yhat32, double* yy, const int* rows, const int* rowoff, int maxm, int Nx,
+                                  int Ny, int Nt, int Nc, FftPlanDf fx, int G, cudaStream_t s, int i0, int W) {
+  return rows_dispatch<dc>(kspace, kstorage, kscale, yhat_df, yhat32, yy, nullptr, rows, rowoff, maxm, Nx, Ny, Nt,
+                           Nc, fx, G, i0, W, s);
 }
 
 constexpr int kCoilGroupMax = 8;
@@ -242,15 +243,15 @@ cudaError_t launch_adjoint_combine(const float2* yhat, const float2* sens, float
   }
 }
 
-cudaError_t launch_adjoint_combine64(const double2* yhat64, const float2* sens, float2* b, const int* rows,
-                                     const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev64 fy, int ncg,
-                                     cudaStream_t s) {
-  return launch_combine_t<double2, void>(yhat64, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, fy, nullptr, nullptr,
-                                         nullptr, ncg, s);
+cudaError_t launch_adjoint_combine_df(const dc* yhat_df, const float2* sens, float2* b, const int* rows,
+                                      const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDf fy, int ncg,
+                                      cudaStream_t s) {
+  return launch_combine_t<dc, void>(yhat_df, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, fy, nullptr, nullptr, nullptr,
+                                    ncg, s);
 }
 
-int row_group_max(int Nx, bool fp64) { return fp64 ? row_group<double2>(Nx) : row_group<float2>(Nx); }
-int coil_group_max(int Nc, int Ny, bool fp64) { return fp64 ? coil_group<double2>(Nc, Ny) : coil_group<float2>(Nc, Ny); }
+int row_group_max(int Nx, bool wide) { return wide ? row_group<dc>(Nx) : row_group<float2>(Nx); }
+int coil_group_max(int Nc, int Ny, bool wide) { return wide ? coil_group<dc>(Nc, Ny) : coil_group<float2>(Nc, Ny); }
 
 // ---- 16-bit k-space with per-frame scales ----------------------------------
 // Three launches: the largest |component| of every frame (float bits into

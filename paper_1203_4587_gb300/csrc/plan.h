@@ -31,6 +31,7 @@ struct Engine {
   int levels = 0;          // frame levels of the Haar prior
   bool fused = false;      // objective data term inside the inverse kernel
   bool obj = false;        // objective on
+  bool stop_test = false;  // some slice stops on Delta(k) < tol: J(k) is formed every iteration
   int storage = 0;
   // temporal launches: K+1 descriptor sets (k = 1..K, then the final prior term)
   void* d_tmp = nullptr;
@@ -75,9 +76,10 @@ struct recon_plan {
   float2* sens = nullptr;
   int* rows = nullptr;
   int* rowoff = nullptr;
+  short* rowidx = nullptr;             // [Nt][Ny]: position of row j among frame t's sampled rows, -1 if unsampled
   float2 *tw_x = nullptr, *tw_y = nullptr, *tw_t = nullptr;
-  double2 *tw64_x = nullptr, *tw64_y = nullptr;
-  double2* yhat64 = nullptr;           // FP64 hybrid data of the prologue
+  recon::dc *twdf_x = nullptr, *twdf_y = nullptr;   // double-float twiddles of the prologue
+  recon::dc* yhat_df = nullptr;        // double-float hybrid data of the prologue
   float* thomas = nullptr;
   float2* yhat = nullptr;               // FP32 hybrid data (FP32 storage)
   void* yhat_lp = nullptr;             // 16-bit storage: hybrid data / yscale[t], 16-bit pairs
@@ -102,7 +104,7 @@ struct recon_plan {
   float2* res_prev = nullptr;          // DFT, Haar: xhat_{K-1}, copied before the last inverse step
   int* flags = nullptr;
   recon::FftPlanDev fx{}, fy{}, ft{};
-  recon::FftPlanDev64 fx64{}, fy64{};
+  recon::FftPlanDf fxdf{}, fydf{};
   int col_stages = 0;
   int last_iters = 0;
   unsigned generation = 0;             // bumped by recon_plan_set_mu: engines built before refuse to run
@@ -181,7 +183,7 @@ const float2* plan_result(const recon_plan* p);   // image (internal layout) aft
 recon_status plan_prologue(recon_plan* p, const void* kspace, int kstorage, const float* kscale, cudaStream_t s);
 recon_status plan_to_user(recon_plan* p, const float2* in, float2* out, cudaStream_t s);
 recon_status plan_to_internal(recon_plan* p, const float2* in, float2* out, cudaStream_t s);
-recon_status plan_adjoint64(recon_plan* p, const void* kspace, int kstorage, const float* kscale, float2* yhat32,
+recon_status plan_adjoint_df(recon_plan* p, const void* kspace, int kstorage, const float* kscale, float2* yhat32,
                             float2* b, double* yy, cudaStream_t s);
 recon_status plan_objective(recon_plan* p, const float2* x, double* acc, cudaStream_t s);
 recon_status plan_fill_info(recon_plan* p, recon_info* info, cudaStream_t s);

@@ -131,6 +131,24 @@ def test_inverse_rounded_once(shape):
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(str(s[k]) for k in ("Nx", "Ny", "Nt", "Nc")))
+def test_adjoint_rounded_once(shape):
+    """H'y is formed in double-float arithmetic (about 48 bits) and rounded
+    once: every element is within half an FP32 ulp of the FP64 oracle's value
+    plus 2^-36 max|H'y|, and the larger elements equal its FP32 rounding."""
+    case = make("tiny", **shape)
+    P = plan_for(case, max_iters=1)
+    b = P.adjoint(gpu(case.kspace)).cpu().numpy()
+    ref = oracle.adjoint_op(case.kspace, case.sens, case.mask)
+    top = np.abs(ref).max()
+    for part in (np.real, np.imag):
+        a, r = part(b).astype(np.float64), part(ref)
+        ulp = np.spacing(np.abs(r).astype(np.float32)).astype(np.float64)
+        assert np.all(np.abs(a - r) <= 0.5 * ulp + 2.0 ** -36 * top)
+        big = np.abs(r) > 1e-2 * top
+        assert np.mean(a[big] == r[big].astype(np.float32)) > 0.999
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(str(s[k]) for k in ("Nx", "Ny", "Nt", "Nc")))
 def test_apply_inverse(shape):
     case = make("tiny", **shape)
     P = plan_for(case, max_iters=1)
