@@ -43,7 +43,8 @@ EXPORTS = ["recon_default_opts", "recon_plan_create", "recon_solve", "recon_solv
 class Opts(C.Structure):
     _fields_ = [("rho", C.c_float), ("max_iters", C.c_int), ("tol", C.c_double), ("storage", C.c_int),
                 ("objective", C.c_int), ("mask_full", C.c_int), ("col_stages", C.c_int), ("profile", C.c_int),
-                ("frame_levels", C.c_int), ("spatial_weight", C.c_float), ("cg_steps", C.c_int)]
+                ("frame_levels", C.c_int), ("spatial_weight", C.c_float), ("cg_steps", C.c_int),
+                ("persistent", C.c_int)]
 
 
 class Info(C.Structure):
@@ -67,7 +68,8 @@ class Tuning(C.Structure):
 
 class Profile(C.Structure):
     _fields_ = [("inverse_ms", C.c_double), ("inverse_launches", C.c_int), ("temporal_ms", C.c_double),
-                ("temporal_launches", C.c_int), ("solve_ms", C.c_double)]
+                ("temporal_launches", C.c_int), ("solve_ms", C.c_double), ("inverse_passes", C.c_int),
+                ("persistent", C.c_int)]
 
 
 class ReconError(RuntimeError):

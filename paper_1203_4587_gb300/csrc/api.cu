@@ -103,6 +103,7 @@ void recon_default_opts(recon_opts* o) {
   o->frame_levels = 2;
   o->spatial_weight = 1.f;
   o->cg_steps = 5;
+  o->persistent = 1;
 }
 
 const char* recon_status_string(recon_status s) {
@@ -369,6 +370,7 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
   recon_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.rho > 0.f) || o.max_iters < 0 || !(o.tol >= 0.0) || o.storage < 0 || o.storage > 2 || o.col_stages < 0 ||
+      o.persistent < 0 || o.persistent > 1 ||
       o.objective < 0 || o.objective > 2 || (prior == RECON_PRIOR_HAAR && (o.frame_levels < 1 || o.frame_levels > 6)) ||
       (prior == RECON_PRIOR_STV && (!(o.spatial_weight >= 0.f) || !std::isfinite(o.spatial_weight) ||
                                     o.cg_steps < 1 || o.cg_steps > 64)))
@@ -656,6 +658,8 @@ recon_status recon_get_profile(recon_plan* p, recon_profile* out) {
   };
   RC(sum(p->ev_col, p->n_col, &out->inverse_ms));
   out->inverse_launches = p->n_col;
+  out->inverse_passes = p->eng && p->eng->persist ? p->n_col * p->eng->K : p->n_col;
+  out->persistent = p->eng && p->eng->persist ? 1 : 0;
   RC(sum(p->ev_tmp, p->n_tmp, &out->temporal_ms));
   out->temporal_launches = p->n_tmp;
   float m = 0.f;

@@ -276,7 +276,7 @@ recon_status recon_batch_autotune(recon_batch* b, recon_tuning* out, void* strea
   recon_status st;
   for (recon_plan* p : b->eng.plans)
     if ((st = prepare_buffers(p, s)) != RECON_OK) return st;
-  if (b->eng.n > 1) RC(cudaMemsetAsync(b->eng.d_err, 0, sizeof(int), s));
+  if (b->eng.n > 1) RC(cudaMemsetAsync(b->eng.d_err, 0, FLAG_COUNT * sizeof(int), s));
   recon_tuning t{};
   if ((st = tune_engine(&b->eng, s, &t)) != RECON_OK) return st;
   RC(cudaStreamSynchronize(s));

@@ -227,6 +227,75 @@ recon_status finish_col_shape(Engine* e, recon_plan* const* plans, int n, int st
   return RECON_OK;
 }
 
+// The persistent TV solve when the engine's slices allow it: temporal TV, FP32
+// inverses, a fixed iteration count, the fused objective (or none) and Nt <=
+// kPersistNtMax, and every plan asks for it (opts.persistent).
+recon_status engine_build_persist(Engine* e, recon_plan* const* plans, int n) {
+  e->persist = false;
+  if (e->prior != RECON_PRIOR_TV || e->storage != 0 || e->stop_test || (e->obj && !e->fused) || e->K < 1 ||
+      e->volume)
+    return RECON_OK;
+  for (int q = 0; q < n; ++q)
+    if (!plans[q]->opts.persistent || plans[q]->Nt > kPersistNtMax) return RECON_OK;
+  // column lists: longest-processing-time over the CTAs as for the per-step
+  // kernel, but with every slice's columns numbered image-column-major
+  // (c' = i Nt + t), so a CTA's list runs through the image columns in order
+  std::vector<long long> cost(n);
+  std::vector<int> ncols(n);
+  for (int q = 0; q < n; ++q) {
+    cost[q] = plans[q]->pk.col_elems * (long long)plans[q]->esize + 4096;
+    ncols[q] = plans[q]->Nx * plans[q]->Nt;
+  }
+  std::vector<unsigned> work;
+  std::vector<int> off;
+  int work_max = 0;
+  lpt_work_lists(cost, ncols, e->grid, work, off, work_max);
+  for (unsigned& w : work) {
+    const int q = (int)(w >> 24), cp = (int)(w & 0xFFFFFFu);
+    const int Nt = plans[q]->Nt, Nx = plans[q]->Nx;
+    const int i = cp / Nt, t = cp - i * Nt;
+    w = ((unsigned)q << 24) | (unsigned)(t * Nx + i);
+  }
+  const int stages = persist_max_stages(e->nb_max, n, work_max);
+  if (stages <= 0) return RECON_OK;   // the lists do not fit in shared memory: one launch per step
+  size_t ncount = 0;
+  for (int q = 0; q < n; ++q) ncount += 2 * (size_t)plans[q]->Nx;
+  RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_pcount), ncount * sizeof(unsigned)));
+  e->pcount_n = ncount;
+  std::vector<PersistSlice> ps(n);
+  size_t o = 0;
+  for (int q = 0; q < n; ++q) {
+    recon_plan* p = plans[q];
+    PersistSlice& d = ps[q];
+    d.A = p->A;
+    d.col_elems = p->pk.col_elems;
+    d.Nx = p->Nx; d.Ny = p->Ny; d.Nt = p->Nt;
+    d.nb = p->pk.nb;
+    d.nunits = p->pk.nunits;
+    d.b = p->b;
+    d.x = p->x;
+    for (int k = 0; k < 2; ++k) { d.m[k] = p->s0[k]; d.d1[k] = p->s1[k]; d.p[k] = p->s2[k]; }
+    d.mu = p->mu;
+    d.tau1 = (float)(p->lam / (2.0 * (p->mu / p->opts.rho)));
+    d.rho = p->opts.rho;
+    d.thomas = p->thomas;
+    d.w_bx = -2.f; d.w_xr = 1.f; d.w_xx = -p->mu;
+    d.do_obj = e->fused ? 1 : 0;
+    d.trace_fid = p->trace_fid;
+    d.trace_prior = p->trace_prior;
+    d.colcnt = e->d_pcount + o;
+    d.tdone = e->d_pcount + o + p->Nx;
+    o += 2 * (size_t)p->Nx;
+  }
+  RC(upload(e->arena, &e->d_pslice, ps));
+  RC(upload(e->arena, &e->d_pwork, work));
+  RC(upload(e->arena, &e->d_pwork_off, off));
+  e->pwork_max = work_max;
+  e->pstages = stages;
+  e->persist = true;
+  return RECON_OK;
+}
+
 recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
   if (n < 1) return fail(RECON_ERR_INVALID_ARG, "empty batch");
   if (n > 255) return fail(RECON_ERR_UNSUPPORTED, "at most 255 slices per batch");
@@ -306,13 +375,15 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
   RC(upload(e->arena, &e->d_work, work));
   RC(upload(e->arena, &e->d_work_off, off));
   if (n == 1) {
-    e->d_err = p0->flags + FLAG_ERR;
+    e->d_err = p0->flags;
   } else {
-    RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_err), sizeof(int)));
-    RC(cudaMemset(e->d_err, 0, sizeof(int)));
+    RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_err), FLAG_COUNT * sizeof(int)));
+    RC(cudaMemset(e->d_err, 0, FLAG_COUNT * sizeof(int)));
   }
-  return finish_col_shape(e, plans, n,
-                          (n == 1 && p0->col_stages_tuned > 0) ? p0->col_stages_tuned : p0->opts.col_stages);
+  recon_status st2 = finish_col_shape(e, plans, n,
+                                      (n == 1 && p0->col_stages_tuned > 0) ? p0->col_stages_tuned : p0->opts.col_stages);
+  if (st2 != RECON_OK) return st2;
+  return engine_build_persist(e, plans, n);
 }
 
 int engine_tile_candidates(const Engine* e, int* out) {
@@ -430,7 +501,7 @@ recon_status engine_build_inverse(Engine* e, recon_plan* p) {
   build_col_work(pl, 1, e->grid, work, off, e->work_max);
   RC(upload(e->arena, &e->d_work, work));
   RC(upload(e->arena, &e->d_work_off, off));
-  e->d_err = p->flags + FLAG_ERR;
+  e->d_err = p->flags;
   return finish_col_shape(e, pl, 1, p->opts.col_stages);
 }
 
@@ -501,7 +572,7 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
     RC(cudaMemsetAsync(p->trace_prior, 0, nt * sizeof(double), s));
     RC(cudaMemsetAsync(p->trace_J, 0xff, nt * sizeof(double), s));  // NaN
   }
-  if (e->n > 1) RC(cudaMemsetAsync(e->d_err, 0, sizeof(int), s));
+  if (e->n > 1) RC(cudaMemsetAsync(e->d_err, 0, FLAG_COUNT * sizeof(int), s));
   if (e->prior == RECON_PRIOR_STV) {   // m = p = x = H'y, d1 = 0
     for (recon_plan* p : e->plans) {
       const size_t bytes = p->nimg() * sizeof(float2);
@@ -520,6 +591,30 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
   if (e->obj)
     for (recon_plan* p : e->plans)
       if ((st = plan_objective(p, p->b, p->trace_fid, s)) != RECON_OK) return st;
+  if (e->persist) {
+    // T_1 from x = m = p = H'y, then iterations 1..K (with T_2..T_{K+1}) in one launch
+    RC(cudaMemsetAsync(e->d_pcount, 0, e->pcount_n * sizeof(unsigned), s));
+    if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, true, s);
+    if ((st = launch_tmp_set(e, 0, s)) != RECON_OK) return st;
+    if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, false, s);
+    PersistLaunch L{};
+    L.slices = e->d_pslice;
+    L.nslices = e->n;
+    L.work = e->d_pwork;
+    L.work_off = e->d_pwork_off;
+    L.work_max = e->pwork_max;
+    L.nb_max = e->nb_max;
+    L.stages = e->pstages;
+    L.K = K;
+    L.err = e->d_err;
+    if (prof) p0->mark(p0->ev_col, p0->n_col, true, s);
+    RC(launch_persist_tv(L, e->grid, s));
+    if (prof) p0->mark(p0->ev_col, p0->n_col, false, s);
+    if (e->obj) RC(launch_finalize(e->d_fin, e->n, 0, K, s));
+    for (recon_plan* p : e->plans)
+      if ((st = launch_residuals(p, s)) != RECON_OK) return st;
+    return RECON_OK;
+  }
   for (int k = 1; k <= K; ++k) {
     if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, true, s);
     if (e->prior == RECON_PRIOR_STV) st = launch_stv_step(e, k - 1, s);
@@ -668,20 +763,24 @@ recon_status recon_batch_solve(recon_batch* b, const float* const* kspace, float
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
   }
+  if (b->no_graph) return RECON_OK;
   RC(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
   st = batch_enqueue(b, kspace, image, b->cap_stream);
   cudaGraph_t g = nullptr;
   cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &g);
-  if (st != RECON_OK) {
-    if (g) cudaGraphDestroy(g);
-    return st;
+  if (st == RECON_OK && ce == cudaSuccess) {
+    ce = cudaGraphInstantiate(&b->graph, g, 0);
+    if (ce != cudaSuccess) b->graph = nullptr;
   }
-  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-  ce = cudaGraphInstantiate(&b->graph, g, 0);
-  cudaGraphDestroy(g);
-  if (ce != cudaSuccess) {
+  if (g) cudaGraphDestroy(g);
+  if (st != RECON_OK || ce != cudaSuccess) {
+    // a launch this runtime cannot capture (the persistent solve is one
+    // cooperative launch): later calls run the same sequence directly
+    (void)cudaGetLastError();
     b->graph = nullptr;
-    return cuda_fail(ce, "cudaGraphInstantiate");
+    b->no_graph = true;
+    set_last_error("");
+    return RECON_OK;
   }
   b->key = key;
   return RECON_OK;
@@ -696,7 +795,7 @@ recon_status recon_batch_info(recon_batch* b, recon_info* info, void* stream) {
     if (st != RECON_OK && worst == RECON_OK) worst = st;
   }
   int err = 0;
-  if (b->eng.n > 1) RC(cudaMemcpy(&err, b->eng.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (b->eng.n > 1) RC(cudaMemcpy(&err, b->eng.d_err + FLAG_ERR, sizeof(int), cudaMemcpyDeviceToHost));
   if (err & DEV_ERR_TIMEOUT) return fail(RECON_ERR_TIMEOUT, "a bounded device-side wait timed out");
   return worst;
 }

@@ -227,11 +227,11 @@ recon_status recon_grad_create(recon_grad** out, recon_plan* const* plans, int n
     e->work_max = work_max;
     if (e->arena.alloc((void**)&e->d_work, work.size() * sizeof(unsigned)) != cudaSuccess ||
         e->arena.alloc((void**)&e->d_work_off, off.size() * sizeof(int)) != cudaSuccess ||
-        e->arena.alloc((void**)&e->d_err, sizeof(int)) != cudaSuccess)
+        e->arena.alloc((void**)&e->d_err, FLAG_COUNT * sizeof(int)) != cudaSuccess)
       return bail(fail(RECON_ERR_OOM, "gradient launch data"));
     cudaMemcpy(e->d_work, work.data(), work.size() * sizeof(unsigned), cudaMemcpyHostToDevice);
     cudaMemcpy(e->d_work_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice);
-    cudaMemset(e->d_err, 0, sizeof(int));
+    cudaMemset(e->d_err, 0, FLAG_COUNT * sizeof(int));
   }
   // descriptors
   int Nt_max = 0;
@@ -403,8 +403,8 @@ recon_status recon_grad_backward(recon_grad* g, const float* const* grad_image, 
       if (grad_mu) grad_mu[q] = acc[0] + acc[1] - acc[2] * tau1 / mu;
     }
     int err[2] = {0, 0};
-    RC(cudaMemcpy(&err[0], g->fwd.d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    RC(cudaMemcpy(&err[1], g->bwd.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    RC(cudaMemcpy(&err[0], g->fwd.d_err + FLAG_ERR, sizeof(int), cudaMemcpyDeviceToHost));
+    RC(cudaMemcpy(&err[1], g->bwd.d_err + FLAG_ERR, sizeof(int), cudaMemcpyDeviceToHost));
     if ((err[0] | err[1]) & DEV_ERR_TIMEOUT) return fail(RECON_ERR_TIMEOUT, "a bounded device-side wait timed out");
   }
   return RECON_OK;

@@ -94,7 +94,7 @@ struct ColLaunch {
   int work_max;              // longest per-CTA list (staged in shared memory)
   int nb_max;                // largest block count of any slice (shared-memory sizing)
   int stages;                // ring depth (a multiple of the consumer warp count)
-  int* err;                  // device error bits of the launch
+  int* err;                  // flags array of the launch: bounded waits report in err[FLAG_ERR]
 };
 
 struct TvSlice {             // temporal step of Algorithm 2 (R = D_t) of one slice
@@ -257,6 +257,46 @@ struct ObjParams {           // ||y - H x||^2 of a given field (no inverse)
   const int* flags;
   int grid;                  // blocks of the warp-per-(column, coil) kernel
 };
+
+// Persistent solve of Algorithm 2 with temporal TV (persist_kernels.cu): all
+// K iterations of a set of slices in one cooperative launch, FP32 inverses,
+// Nt <= kPersistNtMax.  The per-column counters colcnt and tdone ([Nx] per
+// slice) must be zero at the launch.
+constexpr int kPersistNtMax = 40;
+struct PersistSlice {
+  const void* A;             // packed inverses
+  long long col_elems;
+  int Nx, Ny, Nt, nb, nunits;
+  const float2* b;           // H'y   [Nt][Nx][Ny]
+  float2* x;                 // x
+  float2* m[2];              // state by iteration parity
+  float2* d1[2];
+  float2* p[2];
+  float mu, tau1, rho;
+  const float* thomas;       // [Nt] pivots of (rho I + D'D)
+  float w_bx, w_xr, w_xx;    // objective weights (see ColSlice)
+  int do_obj;
+  double* trace_fid;         // [K + 2]
+  double* trace_prior;
+  unsigned* colcnt;          // [Nx] completed frames of the current iteration
+  unsigned* tdone;           // [Nx] temporal steps done in this launch (T_{k+1} sets k)
+};
+
+struct PersistLaunch {
+  const PersistSlice* slices;
+  int nslices;
+  const unsigned* work;      // (slice << 24) | (t * Nx + i), image-column-major per CTA
+  const int* work_off;
+  int work_max;
+  int nb_max;
+  int stages;
+  int K;
+  int* err;
+};
+
+size_t persist_smem(int stages, int nb_max, int nslices, int work_max);
+int persist_max_stages(int nb_max, int nslices, int work_max);   // 0: does not fit
+cudaError_t launch_persist_tv(const PersistLaunch& p, int grid, cudaStream_t s);
 
 // Counts kernel launches of this library (process-wide); every launcher calls it.
 void note_launch();

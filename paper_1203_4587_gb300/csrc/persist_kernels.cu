@@ -1,0 +1,611 @@
+// Persistent solve of Algorithm 2 with temporal TV: every ADMM iteration of
+// one or many slices in one cooperative launch.
+//
+// Every step of the iteration separates along the horizontal axis (Section
+// IV-C; Section V: "separated along the horizontal axis"), so the iteration is
+// a dataflow over image columns (slice q, column i):
+//   T_k(q, i)     the v-, m- and d1-updates of iteration k for the Ny x Nt
+//                 pixels of column i (they couple the frames t), giving
+//                 p_k = m_k - d2_{k-1};
+//   I_k(q, i, t)  the x-update x = A_{i,t} (H'y + mu2 p_k) of one column, with
+//                 the data term of J(k) (the d2-update is implicit: d2 = x - p).
+// I_k(q, i, t) needs T_k(q, i); T_{k+1}(q, i) needs I_k(q, i, t) for every t.
+// No grid barrier is needed: each CTA streams its list of columns (the
+// column-inverse pipeline of colinv.cuh) for k = 1..K in turn, and
+//   * the CTA whose column completes the last frame of (q, i) in iteration k
+//     (a per-column atomic counter) queues T_{k+1}(q, i) to its own four
+//     temporal warps, which publish it in tdone[q][i] = k;
+//   * the r loader waits (bounded) for tdone[q][i] >= k - 1 before it reads
+//     p_k of a column of iteration k.
+// Every dependency points to an earlier iteration, so with all CTAs resident
+// (a cooperative launch) every wait ends; each still has a wall-clock limit
+// after which the kernel sets DEV_ERR_TIMEOUT and leaves.  State buffers
+// alternate by iteration parity as in the per-iteration launches, so the
+// ADMM residuals and the final image read the same buffers.  T_1 (from
+// x = m = p = H'y) runs before the launch; T_{K+1} only forms ||D_t x_K||_1.
+#include "colinv.cuh"
+#include "plan.h"
+
+namespace recon {
+
+constexpr int kPersistTWarps = 4;                 // temporal warps
+constexpr int kPersistTThreads = 32 * kPersistTWarps;
+constexpr int kPersistSeg = 8;                    // Thomas segments (as in k_tv_temporal)
+constexpr int kPersistPx = kPersistTThreads / kPersistSeg;   // pixels per temporal chunk
+constexpr int kPersistLMax = kPersistNtMax / kPersistSeg;   // frames per segment
+constexpr int kPersistQ = 16;                     // temporal task queue depth
+
+__host__ __device__ constexpr int persist_threads() { return col_threads(8) + kPersistTThreads; }
+
+struct PersistLayout {
+  ColLayout c;   // the column-inverse regions; c.slices holds PersistSlice entries
+  size_t tq, tbars, segA, segB, bnd, red, total;
+};
+
+__host__ __device__ inline PersistLayout persist_layout(int stages, int nb, int nslices, int work_max) {
+  PersistLayout L;
+  // the column-inverse layout without its slice table, then a table of
+  // PersistSlice entries, the work list and the temporal warps' regions
+  L.c = col_layout(stages, nb, 0, 0, 8);
+  size_t o = align_up(L.c.slices, 16);
+  L.c.slices = o; o += (size_t)nslices * sizeof(PersistSlice);
+  o = align_up(o, 16);
+  L.c.skip = o;
+  L.c.work = o; o += (size_t)work_max * 4;
+  o = align_up(o, 16);
+  L.tq = o; o += kPersistQ * sizeof(int4);
+  L.tbars = o; o += 2 * kPersistQ * 8;
+  L.segA = o; o += kPersistSeg * kPersistPx * sizeof(float);
+  o = align_up(o, 16);
+  L.segB = o; o += kPersistSeg * kPersistPx * sizeof(float2);
+  L.bnd = o; o += kPersistSeg * kPersistPx * sizeof(float2);
+  L.red = o; o += 32 * sizeof(double);
+  L.total = align_up(o, 128);
+  return L;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait until *p >= want (acquire).  False on timeout (DEV_ERR_TIMEOUT
+// set) or when another CTA has reported an error.
+__device__ __forceinline__ bool wait_at_least(const unsigned* p, unsigned want, int* flags) {
+  if (ld_acquire_u32(p) >= want) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
+    __nanosleep(64);
+    if (ld_acquire_u32(p) >= want) return true;
+    if ((it & 63u) == 0) {
+      if (*((volatile int*)&flags[FLAG_ERR]) != 0) return false;
+      if (global_ns() - t0 > kWaitLimitNs) { atomicOr(&flags[FLAG_ERR], DEV_ERR_TIMEOUT); return false; }
+    }
+  }
+}
+
+__device__ __forceinline__ void tbar() { named_bar_sync(1, kPersistTThreads); }
+
+// T_{k+1}(q, i) by the temporal warps (thread tid of kPersistTThreads): the
+// arithmetic of k_tv_temporal for pixel j = chunk * kPersistPx + px, frames
+// [ta, tb) of segment seg, held in registers.  k == K: only ||D_t x_K||_1.
+__device__ void persist_temporal(const PersistSlice& S, int i, int k, int K, int tid, float* segA, float2* segB,
+                                 float2* bnd, double* red) {
+  const int Nx = S.Nx, Ny = S.Ny, Nt = S.Nt;
+  const bool write = k < K;
+  const int in = k & 1, out = (k + 1) & 1;
+  const int seg = tid / kPersistPx, px = tid - seg * kPersistPx;
+  const int Ls = (Nt + kPersistSeg - 1) / kPersistSeg;
+  const int ta = min(Nt, seg * Ls), tb = min(Nt, ta + Ls), n = tb - ta;
+  const size_t fstride = (size_t)Nx * Ny;            // one frame
+  const float2 z2 = make_float2(0.f, 0.f);
+  const float2* X = S.x;
+  const float2* Mi = S.m[in];
+  const float2* D1i = S.d1[in];
+  const float2* Pi = S.p[in];
+  float tvf = 0.f;
+  for (int c0 = 0; c0 < Ny; c0 += kPersistPx) {
+    const int j = c0 + px;
+    const bool ok = j < Ny;
+    const size_t base = (size_t)i * Ny + j;          // pixel (i, j) of frame 0
+    // xs: x then rhs; ms: m then d then m'; ds: d1 then e; ps: p then f
+    float2 xs[kPersistLMax], ms[kPersistLMax], ds[kPersistLMax], ps[kPersistLMax];
+    float2 xn = z2, mn = z2, mp = z2, dp = z2;
+#pragma unroll
+    for (int u = 0; u < kPersistLMax; ++u) {
+      xs[u] = ms[u] = ds[u] = ps[u] = z2;
+      if (ok && u < n) {
+        const size_t g = (size_t)(ta + u) * fstride + base;
+        xs[u] = __ldcg(X + g);
+        if (write) {
+          ms[u] = __ldcg(Mi + g);
+          ps[u] = __ldcg(Pi + g);
+          if (ta + u + 1 < Nt) ds[u] = __ldcg(D1i + g);
+        }
+      }
+    }
+    if (ok && n > 0 && tb < Nt) {
+      xn = __ldcg(X + (size_t)tb * fstride + base);
+      if (write) mn = __ldcg(Mi + (size_t)tb * fstride + base);
+    }
+    if (ok && n > 0 && ta > 0 && write) {
+      mp = __ldcg(Mi + (size_t)(ta - 1) * fstride + base);
+      dp = __ldcg(D1i + (size_t)(ta - 1) * fstride + base);
+    }
+    // ||D_t x_k||_1 (FP32 per thread, FP64 across the warps)
+#pragma unroll
+    for (int u = 0; u < kPersistLMax; ++u)
+      if (ok && u < n && ta + u + 1 < Nt) tvf += c_abs(c_sub(u + 1 < n ? xs[u + 1] : xn, xs[u]));
+    if (!write) continue;
+    // e_t = d1_t - S(m_{t+1} - m_t + d1_t) (t < Nt - 1), e_{ta-1} recomputed from its own inputs
+    float2 eprev = z2;
+    if (ok && n > 0 && ta > 0) eprev = c_sub(dp, c_soft(c_add(c_sub(ms[0], mp), dp), S.tau1));
+#pragma unroll
+    for (int u = 0; u < kPersistLMax; ++u)
+      if (u < n) ds[u] = (ta + u + 1 < Nt) ? c_sub(ds[u], c_soft(c_add(c_sub(u + 1 < n ? ms[u + 1] : mn, ms[u]), ds[u]), S.tau1))
+                                          : z2;
+    // rhs_t = e_t - e_{t-1} + rho (2 x_t - p_t) into xs;  f_t = p_t - x_t into ps
+#pragma unroll
+    for (int u = 0; u < kPersistLMax; ++u) {
+      if (u < n) {
+        const float2 x_t = xs[u], p_t = ps[u];
+        float2 rhs = c_sub(ds[u], u > 0 ? ds[u - 1] : eprev);
+        rhs.x = fmaf(S.rho, 2.f * x_t.x - p_t.x, rhs.x);
+        rhs.y = fmaf(S.rho, 2.f * x_t.y - p_t.y, rhs.y);
+        xs[u] = rhs;
+        ps[u] = c_sub(p_t, x_t);
+      }
+    }
+    // forward recurrence d_t = inv_t (rhs_t + d_{t-1}) by segments
+    {
+      float A = 1.f;
+      float2 B = z2;
+#pragma unroll
+      for (int u = 0; u < kPersistLMax; ++u)
+        if (u < n) {
+          const float inv = __ldg(S.thomas + ta + u);
+          A *= inv;
+          B = c_scale(c_add(xs[u], B), inv);
+        }
+      segA[seg * kPersistPx + px] = A;
+      segB[seg * kPersistPx + px] = B;
+    }
+    tbar();
+    {
+      float2 d = z2;
+      for (int qq = 0; qq < seg; ++qq) d = c_add(c_scale(d, segA[qq * kPersistPx + px]), segB[qq * kPersistPx + px]);
+#pragma unroll
+      for (int u = 0; u < kPersistLMax; ++u)
+        if (u < n) {
+          d = c_scale(c_add(xs[u], d), __ldg(S.thomas + ta + u));
+          ms[u] = d;
+        }
+    }
+    tbar();
+    // backward recurrence m'_t = d_t + inv_t m'_{t+1} by segments
+    {
+      float A = 1.f;
+      float2 B = z2;
+#pragma unroll
+      for (int u = kPersistLMax - 1; u >= 0; --u)
+        if (u < n) {
+          const float inv = __ldg(S.thomas + ta + u);
+          B = make_float2(fmaf(inv, B.x, ms[u].x), fmaf(inv, B.y, ms[u].y));
+          A *= inv;
+        }
+      segA[seg * kPersistPx + px] = A;
+      segB[seg * kPersistPx + px] = B;
+    }
+    tbar();
+    {
+      float2 mm = z2;
+      for (int qq = kPersistSeg - 1; qq > seg; --qq)
+        mm = c_add(c_scale(mm, segA[qq * kPersistPx + px]), segB[qq * kPersistPx + px]);
+#pragma unroll
+      for (int u = kPersistLMax - 1; u >= 0; --u)
+        if (u < n) {
+          const float inv = __ldg(S.thomas + ta + u);
+          mm = make_float2(fmaf(inv, mm.x, ms[u].x), fmaf(inv, mm.y, ms[u].y));
+          ms[u] = mm;
+        }
+      bnd[seg * kPersistPx + px] = n > 0 ? ms[0] : z2;   // m'_{ta}, read by the previous segment
+    }
+    tbar();
+    // m', d1' = e + D m', p' = m' + f
+    if (ok) {
+      const float2 mnext = (tb < Nt) ? bnd[(seg + 1) * kPersistPx + px] : z2;
+      float2* Mo = S.m[out];
+      float2* Do = S.d1[out];
+      float2* Po = S.p[out];
+#pragma unroll
+      for (int u = 0; u < kPersistLMax; ++u)
+        if (u < n) {
+          const size_t g = (size_t)(ta + u) * fstride + base;
+          Mo[g] = ms[u];
+          Po[g] = c_add(ms[u], ps[u]);
+          if (ta + u + 1 < Nt) Do[g] = c_add(ds[u], c_sub(u + 1 < n ? ms[u + 1] : mnext, ms[u]));
+        }
+    }
+  }
+  // the prior term of J at x_k
+  double v = warp_sum((double)tvf);
+  const int w = tid >> 5, lane = tid & 31;
+  if (lane == 0) red[w] = v;
+  tbar();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int q = 0; q < kPersistTWarps; ++q) s += red[q];
+    atomicAdd(S.trace_prior + k, s);
+  }
+  if (write) {
+    // publish T_{k+1}(q, i): the new state before tdone
+    __threadfence();
+    tbar();
+    if (tid == 0) st_release_u32(S.tdone + i, (unsigned)k);
+  } else {
+    tbar();
+  }
+}
+
+__global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaunch P) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using E = float2;
+  constexpr int kProducers = col_producers(8);
+  constexpr int kConsumerWarps = col_consumer_warps(8);
+  constexpr int kStage = stage_bytes(8);
+  constexpr int kLoader = kConsumerWarps + kProducers;
+  constexpr int kManager = kLoader + 1;
+  constexpr int kTWarp0 = kManager + 1;
+  const PersistLayout PL = persist_layout(P.stages, P.nb_max, P.nslices, P.work_max);
+  const ColLayout& L = PL.c;
+  const int S = P.stages, K = P.K;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
+  uint64_t* empty = full + S;
+  uint64_t* rfull = empty + S;
+  uint64_t* rempty = rfull + kRSlots;
+  uint64_t* rv_full = rempty + kRSlots;
+  uint64_t* yc_empty = rv_full + kRSlots;
+  uint64_t* col_done = yc_empty + kRSlots;
+  unsigned char* ring = smem + L.ring;
+  const int ny32m = P.nb_max * 32;
+  float2* ycopy = reinterpret_cast<float2*>(smem + L.ycopy);
+  float2* rvec = reinterpret_cast<float2*>(smem + L.rvec);
+  float2* bvec = reinterpret_cast<float2*>(smem + L.bvec);
+  float2* rslot = reinterpret_cast<float2*>(smem + L.rslot);
+  PersistSlice* sl = reinterpret_cast<PersistSlice*>(smem + L.slices);
+  int* tiles = reinterpret_cast<int*>(smem + L.tiles);
+  unsigned* wl = reinterpret_cast<unsigned*>(smem + L.work);
+  int4* tq = reinterpret_cast<int4*>(smem + PL.tq);
+  uint64_t* tq_full = reinterpret_cast<uint64_t*>(smem + PL.tbars);
+  uint64_t* tq_empty = tq_full + kPersistQ;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int m = tid; m < P.nb_max * (P.nb_max - 1) / 2; m += blockDim.x) tiles[m] = tile_pq(m);
+  for (int q = tid; q < P.nslices; q += blockDim.x) sl[q] = P.slices[q];
+  for (int j = tid; j < kRSlots * kConsumerWarps * ny32m; j += blockDim.x) ycopy[j] = make_float2(0.f, 0.f);
+  const int w0 = P.work_off[blockIdx.x], w1 = P.work_off[blockIdx.x + 1];
+  for (int w = w0 + tid; w < w1; w += blockDim.x) wl[w - w0] = P.work[w];
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int s = 0; s < kRSlots; ++s) {
+      mbar_init(&rfull[s], 1);
+      mbar_init(&rempty[s], 1);
+      mbar_init(&rv_full[s], 1);
+      mbar_init(&yc_empty[s], 1);
+      mbar_init(&col_done[s], kConsumerWarps);
+    }
+    for (int s = 0; s < kPersistQ; ++s) { mbar_init(&tq_full[s], 1); mbar_init(&tq_empty[s], 1); }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int nw = w1 - w0;            // columns per iteration
+  const int ncol = nw * K;           // columns over the whole solve
+#define WSL(w) ((int)(wl[w] >> 24))
+#define WCOL(w) ((int)(wl[w] & 0xFFFFFFu))
+
+  if (warp >= kConsumerWarps && warp < kLoader) {
+    // ---------------- producers: the packed inverses, K passes over the list ----
+    if (lane == 0) {
+      const int p = warp - kConsumerWarps;
+      const uint64_t pol = policy_evict_first();
+      int st = p, wraps = 0, gu = 0, issued = 0, ncolumn = 0;
+      bool ok = true;
+      for (int n = 0; n < ncol && ok; ++n) {
+        const int w = n % nw;
+        const PersistSlice& c = sl[WSL(w)];
+        const unsigned char* cb = reinterpret_cast<const unsigned char*>(c.A) + (size_t)WCOL(w) * (size_t)c.col_elems * 8;
+        const int rot = unit_rotation(ncolumn++, c.nunits);
+        int u = p - gu % kProducers;
+        if (u < 0) u += kProducers;
+        for (; u < c.nunits; u += kProducers) {
+          if (wraps > 0 && !mbar_wait(&empty[st], (uint32_t)((wraps - 1) & 1), P.err)) { ok = false; break; }
+          const int4 un = decode_unit(rotated_unit(u, rot, c.nunits), c.nb, tiles);
+          const uint32_t bytes = (uint32_t)((un.x == UNIT_TILE ? kTileElems : kDiagElems) * 8);
+          mbar_arrive_expect_tx(&full[st], bytes);
+          bulk_g2s(ring + (size_t)st * kStage, cb + (size_t)un.w * 8, bytes, &full[st], pol);
+          ++issued;
+          st += kProducers;
+          if (st >= S) { st -= S; ++wraps; }
+        }
+        gu += c.nunits;
+      }
+      if (!ok) {
+        const int per = S / kProducers;
+        for (int q = (issued > per ? issued - per : 0); q < issued; ++q) {
+          const long long gi = p + (long long)q * kProducers;
+          uint64_t* bb = &full[gi % S];
+          const uint32_t par = (uint32_t)((gi / S) & 1);
+          const unsigned long long t0 = global_ns();
+          while (!mbar_try_wait(bb, par) && global_ns() - t0 < kWaitLimitNs) {}
+        }
+      }
+    }
+    return;
+  }
+  if (warp == kLoader) {
+    // ---------------- r loader: b and p_k of each column, once T_k is published --
+    for (int n = 0; n < ncol; ++n) {
+      const int w = n % nw, k = n / nw + 1;
+      const PersistSlice& c = sl[WSL(w)];
+      const int col = WCOL(w), i = col % c.Nx;
+      const int slt = n % kRSlots;
+      // lane 0 waits (the slot, then T_k of this image column) and shares the outcome
+      int ok = 1;
+      if (lane == 0) {
+        if (n >= kRSlots) ok = mbar_wait(&rempty[slt], (uint32_t)(((n / kRSlots) - 1) & 1), P.err) ? 1 : 0;
+        if (ok && k >= 2) ok = wait_at_least(c.tdone + i, (unsigned)(k - 1), P.err) ? 1 : 0;
+      }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      float2* d = rslot + (size_t)slt * 3 * ny32m;
+      const size_t cofs = (size_t)col * c.Ny;
+      const float2* pk = c.p[k & 1];
+      if ((c.Ny & 1) == 0) {   // 16-byte aligned columns: two elements per access
+        for (int j = 2 * lane; j < c.Ny; j += 64) {
+          const float4 bv = __ldcg(reinterpret_cast<const float4*>(c.b + cofs + j));
+          const float4 pv = __ldcg(reinterpret_cast<const float4*>(pk + cofs + j));
+          *reinterpret_cast<float4*>(d + j) = bv;
+          *reinterpret_cast<float4*>(d + ny32m + j) = pv;
+        }
+      } else {
+        for (int j = lane; j < c.Ny; j += 32) {
+          d[j] = __ldcg(c.b + cofs + j);
+          d[ny32m + j] = __ldcg(pk + cofs + j);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&rfull[slt]);
+    }
+    return;
+  }
+  if (warp == kManager) {
+    // ---------------- column manager ------------------------------------------
+    auto prepare = [&](int n) -> bool {
+      const int w = n % nw;
+      const PersistSlice& c = sl[WSL(w)];
+      const int ny32 = c.nb * 32;
+      const int slt = n % kRSlots;
+      int got = 1;
+      if (lane == 0) got = mbar_wait(&rfull[slt], (uint32_t)((n / kRSlots) & 1), P.err) ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, got, 0)) return false;
+      const float2* d = rslot + (size_t)slt * 3 * ny32m;
+      float2* rv = rvec + (size_t)(n & 1) * ny32m;
+      float2* bv = bvec + (size_t)(n & 1) * ny32m;
+      for (int j = 2 * lane; j < ny32; j += 64) {
+        float4 v = *reinterpret_cast<const float4*>(d + j);
+        const float4 bb0 = v;
+        float4 bb = bb0;
+        const float4 a = *reinterpret_cast<const float4*>(d + ny32m + j);
+        v.x = fmaf(c.mu, a.x, v.x); v.y = fmaf(c.mu, a.y, v.y);
+        v.z = fmaf(c.mu, a.z, v.z); v.w = fmaf(c.mu, a.w, v.w);
+        if (j >= c.Ny) { v.x = v.y = 0.f; bb.x = bb.y = 0.f; }
+        if (j + 1 >= c.Ny) { v.z = v.w = 0.f; bb.z = bb.w = 0.f; }
+        *reinterpret_cast<float4*>(rv + j) = v;
+        *reinterpret_cast<float4*>(bv + j) = bb;
+      }
+      __syncwarp();
+      if (lane == 0) { mbar_arrive(&rempty[slt]); mbar_arrive(&rv_full[n & 1]); }
+      return true;
+    };
+    int tq_n = 0;   // tasks queued to the temporal warps
+    auto push = [&](int q, int i, int k) -> bool {
+      bool ok = true;
+      if (lane == 0) {
+        const int s = tq_n % kPersistQ;
+        if (tq_n >= kPersistQ) ok = mbar_wait(&tq_empty[s], (uint32_t)(((tq_n / kPersistQ) - 1) & 1), P.err);
+        if (ok) {
+          tq[s] = make_int4(q, i, k, 0);
+          mbar_arrive(&tq_full[s]);
+        }
+      }
+      ++tq_n;
+      return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    };
+    double fid = 0.0;
+    int fid_slice = -1, fid_k = -1;
+    bool ok = true;
+    for (int n = 0; n < ncol && n < kRSlots && ok; ++n) ok = prepare(n);
+    for (int n = 0; n < ncol && ok; ++n) {
+      const int bb = n & 1;
+      const int w = n % nw, k = n / nw + 1;
+      const int q = WSL(w);
+      const PersistSlice& c = sl[q];
+      int got = 1;
+      if (lane == 0) got = mbar_wait(&col_done[bb], (uint32_t)((n >> 1) & 1), P.err) ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, got, 0)) break;
+      if (q != fid_slice || k != fid_k) {
+        if (fid_slice >= 0 && sl[fid_slice].do_obj) {
+          const double f = warp_sum(fid);
+          if (lane == 0) atomicAdd(sl[fid_slice].trace_fid + fid_k, f);
+        }
+        fid = 0.0;
+        fid_slice = q;
+        fid_k = k;
+      }
+      const int ny32 = c.nb * 32;
+      const int col = WCOL(w);
+      const size_t cofs = (size_t)col * c.Ny;
+      float2* yc = ycopy + (size_t)bb * kConsumerWarps * ny32m;
+      const float2* rv = rvec + (size_t)bb * ny32m;
+      const float2* bv = bvec + (size_t)bb * ny32m;
+      float fcol = 0.f;
+      const bool vec_out = ((cofs & 1) == 0);
+      for (int j = 2 * lane; j < ny32; j += 64) {
+        float4 x = *reinterpret_cast<const float4*>(yc + j);
+        *reinterpret_cast<float4*>(yc + j) = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int ww = 1; ww < kConsumerWarps; ++ww) {
+          float4* pw = reinterpret_cast<float4*>(yc + (size_t)ww * ny32m + j);
+          const float4 t = *pw;
+          x.x += t.x; x.y += t.y; x.z += t.z; x.w += t.w;
+          *pw = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (j + 1 < c.Ny && vec_out) {
+          *reinterpret_cast<float4*>(c.x + cofs + j) = x;
+        } else {
+          if (j < c.Ny) c.x[cofs + j] = make_float2(x.x, x.y);
+          if (j + 1 < c.Ny) c.x[cofs + j + 1] = make_float2(x.z, x.w);
+        }
+        if (c.do_obj) {
+          if (j >= c.Ny) x.x = x.y = 0.f;
+          if (j + 1 >= c.Ny) x.z = x.w = 0.f;
+          const float4 r = *reinterpret_cast<const float4*>(rv + j), b = *reinterpret_cast<const float4*>(bv + j);
+          float f = c.w_bx * fmaf(b.x, x.x, fmaf(b.y, x.y, fmaf(b.z, x.z, b.w * x.w)));
+          f = fmaf(c.w_xr, fmaf(x.x, r.x, fmaf(x.y, r.y, fmaf(x.z, r.z, x.w * r.w))), f);
+          f = fmaf(c.w_xx, fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, x.w * x.w))), f);
+          fcol += f;
+        }
+      }
+      fid += (double)fcol;
+      // x of this column is stored: count the frame; the last frame of (q, i)
+      // in iteration k queues T_{k+1}(q, i) (the prior term alone at k = K)
+      __threadfence();
+      __syncwarp();
+      int last = 0;
+      if (lane == 0) {
+        const int i = col % c.Nx;
+        const unsigned old = atomicAdd(c.colcnt + i, 1u);
+        if (old + 1 == (unsigned)c.Nt) {
+          atomicExch(c.colcnt + i, 0u);
+          __threadfence();
+          last = 1;
+        }
+      }
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (lane == 0) mbar_arrive(&yc_empty[bb]);
+      if (last && !push(q, col % c.Nx, k)) break;
+      if (n + kRSlots < ncol) ok = prepare(n + kRSlots);
+    }
+    if (fid_slice >= 0 && sl[fid_slice].do_obj) {
+      fid = warp_sum(fid);
+      if (lane == 0) atomicAdd(sl[fid_slice].trace_fid + fid_k, fid);
+    }
+    push(-1, 0, 0);   // end of the temporal tasks
+    return;
+  }
+  if (warp >= kTWarp0) {
+    // ---------------- temporal warps: T_{k+1} of the columns this CTA completed --
+    const int ttid = tid - 32 * kTWarp0;
+    float* segA = reinterpret_cast<float*>(smem + PL.segA);
+    float2* segB = reinterpret_cast<float2*>(smem + PL.segB);
+    float2* bnd = reinterpret_cast<float2*>(smem + PL.bnd);
+    double* red = reinterpret_cast<double*>(smem + PL.red);
+    volatile int* tq_ok = reinterpret_cast<volatile int*>(red + 31);
+    for (int n = 0;; ++n) {
+      const int s = n % kPersistQ;
+      // one thread waits and the outcome is shared, so all temporal threads
+      // take the same path through the named barriers
+      if (ttid == 0) *tq_ok = mbar_wait(&tq_full[s], (uint32_t)((n / kPersistQ) & 1), P.err) ? 1 : 0;
+      tbar();
+      const bool got = *tq_ok != 0;
+      const int4 task = got ? tq[s] : make_int4(-1, 0, 0, 0);
+      tbar();
+      if (!got) break;
+      if (ttid == 0) mbar_arrive(&tq_empty[s]);
+      if (task.x < 0) break;
+      persist_temporal(sl[task.x], task.y, task.z, K, ttid, segA, segB, bnd, red);
+    }
+    return;
+  }
+
+  // ---------------- consumers (as in k_col_inverse) --------------------------
+  const int dlr = lane >> 2, dlc = lane & 3;
+  const bool diag_has = dlr <= 2 * dlc + 1;
+  const int diag_off = diag_has ? (dlc * (dlc + 1) + dlr) * 2 : 0;
+  int u = warp, st = warp;
+  uint32_t ph = 0;
+  for (int n = 0; n < ncol; ++n) {
+    const PersistSlice& c = sl[WSL(n % nw)];
+    const int bb = n & 1;
+    if (!mbar_wait(&rv_full[bb], (uint32_t)((n >> 1) & 1), P.err)) break;
+    if (n >= 2 && !mbar_wait(&yc_empty[bb], (uint32_t)(((n >> 1) - 1) & 1), P.err)) break;
+    const float2* rv = rvec + (size_t)bb * ny32m;
+    float2* yw = ycopy + ((size_t)bb * kConsumerWarps + warp) * ny32m;
+    bool failed = false;
+    const int rot = unit_rotation(n, c.nunits);
+    for (; u < c.nunits; u += kConsumerWarps) {
+      if (!mbar_wait(&full[st], ph, P.err)) { failed = true; break; }
+      const int4 un = decode_unit(rotated_unit(u, rot, c.nunits), c.nb, tiles);
+      const E* tl = reinterpret_cast<const E*>(ring + (size_t)st * kStage);
+      if (un.x == UNIT_TILE) proc_tile<E>(tl, rv, yw, un.y, un.z, lane, &empty[st], 64, lane * 2, true);
+      else proc_tile<E>(tl, rv, yw, un.y, un.z, lane, &empty[st], 2 * kDiagLanes, diag_off, diag_has);
+      st += kConsumerWarps;
+      if (st >= S) { st -= S; ph ^= 1u; }
+    }
+    if (failed) break;
+    u -= c.nunits;
+    if (lane == 0) mbar_arrive(&col_done[bb]);
+  }
+#undef WSL
+#undef WCOL
+}
+
+size_t persist_smem(int stages, int nb_max, int nslices, int work_max) {
+  return persist_layout(stages, nb_max, nslices, work_max).total;
+}
+
+int persist_max_stages(int nb_max, int nslices, int work_max) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int qn = col_consumer_warps(8);
+  int s = 8 * qn;
+  while (s > qn) {
+    if (persist_smem(s, nb_max, nslices, work_max) + 1024 <= (size_t)optin) break;
+    s -= qn;
+  }
+  return (persist_smem(s, nb_max, nslices, work_max) + 1024 <= (size_t)optin) ? s : 0;
+}
+
+cudaError_t launch_persist_tv(const PersistLaunch& p, int grid, cudaStream_t s) {
+  const size_t smem = persist_smem(p.stages, p.nb_max, p.nslices, p.work_max);
+  static int configured_dev = -1;
+  static size_t configured = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != configured_dev || smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_persist_tv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured_dev = dev;
+    configured = smem;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(persist_threads());
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;   // every CTA resident: the dataflow waits all end
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_persist_tv, p);
+  note_launch();
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace recon

@@ -41,7 +41,7 @@ struct Engine {
   unsigned* d_work = nullptr;
   int* d_work_off = nullptr;
   int grid = 0, nb_max = 0, stages = 0, work_max = 0;
-  int* d_err = nullptr;    // error word shared by the engine's launches
+  int* d_err = nullptr;    // flags array of the engine's launches (a single plan: its own); errors in [FLAG_ERR]
   FinSlice* d_fin = nullptr;
   // spatio-temporal prior: CG steps, per-block partial sums, per-slice block
   // counters and reduction slots (K sets of 2 cg + 1 per slice)
@@ -51,6 +51,14 @@ struct Engine {
   double* d_stv_part = nullptr;
   unsigned* d_stv_count = nullptr;
   std::vector<double*> stv_red;
+  // the persistent TV solve (persist_kernels.cu): all K iterations in one launch
+  bool persist = false;
+  PersistSlice* d_pslice = nullptr;
+  unsigned* d_pwork = nullptr;  // per-CTA column lists, image-column-major
+  int* d_pwork_off = nullptr;
+  int pwork_max = 0, pstages = 0;
+  unsigned* d_pcount = nullptr; // colcnt and tdone of every slice (2 sum Nx), zeroed per solve
+  size_t pcount_n = 0;
   std::vector<unsigned> gens;   // each plan's generation when this engine was built
   DevArena arena;
 };
@@ -146,6 +154,7 @@ struct recon_batch {
   cudaGraphExec_t graph = nullptr;
   std::vector<const void*> key;        // buffers the captured graph reads / writes
   cudaStream_t cap_stream = nullptr;
+  bool no_graph = false;               // capture failed once: every call runs the launches directly
   ~recon_batch();
 };
 

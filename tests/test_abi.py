@@ -70,6 +70,13 @@ def test_invalid_arguments_rejected_before_any_cuda_call(libpath):
     st = lib.recon_plan_create(C.byref(h), 4, 4, 2, 1, C.cast(mask, C.c_void_p), C.cast(sens, C.c_void_p),
                                0.01, 0.1, 0, C.byref(bad), None)
     assert st == 1
+    bad = binding.Opts()
+    lib.recon_default_opts(C.byref(bad))
+    assert bad.persistent == 1
+    bad.persistent = 2
+    st = lib.recon_plan_create(C.byref(h), 4, 4, 2, 1, C.cast(mask, C.c_void_p), C.cast(sens, C.c_void_p),
+                               0.01, 0.1, 0, C.byref(bad), None)
+    assert st == 1
     for field, value in (("cg_steps", 0), ("cg_steps", 65), ("spatial_weight", -0.5)):   # spatio-temporal prior
         bad = binding.Opts()
         lib.recon_default_opts(C.byref(bad))
@@ -94,7 +101,7 @@ def test_invalid_arguments_rejected_before_any_cuda_call(libpath):
     assert lib.recon_status_string(2) == b"RECON_ERR_MASK_NOT_CARTESIAN"
 
 
-@pytest.mark.parametrize("name,cls", [("recon_opts", "Opts"), ("recon_info", "Info")])
+@pytest.mark.parametrize("name,cls", [("recon_opts", "Opts"), ("recon_info", "Info"), ("recon_profile", "Profile")])
 def test_struct_matches_header(name, cls):
     """The binding's ctypes structs list the header's fields in order and type."""
     import re
