@@ -40,6 +40,20 @@ namespace recon {
 
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaError_t SmemAttrCache::ensure(const void* kernel, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices)
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes <= v[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  size_t cur = v[dev].load(std::memory_order_relaxed);
+  while (cur < bytes && !v[dev].compare_exchange_weak(cur, bytes, std::memory_order_relaxed)) {}
+  return cudaSuccess;
+}
 void set_last_error(const std::string& why) { g_last_error = why; }
 
 void fill_twiddles_host(int n, float2* tw) {

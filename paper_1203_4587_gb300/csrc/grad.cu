@@ -112,11 +112,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_tv_backward(const TvBwdSlice* s
 
 static cudaError_t launch_tv_backward(const TvBwdSlice* sls, int nslices, int nblocks, int Nt_max, cudaStream_t s) {
   const size_t smem = (size_t)Nt_max * kBwdThreads * sizeof(float2);
-  static size_t configured = 0;
-  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
-    cudaError_t e = cudaFuncSetAttribute(k_tv_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static SmemAttrCache attr;
+  {
+    const cudaError_t e = attr.ensure(reinterpret_cast<const void*>(k_tv_backward), smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   k_tv_backward<<<nblocks, kBwdThreads, smem, s>>>(sls, nslices);
   note_launch();

@@ -402,23 +402,12 @@ int col_inverse_max_stages(int nb_max, int nslices, int work_max, int esize) {
 
 int col_inverse_stage_quantum(int esize) { return col_consumer_warps(esize); }
 
-template <typename E>
-static size_t& col_configured() {
-  static size_t v = 0;
-  return v;
-}
-
 cudaError_t prepare_col_inverse(int storage, size_t smem) {
-  auto go = [&](auto kern, size_t& conf) -> cudaError_t {
-    if (smem <= conf) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) conf = smem;
-    return e;
-  };
+  static SmemAttrCache c32, c16, cb16;
   switch (storage) {
-    case 0: return go(k_col_inverse<float2>, col_configured<float2>());
-    case 1: return go(k_col_inverse<__half2>, col_configured<__half2>());
-    case 2: return go(k_col_inverse<__nv_bfloat162>, col_configured<__nv_bfloat162>());
+    case 0: return c32.ensure(reinterpret_cast<const void*>(k_col_inverse<float2>), smem);
+    case 1: return c16.ensure(reinterpret_cast<const void*>(k_col_inverse<__half2>), smem);
+    case 2: return cb16.ensure(reinterpret_cast<const void*>(k_col_inverse<__nv_bfloat162>), smem);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -666,19 +655,14 @@ int tv_tile_px(int Nt_max) {
 }
 
 cudaError_t prepare_tv_temporal(int Nt_max, int px) {
-  static size_t configured[3] = {0, 0, 0};
+  static SmemAttrCache c[3];
   const size_t smem = tv_smem(Nt_max, px);
-  const int k = px == 16 ? 0 : px == 32 ? 1 : px == 64 ? 2 : -1;
-  if (k < 0) return cudaErrorInvalidValue;
-  if (smem > configured[k]) {   // also below 48 KB: static shared memory counts toward that limit
-    cudaError_t e = cudaSuccess;
-    if (px == 16) e = cudaFuncSetAttribute(k_tv_temporal<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (px == 32) e = cudaFuncSetAttribute(k_tv_temporal<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (px == 64) e = cudaFuncSetAttribute(k_tv_temporal<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured[k] = smem;
+  switch (px) {
+    case 16: return c[0].ensure(reinterpret_cast<const void*>(k_tv_temporal<16>), smem);
+    case 32: return c[1].ensure(reinterpret_cast<const void*>(k_tv_temporal<32>), smem);
+    case 64: return c[2].ensure(reinterpret_cast<const void*>(k_tv_temporal<64>), smem);
+    default: return cudaErrorInvalidValue;
   }
-  return cudaSuccess;
 }
 
 cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s) {
@@ -770,21 +754,15 @@ __global__ void __launch_bounds__(256) k_dft_temporal(TemporalLaunch L) {
 }
 
 cudaError_t prepare_dft_temporal(int Nt_max, int px) {
-  static size_t configured[4] = {0, 0, 0, 0};
+  static SmemAttrCache c[4];
   const size_t smem = dft_smem(Nt_max, px);
-  const int k = px == 16 ? 0 : px == 32 ? 1 : px == 64 ? 2 : px == 128 ? 3 : -1;
-  if (k < 0) return cudaErrorInvalidValue;
-  if (smem > configured[k]) {   // also below 48 KB: static shared memory counts toward that limit
-    cudaError_t e = cudaSuccess;
-    const int b = (int)smem;
-    if (px == 16) e = cudaFuncSetAttribute(k_dft_temporal<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (px == 32) e = cudaFuncSetAttribute(k_dft_temporal<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (px == 64) e = cudaFuncSetAttribute(k_dft_temporal<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (px == 128) e = cudaFuncSetAttribute(k_dft_temporal<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e != cudaSuccess) return e;
-    configured[k] = smem;
+  switch (px) {
+    case 16: return c[0].ensure(reinterpret_cast<const void*>(k_dft_temporal<16>), smem);
+    case 32: return c[1].ensure(reinterpret_cast<const void*>(k_dft_temporal<32>), smem);
+    case 64: return c[2].ensure(reinterpret_cast<const void*>(k_dft_temporal<64>), smem);
+    case 128: return c[3].ensure(reinterpret_cast<const void*>(k_dft_temporal<128>), smem);
+    default: return cudaErrorInvalidValue;
   }
-  return cudaSuccess;
 }
 
 cudaError_t launch_dft_temporal(const TemporalLaunch& p, cudaStream_t s) {
@@ -939,19 +917,15 @@ __global__ void __launch_bounds__(256) k_haar_temporal(TemporalLaunch L, int lev
 }
 
 cudaError_t prepare_haar_temporal(int Nt_max, int levels, int px) {
-  static size_t configured[3] = {0, 0, 0};
+  static SmemAttrCache c[3];
   const size_t smem = haar_smem(Nt_max, levels, px);
-  const int k = px == 16 ? 0 : px == 32 ? 1 : px == 64 ? 2 : -1;
-  if (k < 0 || smem + 1024 > kSmemOptin) return cudaErrorInvalidValue;
-  if (smem > configured[k]) {
-    cudaError_t e = cudaSuccess;
-    if (px == 16) e = cudaFuncSetAttribute(k_haar_temporal<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (px == 32) e = cudaFuncSetAttribute(k_haar_temporal<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (px == 64) e = cudaFuncSetAttribute(k_haar_temporal<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured[k] = smem;
+  if (smem + 1024 > kSmemOptin) return cudaErrorInvalidValue;
+  switch (px) {
+    case 16: return c[0].ensure(reinterpret_cast<const void*>(k_haar_temporal<16>), smem);
+    case 32: return c[1].ensure(reinterpret_cast<const void*>(k_haar_temporal<32>), smem);
+    case 64: return c[2].ensure(reinterpret_cast<const void*>(k_haar_temporal<64>), smem);
+    default: return cudaErrorInvalidValue;
   }
-  return cudaSuccess;
 }
 
 cudaError_t launch_haar_temporal(const TemporalLaunch& p, int levels, cudaStream_t s) {
@@ -1131,11 +1105,10 @@ static cudaError_t launch_objective_t(const ObjParams& p, cudaStream_t s) {
     if (e != cudaSuccess || done) return e;
   }
   const size_t smem = ((size_t)p.Ny + 2 * (size_t)p.ncg * p.Ny) * sizeof(float2);
-  static size_t configured = 0;
-  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
-    cudaError_t e = cudaFuncSetAttribute(k_objective<YE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static SmemAttrCache attr;
+  {
+    const cudaError_t e = attr.ensure(reinterpret_cast<const void*>(k_objective<YE>), smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   k_objective<YE><<<p.Nx * p.Nt, 256, smem, s>>>(p); note_launch();
   return cudaGetLastError();

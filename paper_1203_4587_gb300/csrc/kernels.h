@@ -11,6 +11,7 @@
 //                  (i,t), column index col = t*Nx + i (see packing below)
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <cuda_runtime.h>
@@ -297,6 +298,16 @@ struct PersistLaunch {
 size_t persist_smem(int stages, int nb_max, int nslices, int work_max);
 int persist_max_stages(int nb_max, int nslices, int work_max);   // 0: does not fit
 cudaError_t launch_persist_tv(const PersistLaunch& p, int grid, cudaStream_t s);
+
+// The dynamic shared-memory limit of a kernel is a per-device attribute.  A
+// launcher keeps, per device ordinal, the largest limit it has set, and raises
+// it on the current device when a launch needs more (a plan on any device of
+// the process works; the first launch on a device sets its attribute).
+constexpr int kMaxDevices = 64;
+struct SmemAttrCache {
+  std::atomic<size_t> v[kMaxDevices] = {};
+  cudaError_t ensure(const void* kernel, size_t bytes);
+};
 
 // Counts kernel launches of this library (process-wide); every launcher calls it.
 void note_launch();

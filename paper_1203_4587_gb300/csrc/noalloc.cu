@@ -27,7 +27,6 @@ namespace recon {
 
 constexpr size_t kScratchBytes = 16u << 20;
 constexpr size_t kScratchStatusBytes = 256;  // status word area at the front
-constexpr int kMaxDevices = 64;
 constexpr int kNoAllocThreads = 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];

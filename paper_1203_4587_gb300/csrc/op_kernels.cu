@@ -94,12 +94,10 @@ static cudaError_t launch_rows_t(const KIn* ksp, const float* kscale, T* yhat, f
   if (maxm <= 0) return cudaSuccess;
   const int G = G_req > 0 ? std::min(G_req, row_group<T>(Nx)) : row_group<T>(Nx);
   const size_t smem = 2 * (size_t)G * (Nx + 1) * sizeof(T);
-  static size_t configured = 0;
-  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
-    cudaError_t e = cudaFuncSetAttribute(k_hybrid_rows<T, KIn>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  static SmemAttrCache attr;
+  {
+    const cudaError_t e = attr.ensure(reinterpret_cast<const void*>(k_hybrid_rows<T, KIn>), smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   dim3 grid((maxm + G - 1) / G, Nc, Nt);
   k_hybrid_rows<T, KIn><<<grid, 256, smem, s>>>(ksp, kscale, yhat, yhat32, yy, ymax, rows, rowoff, Nx, Ny, Nt, Nc,
@@ -216,12 +214,10 @@ static cudaError_t launch_combine_t(const T* yhat, const float2* sens, float2* b
   if (Ny > 1024) return cudaErrorInvalidValue;
   const int ncg = ncg_req > 0 ? std::min(ncg_req, coil_group<T>(Nc, Ny)) : coil_group<T>(Nc, Ny);
   const size_t smem = 2 * (size_t)ncg * Ny * sizeof(T);
-  static size_t configured = 0;
-  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
-    cudaError_t e = cudaFuncSetAttribute(k_adjoint_combine<T, YS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  static SmemAttrCache attr;
+  {
+    const cudaError_t e = attr.ensure(reinterpret_cast<const void*>(k_adjoint_combine<T, YS>), smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   k_adjoint_combine<T, YS><<<dim3(Nx, Nt), 256, smem, s>>>(yhat, sens, b, rows, rowoff, Nx, Ny, Nt, Nc, ncg, fy,
                                                            1.0 / sqrt((double)Ny), ylp, ymax, yscale);
@@ -340,11 +336,10 @@ cudaError_t launch_forward_cols(const float2* x, const float2* sens, float2* zha
                                 const int* rowoff, int Nx, int Ny, int Nt, int Nc, FftPlanDev fy, cudaStream_t s) {
   const int ncg = coil_group<float2>(Nc, Ny);
   const size_t smem = ((size_t)Ny + 2 * (size_t)ncg * Ny) * sizeof(float2);
-  static size_t configured = 0;
-  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
-    cudaError_t e = cudaFuncSetAttribute(k_forward_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static SmemAttrCache attr;
+  {
+    const cudaError_t e = attr.ensure(reinterpret_cast<const void*>(k_forward_cols), smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   k_forward_cols<<<dim3(Nx, Nt), 256, smem, s>>>(x, sens, zhat, rows, rowoff, Nx, Ny, Nt, Nc, ncg, fy,
                                                  (float)(1.0 / sqrt((double)Ny))); note_launch();
@@ -382,11 +377,10 @@ cudaError_t launch_forward_rows(const float2* zhat, float2* kspace, const int* r
                                 int Nx, int Ny, int Nt, int Nc, FftPlanDev fx, cudaStream_t s) {
   if (maxm <= 0) return cudaSuccess;
   const size_t smem = 2 * (size_t)kRowGroup * (Nx + 1) * sizeof(float2);
-  static size_t configured = 0;
-  if (smem > configured) {   // also below 48 KB: static shared memory counts toward that limit
-    cudaError_t e = cudaFuncSetAttribute(k_forward_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static SmemAttrCache attr;
+  {
+    const cudaError_t e = attr.ensure(reinterpret_cast<const void*>(k_forward_rows), smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   dim3 grid((maxm + kRowGroup - 1) / kRowGroup, Nc, Nt);
   k_forward_rows<<<grid, 256, smem, s>>>(zhat, kspace, rows, rowoff, Nx, Ny, Nt, Nc, fx,

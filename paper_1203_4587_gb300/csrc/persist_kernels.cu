@@ -383,14 +383,15 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
   }
   if (warp == kManager) {
     // ---------------- column manager ------------------------------------------
-    auto prepare = [&](int n) -> bool {
+    // It prepares r = H'y + mu2 p_k of column n (once its inputs are in a slot)
+    // and runs the epilogue of column n (once the consumers are done), in
+    // whichever order they become ready: column n + 1 may be the same image
+    // column one iteration later, whose p needs this column's epilogue first.
+    auto prepare = [&](int n) {   // rfull of column n has completed
       const int w = n % nw;
       const PersistSlice& c = sl[WSL(w)];
       const int ny32 = c.nb * 32;
       const int slt = n % kRSlots;
-      int got = 1;
-      if (lane == 0) got = mbar_wait(&rfull[slt], (uint32_t)((n / kRSlots) & 1), P.err) ? 1 : 0;
-      if (!__shfl_sync(0xffffffffu, got, 0)) return false;
       const float2* d = rslot + (size_t)slt * 3 * ny32m;
       float2* rv = rvec + (size_t)(n & 1) * ny32m;
       float2* bv = bvec + (size_t)(n & 1) * ny32m;
@@ -408,7 +409,6 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
       }
       __syncwarp();
       if (lane == 0) { mbar_arrive(&rempty[slt]); mbar_arrive(&rv_full[n & 1]); }
-      return true;
     };
     int tq_n = 0;   // tasks queued to the temporal warps
     auto push = [&](int q, int i, int k) -> bool {
@@ -426,16 +426,11 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
     };
     double fid = 0.0;
     int fid_slice = -1, fid_k = -1;
-    bool ok = true;
-    for (int n = 0; n < ncol && n < kRSlots && ok; ++n) ok = prepare(n);
-    for (int n = 0; n < ncol && ok; ++n) {
+    auto epilogue = [&](int n) -> bool {   // col_done of column n has completed
       const int bb = n & 1;
       const int w = n % nw, k = n / nw + 1;
       const int q = WSL(w);
       const PersistSlice& c = sl[q];
-      int got = 1;
-      if (lane == 0) got = mbar_wait(&col_done[bb], (uint32_t)((n >> 1) & 1), P.err) ? 1 : 0;
-      if (!__shfl_sync(0xffffffffu, got, 0)) break;
       if (q != fid_slice || k != fid_k) {
         if (fid_slice >= 0 && sl[fid_slice].do_obj) {
           const double f = warp_sum(fid);
@@ -496,8 +491,38 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
       }
       last = __shfl_sync(0xffffffffu, last, 0);
       if (lane == 0) mbar_arrive(&yc_empty[bb]);
-      if (last && !push(q, col % c.Nx, k)) break;
-      if (n + kRSlots < ncol) ok = prepare(n + kRSlots);
+      return !last || push(q, col % c.Nx, k);
+    };
+    // np: next column to prepare (at most kRSlots ahead of the epilogues, the
+    // r / b buffers being double-buffered); ne: next epilogue.  Lane 0 polls
+    // both barriers; a wall-clock limit on idle time ends the loop with
+    // DEV_ERR_TIMEOUT.
+    int np = 0, ne = 0;
+    unsigned long long idle0 = 0;
+    unsigned spins = 0;
+    while (ne < ncol) {
+      int act = 0;
+      if (lane == 0) {
+        if (np < ncol && np < ne + kRSlots && mbar_try_wait(&rfull[np % kRSlots], (uint32_t)((np / kRSlots) & 1)))
+          act = 1;
+        else if (ne < np && mbar_try_wait(&col_done[ne & 1], (uint32_t)((ne >> 1) & 1)))
+          act = 2;
+        else if ((++spins & 255u) == 0) {
+          if (*((volatile int*)&P.err[FLAG_ERR]) != 0) act = 3;
+          const unsigned long long now = global_ns();
+          if (idle0 == 0) idle0 = now;
+          else if (now - idle0 > kWaitLimitNs) { atomicOr(&P.err[FLAG_ERR], DEV_ERR_TIMEOUT); act = 3; }
+        }
+        if (act == 1 || act == 2) { idle0 = 0; spins = 0; }
+      }
+      act = __shfl_sync(0xffffffffu, act, 0);
+      if (act == 1) {
+        prepare(np++);
+      } else if (act == 2) {
+        if (!epilogue(ne++)) break;
+      } else if (act == 3) {
+        break;
+      }
     }
     if (fid_slice >= 0 && sl[fid_slice].do_obj) {
       fid = warp_sum(fid);
@@ -582,15 +607,10 @@ int persist_max_stages(int nb_max, int nslices, int work_max) {
 
 cudaError_t launch_persist_tv(const PersistLaunch& p, int grid, cudaStream_t s) {
   const size_t smem = persist_smem(p.stages, p.nb_max, p.nslices, p.work_max);
-  static int configured_dev = -1;
-  static size_t configured = 0;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev != configured_dev || smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_persist_tv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static SmemAttrCache smem_attr;
+  {
+    const cudaError_t e = smem_attr.ensure(reinterpret_cast<const void*>(k_persist_tv), smem);
     if (e != cudaSuccess) return e;
-    configured_dev = dev;
-    configured = smem;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
