@@ -720,13 +720,13 @@ __global__ void __launch_bounds__(256) k_dft_temporal(TemporalLaunch L) {
   float2* W = fft_run(A, B, kDftPix, 1, kDftPix, P.ft, false, tid, nth, bar);
   float2* O = (W == A) ? B : A;
   const float sc = rsqrtf((float)Nt);
-  float l1f = 0.f;   // per-thread FP32 partial (a few terms), FP64 across the block
+  double l1 = 0.0;   // per element in FP64: the sum does not depend on the tile width
   for (int idx = tid; idx < Nt * kDftPix; idx += nth) {
     const int t = idx / kDftPix, pp = idx - t * kDftPix;
     float2 uo = make_float2(0.f, 0.f);
     if (pp < npx) {
       const float2 w = c_scale(W[idx], sc);
-      l1f += c_abs(w);
+      l1 += (double)c_abs(w);
       if (P.write_state) {
         const float2 d = P.first ? make_float2(0.f, 0.f) : c_sub(P.u[t * N + pix0 + pp], w);
         const float2 v = c_soft(c_sub(w, d), P.tau);
@@ -749,7 +749,7 @@ __global__ void __launch_bounds__(256) k_dft_temporal(TemporalLaunch L) {
       }
     }
   }
-  const double s = group_sum((double)l1f, red, tid, nth, bar);
+  const double s = group_sum(l1, red, tid, nth, bar);
   if (tid == 0) atomicAdd(P.prior_acc, s);
 }
 
@@ -854,8 +854,8 @@ __global__ void __launch_bounds__(256) k_haar_temporal(TemporalLaunch L, int lev
   }
   for (int idx = tid; idx < T; idx += nth) W[(size_t)levels * T + idx] = a[idx];
   bar();
-  // w, ||w||_1 (per-thread FP32 partial, FP64 across the block), the v- and d-updates
-  float l1f = 0.f;
+  // w, ||w||_1 (per element in FP64: independent of the tile width), the v- and d-updates
+  double l1 = 0.0;
   const size_t NU = (size_t)Nt * N;          // one channel of u in global memory
   for (int idx = tid; idx < nch * T; idx += nth) {
     const int c = idx / T, rem = idx - c * T;
@@ -865,7 +865,7 @@ __global__ void __launch_bounds__(256) k_haar_temporal(TemporalLaunch L, int lev
       const size_t g = (size_t)c * NU + (size_t)t * N + pix0 + pp;
       const float2 up = P.first ? make_float2(0.f, 0.f) : P.u[g];
       const float2 w = c_add(up, W[idx]);
-      l1f += c_abs(w);
+      l1 += (double)c_abs(w);
       if (P.write_state) {
         const float2 d = P.first ? make_float2(0.f, 0.f) : c_sub(up, w);
         const float2 v = c_soft(c_sub(w, d), P.tau);
@@ -912,7 +912,7 @@ __global__ void __launch_bounds__(256) k_haar_temporal(TemporalLaunch L, int lev
       }
     }
   }
-  const double sum = group_sum((double)l1f, red, tid, nth, bar);
+  const double sum = group_sum(l1, red, tid, nth, bar);
   if (tid == 0) atomicAdd(P.prior_acc, sum);
 }
 

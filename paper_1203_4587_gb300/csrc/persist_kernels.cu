@@ -299,6 +299,7 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
       mbar_init(&col_done[s], kConsumerWarps);
     }
     for (int s = 0; s < kPersistQ; ++s) { mbar_init(&tq_full[s], 1); mbar_init(&tq_empty[s], 1); }
+    *reinterpret_cast<unsigned*>(smem + PL.red + 30 * sizeof(double)) = 0u;
     fence_mbar_init();
   }
   __syncthreads();
@@ -411,6 +412,7 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
       if (lane == 0) { mbar_arrive(&rempty[slt]); mbar_arrive(&rv_full[n & 1]); }
     };
     int tq_n = 0;   // tasks queued to the temporal warps
+    volatile unsigned* beat = reinterpret_cast<volatile unsigned*>(smem + PL.red + 30 * sizeof(double));
     auto push = [&](int q, int i, int k) -> bool {
       bool ok = true;
       if (lane == 0) {
@@ -503,17 +505,22 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
     while (ne < ncol) {
       int act = 0;
       if (lane == 0) {
-        if (np < ncol && np < ne + kRSlots && mbar_try_wait(&rfull[np % kRSlots], (uint32_t)((np / kRSlots) & 1)))
+        // test_wait never suspends: a suspended try_wait on one barrier could
+        // hold back the other, which may be the one its phase depends on
+        if (np < ncol && np < ne + kRSlots && mbar_test_wait(&rfull[np % kRSlots], (uint32_t)((np / kRSlots) & 1)))
           act = 1;
-        else if (ne < np && mbar_try_wait(&col_done[ne & 1], (uint32_t)((ne >> 1) & 1)))
+        else if (ne < np && mbar_test_wait(&col_done[ne & 1], (uint32_t)((ne >> 1) & 1)))
           act = 2;
-        else if ((++spins & 255u) == 0) {
-          if (*((volatile int*)&P.err[FLAG_ERR]) != 0) act = 3;
-          const unsigned long long now = global_ns();
-          if (idle0 == 0) idle0 = now;
-          else if (now - idle0 > kWaitLimitNs) { atomicOr(&P.err[FLAG_ERR], DEV_ERR_TIMEOUT); act = 3; }
+        else {
+          __nanosleep(32);
+          if ((++spins & 255u) == 0) {
+            if (*((volatile int*)&P.err[FLAG_ERR]) != 0) act = 3;
+            const unsigned long long now = global_ns();
+            if (idle0 == 0) idle0 = now;
+            else if (now - idle0 > kWaitLimitNs) { atomicOr(&P.err[FLAG_ERR], DEV_ERR_TIMEOUT); act = 3; }
+          }
         }
-        if (act == 1 || act == 2) { idle0 = 0; spins = 0; }
+        if (act == 1 || act == 2) { idle0 = 0; spins = 0; *beat = *beat + 1; }
       }
       act = __shfl_sync(0xffffffffu, act, 0);
       if (act == 1) {
@@ -539,11 +546,30 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
     float2* bnd = reinterpret_cast<float2*>(smem + PL.bnd);
     double* red = reinterpret_cast<double*>(smem + PL.red);
     volatile int* tq_ok = reinterpret_cast<volatile int*>(red + 31);
+    volatile unsigned* beat = reinterpret_cast<volatile unsigned*>(red + 30);   // the manager's progress count
     for (int n = 0;; ++n) {
       const int s = n % kPersistQ;
       // one thread waits and the outcome is shared, so all temporal threads
-      // take the same path through the named barriers
-      if (ttid == 0) *tq_ok = mbar_wait(&tq_full[s], (uint32_t)((n / kPersistQ) & 1), P.err) ? 1 : 0;
+      // take the same path through the named barriers.  A CTA may get no task
+      // for a long while in a long solve, so the limit runs from the
+      // manager's last progress, not from the start of the wait.
+      if (ttid == 0) {
+        const uint32_t par = (uint32_t)((n / kPersistQ) & 1);
+        int got = 0;
+        unsigned seen = *beat;
+        unsigned long long t0 = global_ns();
+        for (unsigned it = 0;; ++it) {
+          if (mbar_try_wait(&tq_full[s], par)) { got = 1; break; }
+          if ((it & 63u) == 63u) {
+            if (*((volatile int*)&P.err[FLAG_ERR]) != 0) break;
+            const unsigned now_beat = *beat;
+            const unsigned long long now = global_ns();
+            if (now_beat != seen) { seen = now_beat; t0 = now; }
+            else if (now - t0 > kWaitLimitNs) { atomicOr(&P.err[FLAG_ERR], DEV_ERR_TIMEOUT); break; }
+          }
+        }
+        *tq_ok = got;
+      }
       tbar();
       const bool got = *tq_ok != 0;
       const int4 task = got ? tq[s] : make_int4(-1, 0, 0, 0);
