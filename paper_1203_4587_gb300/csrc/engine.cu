@@ -258,10 +258,20 @@ recon_status engine_build_persist(Engine* e, recon_plan* const* plans, int n) {
   }
   const int stages = persist_max_stages(e->nb_max, n, work_max);
   if (stages <= 0) return RECON_OK;   // the lists do not fit in shared memory: one launch per step
-  size_t ncount = 0;
-  for (int q = 0; q < n; ++q) ncount += 2 * (size_t)plans[q]->Nx;
-  RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_pcount), ncount * sizeof(unsigned)));
-  e->pcount_n = ncount;
+  size_t ncount = 0, nx_sum = 0;
+  for (int q = 0; q < n; ++q) {
+    ncount += 2 * (size_t)plans[q]->Nx;
+    nx_sum += (size_t)plans[q]->Nx;
+  }
+  // colcnt and tdone of every slice, then the task queue's head and tail
+  RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_pcount), (ncount + 2) * sizeof(unsigned)));
+  e->pcount_n = ncount + 2;
+  // the temporal task ring: room for several iterations' tasks (one per image column each)
+  unsigned cap = 1024;
+  while (cap < 4 * nx_sum) cap <<= 1;
+  RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_tq_ring), (size_t)cap * sizeof(int4)));
+  e->tq_cap = cap;
+  e->tq_total = (unsigned)((size_t)e->K * nx_sum);
   std::vector<PersistSlice> ps(n);
   size_t o = 0;
   for (int q = 0; q < n; ++q) {
@@ -594,6 +604,7 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
   if (e->persist) {
     // T_1 from x = m = p = H'y, then iterations 1..K (with T_2..T_{K+1}) in one launch
     RC(cudaMemsetAsync(e->d_pcount, 0, e->pcount_n * sizeof(unsigned), s));
+    RC(cudaMemsetAsync(e->d_tq_ring, 0, (size_t)e->tq_cap * sizeof(int4), s));
     if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, true, s);
     if ((st = launch_tmp_set(e, 0, s)) != RECON_OK) return st;
     if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, false, s);
@@ -607,6 +618,11 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
     L.stages = e->pstages;
     L.K = K;
     L.err = e->d_err;
+    L.tq_ring = e->d_tq_ring;
+    L.tq_cap = e->tq_cap;
+    L.tq_head = e->d_pcount + e->pcount_n - 2;
+    L.tq_tail = e->d_pcount + e->pcount_n - 1;
+    L.tq_total = e->tq_total;
     if (prof) p0->mark(p0->ev_col, p0->n_col, true, s);
     RC(launch_persist_tv(L, e->grid, s));
     if (prof) p0->mark(p0->ev_col, p0->n_col, false, s);

@@ -262,7 +262,7 @@ struct ObjParams {           // ||y - H x||^2 of a given field (no inverse)
 // Persistent solve of Algorithm 2 with temporal TV (persist_kernels.cu): all
 // K iterations of a set of slices in one cooperative launch, FP32 inverses,
 // Nt <= kPersistNtMax.  The per-column counters colcnt and tdone ([Nx] per
-// slice) must be zero at the launch.
+// slice), the queue counters and the ring's tags must be zero at the launch.
 constexpr int kPersistNtMax = 40;
 struct PersistSlice {
   const void* A;             // packed inverses
@@ -293,6 +293,13 @@ struct PersistLaunch {
   int stages;
   int K;
   int* err;
+  // the global queue of temporal tasks T_{k+1}(q, i): entry (q, i, k, tag),
+  // tag = ticket + 1 once written, 0 when free; cap a power of two
+  int4* tq_ring;
+  unsigned tq_cap;
+  unsigned* tq_head;         // tickets taken by the temporal warps
+  unsigned* tq_tail;         // tasks produced
+  unsigned tq_total;         // tasks one launch produces: K * sum of Nx
 };
 
 size_t persist_smem(int stages, int nb_max, int nslices, int work_max);

@@ -13,8 +13,11 @@
 // No grid barrier is needed: each CTA streams its list of columns (the
 // column-inverse pipeline of colinv.cuh) for k = 1..K in turn, and
 //   * the CTA whose column completes the last frame of (q, i) in iteration k
-//     (a per-column atomic counter) queues T_{k+1}(q, i) to its own four
-//     temporal warps, which publish it in tdone[q][i] = k;
+//     (a per-column atomic counter) appends T_{k+1}(q, i) to a global task
+//     queue; the four temporal warps of every CTA take tasks from it by
+//     ticket (which CTA completes a column's last frame is systematic, so
+//     running the task there would pile the temporal work onto a few SMs),
+//     and publish each in tdone[q][i] = k;
 //   * the r loader waits (bounded) for tdone[q][i] >= k - 1 before it reads
 //     p_k of a column of iteration k.
 // Every dependency points to an earlier iteration, so with all CTAs resident
@@ -33,13 +36,12 @@ constexpr int kPersistTThreads = 32 * kPersistTWarps;
 constexpr int kPersistSeg = 8;                    // Thomas segments (as in k_tv_temporal)
 constexpr int kPersistPx = kPersistTThreads / kPersistSeg;   // pixels per temporal chunk
 constexpr int kPersistLMax = kPersistNtMax / kPersistSeg;   // frames per segment
-constexpr int kPersistQ = 16;                     // temporal task queue depth
 
 __host__ __device__ constexpr int persist_threads() { return col_threads(8) + kPersistTThreads; }
 
 struct PersistLayout {
   ColLayout c;   // the column-inverse regions; c.slices holds PersistSlice entries
-  size_t tq, tbars, segA, segB, bnd, red, total;
+  size_t segA, segB, bnd, red, total;
 };
 
 __host__ __device__ inline PersistLayout persist_layout(int stages, int nb, int nslices, int work_max) {
@@ -53,8 +55,6 @@ __host__ __device__ inline PersistLayout persist_layout(int stages, int nb, int 
   L.c.skip = o;
   L.c.work = o; o += (size_t)work_max * 4;
   o = align_up(o, 16);
-  L.tq = o; o += kPersistQ * sizeof(int4);
-  L.tbars = o; o += 2 * kPersistQ * 8;
   L.segA = o; o += kPersistSeg * kPersistPx * sizeof(float);
   o = align_up(o, 16);
   L.segB = o; o += kPersistSeg * kPersistPx * sizeof(float2);
@@ -81,6 +81,19 @@ __device__ __forceinline__ bool wait_at_least(const unsigned* p, unsigned want, 
   for (unsigned it = 1;; ++it) {
     __nanosleep(64);
     if (ld_acquire_u32(p) >= want) return true;
+    if ((it & 63u) == 0) {
+      if (*((volatile int*)&flags[FLAG_ERR]) != 0) return false;
+      if (global_ns() - t0 > kWaitLimitNs) { atomicOr(&flags[FLAG_ERR], DEV_ERR_TIMEOUT); return false; }
+    }
+  }
+}
+
+// Bounded wait until *p == 0 (acquire).
+__device__ __forceinline__ bool wait_zero(const unsigned* p, int* flags) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
+    if (ld_acquire_u32(p) == 0u) return true;
+    __nanosleep(64);
     if ((it & 63u) == 0) {
       if (*((volatile int*)&flags[FLAG_ERR]) != 0) return false;
       if (global_ns() - t0 > kWaitLimitNs) { atomicOr(&flags[FLAG_ERR], DEV_ERR_TIMEOUT); return false; }
@@ -279,9 +292,6 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
   PersistSlice* sl = reinterpret_cast<PersistSlice*>(smem + L.slices);
   int* tiles = reinterpret_cast<int*>(smem + L.tiles);
   unsigned* wl = reinterpret_cast<unsigned*>(smem + L.work);
-  int4* tq = reinterpret_cast<int4*>(smem + PL.tq);
-  uint64_t* tq_full = reinterpret_cast<uint64_t*>(smem + PL.tbars);
-  uint64_t* tq_empty = tq_full + kPersistQ;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int m = tid; m < P.nb_max * (P.nb_max - 1) / 2; m += blockDim.x) tiles[m] = tile_pq(m);
@@ -298,8 +308,6 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
       mbar_init(&yc_empty[s], 1);
       mbar_init(&col_done[s], kConsumerWarps);
     }
-    for (int s = 0; s < kPersistQ; ++s) { mbar_init(&tq_full[s], 1); mbar_init(&tq_empty[s], 1); }
-    *reinterpret_cast<unsigned*>(smem + PL.red + 30 * sizeof(double)) = 0u;
     fence_mbar_init();
   }
   __syncthreads();
@@ -411,20 +419,24 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
       __syncwarp();
       if (lane == 0) { mbar_arrive(&rempty[slt]); mbar_arrive(&rv_full[n & 1]); }
     };
-    int tq_n = 0;   // tasks queued to the temporal warps
-    volatile unsigned* beat = reinterpret_cast<volatile unsigned*>(smem + PL.red + 30 * sizeof(double));
+    // T_{k+1}(q, i) into the global queue (lane 0): entry h = the h-th task
+    // produced; its tag h + 1, stored last with release, marks it written
     auto push = [&](int q, int i, int k) -> bool {
-      bool ok = true;
+      int ok = 1;
       if (lane == 0) {
-        const int s = tq_n % kPersistQ;
-        if (tq_n >= kPersistQ) ok = mbar_wait(&tq_empty[s], (uint32_t)(((tq_n / kPersistQ) - 1) & 1), P.err);
+        const unsigned h = atomicAdd(P.tq_tail, 1u);
+        int4* e = P.tq_ring + (h & (P.tq_cap - 1));
+        unsigned* tag = reinterpret_cast<unsigned*>(&e->w);
+        // the slot's previous task (h - cap) must have been taken: never in
+        // practice (the ring holds several iterations of tasks), still bounded
+        if (ld_acquire_u32(tag) != 0u) ok = wait_zero(tag, P.err) ? 1 : 0;
         if (ok) {
-          tq[s] = make_int4(q, i, k, 0);
-          mbar_arrive(&tq_full[s]);
+          e->x = q; e->y = i; e->z = k;
+          __threadfence();
+          st_release_u32(tag, h + 1u);
         }
       }
-      ++tq_n;
-      return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      return __shfl_sync(0xffffffffu, ok, 0) != 0;
     };
     double fid = 0.0;
     int fid_slice = -1, fid_k = -1;
@@ -520,7 +532,7 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
             else if (now - idle0 > kWaitLimitNs) { atomicOr(&P.err[FLAG_ERR], DEV_ERR_TIMEOUT); act = 3; }
           }
         }
-        if (act == 1 || act == 2) { idle0 = 0; spins = 0; *beat = *beat + 1; }
+        if (act == 1 || act == 2) { idle0 = 0; spins = 0; }
       }
       act = __shfl_sync(0xffffffffu, act, 0);
       if (act == 1) {
@@ -535,7 +547,6 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
       fid = warp_sum(fid);
       if (lane == 0) atomicAdd(sl[fid_slice].trace_fid + fid_k, fid);
     }
-    push(-1, 0, 0);   // end of the temporal tasks
     return;
   }
   if (warp >= kTWarp0) {
@@ -545,38 +556,46 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
     float2* segB = reinterpret_cast<float2*>(smem + PL.segB);
     float2* bnd = reinterpret_cast<float2*>(smem + PL.bnd);
     double* red = reinterpret_cast<double*>(smem + PL.red);
-    volatile int* tq_ok = reinterpret_cast<volatile int*>(red + 31);
-    volatile unsigned* beat = reinterpret_cast<volatile unsigned*>(red + 30);   // the manager's progress count
-    for (int n = 0;; ++n) {
-      const int s = n % kPersistQ;
-      // one thread waits and the outcome is shared, so all temporal threads
-      // take the same path through the named barriers.  A CTA may get no task
-      // for a long while in a long solve, so the limit runs from the
-      // manager's last progress, not from the start of the wait.
+    volatile int4* task_sm = reinterpret_cast<volatile int4*>(red + 28);   // the task, shared by the 128 threads
+    for (;;) {
+      // thread 0 takes a ticket and waits for its entry; the outcome is shared
+      // so all temporal threads take the same path through the named
+      // barriers.  Exactly tq_total tasks are produced in a launch; a ticket
+      // beyond that ends this CTA's temporal work.  A wait can legitimately
+      // last long in a long solve, so its limit runs from the last task
+      // produced anywhere (the queue tail), not from the start of the wait.
       if (ttid == 0) {
-        const uint32_t par = (uint32_t)((n / kPersistQ) & 1);
-        int got = 0;
-        unsigned seen = *beat;
-        unsigned long long t0 = global_ns();
-        for (unsigned it = 0;; ++it) {
-          if (mbar_try_wait(&tq_full[s], par)) { got = 1; break; }
-          if ((it & 63u) == 63u) {
-            if (*((volatile int*)&P.err[FLAG_ERR]) != 0) break;
-            const unsigned now_beat = *beat;
-            const unsigned long long now = global_ns();
-            if (now_beat != seen) { seen = now_beat; t0 = now; }
-            else if (now - t0 > kWaitLimitNs) { atomicOr(&P.err[FLAG_ERR], DEV_ERR_TIMEOUT); break; }
+        int4 task = make_int4(-1, 0, 0, 0);
+        const unsigned h = atomicAdd(P.tq_head, 1u);
+        if (h < P.tq_total) {
+          int4* e = P.tq_ring + (h & (P.tq_cap - 1));
+          unsigned* tag = reinterpret_cast<unsigned*>(&e->w);
+          unsigned seen = ld_acquire_u32(P.tq_tail);
+          unsigned long long t0 = global_ns();
+          bool got = false;
+          for (unsigned it = 0;; ++it) {
+            if (ld_acquire_u32(tag) == h + 1u) { got = true; break; }
+            __nanosleep(128);
+            if ((it & 63u) == 63u) {
+              if (*((volatile int*)&P.err[FLAG_ERR]) != 0) break;
+              const unsigned tail = ld_acquire_u32(P.tq_tail);
+              const unsigned long long now = global_ns();
+              if (tail != seen) { seen = tail; t0 = now; }
+              else if (now - t0 > kWaitLimitNs) { atomicOr(&P.err[FLAG_ERR], DEV_ERR_TIMEOUT); break; }
+            }
+          }
+          if (got) {
+            task = make_int4(__ldcg(&e->x), __ldcg(&e->y), __ldcg(&e->z), 0);
+            st_release_u32(tag, 0u);   // the slot is free for entry h + cap
           }
         }
-        *tq_ok = got;
+        task_sm->x = task.x; task_sm->y = task.y; task_sm->z = task.z;
       }
       tbar();
-      const bool got = *tq_ok != 0;
-      const int4 task = got ? tq[s] : make_int4(-1, 0, 0, 0);
+      const int4 task = make_int4(task_sm->x, task_sm->y, task_sm->z, 0);
       tbar();
-      if (!got) break;
-      if (ttid == 0) mbar_arrive(&tq_empty[s]);
       if (task.x < 0) break;
+      __threadfence();   // order this thread's reads of x, m, d1, p after the task's acquire
       persist_temporal(sl[task.x], task.y, task.z, K, ttid, segA, segB, bnd, red);
     }
     return;

@@ -57,8 +57,10 @@ struct Engine {
   unsigned* d_pwork = nullptr;  // per-CTA column lists, image-column-major
   int* d_pwork_off = nullptr;
   int pwork_max = 0, pstages = 0;
-  unsigned* d_pcount = nullptr; // colcnt and tdone of every slice (2 sum Nx), zeroed per solve
+  unsigned* d_pcount = nullptr; // colcnt and tdone of every slice (2 sum Nx), queue head and tail; zeroed per solve
   size_t pcount_n = 0;
+  int4* d_tq_ring = nullptr;    // temporal task ring (zeroed per solve)
+  unsigned tq_cap = 0, tq_total = 0;
   std::vector<unsigned> gens;   // each plan's generation when this engine was built
   DevArena arena;
 };
