@@ -258,20 +258,20 @@ recon_status engine_build_persist(Engine* e, recon_plan* const* plans, int n) {
   }
   const int stages = persist_max_stages(e->nb_max, n, work_max);
   if (stages <= 0) return RECON_OK;   // the lists do not fit in shared memory: one launch per step
-  size_t ncount = 0, nx_sum = 0;
+  size_t ncount = 0, task_sum = 0;   // task_sum: temporal chunks of one iteration
   for (int q = 0; q < n; ++q) {
     ncount += 2 * (size_t)plans[q]->Nx;
-    nx_sum += (size_t)plans[q]->Nx;
+    task_sum += (size_t)plans[q]->Nx * ((plans[q]->Ny + kPersistChunkPx - 1) / kPersistChunkPx);
   }
   // colcnt and tdone of every slice, then the task queue's head and tail
   RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_pcount), (ncount + 2) * sizeof(unsigned)));
   e->pcount_n = ncount + 2;
   // the temporal task ring: room for several iterations' tasks (one per image column each)
   unsigned cap = 1024;
-  while (cap < 4 * nx_sum) cap <<= 1;
+  while (cap < 4 * task_sum) cap <<= 1;
   RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_tq_ring), (size_t)cap * sizeof(int4)));
   e->tq_cap = cap;
-  e->tq_total = (unsigned)((size_t)e->K * nx_sum);
+  e->tq_total = (unsigned)((size_t)e->K * task_sum);
   std::vector<PersistSlice> ps(n);
   size_t o = 0;
   for (int q = 0; q < n; ++q) {
@@ -282,6 +282,7 @@ recon_status engine_build_persist(Engine* e, recon_plan* const* plans, int n) {
     d.Nx = p->Nx; d.Ny = p->Ny; d.Nt = p->Nt;
     d.nb = p->pk.nb;
     d.nunits = p->pk.nunits;
+    d.nch = (p->Ny + kPersistChunkPx - 1) / kPersistChunkPx;
     d.b = p->b;
     d.x = p->x;
     for (int k = 0; k < 2; ++k) { d.m[k] = p->s0[k]; d.d1[k] = p->s1[k]; d.p[k] = p->s2[k]; }

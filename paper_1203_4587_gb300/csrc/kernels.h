@@ -261,9 +261,10 @@ struct ObjParams {           // ||y - H x||^2 of a given field (no inverse)
 
 // Persistent solve of Algorithm 2 with temporal TV (persist_kernels.cu): all
 // K iterations of a set of slices in one cooperative launch, FP32 inverses,
-// Nt <= kPersistNtMax.  The per-column counters colcnt and tdone ([Nx] per
+// Nt <= kPersistNtMax, Nx < 2^20.  The per-column counters colcnt and tdone ([Nx] per
 // slice), the queue counters and the ring's tags must be zero at the launch.
 constexpr int kPersistNtMax = 40;
+constexpr int kPersistChunkPx = 16;   // pixels of an image column per temporal task
 struct PersistSlice {
   const void* A;             // packed inverses
   long long col_elems;
@@ -279,8 +280,9 @@ struct PersistSlice {
   int do_obj;
   double* trace_fid;         // [K + 2]
   double* trace_prior;
+  int nch;                   // temporal chunks per image column (ceil(Ny / 16))
   unsigned* colcnt;          // [Nx] completed frames of the current iteration
-  unsigned* tdone;           // [Nx] temporal steps done in this launch (T_{k+1} sets k)
+  unsigned* tdone;           // [Nx] temporal chunks done in this launch
 };
 
 struct PersistLaunch {
@@ -299,7 +301,7 @@ struct PersistLaunch {
   unsigned tq_cap;
   unsigned* tq_head;         // tickets taken by the temporal warps
   unsigned* tq_tail;         // tasks produced
-  unsigned tq_total;         // tasks one launch produces: K * sum of Nx
+  unsigned tq_total;         // tasks one launch produces: K * sum over slices of Nx * nch
 };
 
 size_t persist_smem(int stages, int nb_max, int nslices, int work_max);

@@ -17,9 +17,10 @@
 //     queue; the four temporal warps of every CTA take tasks from it by
 //     ticket (which CTA completes a column's last frame is systematic, so
 //     running the task there would pile the temporal work onto a few SMs),
-//     and publish each in tdone[q][i] = k;
-//   * the r loader waits (bounded) for tdone[q][i] >= k - 1 before it reads
-//     p_k of a column of iteration k.
+//     and count each finished chunk (kPersistPx pixels of the column, every
+//     frame; a task is one chunk) in tdone[q][i];
+//   * the r loader waits (bounded) for tdone[q][i] >= (k - 1) * chunks before
+//     it reads p_k of a column of iteration k.
 // Every dependency points to an earlier iteration, so with all CTAs resident
 // (a cooperative launch) every wait ends; each still has a wall-clock limit
 // after which the kernel sets DEV_ERR_TIMEOUT and leaves.  State buffers
@@ -35,26 +36,31 @@ constexpr int kPersistTWarps = 4;                 // temporal warps
 constexpr int kPersistTThreads = 32 * kPersistTWarps;
 constexpr int kPersistSeg = 8;                    // Thomas segments (as in k_tv_temporal)
 constexpr int kPersistPx = kPersistTThreads / kPersistSeg;   // pixels per temporal chunk
+static_assert(kPersistPx == kPersistChunkPx, "temporal chunk width");
 constexpr int kPersistLMax = kPersistNtMax / kPersistSeg;   // frames per segment
+constexpr int kPersistRSlots = 4;                 // the r loader's lookahead (columns)
 
 __host__ __device__ constexpr int persist_threads() { return col_threads(8) + kPersistTThreads; }
 
 struct PersistLayout {
   ColLayout c;   // the column-inverse regions; c.slices holds PersistSlice entries
-  size_t segA, segB, bnd, red, total;
+  size_t rbars, rslot, segA, segB, bnd, red, total;
 };
 
 __host__ __device__ inline PersistLayout persist_layout(int stages, int nb, int nslices, int work_max) {
   PersistLayout L;
   // the column-inverse layout without its slice table, then a table of
   // PersistSlice entries, the work list and the temporal warps' regions
-  L.c = col_layout(stages, nb, 0, 0, 8);
+  L.c = col_layout(stages, nb, 0, 0, 8);   // its 2-slot r ring and barriers are left unused
   size_t o = align_up(L.c.slices, 16);
   L.c.slices = o; o += (size_t)nslices * sizeof(PersistSlice);
   o = align_up(o, 16);
   L.c.skip = o;
   L.c.work = o; o += (size_t)work_max * 4;
   o = align_up(o, 16);
+  L.rbars = o; o += 2 * kPersistRSlots * 8;              // rfull, rempty of the deeper slot ring
+  o = align_up(o, 16);
+  L.rslot = o; o += (size_t)kPersistRSlots * 2 * (size_t)nb * 32 * sizeof(float2);   // [slot][b, p][ny32]
   L.segA = o; o += kPersistSeg * kPersistPx * sizeof(float);
   o = align_up(o, 16);
   L.segB = o; o += kPersistSeg * kPersistPx * sizeof(float2);
@@ -103,11 +109,13 @@ __device__ __forceinline__ bool wait_zero(const unsigned* p, int* flags) {
 
 __device__ __forceinline__ void tbar() { named_bar_sync(1, kPersistTThreads); }
 
-// T_{k+1}(q, i) by the temporal warps (thread tid of kPersistTThreads): the
-// arithmetic of k_tv_temporal for pixel j = chunk * kPersistPx + px, frames
-// [ta, tb) of segment seg, held in registers.  k == K: only ||D_t x_K||_1.
-__device__ void persist_temporal(const PersistSlice& S, int i, int k, int K, int tid, float* segA, float2* segB,
-                                 float2* bnd, double* red) {
+// One chunk of T_{k+1}(q, i) -- pixels j = chunk * kPersistPx + px of image
+// column i, every frame -- by the temporal warps (thread tid of
+// kPersistTThreads): the arithmetic of k_tv_temporal, frames [ta, tb) of
+// segment seg held in registers.  k == K: only ||D_t x_K||_1.  A column's
+// chunks are independent tasks, so tdone[i] counts chunks.
+__device__ void persist_temporal(const PersistSlice& S, int i, int chunk, int k, int K, int tid, float* segA,
+                                 float2* segB, float2* bnd, double* red) {
   const int Nx = S.Nx, Ny = S.Ny, Nt = S.Nt;
   const bool write = k < K;
   const int in = k & 1, out = (k + 1) & 1;
@@ -121,8 +129,8 @@ __device__ void persist_temporal(const PersistSlice& S, int i, int k, int K, int
   const float2* D1i = S.d1[in];
   const float2* Pi = S.p[in];
   float tvf = 0.f;
-  for (int c0 = 0; c0 < Ny; c0 += kPersistPx) {
-    const int j = c0 + px;
+  {
+    const int j = chunk * kPersistPx + px;
     const bool ok = j < Ny;
     const size_t base = (size_t)i * Ny + j;          // pixel (i, j) of frame 0
     // xs: x then rhs; ms: m then d then m'; ds: d1 then e; ps: p then f
@@ -153,7 +161,7 @@ __device__ void persist_temporal(const PersistSlice& S, int i, int k, int K, int
 #pragma unroll
     for (int u = 0; u < kPersistLMax; ++u)
       if (ok && u < n && ta + u + 1 < Nt) tvf += c_abs(c_sub(u + 1 < n ? xs[u + 1] : xn, xs[u]));
-    if (!write) continue;
+    if (write) {
     // e_t = d1_t - S(m_{t+1} - m_t + d1_t) (t < Nt - 1), e_{ta-1} recomputed from its own inputs
     float2 eprev = z2;
     if (ok && n > 0 && ta > 0) eprev = c_sub(dp, c_soft(c_add(c_sub(ms[0], mp), dp), S.tau1));
@@ -243,6 +251,7 @@ __device__ void persist_temporal(const PersistSlice& S, int i, int k, int K, int
           if (ta + u + 1 < Nt) Do[g] = c_add(ds[u], c_sub(u + 1 < n ? ms[u + 1] : mnext, ms[u]));
         }
     }
+    }   // write
   }
   // the prior term of J at x_k
   double v = warp_sum((double)tvf);
@@ -255,10 +264,13 @@ __device__ void persist_temporal(const PersistSlice& S, int i, int k, int K, int
     atomicAdd(S.trace_prior + k, s);
   }
   if (write) {
-    // publish T_{k+1}(q, i): the new state before tdone
+    // publish this chunk of T_{k+1}(q, i): the new state before the count
     __threadfence();
     tbar();
-    if (tid == 0) st_release_u32(S.tdone + i, (unsigned)k);
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(S.tdone + i, 1u);
+    }
   } else {
     tbar();
   }
@@ -278,9 +290,7 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
   const int S = P.stages, K = P.K;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
   uint64_t* empty = full + S;
-  uint64_t* rfull = empty + S;
-  uint64_t* rempty = rfull + kRSlots;
-  uint64_t* rv_full = rempty + kRSlots;
+  uint64_t* rv_full = empty + S + 2 * kRSlots;   // after the unused rfull / rempty of colinv.cuh
   uint64_t* yc_empty = rv_full + kRSlots;
   uint64_t* col_done = yc_empty + kRSlots;
   unsigned char* ring = smem + L.ring;
@@ -288,7 +298,9 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
   float2* ycopy = reinterpret_cast<float2*>(smem + L.ycopy);
   float2* rvec = reinterpret_cast<float2*>(smem + L.rvec);
   float2* bvec = reinterpret_cast<float2*>(smem + L.bvec);
-  float2* rslot = reinterpret_cast<float2*>(smem + L.rslot);
+  uint64_t* rfull = reinterpret_cast<uint64_t*>(smem + PL.rbars);
+  uint64_t* rempty = rfull + kPersistRSlots;
+  float2* rslot = reinterpret_cast<float2*>(smem + PL.rslot);
   PersistSlice* sl = reinterpret_cast<PersistSlice*>(smem + L.slices);
   int* tiles = reinterpret_cast<int*>(smem + L.tiles);
   unsigned* wl = reinterpret_cast<unsigned*>(smem + L.work);
@@ -301,9 +313,11 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
   for (int w = w0 + tid; w < w1; w += blockDim.x) wl[w - w0] = P.work[w];
   if (tid == 0) {
     for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int s = 0; s < kRSlots; ++s) {
+    for (int s = 0; s < kPersistRSlots; ++s) {
       mbar_init(&rfull[s], 1);
       mbar_init(&rempty[s], 1);
+    }
+    for (int s = 0; s < kRSlots; ++s) {
       mbar_init(&rv_full[s], 1);
       mbar_init(&yc_empty[s], 1);
       mbar_init(&col_done[s], kConsumerWarps);
@@ -361,15 +375,15 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
       const int w = n % nw, k = n / nw + 1;
       const PersistSlice& c = sl[WSL(w)];
       const int col = WCOL(w), i = col % c.Nx;
-      const int slt = n % kRSlots;
+      const int slt = n % kPersistRSlots;
       // lane 0 waits (the slot, then T_k of this image column) and shares the outcome
       int ok = 1;
       if (lane == 0) {
-        if (n >= kRSlots) ok = mbar_wait(&rempty[slt], (uint32_t)(((n / kRSlots) - 1) & 1), P.err) ? 1 : 0;
-        if (ok && k >= 2) ok = wait_at_least(c.tdone + i, (unsigned)(k - 1), P.err) ? 1 : 0;
+        if (n >= kPersistRSlots) ok = mbar_wait(&rempty[slt], (uint32_t)(((n / kPersistRSlots) - 1) & 1), P.err) ? 1 : 0;
+        if (ok && k >= 2) ok = wait_at_least(c.tdone + i, (unsigned)(k - 1) * (unsigned)c.nch, P.err) ? 1 : 0;
       }
       if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-      float2* d = rslot + (size_t)slt * 3 * ny32m;
+      float2* d = rslot + (size_t)slt * 2 * ny32m;
       const size_t cofs = (size_t)col * c.Ny;
       const float2* pk = c.p[k & 1];
       if ((c.Ny & 1) == 0) {   // 16-byte aligned columns: two elements per access
@@ -400,8 +414,8 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
       const int w = n % nw;
       const PersistSlice& c = sl[WSL(w)];
       const int ny32 = c.nb * 32;
-      const int slt = n % kRSlots;
-      const float2* d = rslot + (size_t)slt * 3 * ny32m;
+      const int slt = n % kPersistRSlots;
+      const float2* d = rslot + (size_t)slt * 2 * ny32m;
       float2* rv = rvec + (size_t)(n & 1) * ny32m;
       float2* bv = bvec + (size_t)(n & 1) * ny32m;
       for (int j = 2 * lane; j < ny32; j += 64) {
@@ -421,22 +435,27 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
     };
     // T_{k+1}(q, i) into the global queue (lane 0): entry h = the h-th task
     // produced; its tag h + 1, stored last with release, marks it written
+    // every chunk of T_{k+1}(q, i) as its own task, lanes in parallel
     auto push = [&](int q, int i, int k) -> bool {
+      const int nch = sl[q].nch;
+      unsigned h0 = 0;
+      if (lane == 0) h0 = atomicAdd(P.tq_tail, (unsigned)nch);
+      h0 = __shfl_sync(0xffffffffu, h0, 0);
       int ok = 1;
-      if (lane == 0) {
-        const unsigned h = atomicAdd(P.tq_tail, 1u);
+      for (int ch = lane; ch < nch && ok; ch += 32) {
+        const unsigned h = h0 + (unsigned)ch;
         int4* e = P.tq_ring + (h & (P.tq_cap - 1));
         unsigned* tag = reinterpret_cast<unsigned*>(&e->w);
         // the slot's previous task (h - cap) must have been taken: never in
         // practice (the ring holds several iterations of tasks), still bounded
         if (ld_acquire_u32(tag) != 0u) ok = wait_zero(tag, P.err) ? 1 : 0;
         if (ok) {
-          e->x = q; e->y = i; e->z = k;
+          e->x = q; e->y = i | (ch << 20); e->z = k;
           __threadfence();
           st_release_u32(tag, h + 1u);
         }
       }
-      return __shfl_sync(0xffffffffu, ok, 0) != 0;
+      return __all_sync(0xffffffffu, ok) != 0;
     };
     double fid = 0.0;
     int fid_slice = -1, fid_k = -1;
@@ -519,7 +538,8 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
       if (lane == 0) {
         // test_wait never suspends: a suspended try_wait on one barrier could
         // hold back the other, which may be the one its phase depends on
-        if (np < ncol && np < ne + kRSlots && mbar_test_wait(&rfull[np % kRSlots], (uint32_t)((np / kRSlots) & 1)))
+        if (np < ncol && np < ne + kRSlots &&
+            mbar_test_wait(&rfull[np % kPersistRSlots], (uint32_t)((np / kPersistRSlots) & 1)))
           act = 1;
         else if (ne < np && mbar_test_wait(&col_done[ne & 1], (uint32_t)((ne >> 1) & 1)))
           act = 2;
@@ -596,7 +616,7 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
       tbar();
       if (task.x < 0) break;
       __threadfence();   // order this thread's reads of x, m, d1, p after the task's acquire
-      persist_temporal(sl[task.x], task.y, task.z, K, ttid, segA, segB, bnd, red);
+      persist_temporal(sl[task.x], task.y & 0xFFFFF, task.y >> 20, task.z, K, ttid, segA, segB, bnd, red);
     }
     return;
   }
