@@ -371,6 +371,8 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
   }
   if (warp == kLoader) {
     // ---------------- r loader: b and p_k of each column, once T_k is published --
+    const uint64_t pol_first = policy_evict_first();
+    int issued = 0;   // columns whose bulk copies lane 0 issued (for the error path)
     for (int n = 0; n < ncol; ++n) {
       const int w = n % nw, k = n / nw + 1;
       const PersistSlice& c = sl[WSL(w)];
@@ -386,13 +388,21 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
       float2* d = rslot + (size_t)slt * 2 * ny32m;
       const size_t cofs = (size_t)col * c.Ny;
       const float2* pk = c.p[k & 1];
-      if ((c.Ny & 1) == 0) {   // 16-byte aligned columns: two elements per access
-        for (int j = 2 * lane; j < c.Ny; j += 64) {
-          const float4 bv = __ldcg(reinterpret_cast<const float4*>(c.b + cofs + j));
-          const float4 pv = __ldcg(reinterpret_cast<const float4*>(pk + cofs + j));
-          *reinterpret_cast<float4*>(d + j) = bv;
-          *reinterpret_cast<float4*>(d + ny32m + j) = pv;
+      if ((c.Ny & 1) == 0) {
+        // 16-byte aligned columns: two bulk copies, completion counted on the
+        // slot's barrier, so the loader moves on to the next column at once.
+        // p_k was written by other CTAs' generic stores, published by tdone
+        // (acquired above); the proxy fence orders those writes before this
+        // thread's async-proxy reads.
+        if (lane == 0) {
+          const uint32_t bytes = (uint32_t)c.Ny * 8u;
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+          mbar_arrive_expect_tx(&rfull[slt], 2u * bytes);
+          bulk_g2s(d, c.b + cofs, bytes, &rfull[slt], pol_first);
+          bulk_g2s(d + ny32m, pk + cofs, bytes, &rfull[slt], pol_first);
         }
+        issued = n + 1;
+        continue;
       } else {
         for (int j = lane; j < c.Ny; j += 32) {
           d[j] = __ldcg(c.b + cofs + j);
@@ -401,6 +411,14 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&rfull[slt]);
+    }
+    if (lane == 0) {
+      // bulk copies of the last slots may still be in flight if the kernel quits early
+      for (int h = (issued > kPersistRSlots ? issued - kPersistRSlots : 0); h < issued; ++h) {
+        const unsigned long long t0 = global_ns();
+        while (!mbar_try_wait(&rfull[h % kPersistRSlots], (uint32_t)((h / kPersistRSlots) & 1)) &&
+               global_ns() - t0 < kWaitLimitNs) {}
+      }
     }
     return;
   }
