@@ -756,7 +756,7 @@ recon_status recon_export_inverse(recon_plan* p, int i, int t, float* dense, voi
   if (!p || !dense || i < 0 || i >= p->Nx || t < 0 || t >= p->Nt) return fail(RECON_ERR_INVALID_ARG, "bad argument");
   if (p->broken) return fail(RECON_ERR_INVALID_ARG, "the plan failed recon_plan_set_mu and is unusable");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  RC(launch_unpack(p->A, p->storage, p->pk, (long long)t * p->Nx + i, p->Ny, reinterpret_cast<float2*>(dense), s));
+  RC(launch_unpack(p->A, p->storage, p->pk, (long long)i * p->Nt + t, p->Ny, reinterpret_cast<float2*>(dense), s));
   return RECON_OK;
 }
 

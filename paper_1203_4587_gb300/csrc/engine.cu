@@ -46,7 +46,10 @@ cudaError_t upload(DevArena& a, T** dst, const std::vector<T>& v) {
 }  // namespace
 
 // Column work lists of a batch: every column of every slice, by the bytes it
-// streams (host_logic.h: lpt_work_lists).
+// streams (host_logic.h: lpt_work_lists), numbered image-column-major
+// (c' = i Nt + t, the order of the packed stream) and stored as
+// col = t Nx + i: a CTA's list runs through the image columns in order, and
+// the CTAs of a launch read adjacent stretches of the stream.
 void build_col_work(recon_plan* const* plans, int n, int grid, std::vector<unsigned>& work, std::vector<int>& off,
                     int& work_max) {
   std::vector<long long> cost(n);
@@ -56,6 +59,12 @@ void build_col_work(recon_plan* const* plans, int n, int grid, std::vector<unsig
     ncols[q] = plans[q]->Nx * plans[q]->Nt;
   }
   lpt_work_lists(cost, ncols, grid, work, off, work_max);
+  for (unsigned& w : work) {
+    const int q = (int)(w >> 24), cp = (int)(w & 0xFFFFFFu);
+    const int Nt = plans[q]->Nt, Nx = plans[q]->Nx;
+    const int i = cp / Nt, t = cp - i * Nt;
+    w = ((unsigned)q << 24) | (unsigned)(t * Nx + i);
+  }
 }
 
 namespace {
@@ -178,6 +187,8 @@ ColSlice col_desc(recon_plan* p, int k, bool fused) {
   ColSlice c{};
   c.A = p->A;
   c.col_elems = p->pk.col_elems;
+  c.Nx = p->Nx;
+  c.Nt = p->Nt;
   c.Ny = p->Ny;
   c.nb = p->pk.nb;
   c.nunits = p->pk.nunits;
@@ -237,25 +248,11 @@ recon_status engine_build_persist(Engine* e, recon_plan* const* plans, int n) {
     return RECON_OK;
   for (int q = 0; q < n; ++q)
     if (!plans[q]->opts.persistent || plans[q]->Nt > kPersistNtMax) return RECON_OK;
-  // column lists: longest-processing-time over the CTAs as for the per-step
-  // kernel, but with every slice's columns numbered image-column-major
-  // (c' = i Nt + t), so a CTA's list runs through the image columns in order
-  std::vector<long long> cost(n);
-  std::vector<int> ncols(n);
-  for (int q = 0; q < n; ++q) {
-    cost[q] = plans[q]->pk.col_elems * (long long)plans[q]->esize + 4096;
-    ncols[q] = plans[q]->Nx * plans[q]->Nt;
-  }
+  // the per-step kernel's column lists (image-column-major, see build_col_work)
   std::vector<unsigned> work;
   std::vector<int> off;
   int work_max = 0;
-  lpt_work_lists(cost, ncols, e->grid, work, off, work_max);
-  for (unsigned& w : work) {
-    const int q = (int)(w >> 24), cp = (int)(w & 0xFFFFFFu);
-    const int Nt = plans[q]->Nt, Nx = plans[q]->Nx;
-    const int i = cp / Nt, t = cp - i * Nt;
-    w = ((unsigned)q << 24) | (unsigned)(t * Nx + i);
-  }
+  build_col_work(plans, n, e->grid, work, off, work_max);
   const int stages = persist_max_stages(e->nb_max, n, work_max);
   if (stages <= 0) return RECON_OK;   // the lists do not fit in shared memory: one launch per step
   size_t ncount = 0, task_sum = 0;   // task_sum: temporal chunks of one iteration

@@ -269,6 +269,8 @@ recon_status recon_grad_create(recon_grad** out, recon_plan* const* plans, int n
       ColSlice c{};
       c.A = p->A;
       c.col_elems = p->pk.col_elems;
+      c.Nx = p->Nx;
+      c.Nt = p->Nt;
       c.Ny = p->Ny;
       c.nb = p->pk.nb;
       c.nunits = p->pk.nunits;

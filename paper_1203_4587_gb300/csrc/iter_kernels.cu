@@ -133,7 +133,8 @@ __global__ void __launch_bounds__(col_threads(Elem<E>::bytes), 1) k_col_inverse(
       for (int w = w0; w < w1 && ok; ++w) {
         if (skip[WSL(w)]) continue;
         const ColSlice& c = sl[WSL(w)];
-        const unsigned char* cb = reinterpret_cast<const unsigned char*>(c.A) + (size_t)WCOL(w) * (size_t)c.col_elems * ES;
+        const unsigned char* cb = reinterpret_cast<const unsigned char*>(c.A) +
+                                  (size_t)packed_index(WCOL(w), c.Nx, c.Nt) * (size_t)c.col_elems * ES;
         const int rot = unit_rotation(ncolumn++, c.nunits);
         // first position of this column whose global index is p mod kProducers
         int u = p - gu % kProducers;

@@ -8,7 +8,8 @@
 //   hybrid data    yhat = F_h' y on sampled rows: frame t starts at
 //                  rowoff[t]*Nx*Nc, then [Nx][Nc][m_t]
 //   inverses       one packed stream of `col_elems` elements per column
-//                  (i,t), column index col = t*Nx + i (see packing below)
+//                  (i,t), stored image-column-major at i*Nt + t (see packing
+//                  below); work lists and the other fields use col = t*Nx + i
 #pragma once
 
 #include <atomic>
@@ -43,6 +44,14 @@ constexpr int kTileElems = 1024;
 constexpr int kDiagElems = 640;
 constexpr int kDiagLanes = 20;   // lanes of a diagonal block with stored elements
 
+// Position of column col = t * Nx + i in the packed stream: image-column-major,
+// so the columns a launch takes in turn (work lists run through the image
+// columns, every frame of one after the other) are adjacent in memory.
+__host__ __device__ inline long long packed_index(int col, int Nx, int Nt) {
+  const int t = col / Nx, i = col - t * Nx;
+  return (long long)i * Nt + t;
+}
+
 struct PackInfo {
   int nb;          // 32-blocks per column
   int nunits;
@@ -64,8 +73,9 @@ void fill_twiddles_host_df(int n, float4* host_tw);   // exp(-2 pi i k/n) as dou
 // launches only point at set k and a whole solve can be captured as a graph.
 
 struct ColSlice {            // data-consistency inverse x = A r of one slice
-  const void* A;             // packed stream base
+  const void* A;             // packed stream base (column (i, t) at i*Nt + t)
   long long col_elems;
+  int Nx, Nt;                // for the stream index of col = t*Nx + i
   int Ny, nb;
   int nunits;                // units per column (decoded from the index and nb)
   int r_tma;                 // 1: r inputs move by bulk copy (Ny*8 a multiple of 16)
@@ -288,7 +298,7 @@ struct PersistSlice {
 struct PersistLaunch {
   const PersistSlice* slices;
   int nslices;
-  const unsigned* work;      // (slice << 24) | (t * Nx + i), image-column-major per CTA
+  const unsigned* work;      // (slice << 24) | (t * Nx + i), image-column-major per CTA (build_col_work)
   const int* work_off;
   int work_max;
   int nb_max;

@@ -340,7 +340,8 @@ __global__ void __launch_bounds__(persist_threads(), 1) k_persist_tv(PersistLaun
       for (int n = 0; n < ncol && ok; ++n) {
         const int w = n % nw;
         const PersistSlice& c = sl[WSL(w)];
-        const unsigned char* cb = reinterpret_cast<const unsigned char*>(c.A) + (size_t)WCOL(w) * (size_t)c.col_elems * 8;
+        const unsigned char* cb = reinterpret_cast<const unsigned char*>(c.A) +
+                                  (size_t)packed_index(WCOL(w), c.Nx, c.Nt) * (size_t)c.col_elems * 8;
         const int rot = unit_rotation(ncolumn++, c.nunits);
         int u = p - gu % kProducers;
         if (u < 0) u += kProducers;

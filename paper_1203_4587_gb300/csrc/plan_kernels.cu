@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan_inverse(const float2* 
       __syncthreads();
     }
     // W = -M^{-1}: A[j][k] = -conj(W[k][j]) for j <= k, rounded once
-    E* Ac = A + (size_t)mat * col_elems;
+    E* Ac = A + (size_t)((long long)i * Nt + t) * col_elems;   // image-column-major (kernels.h)
     for (int jb = 0; jb < n; jb += kPlanRows) {
       for (int kb = jb / 16 * 16; kb < n; kb += 16) {
         const int j = jb + ty, k = kb + tx;
