@@ -130,11 +130,12 @@ typedef struct {
   int frame_levels; /* levels L of RECON_PRIOR_HAAR, 1..6 (default 2); the frame has L+1 channels */
   float spatial_weight; /* w of RECON_PRIOR_STV, >= 0 (default 1) */
   int cg_steps;     /* CG steps per iteration of RECON_PRIOR_STV, 1..64 (default 5) */
-  int persistent;   /* 1 (default): a temporal-TV solve with FP32 storage, a fixed K (tol = 0), the
-                       fused or no objective and Nt <= 40 runs its K iterations as one persistent
-                       launch (Section IV-C: columns are independent, so each column waits only for
-                       its own image column's temporal step, never for a grid barrier); 0: one
-                       launch per step.  Both give the same iterates up to FP32 rounding order. */
+  int persistent;   /* 0 (default): one launch per step.  1: a temporal-TV solve with FP32 storage,
+                       a fixed K (tol = 0), the fused or no objective and Nt <= 40 runs its K
+                       iterations as one persistent cooperative launch (Section IV-C: columns are
+                       independent, so each column waits only for its own image column's temporal
+                       step, never for a grid barrier); other solves ignore it.  Both give the same
+                       iterates up to FP32 rounding order. */
 } recon_opts;
 
 typedef struct {

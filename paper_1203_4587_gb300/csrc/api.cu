@@ -117,7 +117,7 @@ void recon_default_opts(recon_opts* o) {
   o->frame_levels = 2;
   o->spatial_weight = 1.f;
   o->cg_steps = 5;
-  o->persistent = 1;
+  o->persistent = 0;
 }
 
 const char* recon_status_string(recon_status s) {

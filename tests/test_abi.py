@@ -72,7 +72,7 @@ def test_invalid_arguments_rejected_before_any_cuda_call(libpath):
     assert st == 1
     bad = binding.Opts()
     lib.recon_default_opts(C.byref(bad))
-    assert bad.persistent == 1
+    assert bad.persistent == 0
     bad.persistent = 2
     st = lib.recon_plan_create(C.byref(h), 4, 4, 2, 1, C.cast(mask, C.c_void_p), C.cast(sens, C.c_void_p),
                                0.01, 0.1, 0, C.byref(bad), None)

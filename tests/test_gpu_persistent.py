@@ -54,7 +54,7 @@ SHAPES = [
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(str(s[k]) for k in ("Nx", "Ny", "Nt", "Nc")))
 def test_persistent_solve_matches_oracle_and_per_step(shape):
     c = make("tiny", iters=25, **shape)
-    P1 = plan(c)
+    P1 = plan(c, persistent=1)
     x1, i1 = P1.solve(gpu(c.kspace))
     P0 = plan(c, persistent=0)
     x0, i0 = P0.solve(gpu(c.kspace))
@@ -79,7 +79,7 @@ def test_persistent_solve_matches_oracle_and_per_step(shape):
 
 def test_profile_reports_one_persistent_launch():
     c = make("tiny", iters=12)
-    P = plan(c, profile=1)
+    P = plan(c, profile=1, persistent=1)
     P.solve(gpu(c.kspace))
     pr = P.profile()
     assert pr.persistent == 1 and pr.inverse_launches == 1 and pr.inverse_passes == 12
@@ -93,16 +93,21 @@ def test_profile_reports_one_persistent_launch():
 
 
 def test_paths_not_eligible_run_per_step():
-    """An early stop (tol > 0), 16-bit storage with the objective, or Nt > 40
-    keep one launch per step."""
+    """With the persistent launch asked for, an early stop (tol > 0), 16-bit
+    storage with the objective, or Nt > 40 keep one launch per step; the
+    default is one launch per step."""
     c = make("tiny", Nx=16, Ny=32, Nt=4, Nc=2, iters=6)
     for opts in (dict(tol=1e-9), dict(storage="fp16"), dict(objective=2)):
-        P = plan(c, profile=1, **opts)
+        P = plan(c, profile=1, persistent=1, **opts)
         P.solve(gpu(c.kspace))
         assert P.profile().persistent == 0, opts
         P.close()
+    P = plan(c, profile=1)
+    P.solve(gpu(c.kspace))
+    assert P.profile().persistent == 0
+    P.close()
     c2 = make("tiny", Nx=8, Ny=32, Nt=41, Nc=2, iters=3)
-    P = plan(c2, profile=1)
+    P = plan(c2, profile=1, persistent=1)
     P.solve(gpu(c2.kspace))
     assert P.profile().persistent == 0
     P.close()
@@ -123,7 +128,7 @@ def test_persistent_batch_matches_oracle_twice():
     from paper_1203_4587_gb300 import Batch
     iters = 15
     cases = [make("tiny", iters=iters, **sh) for sh in BATCH]
-    plans = [plan(c) for c in cases]
+    plans = [plan(c, persistent=1) for c in cases]
     batch = Batch(plans)
     ks = [gpu(c.kspace) for c in cases]
     refs = []
@@ -149,7 +154,7 @@ def test_repeated_persistent_solves_are_identical():
     """The dataflow order between CTAs varies from run to run, but every
     column's and pixel's arithmetic does not: results are bit-identical."""
     c = make("tiny", Nx=96, Ny=64, Nt=12, Nc=3, iters=20)
-    P = plan(c)
+    P = plan(c, persistent=1)
     k = gpu(c.kspace)
     a = P.solve(k)[0].cpu().numpy()
     b = P.solve(k)[0].cpu().numpy()
