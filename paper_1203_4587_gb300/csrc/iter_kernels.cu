@@ -9,6 +9,7 @@
 // k_objective    ||y - Hx||^2 of a given field (J(0)).
 // k_finalize     J(k) = fid + lambda * prior, Delta(k) and the stop flag.
 #include "colinv.cuh"
+#include "tv_chunk.cuh"
 
 namespace recon {
 
@@ -439,241 +440,72 @@ __device__ __forceinline__ int find_slice(const SliceT* sl, int n, int blk) {
 }
 
 // ---------------------------------------------------------------------------
-// Algorithm 2 temporal step on a tile of PX pixels x Nt frames (the column
-// layout keeps a tile's pixels contiguous for every t):
-//   v  = S(D_t m + d1, lambda/(2 mu1))
-//   m' = (rho I + D_t'D_t)^{-1} [D_t'(v - d1) + rho (x + d2)]
-//   d1' = d1 - (v - D_t m')
-// with d2 = x - p, and p' = m' - d2 handed to the inverse step, which forms
-// r = H'y + mu2 (m' - d2) = b + mu2 p'.  The next d2 is then x' - p'.  Also
-// accumulates ||D_t x||_1 of the incoming x (the prior term of J).
-//
-// 8 * PX threads; every phase keeps all of them busy:
-//   1. the tile (m, d1, x, p) is staged with 16-byte asynchronous copies;
-//   2. e = d1 - v, then rhs = e_t - e_{t-1} + rho (2 x - p) and f = p - x;
-//   3. the tridiagonal solve by the Thomas recurrences, run as kTvSeg fixed
-//      segments of ceil(Nt / kTvSeg) frames per pixel: each segment composes
-//      its affine recurrence (forward d_t = inv_t (rhs_t + d_{t-1}), backward
-//      m'_t = d_t + inv_t m'_{t+1}), the segments' maps are chained in order,
-//      and each segment then replays its frames from its incoming value.  The
-//      segmentation depends on Nt only, so every tile width gives the same
-//      rounding;
-//   4. m', d1' = e + D m', p' = m' + f stored with 16-byte accesses.
+// Algorithm 2 temporal step (v-, m- and d1-updates along t) for every pixel:
+// one block of kTvChunkThreads threads per chunk of kTvChunkPx consecutive
+// pixels (the column layout keeps them contiguous in every frame), all
+// values in registers (tv_chunk.cuh).  LMAX >= ceil(Nt / kTvSeg) frames per
+// segment.  Also accumulates ||D_t x||_1 of the incoming x (the prior term
+// of J): FP32 per thread, FP64 across the block.
 // ---------------------------------------------------------------------------
-constexpr int kTvSeg = 8;
-
-// 16 bytes (two adjacent pixels) when both are in the tile and the frame
-// offsets keep 16-byte alignment (even npix), else 8 bytes per pixel
-__device__ __forceinline__ void tile_load2(float2* dst, const float2* src, bool pair) {
-  if (pair) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(dst)), "l"(src) : "memory");
-  } else {
-    cp_async8(dst, src);
-  }
-}
-
-template <int PX>
-__global__ void __launch_bounds__(kTvSeg * PX, 1) k_tv_temporal(TemporalLaunch L) {
-  constexpr int NTH = kTvSeg * PX;
-  extern __shared__ __align__(16) float2 sm_tv[];
+template <int LMAX>
+__global__ void __launch_bounds__(kTvChunkThreads) k_tv_temporal(TemporalLaunch L) {
+  __shared__ float seg_a[kTvChunkThreads];
+  __shared__ float2 seg_b[kTvChunkThreads];
+  __shared__ float2 bnd[kTvChunkThreads];
   __shared__ double red[32];
-  __shared__ float2 segB[kTvSeg][PX];
-  __shared__ float segA[kTvSeg][PX];
   const TvSlice* sls = static_cast<const TvSlice*>(L.slices);
   const TvSlice& P = sls[find_slice(sls, L.nslices, (int)blockIdx.x)];
   if (P.stop && *P.stop) return;
-  const int tid = threadIdx.x, Nt = P.Nt;
-  const long long N = P.npix;
-  const long long pix0 = (long long)(blockIdx.x - P.tile0) * PX;
-  const int npx = (int)min((long long)PX, N - pix0);
-  const bool even = (N & 1) == 0;
-  const int T = Nt * PX;
-  // [Nt][PX] tiles: m (then d, then m'), d1 (then e), x (then rhs), p (then f)
-  float2* sm_m = sm_tv;
-  float2* sm_d1 = sm_m + T;
-  float2* sm_x = sm_d1 + T;
-  float2* sm_p = sm_x + T;
-  // ---- 1. stage: thread -> (frame, pixel pair)
-  {
-    constexpr int PAIRS = PX / 2;
-    for (int idx = tid; idx < Nt * PAIRS; idx += NTH) {
-      const int t = idx / PAIRS, pp = 2 * (idx - t * PAIRS);
-      if (pp >= npx) continue;
-      const bool pair = even && pp + 1 < npx;
-      const long long g = t * N + pix0 + pp;
-      const int o = t * PX + pp;
-      for (int h = 0; h < (pair ? 1 : min(2, npx - pp)); ++h) {
-        tile_load2(&sm_x[o + h], P.x + g + h, pair);
-        if (P.write_state) {
-          tile_load2(&sm_m[o + h], P.m + g + h, pair);
-          tile_load2(&sm_p[o + h], P.p + g + h, pair);
-          if (P.d1 && t + 1 < Nt) tile_load2(&sm_d1[o + h], P.d1 + g + h, pair);
-        }
-      }
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  // element phases: thread -> pixel pp = tid % PX, frames t0, t0 + kTvSeg, ...
-  const int pp = tid % PX, t0 = tid / PX;
-  const bool mine = pp < npx;
-  // ||D_t x||_1: at most ceil(Nt / kTvSeg) terms per thread in FP32, then
-  // FP64 across the block (GB300's FP64 pipe is too narrow for per-element use)
-  float tvf = 0.f;
-  if (mine)
-    for (int t = t0; t + 1 < Nt; t += kTvSeg) tvf += c_abs(c_sub(sm_x[(t + 1) * PX + pp], sm_x[t * PX + pp]));
-  const double tv = (double)tvf;
-  if (P.write_state) {
-    // ---- 2a. e_t = d1_t - S(m_{t+1} - m_t + d1_t) for t < Nt-1 (0 at t = Nt-1)
-    if (mine)
-      for (int t = t0; t < Nt; t += kTvSeg) {
-        const int idx = t * PX + pp;
-        float2 e = make_float2(0.f, 0.f);
-        if (t + 1 < Nt) {
-          const float2 d1_t = P.d1 ? sm_d1[idx] : make_float2(0.f, 0.f);
-          const float2 v = c_soft(c_add(c_sub(sm_m[idx + PX], sm_m[idx]), d1_t), P.tau1);
-          e = c_sub(d1_t, v);
-        }
-        sm_d1[idx] = e;
-      }
-    __syncthreads();
-    // ---- 2b. rhs_t = e_t - e_{t-1} + rho (2 x_t - p_t);  f_t = p_t - x_t
-    if (mine)
-      for (int t = t0; t < Nt; t += kTvSeg) {
-        const int idx = t * PX + pp;
-        const float2 x_t = sm_x[idx], p_t = sm_p[idx];
-        float2 rhs = sm_d1[idx];
-        if (t > 0) rhs = c_sub(rhs, sm_d1[idx - PX]);
-        rhs.x = fmaf(P.rho, 2.f * x_t.x - p_t.x, rhs.x);
-        rhs.y = fmaf(P.rho, 2.f * x_t.y - p_t.y, rhs.y);
-        sm_x[idx] = rhs;
-        sm_p[idx] = c_sub(p_t, x_t);
-      }
-    __syncthreads();
-    // ---- 3. Thomas recurrences by segments: thread -> (pixel pp, segment t0)
-    const int Ls = (Nt + kTvSeg - 1) / kTvSeg;
-    const int ta = min(Nt, t0 * Ls), tb = min(Nt, ta + Ls);
-    // forward: d_t = inv_t (rhs_t + d_{t-1}); the segment's map d_out = A d_in + B
-    {
-      float A = 1.f;
-      float2 B = make_float2(0.f, 0.f);
-      for (int t = ta; t < tb; ++t) {
-        const float inv = __ldg(P.thomas + t);
-        A *= inv;
-        B = c_scale(c_add(sm_x[t * PX + pp], B), inv);
-      }
-      segA[t0][pp] = A;
-      segB[t0][pp] = B;
-    }
-    __syncthreads();
-    {
-      float2 d = make_float2(0.f, 0.f);
-      for (int q = 0; q < t0; ++q) d = c_add(c_scale(d, segA[q][pp]), segB[q][pp]);
-      for (int t = ta; t < tb; ++t) {
-        d = c_scale(c_add(sm_x[t * PX + pp], d), __ldg(P.thomas + t));
-        sm_m[t * PX + pp] = d;
-      }
-    }
-    __syncthreads();
-    // backward: m'_t = d_t + inv_t m'_{t+1}; the segment's map m'_first = A m'_in + B
-    {
-      float A = 1.f;
-      float2 B = make_float2(0.f, 0.f);
-      for (int t = tb - 1; t >= ta; --t) {
-        const float inv = __ldg(P.thomas + t);
-        const float2 dt = sm_m[t * PX + pp];
-        B = make_float2(fmaf(inv, B.x, dt.x), fmaf(inv, B.y, dt.y));
-        A *= inv;
-      }
-      segA[t0][pp] = A;
-      segB[t0][pp] = B;
-    }
-    __syncthreads();
-    {
-      float2 mn = make_float2(0.f, 0.f);
-      for (int q = kTvSeg - 1; q > t0; --q) mn = c_add(c_scale(mn, segA[q][pp]), segB[q][pp]);
-      for (int t = tb - 1; t >= ta; --t) {
-        const float inv = __ldg(P.thomas + t);
-        const float2 dt = sm_m[t * PX + pp];
-        mn = make_float2(fmaf(inv, mn.x, dt.x), fmaf(inv, mn.y, dt.y));
-        sm_m[t * PX + pp] = mn;
-      }
-    }
-    __syncthreads();
-    // ---- 4. m', d1' = e + D m', p' = m' + f: thread -> (frame, pixel pair)
-    {
-      constexpr int PAIRS = PX / 2;
-      for (int idx = tid; idx < Nt * PAIRS; idx += NTH) {
-        const int t = idx / PAIRS, q = 2 * (idx - t * PAIRS);
-        if (q >= npx) continue;
-        const int o = t * PX + q;
-        const long long g = t * N + pix0 + q;
-        const float2 m0 = sm_m[o], m1 = sm_m[o + 1];
-        const float2 p0 = c_add(m0, sm_p[o]), p1 = c_add(m1, sm_p[o + 1]);
-        float2 e0 = make_float2(0.f, 0.f), e1 = e0;
-        if (t + 1 < Nt) {
-          e0 = c_add(sm_d1[o], c_sub(sm_m[o + PX], m0));
-          e1 = c_add(sm_d1[o + 1], c_sub(sm_m[o + 1 + PX], m1));
-        }
-        if (even && q + 1 < npx) {
-          *reinterpret_cast<float4*>(P.m_out + g) = make_float4(m0.x, m0.y, m1.x, m1.y);
-          *reinterpret_cast<float4*>(P.p_out + g) = make_float4(p0.x, p0.y, p1.x, p1.y);
-          if (t + 1 < Nt) *reinterpret_cast<float4*>(P.d1_out + g) = make_float4(e0.x, e0.y, e1.x, e1.y);
-        } else {
-          P.m_out[g] = m0;
-          P.p_out[g] = p0;
-          if (t + 1 < Nt) P.d1_out[g] = e0;
-          if (q + 1 < npx) {
-            P.m_out[g + 1] = m1;
-            P.p_out[g + 1] = p1;
-            if (t + 1 < Nt) P.d1_out[g + 1] = e1;
-          }
-        }
-      }
-    }
-  }
-  const double s = group_sum(tv, red, tid, NTH, BlockBar());
-  if (tid == 0) atomicAdd(P.prior_acc, s);
+  const long long pix0 = (long long)(blockIdx.x - P.tile0) * kTvChunkPx;
+  TvChunkIO io;
+  io.x = P.x;
+  io.m = P.m;
+  io.d1 = P.d1;
+  io.p = P.p;
+  io.m_out = P.m_out;
+  io.d1_out = P.d1_out;
+  io.p_out = P.p_out;
+  io.thomas = P.thomas;
+  io.tau1 = P.tau1;
+  io.rho = P.rho;
+  io.Nt = P.Nt;
+  io.fstride = (size_t)P.npix;
+  io.base = (size_t)pix0;
+  io.nvalid = (int)min((long long)kTvChunkPx, P.npix - pix0);
+  io.write = P.write_state != 0;
+  const float tvf = tv_chunk<LMAX>(io, (int)threadIdx.x, seg_a, seg_b, bnd, BlockBar());
+  const double s = group_sum((double)tvf, red, (int)threadIdx.x, kTvChunkThreads, BlockBar());
+  if (threadIdx.x == 0) atomicAdd(P.prior_acc, s);
 }
 
-// four [Nt][px] complex tiles; px in {16, 32, 64} (8 px threads); the default
-// is 32, or the widest that fits
 constexpr size_t kSmemOptin = 227 * 1024;
-static size_t tv_smem(int Nt_max, int px) { return 4 * (size_t)Nt_max * px * sizeof(float2); }
-static size_t tv_static_smem(int px) { return 32 * sizeof(double) + kTvSeg * (size_t)px * (sizeof(float2) + sizeof(float)); }
+// one chunk width; the kernel's frames-per-segment array covers Nt <= 128
 int tv_tile_candidates(int Nt_max, int* out) {
-  int n = 0;
-  for (int px : {16, 32, 64})
-    if (tv_smem(Nt_max, px) + tv_static_smem(px) + 1024 <= kSmemOptin) out[n++] = px;
-  return n;
+  (void)Nt_max;
+  out[0] = kTvChunkPx;
+  return 1;
 }
 int tv_tile_px(int Nt_max) {
-  int c[4];
-  const int n = tv_tile_candidates(Nt_max, c);
-  for (int i = n - 1; i >= 0; --i)
-    if (c[i] <= 32) return c[i];
-  return 16;
+  (void)Nt_max;
+  return kTvChunkPx;
 }
-
-cudaError_t prepare_tv_temporal(int Nt_max, int px) {
-  static SmemAttrCache c[3];
-  const size_t smem = tv_smem(Nt_max, px);
-  switch (px) {
-    case 16: return c[0].ensure(reinterpret_cast<const void*>(k_tv_temporal<16>), smem);
-    case 32: return c[1].ensure(reinterpret_cast<const void*>(k_tv_temporal<32>), smem);
-    case 64: return c[2].ensure(reinterpret_cast<const void*>(k_tv_temporal<64>), smem);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t prepare_tv_temporal(int Nt_max, int px) {   // static shared memory only
+  return (px == kTvChunkPx && Nt_max <= 16 * kTvSeg) ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s) {
   cudaError_t e = prepare_tv_temporal(p.Nt_max, p.tile_px);
   if (e != cudaSuccess) return e;
-  const size_t smem = tv_smem(p.Nt_max, p.tile_px);
-  if (p.tile_px == 32) k_tv_temporal<32><<<p.nblocks, kTvSeg * 32, smem, s>>>(p);
-  else if (p.tile_px == 16) k_tv_temporal<16><<<p.nblocks, kTvSeg * 16, smem, s>>>(p);
-  else if (p.tile_px == 64) k_tv_temporal<64><<<p.nblocks, kTvSeg * 64, smem, s>>>(p);
-  else return cudaErrorInvalidValue;
+  const int ls = (p.Nt_max + kTvSeg - 1) / kTvSeg;
+  if (ls <= 1) k_tv_temporal<1><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else if (ls <= 2) k_tv_temporal<2><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else if (ls <= 3) k_tv_temporal<3><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else if (ls <= 4) k_tv_temporal<4><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else if (ls <= 5) k_tv_temporal<5><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else if (ls <= 6) k_tv_temporal<6><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else if (ls <= 8) k_tv_temporal<8><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else if (ls <= 12) k_tv_temporal<12><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else k_tv_temporal<16><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
   note_launch();
   return cudaGetLastError();
 }

@@ -28,15 +28,16 @@
 // ADMM residuals and the final image read the same buffers.  T_1 (from
 // x = m = p = H'y) runs before the launch; T_{K+1} only forms ||D_t x_K||_1.
 #include "colinv.cuh"
+#include "tv_chunk.cuh"
 #include "plan.h"
 
 namespace recon {
 
 constexpr int kPersistTWarps = 4;                 // temporal warps
 constexpr int kPersistTThreads = 32 * kPersistTWarps;
-constexpr int kPersistSeg = 8;                    // Thomas segments (as in k_tv_temporal)
-constexpr int kPersistPx = kPersistTThreads / kPersistSeg;   // pixels per temporal chunk
-static_assert(kPersistPx == kPersistChunkPx, "temporal chunk width");
+constexpr int kPersistSeg = kTvSeg;               // Thomas segments (tv_chunk.cuh)
+constexpr int kPersistPx = kTvChunkPx;            // pixels per temporal chunk
+static_assert(kPersistTThreads == kTvChunkThreads && kPersistPx == kPersistChunkPx, "temporal chunk shape");
 constexpr int kPersistLMax = kPersistNtMax / kPersistSeg;   // frames per segment
 constexpr int kPersistRSlots = 4;                 // the r loader's lookahead (columns)
 
@@ -111,148 +112,33 @@ __device__ __forceinline__ void tbar() { named_bar_sync(1, kPersistTThreads); }
 
 // One chunk of T_{k+1}(q, i) -- pixels j = chunk * kPersistPx + px of image
 // column i, every frame -- by the temporal warps (thread tid of
-// kPersistTThreads): the arithmetic of k_tv_temporal, frames [ta, tb) of
-// segment seg held in registers.  k == K: only ||D_t x_K||_1.  A column's
-// chunks are independent tasks, so tdone[i] counts chunks.
+// kPersistTThreads), the arithmetic of tv_chunk.cuh.  k == K: only
+// ||D_t x_K||_1.  A column's chunks are independent tasks, so tdone[i] counts
+// chunks.
 __device__ void persist_temporal(const PersistSlice& S, int i, int chunk, int k, int K, int tid, float* segA,
                                  float2* segB, float2* bnd, double* red) {
-  const int Nx = S.Nx, Ny = S.Ny, Nt = S.Nt;
   const bool write = k < K;
   const int in = k & 1, out = (k + 1) & 1;
-  const int seg = tid / kPersistPx, px = tid - seg * kPersistPx;
-  const int Ls = (Nt + kPersistSeg - 1) / kPersistSeg;
-  const int ta = min(Nt, seg * Ls), tb = min(Nt, ta + Ls), n = tb - ta;
-  const size_t fstride = (size_t)Nx * Ny;            // one frame
-  const float2 z2 = make_float2(0.f, 0.f);
-  const float2* X = S.x;
-  const float2* Mi = S.m[in];
-  const float2* D1i = S.d1[in];
-  const float2* Pi = S.p[in];
-  float tvf = 0.f;
-  {
-    const int j = chunk * kPersistPx + px;
-    const bool ok = j < Ny;
-    const size_t base = (size_t)i * Ny + j;          // pixel (i, j) of frame 0
-    // xs: x then rhs; ms: m then d then m'; ds: d1 then e; ps: p then f
-    float2 xs[kPersistLMax], ms[kPersistLMax], ds[kPersistLMax], ps[kPersistLMax];
-    float2 xn = z2, mn = z2, mp = z2, dp = z2;
-#pragma unroll
-    for (int u = 0; u < kPersistLMax; ++u) {
-      xs[u] = ms[u] = ds[u] = ps[u] = z2;
-      if (ok && u < n) {
-        const size_t g = (size_t)(ta + u) * fstride + base;
-        xs[u] = __ldcg(X + g);
-        if (write) {
-          ms[u] = __ldcg(Mi + g);
-          ps[u] = __ldcg(Pi + g);
-          if (ta + u + 1 < Nt) ds[u] = __ldcg(D1i + g);
-        }
-      }
-    }
-    if (ok && n > 0 && tb < Nt) {
-      xn = __ldcg(X + (size_t)tb * fstride + base);
-      if (write) mn = __ldcg(Mi + (size_t)tb * fstride + base);
-    }
-    if (ok && n > 0 && ta > 0 && write) {
-      mp = __ldcg(Mi + (size_t)(ta - 1) * fstride + base);
-      dp = __ldcg(D1i + (size_t)(ta - 1) * fstride + base);
-    }
-    // ||D_t x_k||_1 (FP32 per thread, FP64 across the warps)
-#pragma unroll
-    for (int u = 0; u < kPersistLMax; ++u)
-      if (ok && u < n && ta + u + 1 < Nt) tvf += c_abs(c_sub(u + 1 < n ? xs[u + 1] : xn, xs[u]));
-    if (write) {
-    // e_t = d1_t - S(m_{t+1} - m_t + d1_t) (t < Nt - 1), e_{ta-1} recomputed from its own inputs
-    float2 eprev = z2;
-    if (ok && n > 0 && ta > 0) eprev = c_sub(dp, c_soft(c_add(c_sub(ms[0], mp), dp), S.tau1));
-#pragma unroll
-    for (int u = 0; u < kPersistLMax; ++u)
-      if (u < n) ds[u] = (ta + u + 1 < Nt) ? c_sub(ds[u], c_soft(c_add(c_sub(u + 1 < n ? ms[u + 1] : mn, ms[u]), ds[u]), S.tau1))
-                                          : z2;
-    // rhs_t = e_t - e_{t-1} + rho (2 x_t - p_t) into xs;  f_t = p_t - x_t into ps
-#pragma unroll
-    for (int u = 0; u < kPersistLMax; ++u) {
-      if (u < n) {
-        const float2 x_t = xs[u], p_t = ps[u];
-        float2 rhs = c_sub(ds[u], u > 0 ? ds[u - 1] : eprev);
-        rhs.x = fmaf(S.rho, 2.f * x_t.x - p_t.x, rhs.x);
-        rhs.y = fmaf(S.rho, 2.f * x_t.y - p_t.y, rhs.y);
-        xs[u] = rhs;
-        ps[u] = c_sub(p_t, x_t);
-      }
-    }
-    // forward recurrence d_t = inv_t (rhs_t + d_{t-1}) by segments
-    {
-      float A = 1.f;
-      float2 B = z2;
-#pragma unroll
-      for (int u = 0; u < kPersistLMax; ++u)
-        if (u < n) {
-          const float inv = __ldg(S.thomas + ta + u);
-          A *= inv;
-          B = c_scale(c_add(xs[u], B), inv);
-        }
-      segA[seg * kPersistPx + px] = A;
-      segB[seg * kPersistPx + px] = B;
-    }
-    tbar();
-    {
-      float2 d = z2;
-      for (int qq = 0; qq < seg; ++qq) d = c_add(c_scale(d, segA[qq * kPersistPx + px]), segB[qq * kPersistPx + px]);
-#pragma unroll
-      for (int u = 0; u < kPersistLMax; ++u)
-        if (u < n) {
-          d = c_scale(c_add(xs[u], d), __ldg(S.thomas + ta + u));
-          ms[u] = d;
-        }
-    }
-    tbar();
-    // backward recurrence m'_t = d_t + inv_t m'_{t+1} by segments
-    {
-      float A = 1.f;
-      float2 B = z2;
-#pragma unroll
-      for (int u = kPersistLMax - 1; u >= 0; --u)
-        if (u < n) {
-          const float inv = __ldg(S.thomas + ta + u);
-          B = make_float2(fmaf(inv, B.x, ms[u].x), fmaf(inv, B.y, ms[u].y));
-          A *= inv;
-        }
-      segA[seg * kPersistPx + px] = A;
-      segB[seg * kPersistPx + px] = B;
-    }
-    tbar();
-    {
-      float2 mm = z2;
-      for (int qq = kPersistSeg - 1; qq > seg; --qq)
-        mm = c_add(c_scale(mm, segA[qq * kPersistPx + px]), segB[qq * kPersistPx + px]);
-#pragma unroll
-      for (int u = kPersistLMax - 1; u >= 0; --u)
-        if (u < n) {
-          const float inv = __ldg(S.thomas + ta + u);
-          mm = make_float2(fmaf(inv, mm.x, ms[u].x), fmaf(inv, mm.y, ms[u].y));
-          ms[u] = mm;
-        }
-      bnd[seg * kPersistPx + px] = n > 0 ? ms[0] : z2;   // m'_{ta}, read by the previous segment
-    }
-    tbar();
-    // m', d1' = e + D m', p' = m' + f
-    if (ok) {
-      const float2 mnext = (tb < Nt) ? bnd[(seg + 1) * kPersistPx + px] : z2;
-      float2* Mo = S.m[out];
-      float2* Do = S.d1[out];
-      float2* Po = S.p[out];
-#pragma unroll
-      for (int u = 0; u < kPersistLMax; ++u)
-        if (u < n) {
-          const size_t g = (size_t)(ta + u) * fstride + base;
-          Mo[g] = ms[u];
-          Po[g] = c_add(ms[u], ps[u]);
-          if (ta + u + 1 < Nt) Do[g] = c_add(ds[u], c_sub(u + 1 < n ? ms[u + 1] : mnext, ms[u]));
-        }
-    }
-    }   // write
-  }
+  TvChunkIO io;
+  io.x = S.x;
+  io.m = S.m[in];
+  io.d1 = S.d1[in];
+  io.p = S.p[in];
+  io.m_out = S.m[out];
+  io.d1_out = S.d1[out];
+  io.p_out = S.p[out];
+  io.thomas = S.thomas;
+  io.tau1 = S.tau1;
+  io.rho = S.rho;
+  io.Nt = S.Nt;
+  io.fstride = (size_t)S.Nx * S.Ny;
+  io.base = (size_t)i * S.Ny + (size_t)chunk * kPersistPx;
+  io.nvalid = min(kPersistPx, S.Ny - chunk * kPersistPx);
+  io.write = write;
+  struct TBar {
+    __device__ void operator()() const { tbar(); }
+  };
+  const float tvf = tv_chunk<kPersistLMax>(io, tid, segA, segB, bnd, TBar());
   // the prior term of J at x_k
   double v = warp_sum((double)tvf);
   const int w = tid >> 5, lane = tid & 31;
