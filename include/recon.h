@@ -390,7 +390,7 @@ recon_status recon_quantize_kspace(int Nx, int Ny, int Nt, int Nc, const float* 
  * a plan of a shape already tuned takes the cached choice at once.  Not part
  * of the paper; it only picks launch shapes, never the arithmetic. */
 typedef struct {
-  int temporal_tile_px;   /* pixels per block of the temporal kernel (TV 32/64/128, DFT 16..128) */
+  int temporal_tile_px;   /* pixels per block of the temporal kernel (TV 16, DFT 16..128, Haar 16..64) */
   int col_stages;         /* ring depth of the column-inverse kernel */
   int rows_per_block;     /* k-space rows per block of the prologue's row FFTs (1..8) */
   int combine_coils;      /* coils per pass of the prologue's column FFTs and coil combine (1..8) */

@@ -1,7 +1,7 @@
 // Launch-shape autotuner.  For each kernel with a free tile shape it times
 // every candidate on the plan's (or batch's) own device buffers with CUDA
 // events and keeps the fastest:
-//   temporal kernel       pixels per block (TV: 32/64/128, DFT: 16..128)
+//   temporal kernel       pixels per block (TV: 16, DFT: 16..128, Haar: 16..64)
 //   column-inverse kernel ring depth (multiples of 8 that fit)
 //   prologue row FFTs     k-space rows per block (1, 2, 4, 8)
 //   prologue column FFTs  coils per pass of the coil combine (1, 2, 4, 8)

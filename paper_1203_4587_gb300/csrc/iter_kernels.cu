@@ -441,26 +441,23 @@ __device__ __forceinline__ int find_slice(const SliceT* sl, int n, int blk) {
 
 // ---------------------------------------------------------------------------
 // Algorithm 2 temporal step (v-, m- and d1-updates along t) for every pixel:
-// one block of kTvChunkThreads threads per chunk of consecutive pixels (the
-// column layout keeps them contiguous in every frame), all values in
-// registers (tv_chunk.cuh).  PPT pixels a thread: 1 (chunks of kTvChunkPx,
-// tv_chunk) or 2 (chunks of kTvChunk2Px, tv_chunk2: half the address,
-// pivot and barrier work per pixel, twice the registers).  Both give the same
-// state bit for bit; the autotuner picks by time.  LMAX >= ceil(Nt / kTvSeg)
-// frames per segment.  Also accumulates ||D_t x||_1 of the incoming x (the
-// prior term of J): FP32 per thread and pixel, FP64 across the block.
+// one block of kTvChunkThreads threads per chunk of kTvChunkPx consecutive
+// pixels (the column layout keeps them contiguous in every frame), all values
+// in registers (tv_chunk.cuh).  LMAX >= ceil(Nt / kTvSeg) frames per
+// segment.  Also accumulates ||D_t x||_1 of the incoming x (the prior term of
+// J): FP32 per thread and across each warp, one FP64 value per warp (GB300's
+// FP64 pipe is too narrow for a conversion per thread).
 // ---------------------------------------------------------------------------
-template <int LMAX, int PPT>
+template <int LMAX>
 __global__ void __launch_bounds__(kTvChunkThreads) k_tv_temporal(TemporalLaunch L) {
-  __shared__ float seg_a[PPT * kTvChunkThreads];
-  __shared__ float2 seg_b[PPT * kTvChunkThreads];
-  __shared__ float2 bnd[PPT * kTvChunkThreads];
-  __shared__ double red[32];
-  constexpr int CPX = PPT * kTvChunkPx;
+  __shared__ float seg_a[kTvChunkThreads];
+  __shared__ float2 seg_b[kTvChunkThreads];
+  __shared__ float2 bnd[kTvChunkThreads];
+  __shared__ double red[kTvChunkThreads / 32];
   const TvSlice* sls = static_cast<const TvSlice*>(L.slices);
   const TvSlice& P = sls[find_slice(sls, L.nslices, (int)blockIdx.x)];
   if (P.stop && *P.stop) return;
-  const long long pix0 = (long long)(blockIdx.x - P.tile0) * CPX;
+  const long long pix0 = (long long)(blockIdx.x - P.tile0) * kTvChunkPx;
   TvChunkIO io;
   io.x = P.x;
   io.m = P.m;
@@ -475,49 +472,49 @@ __global__ void __launch_bounds__(kTvChunkThreads) k_tv_temporal(TemporalLaunch 
   io.Nt = P.Nt;
   io.fstride = (size_t)P.npix;
   io.base = (size_t)pix0;
-  io.nvalid = (int)min((long long)CPX, P.npix - pix0);
+  io.nvalid = (int)min((long long)kTvChunkPx, P.npix - pix0);
   io.write = P.write_state != 0;
-  double tv;
-  if constexpr (PPT == 2) tv = tv_chunk2<LMAX>(io, (int)threadIdx.x, seg_a, seg_b, bnd, BlockBar());
-  else tv = (double)tv_chunk<LMAX>(io, (int)threadIdx.x, seg_a, seg_b, bnd, BlockBar());
-  const double s = group_sum(tv, red, (int)threadIdx.x, kTvChunkThreads, BlockBar());
-  if (threadIdx.x == 0) atomicAdd(P.prior_acc, s);
-}
-
-template <int PPT>
-static void launch_tv_ppt(const TemporalLaunch& p, cudaStream_t s) {
-  const int ls = (p.Nt_max + kTvSeg - 1) / kTvSeg;
-  if (ls <= 1) k_tv_temporal<1, PPT><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else if (ls <= 2) k_tv_temporal<2, PPT><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else if (ls <= 3) k_tv_temporal<3, PPT><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else if (ls <= 4) k_tv_temporal<4, PPT><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else if (ls <= 5) k_tv_temporal<5, PPT><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else if (ls <= 6) k_tv_temporal<6, PPT><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else if (ls <= 8) k_tv_temporal<8, PPT><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else if (ls <= 12) k_tv_temporal<12, PPT><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else k_tv_temporal<16, PPT><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  float tvf = tv_chunk<LMAX>(io, (int)threadIdx.x, seg_a, seg_b, bnd, BlockBar());
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tvf += __shfl_down_sync(0xffffffffu, tvf, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)tvf;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kTvChunkThreads / 32; ++w) s += red[w];
+    atomicAdd(P.prior_acc, s);
+  }
 }
 
 constexpr size_t kSmemOptin = 227 * 1024;
-// chunk widths 16 (one pixel a thread) and 32 (two); the frames-per-segment
-// array covers Nt <= 128.  Above 96 frames the two-pixel form would spill.
+// one chunk width; the frames-per-segment array covers Nt <= 128
 int tv_tile_candidates(int Nt_max, int* out) {
+  (void)Nt_max;
   out[0] = kTvChunkPx;
-  if (Nt_max > 12 * kTvSeg) return 1;
-  out[1] = kTvChunk2Px;
-  return 2;
+  return 1;
 }
-int tv_tile_px(int Nt_max) { return Nt_max > 12 * kTvSeg ? kTvChunkPx : kTvChunk2Px; }
+int tv_tile_px(int Nt_max) {
+  (void)Nt_max;
+  return kTvChunkPx;
+}
 cudaError_t prepare_tv_temporal(int Nt_max, int px) {   // static shared memory only
-  if (Nt_max > 16 * kTvSeg) return cudaErrorInvalidValue;
-  return (px == kTvChunkPx || (px == kTvChunk2Px && Nt_max <= 12 * kTvSeg)) ? cudaSuccess : cudaErrorInvalidValue;
+  return (px == kTvChunkPx && Nt_max <= 16 * kTvSeg) ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s) {
   cudaError_t e = prepare_tv_temporal(p.Nt_max, p.tile_px);
   if (e != cudaSuccess) return e;
-  if (p.tile_px == kTvChunk2Px) launch_tv_ppt<2>(p, s);
-  else launch_tv_ppt<1>(p, s);
+  const int ls = (p.Nt_max + kTvSeg - 1) / kTvSeg;
+  if (ls <= 1) k_tv_temporal<1><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else if (ls <= 2) k_tv_temporal<2><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else if (ls <= 3) k_tv_temporal<3><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else if (ls <= 4) k_tv_temporal<4><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else if (ls <= 5) k_tv_temporal<5><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else if (ls <= 6) k_tv_temporal<6><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else if (ls <= 8) k_tv_temporal<8><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else if (ls <= 12) k_tv_temporal<12><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  else k_tv_temporal<16><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
   note_launch();
   return cudaGetLastError();
 }

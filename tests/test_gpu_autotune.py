@@ -36,7 +36,7 @@ def test_autotune_leaves_results_unchanged(prior, storage, objective):
     x0, i0 = P.solve(k)
     x0 = x0.cpu().numpy()
     t = P.autotune()
-    assert t.temporal_tile_px in ((16, 32, 64) if prior == "tv" else (16, 32, 64, 128))
+    assert t.temporal_tile_px in ((16,) if prior == "tv" else (16, 32, 64, 128))
     quantum = 8 if storage == "fp32" else 12          # the consumer warp count of the inverse kernel
     assert t.col_stages % quantum == 0 and t.col_stages >= quantum
     assert 1 <= t.rows_per_block <= 8 and 1 <= t.combine_coils <= 8
@@ -72,7 +72,7 @@ def test_batch_autotune_leaves_results_unchanged():
     ks = [gpu(c.kspace) for c in cases]
     x0 = [x.cpu().numpy() for x in b.solve(ks)]
     t = b.autotune()
-    assert t.temporal_tile_px in (16, 32, 64) and t.col_stages % 8 == 0
+    assert t.temporal_tile_px == 16 and t.col_stages % 8 == 0
     x1 = [x.cpu().numpy() for x in b.solve(ks)]      # re-captured graph
     x2 = [x.cpu().numpy() for x in b.solve(ks)]      # replay
     for a, c, d in zip(x0, x1, x2):
