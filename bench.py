@@ -78,6 +78,11 @@ def parse():
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-comparison", action="store_true")
+    ap.add_argument("--shard", default="slices", choices=["slices", "columns"],
+                    help="slices: each rank solves its own slice (weak scaling); columns: the ranks split one "
+                         "problem's image columns, each a slab plan over the whole k-space (strong scaling)")
+    ap.add_argument("--persistent", action="store_true",
+                    help="temporal-TV solves as one persistent launch (opts.persistent)")
     ap.add_argument("--detail", default=None,
                     help="also write the full record (notes, tunings, every timing) as JSON to this path")
     ap.add_argument("--grad-only", action="store_true",
@@ -179,6 +184,22 @@ def reduce_max(x, dist, device):
 def weak_value(world, steps, iters_per_step, ms):
     """Whole-job iterations/s: every rank runs `steps` solves of its own slice."""
     return world * steps * iters_per_step / (ms / 1e3)
+
+
+def column_shard(Nx, world, rank):
+    """The image columns i0 .. i0 + W - 1 that rank `rank` of `world` solves
+    when one problem is split along the horizontal axis: contiguous, sizes
+    differing by at most one.  Every step of the iteration separates along
+    that axis (Section IV-C, Section V), so the ranks need no exchange on the
+    data path; each holds the whole k-space (its rows are broadcast once)."""
+    base, extra = divmod(Nx, world)
+    i0 = rank * base + min(rank, extra)
+    return i0, base + (1 if rank < extra else 0)
+
+
+def strong_value(steps, iters_per_step, ms):
+    """Whole-job iterations/s when all ranks together solve one problem per step."""
+    return steps * iters_per_step / (ms / 1e3)
 
 
 def dist_env():
@@ -368,7 +389,7 @@ def make_batched_inputs(nslices, seed=64):
         return shapes, list(ex.map(one, shapes))
 
 
-def measure_batched(nslices, storage, steps=3):
+def measure_batched(nslices, storage, steps=3, persistent=False):
     """64 uneven slices, 80 iterations each, one launch per step, graph replay."""
     import torch
 
@@ -381,7 +402,7 @@ def measure_batched(nslices, storage, steps=3):
     plans, ks = [], []
     for sh, (k, s_, m) in zip(shapes, data):
         plans.append(Plan(m, torch.from_numpy(s_).cuda(), sh["lam"], sh["mu"], prior=sh["prior"], rho=sh["rho"],
-                          max_iters=sh["iters"], storage=storage))
+                          max_iters=sh["iters"], storage=storage, persistent=1 if persistent else 0))
         ks.append(torch.from_numpy(k).cuda())
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
@@ -660,13 +681,17 @@ def run_native(args):
         torch.cuda.synchronize()
 
     w = WORKLOAD
-    case = synthdata.make_case(w["name"], seed=2 + rank)   # each rank: its own slice
+    by_columns = args.shard == "columns" and world > 1 and args.prior != "stv"
+    # slices: each rank its own slice; columns: one problem, the ranks' slabs
+    case = synthdata.make_case(w["name"], seed=2 if by_columns else 2 + rank)
     kspace = torch.from_numpy(case.kspace.astype(np.complex64)).cuda()
     sens = torch.from_numpy(case.sens.astype(np.complex64)).cuda()
     mask = case.mask.astype(np.uint8)
+    slab = column_shard(w["Nx"], world, rank) if by_columns else None
     t0 = time.perf_counter()
     plan = Plan(mask, sens, w["lam"], w["mu"], prior=args.prior, rho=w["rho"], max_iters=w["iters"],
-                profile=1, storage=args.storage, spatial_weight=1.0, cg_steps=5)
+                profile=1, storage=args.storage, spatial_weight=1.0, cg_steps=5, slab=slab,
+                persistent=1 if args.persistent else 0)
     plan_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     plan.set_mu(w["mu"])                     # mu-reuse path: the inverses again, no allocation or upload
@@ -695,12 +720,15 @@ def run_native(args):
     clocks = sampler.stop() if sampler else None
     launches = binding.kernel_launches() - launches0
     ms = reduce_max(e0.elapsed_time(e1), dist, "cuda")
-    value = weak_value(world, args.steps, w["iters"], ms)
+    value = (strong_value(args.steps, w["iters"], ms) if by_columns else
+             weak_value(world, args.steps, w["iters"], ms))
     prof = plan.profile()
     _, info = plan.solve(kspace, out, info=True)
 
-    # roofline of the column-inverse kernel: algorithmic bytes per launch
-    Nx, Ny, Nt, Nc = w["Nx"], w["Ny"], w["Nt"], w["Nc"]
+    # roofline of the column-inverse kernel: algorithmic bytes per launch (a
+    # slab plan streams its own columns only)
+    Ny, Nt, Nc = w["Ny"], w["Nt"], w["Nc"]
+    Nx = slab[1] if slab else w["Nx"]
     esize = 8 if args.storage == "fp32" else 4
     total_rows = int(case.mask.sum())
     bytes_A = esize * Nx * Nt * Ny * (Ny + 1) // 2
@@ -730,9 +758,12 @@ def run_native(args):
                 "temporal_avg_ms": prof.temporal_ms / max(prof.temporal_launches, 1)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong" if by_columns else "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_obj(args.prior, args.storage), "roofline": roofline, "clocks": clocks,
+            "config": dict(config_obj(args.prior, args.storage),
+                           parallelism="columns (one slab plan per rank)" if by_columns else "replicas"),
+            "roofline": roofline, "clocks": clocks,
             "gpu_launches": launches, "plan_s": plan_s, "set_mu_s": set_mu_s, "tuning": tuning,
             "check": {"iters": info.iters, "J0": info.J0, "J": info.J, "primal_res": info.primal_res,
                       "dual_res": info.dual_res}}
@@ -740,7 +771,7 @@ def run_native(args):
     # end to end through the public API with host buffers
     if not args.no_e2e:
         kh = torch.from_numpy(case.kspace.astype(np.complex64)).pin_memory()
-        ih = torch.empty((Nt, Ny, Nx), dtype=torch.complex64).pin_memory()
+        ih = torch.empty((Nt, Ny, w["Nx"]), dtype=torch.complex64).pin_memory()
         plan.solve_host(kh, ih)
         n_e2e = max(3, args.steps // 2)
         barrier()
@@ -748,7 +779,9 @@ def run_native(args):
         for _ in range(n_e2e):
             plan.solve_host(kh, ih)
         el = reduce_max(time.perf_counter() - t0, dist, "cuda")
-        line["e2e"] = {"value": weak_value(world, n_e2e, w["iters"], el * 1e3), "unit": UNIT,
+        e2e_value = (strong_value(n_e2e, w["iters"], el * 1e3) if by_columns else
+                     weak_value(world, n_e2e, w["iters"], el * 1e3))
+        line["e2e"] = {"value": e2e_value, "unit": UNIT,
                        "h2d_bytes_per_step": int(kh.numel() * 8), "d2h_bytes_per_step": int(ih.numel() * 8),
                        "step": "recon_solve_host: pinned H2D, solve, D2H"}
 
@@ -792,7 +825,7 @@ def run_native(args):
         plan.close()
         torch.cuda.empty_cache()
         try:
-            line["batched"] = measure_batched(args.batched_slices, args.storage)
+            line["batched"] = measure_batched(args.batched_slices, args.storage, persistent=args.persistent)
         except Exception as e:  # report, never fake
             line["batched"] = {"error": str(e)[:300]}
 

@@ -42,16 +42,18 @@
  *   - Every function returns a recon_status; no function throws or aborts.
  *     recon_last_error() gives a human-readable reason for the last failure
  *     of the calling thread.
- *   - One device per process: the kernels' raised shared-memory limits are
- *     set once per process, on the device of the first launch.  Plans on a
- *     second device in the same process fail at their first large launch
- *     with RECON_ERR_CUDA (run one process per GPU).
+ *   - Devices: a plan lives on the device that was current at its creation,
+ *     and every call on it (or on a batch, volume or gradient engine built on
+ *     it) must be made with that device current.  Plans on several devices
+ *     of one process are fine: each kernel's raised shared-memory limit is
+ *     set on the current device at its first launch there and remembered per
+ *     device ordinal.
  *   - Host threads: calls on different plans may come from different threads;
  *     calls that use one plan (or a batch, volume or gradient engine built
- *     on it) must not overlap.  The limits above are raised without a lock,
- *     so run one solve of each shape before solving from several threads at
- *     once (two first launches racing can fail with RECON_ERR_CUDA).  The
- *     autotuner's cache and the allocation-free workspace are locked.
+ *     on it) must not overlap.  The per-device limits above are kept in
+ *     atomics (two first launches racing both set the attribute, which is
+ *     harmless); the autotuner's cache and the allocation-free workspace are
+ *     locked.
  */
 #ifndef RECON_H
 #define RECON_H
