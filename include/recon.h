@@ -98,7 +98,7 @@ typedef enum {
 
 /* Storage of the data a solve keeps in device memory.  For a plan (opts.storage):
  *   FP32  packed inverses and hybrid coil data F_h'y in complex64; the H'y
- *         prologue in FP64, rounded once.
+ *         prologue in double-float arithmetic (about 48 bits), rounded once.
  *   FP16 / BF16  packed inverses (double-float inversion rounded once) and the
  *         hybrid coil data (per-frame power-of-two scales) as 16-bit (re, im)
  *         pairs; FFT butterflies, products and accumulation in FP32; the
@@ -138,6 +138,12 @@ typedef struct {
                        independent, so each column waits only for its own image column's temporal
                        step, never for a grid barrier); other solves ignore it.  Both give the same
                        iterates up to FP32 rounding order. */
+  int overlap;      /* 1 (default): in a one-launch-per-step temporal-TV solve, each inverse and
+                       temporal launch carries a programmatic dependency on the kernel before it, so
+                       its launch and set-up (and the inverse kernel's stream of the packed inverses,
+                       which no step writes) overlap the end of that kernel; the kernel waits in-device
+                       before it touches the iteration's state.  Not used with a stopping test or
+                       with profile = 1.  0: plain stream order.  Results are identical either way. */
 } recon_opts;
 
 typedef struct {
@@ -244,6 +250,11 @@ recon_status recon_solve_host(recon_plan* plan, const float* kspace_host, float*
 /* Copies J(0..n-1) of the last solve to `J_host` (synchronises the plan's
  * last stream).  Entries past the last iteration are NaN. */
 recon_status recon_get_trace(recon_plan* plan, double* J_host, int n);
+
+/* Turns the per-kernel CUDA-event timing of later solves on (1) or off (0),
+ * as opts.profile at creation; creates the events on first use.  Errors:
+ * INVALID_ARG (NULL plan, on not 0 or 1), CUDA. */
+recon_status recon_plan_set_profile(recon_plan* plan, int on);
 
 /* Device time of the kernels of the last solve, from CUDA events recorded on
  * the solve's stream when opts.profile == 1 (synchronises that stream).

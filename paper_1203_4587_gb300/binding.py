@@ -37,14 +37,14 @@ EXPORTS = ["recon_default_opts", "recon_plan_create", "recon_solve", "recon_solv
            "recon_grad_create", "recon_grad_forward", "recon_grad_backward", "recon_grad_destroy",
            "recon_solve_kspace", "recon_quantize_kspace", "recon_autotune", "recon_batch_autotune",
            "recon_plan_create_slab", "recon_solve_slabs", "recon_plan_set_mu", "recon_selftest_wait_timeout",
-           "recon_volume_create"]
+           "recon_volume_create", "recon_plan_set_profile"]
 
 
 class Opts(C.Structure):
     _fields_ = [("rho", C.c_float), ("max_iters", C.c_int), ("tol", C.c_double), ("storage", C.c_int),
                 ("objective", C.c_int), ("mask_full", C.c_int), ("col_stages", C.c_int), ("profile", C.c_int),
                 ("frame_levels", C.c_int), ("spatial_weight", C.c_float), ("cg_steps", C.c_int),
-                ("persistent", C.c_int)]
+                ("persistent", C.c_int), ("overlap", C.c_int)]
 
 
 class Info(C.Structure):
@@ -155,6 +155,8 @@ def load(path: str = LIB_PATH):
     lib.recon_autotune.restype = i
     lib.recon_batch_autotune.argtypes = [vp, C.POINTER(Tuning), vp]
     lib.recon_batch_autotune.restype = i
+    lib.recon_plan_set_profile.argtypes = [vp, i]
+    lib.recon_plan_set_profile.restype = i
     _lib = lib
     return lib
 
@@ -364,6 +366,10 @@ class Plan:
         out = torch.empty((Ny, Ny), dtype=torch.complex64, device="cuda")
         _check(load().recon_export_inverse(self._h, int(i), int(t), _ptr(out), _stream(stream)))
         return out
+
+    def set_profile(self, on: bool):
+        """Per-kernel event timing of later solves on or off (recon_plan_set_profile)."""
+        _check(load().recon_plan_set_profile(self._h, 1 if on else 0))
 
     def profile(self) -> Profile:
         pr = Profile()

@@ -86,13 +86,35 @@ static FftPlanT<T> fft_plan_t(int n, const T* d_tw) {
 FftPlanDev make_fft_plan_host(int n, const float2* d_tw) { return fft_plan_t<float2>(n, d_tw); }
 FftPlanDf make_fft_plan_host_df(int n, const dc* d_tw) { return fft_plan_t<dc>(n, d_tw); }
 
+cudaError_t plan_create_events(recon_plan* p) {
+  if (!p->ev_col.empty()) return cudaSuccess;
+  const size_t ne = 2 * ((size_t)p->opts.max_iters + 2);
+  p->ev_col.assign(ne, nullptr);
+  p->ev_tmp.assign(ne, nullptr);
+  for (auto& e : p->ev_col) {
+    const cudaError_t ce = cudaEventCreate(&e);
+    if (ce != cudaSuccess) return ce;
+  }
+  for (auto& e : p->ev_tmp) {
+    const cudaError_t ce = cudaEventCreate(&e);
+    if (ce != cudaSuccess) return ce;
+  }
+  for (auto& e : p->ev_solve) {
+    const cudaError_t ce = cudaEventCreate(&e);
+    if (ce != cudaSuccess) return ce;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace recon
 
 recon_plan::~recon_plan() {
   delete eng;
   delete eng_inv;
-  for (cudaEvent_t e : ev_col) cudaEventDestroy(e);
-  for (cudaEvent_t e : ev_tmp) cudaEventDestroy(e);
+  for (cudaEvent_t e : ev_col)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : ev_tmp)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : ev_solve)
     if (e) cudaEventDestroy(e);
   for (void* q : allocs) cudaFree(q);
@@ -118,6 +140,7 @@ void recon_default_opts(recon_opts* o) {
   o->spatial_weight = 1.f;
   o->cg_steps = 5;
   o->persistent = 0;
+  o->overlap = 1;
 }
 
 const char* recon_status_string(recon_status s) {
@@ -384,7 +407,7 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
   recon_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.rho > 0.f) || o.max_iters < 0 || !(o.tol >= 0.0) || o.storage < 0 || o.storage > 2 || o.col_stages < 0 ||
-      o.persistent < 0 || o.persistent > 1 ||
+      o.persistent < 0 || o.persistent > 1 || o.overlap < 0 || o.overlap > 1 ||
       o.objective < 0 || o.objective > 2 || (prior == RECON_PRIOR_HAAR && (o.frame_levels < 1 || o.frame_levels > 6)) ||
       (prior == RECON_PRIOR_STV && (!(o.spatial_weight >= 0.f) || !std::isfinite(o.spatial_weight) ||
                                     o.cg_steps < 1 || o.cg_steps > 64)))
@@ -549,15 +572,7 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
     if (st != RECON_OK) return cleanup(st);
     p->col_stages = p->eng->stages;
   }
-  if (o.profile) {
-    const size_t ne = 2 * ((size_t)o.max_iters + 2);
-    p->ev_col.resize(ne);
-    p->ev_tmp.resize(ne);
-    for (auto& e : p->ev_col) PC(cudaEventCreate(&e));
-    for (auto& e : p->ev_tmp) PC(cudaEventCreate(&e));
-    PC(cudaEventCreate(&p->ev_solve[0]));
-    PC(cudaEventCreate(&p->ev_solve[1]));
-  }
+  if (o.profile) PC(plan_create_events(p));
   p->last_stream = s;
   *out = p;
   return RECON_OK;
@@ -650,6 +665,17 @@ recon_status recon_quantize_kspace(int Nx, int Ny, int Nt, int Nc, const float* 
     return fail(RECON_ERR_INVALID_ARG, "storage must be RECON_STORAGE_FP16 or RECON_STORAGE_BF16");
   RC(launch_quantize_kspace(reinterpret_cast<const float2*>(kspace), (long long)Nc * Ny * Nx, Nt, storage, out,
                             frame_scale, static_cast<cudaStream_t>(stream)));
+  return RECON_OK;
+}
+
+recon_status recon_plan_set_profile(recon_plan* p, int on) {
+  g_last_error.clear();
+  if (!p || (on != 0 && on != 1)) return fail(RECON_ERR_INVALID_ARG, "plan must be non-NULL and on 0 or 1");
+  if (on) {
+    cudaSetDevice(p->device);
+    RC(plan_create_events(p));
+  }
+  p->opts.profile = on;
   return RECON_OK;
 }
 

@@ -198,6 +198,16 @@ __device__ __forceinline__ f32x2 ffma2(f32x2 a, f32x2 b, f32x2 c) {   // a * b +
   return d;
 }
 
+// ---- programmatic dependent launch ------------------------------------------
+// A grid launched with cudaLaunchAttributeProgrammaticStreamSerialization may
+// start while the previous kernel of its stream is still running.
+// pdl_wait(): the calling thread waits until the grids this one depends on
+// have completed and their memory operations are visible (returns at once
+// for a grid launched without the attribute).  pdl_trigger(): this CTA lets
+// the next such grid be scheduled once every CTA has triggered or exited.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---- timers, barriers ------------------------------------------------------
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;

@@ -323,6 +323,8 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
   e->obj = p0->opts.objective != 0 || p0->opts.tol > 0.0;
   e->stop_test = false;
   for (int q = 0; q < n; ++q) e->stop_test = e->stop_test || plans[q]->opts.tol > 0.0;
+  e->overlap = true;
+  for (int q = 0; q < n; ++q) e->overlap = e->overlap && plans[q]->opts.overlap != 0;
   e->fused = e->obj && p0->opts.objective != 2 && p0->storage == 0;
   for (int q = 1; q < n; ++q) {
     const recon_plan* p = plans[q];
@@ -452,12 +454,18 @@ recon_status engine_set_tile(Engine* e, int px) {
     RC(upload(e->arena, reinterpret_cast<StvSlice**>(&e->d_tmp), t));
   } else if (e->tv) {
     std::vector<TvSlice> t((size_t)(K + 1) * n);
-    for (int k = 1; k <= K + 1; ++k)
+    e->tv_full.assign((size_t)K + 1, 0);
+    const int ls = (e->Nt_max + kTvSeg - 1) / kTvSeg;
+    for (int k = 1; k <= K + 1; ++k) {
+      bool full = ls <= kTvFullLMax;
       for (int q = 0; q < n; ++q) {
         TvSlice d = tv_desc(e->plans[q], k, K);
         d.tile0 = tile0[q];
         t[(size_t)(k - 1) * n + q] = d;
+        full = full && d.Nt == kTvSeg * ls && d.npix % kTvChunkPx == 0 && d.d1 && d.write_state;
       }
+      e->tv_full[(size_t)k - 1] = full ? 1 : 0;
+    }
     RC(upload(e->arena, reinterpret_cast<TvSlice**>(&e->d_tmp), t));
     RC(prepare_tv_temporal(e->Nt_max, px));
   } else if (e->prior == RECON_PRIOR_HAAR) {
@@ -513,7 +521,7 @@ recon_status engine_build_inverse(Engine* e, recon_plan* p) {
   return finish_col_shape(e, pl, 1, p->opts.col_stages);
 }
 
-recon_status launch_col_set(Engine* e, int set, cudaStream_t s) {
+recon_status launch_col_set(Engine* e, int set, cudaStream_t s, bool pdl) {
   ColLaunch L{};
   L.slices = e->d_col + (size_t)set * e->n;
   L.nslices = e->n;
@@ -523,11 +531,11 @@ recon_status launch_col_set(Engine* e, int set, cudaStream_t s) {
   L.nb_max = e->nb_max;
   L.stages = e->stages;
   L.err = e->d_err;
-  RC(launch_col_inverse(L, e->storage, e->grid, s));
+  RC(launch_col_inverse(L, e->storage, e->grid, s, pdl));
   return RECON_OK;
 }
 
-recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s) {
+recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s, bool pdl) {
   TemporalLaunch L{};
   L.nslices = e->n;
   L.nblocks = e->tmp_blocks;
@@ -541,7 +549,8 @@ recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s) {
     RC(launch_stv_prior(S, s));
   } else if (e->tv) {
     L.slices = static_cast<TvSlice*>(e->d_tmp) + (size_t)set * e->n;
-    RC(launch_tv_temporal(L, s));
+    L.full = (size_t)set < e->tv_full.size() ? e->tv_full[(size_t)set] : 0;
+    RC(launch_tv_temporal(L, s, pdl));
   } else if (e->prior == RECON_PRIOR_HAAR) {
     L.slices = static_cast<HaarSlice*>(e->d_tmp) + (size_t)set * e->n;
     RC(launch_haar_temporal(L, e->levels, s));
@@ -629,10 +638,15 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
       if ((st = launch_residuals(p, s)) != RECON_OK) return st;
     return RECON_OK;
   }
+  // Programmatic dependent launches between the TV temporal and inverse
+  // kernels: both wait in-device for the kernel before them.  Not with a
+  // stopping test (the inverse kernel reads the stop flags before its wait) or
+  // with profiling events between the launches.
+  const bool pdl = e->overlap && e->tv && !e->stop_test && !prof;
   for (int k = 1; k <= K; ++k) {
     if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, true, s);
     if (e->prior == RECON_PRIOR_STV) st = launch_stv_step(e, k - 1, s);
-    else st = launch_tmp_set(e, k - 1, s);
+    else st = launch_tmp_set(e, k - 1, s, pdl);
     if (st != RECON_OK) return st;
     if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, false, s);
     if (e->stop_test) RC(launch_finalize(e->d_fin, e->n, k - 1, k - 1, s));
@@ -640,14 +654,14 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
       for (recon_plan* p : e->plans)
         RC(cudaMemcpyAsync(p->res_prev, p->x, p->nimg() * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     if (prof) p0->mark(p0->ev_col, p0->n_col, true, s);
-    if ((st = launch_col_set(e, k - 1, s)) != RECON_OK) return st;
+    if ((st = launch_col_set(e, k - 1, s, pdl)) != RECON_OK) return st;
     if (prof) p0->mark(p0->ev_col, p0->n_col, false, s);
     if (e->obj && !e->fused)
       for (recon_plan* p : e->plans)
         if ((st = plan_objective(p, p->x, p->trace_fid + k, s)) != RECON_OK) return st;
   }
   if (e->obj) {
-    if ((st = launch_tmp_set(e, K, s)) != RECON_OK) return st;
+    if ((st = launch_tmp_set(e, K, s, pdl)) != RECON_OK) return st;
     // with a fixed iteration count J(0) .. J(K) are formed here, in one launch
     RC(launch_finalize(e->d_fin, e->n, e->stop_test ? K : 0, K, s));
   }

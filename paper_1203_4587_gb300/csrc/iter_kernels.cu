@@ -111,6 +111,13 @@ __global__ void __launch_bounds__(col_threads(Elem<E>::bytes), 1) k_col_inverse(
     fence_mbar_init();
   }
   __syncthreads();
+  // Launched after the temporal step with a programmatic dependency, the
+  // producers start streaming the packed inverses (which no earlier kernel
+  // writes) at once; every other role waits for the previous kernel before it
+  // reads or writes the iteration's state.  The stop flags read above change
+  // only with a stopping test, where the engine launches without the
+  // dependency.  The next kernel may be scheduled as soon as every CTA runs.
+  pdl_trigger();
   constexpr int ES = Elem<E>::bytes;
   const int w0 = 0, w1 = P.work_off[blockIdx.x + 1] - P.work_off[blockIdx.x];
   // work entry: slice in the high byte, column in the low 24 bits
@@ -168,6 +175,7 @@ __global__ void __launch_bounds__(col_threads(Elem<E>::bytes), 1) k_col_inverse(
     }
     return;
   }
+  pdl_wait();
   if (warp == kConsumerWarps + kProducers) {
     // ---------------- r loader: each column's inputs into a slot -------------
     // With 16-byte aligned columns (Ny even) lane 0 moves them with the TMA
@@ -414,16 +422,34 @@ cudaError_t prepare_col_inverse(int storage, size_t smem) {
   }
 }
 
-cudaError_t launch_col_inverse(const ColLaunch& p, int storage, int grid, cudaStream_t s) {
+// cudaLaunchKernelEx with the programmatic-dependency attribute when `pdl`.
+template <typename... Args>
+static cudaError_t launch_ex(void (*kern)(Args...), int grid, int threads, size_t smem, cudaStream_t s, bool pdl,
+                             Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+cudaError_t launch_col_inverse(const ColLaunch& p, int storage, int grid, cudaStream_t s, bool pdl) {
   const size_t smem = col_inverse_smem(p.stages, p.nb_max, p.nslices, p.work_max, storage ? 4 : 8);
   cudaError_t e = prepare_col_inverse(storage, smem);
   if (e != cudaSuccess) return e;
   switch (storage) {
-    case 0: k_col_inverse<float2><<<grid, col_threads(8), smem, s>>>(p); break;
-    case 1: k_col_inverse<__half2><<<grid, col_threads(4), smem, s>>>(p); break;
-    case 2: k_col_inverse<__nv_bfloat162><<<grid, col_threads(4), smem, s>>>(p); break;
+    case 0: e = launch_ex(k_col_inverse<float2>, grid, col_threads(8), smem, s, pdl, p); break;
+    case 1: e = launch_ex(k_col_inverse<__half2>, grid, col_threads(4), smem, s, pdl, p); break;
+    case 2: e = launch_ex(k_col_inverse<__nv_bfloat162>, grid, col_threads(4), smem, s, pdl, p); break;
     default: return cudaErrorInvalidValue;
   }
+  if (e != cudaSuccess) return e;
   note_launch();
   return cudaGetLastError();
 }
@@ -448,12 +474,18 @@ __device__ __forceinline__ int find_slice(const SliceT* sl, int n, int blk) {
 // J): FP32 per thread and across each warp, one FP64 value per warp (GB300's
 // FP64 pipe is too narrow for a conversion per thread).
 // ---------------------------------------------------------------------------
-template <int LMAX>
-__global__ void __launch_bounds__(kTvChunkThreads) k_tv_temporal(TemporalLaunch L) {
+// Up to 4 frames a segment, 8 blocks an SM (64 registers) hide the load latency
+// best; more frames need the registers.
+template <int LMAX, bool FULL>
+__global__ void __launch_bounds__(kTvChunkThreads, LMAX <= 4 ? 8 : 1) k_tv_temporal(TemporalLaunch L) {
   __shared__ float seg_a[kTvChunkThreads];
   __shared__ float2 seg_b[kTvChunkThreads];
   __shared__ float2 bnd[kTvChunkThreads];
   __shared__ double red[kTvChunkThreads / 32];
+  // launched after the inverse step with a programmatic dependency: wait for
+  // it (x, and the stop flag), then let the next inverse step be scheduled
+  pdl_wait();
+  pdl_trigger();
   const TvSlice* sls = static_cast<const TvSlice*>(L.slices);
   const TvSlice& P = sls[find_slice(sls, L.nslices, (int)blockIdx.x)];
   if (P.stop && *P.stop) return;
@@ -474,7 +506,7 @@ __global__ void __launch_bounds__(kTvChunkThreads) k_tv_temporal(TemporalLaunch 
   io.base = (size_t)pix0;
   io.nvalid = (int)min((long long)kTvChunkPx, P.npix - pix0);
   io.write = P.write_state != 0;
-  float tvf = tv_chunk<LMAX>(io, (int)threadIdx.x, seg_a, seg_b, bnd, BlockBar());
+  float tvf = tv_chunk<LMAX, FULL>(io, (int)threadIdx.x, seg_a, seg_b, bnd, BlockBar());
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tvf += __shfl_down_sync(0xffffffffu, tvf, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)tvf;
@@ -502,19 +534,31 @@ cudaError_t prepare_tv_temporal(int Nt_max, int px) {   // static shared memory 
   return (px == kTvChunkPx && Nt_max <= 16 * kTvSeg) ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s) {
+cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s, bool pdl) {
   cudaError_t e = prepare_tv_temporal(p.Nt_max, p.tile_px);
   if (e != cudaSuccess) return e;
   const int ls = (p.Nt_max + kTvSeg - 1) / kTvSeg;
-  if (ls <= 1) k_tv_temporal<1><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else if (ls <= 2) k_tv_temporal<2><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else if (ls <= 3) k_tv_temporal<3><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else if (ls <= 4) k_tv_temporal<4><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else if (ls <= 5) k_tv_temporal<5><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else if (ls <= 6) k_tv_temporal<6><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else if (ls <= 8) k_tv_temporal<8><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else if (ls <= 12) k_tv_temporal<12><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
-  else k_tv_temporal<16><<<p.nblocks, kTvChunkThreads, 0, s>>>(p);
+  const int nb = p.nblocks, nt = kTvChunkThreads;
+  if (p.full) {   // every chunk whole (set by the engine): the specialised instantiation
+    switch (ls) {
+      case 1: e = launch_ex(k_tv_temporal<1, true>, nb, nt, 0, s, pdl, p); break;
+      case 2: e = launch_ex(k_tv_temporal<2, true>, nb, nt, 0, s, pdl, p); break;
+      case 3: e = launch_ex(k_tv_temporal<3, true>, nb, nt, 0, s, pdl, p); break;
+      case 4: e = launch_ex(k_tv_temporal<4, true>, nb, nt, 0, s, pdl, p); break;
+      case 5: e = launch_ex(k_tv_temporal<5, true>, nb, nt, 0, s, pdl, p); break;
+      case 6: e = launch_ex(k_tv_temporal<6, true>, nb, nt, 0, s, pdl, p); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else if (ls <= 1) e = launch_ex(k_tv_temporal<1, false>, nb, nt, 0, s, pdl, p);
+  else if (ls <= 2) e = launch_ex(k_tv_temporal<2, false>, nb, nt, 0, s, pdl, p);
+  else if (ls <= 3) e = launch_ex(k_tv_temporal<3, false>, nb, nt, 0, s, pdl, p);
+  else if (ls <= 4) e = launch_ex(k_tv_temporal<4, false>, nb, nt, 0, s, pdl, p);
+  else if (ls <= 5) e = launch_ex(k_tv_temporal<5, false>, nb, nt, 0, s, pdl, p);
+  else if (ls <= 6) e = launch_ex(k_tv_temporal<6, false>, nb, nt, 0, s, pdl, p);
+  else if (ls <= 8) e = launch_ex(k_tv_temporal<8, false>, nb, nt, 0, s, pdl, p);
+  else if (ls <= 12) e = launch_ex(k_tv_temporal<12, false>, nb, nt, 0, s, pdl, p);
+  else e = launch_ex(k_tv_temporal<16, false>, nb, nt, 0, s, pdl, p);
+  if (e != cudaSuccess) return e;
   note_launch();
   return cudaGetLastError();
 }

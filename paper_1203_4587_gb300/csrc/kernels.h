@@ -206,12 +206,21 @@ struct StvLaunch {
   int step;                  // CG step j of the direction / update kernels
 };
 
+// Temporal TV kernel shape (tv_chunk.cuh): chunks of kTvChunkPx pixels, the
+// t-axis cut into kTvSeg segments; whole chunks with up to kTvFullLMax frames
+// a segment take the specialised instantiation.
+constexpr int kTvSeg = 8;
+constexpr int kTvChunkPx = 16;
+constexpr int kTvFullLMax = 6;
+
 struct TemporalLaunch {      // one launch over the tiles of several slices
   const void* slices;        // TvSlice[], DftSlice[] or HaarSlice[]
   int nslices;
   int nblocks;
   int Nt_max;                // shared-memory sizing
   int tile_px;               // pixels per block (TV)
+  int full;                  // TV: every slice has Nt == 8 * ceil(Nt_max / 8) <= 48, Nx*Ny a
+                             // multiple of 16, d1 present and state written (whole chunks)
 };
 
 struct TvBwdSlice {          // reverse of one Algorithm 2 step (see grad.cu), one slice
@@ -334,7 +343,9 @@ void note_launch();
 void set_last_error(const std::string& why);
 
 // ---- launchers (return cudaGetLastError()) ---------------------------------
-cudaError_t launch_col_inverse(const ColLaunch& p, int storage, int grid, cudaStream_t s);
+// pdl: launch with a programmatic dependency on the previous kernel of `s`
+// (the kernel waits for it in-device; see pdl_wait in common.cuh)
+cudaError_t launch_col_inverse(const ColLaunch& p, int storage, int grid, cudaStream_t s, bool pdl = false);
 // esize: bytes per stored element (8 FP32, 4 FP16/BF16)
 size_t col_inverse_smem(int stages, int nb_max, int nslices, int work_max, int esize);
 int col_inverse_max_stages(int nb_max, int nslices, int work_max, int esize);
@@ -346,7 +357,7 @@ int tv_tile_px(int Nt_max);                         // default pixels per block
 int dft_tile_px();
 int tv_tile_candidates(int Nt_max, int* out);       // tile widths that fit (<= 4 entries)
 int dft_tile_candidates(int Nt_max, int* out);
-cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s);
+cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s, bool pdl = false);
 cudaError_t launch_dft_temporal(const TemporalLaunch& p, cudaStream_t s);
 cudaError_t launch_haar_temporal(const TemporalLaunch& p, int levels, cudaStream_t s);
 cudaError_t prepare_haar_temporal(int Nt_max, int levels, int px);

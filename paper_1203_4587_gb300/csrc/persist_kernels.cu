@@ -138,7 +138,7 @@ __device__ void persist_temporal(const PersistSlice& S, int i, int chunk, int k,
   struct TBar {
     __device__ void operator()() const { tbar(); }
   };
-  const float tvf = tv_chunk<kPersistLMax>(io, tid, segA, segB, bnd, TBar());
+  const float tvf = tv_chunk<kPersistLMax, false>(io, tid, segA, segB, bnd, TBar());
   // the prior term of J at x_k
   double v = warp_sum((double)tvf);
   const int w = tid >> 5, lane = tid & 31;

@@ -36,6 +36,8 @@ struct Engine {
   // temporal launches: K+1 descriptor sets (k = 1..K, then the final prior term)
   void* d_tmp = nullptr;
   int tmp_blocks = 0, Nt_max = 0, tile_px = 0;
+  std::vector<char> tv_full;  // per temporal set: every TV chunk whole (TemporalLaunch::full)
+  bool overlap = false;       // every plan asks for programmatic dependent launches (opts.overlap)
   // column-inverse launches: K descriptor sets
   ColSlice* d_col = nullptr;
   unsigned* d_work = nullptr;
@@ -175,8 +177,11 @@ recon_status cuda_fail(cudaError_t e, const char* where);
 void build_col_work(recon_plan* const* plans, int n, int grid, std::vector<unsigned>& work, std::vector<int>& off,
                     int& work_max);
 recon_status finish_col_shape(Engine* e, recon_plan* const* plans, int n, int stages_req);
-recon_status launch_col_set(Engine* e, int set, cudaStream_t s);   // descriptor set `set` of d_col
-recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s);   // descriptor set `set` of d_tmp
+// descriptor set `set` of d_col / d_tmp; pdl: with a programmatic dependency on
+// the previous kernel of `s` (TV temporal and inverse kernels only)
+recon_status launch_col_set(Engine* e, int set, cudaStream_t s, bool pdl = false);
+recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s, bool pdl = false);
+cudaError_t plan_create_events(recon_plan* p);   // the profiling events, once
 recon_status engine_build(Engine* e, recon_plan* const* plans, int n);
 recon_status engine_set_tile(Engine* e, int px);   // temporal tile width (rebuilds its descriptor sets)
 int engine_tile_candidates(const Engine* e, int* out);   // temporal tile widths that fit

@@ -72,11 +72,15 @@ def test_invalid_arguments_rejected_before_any_cuda_call(libpath):
     assert st == 1
     bad = binding.Opts()
     lib.recon_default_opts(C.byref(bad))
-    assert bad.persistent == 0
-    bad.persistent = 2
-    st = lib.recon_plan_create(C.byref(h), 4, 4, 2, 1, C.cast(mask, C.c_void_p), C.cast(sens, C.c_void_p),
-                               0.01, 0.1, 0, C.byref(bad), None)
-    assert st == 1
+    assert bad.persistent == 0 and bad.overlap == 1
+    for field in ("persistent", "overlap"):
+        bad = binding.Opts()
+        lib.recon_default_opts(C.byref(bad))
+        setattr(bad, field, 2)
+        st = lib.recon_plan_create(C.byref(h), 4, 4, 2, 1, C.cast(mask, C.c_void_p), C.cast(sens, C.c_void_p),
+                                   0.01, 0.1, 0, C.byref(bad), None)
+        assert st == 1, field
+    assert lib.recon_plan_set_profile(None, 1) == 1
     for field, value in (("cg_steps", 0), ("cg_steps", 65), ("spatial_weight", -0.5)):   # spatio-temporal prior
         bad = binding.Opts()
         lib.recon_default_opts(C.byref(bad))
