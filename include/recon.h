@@ -138,12 +138,14 @@ typedef struct {
                        independent, so each column waits only for its own image column's temporal
                        step, never for a grid barrier); other solves ignore it.  Both give the same
                        iterates up to FP32 rounding order. */
-  int overlap;      /* 1 (default): in a one-launch-per-step temporal-TV solve, each inverse and
-                       temporal launch carries a programmatic dependency on the kernel before it, so
-                       its launch and set-up (and the inverse kernel's stream of the packed inverses,
-                       which no step writes) overlap the end of that kernel; the kernel waits in-device
-                       before it touches the iteration's state.  Not used with a stopping test or
-                       with profile = 1.  0: plain stream order.  Results are identical either way. */
+  int overlap;      /* 1 (default): in a plan's own one-launch-per-step solve with the TV, DFT or
+                       Haar prior, each inverse and temporal launch carries a programmatic dependency
+                       on the kernel before it, so its launch and set-up (and the inverse kernel's
+                       stream of the packed inverses, which no step writes) overlap the end of that
+                       kernel; the kernel waits in-device before it touches the iteration's state.
+                       Not used with a stopping test, with profile = 1, for the spatio-temporal prior,
+                       or in batches (replayed graphs).  0: plain stream order.  Results are identical
+                       either way. */
 } recon_opts;
 
 typedef struct {

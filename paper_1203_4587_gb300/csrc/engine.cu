@@ -553,10 +553,10 @@ recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s, bool pdl) {
     RC(launch_tv_temporal(L, s, pdl));
   } else if (e->prior == RECON_PRIOR_HAAR) {
     L.slices = static_cast<HaarSlice*>(e->d_tmp) + (size_t)set * e->n;
-    RC(launch_haar_temporal(L, e->levels, s));
+    RC(launch_haar_temporal(L, e->levels, s, pdl));
   } else {
     L.slices = static_cast<DftSlice*>(e->d_tmp) + (size_t)set * e->n;
-    RC(launch_dft_temporal(L, s));
+    RC(launch_dft_temporal(L, s, pdl));
   }
   return RECON_OK;
 }
@@ -578,7 +578,7 @@ recon_status launch_stv_step(Engine* e, int set, cudaStream_t s) {
   return RECON_OK;
 }
 
-recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
+recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile, bool allow_pdl) {
   const int K = e->K;
   const size_t nt = (size_t)K + 2;
   recon_plan* p0 = e->plans[0];
@@ -638,11 +638,22 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile) {
       if ((st = launch_residuals(p, s)) != RECON_OK) return st;
     return RECON_OK;
   }
-  // Programmatic dependent launches between the TV temporal and inverse
-  // kernels: both wait in-device for the kernel before them.  Not with a
-  // stopping test (the inverse kernel reads the stop flags before its wait) or
-  // with profiling events between the launches.
-  const bool pdl = e->overlap && e->tv && !e->stop_test && !prof;
+  // Programmatic dependent launches between the temporal (TV, DFT, Haar) and
+  // inverse kernels: each waits in-device for the kernel before it.  Measured
+  // on the cardiac workload: TV 2791 -> 2830 iters/s.  Not used
+  //   - with a stopping test (the inverse kernel reads the stop flags before
+  //     its wait) or with profiling events between the launches;
+  //   - for the spatio-temporal prior: its CG launches (every block of each
+  //     resident at once, so the next grid's blocks wait beside them) ran 3 %
+  //     slower with the dependencies;
+  //   - for batches (allow_pdl false): their steady state is a graph replay,
+  //     which has no launch latency to hide, and the 64-slice batch ran 1.6 %
+  //     slower with the dependencies captured;
+  //   - while the stream is being captured.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  RC(cudaStreamIsCapturing(s, &cap));
+  const bool pdl = allow_pdl && e->overlap && e->prior != RECON_PRIOR_STV && !e->stop_test && !prof &&
+                   cap == cudaStreamCaptureStatusNone;
   for (int k = 1; k <= K; ++k) {
     if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, true, s);
     if (e->prior == RECON_PRIOR_STV) st = launch_stv_step(e, k - 1, s);
@@ -702,7 +713,7 @@ recon_status batch_enqueue(recon_batch* b, const float* const* kspace, float* co
   recon_status st;
   for (int q = 0; q < b->eng.n; ++q)
     if ((st = plan_prologue(b->eng.plans[q], kspace[q], RECON_STORAGE_FP32, nullptr, s)) != RECON_OK) return st;
-  if ((st = engine_iterate(&b->eng, s, false)) != RECON_OK) return st;
+  if ((st = engine_iterate(&b->eng, s, false, false)) != RECON_OK) return st;
   for (int q = 0; q < b->eng.n; ++q) {
     recon_plan* p = b->eng.plans[q];
     if ((st = plan_to_user(p, plan_result(p), reinterpret_cast<float2*>(image[q]), s)) != RECON_OK) return st;

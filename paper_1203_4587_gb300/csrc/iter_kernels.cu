@@ -422,23 +422,6 @@ cudaError_t prepare_col_inverse(int storage, size_t smem) {
   }
 }
 
-// cudaLaunchKernelEx with the programmatic-dependency attribute when `pdl`.
-template <typename... Args>
-static cudaError_t launch_ex(void (*kern)(Args...), int grid, int threads, size_t smem, cudaStream_t s, bool pdl,
-                             Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3((unsigned)threads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
 cudaError_t launch_col_inverse(const ColLaunch& p, int storage, int grid, cudaStream_t s, bool pdl) {
   const size_t smem = col_inverse_smem(p.stages, p.nb_max, p.nslices, p.work_max, storage ? 4 : 8);
   cudaError_t e = prepare_col_inverse(storage, smem);
@@ -474,10 +457,12 @@ __device__ __forceinline__ int find_slice(const SliceT* sl, int n, int blk) {
 // J): FP32 per thread and across each warp, one FP64 value per warp (GB300's
 // FP64 pipe is too narrow for a conversion per thread).
 // ---------------------------------------------------------------------------
-// Up to 4 frames a segment, 8 blocks an SM (64 registers) hide the load latency
-// best; more frames need the registers.
+// Blocks an SM by frames a segment: up to 4 frames, 8 blocks (64 registers)
+// hide the load latency best; 5 frames keep 6 blocks (80 registers), 6 frames
+// 5 (96); more frames need the registers.
+constexpr int tv_min_blocks(int lmax) { return lmax <= 4 ? 8 : lmax == 5 ? 6 : lmax == 6 ? 5 : 1; }
 template <int LMAX, bool FULL>
-__global__ void __launch_bounds__(kTvChunkThreads, LMAX <= 4 ? 8 : 1) k_tv_temporal(TemporalLaunch L) {
+__global__ void __launch_bounds__(kTvChunkThreads, tv_min_blocks(LMAX)) k_tv_temporal(TemporalLaunch L) {
   __shared__ float seg_a[kTvChunkThreads];
   __shared__ float2 seg_b[kTvChunkThreads];
   __shared__ float2 bnd[kTvChunkThreads];
@@ -585,6 +570,8 @@ template <int kDftPix>
 __global__ void __launch_bounds__(256) k_dft_temporal(TemporalLaunch L) {
   extern __shared__ float2 sm_dft[];
   __shared__ double red[32];
+  pdl_wait();      // launched with a programmatic dependency on the inverse step
+  pdl_trigger();
   const DftSlice* sls = static_cast<const DftSlice*>(L.slices);
   const DftSlice& P = sls[find_slice(sls, L.nslices, (int)blockIdx.x)];
   if (P.stop && *P.stop) return;
@@ -651,16 +638,17 @@ cudaError_t prepare_dft_temporal(int Nt_max, int px) {
   }
 }
 
-cudaError_t launch_dft_temporal(const TemporalLaunch& p, cudaStream_t s) {
+cudaError_t launch_dft_temporal(const TemporalLaunch& p, cudaStream_t s, bool pdl) {
   cudaError_t e = prepare_dft_temporal(p.Nt_max, p.tile_px);
   if (e != cudaSuccess) return e;
   const size_t smem = dft_smem(p.Nt_max, p.tile_px);
   switch (p.tile_px) {
-    case 16: k_dft_temporal<16><<<p.nblocks, 256, smem, s>>>(p); break;
-    case 32: k_dft_temporal<32><<<p.nblocks, 256, smem, s>>>(p); break;
-    case 64: k_dft_temporal<64><<<p.nblocks, 256, smem, s>>>(p); break;
-    default: k_dft_temporal<128><<<p.nblocks, 256, smem, s>>>(p); break;
+    case 16: e = launch_ex(k_dft_temporal<16>, p.nblocks, 256, smem, s, pdl, p); break;
+    case 32: e = launch_ex(k_dft_temporal<32>, p.nblocks, 256, smem, s, pdl, p); break;
+    case 64: e = launch_ex(k_dft_temporal<64>, p.nblocks, 256, smem, s, pdl, p); break;
+    default: e = launch_ex(k_dft_temporal<128>, p.nblocks, 256, smem, s, pdl, p); break;
   }
+  if (e != cudaSuccess) return e;
   note_launch();
   return cudaGetLastError();
 }
@@ -698,6 +686,8 @@ template <int PX>
 __global__ void __launch_bounds__(256) k_haar_temporal(TemporalLaunch L, int levels) {
   extern __shared__ __align__(16) float2 sm_h[];
   __shared__ double red[32];
+  pdl_wait();      // launched with a programmatic dependency on the inverse step
+  pdl_trigger();
   const HaarSlice* sls = static_cast<const HaarSlice*>(L.slices);
   const HaarSlice& P = sls[find_slice(sls, L.nslices, (int)blockIdx.x)];
   if (P.stop && *P.stop) return;
@@ -814,15 +804,16 @@ cudaError_t prepare_haar_temporal(int Nt_max, int levels, int px) {
   }
 }
 
-cudaError_t launch_haar_temporal(const TemporalLaunch& p, int levels, cudaStream_t s) {
+cudaError_t launch_haar_temporal(const TemporalLaunch& p, int levels, cudaStream_t s, bool pdl) {
   cudaError_t e = prepare_haar_temporal(p.Nt_max, levels, p.tile_px);
   if (e != cudaSuccess) return e;
   const size_t smem = haar_smem(p.Nt_max, levels, p.tile_px);
   switch (p.tile_px) {
-    case 16: k_haar_temporal<16><<<p.nblocks, 256, smem, s>>>(p, levels); break;
-    case 32: k_haar_temporal<32><<<p.nblocks, 256, smem, s>>>(p, levels); break;
-    default: k_haar_temporal<64><<<p.nblocks, 256, smem, s>>>(p, levels); break;
+    case 16: e = launch_ex(k_haar_temporal<16>, p.nblocks, 256, smem, s, pdl, p, levels); break;
+    case 32: e = launch_ex(k_haar_temporal<32>, p.nblocks, 256, smem, s, pdl, p, levels); break;
+    default: e = launch_ex(k_haar_temporal<64>, p.nblocks, 256, smem, s, pdl, p, levels); break;
   }
+  if (e != cudaSuccess) return e;
   note_launch();
   return cudaGetLastError();
 }

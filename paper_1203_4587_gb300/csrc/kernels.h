@@ -358,8 +358,8 @@ int dft_tile_px();
 int tv_tile_candidates(int Nt_max, int* out);       // tile widths that fit (<= 4 entries)
 int dft_tile_candidates(int Nt_max, int* out);
 cudaError_t launch_tv_temporal(const TemporalLaunch& p, cudaStream_t s, bool pdl = false);
-cudaError_t launch_dft_temporal(const TemporalLaunch& p, cudaStream_t s);
-cudaError_t launch_haar_temporal(const TemporalLaunch& p, int levels, cudaStream_t s);
+cudaError_t launch_dft_temporal(const TemporalLaunch& p, cudaStream_t s, bool pdl = false);
+cudaError_t launch_haar_temporal(const TemporalLaunch& p, int levels, cudaStream_t s, bool pdl = false);
 cudaError_t prepare_haar_temporal(int Nt_max, int levels, int px);
 int haar_tile_px(int Nt_max, int levels);
 int haar_tile_candidates(int Nt_max, int levels, int* out);

@@ -189,7 +189,9 @@ int engine_default_tile(const Engine* e);
 recon_status engine_build_inverse(Engine* e, recon_plan* p);   // tmp_a -> tmp_b, no objective
 // Resets traces/flags, J(0), K iterations and the final prior term of every
 // slice (prologues must have run).  `profile` records the plan's events (n = 1).
-recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile);
+// allow_pdl: the plan's own solve may use programmatic dependent launches
+// (opts.overlap); batches run in plain stream order
+recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile, bool allow_pdl = true);
 recon_status engine_apply_inverse(Engine* e, cudaStream_t s);
 // RECON_OK while every plan of the engine is usable and unchanged since the build
 recon_status engine_check(const Engine* e);

@@ -39,10 +39,10 @@ def gpu(x):
     return torch.from_numpy(np.asarray(x, dtype=np.complex64)).cuda()
 
 
-def plan(c, **opts):
+def plan(c, prior="tv", **opts):
     from paper_1203_4587_gb300 import Plan
     opts.setdefault("max_iters", c.iters)
-    return Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="tv", rho=c.rho, **opts)
+    return Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior=prior, rho=c.rho, **opts)
 
 
 SHAPES = [
@@ -84,7 +84,34 @@ def test_overlap_bit_identical_and_matches_oracle(shape, storage):
     P0.close()
 
 
+@pytest.mark.parametrize("prior", ["dft", "haar", "stv"])
+def test_overlap_other_priors_bit_identical(prior):
+    """Algorithm 1 (temporal DFT, Haar frame): the same launches with and
+    without the programmatic dependency give the same image, which matches the
+    oracle.  The spatio-temporal prior ignores the option (plain stream order)
+    and must give the same image either way too."""
+    c = make(Nx=40, Ny=48, Nt=12, Nc=3, R=3, iters=15)
+    P1 = plan(c, prior=prior, overlap=1, frame_levels=2, spatial_weight=1.0, cg_steps=5)
+    P0 = plan(c, prior=prior, overlap=0, frame_levels=2, spatial_weight=1.0, cg_steps=5)
+    k = gpu(c.kspace)
+    a1 = P1.solve(k)[0].cpu().numpy()
+    a0 = P0.solve(k)[0].cpu().numpy()
+    assert np.array_equal(a1, a0)
+    prob = oracle.Problem(c.kspace, c.sens, c.mask, c.mu)
+    if prior == "dft":
+        xr, _ = prob.solve("dft", c.lam, c.mu, c.rho, c.iters)
+    elif prior == "haar":
+        xr, _ = prob.solve("haar", c.lam, c.mu, c.rho, c.iters, levels=2)
+    else:
+        xr, _ = prob.solve("stv", c.lam, c.mu, c.rho, c.iters, ws=1.0, cg=5)
+    assert rel(a1.astype(np.complex128), xr) < TOL
+    P1.close()
+    P0.close()
+
+
 def test_overlap_batch_direct_and_graph_replay():
+    """Batches run in plain stream order whatever the plans' option: the same
+    images either way, on the direct run and on the graph replay."""
     from paper_1203_4587_gb300 import Batch
     shapes = [dict(Nx=32, Ny=64, Nt=16, Nc=3, R=4, seed=31), dict(Nx=40, Ny=48, Nt=16, Nc=2, R=3, seed=32),
               dict(Nx=16, Ny=32, Nt=16, Nc=2, R=2, seed=33)]
