@@ -491,7 +491,25 @@ __global__ void __launch_bounds__(kTvChunkThreads, tv_min_blocks(LMAX)) k_tv_tem
   io.base = (size_t)pix0;
   io.nvalid = (int)min((long long)kTvChunkPx, P.npix - pix0);
   io.write = P.write_state != 0;
-  float tvf = tv_chunk<LMAX, FULL>(io, (int)threadIdx.x, seg_a, seg_b, bnd, BlockBar());
+  float tvf;
+  if (FULL) {
+    tvf = tv_chunk<LMAX, true>(io, (int)threadIdx.x, seg_a, seg_b, bnd, BlockBar());
+  } else {
+    // a launch over slices of several Nt (a batch): a whole chunk of a slice
+    // with Nt = 8 l takes the whole-chunk code for its own l (the same
+    // arithmetic), the rest the general code
+    const int l = (P.Nt % kTvSeg == 0) ? P.Nt / kTvSeg : 0;
+    const bool whole = io.nvalid == kTvChunkPx && io.d1 != nullptr && io.write;
+    const int tid = (int)threadIdx.x;
+    if (whole && l == LMAX && LMAX <= kTvFullLMax) tvf = tv_chunk<LMAX, true>(io, tid, seg_a, seg_b, bnd, BlockBar());
+    else if (whole && l == LMAX - 1 && LMAX - 1 >= 1 && LMAX <= kTvFullLMax)
+      tvf = tv_chunk<(LMAX > 1 ? LMAX - 1 : 1), true>(io, tid, seg_a, seg_b, bnd, BlockBar());
+    else if (whole && l == LMAX - 2 && LMAX - 2 >= 1 && LMAX <= kTvFullLMax)
+      tvf = tv_chunk<(LMAX > 2 ? LMAX - 2 : 1), true>(io, tid, seg_a, seg_b, bnd, BlockBar());
+    else if (whole && l == LMAX - 3 && LMAX - 3 >= 1 && LMAX <= kTvFullLMax)
+      tvf = tv_chunk<(LMAX > 3 ? LMAX - 3 : 1), true>(io, tid, seg_a, seg_b, bnd, BlockBar());
+    else tvf = tv_chunk<LMAX, false>(io, tid, seg_a, seg_b, bnd, BlockBar());
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tvf += __shfl_down_sync(0xffffffffu, tvf, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)tvf;
