@@ -156,13 +156,14 @@ typedef struct {
   int stopped;      /* 1 when the tolerance test ended the run */
   double primal_res; /* ADMM residuals of the last iteration of a solve of all K iterations
                         (Boyd et al. 2011, Sec. 3.3, the paper's penalty weights).
-                        RECON_PRIOR_TV, splits v = D_t m (mu1) and m = x (mu2), stacked:
-                        sqrt(||v - D_t m||^2 + ||m - x||^2).
-                        RECON_PRIOR_DFT and RECON_PRIOR_HAAR, split v = w (mu): ||w - v||
-                        (w the frame coefficients) */
-  double dual_res;  /* TV: sqrt(mu1^2 ||D_t (m_K - m_{K-1})||^2 + mu2^2 ||m_K - m_{K-1}||^2);
-                        DFT, Haar: mu ||w_K - w_{K-1}||.  Both NaN for RECON_PRIOR_STV and
-                        after an early stop.  Summed in FP64. */
+                        RECON_PRIOR_TV and RECON_PRIOR_STV (R = D_t, or the stacked
+                        spatio-temporal R), splits v = R m (mu1) and m = x (mu2):
+                        sqrt(||v - R m||^2 + ||m - x||^2); a volume's slices all report the
+                        volume's.  RECON_PRIOR_DFT and RECON_PRIOR_HAAR, split v = w (mu):
+                        ||w - v|| (w the frame coefficients) */
+  double dual_res;  /* TV, STV: sqrt(mu1^2 ||R (m_K - m_{K-1})||^2 + mu2^2 ||m_K - m_{K-1}||^2);
+                        DFT, Haar: mu ||w_K - w_{K-1}||.  Both NaN after an early stop.
+                        Summed in FP64. */
 } recon_info;
 
 /* Fills `opts` with the defaults listed above.  NULL-safe. */

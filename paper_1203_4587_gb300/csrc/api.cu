@@ -354,12 +354,12 @@ recon_status plan_fill_info(recon_plan* p, recon_info* info, cudaStream_t s) {
     info->J = J[iters];
     info->J0 = J[0];
     info->delta = (iters >= 1) ? (J[iters - 1] - J[iters]) / J[iters] : NAN;
-    // ADMM residuals (TV, DFT or Haar frame, a solve that ran all K iterations)
+    // ADMM residuals (a solve that ran all K iterations)
     info->primal_res = info->dual_res = NAN;
-    if (p->prior != RECON_PRIOR_STV && K >= 1 && !fl[FLAG_STOP]) {
+    if (K >= 1 && !fl[FLAG_STOP]) {
       double a[4];
       RC(cudaMemcpy(a, p->res_acc, sizeof(a), cudaMemcpyDeviceToHost));
-      if (p->prior == RECON_PRIOR_TV) {
+      if (p->prior == RECON_PRIOR_TV || p->prior == RECON_PRIOR_STV) {   // Algorithm 2
         const double mu2 = p->mu, mu1 = p->mu / p->opts.rho;
         info->primal_res = std::sqrt(a[0] + a[1]);
         info->dual_res = std::sqrt(mu1 * mu1 * a[3] + mu2 * mu2 * a[2]);
@@ -492,8 +492,9 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
     }
   }
   if (prior == RECON_PRIOR_STV) PC(p->alloc((void**)&p->cgd, nimg * sizeof(float2)));
-  if (prior == RECON_PRIOR_DFT || prior == RECON_PRIOR_HAAR)   // xhat_{K-1} for the residuals
+  if (prior == RECON_PRIOR_DFT || prior == RECON_PRIOR_HAAR || prior == RECON_PRIOR_STV)   // for the residuals
     PC(p->alloc((void**)&p->res_prev, nimg * sizeof(float2)));
+  if (prior == RECON_PRIOR_STV) PC(p->alloc((void**)&p->res_d1, 4 * nimg * sizeof(float2)));
   PC(p->alloc((void**)&p->x, nimg * sizeof(float2)));
   if (prior != RECON_PRIOR_TV) PC(p->alloc((void**)&p->r, nimg * sizeof(float2)));
   PC(p->alloc((void**)&p->tmp_a, nimg * sizeof(float2)));

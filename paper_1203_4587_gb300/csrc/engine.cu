@@ -180,6 +180,15 @@ StvSlice stv_desc(recon_plan* p, int k, int K, double* red) {
   d.stop = p->flags + FLAG_STOP;
   d.red = red + (size_t)(std::min(k, std::max(K, 1)) - 1) * (2 * d.cg + 1);
   d.prior_acc = p->trace_prior + (k - 1);
+  // residuals: iteration K-1 keeps d1, iteration K sums its change; the final
+  // set reads m_{K-1}
+  d.res_acc = p->res_acc;
+  if (k == K - 1) d.d1_keep = p->res_d1;
+  if (k == K) {
+    d.res_last = 1;
+    d.d1_ref = K >= 2 ? p->res_d1 : nullptr;
+  }
+  if (k == K + 1) d.m_prev = p->res_prev;
   return d;
 }
 
@@ -438,6 +447,7 @@ recon_status engine_set_tile(Engine* e, int px) {
         d.nblk = (e->plans[q]->Nt * e->plans[q]->Nx + px - 1) / px;
         d.part = e->d_stv_part;
         if (e->volume) {   // neighbours at q -1 / q + 1, one sum over every slice
+          d.res_acc = e->plans[0]->res_acc;   // the residuals of the volume
           d.wz = e->wz;
           d.zprev = q > 0;
           d.znext = q + 1 < n;
@@ -584,6 +594,7 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile, bool allow_
   recon_plan* p0 = e->plans[0];
   const bool prof = profile && e->n == 1;
   for (recon_plan* p : e->plans) {
+    RC(cudaMemsetAsync(p->res_acc, 0, 4 * sizeof(double), s));
     RC(cudaMemsetAsync(p->flags, 0, FLAG_COUNT * sizeof(int), s));
     RC(cudaMemsetAsync(p->trace_fid, 0, nt * sizeof(double), s));
     RC(cudaMemsetAsync(p->trace_prior, 0, nt * sizeof(double), s));
@@ -655,6 +666,9 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile, bool allow_
   const bool pdl = allow_pdl && e->overlap && e->prior != RECON_PRIOR_STV && !e->stop_test && !prof &&
                    cap == cudaStreamCaptureStatusNone;
   for (int k = 1; k <= K; ++k) {
+    if (k == K && e->prior == RECON_PRIOR_STV)   // m_{K-1}, before the last m-update
+      for (recon_plan* p : e->plans)
+        RC(cudaMemcpyAsync(p->res_prev, p->s0[0], p->nimg() * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     if (prof) p0->mark(p0->ev_tmp, p0->n_tmp, true, s);
     if (e->prior == RECON_PRIOR_STV) st = launch_stv_step(e, k - 1, s);
     else st = launch_tmp_set(e, k - 1, s, pdl);
@@ -675,6 +689,19 @@ recon_status engine_iterate(Engine* e, cudaStream_t s, bool profile, bool allow_
     if ((st = launch_tmp_set(e, K, s, pdl)) != RECON_OK) return st;
     // with a fixed iteration count J(0) .. J(K) are formed here, in one launch
     RC(launch_finalize(e->d_fin, e->n, e->stop_test ? K : 0, K, s));
+  }
+  if (e->prior == RECON_PRIOR_STV) {
+    if (K >= 1) {   // the sums of the final set (the last iteration's d1 change is already in)
+      StvLaunch S{};
+      S.slices = static_cast<StvSlice*>(e->d_tmp) + (size_t)K * e->n;
+      S.nslices = e->n;
+      S.nblocks = e->tmp_blocks;
+      RC(launch_stv_residuals(S, s));
+      if (e->volume)   // every slice reports the volume's residuals
+        for (int q = 1; q < e->n; ++q)
+          RC(cudaMemcpyAsync(e->plans[q]->res_acc, p0->res_acc, 4 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    return RECON_OK;
   }
   for (recon_plan* p : e->plans)
     if ((st = launch_residuals(p, s)) != RECON_OK) return st;

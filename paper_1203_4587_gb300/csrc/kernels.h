@@ -197,6 +197,13 @@ struct StvSlice {
   const int* stop;
   int tile0;                 // first block of this slice in the launch
   int nblk;                  // blocks of this slice (kStvRows image columns each)
+  // ADMM residuals of a solve of K iterations (k_stv_finish of iterations
+  // K-1 and K, k_stv_residuals after the loop):
+  float2* d1_keep;           // iteration K-1: d1 (every component) stored here
+  const float2* d1_ref;      // iteration K: d1_{K-1} (null: d1_0 = 0) ...
+  int res_last;              // ... and res_acc[1] += ||d1_{K-1} - d1_K||^2 when 1
+  double* res_acc;           // [4] sums (the first slice's for a volume)
+  const float2* m_prev;      // final set: m_{K-1}, copied before the last m-update
 };
 
 struct StvLaunch {
@@ -374,6 +381,9 @@ cudaError_t launch_stv_rhs(const StvLaunch& L, cudaStream_t s);      // r = rhs 
 cudaError_t launch_stv_dir(const StvLaunch& L, cudaStream_t s);      // p_j, q = M p_j, <p_j, q>
 cudaError_t launch_stv_update(const StvLaunch& L, cudaStream_t s);   // m, r, gamma_{j+1}
 cudaError_t launch_stv_finish(const StvLaunch& L, cudaStream_t s);   // d1 = e + R m, p, next e
+// with the final descriptor set: res_acc[0] += ||m_K - x_K||^2, [2] += ||dm||^2,
+// [3] += ||R dm||^2 (dm = m_K - m_{K-1})
+cudaError_t launch_stv_residuals(const StvLaunch& L, cudaStream_t s);
 // per slice, for k = k0 .. k1: J(k) = fid[k] + (yy ? *yy : 0) + lambda prior[k]; Delta(k); stop flag.
 cudaError_t launch_finalize(const FinSlice* fins, int nslices, int k0, int k1, cudaStream_t s);
 

@@ -113,7 +113,9 @@ struct recon_plan {
   double* trace_J = nullptr;
   double* yy = nullptr;                // ||y||^2 over the sampled entries (FP64)
   double* res_acc = nullptr;           // [4] sums of the ADMM residuals (TV, DFT, Haar; residual.cu)
-  float2* res_prev = nullptr;          // DFT, Haar: xhat_{K-1}, copied before the last inverse step
+  float2* res_prev = nullptr;          // DFT, Haar: xhat_{K-1}, copied before the last inverse step;
+                                       // spatio-temporal: m_{K-1}, copied before the last m-update
+  float2* res_d1 = nullptr;            // spatio-temporal: d1_{K-1} (4 components), kept by that iteration
   int* flags = nullptr;
   recon::FftPlanDev fx{}, fy{}, ft{};
   recon::FftPlanDf fxdf{}, fydf{};

@@ -169,8 +169,11 @@ __device__ __forceinline__ float rx_l1(const StvSlice& P, const StvSlice* Pn, co
 }
 
 // e = d1 - S(R m + d1) into the padded components, with d1 = e + R m (the
-// previous e, from k_stv_finish) or d1 = 0 (first = true, from k_stv_init)
-__device__ __forceinline__ void threshold(const StvSlice& P, const StvSlice* Pn, const Pos& q, bool first) {
+// previous e, from k_stv_finish) or d1 = 0 (first = true, from k_stv_init).
+// With the residual fields set (iterations K-1 and K), d1 is also kept, or
+// its change ||d1_{K-1} - d1_K||^2 added to *dd1.
+__device__ __forceinline__ void threshold(const StvSlice& P, const StvSlice* Pn, const Pos& q, bool first,
+                                          KahanSum* dd1 = nullptr) {
   float2 rm[4];
   diffs(P, P.m, Pn ? Pn->m : nullptr, q, rm);
   const int nc = (P.zprev || P.znext) ? 4 : 3;
@@ -179,6 +182,11 @@ __device__ __forceinline__ void threshold(const StvSlice& P, const StvSlice* Pn,
     if (k >= nc) break;
     const long long o = (long long)k * P.n + q.idx;
     const float2 dd = first ? make_float2(0.f, 0.f) : c_add(P.e[o], rm[k]);
+    if (P.d1_keep) P.d1_keep[o] = dd;
+    if (dd1) {
+      const float2 df = c_sub(P.d1_ref ? P.d1_ref[o] : make_float2(0.f, 0.f), dd);
+      dd1->add(fmaf(df.x, df.x, df.y * df.y));
+    }
     P.e[o] = c_sub(dd, c_soft(c_add(rm[k], dd), P.tau1));
   }
 }
@@ -344,18 +352,71 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_update(StvLaunch L) {
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_finish(StvLaunch L) {
+  __shared__ double red[32];
   const int si = slice_of(L);
   const StvSlice& P = L.slices[si];
   if (P.stop && *P.stop) return;
   const StvSlice* Pn = above(L, si);
   const Blk b = blk_of(P);
+  KahanSum dd1;
 #pragma unroll 4
   for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
     const Pos q = pos_of(P, b, e);
     const int idx = q.idx;
     // e (the previous threshold's d1 - v) is read and replaced element by element
-    threshold(P, Pn, q, false);
+    threshold(P, Pn, q, false, P.res_last ? &dd1 : nullptr);
     P.p[idx] = c_add(P.m[idx], c_sub(P.p[idx], P.x[idx]));
+  }
+  if (P.res_last) {   // the last iteration: v_K - R m_K = d1_{K-1} - d1_K
+    const double sdd = group_sum((double)dd1.s, red, threadIdx.x, kStvThreads, BlockBar());
+    if (threadIdx.x == 0) atomicAdd(P.res_acc + 1, sdd);
+  }
+}
+
+// R (m_K - m_{K-1}) at q from the two fields (and the slice above's, in a volume)
+__device__ __forceinline__ void diffs_dm(const StvSlice& P, const StvSlice* Pn, const Pos& q, float2 (&d)[4]) {
+  const float2* m = P.m;
+  const float2* mp = P.m_prev;
+  auto dm = [m, mp](int o) { return c_sub(m[o], mp[o]); };
+  const float2 c = dm(q.idx);
+  const float2 z = make_float2(0.f, 0.f);
+  d[0] = (q.t + 1 < P.Nt) ? c_sub(dm(q.idx + P.Nx * P.Ny), c) : z;
+  d[1] = (q.i + 1 < P.Nx) ? c_scale(c_sub(dm(q.idx + P.Ny), c), P.ws) : z;
+  d[2] = (q.j + 1 < P.Ny) ? c_scale(c_sub(dm(q.idx + 1), c), P.ws) : z;
+  d[3] = Pn ? c_scale(c_sub(c_sub(Pn->m[q.idx], Pn->m_prev[q.idx]), c), P.wz) : z;
+}
+
+// ADMM residual sums after the loop (final descriptor set): res_acc[0] +=
+// ||m_K - x_K||^2, [2] += ||m_K - m_{K-1}||^2, [3] += ||R (m_K - m_{K-1})||^2
+// ([1] came from k_stv_finish of the last iteration).
+__global__ void __launch_bounds__(kStvThreads) k_stv_residuals(StvLaunch L) {
+  __shared__ double red[32];
+  const int si = slice_of(L);
+  const StvSlice& P = L.slices[si];
+  const StvSlice* Pn = above(L, si);
+  const Blk b = blk_of(P);
+  KahanSum a0, a2, a3;
+#pragma unroll 2
+  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
+    const Pos q = pos_of(P, b, e);
+    const float2 mv = P.m[q.idx];
+    const float2 mx = c_sub(mv, P.x[q.idx]), dm = c_sub(mv, P.m_prev[q.idx]);
+    a0.add(fmaf(mx.x, mx.x, mx.y * mx.y));
+    a2.add(fmaf(dm.x, dm.x, dm.y * dm.y));
+    float2 d[4];
+    diffs_dm(P, Pn, q, d);
+    float s3 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s3 = fmaf(d[k].x, d[k].x, fmaf(d[k].y, d[k].y, s3));
+    a3.add(s3);
+  }
+  const double s0 = group_sum((double)a0.s, red, threadIdx.x, kStvThreads, BlockBar());
+  const double s2 = group_sum((double)a2.s, red, threadIdx.x, kStvThreads, BlockBar());
+  const double s3 = group_sum((double)a3.s, red, threadIdx.x, kStvThreads, BlockBar());
+  if (threadIdx.x == 0) {
+    atomicAdd(P.res_acc + 0, s0);
+    atomicAdd(P.res_acc + 2, s2);
+    atomicAdd(P.res_acc + 3, s3);
   }
 }
 
@@ -375,5 +436,6 @@ cudaError_t launch_stv_rhs(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_st
 cudaError_t launch_stv_dir(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_dir); }
 cudaError_t launch_stv_update(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_update); }
 cudaError_t launch_stv_finish(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_finish); }
+cudaError_t launch_stv_residuals(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_residuals); }
 
 }  // namespace recon

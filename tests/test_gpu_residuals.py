@@ -1,5 +1,6 @@
 """GPU parity of the ADMM residuals recon_info reports, against the FP64 oracle
-on its own iterates.
+on its own iterates (every prior: temporal TV, the spatio-temporal R and
+volumes, the DFT and the Haar frame).
 
 Algorithm 2 (temporal TV, oracle.tv_residuals): primal sqrt(||v - D_t m||^2 +
 ||m - x||^2) and dual sqrt(mu1^2 ||D_t dm||^2 + mu2^2 ||dm||^2), dm = m_K -
@@ -111,12 +112,54 @@ def test_haar_residuals_match_oracle(iters, levels):
     check_dft(info, oinfo, xr, c.mu)
 
 
+def check_stv(info, oinfo, xr, mu1):
+    _, m, d1, _ = oinfo["state"]
+    scale = np.linalg.norm(xr) + np.linalg.norm(m) + sum(np.linalg.norm(c) for c in d1)
+    for got, ref, w in ((info.primal_res, oinfo["primal_res"], 1.0), (info.dual_res, oinfo["dual_res"], mu1)):
+        assert np.isfinite(got)
+        assert abs(got - ref) <= 4e-5 * w * 4 * scale + 1e-4 * ref, (got, ref)
+
+
+@pytest.mark.parametrize("iters,ws", [(1, 1.0), (2, 0.5), (12, 1.0)])
+def test_stv_residuals_match_oracle(iters, ws):
+    """Algorithm 2 with the spatio-temporal R (oracle.stacked_residuals): the
+    finishing kernels of iterations K-1 and K keep d1 and sum its change
+    (v_K - R m_K = d1_{K-1} - d1_K), and a pass after the loop sums
+    ||m_K - x_K||^2, ||dm||^2 and ||R dm||^2 from m_{K-1} copied aside."""
+    from paper_1203_4587_gb300 import Plan
+    c = case64("tiny", Nx=24, Ny=32, Nt=5, Nc=2, seed=87)
+    P = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="stv", rho=c.rho, max_iters=iters,
+             spatial_weight=ws, cg_steps=4)
+    _, info = P.solve(gpu(c.kspace))
+    prob = oracle.Problem(c.kspace, c.sens, c.mask, c.mu)
+    xr, oinfo = prob.solve("stv", c.lam, c.mu, c.rho, iters, objective=False, ws=ws, cg=4)
+    check_stv(info, oinfo, xr, c.mu / c.rho)
+
+
+def test_volume_residuals_match_oracle():
+    """A volume of 3 slices: every slice reports the volume's residuals (sums
+    over all slices, z-differences included)."""
+    from paper_1203_4587_gb300 import Plan, Volume
+    cases = [case64("tiny", Nx=24, Ny=32, Nt=4, Nc=2, R=2, seed=70 + z) for z in range(3)]
+    iters, ws, wz, cg = 8, 0.8, 0.6, 4
+    plans = [Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="stv", rho=c.rho, max_iters=iters,
+                  spatial_weight=ws, cg_steps=cg) for c in cases]
+    V = Volume(plans, wz)
+    V.solve([gpu(c.kspace) for c in cases])
+    probs = [oracle.Problem(c.kspace, c.sens, c.mask, c.mu) for c in cases]
+    c0 = cases[0]
+    xr, oinfo = oracle.admm_analysis_stv_volume([p.b for p in probs], [p.inv for p in probs], c0.lam, c0.mu, c0.rho,
+                                                iters, ws=ws, wz=wz, cg=cg)
+    for info in V.info():
+        check_stv(info, oinfo, xr, c0.mu / c0.rho)
+
+
 def test_residuals_nan_where_not_defined():
     from paper_1203_4587_gb300 import Plan
     c = case64("tiny", Nx=24, Ny=32, Nt=4, Nc=2, seed=83)
-    P = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="stv", max_iters=5)
-    _, info = P.solve(gpu(c.kspace))
-    assert np.isnan(info.primal_res) and np.isnan(info.dual_res)
     Q = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="tv", rho=c.rho, max_iters=200, tol=1e-2)
     _, info = Q.solve(gpu(c.kspace))
+    assert info.stopped == 1 and np.isnan(info.primal_res) and np.isnan(info.dual_res)
+    S = Plan(c.mask.astype(np.uint8), gpu(c.sens), c.lam, c.mu, prior="stv", rho=c.rho, max_iters=200, tol=1e-2)
+    _, info = S.solve(gpu(c.kspace))
     assert info.stopped == 1 and np.isnan(info.primal_res) and np.isnan(info.dual_res)
