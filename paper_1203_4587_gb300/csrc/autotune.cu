@@ -127,7 +127,10 @@ recon_status tune_engine(Engine* e, cudaStream_t s, recon_tuning* t) {
     recon_status st = engine_set_tile(e, cand[i]);
     if (st != RECON_OK) return st;
     float ms = 0.f;
-    if ((st = time_ms([&] { return launch_tmp_set(e, 0, s); }, s, &ms)) != RECON_OK) return st;
+    // the spatio-temporal prior times its whole step (r, the CG launches, finish)
+    if ((st = time_ms([&] { return e->prior == RECON_PRIOR_STV ? launch_stv_step(e, 0, s) : launch_tmp_set(e, 0, s); },
+                      s, &ms)) != RECON_OK)
+      return st;
     if (ms < best) { best = ms; best_px = cand[i]; }
   }
   recon_status st = engine_set_tile(e, best_px);

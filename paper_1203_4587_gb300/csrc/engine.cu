@@ -357,7 +357,7 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
     RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_stv_count), (size_t)n * sizeof(unsigned)));
     RC(cudaMemset(e->d_stv_count, 0, (size_t)n * sizeof(unsigned)));
     int blocks = 0;
-    for (int q = 0; q < n; ++q) blocks += (plans[q]->Nt * plans[q]->Nx + kStvRows - 1) / kStvRows;
+    for (int q = 0; q < n; ++q) blocks += (plans[q]->Nt * plans[q]->Nx + kStvRowsMin - 1) / kStvRowsMin;
     RC(e->arena.alloc(reinterpret_cast<void**>(&e->d_stv_part), (size_t)std::max(blocks, 1) * sizeof(double)));
   }
   const int K = e->K;
@@ -406,9 +406,10 @@ recon_status engine_build(Engine* e, recon_plan* const* plans, int n) {
 }
 
 int engine_tile_candidates(const Engine* e, int* out) {
-  if (e->prior == RECON_PRIOR_STV) {   // fixed image columns per block
-    out[0] = kStvRows;
-    return 1;
+  if (e->prior == RECON_PRIOR_STV) {   // image columns per block
+    int nc = 0;
+    for (int r : kStvRowCands) out[nc++] = r;
+    return nc;
   }
   if (e->tv) return tv_tile_candidates(e->Nt_max, out);
   if (e->prior == RECON_PRIOR_HAAR) return haar_tile_candidates(e->Nt_max, e->levels, out);
@@ -445,6 +446,7 @@ recon_status engine_set_tile(Engine* e, int px) {
         StvSlice d = stv_desc(e->plans[q], k, K, e->stv_red[q]);
         d.tile0 = tile0[q];
         d.nblk = (e->plans[q]->Nt * e->plans[q]->Nx + px - 1) / px;
+        d.rows = px;
         d.part = e->d_stv_part;
         if (e->volume) {   // neighbours at q -1 / q + 1, one sum over every slice
           d.res_acc = e->plans[0]->res_acc;   // the residuals of the volume

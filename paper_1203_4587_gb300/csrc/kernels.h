@@ -196,7 +196,8 @@ struct StvSlice {
   double* prior_acc;         // += ||R x||_1 of the incoming x
   const int* stop;
   int tile0;                 // first block of this slice in the launch
-  int nblk;                  // blocks of this slice (kStvRows image columns each)
+  int nblk;                  // blocks of this slice (rows image columns each)
+  int rows;                  // image columns (t, i) per block, at most kStvRows
   // ADMM residuals of a solve of K iterations (k_stv_finish of iterations
   // K-1 and K, k_stv_residuals after the loop):
   float2* d1_keep;           // iteration K-1: d1 (every component) stored here
@@ -371,10 +372,13 @@ cudaError_t prepare_haar_temporal(int Nt_max, int levels, int px);
 int haar_tile_px(int Nt_max, int levels);
 int haar_tile_candidates(int Nt_max, int levels, int* out);
 cudaError_t launch_objective(const ObjParams& p, cudaStream_t s);
-// spatio-temporal Algorithm 2 (stv_kernels.cu): a block walks kStvRows image
-// columns (t, i) of Ny elements
+// spatio-temporal Algorithm 2 (stv_kernels.cu): a block walks StvSlice::rows
+// image columns (t, i) of Ny elements, one of kStvRowCands (picked by the
+// autotuner; kStvRows by default)
 constexpr int kStvThreads = 256;
 constexpr int kStvRows = 16;
+constexpr int kStvRowsMin = 4;
+constexpr int kStvRowCands[] = {4, 8, 16};
 cudaError_t launch_stv_init(const StvLaunch& L, cudaStream_t s);     // e = -S(R m) (d1 = 0)
 cudaError_t launch_stv_prior(const StvLaunch& L, cudaStream_t s);    // ||R x||_1
 cudaError_t launch_stv_rhs(const StvLaunch& L, cudaStream_t s);      // r = rhs - M m, gamma_0, ||R x||_1

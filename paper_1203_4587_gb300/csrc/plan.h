@@ -184,6 +184,8 @@ recon_status finish_col_shape(Engine* e, recon_plan* const* plans, int n, int st
 recon_status launch_col_set(Engine* e, int set, cudaStream_t s, bool pdl = false);
 recon_status launch_tmp_set(Engine* e, int set, cudaStream_t s, bool pdl = false);
 cudaError_t plan_create_events(recon_plan* p);   // the profiling events, once
+// spatio-temporal prior: the step of iteration set+1 (r, CG, finish)
+recon_status launch_stv_step(Engine* e, int set, cudaStream_t s);
 recon_status engine_build(Engine* e, recon_plan* const* plans, int n);
 recon_status engine_set_tile(Engine* e, int px);   // temporal tile width (rebuilds its descriptor sets)
 int engine_tile_candidates(const Engine* e, int* out);   // temporal tile widths that fit

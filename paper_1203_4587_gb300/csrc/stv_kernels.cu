@@ -22,7 +22,7 @@
 //
 // Fields are [Nt][Nx][Ny]; a "row" is one image column (t, i) of Ny
 // elements, with neighbours at +-1 (j), +-Ny (i) and +-Nx Ny (t).  A block
-// walks kStvRows consecutive rows; (t, i) of its first row is found once and
+// walks P.rows (<= kStvRows) consecutive rows; (t, i) of its first row is found once and
 // stepped, and an element's row within the block comes from an FP32
 // reciprocal that is exact at these sizes (see row_of).  e keeps its three
 // components padded to the grid, with zeros where a difference leaves it
@@ -36,7 +36,7 @@
 // A volume of one slice runs exactly the 2D arithmetic.
 //
 // CG inner products are sums over the whole slice (over the whole volume).  A thread adds its
-// elements (kStvRows * Ny / 256 of them, at most 64) in FP32 with Kahan's
+// elements (rows * Ny / 256 of them, at most 64) in FP32 with Kahan's
 // compensated summation (error about 2 eps, not n eps); the block sums
 // its threads in FP64 and writes a partial, and the last block of the slice
 // to finish (an atomic counter after a fence) adds the partials in block
@@ -59,15 +59,15 @@ struct Blk {
 
 __device__ __forceinline__ Blk blk_of(const StvSlice& P) {
   Blk b;
-  b.row0 = ((int)blockIdx.x - P.tile0) * kStvRows;
-  b.nrows = min(kStvRows, P.Nt * P.Nx - b.row0);
+  b.row0 = ((int)blockIdx.x - P.tile0) * P.rows;
+  b.nrows = min(P.rows, P.Nt * P.Nx - b.row0);
   b.t0 = b.row0 / P.Nx;
   b.i0 = b.row0 - b.t0 * P.Nx;
   b.inv_ny = 1.f / (float)P.Ny;
   return b;
 }
 
-// Row within the block of local element e < kStvRows * Ny: (e + 1/2)/Ny has
+// Row within the block of local element e < rows * Ny <= kStvRows * Ny: (e + 1/2)/Ny has
 // fractional part >= 1/(2 Ny) >= 2^-11 away from an integer, and its FP32
 // rounding error is below 2^14 * 2^-24, so the truncation is exact.
 __device__ __forceinline__ int row_of(const Blk& b, int e) {
@@ -84,7 +84,7 @@ __device__ __forceinline__ Pos pos_of(const StvSlice& P, const Blk& b, int e) {
   q.j = e - r * P.Ny;
   q.i = b.i0 + r;
   q.t = b.t0;
-  while (q.i >= P.Nx) { q.i -= P.Nx; ++q.t; }   // at most kStvRows steps
+  while (q.i >= P.Nx) { q.i -= P.Nx; ++q.t; }   // at most P.rows steps
   q.idx = (b.row0 + r) * P.Ny + q.j;
   return q;
 }
