@@ -580,6 +580,9 @@ recon_status launch_stv_step(Engine* e, int set, cudaStream_t s) {
   S.slices = static_cast<StvSlice*>(e->d_tmp) + (size_t)set * e->n;
   S.nslices = e->n;
   S.nblocks = e->tmp_blocks;
+  int ny_max = 0;
+  for (recon_plan* p : e->plans) ny_max = std::max(ny_max, p->Ny);
+  S.dir_threads = (ny_max + 31) / 32 * 32;
   RC(launch_stv_rhs(S, s));
   for (int j = 0; j < e->cg; ++j) {
     S.step = j;

@@ -212,6 +212,7 @@ struct StvLaunch {
   int nslices;
   int nblocks;
   int step;                  // CG step j of the direction / update kernels
+  int dir_threads;           // direction kernel: one thread per j, Ny_max rounded up to 32
 };
 
 // Temporal TV kernel shape (tv_chunk.cuh): chunks of kTvChunkPx pixels, the
@@ -376,6 +377,7 @@ cudaError_t launch_objective(const ObjParams& p, cudaStream_t s);
 // image columns (t, i) of Ny elements, one of kStvRowCands (picked by the
 // autotuner; kStvRows by default)
 constexpr int kStvThreads = 256;
+constexpr int kStvDirMaxThreads = 1024;   // the direction kernel's block: Ny <= 1023
 constexpr int kStvRows = 16;
 constexpr int kStvRowsMin = 4;
 constexpr int kStvRowCands[] = {4, 8, 16};

@@ -139,32 +139,40 @@ __device__ __forceinline__ const StvSlice* above(const StvLaunch& L, int si) {
 }
 
 // Sum of v over the slice (the volume) into *slot (deterministic order); see
-// the file comment.
-__device__ void slice_sum(const StvSlice& P, double v, double* slot) {
+// the file comment.  Takes the reduction fields by value, so a kernel's
+// register copy of its descriptor never needs a memory home.
+struct SliceSum {
+  double* part;
+  unsigned* count;
+  int red0, rednblk;
+};
+__device__ __forceinline__ SliceSum slice_sum_of(const StvSlice& P) { return SliceSum{P.part, P.count, P.red0, P.rednblk}; }
+
+__device__ __forceinline__ void slice_sum(SliceSum S, double v, double* slot) {
   __shared__ double red[32];
   __shared__ int last;
-  const int tid = threadIdx.x;
-  const double s = group_sum(v, red, tid, kStvThreads, BlockBar());
+  const int tid = threadIdx.x, nth = (int)blockDim.x;
+  const double s = group_sum(v, red, tid, nth, BlockBar());
   if (tid == 0) {
-    P.part[blockIdx.x] = s;
+    S.part[blockIdx.x] = s;
     __threadfence();
-    last = (atomicAdd(P.count, 1u) == (unsigned)(P.rednblk - 1));
+    last = (atomicAdd(S.count, 1u) == (unsigned)(S.rednblk - 1));
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   double a = 0.0;
-  for (int b = tid; b < P.rednblk; b += kStvThreads) a += __ldcg(P.part + P.red0 + b);
-  const double tot = group_sum(a, red, tid, kStvThreads, BlockBar());
+  for (int b = tid; b < S.rednblk; b += nth) a += __ldcg(S.part + S.red0 + b);
+  const double tot = group_sum(a, red, tid, nth, BlockBar());
   if (tid == 0) {
     *slot = tot;
-    *P.count = 0u;
+    *S.count = 0u;
   }
 }
 
-__device__ __forceinline__ float rx_l1(const StvSlice& P, const StvSlice* Pn, const Pos& q) {
+__device__ __forceinline__ float rx_l1(const StvSlice& P, const float2* xz, const Pos& q) {
   float2 d[4];
-  diffs(P, P.x, Pn ? Pn->x : nullptr, q, d);
+  diffs(P, P.x, xz, q, d);
   return c_abs(d[0]) + c_abs(d[1]) + c_abs(d[2]) + c_abs(d[3]);
 }
 
@@ -172,10 +180,10 @@ __device__ __forceinline__ float rx_l1(const StvSlice& P, const StvSlice* Pn, co
 // previous e, from k_stv_finish) or d1 = 0 (first = true, from k_stv_init).
 // With the residual fields set (iterations K-1 and K), d1 is also kept, or
 // its change ||d1_{K-1} - d1_K||^2 added to *dd1.
-__device__ __forceinline__ void threshold(const StvSlice& P, const StvSlice* Pn, const Pos& q, bool first,
+__device__ __forceinline__ void threshold(const StvSlice& P, const float2* mz, const Pos& q, bool first,
                                           KahanSum* dd1 = nullptr) {
   float2 rm[4];
-  diffs(P, P.m, Pn ? Pn->m : nullptr, q, rm);
+  diffs(P, P.m, mz, q, rm);
   const int nc = (P.zprev || P.znext) ? 4 : 3;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -193,23 +201,25 @@ __device__ __forceinline__ void threshold(const StvSlice& P, const StvSlice* Pn,
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_init(StvLaunch L) {
   const int si = slice_of(L);
-  const StvSlice& P = L.slices[si];
+  const StvSlice P = L.slices[si];   // a register copy: the loops store through global pointers
   if (P.stop && *P.stop) return;
   const StvSlice* Pn = above(L, si);
   const Blk b = blk_of(P);
-  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) threshold(P, Pn, pos_of(P, b, e), true);
+  const float2* mz = Pn ? Pn->m : nullptr;
+  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) threshold(P, mz, pos_of(P, b, e), true);
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_prior(StvLaunch L) {
   __shared__ double red[32];
   const int si = slice_of(L);
-  const StvSlice& P = L.slices[si];
+  const StvSlice P = L.slices[si];   // a register copy: the loops store through global pointers
   if (P.stop && *P.stop) return;
   const StvSlice* Pn = above(L, si);
   const Blk b = blk_of(P);
   KahanSum l1;
 #pragma unroll 4
-  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) l1.add(rx_l1(P, Pn, pos_of(P, b, e)));
+  const float2* xz = Pn ? Pn->x : nullptr;
+  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) l1.add(rx_l1(P, xz, pos_of(P, b, e)));
   const double s = group_sum((double)l1.s, red, threadIdx.x, kStvThreads, BlockBar());
   if (threadIdx.x == 0) atomicAdd(P.prior_acc, s);
 }
@@ -217,7 +227,7 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_prior(StvLaunch L) {
 __global__ void __launch_bounds__(kStvThreads) k_stv_rhs(StvLaunch L) {
   __shared__ double red[32];
   const int si = slice_of(L);
-  const StvSlice& P = L.slices[si];
+  const StvSlice P = L.slices[si];   // a register copy: the loops store through global pointers
   if (P.stop && *P.stop) return;
   const StvSlice* Pp = below(L, si);
   const StvSlice* Pn = above(L, si);
@@ -231,12 +241,13 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_rhs(StvLaunch L) {
   const float2* mn = Pn ? Pn->m : m;
   const float2* ez = P.e + 3 * (long long)P.n;
   const float2* ezp = Pp ? Pp->e + 3 * (long long)Pp->n : ez;
+  const float2* xz = Pn ? Pn->x : nullptr;
   KahanSum g, l1;
 #pragma unroll 4
   for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
     const Pos q = pos_of(P, b, e);
     const int idx = q.idx;
-    l1.add(rx_l1(P, Pn, q));
+    l1.add(rx_l1(P, xz, q));
     // R'e (the padded components are zero past the last index)
     float2 rt = make_float2(-et[idx].x, -et[idx].y), rs = make_float2(-ex[idx].x - ey[idx].x, -ex[idx].y - ey[idx].y);
     if (q.t > 0) rt = c_add(rt, et[idx - st]);
@@ -260,12 +271,19 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_rhs(StvLaunch L) {
   }
   const double s = group_sum((double)l1.s, red, threadIdx.x, kStvThreads, BlockBar());
   if (threadIdx.x == 0) atomicAdd(P.prior_acc, s);
-  slice_sum(P, (double)g.s, P.red);
+  slice_sum(slice_sum_of(P), (double)g.s, P.red);
 }
 
-__global__ void __launch_bounds__(kStvThreads) k_stv_dir(StvLaunch L) {
+// p_j = r + beta p_{j-1} and q = M p_j, <p_j, q>.  One thread per j (the
+// block is Ny_max rounded up to a warp), marching the block's image columns
+// (t, i) in order: p_j of the next column (i+1) is formed once and kept for
+// two steps, so a point costs the loads of r and p_{j-1} at (i+1) and at
+// t -+ 1 (and z -+ 1 in a volume); the j-neighbours come through shared
+// memory.  M = rho I + R'R in the grouping of rtr().
+__global__ void __launch_bounds__(kStvDirMaxThreads) k_stv_dir(StvLaunch L) {
+  __shared__ float2 rowbuf[2][kStvDirMaxThreads + 2];
   const int si = slice_of(L);
-  const StvSlice& P = L.slices[si];
+  const StvSlice P = L.slices[si];   // a register copy: the loops store through global pointers
   if (P.stop && *P.stop) return;
   const StvSlice* Pp = below(L, si);
   const StvSlice* Pn = above(L, si);
@@ -275,43 +293,95 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_dir(StvLaunch L) {
   if (j > 0 && P.red[j - 1] > 0.0) beta = P.red[j] / P.red[j - 1];
   const float be = (float)beta;
   const float2* r = P.r;
-  const float2* po = P.pc[(j + 1) & 1];
-  float2* pn = P.pc[j & 1];
+  // the two direction buffers, picked without a dynamic index into the
+  // descriptor (which would give its register copy a memory home)
+  const float2* po = (j & 1) ? P.pc[0] : P.pc[1];
+  float2* pn = (j & 1) ? P.pc[1] : P.pc[0];
   auto dir_of = [be, j](const float2* rr, const float2* pp, int o) {
     const float2 rv = rr[o];
     if (j == 0) return rv;
     const float2 pv = pp[o];
     return make_float2(fmaf(be, pv.x, rv.x), fmaf(be, pv.y, rv.y));
   };
-  auto dir = [&](int o) { return dir_of(r, po, o); };
   const float2* rp = Pp ? Pp->r : r;
-  const float2* pop = Pp ? Pp->pc[(j + 1) & 1] : po;
+  const float2* pop = Pp ? ((j & 1) ? Pp->pc[0] : Pp->pc[1]) : po;
   const float2* rn = Pn ? Pn->r : r;
-  const float2* pon = Pn ? Pn->pc[(j + 1) & 1] : po;
-  auto dirp = [&](int o) { return dir_of(rp, pop, o); };
-  auto dirn = [&](int o) { return dir_of(rn, pon, o); };
-  KahanSum pq;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
-    const Pos q = pos_of(P, b, e);
-    const float2 pv = dir(q.idx);
-    const float2 l = rtr(P, dir, dirp, dirn, q);
-    const float2 qv = make_float2(fmaf(P.rho, pv.x, l.x), fmaf(P.rho, pv.y, l.y));
-    pn[q.idx] = pv;
-    P.q[q.idx] = qv;
-    pq.add(fmaf(pv.x, qv.x, pv.y * qv.y));
+  const float2* pon = Pn ? ((j & 1) ? Pn->pc[0] : Pn->pc[1]) : po;
+  const int Nx = P.Nx, Ny = P.Ny, Nt = P.Nt, st = Nx * Ny;
+  const int jj = threadIdx.x;
+  const bool act = jj < Ny;
+  const float2 z = make_float2(0.f, 0.f);
+  const float w2 = P.ws * P.ws, z2 = P.wz * P.wz;
+  if (jj == 0) {   // the zero halo of the j-neighbour exchange
+    rowbuf[0][0] = rowbuf[1][0] = z;
+    rowbuf[0][Ny + 1] = rowbuf[1][Ny + 1] = z;
   }
-  slice_sum(P, (double)pq.s, P.red + P.cg + 1 + j);
+  int t = b.t0, i = b.i0;
+  int idx = (t * Nx + i) * Ny + jj;
+  float2 cur = z, prev = z;
+  if (act) {
+    cur = dir_of(r, po, idx);
+    if (i > 0) prev = dir_of(r, po, idx - Ny);
+  }
+  KahanSum pq;
+  for (int rr = 0; rr < b.nrows; ++rr) {
+    float2 nxt = z, tm = z, tp = z, zm = z, zp = z;
+    if (act) {
+      if (i + 1 < Nx) nxt = dir_of(r, po, idx + Ny);
+      if (t > 0) tm = dir_of(r, po, idx - st);
+      if (t + 1 < Nt) tp = dir_of(r, po, idx + st);
+      if (P.zprev) zm = dir_of(rp, pop, idx);
+      if (P.znext) zp = dir_of(rn, pon, idx);
+      rowbuf[rr & 1][jj + 1] = cur;
+    }
+    __syncthreads();
+    if (act) {
+      const float2 jm = rowbuf[rr & 1][jj], jp = rowbuf[rr & 1][jj + 2];
+      const float2 c = cur;
+      float2 lz = z;
+      if (P.zprev) lz = c_add(lz, c_sub(c, zm));
+      if (P.znext) lz = c_sub(lz, c_sub(zp, c));
+      float2 lt = z, ls = z;
+      if (t > 0) lt = c_add(lt, c_sub(c, tm));
+      if (t + 1 < Nt) lt = c_sub(lt, c_sub(tp, c));
+      if (i > 0) ls = c_add(ls, c_sub(c, prev));
+      if (i + 1 < Nx) ls = c_sub(ls, c_sub(nxt, c));
+      if (jj > 0) ls = c_add(ls, c_sub(c, jm));
+      if (jj + 1 < Ny) ls = c_sub(ls, c_sub(jp, c));
+      const float2 l = make_float2(fmaf(z2, lz.x, fmaf(w2, ls.x, lt.x)), fmaf(z2, lz.y, fmaf(w2, ls.y, lt.y)));
+      const float2 qv = make_float2(fmaf(P.rho, c.x, l.x), fmaf(P.rho, c.y, l.y));
+      pn[idx] = c;
+      P.q[idx] = qv;
+      pq.add(fmaf(c.x, qv.x, c.y * qv.y));
+    }
+    // next image column of the block: (t, i+1), or (t+1, 0) past the last i
+    if (i + 1 < Nx) {
+      prev = cur;
+      cur = nxt;
+      ++i;
+      idx += Ny;
+    } else {
+      ++t;
+      i = 0;
+      idx += Ny;
+      prev = z;
+      cur = (act && rr + 1 < b.nrows) ? dir_of(r, po, idx) : z;
+    }
+  }
+  slice_sum(slice_sum_of(P), (double)pq.s, P.red + P.cg + 1 + j);
 }
 
+// m += alpha p_j, r -= alpha q, gamma_{j+1} = <r, r>.  (Splitting each tile
+// over 4 blocks for more warps in flight measured slower: 0.346 -> 0.396 ms a
+// spatio-temporal step on the cardiac workload.)
 __global__ void __launch_bounds__(kStvThreads) k_stv_update(StvLaunch L) {
-  const StvSlice& P = L.slices[slice_of(L)];
+  const StvSlice P = L.slices[slice_of(L)];
   if (P.stop && *P.stop) return;
   const int j = L.step;
   const Blk b = blk_of(P);
   const double gam = P.red[j], pq = P.red[P.cg + 1 + j];
   const float alpha = (pq > 0.0 && gam > 0.0) ? (float)(gam / pq) : 0.f;
-  const float2* pn = P.pc[j & 1];
+  const float2* pn = (j & 1) ? P.pc[1] : P.pc[0];
   const int base = b.row0 * P.Ny;
   const int ne = b.nrows * P.Ny;
   KahanSum g;
@@ -348,23 +418,24 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_update(StvLaunch L) {
       g.add(fmaf(rv.x, rv.x, rv.y * rv.y));
     }
   }
-  slice_sum(P, (double)g.s, P.red + j + 1);
+  slice_sum(slice_sum_of(P), (double)g.s, P.red + j + 1);
 }
 
 __global__ void __launch_bounds__(kStvThreads) k_stv_finish(StvLaunch L) {
   __shared__ double red[32];
   const int si = slice_of(L);
-  const StvSlice& P = L.slices[si];
+  const StvSlice P = L.slices[si];   // a register copy: the loops store through global pointers
   if (P.stop && *P.stop) return;
   const StvSlice* Pn = above(L, si);
   const Blk b = blk_of(P);
+  const float2* mz = Pn ? Pn->m : nullptr;
   KahanSum dd1;
 #pragma unroll 4
   for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
     const Pos q = pos_of(P, b, e);
     const int idx = q.idx;
     // e (the previous threshold's d1 - v) is read and replaced element by element
-    threshold(P, Pn, q, false, P.res_last ? &dd1 : nullptr);
+    threshold(P, mz, q, false, P.res_last ? &dd1 : nullptr);
     P.p[idx] = c_add(P.m[idx], c_sub(P.p[idx], P.x[idx]));
   }
   if (P.res_last) {   // the last iteration: v_K - R m_K = d1_{K-1} - d1_K
@@ -374,7 +445,8 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_finish(StvLaunch L) {
 }
 
 // R (m_K - m_{K-1}) at q from the two fields (and the slice above's, in a volume)
-__device__ __forceinline__ void diffs_dm(const StvSlice& P, const StvSlice* Pn, const Pos& q, float2 (&d)[4]) {
+__device__ __forceinline__ void diffs_dm(const StvSlice& P, const float2* mz, const float2* mpz, const Pos& q,
+                                         float2 (&d)[4]) {
   const float2* m = P.m;
   const float2* mp = P.m_prev;
   auto dm = [m, mp](int o) { return c_sub(m[o], mp[o]); };
@@ -383,7 +455,7 @@ __device__ __forceinline__ void diffs_dm(const StvSlice& P, const StvSlice* Pn, 
   d[0] = (q.t + 1 < P.Nt) ? c_sub(dm(q.idx + P.Nx * P.Ny), c) : z;
   d[1] = (q.i + 1 < P.Nx) ? c_scale(c_sub(dm(q.idx + P.Ny), c), P.ws) : z;
   d[2] = (q.j + 1 < P.Ny) ? c_scale(c_sub(dm(q.idx + 1), c), P.ws) : z;
-  d[3] = Pn ? c_scale(c_sub(c_sub(Pn->m[q.idx], Pn->m_prev[q.idx]), c), P.wz) : z;
+  d[3] = mz ? c_scale(c_sub(c_sub(mz[q.idx], mpz[q.idx]), c), P.wz) : z;
 }
 
 // ADMM residual sums after the loop (final descriptor set): res_acc[0] +=
@@ -392,9 +464,11 @@ __device__ __forceinline__ void diffs_dm(const StvSlice& P, const StvSlice* Pn, 
 __global__ void __launch_bounds__(kStvThreads) k_stv_residuals(StvLaunch L) {
   __shared__ double red[32];
   const int si = slice_of(L);
-  const StvSlice& P = L.slices[si];
+  const StvSlice P = L.slices[si];   // a register copy: the loops store through global pointers
   const StvSlice* Pn = above(L, si);
   const Blk b = blk_of(P);
+  const float2* mz = Pn ? Pn->m : nullptr;
+  const float2* mpz = Pn ? Pn->m_prev : nullptr;
   KahanSum a0, a2, a3;
 #pragma unroll 2
   for (int e = threadIdx.x; e < b.nrows * P.Ny; e += kStvThreads) {
@@ -404,7 +478,7 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_residuals(StvLaunch L) {
     a0.add(fmaf(mx.x, mx.x, mx.y * mx.y));
     a2.add(fmaf(dm.x, dm.x, dm.y * dm.y));
     float2 d[4];
-    diffs_dm(P, Pn, q, d);
+    diffs_dm(P, mz, mpz, q, d);
     float s3 = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) s3 = fmaf(d[k].x, d[k].x, fmaf(d[k].y, d[k].y, s3));
@@ -433,7 +507,13 @@ __global__ void __launch_bounds__(kStvThreads) k_stv_residuals(StvLaunch L) {
 cudaError_t launch_stv_init(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_init); }
 cudaError_t launch_stv_prior(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_prior); }
 cudaError_t launch_stv_rhs(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_rhs); }
-cudaError_t launch_stv_dir(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_dir); }
+cudaError_t launch_stv_dir(const StvLaunch& L, cudaStream_t s) {
+  if (L.nblocks < 1) return cudaSuccess;
+  if (L.dir_threads < 32 || L.dir_threads > kStvDirMaxThreads) return cudaErrorInvalidValue;
+  k_stv_dir<<<L.nblocks, L.dir_threads, 0, s>>>(L);
+  note_launch();
+  return cudaGetLastError();
+}
 cudaError_t launch_stv_update(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_update); }
 cudaError_t launch_stv_finish(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_finish); }
 cudaError_t launch_stv_residuals(const StvLaunch& L, cudaStream_t s) { STV_LAUNCH(k_stv_residuals); }
