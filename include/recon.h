@@ -419,10 +419,13 @@ typedef struct {
  * Errors: INVALID_ARG, CUDA, OOM. */
 recon_status recon_autotune(recon_plan* plan, recon_tuning* out, void* stream);
 
-/* Tunes the batch's temporal tile width and ring depth over all of its slices
- * (synchronises `stream`; drops a captured graph, which is re-captured at the
- * next recon_batch_solve).  Fills temporal_tile_px, col_stages and their
- * times.  Errors: INVALID_ARG, CUDA. */
+/* Tunes the batch's temporal tile width and ring depth over all of its slices,
+ * and each slice's prologue shapes (rows per block, coils per pass, the
+ * explicit objective's coils per pass), once per problem shape (synchronises
+ * `stream`; drops a captured graph, which is re-captured at the next
+ * recon_batch_solve).  Fills temporal_tile_px, col_stages and their times,
+ * the largest slice's prologue shapes and the sum of the slices' prologue
+ * times.  Errors: INVALID_ARG, CUDA, OOM. */
 recon_status recon_batch_autotune(recon_batch* batch, recon_tuning* out, void* stream);
 
 /* Frees the plan and all its device memory.  NULL-safe. */

@@ -151,9 +151,10 @@ recon_status tune_engine(Engine* e, cudaStream_t s, recon_tuning* t) {
   return RECON_OK;
 }
 
-recon_status tune_plan(recon_plan* p, cudaStream_t s, recon_tuning* t) {
-  recon_status st = prepare_buffers(p, s);
-  if (st != RECON_OK) return st;
+// The prologue's row-FFT and coil-combine shapes and the explicit objective's
+// coils per pass of one plan (its buffers already filled by prepare_buffers).
+recon_status tune_prologue(recon_plan* p, cudaStream_t s, recon_tuning* t) {
+  recon_status st;
   // prologue: a patterned complex64 k-space
   const size_t nk = (size_t)p->Nt * p->Nc * p->Ny * p->Nx_full;
   void* k = nullptr;
@@ -220,6 +221,13 @@ recon_status tune_plan(recon_plan* p, cudaStream_t s, recon_tuning* t) {
     p->obj_coils = t->objective_coils = best_o;
     t->objective_ms = best;
   }
+  return RECON_OK;
+}
+
+recon_status tune_plan(recon_plan* p, cudaStream_t s, recon_tuning* t) {
+  recon_status st = prepare_buffers(p, s);
+  if (st != RECON_OK) return st;
+  if ((st = tune_prologue(p, s, t)) != RECON_OK) return st;
   // iteration kernels on the plan's own engine
   if ((st = tune_engine(p->eng, s, t)) != RECON_OK) return st;
   p->tile_px = t->temporal_tile_px;
@@ -281,6 +289,49 @@ recon_status recon_batch_autotune(recon_batch* b, recon_tuning* out, void* strea
     if ((st = prepare_buffers(p, s)) != RECON_OK) return st;
   if (b->eng.n > 1) RC(cudaMemsetAsync(b->eng.d_err, 0, FLAG_COUNT * sizeof(int), s));
   recon_tuning t{};
+  // each slice's prologue shapes, once per problem shape (the plan cache's
+  // entry when the plan was tuned on its own, else the batch's own); the
+  // batch reports the largest slice's choice and the sum of the slices' times
+  {
+    std::map<Key, recon_tuning> seen;
+    size_t largest = 0;
+    float rows_ms = 0.f, combine_ms = 0.f, objective_ms = 0.f;
+    for (recon_plan* p : b->eng.plans) {
+      const Key key = key_of(p);
+      recon_tuning pt{};
+      bool hit = false;
+      {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) { pt = it->second; hit = true; }
+      }
+      if (!hit) {
+        auto it = seen.find(key);
+        if (it != seen.end()) { pt = it->second; hit = true; }
+      }
+      if (hit) {
+        p->rows_per_block = pt.rows_per_block;
+        p->combine_coils = pt.combine_coils;
+        p->obj_coils = pt.objective_coils;
+      } else {
+        if ((st = tune_prologue(p, s, &pt)) != RECON_OK) return st;
+        seen[key] = pt;
+      }
+      rows_ms += pt.rows_ms;
+      combine_ms += pt.combine_ms;
+      objective_ms += pt.objective_ms;
+      const size_t size = (size_t)p->Nt * p->Nc * p->Ny * p->Nx_full;
+      if (size > largest) {
+        largest = size;
+        t.rows_per_block = p->rows_per_block;
+        t.combine_coils = p->combine_coils;
+        t.objective_coils = p->obj_coils;
+      }
+    }
+    t.rows_ms = rows_ms;
+    t.combine_ms = combine_ms;
+    t.objective_ms = objective_ms;
+  }
   if ((st = tune_engine(&b->eng, s, &t)) != RECON_OK) return st;
   RC(cudaStreamSynchronize(s));
   if (b->graph) {   // the captured launches used the old shapes

@@ -73,6 +73,8 @@ def test_batch_autotune_leaves_results_unchanged():
     x0 = [x.cpu().numpy() for x in b.solve(ks)]
     t = b.autotune()
     assert t.temporal_tile_px == 16 and t.col_stages % 8 == 0
+    # each slice's prologue shapes, reported for the largest slice
+    assert 1 <= t.rows_per_block <= 8 and 1 <= t.combine_coils <= 8 and t.rows_ms > 0 and t.combine_ms > 0
     x1 = [x.cpu().numpy() for x in b.solve(ks)]      # re-captured graph
     x2 = [x.cpu().numpy() for x in b.solve(ks)]      # replay
     for a, c, d in zip(x0, x1, x2):
