@@ -87,6 +87,9 @@ def parse():
                     help="also write the full record (notes, tunings, every timing) as JSON to this path")
     ap.add_argument("--grad-only", action="store_true",
                     help="only the differentiable-form measurement (one JSON line with its numbers)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched-form measurement (one JSON line with its numbers); --steps "
+                         "sets its timed batches")
     return ap.parse_args()
 
 
@@ -886,6 +889,10 @@ def main():
         return run_reference(args)
     if args.grad_only:
         print(json.dumps({"grad": measure_grad(args.storage, steps=args.steps)}), flush=True)
+        return 0
+    if args.batched_only:
+        b = measure_batched(args.batched_slices, args.storage, steps=args.steps, persistent=args.persistent)
+        print(json.dumps({"batched": finite_json(b)}), flush=True)
         return 0
     return run_native(args)
 
