@@ -243,9 +243,12 @@ recon_status recon_solve_slabs(int Nx, int Ny, int Nt, int Nc, const uint8_t* ma
  * Errors: INVALID_ARG, CUDA, TIMEOUT, NONFINITE (only reported when info != NULL). */
 recon_status recon_solve(recon_plan* plan, const float* kspace, float* image, recon_info* info, void* stream);
 
-/* Same as recon_solve with HOST buffers: copies kspace host->device, solves,
- * copies the image device->host and synchronises `stream`.  Pinned host memory
- * gives asynchronous, full-bandwidth copies; pageable memory works too.
+/* Same as recon_solve with HOST buffers: solves, copies the image
+ * device->host and synchronises `stream`.  Page-locked (pinned) k-space is
+ * read in place by the prologue through its device mapping, only the sampled
+ * rows (1/R of the array); pageable k-space is first copied whole to a device
+ * staging buffer.  The caller must not write kspace_host until the call
+ * returns.
  *   kspace_host  complex64 [Nt][Nc][Ny][Nx];  image_host complex64 [Nt][Ny][Nx] */
 recon_status recon_solve_host(recon_plan* plan, const float* kspace_host, float* image_host, recon_info* info,
                               void* stream);

@@ -719,10 +719,25 @@ recon_status recon_solve_host(recon_plan* p, const float* kspace_host, float* im
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t kbytes = (size_t)p->Nt * p->Nc * p->Ny * p->Nx_full * sizeof(float2);
   const size_t ibytes = (size_t)p->Nt * p->Ny * p->Nx_full * sizeof(float2);
-  if (!p->kstage) RC(p->alloc((void**)&p->kstage, kbytes));
   if (!p->istage) RC(p->alloc((void**)&p->istage, ibytes));
-  RC(cudaMemcpyAsync(p->kstage, kspace_host, kbytes, cudaMemcpyHostToDevice, s));
-  recon_status st = recon_solve(p, reinterpret_cast<const float*>(p->kstage), reinterpret_cast<float*>(p->istage),
+  // Page-locked host memory is mapped into the device's address space: the
+  // prologue then reads only the sampled k-space rows (1/R of the array)
+  // straight from it, instead of a copy of the whole array first.  Pageable
+  // memory is copied to a device staging buffer.
+  const void* kdev = nullptr;
+  {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, kspace_host) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer)
+      kdev = at.devicePointer;
+    else
+      (void)cudaGetLastError();
+  }
+  if (!kdev) {
+    if (!p->kstage) RC(p->alloc((void**)&p->kstage, kbytes));
+    RC(cudaMemcpyAsync(p->kstage, kspace_host, kbytes, cudaMemcpyHostToDevice, s));
+    kdev = p->kstage;
+  }
+  recon_status st = recon_solve(p, reinterpret_cast<const float*>(kdev), reinterpret_cast<float*>(p->istage),
                                 nullptr, stream);
   if (st != RECON_OK) return st;
   if (p->Nx == p->Nx_full) {
