@@ -178,13 +178,18 @@ void recon_default_opts(recon_opts* opts);
  * storage type.
  *   out     receives the plan (set to NULL on failure)
  *   Nx, Ny, Nt, Nc >= 1
- *   mask    host or device uint8, nonzero = sampled row (see opts.mask_full)
+ *   mask    host or device uint8, nonzero = sampled row (see opts.mask_full); at least one
+ *           row sampled in some frame (a frame may have none: its inverses are I / mu2)
  *   sens    host or device complex64 [Nc][Ny][Nx]
  *   lambda  >= 0;  mu > 0: mu of Algorithm 1, mu2 of Algorithm 2 (mu1 = mu / rho)
  *   opts    NULL for defaults
  * Blocks until the plan is built (the factorisation is done once, outside
- * the timed iterations, as in Section V).  Errors: INVALID_ARG,
- * MASK_NOT_CARTESIAN, OOM, CUDA, NONFINITE (a block not positive definite). */
+ * the timed iterations, as in Section V).  Size limits (UNSUPPORTED beyond
+ * them): Nx <= 1024, Nt <= 128, Nc <= 64, (Nc + 1) Ny <= 12800, and Ny <= 768
+ * with FP32 storage, 640 with 16-bit storage (the column-inverse kernel keeps
+ * a column's vectors and partial sums in shared memory).  Errors: INVALID_ARG,
+ * MASK_NOT_CARTESIAN, OOM, CUDA, UNSUPPORTED, NONFINITE (a block not positive
+ * definite). */
 recon_status recon_plan_create(recon_plan** out, int Nx, int Ny, int Nt, int Nc, const uint8_t* mask,
                                const float* sens, float lambda, float mu, recon_prior prior,
                                const recon_opts* opts, void* stream);

@@ -412,6 +412,27 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
       (prior == RECON_PRIOR_STV && (!(o.spatial_weight >= 0.f) || !std::isfinite(o.spatial_weight) ||
                                     o.cg_steps < 1 || o.cg_steps > 64)))
     return fail(RECON_ERR_INVALID_ARG, "invalid options");
+  {
+    // the column-inverse kernel keeps a column's vectors and its consumers'
+    // partial sums in shared memory: Ny up to 768 with FP32 storage, 640 with
+    // 16-bit (checked here, before any allocation, for the plan's own shape)
+    int dev = 0, optin = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int es = o.storage == 0 ? 8 : 4;
+    const int q = col_inverse_stage_quantum(es);
+    const int work_est = (int)(((long long)Nx * Nt + std::max(sms, 1) - 1) / std::max(sms, 1)) + 2;
+    auto fits = [&](int nb) { return col_inverse_smem(q, nb, 1, work_est, es) <= (size_t)optin; };
+    const int nb = (Ny + 31) / 32;
+    if (optin > 0 && !fits(nb)) {
+      int nb_max = nb;
+      while (nb_max > 1 && !fits(nb_max)) --nb_max;
+      return fail(RECON_ERR_UNSUPPORTED, "Ny = " + std::to_string(Ny) +
+                                             " does not fit the column-inverse kernel's shared memory; this storage "
+                                             "supports Ny <= " + std::to_string(32 * nb_max));
+    }
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   // mask -> sampled row lists (host)
@@ -436,6 +457,10 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
       delete p;
       return fail(RECON_ERR_MASK_NOT_CARTESIAN, "mask differs along kx (row " + std::to_string(bad_j) +
                                                     ", frame " + std::to_string(bad_t) + ")");
+    }
+    if (maxm == 0) {   // no data at all: nothing to reconstruct from (and no row to launch over)
+      delete p;
+      return fail(RECON_ERR_INVALID_ARG, "the mask samples no k-space row");
     }
     p->maxm = maxm;
   }

@@ -242,7 +242,8 @@ recon_status finish_col_shape(Engine* e, recon_plan* const* plans, int n, int st
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem > (size_t)optin)
-    return fail(RECON_ERR_UNSUPPORTED, "batch too large for one launch (work lists exceed shared memory)");
+    return fail(RECON_ERR_UNSUPPORTED, "column-inverse kernel: the largest Ny and the work lists of this set of "
+                                       "slices exceed shared memory");
   RC(prepare_col_inverse(e->storage, smem));
   return RECON_OK;
 }
