@@ -412,9 +412,12 @@ recon_status recon_quantize_kspace(int Nx, int Ny, int Nt, int Nc, const float* 
  * buffers are overwritten with a pattern (a later solve re-initialises every
  * state it reads).  Results are cached per problem shape for the process, so
  * a plan of a shape already tuned takes the cached choice at once.  Not part
- * of the paper; it only picks launch shapes, never the arithmetic. */
+ * of the paper; it only picks launch shapes, never the arithmetic (for
+ * RECON_PRIOR_STV the block rows also move the CG inner products' partial
+ * sums, so the image may change in rounding). */
 typedef struct {
-  int temporal_tile_px;   /* pixels per block of the temporal kernel (TV 16, DFT 16..128, Haar 16..64) */
+  int temporal_tile_px;   /* pixels per block of the temporal kernel (TV 16, DFT 16..128, Haar 16..64);
+                             for RECON_PRIOR_STV the image columns per block of its kernels (4, 8, 16) */
   int col_stages;         /* ring depth of the column-inverse kernel */
   int rows_per_block;     /* k-space rows per block of the prologue's row FFTs (1..8) */
   int combine_coils;      /* coils per pass of the prologue's column FFTs and coil combine (1..8) */
