@@ -289,6 +289,12 @@ namespace recon {
 // exact objective mode or with 16-bit inverses, where (mu I + H'H) x = r
 // holds only to the storage precision).
 recon_status plan_objective(recon_plan* p, const float2* x, double* acc, cudaStream_t s) {
+  if (p->tc_nitems > 0 && (x == p->x || x == p->b)) {   // on the tensor cores (objective_tc.cu)
+    ObjTcParams q = p->tc_par[x == p->x ? 0 : 1];
+    q.fid_acc = acc;
+    RC(launch_objective_tc(q, s));
+    return RECON_OK;
+  }
   ObjParams o{};
   o.Nx = p->Nx; o.Ny = p->Ny; o.Nt = p->Nt; o.Nc = p->Nc;
   o.ncg = p->obj_coils > 0 ? std::min(p->obj_coils, coil_group_for(p->Nc, p->Ny)) : coil_group_for(p->Nc, p->Ny);
@@ -580,6 +586,53 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(tmp);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "sensitivity upload"));
+  }
+
+  // the explicit objective (16-bit storage, or objective = 2) on the tensor
+  // cores: the sampled DFT rows of every frame as FP16-pair operand tiles,
+  // the work items, and the sensitivities' column maxima.  Even Ny only (the
+  // kernel reads s and x two values at a time); odd Ny keeps the FFT kernels.
+  if ((o.storage != 0 || o.objective == 2) && Ny % 2 == 0) {
+    const int tiles_c = (Nx * Nc + 255) / 256;
+    std::vector<int> tile0(Nt + 1, 0);
+    for (int t = 0; t < Nt; ++t) {
+      const int mt = p->h_rowoff[t + 1] - p->h_rowoff[t];
+      tile0[t + 1] = tile0[t] + (mt + 63) / 64;
+    }
+    const size_t per = objective_tc_a_bytes_per_tile(Ny);
+    std::vector<unsigned char> ha((size_t)std::max(tile0[Nt], 1) * per, 0);
+    std::vector<int4> items;
+    for (int t = 0; t < Nt; ++t) {
+      const int r0 = p->h_rowoff[t], mt = p->h_rowoff[t + 1] - r0;
+      for (int rt = 0; rt * 64 < mt; ++rt) {
+        objective_tc_build_a(Ny, p->h_rows.data() + r0 + 64 * rt, std::min(64, mt - 64 * rt),
+                             ha.data() + (size_t)(tile0[t] + rt) * per);
+        for (int ct = 0; ct < tiles_c; ++ct) items.push_back(make_int4(t, rt, ct, tile0[t] + rt));
+      }
+    }
+    PC(p->alloc(&p->tc_A, ha.size()));
+    PC(cudaMemcpy(p->tc_A, ha.data(), ha.size(), cudaMemcpyHostToDevice));
+    PC(p->alloc((void**)&p->tc_items, std::max<size_t>(1, items.size()) * sizeof(int4)));
+    if (!items.empty())
+      PC(cudaMemcpy(p->tc_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    PC(p->alloc((void**)&p->tc_smax, (size_t)Nx * Nc * sizeof(float)));
+    PC(p->alloc((void**)&p->tc_xmax, (size_t)Nt * Nx * sizeof(float)));
+    PC(launch_col_absmax(p->sens, Nx * Nc, Ny, p->tc_smax, s));
+    ObjTcParams q{};
+    q.Nx = Nx; q.Ny = Ny; q.Nt = Nt; q.Nc = Nc;
+    q.smax = p->tc_smax; q.xmax = p->tc_xmax;
+    q.yhat = o.storage ? p->yhat_lp : static_cast<const void*>(p->yhat);
+    q.ystorage = o.storage;
+    q.yscale = p->yscale;
+    q.rowoff = p->rowoff;
+    q.A = p->tc_A; q.items = p->tc_items; q.nitems = (int)items.size();
+    q.grid = std::max(1, p->num_sms);
+    q.flags = p->flags; q.err = p->flags;
+    p->tc_par.assign(2, q);
+    // the tiles do not fit or the driver has no tensor maps: the FFT kernels stay
+    if (objective_tc_prepare(p->tc_par[0], p->x, p->sens) && objective_tc_prepare(p->tc_par[1], p->b, p->sens))
+      p->tc_nitems = (int)items.size();
+    PC(cudaStreamSynchronize(s));
   }
 
   // packed inverses (double-float inversion, rounded once)

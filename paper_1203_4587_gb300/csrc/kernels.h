@@ -15,6 +15,7 @@
 #include <atomic>
 #include <cstdint>
 #include <string>
+#include <cuda.h>   // CUtensorMap (type only; no driver library is linked)
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
@@ -286,6 +287,42 @@ struct ObjParams {           // ||y - H x||^2 of a given field (no inverse)
   const int* flags;
   int grid;                  // blocks of the warp-per-(column, coil) kernel
 };
+
+// ||y - H x||^2 on the tensor cores (objective_tc.cu): per (frame, tile of 64
+// sampled rows, tile of 256 columns (i, c)) item, D = A B' with A the frame's
+// sampled DFT rows (built on the host, objective_tc_build_a) and B = s_c . x,
+// both split into FP16 pairs.
+struct ObjTcParams {        // 64-byte aligned by its tensor maps
+  CUtensorMap smap;          // s as [Nx * Nc][2 Ny] floats, box 256 x 32, 128-byte swizzle
+  CUtensorMap xmap;          // x as [Nt][Nx][2 Ny] floats, box 1 x ni x 32, 128-byte swizzle
+  int Nx, Ny, Nt, Nc;
+  int nk;                    // K chunks of 16 values of j: ceil(Ny / 16)
+  int ni;                    // image columns in an x tile (a column tile of 256 (i, c) spans at most ni)
+  int raw_depth;             // raw tile stages (2 or 3)
+  int raw_bytes;             // bytes of a raw stage: the s tile, then the x tile (1024-byte multiple)
+  const float2* x;           // [Nt][Nx][Ny]: the image xmap describes
+  const float* smax;         // [Nx * Nc]: max_j |s_{i,c}[j]| (rounded up)
+  float* xmax;               // [Nt * Nx]: max_j |x_t[i][j]| (rounded up), formed before each launch
+  const void* yhat;          // hybrid data as in ObjParams
+  int ystorage;
+  const float* yscale;
+  const int* rowoff;
+  const void* A;             // operand tiles, objective_tc_a_bytes_per_tile(Ny) bytes each
+  const int4* items;         // (t, row tile, column tile, A tile index)
+  int nitems;
+  int grid;                  // CTAs (one per SM)
+  double* fid_acc;
+  const int* flags;          // FLAG_STOP read
+  int* err;                  // flags base: errors in [FLAG_ERR]
+};
+size_t objective_tc_a_bytes_per_tile(int Ny);
+void objective_tc_build_a(int Ny, const int* rows, int count, unsigned char* out);   // host
+// Fills the tensor maps, ni and the raw stages of q for image x and
+// sensitivities sens (q.Nx, q.Ny, q.Nt, q.Nc set); false where the tiles do
+// not fit in shared memory or the driver rejects a map.
+bool objective_tc_prepare(ObjTcParams& q, const float2* x, const float2* sens);
+cudaError_t launch_objective_tc(const ObjTcParams& p, cudaStream_t s);
+cudaError_t launch_col_absmax(const float2* s, int ncols, int Ny, float* out, cudaStream_t st);
 
 // Persistent solve of Algorithm 2 with temporal TV (persist_kernels.cu): all
 // K iterations of a set of slices in one cooperative launch, FP32 inverses,

@@ -116,6 +116,13 @@ struct recon_plan {
   float2* res_prev = nullptr;          // DFT, Haar: xhat_{K-1}, copied before the last inverse step;
                                        // spatio-temporal: m_{K-1}, copied before the last m-update
   float2* res_d1 = nullptr;            // spatio-temporal: d1_{K-1} (4 components), kept by that iteration
+  // explicit objective on the tensor cores (16-bit storage; objective_tc.cu)
+  void* tc_A = nullptr;                // operand tiles of every (frame, 64 sampled rows)
+  int4* tc_items = nullptr;
+  int tc_nitems = 0;                   // 0: the FFT kernels form the explicit objective
+  float* tc_smax = nullptr;            // [Nx * Nc]
+  float* tc_xmax = nullptr;            // [Nt * Nx]
+  std::vector<recon::ObjTcParams> tc_par;   // launch parameters for x = this->x and x = this->b
   int* flags = nullptr;
   recon::FftPlanDev fx{}, fy{}, ft{};
   recon::FftPlanDf fxdf{}, fydf{};
