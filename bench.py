@@ -87,6 +87,12 @@ def parse():
                     help="also write the full record (notes, tunings, every timing) as JSON to this path")
     ap.add_argument("--grad-only", action="store_true",
                     help="only the differentiable-form measurement (one JSON line with its numbers)")
+    ap.add_argument("--precision-only", action="store_true",
+                    help="only the precision-form measurement (one JSON line with its numbers); --steps sets its "
+                         "timed solves")
+    ap.add_argument("--precision-frames", type=int, default=None, help="frames of the precision workload (48)")
+    ap.add_argument("--precision-iters", type=int, default=None, help="iterations of the precision workload (100)")
+    ap.add_argument("--precision-storage", default="fp32,fp16,bf16", help="comma-separated storages to measure")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched-form measurement (one JSON line with its numbers); --steps "
                          "sets its timed batches")
@@ -447,25 +453,27 @@ def measure_batched(nslices, storage, steps=3, persistent=False):
                      "from a captured CUDA graph; plan (double-float inversion) reported separately")}
 
 
-def measure_precision(steps=3):
-    """The precision workload with FP32, FP16 and BF16 storage, J(k) every iteration."""
+def measure_precision(steps=3, frames=None, iters=None, storages=("fp32", "fp16", "bf16")):
+    """The precision workload with FP32, FP16 and BF16 storage, J(k) every iteration
+    (frames / iters: a smaller case of the same shape, e.g. for a profile)."""
     import numpy as np
     import torch
 
     import synthdata
     from paper_1203_4587_gb300 import Plan
     from paper_1203_4587_gb300.binding import quantize_kspace
-    c = synthdata.make_case("precision")
+    over = {k: v for k, v in (("Nt", frames), ("iters", iters)) if v is not None}
+    c = synthdata.make_case("precision", **over)
     sens = torch.from_numpy(c.sens.astype(np.complex64)).cuda()
     k = torch.from_numpy(c.kspace.astype(np.complex64)).cuda()
     mask = c.mask.astype(np.uint8)
     Nt, Ny, Nx = c.x_true.shape
     peak, peak_kind = hbm_peak()
-    out = {"workload": "384x384x48 frames x16 coils, R=6, TV, lambda=0.005, mu=0.1, 100 iterations, "
-                       "J(k) every iteration (fused for FP32, explicit FFTs for 16-bit)",
+    out = {"workload": f"384x384x{Nt} frames x16 coils, R=6, TV, lambda=0.005, mu=0.1, {c.iters} iterations, "
+                       "J(k) every iteration (fused for FP32; explicit for 16-bit, on the tensor cores)",
            "peak_source": f"{peak_kind} hbm_gbs (copy)"}
     stream = torch.cuda.current_stream()
-    for storage in ("fp32", "fp16", "bf16"):
+    for storage in storages:
         t0 = time.perf_counter()
         p = Plan(mask, sens, c.lam, c.mu, prior="tv", rho=c.rho, max_iters=c.iters, storage=storage, profile=1)
         torch.cuda.synchronize()
@@ -891,6 +899,11 @@ def main():
         return run_reference(args)
     if args.grad_only:
         print(json.dumps({"grad": measure_grad(args.storage, steps=args.steps)}), flush=True)
+        return 0
+    if args.precision_only:
+        pr = measure_precision(steps=args.steps, frames=args.precision_frames, iters=args.precision_iters,
+                               storages=tuple(args.precision_storage.split(",")))
+        print(json.dumps({"precision": finite_json(pr)}), flush=True)
         return 0
     if args.batched_only:
         b = measure_batched(args.batched_slices, args.storage, steps=args.steps, persistent=args.persistent)

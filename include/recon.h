@@ -122,8 +122,10 @@ typedef struct {
                        uses (mu I + H'H) x = r of the inverse step, in the inverse kernel; its absolute
                        error is <x, e>, e the FP32 residual of that system, at most about
                        2 (1 + mu) sqrt(Ny) eps ||x||^2 (eps = 2^-24), adequate for Delta(k) (Eq. r_ratio).
-                       Exact: ||y - Hx||^2 by explicit FFTs after each inverse step.  16-bit storage
-                       always uses the exact form. */
+                       Exact: ||y - Hx||^2 formed explicitly after each inverse step: for even Ny
+                       on the tensor cores (the sampled DFT rows times s_c . x, operands split into
+                       FP16 pairs, three products accumulated in FP32: about 22 bits), else by FFTs.
+                       16-bit storage always uses the exact form. */
   int mask_full;    /* 1 = mask is [Nt][Ny][Nx] and must be constant along kx (default 0) */
   int col_stages;   /* ring depth of the inverse kernel, rounded down to a multiple of its consumer
                        warp count (8 at FP32 storage, 12 at 16 bit; at least that count) and
@@ -421,7 +423,8 @@ typedef struct {
   int col_stages;         /* ring depth of the column-inverse kernel */
   int rows_per_block;     /* k-space rows per block of the prologue's row FFTs (1..8) */
   int combine_coils;      /* coils per pass of the prologue's column FFTs and coil combine (1..8) */
-  int objective_coils;    /* coils per pass of the explicit objective; 0 when the plan does not use it */
+  int objective_coils;    /* coils per pass of the explicit objective; 0 when the plan does not use it,
+                             1 for its tensor-core form (all coils of 256 columns (i, c) in one item) */
   float temporal_ms, col_ms, rows_ms, combine_ms, objective_ms;   /* time per launch of the chosen shape */
   int from_cache;         /* 1 when the plan took a cached result */
 } recon_tuning;

@@ -208,7 +208,12 @@ recon_status tune_prologue(recon_plan* p, cudaStream_t s, recon_tuning* t) {
   const bool exact = objective_on && (p->opts.objective == 2 || p->storage != 0);
   t->objective_coils = 0;
   t->objective_ms = 0.f;
-  if (exact) {
+  if (exact && p->tc_nitems > 0) {   // the tensor-core form: no coil passes to choose
+    float ms = 0.f;
+    if ((st = time_ms([&] { return plan_objective(p, p->x, p->trace_fid, s); }, s, &ms)) != RECON_OK) return st;
+    p->obj_coils = t->objective_coils = 1;
+    t->objective_ms = ms;
+  } else if (exact) {
     best = 3.4e38f;
     int best_o = 0;
     for (int c : {1, 2, 4, 8}) {
