@@ -589,8 +589,8 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
   }
 
   // the explicit objective (16-bit storage, or objective = 2) on the tensor
-  // cores: the sampled DFT rows of every frame as FP16-pair operand tiles,
-  // the work items, and the sensitivities' column maxima.  Even Ny only (the
+  // cores: the sampled rows of every (frame, row tile), the DFT twiddles as
+  // FP16 pairs, the work items, and the sensitivities' column maxima.  Even Ny only (the
   // kernel reads s and x two values at a time); odd Ny keeps the FFT kernels.
   if ((o.storage != 0 || o.objective == 2) && Ny % 2 == 0) {
     const int tiles_c = (Nx * Nc + 255) / 256;
@@ -599,19 +599,22 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
       const int mt = p->h_rowoff[t + 1] - p->h_rowoff[t];
       tile0[t + 1] = tile0[t] + (mt + 63) / 64;
     }
-    const size_t per = objective_tc_a_bytes_per_tile(Ny);
-    std::vector<unsigned char> ha((size_t)std::max(tile0[Nt], 1) * per, 0);
+    std::vector<int> hrows((size_t)std::max(tile0[Nt], 1) * 64, -1);   // sampled rows of each row tile
     std::vector<int4> items;
     for (int t = 0; t < Nt; ++t) {
       const int r0 = p->h_rowoff[t], mt = p->h_rowoff[t + 1] - r0;
       for (int rt = 0; rt * 64 < mt; ++rt) {
-        objective_tc_build_a(Ny, p->h_rows.data() + r0 + 64 * rt, std::min(64, mt - 64 * rt),
-                             ha.data() + (size_t)(tile0[t] + rt) * per);
+        for (int m = 0; m < std::min(64, mt - 64 * rt); ++m)
+          hrows[(size_t)(tile0[t] + rt) * 64 + m] = p->h_rows[r0 + 64 * rt + m];
         for (int ct = 0; ct < tiles_c; ++ct) items.push_back(make_int4(t, rt, ct, tile0[t] + rt));
       }
     }
-    PC(p->alloc(&p->tc_A, ha.size()));
-    PC(cudaMemcpy(p->tc_A, ha.data(), ha.size(), cudaMemcpyHostToDevice));
+    std::vector<uint2> htw((size_t)Ny);
+    objective_tc_twiddle(Ny, htw.data());
+    PC(p->alloc((void**)&p->tc_rows, hrows.size() * sizeof(int)));
+    PC(cudaMemcpy(p->tc_rows, hrows.data(), hrows.size() * sizeof(int), cudaMemcpyHostToDevice));
+    PC(p->alloc((void**)&p->tc_twiddle, htw.size() * sizeof(uint2)));
+    PC(cudaMemcpy(p->tc_twiddle, htw.data(), htw.size() * sizeof(uint2), cudaMemcpyHostToDevice));
     PC(p->alloc((void**)&p->tc_items, std::max<size_t>(1, items.size()) * sizeof(int4)));
     if (!items.empty())
       PC(cudaMemcpy(p->tc_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
@@ -625,7 +628,8 @@ recon_status plan_create_impl(recon_plan** out, int Nxf, int Ny, int Nt, int Nc,
     q.ystorage = o.storage;
     q.yscale = p->yscale;
     q.rowoff = p->rowoff;
-    q.A = p->tc_A; q.items = p->tc_items; q.nitems = (int)items.size();
+    q.tile_rows = p->tc_rows; q.twiddle = p->tc_twiddle;
+    q.items = p->tc_items; q.nitems = (int)items.size();
     q.grid = std::max(1, p->num_sms);
     q.flags = p->flags; q.err = p->flags;
     p->tc_par.assign(2, q);

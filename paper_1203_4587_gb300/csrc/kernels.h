@@ -290,7 +290,7 @@ struct ObjParams {           // ||y - H x||^2 of a given field (no inverse)
 
 // ||y - H x||^2 on the tensor cores (objective_tc.cu): per (frame, tile of 64
 // sampled rows, tile of 256 columns (i, c)) item, D = A B' with A the frame's
-// sampled DFT rows (built on the host, objective_tc_build_a) and B = s_c . x,
+// sampled DFT rows (formed in the kernel from a twiddle table) and B = s_c . x,
 // both split into FP16 pairs.
 struct ObjTcParams {        // 64-byte aligned by its tensor maps
   CUtensorMap smap;          // s as [Nx * Nc][2 Ny] floats, box 256 x 32, 128-byte swizzle
@@ -299,6 +299,7 @@ struct ObjTcParams {        // 64-byte aligned by its tensor maps
   int nk;                    // K chunks of 16 values of j: ceil(Ny / 16)
   int ni;                    // image columns in an x tile (a column tile of 256 (i, c) spans at most ni)
   int raw_depth;             // raw tile stages (2 or 3)
+  int op_stages;             // operand (A and B) stages (2 or 3)
   int raw_bytes;             // bytes of a raw stage: the s tile, then the x tile (1024-byte multiple)
   const float2* x;           // [Nt][Nx][Ny]: the image xmap describes
   const float* smax;         // [Nx * Nc]: max_j |s_{i,c}[j]| (rounded up)
@@ -307,16 +308,16 @@ struct ObjTcParams {        // 64-byte aligned by its tensor maps
   int ystorage;
   const float* yscale;
   const int* rowoff;
-  const void* A;             // operand tiles, objective_tc_a_bytes_per_tile(Ny) bytes each
-  const int4* items;         // (t, row tile, column tile, A tile index)
+  const int* tile_rows;      // [row tiles][64]: sampled row q of each (frame, row tile); -1 past its rows
+  const uint2* twiddle;      // [Ny]: objective_tc_twiddle
+  const int4* items;         // (t, row tile, column tile, row tile index into tile_rows)
   int nitems;
   int grid;                  // CTAs (one per SM)
   double* fid_acc;
   const int* flags;          // FLAG_STOP read
   int* err;                  // flags base: errors in [FLAG_ERR]
 };
-size_t objective_tc_a_bytes_per_tile(int Ny);
-void objective_tc_build_a(int Ny, const int* rows, int count, unsigned char* out);   // host
+void objective_tc_twiddle(int Ny, uint2* out);   // host: [Ny] FP16-pair twiddles of the scaled DFT
 // Fills the tensor maps, ni and the raw stages of q for image x and
 // sensitivities sens (q.Nx, q.Ny, q.Nt, q.Nc set); false where the tiles do
 // not fit in shared memory or the driver rejects a map.

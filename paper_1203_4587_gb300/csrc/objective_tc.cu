@@ -24,19 +24,21 @@
 //   issuer (1 warp, one thread): copies the raw tiles of each chunk (s of
 //   the 256 columns and x of the image columns they span, 16 values of j
 //   each) by TMA tensor copies into a ring of 2-3 stages, 2-3 chunks ahead
-//   (out-of-range columns and j >= Ny read as zeros); copies each chunk's A
-//   (hi and lo, 16 KB, precomputed at plan time in the operand layout below)
-//   by one bulk copy into a ring of 3 stages, one chunk ahead; and issues the
-//   6 MMAs of a chunk (3 products x 2 K-steps of 16) once its B is formed,
-//   committing them to the B stage's mbarrier and, after an item's last
+//   (out-of-range columns and j >= Ny read as zeros), and issues the 6 MMAs
+//   of a chunk (3 products x 2 K-steps of 16) once its operands are formed,
+//   committing them to the operand stage's mbarrier and, after an item's last
 //   chunk, to its accumulator's;
-//   converters (16 warps): form each chunk's B (hi and lo, 32 KB) in one of
-//   two stages from the raw tiles: a lane holds two columns (i, c), (i, c + 1)
-//   at two adjacent values j, j + 1, reads them with 16-byte shared loads and
-//   writes 8 bytes of a core row per column and half.  They also run each
-//   item's epilogue (D read from tensor memory, |y_hat - C|^2 summed over the
-//   valid rows and columns) during the next item's first chunks, 8 columns a
-//   chunk, the loads of y_hat in flight while the chunk is formed.
+//   converters (16 warps): form each chunk's operands in one of two stages.
+//   A (hi and lo, 16 KB): a lane writes one K pair of a real row [Re F, -Im F]
+//   and of its imaginary row [Im F, Re F] for two values j, from a table of
+//   the Ny twiddles exp(-2 pi i d / Ny) as FP16 pairs in shared memory (index
+//   q j mod Ny, stepped by 16 q a chunk).  B (hi and lo, 32 KB): a lane holds
+//   two columns (i, c), (i, c + 1) at two adjacent values j, j + 1 of the raw
+//   tiles, reads them with 16-byte shared loads and writes 8 bytes of a core
+//   row per column and half.  They also run each item's epilogue (D read from
+//   tensor memory, |y_hat - C|^2 summed over the valid rows and columns)
+//   during the next item's first chunks, 8 columns a chunk, the loads of y_hat
+//   in flight while the chunk is formed.
 // Two accumulators of 256 columns in tensor memory alternate between items.
 // The per-column scales come from max_j |x_t[i][j]| (k_col_absmax over x
 // before the launch) and max_j |s_c[i][j]| (at plan time).
@@ -74,16 +76,13 @@ constexpr int kTcEB = 8;                            // of them a batch
 constexpr int kTcENB = kTcEpCols / kTcEB;
 constexpr int kTcAHalf = kTcM * kTcKc * 2;    // bytes of one FP16 half (hi or lo) of an A chunk: 8 KB
 constexpr int kTcBHalf = kTcN * kTcKc * 2;    // 16 KB
-constexpr int kTcAStage = 2 * kTcAHalf;      // 16 KB: A hi, A lo of a chunk
-constexpr int kTcBStage = 2 * kTcBHalf;      // 32 KB: B hi, B lo of a chunk
-constexpr int kTcAStages = 3;                // A ring: a chunk's A is copied one chunk ahead
+constexpr int kTcStage = 2 * kTcAHalf + 2 * kTcBHalf;   // 48 KB: A hi, A lo, B hi, B lo of a chunk
 constexpr int kTcRawS = kTcN * kTcJc * 8;     // 32 KB: s of 256 columns x 16 values
 constexpr int kTcRawRow = kTcJc * 8;          // 128 bytes: one column's 16 values
 constexpr int kTcTmemCols = 2 * kTcN;   // two accumulators: an item's epilogue overlaps the next item
 constexpr int kTcSmemMax = 227 * 1024;
 static_assert(kTcN / 8 == 2 * (kTcConv / 32), "a warp forms the cores of two row groups n8");
 static_assert(kTcRawRow == 128, "raw rows are one 128-byte swizzle row");
-static_assert(kTcAStages == 3, "the A of chunk g + 1 is copied once the MMAs of chunk g - 2 are done");
 
 __device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
@@ -104,12 +103,6 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t ad, uint64_t bd
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                :: "r"(smem_u32(bar)) : "memory");
-}
-// L2 policy for the A chunks (every column tile of a frame reads them again)
-__device__ __forceinline__ uint64_t policy_evict_last() {
-  uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -155,7 +148,7 @@ __device__ __forceinline__ void conv_sync() { asm volatile("bar.sync 1, %0;" :: 
 template <class YE>
 __global__ void __launch_bounds__(kTcThreads, 1) k_objective_tc(const __grid_constant__ ObjTcParams P) {
   extern __shared__ unsigned char sm_dyn[];
-  __shared__ __align__(8) uint64_t a_bar[kTcAStages], mma_bar[2], raw_bar[3], bfull[2], acc_full[2], acc_empty[2];
+  __shared__ __align__(8) uint64_t mma_bar[3], raw_bar[3], bfull[3], acc_full[2], acc_empty[2];
   __shared__ uint32_t tslot;
   __shared__ double red[32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -165,14 +158,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_objective_tc(const __grid_con
   const uint32_t pad = ((s0 + 1023u) & ~1023u) - s0;
   unsigned char* sm = sm_dyn + pad;
   const int D = P.raw_depth;
+  const int S = P.op_stages;   // operand stages (2 or 3): chunk g in stage g mod S
   const int raw_bytes = P.raw_bytes;
-  unsigned char* bst0 = sm + kTcAStages * kTcAStage;   // B stages
-  unsigned char* raw0 = bst0 + 2 * kTcBStage;          // raw ring
+  unsigned char* raw0 = sm + S * kTcStage;   // raw ring after the operand stages
   float* escale = reinterpret_cast<float*>(raw0 + D * raw_bytes);   // [kTcN] 2^e of column n
   float* unscale = escale + kTcN;                                   // [2][kTcN] 2^-(e + 12), by item parity
+  uint2* twid = reinterpret_cast<uint2*>(unscale + 2 * kTcN);       // [Ny] DFT twiddles, FP16 pairs
   if (tid == 0) {
-    for (int b = 0; b < kTcAStages; ++b) mbar_init(&a_bar[b], 1);
-    for (int b = 0; b < 2; ++b) { mbar_init(&mma_bar[b], 1); mbar_init(&bfull[b], kTcConv / 32); }
+    for (int b = 0; b < S; ++b) { mbar_init(&mma_bar[b], 1); mbar_init(&bfull[b], kTcConv / 32); }
     for (int b = 0; b < D; ++b) mbar_init(&raw_bar[b], 1);
     for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], kTcConv / 32); }
     fence_mbar_init();
@@ -197,100 +190,71 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_objective_tc(const __grid_con
     // ---- issuer warp: lane 0 issues every copy and MMA of this CTA ----
     // (32-bit counters stepped by one: no integer division on this serial path)
     if (lane == 0) {
-      const uint64_t pol = policy_evict_last();
-      uint32_t pend_a = 0u, pend_m = 0u, pend_r = 0u;   // copies / MMA groups in flight, by stage
-      uint32_t par_a = 0u, par_m = 0u, par_r = 0u;
-      // a cursor over this CTA's chunks: item li, K chunk kc, ring stage st and its phase parity
-      struct Cursor {
-        int li, kc, st, ph;
-        int4 it;
-        __device__ void step(int nk, int depth) {
-          if (++kc == nk) { kc = 0; ++li; }
-          if (++st == depth) { st = 0; ph ^= 1; }
-        }
-      };
-      const int4 it0 = G > 0 ? P.items[blockIdx.x] : make_int4(0, 0, 0, 0);
-      Cursor cr{0, 0, 0, 0, it0}, ca{0, 0, 0, 0, it0};
-      auto refresh = [&](Cursor& c) {   // the item of a cursor that has just moved to the next one
-        if (c.kc == 0 && c.li < nmine) c.it = P.items[(int)blockIdx.x + c.li * (int)gridDim.x];
-      };
-      // raw tiles of cursor cr's chunk into its stage
+      uint32_t pend_m = 0u, pend_r = 0u;   // MMA groups / copies in flight, by stage
+      uint32_t par_m = 0u, par_r = 0u;
+      // raw-tile cursor over this CTA's chunks: item li, K chunk kc, ring stage st, phase parity
+      int cli = 0, ckc = 0, cst = 0;
+      uint32_t cph = 0u;
+      int4 cit = G > 0 ? P.items[blockIdx.x] : make_int4(0, 0, 0, 0);
+      // raw tiles of the cursor's chunk into its stage
       auto issue_raw = [&]() {
-        const int st = cr.st, n0 = cr.it.z * kTcN;
-        const uint32_t dst = smem_u32(raw0) + (uint32_t)(st * raw_bytes);
-        mbar_arrive_expect_tx(&raw_bar[st], (uint32_t)(kTcRawS + P.ni * kTcRawRow));
-        tma_tile_2d(dst, &P.smap, cr.kc * 2 * kTcJc, n0, &raw_bar[st]);
-        tma_tile_3d(dst + kTcRawS, &P.xmap, cr.kc * 2 * kTcJc, n0 / Nc, cr.it.x, &raw_bar[st]);
-        pend_r |= 1u << st;
-        par_r = (par_r & ~(1u << st)) | ((uint32_t)cr.ph << st);
-        cr.step(nk, D);
-        refresh(cr);
-      };
-      // A chunk of cursor ca's chunk into its stage (chunk c into stage c mod 3)
-      auto issue_a = [&]() {
-        const int st = ca.st;
-        const unsigned char* src = static_cast<const unsigned char*>(P.A) + ((size_t)ca.it.w * nk + ca.kc) * kTcAStage;
-        mbar_arrive_expect_tx(&a_bar[st], kTcAStage);
-        bulk_g2s(sm + st * kTcAStage, src, kTcAStage, &a_bar[st], pol);
-        pend_a |= 1u << st;
-        par_a = (par_a & ~(1u << st)) | ((uint32_t)ca.ph << st);
-        ca.step(nk, kTcAStages);
-        refresh(ca);
+        const int n0 = cit.z * kTcN;
+        const uint32_t dst = smem_u32(raw0) + (uint32_t)(cst * raw_bytes);
+        mbar_arrive_expect_tx(&raw_bar[cst], (uint32_t)(kTcRawS + P.ni * kTcRawRow));
+        tma_tile_2d(dst, &P.smap, ckc * 2 * kTcJc, n0, &raw_bar[cst]);
+        tma_tile_3d(dst + kTcRawS, &P.xmap, ckc * 2 * kTcJc, n0 / Nc, cit.x, &raw_bar[cst]);
+        pend_r |= 1u << cst;
+        par_r = (par_r & ~(1u << cst)) | (cph << cst);
+        if (++ckc == nk) {
+          ckc = 0;
+          if (++cli < nmine) cit = P.items[(int)blockIdx.x + cli * (int)gridDim.x];
+        }
+        if (++cst == D) { cst = 0; cph ^= 1u; }
       };
       for (int c = 0; c < G && c < D; ++c) issue_raw();
-      if (G > 0) issue_a();
       bool ok = true;
-      int kc = 0, li = 0, st = 0, sa = 0;      // chunk g: K chunk, item, raw stage, A stage
-      uint32_t ph_a = 0u;                      // the A stage's phase parity
+      int kc = 0, li = 0, st = 0;      // chunk g: K chunk, item, raw stage
+      int b = 0;                       // its operand stage (g mod S)
+      uint32_t ph = 0u;                // and that stage's phase parity ((g / S) mod 2)
       for (int g = 0; g < G && ok; ++g) {
-        const int b = g & 1;
-        if (g >= 2) {   // the MMAs of chunk g-2 have read A stage (g+1) mod 3
-          if (!mbar_wait(&mma_bar[b], (uint32_t)(((g - 2) >> 1) & 1), err)) { ok = false; break; }
-          pend_m &= ~(1u << b);
-        }
-        if (g + 1 < G) issue_a();
         if (kc == 0 && li >= 2) {   // the epilogue of item li - 2 has read accumulator li mod 2
           if (!mbar_wait(&acc_empty[li & 1], (uint32_t)(((li - 2) >> 1) & 1), err)) { ok = false; break; }
         }
-        if (!mbar_wait(&bfull[b], (uint32_t)((g >> 1) & 1), err)) { ok = false; break; }   // B formed, raw st read
+        // A and B of chunk g formed (after the MMAs of chunk g - S left the stage), raw stage read
+        if (!mbar_wait(&bfull[b], ph, err)) { ok = false; break; }
+        pend_m &= ~(1u << b);   // the converters saw the MMAs of chunk g - S complete
+        pend_r &= ~(1u << st);  // and the raw tiles of chunk g land
         if (g + D < G) issue_raw();
-        if (!mbar_wait(&a_bar[sa], ph_a, err)) { ok = false; break; }
-        pend_a &= ~(1u << sa);
-        pend_r &= ~(1u << st);   // the converters saw it land before they arrived on bfull
         tc_fence_after();
-        const uint32_t a_hi = smem_u32(sm) + (uint32_t)(sa * kTcAStage), a_lo = a_hi + kTcAHalf;
-        const uint32_t b_hi = smem_u32(bst0) + (uint32_t)(b * kTcBStage), b_lo = b_hi + kTcBHalf;
+        const uint32_t a_hi = smem_u32(sm) + (uint32_t)(b * kTcStage), a_lo = a_hi + kTcAHalf;
+        const uint32_t b_hi = a_hi + 2 * kTcAHalf, b_lo = b_hi + kTcBHalf;
         const uint32_t lboA = (kTcM / 8) * 128, lboB = (kTcN / 8) * 128;
         const uint32_t pa[3] = {a_hi, a_hi, a_lo}, pb[3] = {b_hi, b_lo, b_hi};
 #pragma unroll
         for (int pr = 0; pr < 3; ++pr)
 #pragma unroll
           for (int kk = 0; kk < kTcKc / 16; ++kk)
-            tc_mma(tmem + (uint32_t)((li & 1) * kTcN), tc_sdesc(pa[pr] + kk * 2 * lboA, lboA, 128), tc_sdesc(pb[pr] + kk * 2 * lboB, lboB, 128),
-                   (kc > 0 || pr > 0 || kk > 0) ? 1u : 0u);
+            tc_mma(tmem + (uint32_t)((li & 1) * kTcN), tc_sdesc(pa[pr] + kk * 2 * lboA, lboA, 128),
+                   tc_sdesc(pb[pr] + kk * 2 * lboB, lboB, 128), (kc > 0 || pr > 0 || kk > 0) ? 1u : 0u);
         tc_commit(&mma_bar[b]);
         if (kc == nk - 1) tc_commit(&acc_full[li & 1]);   // the item's accumulator is complete
         pend_m |= 1u << b;
-        par_m = (par_m & ~(1u << b)) | ((uint32_t)((g >> 1) & 1) << b);
+        par_m = (par_m & ~(1u << b)) | (ph << b);
         if (++kc == nk) { kc = 0; ++li; }
         if (++st == D) st = 0;
-        if (++sa == kTcAStages) { sa = 0; ph_a ^= 1u; }
+        if (++b == S) { b = 0; ph ^= 1u; }
       }
       if (!ok) {   // let the copies and MMAs in flight land before the memory is released
-        for (int b = 0; b < kTcAStages; ++b) {
+        for (int b = 0; b < 3; ++b) {
           unsigned long long t0 = global_ns();
-          if ((pend_a >> b) & 1u)
-            while (!mbar_try_wait(&a_bar[b], (par_a >> b) & 1u) && global_ns() - t0 < kWaitLimitNs) {}
-          t0 = global_ns();
-          if (b < 2 && ((pend_m >> b) & 1u))
+          if ((pend_m >> b) & 1u)
             while (!mbar_try_wait(&mma_bar[b], (par_m >> b) & 1u) && global_ns() - t0 < kWaitLimitNs) {}
           t0 = global_ns();
-          if (b < 3 && ((pend_r >> b) & 1u))
+          if ((pend_r >> b) & 1u)
             while (!mbar_try_wait(&raw_bar[b], (par_r >> b) & 1u) && global_ns() - t0 < kWaitLimitNs) {}
         }
-      } else if (G > 0) {   // the last MMAs complete before the tensor memory is freed
-        const int gl = G - 1;
-        mbar_wait(&mma_bar[gl & 1], (uint32_t)((gl >> 1) & 1), err);
+      } else if (nmine > 0) {   // the last MMAs (committed to the last item's accumulator) complete
+        mbar_wait(&acc_full[(nmine - 1) & 1], (uint32_t)(((nmine - 1) >> 1) & 1), err);
       }
     }
     __syncwarp();
@@ -353,10 +317,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_objective_tc(const __grid_con
       if (lane == 0) mbar_arrive(&acc_empty[li_prev & 1]);   // this warp has read the accumulator
     };
     const int per = (kTcENB + nk - 1) / nk;   // epilogue batches a chunk
+    // A share: sampled row m = 4 warp + lane / 8 of the tile (real part in D row m,
+    // imaginary in row m + 64), values j = jj, jj + 8 of each chunk; 4 bytes (a
+    // K pair) of a core row each, for hi and lo
+    const int am = 4 * warp + (lane >> 3), ajj = lane & 7;
+    uint32_t aoff[2];
+#pragma unroll
+    for (int pa = 0; pa < 2; ++pa) {
+      const int j = ajj + 8 * pa;
+      aoff[pa] = (uint32_t)(((j >> 2) * (kTcM / 8) + (am >> 3)) * 128 + (am & 7) * 16 + (j & 3) * 4);
+    }
+    for (int d = tid; d < P.Ny; d += kTcConv) twid[d] = P.twiddle[d];   // ordered by the first conv_sync
     bool ok = true;
     int g = 0;                 // chunks of this CTA seen
     int st = 0;                // their raw stage (g mod D)
     uint32_t ph_r = 0u;        // and its phase parity ((g / D) mod 2)
+    int b = 0;                 // their operand stage (g mod S)
+    uint32_t ph_b = 0u;        // and its phase parity ((g / S) mod 2)
     // every converter warp takes both named barriers of every item, also after
     // a failed wait (ok = false then skips the work), so that none waits forever
     for (int li = 0; li < nmine; ++li) {
@@ -371,6 +348,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_objective_tc(const __grid_con
       }
       conv_sync();
       if (!ok) continue;
+      // this lane's sampled row q (-1: none) and its twiddle indices q j mod Ny
+      const int aq = P.tile_rows[(size_t)it.w * kTcRows + am];
+      const int aq16 = aq >= 0 ? (aq * kTcJc) % P.Ny : 0;   // q < Ny <= 768: no overflow
+      int ad[2];
+#pragma unroll
+      for (int pa = 0; pa < 2; ++pa) ad[pa] = aq >= 0 ? (aq * (ajj + 8 * pa)) % P.Ny : 0;
       float esv[2][2];
       uint32_t offx[2][2];
 #pragma unroll
@@ -383,15 +366,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_objective_tc(const __grid_con
           offx[pp][cc] = (uint32_t)kTcRawS + raw_off(xr, jq);
         }
       for (int kc = 0; kc < nk; ++kc, ++g) {
-        const int b = g & 1;
         const int eb0 = li > 0 ? min(kTcENB, kc * per) : kTcENB, eb1 = min(kTcENB, eb0 + per);
         float yb[kTcEB];
         if (eb0 < eb1) load_y(yb, eb0);   // in flight during the conversion
-        // the MMAs of chunk g-2 have read B stage b
-        if (g >= 2 && !mbar_wait(&mma_bar[b], (uint32_t)(((g - 2) >> 1) & 1), err)) { ok = false; break; }
+        // the MMAs of chunk g - S have read operand stage b
+        if (g >= S && !mbar_wait(&mma_bar[b], ph_b ^ 1u, err)) { ok = false; break; }
         if (!mbar_wait(&raw_bar[st], ph_r, err)) { ok = false; break; }
         const unsigned char* rs = raw0 + st * raw_bytes;
-        unsigned char* Bh = bst0 + b * kTcBStage;
+        unsigned char* Ah = sm + b * kTcStage;
+        unsigned char* Bh = Ah + 2 * kTcAHalf;
+        // A: rows [Re F, -Im F] and [Im F, Re F] of the twiddle exp(-2 pi i q j / Ny) (scaled)
+#pragma unroll
+        for (int pa = 0; pa < 2; ++pa) {
+          uint2 w = make_uint2(0u, 0u);   // (hi re, hi im), (lo re, lo im) as FP16 pairs
+          if (aq >= 0 && kc * kTcJc + ajj + 8 * pa < P.Ny) w = twid[ad[pa]];
+          const uint32_t o = aoff[pa];
+          *reinterpret_cast<uint32_t*>(Ah + o) = w.x ^ 0x80000000u;                            // (Re, -Im) hi
+          *reinterpret_cast<uint32_t*>(Ah + o + 1024) = __funnelshift_l(w.x, w.x, 16);        // (Im, Re) hi
+          *reinterpret_cast<uint32_t*>(Ah + kTcAHalf + o) = w.y ^ 0x80000000u;                 // lo
+          *reinterpret_cast<uint32_t*>(Ah + kTcAHalf + o + 1024) = __funnelshift_l(w.y, w.y, 16);
+          ad[pa] += aq16;
+          if (ad[pa] >= P.Ny) ad[pa] -= P.Ny;
+        }
 #pragma unroll
         for (int pp = 0; pp < 2; ++pp)
 #pragma unroll
@@ -414,6 +410,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_objective_tc(const __grid_con
         __syncwarp();
         if (lane == 0) mbar_arrive(&bfull[b]);
         if (++st == D) { st = 0; ph_r ^= 1u; }
+        if (++b == S) { b = 0; ph_b ^= 1u; }
         // the epilogue batches of item li - 1 that fall on this chunk
         if (eb0 < eb1) {
           if (eb0 == 0) {
@@ -467,10 +464,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_objective_tc(const __grid_con
 }
 
 // shared memory of a launch: 1 KB alignment slack, two operand stages, the
-// raw ring, the column scales
-size_t tc_smem_bytes(int raw_depth, int raw_bytes) {
-  return 1024 + (size_t)kTcAStages * kTcAStage + 2 * (size_t)kTcBStage + (size_t)raw_depth * raw_bytes +
-         3 * kTcN * sizeof(float);
+// raw ring, the column scales, the twiddle table
+size_t tc_smem_bytes(int op_stages, int raw_depth, int raw_bytes, int Ny) {
+  return 1024 + (size_t)op_stages * kTcStage + (size_t)raw_depth * raw_bytes + 3 * kTcN * sizeof(float) +
+         (size_t)((Ny + 1) / 2) * 2 * sizeof(uint2);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -508,8 +505,6 @@ __global__ void k_col_absmax(const float2* __restrict__ s, int ncols, int Ny, fl
   }
 }
 
-size_t objective_tc_a_bytes_per_tile(int Ny) { return (size_t)((Ny + kTcJc - 1) / kTcJc) * 2 * kTcAHalf; }
-
 cudaError_t launch_col_absmax(const float2* s, int ncols, int Ny, float* out, cudaStream_t st) {
   if (ncols < 1) return cudaSuccess;
   k_col_absmax<<<(ncols + 7) / 8, 256, 0, st>>>(s, ncols, Ny, out);
@@ -517,40 +512,18 @@ cudaError_t launch_col_absmax(const float2* s, int ncols, int Ny, float* out, cu
   return cudaGetLastError();
 }
 
-// The A operand of one (frame, row tile): rows q of the sampled rows
-// rows[r0 + 64 rt ..] (fewer than 64 at the end: zero rows), every chunk of
-// 16 values of j (j >= Ny: zero columns), hi then lo, in the operand layout.
-void objective_tc_build_a(int Ny, const int* rows, int count, unsigned char* out) {
-  const int nk = (Ny + kTcJc - 1) / kTcJc;
+// The twiddles exp(-2 pi i d / Ny) 2^12 / sqrt(Ny), d = 0..Ny-1, each part split
+// into an FP16 pair from FP64: x = (hi re, hi im), y = (lo re, lo im), the
+// low half of each word the real part.
+void objective_tc_twiddle(int Ny, uint2* out) {
   const double scl = 4096.0 / std::sqrt((double)Ny);
-  std::vector<double> cs((size_t)Ny), sn((size_t)Ny);   // exp(-2 pi i d / Ny)
+  auto bits = [](__half h) { return (uint32_t)__half_as_ushort(h); };
   for (int d = 0; d < Ny; ++d) {
     const double a = -2.0 * M_PI * (double)d / (double)Ny;
-    cs[d] = std::cos(a) * scl;
-    sn[d] = std::sin(a) * scl;
-  }
-  for (int kc = 0; kc < nk; ++kc) {
-    unsigned char* hi = out + (size_t)kc * 2 * kTcAHalf;
-    unsigned char* lo = hi + kTcAHalf;
-    for (int r = 0; r < kTcM; ++r) {
-      const int m = r & (kTcRows - 1);
-      const bool imrow = r >= kTcRows;
-      for (int k = 0; k < kTcKc; ++k) {
-        const int j = kc * kTcJc + k / 2;
-        double v = 0.0;
-        if (m < count && j < Ny) {
-          const size_t d = (size_t)(((long long)rows[m] * j) % Ny);
-          const double fr = cs[d], fi = sn[d];
-          // D rows: Re C = Re F Re u - Im F Im u;  Im C = Im F Re u + Re F Im u
-          v = imrow ? ((k & 1) ? fr : fi) : ((k & 1) ? -fi : fr);
-        }
-        const __half h = __double2half(v);
-        const __half l = __double2half(v - (double)__half2float(h));
-        const size_t o = (size_t)((k / 8) * (kTcM / 8) + r / 8) * 128 + (r % 8) * 16 + (k % 8) * 2;
-        *reinterpret_cast<__half*>(hi + o) = h;
-        *reinterpret_cast<__half*>(lo + o) = l;
-      }
-    }
+    const double fr = std::cos(a) * scl, fi = std::sin(a) * scl;
+    const __half hr = __double2half(fr), hi = __double2half(fi);
+    const __half lr = __double2half(fr - (double)__half2float(hr)), li = __double2half(fi - (double)__half2float(hi));
+    out[d] = make_uint2(bits(hr) | (bits(hi) << 16), bits(lr) | (bits(li) << 16));
   }
 }
 
@@ -560,8 +533,14 @@ bool objective_tc_prepare(ObjTcParams& q, const float2* x, const float2* sens) {
   // image columns spanned by a tile of 256 columns (i, c)
   q.ni = std::min(Nx, std::min(256, (kTcN - 1) / Nc + 2));
   q.raw_bytes = kTcRawS + ((q.ni * kTcRawRow + 1023) / 1024) * 1024;
-  q.raw_depth = tc_smem_bytes(3, q.raw_bytes) <= (size_t)kTcSmemMax - 1024 ? 3 : 2;
-  if (tc_smem_bytes(q.raw_depth, q.raw_bytes) > (size_t)kTcSmemMax - 1024) return false;
+  // the deepest rings that fit: three operand stages first (they hide the MMAs' completion
+  // latency), then a third raw stage
+  const size_t cap = (size_t)kTcSmemMax - 1024;   // the static shared memory's share
+  q.op_stages = 0;
+  for (int S : {3, 2})
+    for (int D : {3, 2})
+      if (!q.op_stages && tc_smem_bytes(S, D, q.raw_bytes, Ny) <= cap) { q.op_stages = S; q.raw_depth = D; }
+  if (!q.op_stages) return false;
   q.nk = (Ny + kTcJc - 1) / kTcJc;
   q.x = x;
   EncodeTiledFn enc = encode_tiled_fn();
@@ -593,8 +572,9 @@ cudaError_t launch_objective_tc(const ObjTcParams& p, cudaStream_t s) {
   const void* fn[3] = {reinterpret_cast<const void*>(k_objective_tc<float2>),
                        reinterpret_cast<const void*>(k_objective_tc<__half2>),
                        reinterpret_cast<const void*>(k_objective_tc<__nv_bfloat162>)};
-  if (p.ystorage < 0 || p.ystorage > 2 || p.raw_depth < 2 || p.raw_depth > 3) return cudaErrorInvalidValue;
-  const size_t smem = tc_smem_bytes(p.raw_depth, p.raw_bytes);
+  if (p.ystorage < 0 || p.ystorage > 2 || p.raw_depth < 2 || p.raw_depth > 3 || p.op_stages < 2 || p.op_stages > 3)
+    return cudaErrorInvalidValue;
+  const size_t smem = tc_smem_bytes(p.op_stages, p.raw_depth, p.raw_bytes, p.Ny);
   cudaError_t e = cache[p.ystorage].ensure(fn[p.ystorage], smem);
   if (e != cudaSuccess) return e;
   if ((e = launch_col_absmax(p.x, p.Nt * p.Nx, p.Ny, p.xmax, s)) != cudaSuccess) return e;

@@ -117,7 +117,8 @@ struct recon_plan {
                                        // spatio-temporal: m_{K-1}, copied before the last m-update
   float2* res_d1 = nullptr;            // spatio-temporal: d1_{K-1} (4 components), kept by that iteration
   // explicit objective on the tensor cores (16-bit storage; objective_tc.cu)
-  void* tc_A = nullptr;                // operand tiles of every (frame, 64 sampled rows)
+  int* tc_rows = nullptr;              // [row tiles][64] sampled rows of every (frame, row tile)
+  uint2* tc_twiddle = nullptr;         // [Ny] DFT twiddles as FP16 pairs
   int4* tc_items = nullptr;
   int tc_nitems = 0;                   // 0: the FFT kernels form the explicit objective
   float* tc_smax = nullptr;            // [Nx * Nc]
