@@ -54,3 +54,37 @@ def test_tensor_core_objective_matches_oracle(shape, prior):
     Jr = np.array(oinfo["J"])
     assert rel(x.cpu().numpy().astype(np.complex128), xr) < TOL
     assert np.max(np.abs(J - Jr) / Jr) < TOL
+
+
+def test_dispatch_tensor_cores_for_even_ny_only():
+    """16-bit plans form J(k) on the tensor cores for even Ny: two launches an
+    iteration (the scales' max |x| pass and k_objective_tc) where the FFT form
+    for odd Ny takes one, everything else being equal; the autotuner reports
+    the tensor-core form's one shape (objective_coils = 1)."""
+    from paper_1203_4587_gb300 import Plan
+    from paper_1203_4587_gb300.binding import kernel_launches
+
+    def per_iteration(Ny):
+        c = synthdata.make_case("tiny", Nx=24, Ny=Ny, Nt=4, Nc=8, R=3, iters=4)
+        sens = torch.from_numpy(c.sens.astype(np.complex64)).cuda()
+        k = torch.from_numpy(c.kspace.astype(np.complex64)).cuda()
+        n = []
+        for K in (2, 4):
+            P = Plan(c.mask.astype(np.uint8), sens, c.lam, c.mu, prior="tv", rho=c.rho, max_iters=K, storage="fp16")
+            P.solve(k)
+            torch.cuda.synchronize()
+            n0 = kernel_launches()
+            P.solve(k)
+            torch.cuda.synchronize()
+            n.append(kernel_launches() - n0)
+            if K == 4:
+                t = P.autotune()
+                assert t.objective_ms > 0
+                coils = t.objective_coils
+            P.close()
+        return (n[1] - n[0]) / 2, coils
+
+    even, coils_even = per_iteration(40)
+    odd, _ = per_iteration(33)
+    assert even == odd + 1
+    assert coils_even == 1
